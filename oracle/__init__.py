@@ -1,0 +1,254 @@
+"""FP64 oracle for the LArTPC signal-simulation hot path (arXiv 2203.02479).
+
+TEST INFRASTRUCTURE ONLY: the tests, the package's ``smoke()`` check and the
+benchmark's CPU-baseline leg may import this package; the product path never
+does.  It shares no code with the CUDA library: the per-depo loops are plain
+C in ``wsoracle.c`` (compiled here with gcc on first use), the convolution of
+Eq. 2 uses numpy's FFT in double precision, and Eq. 1's direct sum is in C.
+
+Every function is pinned by ``tests/test_oracle_pins.py`` against something
+other than itself; the pins are listed in each docstring.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import sys
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "wsoracle.c")
+_SO = os.path.join(_HERE, "_wsoracle.so")
+_lock = threading.Lock()
+_handle = None
+
+_f32p = np.ctypeslib.ndpointer(np.float32, flags="C_CONTIGUOUS")
+_f64p = np.ctypeslib.ndpointer(np.float64, flags="C_CONTIGUOUS")
+_i32p = np.ctypeslib.ndpointer(np.int32, flags="C_CONTIGUOUS")
+_u32p = np.ctypeslib.ndpointer(np.uint32, flags="C_CONTIGUOUS")
+
+
+def build(force: bool = False) -> str:
+    """Compile ``wsoracle.c`` into ``_wsoracle.so`` with gcc (plain -O2, libm)."""
+    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
+        tmp = _SO + f".{os.getpid()}.tmp"
+        cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fno-fast-math",
+               "-ffp-contract=off", "-o", tmp, _SRC, "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _SO)
+    return _SO
+
+
+def _lib():
+    global _handle
+    with _lock:
+        if _handle is None:
+            build()
+            h = ctypes.CDLL(_SO)
+            h.wso_philox4x32_10.argtypes = [_u32p, _u32p, _u32p]
+            h.wso_philox4x32_10.restype = None
+            h.wso_sigmas.argtypes = [ctypes.c_int64, _f32p, ctypes.c_double, ctypes.c_double,
+                                     ctypes.c_double, _f64p, _f64p]
+            h.wso_sigmas.restype = None
+            h.wso_axis_weights.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                           ctypes.c_double, ctypes.c_int,
+                                           ctypes.POINTER(ctypes.c_int64), _f64p]
+            h.wso_axis_weights.restype = ctypes.c_int
+            h.wso_survive_threshold.argtypes = [ctypes.c_double]
+            h.wso_survive_threshold.restype = ctypes.c_uint32
+            h.wso_binomial.argtypes = [ctypes.c_int64, ctypes.c_double, ctypes.c_int, _u32p,
+                                       ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32]
+            h.wso_binomial.restype = ctypes.c_int64
+            opt_f32 = ctypes.c_void_p
+            h.wso_raster_scatter.argtypes = [
+                ctypes.c_int64, _f32p, _f32p, _f32p, opt_f32, opt_f32,
+                ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                ctypes.c_int, ctypes.c_double, ctypes.c_uint64, ctypes.c_uint32,
+                ctypes.c_uint32, ctypes.c_int, _f64p]
+            h.wso_raster_scatter.restype = ctypes.c_int64
+            h.wso_patch_extents.argtypes = [
+                ctypes.c_int64, _f32p, _f32p, opt_f32, opt_f32,
+                ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                _i32p, _i32p, _i32p, _i32p]
+            h.wso_patch_extents.restype = ctypes.c_int64
+            h.wso_convolve_direct.argtypes = [_f64p, ctypes.c_int, ctypes.c_int, _f32p,
+                                              ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                              ctypes.c_int, _f64p]
+            h.wso_convolve_direct.restype = None
+            h.wso_convolve_points.argtypes = [_f64p, ctypes.c_int, ctypes.c_int, _f32p,
+                                              ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                              ctypes.c_int, ctypes.c_int64, _i32p, _i32p, _f64p]
+            h.wso_convolve_points.restype = None
+            _handle = h
+    return _handle
+
+
+# ----------------------------------------------------------------- defaults
+PITCH_MM = 5.0
+TICK_US = 0.5
+NSIGMA = 3.0
+DL = 4.0e-4
+DT = 8.8e-4
+V = 1.6
+EXACT_MAX = 32
+
+
+def _c32(a):
+    return np.ascontiguousarray(np.asarray(a, dtype=np.float32))
+
+
+def _opt_ptr(a):
+    return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+
+
+# ------------------------------------------------------------------- Philox
+def philox(ctr, key) -> np.ndarray:
+    """Philox4x32-10 block for a 4-word counter and 2-word key (SC'11).
+
+    Pinned against cuRAND's host Philox4_32_10 generator."""
+    c = np.ascontiguousarray(np.asarray(ctr, dtype=np.uint32).reshape(4))
+    k = np.ascontiguousarray(np.asarray(key, dtype=np.uint32).reshape(2))
+    out = np.zeros(4, dtype=np.uint32)
+    _lib().wso_philox4x32_10(c, k, out)
+    return out
+
+
+def seed_key(seed: int) -> np.ndarray:
+    return np.array([seed & 0xFFFFFFFF, (seed >> 32) & 0xFFFFFFFF], dtype=np.uint32)
+
+
+def survive_threshold(p: float) -> int:
+    return int(_lib().wso_survive_threshold(float(p)))
+
+
+def binomial(N: int, p: float, seed: int, bin_index: int, depo: int, event_id: int = 0,
+             plane_id: int = 0, exact_max: int = EXACT_MAX) -> int:
+    """Binomial(N, p) survivor count of one bin (Sec. 3.1 reading).
+
+    Pinned by chi-square against scipy.stats.binom (exact branch) and by the
+    first two moments (normal branch)."""
+    key = seed_key(seed)
+    evpl = ((event_id << 4) | (plane_id & 15)) & 0xFFFFFFFF
+    return int(_lib().wso_binomial(int(N), float(p), int(exact_max), key,
+                                   bin_index & 0xFFFFFFFF, depo & 0xFFFFFFFF, evpl))
+
+
+# ---------------------------------------------------------------- diffusion
+def sigmas(t_us, DL_: float = DL, DT_: float = DT, v: float = V):
+    """sigma_L [us] = sqrt(2 D_L t)/v and sigma_T [mm] = sqrt(2 D_T t) (Sec. 2.2).
+
+    Pinned by closed-form values."""
+    t = _c32(t_us)
+    st = np.zeros(t.shape[0]); sx = np.zeros(t.shape[0])
+    _lib().wso_sigmas(t.shape[0], t, DL_, DT_, v, st, sx)
+    return st, sx
+
+
+def axis_weights(mu: float, sigma: float, delta: float, nsig: float = NSIGMA):
+    """(first bin, weights) of a truncated, binned 1D Gaussian (Sec. 2.2).
+
+    Pinned against Gauss-Legendre quadrature of the Gaussian density."""
+    lo = ctypes.c_int64(0)
+    cap = 1 << 16
+    w = np.zeros(cap)
+    n = _lib().wso_axis_weights(float(mu), float(sigma), float(delta), float(nsig), cap,
+                                ctypes.byref(lo), w)
+    if n < 0:
+        raise ValueError("patch too large for the oracle")
+    return int(lo.value), w[:n].copy()
+
+
+# ------------------------------------------------------------ raster+scatter
+def raster_scatter(q, x_mm, t_us, nwires: int, nticks: int, *, sig_t_us=None, sig_x_mm=None,
+                   pitch_mm: float = PITCH_MM, tick_us: float = TICK_US, nsig: float = NSIGMA,
+                   DL_: float = DL, DT_: float = DT, v: float = V, fluctuate: bool = False,
+                   p: float = 1.0, seed: int = 0, event_id: int = 0, plane_id: int = 0,
+                   exact_max: int = EXACT_MAX, return_skipped: bool = False):
+    """Raster every depo into its patch and scatter-add into S[wire][tick] (FP64).
+
+    Sec. 2.2 (raster, scatter-add), Sec. 3.1 (binomial fluctuation).  Pinned
+    by patch sums (closed form), linearity and the pins of its parts."""
+    q = _c32(q); x = _c32(x_mm); t = _c32(t_us)
+    st = None if sig_t_us is None else _c32(sig_t_us)
+    sx = None if sig_x_mm is None else _c32(sig_x_mm)
+    S = np.zeros((nwires, nticks))
+    skipped = _lib().wso_raster_scatter(
+        q.shape[0], q, x, t, _opt_ptr(st), _opt_ptr(sx), nwires, nticks, pitch_mm, tick_us,
+        nsig, DL_, DT_, v, int(bool(fluctuate)), float(p), int(seed) & (2 ** 64 - 1),
+        event_id & 0xFFFFFFFF, plane_id & 0xFFFFFFFF, int(exact_max), S)
+    return (S, int(skipped)) if return_skipped else S
+
+
+def patch_extents(x_mm, t_us, nwires: int, nticks: int, *, sig_t_us=None, sig_x_mm=None,
+                  pitch_mm: float = PITCH_MM, tick_us: float = TICK_US, nsig: float = NSIGMA,
+                  DL_: float = DL, DT_: float = DT, v: float = V):
+    """Per-depo (w0, nw, t0, nt) of each patch clipped to the grid, and the bin total."""
+    x = _c32(x_mm); t = _c32(t_us)
+    n = x.shape[0]
+    st = None if sig_t_us is None else _c32(sig_t_us)
+    sx = None if sig_x_mm is None else _c32(sig_x_mm)
+    w0 = np.zeros(n, np.int32); nw = np.zeros(n, np.int32)
+    t0 = np.zeros(n, np.int32); nt = np.zeros(n, np.int32)
+    total = _lib().wso_patch_extents(n, x, t, _opt_ptr(st), _opt_ptr(sx), nwires, nticks,
+                                     pitch_mm, tick_us, nsig, DL_, DT_, v, w0, nw, t0, nt)
+    return w0, nw, t0, nt, int(total)
+
+
+# -------------------------------------------------------------- convolution
+def convolve_fft(S, R, wire_center: int, circular: bool = False) -> np.ndarray:
+    """Eq. 2: FT of S, multiply by the FT of R, inverse FT (numpy, FP64).
+
+    R[r][j] is the response at wire offset r - wire_center and tick offset j.
+    Linear mode transforms at the full linear-convolution size (nw + Kw - 1,
+    nt + Kt - 1), so nothing wraps, and keeps the grid window; circular mode
+    transforms at the grid size with the response wrapped onto it.
+
+    Pinned against the direct sum of Eq. 1 and scipy.signal.convolve2d."""
+    S = np.asarray(S, dtype=np.float64)
+    R = np.asarray(R, dtype=np.float64)
+    nw, nt = S.shape
+    kw, kt = R.shape
+    if circular:
+        Rc = np.zeros((nw, nt))
+        for r in range(kw):
+            for j in range(kt):
+                Rc[(r - wire_center) % nw, j % nt] += R[r, j]
+        return np.fft.irfft2(np.fft.rfft2(S) * np.fft.rfft2(Rc), s=(nw, nt))
+    lw, lt = nw + kw - 1, nt + kt - 1
+    full = np.fft.irfft2(np.fft.rfft2(S, s=(lw, lt)) * np.fft.rfft2(R, s=(lw, lt)), s=(lw, lt))
+    return np.ascontiguousarray(full[wire_center:wire_center + nw, :nt])
+
+
+def convolve_direct(S, R, wire_center: int, circular: bool = False) -> np.ndarray:
+    """Eq. 1 as a direct double sum (C).  Brute force for small grids."""
+    S = np.ascontiguousarray(np.asarray(S, dtype=np.float64))
+    R32 = _c32(R)
+    nw, nt = S.shape
+    M = np.zeros_like(S)
+    _lib().wso_convolve_direct(S, nw, nt, R32, R32.shape[0], R32.shape[1], int(wire_center),
+                               int(bool(circular)), M)
+    return M
+
+
+def convolve_points(S, R, wire_center: int, pw, pt, circular: bool = False) -> np.ndarray:
+    """Eq. 1's direct sum at selected output points (w[i], t[i])."""
+    S = np.ascontiguousarray(np.asarray(S, dtype=np.float64))
+    R32 = _c32(R)
+    pw = np.ascontiguousarray(np.asarray(pw, dtype=np.int32))
+    pt = np.ascontiguousarray(np.asarray(pt, dtype=np.int32))
+    out = np.zeros(pw.shape[0])
+    _lib().wso_convolve_points(S, S.shape[0], S.shape[1], R32, R32.shape[0], R32.shape[1],
+                               int(wire_center), int(bool(circular)), pw.shape[0], pw, pt, out)
+    return out
+
+
+def simulate(q, x_mm, t_us, nwires: int, nticks: int, R, wire_center: int = 10, *,
+             circular: bool = False, **kw) -> np.ndarray:
+    """The whole hot path: raster, (fluctuate), scatter-add, convolve (Eq. 2)."""
+    S = raster_scatter(q, x_mm, t_us, nwires, nticks, **kw)
+    return convolve_fft(S, R, wire_center, circular)

@@ -1,0 +1,314 @@
+/*
+ * FP64 oracle for the LArTPC signal-simulation hot path (arXiv 2203.02479).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product path links, loads or
+ * calls this file; only the tests, the package's smoke check and the
+ * benchmark's CPU-baseline leg do.  It shares no code, header, table or
+ * constant generator with the CUDA library.
+ *
+ * Plain single-threaded loops in double precision, following the method in
+ * the order the paper gives it:
+ *   - diffusion of each depo into a 2D distribution (Sec. 2.2),
+ *   - raster: binning that distribution into a patch (Sec. 2.2, "Raster"),
+ *   - optional binomial charge fluctuation (Sec. 3.1),
+ *   - scatter-add of patches into a dense wire x tick grid (Sec. 2.2,
+ *     "Scatter-add"; Sec. 2.3 dense matrix),
+ *   - the convolution of Eq. 1 written out as a direct sum (the FFT form of
+ *     Eq. 2 lives in the Python layer, on numpy's FFT).
+ * Where the paper is silent (bin edges, truncation, normalisation, the
+ * fluctuation sampler and its random stream) the readings are stated next to
+ * the code that takes them.
+ *
+ * Every function below is pinned by tests against something other than
+ * itself: Gauss-Legendre quadrature of the Gaussian (bin weights), closed
+ * forms (patch sums, delta response), cuRAND's host Philox generator (the
+ * random stream), binomial moments (the sampler) and scipy's convolve2d
+ * (the convolution).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#ifndef M_PI
+#define M_PI 3.14159265358979323846
+#endif
+
+/* ------------------------------------------------------------------------ */
+/* Philox4x32-10 counter-based generator, as defined by Salmon, Moraes, Dror
+ * and Shaw, "Parallel random numbers: as easy as 1, 2, 3" (SC'11): ten
+ * rounds of two 32x32->64 multiplies by fixed odd constants, the high halves
+ * XORed with the other two counter words and the key, the key bumped by the
+ * golden-ratio and sqrt(3)-1 Weyl constants between rounds. */
+#define WSO_PHILOX_M0 0xD2511F53u
+#define WSO_PHILOX_M1 0xCD9E8D57u
+#define WSO_PHILOX_W0 0x9E3779B9u
+#define WSO_PHILOX_W1 0xBB67AE85u
+
+void wso_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4])
+{
+    uint32_t x0 = ctr[0], x1 = ctr[1], x2 = ctr[2], x3 = ctr[3];
+    uint32_t k0 = key[0], k1 = key[1];
+    for (int r = 0; r < 10; ++r) {
+        if (r > 0) { k0 += WSO_PHILOX_W0; k1 += WSO_PHILOX_W1; }
+        uint64_t p0 = (uint64_t)WSO_PHILOX_M0 * (uint64_t)x0;
+        uint64_t p1 = (uint64_t)WSO_PHILOX_M1 * (uint64_t)x2;
+        uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+        uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+        uint32_t y0 = hi1 ^ x1 ^ k0;
+        uint32_t y1 = lo1;
+        uint32_t y2 = hi0 ^ x3 ^ k1;
+        uint32_t y3 = lo0;
+        x0 = y0; x1 = y1; x2 = y2; x3 = y3;
+    }
+    out[0] = x0; out[1] = x1; out[2] = x2; out[3] = x3;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Diffusion along the drift (Sec. 2.2): longitudinal width in time
+ * sigma_L = sqrt(2 D_L t) / v, transverse width in pitch sigma_T =
+ * sqrt(2 D_T t).  Units: mm, microseconds. */
+void wso_sigmas(int64_t n, const float* t_us, double DL, double DT, double v,
+                double* sig_t_us, double* sig_x_mm)
+{
+    for (int64_t i = 0; i < n; ++i) {
+        double t = (double)t_us[i];
+        sig_t_us[i] = sqrt(2.0 * DL * t) / v;
+        sig_x_mm[i] = sqrt(2.0 * DT * t);
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Raster along one axis (Sec. 2.2, "Raster").
+ *
+ * Readings (the paper only says each distribution is "binned"):
+ *   - bin k covers [k*delta, (k+1)*delta);
+ *   - the Gaussian is truncated to [mu - nsig*sigma, mu + nsig*sigma] and
+ *     the bins overlapping that window form the patch;
+ *   - each bin's weight is the Gaussian mass on the bin clipped to the
+ *     window, Phi(b) - Phi(a) = (erf(b') - erf(a'))/2, divided by the
+ *     window's total mass erf(nsig/sqrt 2), so the weights sum to one;
+ *   - sigma <= 1e-6*delta is a point charge: weight 1 in floor(mu/delta).
+ * Returns the number of bins n and writes lo (first bin) and w[0..n);
+ * w must hold at least maxn values; returns -1 if n > maxn. */
+int wso_axis_weights(double mu, double sigma, double delta, double nsig,
+                     int maxn, int64_t* lo, double* w)
+{
+    if (!(sigma > 1e-6 * delta)) {
+        *lo = (int64_t)floor(mu / delta);
+        if (maxn < 1) return -1;
+        w[0] = 1.0;
+        return 1;
+    }
+    double a = mu - nsig * sigma, b = mu + nsig * sigma;
+    int64_t klo = (int64_t)floor(a / delta), khi = (int64_t)floor(b / delta);
+    int64_t n = khi - klo + 1;
+    if (n > maxn) return -1;
+    double norm = erf(nsig / sqrt(2.0));
+    double s2 = sqrt(2.0) * sigma;
+    for (int64_t k = klo; k <= khi; ++k) {
+        double e0 = fmax((double)k * delta, a);
+        double e1 = fmin((double)(k + 1) * delta, b);
+        w[k - klo] = 0.5 * (erf((e1 - mu) / s2) - erf((e0 - mu) / s2)) / norm;
+    }
+    *lo = klo;
+    return (int)n;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Binomial charge fluctuation (Sec. 3.1: the CPU reference draws binomial
+ * numbers).  Reading: each bin holds N = floor(q*w + 1/2) electrons, each
+ * surviving independently with probability p; the bins draw independently
+ * from Philox keyed by the seed, with the counter (block j, global bin,
+ * depo index, event << 4 | plane).
+ *   - N <= exact_max: k = number of i < N whose 32-bit word i (word i%4 of
+ *     block i/4) is below T = floor(p * 2^32); integer-only.
+ *   - N > exact_max: normal approximation from block 0,
+ *     u1 = (x0 + 1/2)/2^32, u2 = (x1 + 1/2)/2^32,
+ *     z = sqrt(-2 ln u1) cos(2 pi u2),
+ *     k = clamp(floor(N p + z sqrt(N p (1 - p)) + 1/2), 0, N), p = T/2^32.
+ *   - p >= 1 keeps every electron, p <= 0 none. */
+uint32_t wso_survive_threshold(double p)
+{
+    if (!(p > 0.0)) return 0u;
+    if (p >= 1.0) return 0xFFFFFFFFu;
+    return (uint32_t)floor(p * 4294967296.0);
+}
+
+int64_t wso_binomial(int64_t N, double p, int exact_max, const uint32_t key[2],
+                     uint32_t bin, uint32_t depo, uint32_t evpl)
+{
+    if (N <= 0) return 0;
+    if (!(p > 0.0)) return 0;
+    if (p >= 1.0) return N;
+    uint32_t T = wso_survive_threshold(p);
+    uint32_t ctr[4], x[4];
+    if (N <= exact_max) {
+        int64_t k = 0;
+        for (int64_t i = 0; i < N; ++i) {
+            if (i % 4 == 0) {
+                ctr[0] = (uint32_t)(i / 4); ctr[1] = bin; ctr[2] = depo; ctr[3] = evpl;
+                wso_philox4x32_10(ctr, key, x);
+            }
+            if (x[i % 4] < T) ++k;
+        }
+        return k;
+    }
+    ctr[0] = 0; ctr[1] = bin; ctr[2] = depo; ctr[3] = evpl;
+    wso_philox4x32_10(ctr, key, x);
+    double u1 = ((double)x[0] + 0.5) / 4294967296.0;
+    double u2 = ((double)x[1] + 0.5) / 4294967296.0;
+    double z = sqrt(-2.0 * log(u1)) * cos(2.0 * M_PI * u2);
+    double pe = (double)T / 4294967296.0;
+    double mean = (double)N * pe;
+    double k = floor(mean + z * sqrt(mean * (1.0 - pe)) + 0.5);
+    if (k < 0.0) k = 0.0;
+    if (k > (double)N) k = (double)N;
+    return (int64_t)k;
+}
+
+/* ------------------------------------------------------------------------ */
+/* One plane's raster + fluctuation + scatter-add (Sec. 2.2).  Depos are
+ * processed one by one; each patch bin inside the nwires x nticks grid is
+ * added into S (row-major [wire][tick], double).  Bins outside the grid are
+ * dropped: charge leaving the readout is lost.  A depo with a non-finite
+ * input or negative drift time contributes nothing and is counted in the
+ * return value.
+ *
+ * sig_t_us / sig_x_mm may be NULL, in which case they come from diffusion.
+ * If fluctuate == 0 a bin receives the expected value p*q*w_t*w_x; else it
+ * receives a binomial count (see wso_binomial). */
+#define WSO_MAXBINS 65536
+
+int64_t wso_raster_scatter(int64_t n, const float* q, const float* x_mm, const float* t_us,
+                           const float* sig_t_us, const float* sig_x_mm,
+                           int nwires, int nticks, double pitch_mm, double tick_us,
+                           double nsig, double DL, double DT, double v,
+                           int fluctuate, double p, uint64_t seed, uint32_t event_id,
+                           uint32_t plane_id, int exact_max, double* S)
+{
+    double* wt = (double*)malloc(sizeof(double) * WSO_MAXBINS);
+    double* wx = (double*)malloc(sizeof(double) * WSO_MAXBINS);
+    uint32_t key[2] = {(uint32_t)(seed & 0xFFFFFFFFu), (uint32_t)(seed >> 32)};
+    uint32_t evpl = (event_id << 4) | (plane_id & 15u);
+    int64_t skipped = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        double qi = q[i], xi = x_mm[i], ti = t_us[i];
+        double st, sx;
+        if (sig_t_us) { st = sig_t_us[i]; sx = sig_x_mm[i]; }
+        else { st = sqrt(2.0 * DL * ti) / v; sx = sqrt(2.0 * DT * ti); }
+        if (!isfinite(qi) || !isfinite(xi) || !isfinite(ti) || !isfinite(st) || !isfinite(sx) ||
+            st < 0.0 || sx < 0.0) { ++skipped; continue; }
+        int64_t klo, wlo;
+        int nt = wso_axis_weights(ti, st, tick_us, nsig, WSO_MAXBINS, &klo, wt);
+        int nw = wso_axis_weights(xi, sx, pitch_mm, nsig, WSO_MAXBINS, &wlo, wx);
+        if (nt < 0 || nw < 0) { ++skipped; continue; }
+        for (int a = 0; a < nw; ++a) {
+            int64_t w = wlo + a;
+            if (w < 0 || w >= nwires) continue;
+            for (int b = 0; b < nt; ++b) {
+                int64_t k = klo + b;
+                if (k < 0 || k >= nticks) continue;
+                double val;
+                if (fluctuate) {
+                    int64_t N = (int64_t)floor(qi * wt[b] * wx[a] + 0.5);
+                    uint32_t bin = (uint32_t)(w * (int64_t)nticks + k);
+                    val = (double)wso_binomial(N, p, exact_max, key, bin, (uint32_t)i, evpl);
+                } else {
+                    val = p * qi * wt[b] * wx[a];
+                }
+                S[w * (int64_t)nticks + k] += val;
+            }
+        }
+    }
+    free(wt); free(wx);
+    return skipped;
+}
+
+/* Per-depo patch extents, clipped to the grid (for comparing patch lists).
+ * Writes w0, nw, t0, nt per depo (nw = nt = 0 for an empty or skipped
+ * patch).  Returns the total number of in-grid bins. */
+int64_t wso_patch_extents(int64_t n, const float* x_mm, const float* t_us,
+                          const float* sig_t_us, const float* sig_x_mm,
+                          int nwires, int nticks, double pitch_mm, double tick_us,
+                          double nsig, double DL, double DT, double v,
+                          int32_t* w0, int32_t* nw, int32_t* t0, int32_t* nt)
+{
+    double* tmp = (double*)malloc(sizeof(double) * WSO_MAXBINS);
+    int64_t total = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        double xi = x_mm[i], ti = t_us[i];
+        double st, sx;
+        if (sig_t_us) { st = sig_t_us[i]; sx = sig_x_mm[i]; }
+        else { st = sqrt(2.0 * DL * ti) / v; sx = sqrt(2.0 * DT * ti); }
+        w0[i] = nw[i] = t0[i] = nt[i] = 0;
+        if (!isfinite(xi) || !isfinite(ti) || !isfinite(st) || !isfinite(sx) || st < 0 || sx < 0)
+            continue;
+        int64_t klo, wlo;
+        int ntt = wso_axis_weights(ti, st, tick_us, nsig, WSO_MAXBINS, &klo, tmp);
+        int nww = wso_axis_weights(xi, sx, pitch_mm, nsig, WSO_MAXBINS, &wlo, tmp);
+        if (ntt < 0 || nww < 0) continue;
+        int64_t a0 = wlo < 0 ? 0 : wlo, a1 = wlo + nww > nwires ? nwires : wlo + nww;
+        int64_t b0 = klo < 0 ? 0 : klo, b1 = klo + ntt > nticks ? nticks : klo + ntt;
+        if (a1 <= a0 || b1 <= b0) continue;
+        w0[i] = (int32_t)a0; nw[i] = (int32_t)(a1 - a0);
+        t0[i] = (int32_t)b0; nt[i] = (int32_t)(b1 - b0);
+        total += (a1 - a0) * (b1 - b0);
+    }
+    free(tmp);
+    return total;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Eq. 1 written out: M(t, x) = sum over t', x' of R(t - t', x - x') S(t', x')
+ * on the discrete grid.  R is resp_nw x resp_nt (row-major [wire][tick]);
+ * response row r holds wire offset d = r - wire_center, column j holds tick
+ * offset j (causal).  circular == 0: S is zero outside the grid and M is
+ * kept on the grid; circular != 0: indices wrap modulo the grid (the
+ * literal discrete form of Eq. 2). */
+void wso_convolve_direct(const double* S, int nwires, int nticks,
+                         const float* R, int resp_nw, int resp_nt, int wire_center,
+                         int circular, double* M)
+{
+    for (int64_t w = 0; w < nwires; ++w) {
+        for (int64_t t = 0; t < nticks; ++t) {
+            double acc = 0.0;
+            for (int r = 0; r < resp_nw; ++r) {
+                int64_t ws = w - (r - wire_center);
+                if (circular) { ws %= nwires; if (ws < 0) ws += nwires; }
+                else if (ws < 0 || ws >= nwires) continue;
+                for (int j = 0; j < resp_nt; ++j) {
+                    int64_t ts = t - j;
+                    if (circular) { ts %= nticks; if (ts < 0) ts += nticks; }
+                    else if (ts < 0) break;
+                    acc += (double)R[r * resp_nt + j] * S[ws * nticks + ts];
+                }
+            }
+            M[w * nticks + t] = acc;
+        }
+    }
+}
+
+/* The same sum at selected output points only (w[i], t[i]). */
+void wso_convolve_points(const double* S, int nwires, int nticks,
+                         const float* R, int resp_nw, int resp_nt, int wire_center,
+                         int circular, int64_t npts, const int32_t* pw, const int32_t* pt,
+                         double* out)
+{
+    for (int64_t i = 0; i < npts; ++i) {
+        int64_t w = pw[i], t = pt[i];
+        double acc = 0.0;
+        for (int r = 0; r < resp_nw; ++r) {
+            int64_t ws = w - (r - wire_center);
+            if (circular) { ws %= nwires; if (ws < 0) ws += nwires; }
+            else if (ws < 0 || ws >= nwires) continue;
+            for (int j = 0; j < resp_nt; ++j) {
+                int64_t ts = t - j;
+                if (circular) { ts %= nticks; if (ts < 0) ts += nticks; }
+                else if (ts < 0) break;
+                acc += (double)R[r * resp_nt + j] * S[ws * nticks + ts];
+            }
+        }
+        out[i] = acc;
+    }
+}
