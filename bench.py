@@ -1,0 +1,395 @@
+#!/usr/bin/env python
+"""Throughput of the signal-simulation hot path on one GB300 (or N, weak scaling).
+
+A step simulates one event on the three-plane detector (800/800/960 wires x
+6000 ticks, 100,000 track depos, binomial fluctuation with survival 0.7):
+for every plane, diffusion + raster + fluctuation + scatter-add into the
+grid, then the FFT convolution with that plane's response.  The metric is
+depos per second through the whole path (a depo counts once per plane it is
+simulated on), with planes per second and the raster+scatter-only rate
+reported beside it.
+
+Prints ONE JSON line (rank 0).  ``--impl reference`` times the FP64 oracle
+on the host cores instead (the CPU baseline arm).
+
+Timing: W untimed warm-up steps; then K steps, each bracketed by CUDA events
+on the launching stream, with L2 flushed (a 512 MiB write) between steps,
+outside the events; barrier + synchronize on both sides; the max over ranks.
+Per-kernel device times come from the library's own launch trace (CUDA
+events around every launch, on the same stream) over the same timed steps.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2203_02479_gb300 import inputs  # noqa: E402
+
+METRIC = "depos/sec and planes/sec (raster+scatter+FFT conv) at 1 GB300; % of HBM roofline"
+UNIT = "depos/s"
+FP32_LANES_PER_SM = 128
+NUM_SMS_GB300 = 152
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), float(p.get("sm_max_mhz", 2070.0)), "measured"
+    except Exception:
+        return 6800.0, 2070.0, "fallback"
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.proc = None
+        self.tmp = tempfile.NamedTemporaryFile(prefix="clocks_", suffix=".csv", delete=False)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(gpu_index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=self.tmp, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.tmp.close()
+        rows = []
+        with open(self.tmp.name) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.tmp.name)
+        if not rows:
+            return None
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+
+        sm = [num(r[1]) for r in rows if num(r[1]) is not None]
+        mx = [num(r[2]) for r in rows if num(r[2]) is not None]
+        reasons = set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for r in rows:
+            for name, v in zip(names, r[5:9]):
+                if v.strip().lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(rows)}
+
+
+# ------------------------------------------------------------ distributed
+def _dist():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def _init_pg(world, backend):
+    if world <= 1:
+        return None
+    import torch.distributed as dist
+    dist.init_process_group(backend=backend)
+    return dist
+
+
+def _barrier(dist):
+    if dist is not None:
+        dist.barrier()
+
+
+def _max_over_ranks(dist, value: float, device) -> float:
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def _sum_over_ranks(dist, value: float, device) -> float:
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+# -------------------------------------------------------------- workloads
+def make_workload(name: str, rank: int):
+    if name == "three_planes":
+        return inputs.three_planes(seed=1001 + 7919 * rank)
+    if name == "single_plane":
+        return inputs.single_plane(seed=1000 + 7919 * rank)
+    raise SystemExit(f"unknown workload {name}")
+
+
+def algorithmic_bytes(kernel: str, nw: int, nt: int, nfreq: int, kw: int, ndepo: int) -> float:
+    """Bytes a kernel's step must move at minimum (inputs read once, outputs
+    written once), per launch on one plane."""
+    spec = 8.0 * nfreq * nw
+    if kernel == "raster_scatter":
+        return 12.0 * ndepo + 4.0 * nw * nt
+    if kernel == "fwd_rows":
+        return 4.0 * nw * nt + spec
+    if kernel == "wire_conv":
+        return 2.0 * spec + 8.0 * nfreq * kw
+    if kernel == "inv_rows":
+        return spec + 4.0 * nw * nt
+    if kernel == "memset_grid":
+        return 4.0 * nw * nt
+    return 0.0
+
+
+# ------------------------------------------------------------------ oracle
+_ORACLE_NEXT = [0]
+
+
+def oracle_sample(w, budget_s: float):
+    """Run the FP64 oracle over the workload's planes (cycling through them
+    across calls) for about budget_s seconds, at least one plane; returns
+    (depo-planes processed, seconds, planes)."""
+    import oracle
+    done = 0
+    planes = 0
+    t0 = time.perf_counter()
+    while True:
+        i = _ORACLE_NEXT[0]
+        _ORACLE_NEXT[0] += 1
+        sp = w.planes[i % len(w.planes)]
+        d = w.events[0][i % len(w.planes)]
+        S = oracle.raster_scatter(d.q, d.x_mm, d.t_us, sp.nwires, sp.nticks, fluctuate=w.fluctuate,
+                                  p=w.p_survive, seed=w.seed, plane_id=sp.plane_id)
+        oracle.convolve_fft(S, sp.response, 10)
+        done += d.n
+        planes += 1
+        if time.perf_counter() - t0 >= budget_s:
+            break
+    return done, time.perf_counter() - t0, planes
+
+
+def run_reference(args):
+    world, rank, _ = _dist()
+    if rank != 0:
+        return
+    w = make_workload(args.workload, 0)
+    for _ in range(args.warmup):
+        oracle_sample(w, 0.0)
+    t0 = time.perf_counter()
+    done = 0
+    planes = 0
+    for _ in range(args.steps):
+        d, _, p = oracle_sample(w, 0.0)   # one plane per step
+        done += d
+        planes += p
+    dt = time.perf_counter() - t0
+    value = done / dt
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": w.name, "sample": "one plane of the event per step (cycling U, V, W)",
+                   "depos_per_plane": w.events[0][0].n},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"{args.steps} steps x one plane of {w.events[0][0].n} depos"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "planes_per_s": planes / dt,
+    }
+    print(json.dumps(line), flush=True)
+
+
+# -------------------------------------------------------------------- main
+def run_gpu(args):
+    import torch
+    from paper_2203_02479_gb300 import wiresim
+
+    world, rank, local = _dist()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = _init_pg(world, "nccl")
+    wiresim.load_library()
+
+    w = make_workload(args.workload, rank)
+    ev = w.events[0]
+    planes = [wiresim.Plane(sp.nwires, sp.nticks, sp.response, plane_id=sp.plane_id, device=dev)
+              for sp in w.planes]
+    depos = [wiresim.DeviceDepos.from_plane_depos(d, device=dev) for d in ev]
+    outs = [torch.empty((sp.nwires, sp.nticks), dtype=torch.float32, device=dev) for sp in w.planes]
+    params = wiresim.Params(fluctuate=w.fluctuate, p_survive=w.p_survive, seed=w.seed, event_id=rank)
+    ndepo_planes = sum(d.n for d in ev)
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device=dev)
+
+    def step():
+        for pl, dd, o in zip(planes, depos, outs):
+            pl.simulate(dd, params, out=o, stream=stream)
+
+    for _ in range(max(args.warmup, 0)):
+        step()
+    torch.cuda.synchronize(dev)
+
+    for pl in planes:
+        pl.trace(args.steps * 8 + 16)
+    sampler = ClockSampler(local) if local == 0 else None
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    _barrier(dist)
+    torch.cuda.synchronize(dev)
+    for i in range(args.steps):
+        flush.zero_()
+        starts[i].record(stream)
+        step()
+        ends[i].record(stream)
+    torch.cuda.synchronize(dev)
+    _barrier(dist)
+    clocks = sampler.stop() if sampler else None
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    total_ms = _max_over_ranks(dist, float(sum(step_ms)), dev)
+
+    # per-kernel device times from the launch trace over the timed steps
+    kern = {}
+    kbytes = {}
+    for pl, sp, d in zip(planes, w.planes, ev):
+        stats = pl.trace_read()
+        pl.trace(0)
+        for name, (n, ms) in stats.items():
+            a = kern.setdefault(name, [0, 0.0])
+            a[0] += n
+            a[1] += ms
+            kbytes[name] = kbytes.get(name, 0.0) + n * algorithmic_bytes(
+                name, sp.nwires, sp.nticks, pl.info.nfreq, sp.response.shape[0], d.n)
+    launches = sum(n for name, (n, _) in kern.items() if name != "memset_grid")
+    dominant = max((k for k in kern if k != "memset_grid"), key=lambda k: kern[k][1])
+    dn, dms = kern[dominant]
+    peak_gbs, sm_max, peak_src = _peaks()
+    achieved = kbytes[dominant] / dn / (dms / dn * 1e-3) / 1e9
+    raster_ms = kern.get("raster_scatter", [0, 0.0])[1] + kern.get("memset_grid", [0, 0.0])[1]
+
+    # end to end through the public API with host buffers
+    e2e = None
+    if not args.no_e2e:
+        host_in = [[torch.from_numpy(a).pin_memory() for a in (d.q, d.x_mm, d.t_us)] for d in ev]
+        host_out = [torch.empty((sp.nwires, sp.nticks), dtype=torch.float32).pin_memory() for sp in w.planes]
+        dev_in = [[torch.empty_like(a, device=dev) for a in trip] for trip in host_in]
+        dd_e2e = [wiresim.DeviceDepos(*trip, device=dev) for trip in dev_in]
+        h2d = sum(a.numel() * 4 for trip in host_in for a in trip)
+        d2h = sum(o.numel() * 4 for o in host_out)
+
+        def e2e_step():
+            for trip_h, trip_d, dd, pl, o, oh in zip(host_in, dev_in, dd_e2e, planes, outs, host_out):
+                for a_h, a_d in zip(trip_h, trip_d):
+                    a_d.copy_(a_h, non_blocking=True)
+                pl.simulate(dd, params, out=o, stream=stream)
+                oh.copy_(o, non_blocking=True)
+
+        for _ in range(max(args.warmup, 1)):
+            e2e_step()
+        torch.cuda.synchronize(dev)
+        s0 = torch.cuda.Event(enable_timing=True)
+        s1 = torch.cuda.Event(enable_timing=True)
+        e_steps = max(1, args.steps)
+        _barrier(dist)
+        torch.cuda.synchronize(dev)
+        s0.record(stream)
+        for _ in range(e_steps):
+            e2e_step()
+        s1.record(stream)
+        torch.cuda.synchronize(dev)
+        _barrier(dist)
+        e_ms = _max_over_ranks(dist, s0.elapsed_time(s1), dev)
+        e_total = _sum_over_ranks(dist, float(ndepo_planes * e_steps), dev)
+        e2e = {"value": e_total / (e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h}
+
+    all_depos = _sum_over_ranks(dist, float(ndepo_planes * args.steps), dev)
+    all_planes = _sum_over_ranks(dist, float(len(planes) * args.steps), dev)
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return
+    value = all_depos / (total_ms * 1e-3)
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        done, secs, nplanes = oracle_sample(w, args.cpu_seconds)
+        cpu = {"value": done / secs, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"{nplanes} planes of this event ({done} depo-planes), FP64, single thread"}
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": w.name, "depos_per_event": ev[0].n, "planes": len(planes),
+                   "wires": [sp.nwires for sp in w.planes], "nticks": w.planes[0].nticks,
+                   "fluctuate": w.fluctuate, "p_survive": w.p_survive,
+                   "fft_len_tick": planes[0].info.fft_len_tick,
+                   "l2": "flushed between timed steps (512 MiB write)"},
+        "planes_per_s": all_planes / (total_ms * 1e-3),
+        "raster_scatter_depos_per_s": all_depos / (raster_ms * 1e-3) if raster_ms > 0 else None,
+        "kernels_ms_per_step": {k: v[1] / args.steps for k, v in sorted(kern.items())},
+        "roofline": {"kernel": dominant, "bound": "hbm", "achieved": achieved, "peak": peak_gbs,
+                     "unit": "GB/s", "frac": achieved / peak_gbs, "traffic": None,
+                     "peak_source": f"{peak_src} hbm_gbs"},
+        "gpu_launches": launches,
+        "clocks": clocks,
+        "e2e": e2e,
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="wiresim", choices=["wiresim", "reference"])
+    ap.add_argument("--workload", default="three_planes", choices=["three_planes", "single_plane"])
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "wiresim":
+        print("warning: fewer than 3 warm-up steps", file=sys.stderr)
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

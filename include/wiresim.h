@@ -1,0 +1,235 @@
+/*
+ * wiresim: GB300 (sm_103a) kernels for the LArTPC signal-simulation hot path
+ * of arXiv 2203.02479 (Dong, Knoepfel, Lin, Viren, Yu, "Evaluation of
+ * Portable Programming Models to Accelerate LArTPC Detector Simulations").
+ *
+ * The path, per wire plane (Sec. 2.1, Sec. 2.2):
+ *   diffusion   each ionization deposition ("depo") spreads into a 2D
+ *               Gaussian along drift time and wire pitch (Sec. 2.2);
+ *   raster      that Gaussian is binned into a patch of (wire, tick) bins
+ *               (Sec. 2.2, "Raster"), optionally with binomial charge
+ *               fluctuation (Sec. 3.1);
+ *   scatter-add the patches are summed into a dense wire x tick grid S
+ *               (Sec. 2.2, "Scatter-add"; Sec. 2.3, dense matrix);
+ *   convolution the grid is convolved with the detector response R by
+ *               FFT, spectrum multiply and inverse FFT (Eq. 1, Eq. 2).
+ *
+ * Conventions shared by every entry point:
+ *   - Pointers named *_dev are device pointers; all other pointers are host
+ *     pointers.  The caller owns every buffer it passes; the library keeps
+ *     only the host-side plane object and uses the caller's workspace.
+ *   - Grids are float32, row-major [wire][tick] (ticks contiguous).
+ *   - Work is stream-ordered on the cudaStream_t passed as `stream` (NULL
+ *     is the legacy default stream).  No call synchronises the host unless
+ *     its comment says so.
+ *   - Every call returns a ws_status; nothing throws across the ABI.
+ *     Argument errors are returned before anything is enqueued.  Errors the
+ *     device detects in the data (a non-finite depo, a negative width, a
+ *     patch buffer too small) never trap: the depo or patch is skipped and a
+ *     bit is set in the plane's device status word (WS_DEV_*), read back by
+ *     ws_plane_sync.
+ *   - A plane's workspace is shared by all calls on that plane: calls on one
+ *     plane must be ordered (one stream, or events between streams).
+ *
+ * Units: pitch in mm, time in microseconds, charge in electrons.
+ * Bin conventions (the paper is silent; the oracle follows the same):
+ *   wire bin w covers pitch [w*pitch, (w+1)*pitch), tick bin k covers time
+ *   [k*tick, (k+1)*tick); x and t are measured from the low edge of bin 0.
+ */
+#ifndef WIRESIM_H
+#define WIRESIM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    WS_OK = 0,
+    WS_ERR_INVALID_ARG = 1,       /* NULL or misaligned pointer, bad value  */
+    WS_ERR_UNSUPPORTED_SIZE = 2,  /* FFT length not 2/3/5-smooth or too big */
+    WS_ERR_OOM = 3,               /* host allocation of the plane failed    */
+    WS_ERR_CUDA = 4,              /* a CUDA call failed: see ws_last_error  */
+    WS_ERR_TIMEOUT = 5,           /* a bounded device wait gave up          */
+    WS_ERR_WORKSPACE = 6,         /* workspace too small                    */
+    WS_ERR_BAD_INPUT = 7          /* device status word reports bad data    */
+} ws_status;
+
+/* Bits of the plane's device status word. */
+#define WS_DEV_BAD_DEPO       0x1u  /* depo with non-finite q/x/t/sigma or negative
+                                       sigma or drift time: skipped            */
+#define WS_DEV_PATCH_OVERFLOW 0x2u  /* ws_rasterize: patch buffer too small;
+                                       patches past the capacity not written   */
+#define WS_DEV_TIMEOUT        0x4u  /* a bounded spin-wait gave up             */
+
+enum { WS_CONV_LINEAR = 0, WS_CONV_CIRCULAR = 1 };
+enum { WS_PREC_FP32 = 0, WS_PREC_FP32_COMP = 1, WS_PREC_FP64 = 2 };
+
+/* One wire plane: grid geometry and the response's shape.  Copied at
+ * creation. */
+typedef struct {
+    int32_t nwires;           /* grid rows                                  */
+    int32_t nticks;           /* grid columns                               */
+    double pitch_mm;          /* wire pitch                                 */
+    double tick_us;           /* sampling period                            */
+    int32_t resp_nwires;      /* response rows K_w (<= 21)                  */
+    int32_t resp_nticks;      /* response columns K_t                       */
+    int32_t resp_wire_center; /* response row holding wire offset 0         */
+    int32_t conv_mode;        /* WS_CONV_LINEAR (zero outside the grid) or
+                                 WS_CONV_CIRCULAR (indices wrap, Eq. 2 on
+                                 the grid itself)                           */
+    int32_t fft_len_tick;     /* 0: smallest 2/3/5-smooth length >=
+                                 nticks + K_t - 1 (linear) or nticks
+                                 (circular); else that length               */
+    double nsigma;            /* Gaussian truncation in sigmas (3.0)        */
+    int32_t plane_id;         /* 0..15, part of the random-stream key       */
+} ws_plane_desc;
+
+/* Depos of one event as seen by one plane: structure of arrays of float32
+ * device pointers, all of length n (Sec. 2.3: the depo arrays are laid out
+ * as structures of arrays).  sigma_t_us / sigma_x_mm are either both NULL
+ * (widths come from diffusion, see ws_params) or both set (given widths). */
+typedef struct {
+    const float* q;           /* charge [electrons]                         */
+    const float* x_mm;        /* pitch position                             */
+    const float* t_us;        /* drift time                                 */
+    const float* sigma_t_us;  /* longitudinal width in time, or NULL        */
+    const float* sigma_x_mm;  /* transverse width in pitch, or NULL         */
+    int64_t n;
+} ws_depos;
+
+/* Physics and numerics of one simulation call. */
+typedef struct {
+    double DL_mm2_us;         /* longitudinal diffusion constant            */
+    double DT_mm2_us;         /* transverse diffusion constant              */
+    double v_mm_us;           /* drift speed                                */
+    int32_t fluctuate;        /* 0: expected value p*q*w per bin;
+                                 1: Binomial(floor(q*w + 1/2), p) per bin   */
+    double p_survive;         /* electron survival probability p            */
+    uint64_t seed;            /* Philox key                                 */
+    uint32_t event_id;        /* < 2^28, part of the Philox counter         */
+    int32_t fluct_exact_max;  /* bins with N <= this draw N Bernoulli trials
+                                 exactly; larger N use the normal
+                                 approximation                              */
+    int32_t precision;        /* WS_PREC_*                                  */
+} ws_params;
+
+/* Patches as produced by ws_rasterize: caller-allocated device arrays.
+ * Patch i covers wires [w0[i], w0[i]+nw[i]) and ticks [t0[i], t0[i]+nt[i])
+ * of the grid (already clipped to it); its values are val[off[i] ...
+ * off[i] + nw[i]*nt[i]) row-major [wire][tick].  off has n + 1 entries,
+ * off[n] being the total number of bins. */
+typedef struct {
+    float* val;
+    int32_t* w0;
+    int32_t* t0;
+    int32_t* nw;
+    int32_t* nt;
+    int64_t* off;
+    int64_t capacity_bins;    /* length of val                              */
+    int64_t n;                /* number of patches (== depos)               */
+} ws_patches;
+
+/* Plane facts chosen at creation, for callers and tests. */
+typedef struct {
+    int32_t fft_len_tick;     /* L_t                                        */
+    int32_t nfreq;            /* L_t/2 + 1 half-spectrum bins               */
+    int32_t nfreq_stride;     /* row stride of the spectra, complex elems   */
+    int32_t npasses;          /* FFT radix passes                           */
+    int32_t radices[16];
+    size_t workspace_bytes;
+} ws_plane_info;
+
+typedef struct ws_plane ws_plane;
+
+/* Bytes of device workspace a plane with this description needs (response
+ * spectrum, twiddles, two spectra of nwires x (L_t/2+1) complex64, status
+ * word and scan scratch).  Host-only; fails with WS_ERR_UNSUPPORTED_SIZE if
+ * the FFT length is not 2/3/5-smooth or exceeds 14336. */
+ws_status ws_plane_workspace_bytes(const ws_plane_desc* desc, size_t* bytes);
+
+/* Create a plane over a caller-owned device workspace (>= the size above,
+ * 256-byte aligned) and compute the response spectrum once (the transform
+ * of R in Eq. 2) on `stream`.  response_dev: K_w x K_t float32, row-major,
+ * row r holding wire offset r - resp_wire_center, column j tick offset j
+ * (causal).  The response is read during this call's stream work only.
+ * The plane object itself is host memory, freed by ws_plane_destroy. */
+ws_status ws_plane_create(const ws_plane_desc* desc, const float* response_dev,
+                          void* workspace_dev, size_t workspace_bytes, void* stream,
+                          ws_plane** out);
+
+/* Free the host plane object; the workspace stays the caller's. */
+ws_status ws_plane_destroy(ws_plane* plane);
+
+ws_status ws_plane_get_info(const ws_plane* plane, ws_plane_info* info);
+
+/* Exact number of in-grid patch bins ws_rasterize will write for these
+ * depos.  SYNCHRONISES `stream` (reads one counter back). */
+ws_status ws_patch_capacity(ws_plane* plane, const ws_depos* depos, const ws_params* params,
+                            void* stream, int64_t* bins_out);
+
+/* Diffusion + raster (+ fluctuation) of every depo into its own patch
+ * (Sec. 2.2 "Raster", Sec. 3.1).  One warp per depo.  Each bin holds
+ * q * p * w_t * w_x (expected value) or a binomial survivor count, with
+ * w the Gaussian mass of the bin clipped to mu +- nsigma*sigma over the
+ * window's total mass.  Writes out->off (exclusive scan of patch sizes),
+ * w0/t0/nw/nt and val.  If the total exceeds capacity_bins the device
+ * status word gets WS_DEV_PATCH_OVERFLOW and the patches that do not fit are
+ * not written (their nw/nt are set to 0). */
+ws_status ws_rasterize(ws_plane* plane, const ws_depos* depos, const ws_params* params,
+                       ws_patches* out, void* stream);
+
+/* Scatter-add of patches into a grid (Sec. 2.2 "Scatter-add"):
+ * grid_dev[w][t] += val of every patch bin at (w, t).  The grid is
+ * accumulated into, not cleared. */
+ws_status ws_scatter(ws_plane* plane, const ws_patches* patches, float* grid_dev,
+                     void* stream);
+
+/* Eq. 2: out = IFFT(R_hat * FFT(grid)), i.e. Eq. 1's sum of
+ * R[d + c][j] * S[w - d][t - j] with S = 0 outside the grid (linear) or
+ * indices wrapping (circular).  grid_dev and out_dev are nwires x nticks;
+ * they may be the same buffer.  Uses the plane's workspace. */
+ws_status ws_convolve(ws_plane* plane, const float* grid_dev, float* out_dev, void* stream);
+
+/* The whole hot path for one plane and one event: clear out_dev, raster +
+ * fluctuate + scatter-add every depo straight into it (no patch buffer),
+ * then convolve in place.  out_dev: nwires x nticks float32. */
+ws_status ws_simulate(ws_plane* plane, const ws_depos* depos, const ws_params* params,
+                      float* out_dev, void* stream);
+
+/* Copy the plane's device status word to *bits.  SYNCHRONISES `stream`. */
+ws_status ws_plane_sync(ws_plane* plane, void* stream, uint32_t* bits);
+
+/* Clear the plane's device status word (stream-ordered). */
+ws_status ws_plane_clear_status(ws_plane* plane, void* stream);
+
+/* Launch tracing (timing of each kernel with CUDA events).  With
+ * max_records > 0, every later launch on this plane is bracketed by a pair
+ * of CUDA events, up to max_records launches (later ones are not recorded);
+ * max_records == 0 turns tracing off.  Creates host-side CUDA events only. */
+ws_status ws_plane_trace(ws_plane* plane, int max_records);
+
+typedef struct {
+    const char* name;         /* kernel name (static string)                */
+    int64_t launches;
+    double total_ms;          /* summed event-to-event device time          */
+} ws_trace_stat;
+
+/* Per-kernel totals of the records since tracing began or the last read;
+ * clears the records.  SYNCHRONISES on the last recorded event.  Writes at
+ * most max_stats entries and their count to *nstats. */
+ws_status ws_plane_trace_read(ws_plane* plane, ws_trace_stat* stats, int max_stats, int* nstats);
+
+const char* ws_status_string(ws_status status);
+
+/* Text of the last CUDA error seen by a ws_* call on this thread ("" if
+ * none). */
+const char* ws_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* WIRESIM_H */

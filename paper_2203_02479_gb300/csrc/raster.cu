@@ -1,0 +1,397 @@
+// Diffusion, raster, binomial fluctuation and scatter-add (Sec. 2.2, Sec. 3.1).
+//
+// One warp per depo (Sec. 2.3: parallelism at the level of individual
+// ionization electron groups).  The lanes evaluate the complementary error
+// function at the patch's bin edges into a per-warp shared-memory edge
+// table, difference neighbouring edges into 1D bin weights for each axis,
+// and then emit the outer product, one bin per lane, either straight into
+// the grid with red.global.add (fused raster + scatter) or into a patch
+// buffer.
+//
+// Bin weight of bin [e0, e1] clipped to mu +- n sigma: with u = (e - mu) /
+// (sqrt 2 sigma) clamped to +-n/sqrt 2 and c = erfc(|u|), the mass is
+//   (c0 - c1)/2 if u0 >= 0,  (c1 - c0)/2 if u1 <= 0,  1 - (c0 + c1)/2 else,
+// which equals (erf(u1) - erf(u0))/2 without cancelling in the tails; it is
+// divided by the window mass erf(n / sqrt 2).
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "ws_internal.cuh"
+
+namespace ws {
+namespace {
+
+constexpr int kChunk = 64;        // bins per axis held in the per-warp tables
+constexpr int kWarpsPerBlock = 8;
+
+// Philox4x32-10 (Salmon et al., SC'11): ten rounds of two 32x32 multiplies
+// whose high halves are mixed with the other counter words and the key; the
+// key advances by two Weyl constants per round.
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
+        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    return c;
+}
+
+// Survivors of N electrons with survival threshold T (p = T / 2^32).
+// N <= exact_max: count the first N Philox words below T (blocks j = 0..).
+// Otherwise the normal approximation from block 0 (Box-Muller), with the
+// integer part of N p taken exactly from the 64-bit product N T.
+__device__ float binomial_draw(int N, const RasterArgs& a, uint32_t bin, uint32_t depo) {
+    if (N <= 0 || a.T == 0u) return 0.f;
+    if (a.p >= 1.f) return (float)N;
+    if (N <= a.exact_max) {
+        int k = 0;
+        for (int j = 0; 4 * j < N; ++j) {
+            const uint4 x = philox4x32_10(make_uint4((uint32_t)j, bin, depo, a.evpl), a.key0, a.key1);
+            const int m = N - 4 * j;
+            k += (x.x < a.T);
+            if (m > 1) k += (x.y < a.T);
+            if (m > 2) k += (x.z < a.T);
+            if (m > 3) k += (x.w < a.T);
+        }
+        return (float)k;
+    }
+    const uint4 x = philox4x32_10(make_uint4(0u, bin, depo, a.evpl), a.key0, a.key1);
+    const float two_m32 = 2.3283064365386963e-10f;  // 2^-32
+    const float u1 = fmaf((float)x.x, two_m32, 0.5f * two_m32);
+    const float u2 = fmaf((float)x.y, two_m32, 0.5f * two_m32);
+    const float z = sqrtf(-2.f * logf(u1)) * cospif(2.f * u2);
+    const uint64_t nt = (uint64_t)(uint32_t)N * (uint64_t)a.T;
+    const float ipart = (float)(uint32_t)(nt >> 32);
+    const float frac = (float)(uint32_t)nt * two_m32;
+    const float pe = (float)a.T * two_m32;
+    const float mean = ipart + frac;
+    const float sd = sqrtf(mean * (1.f - pe));
+    float k = ipart + floorf(frac + z * sd + 0.5f);
+    k = fminf(fmaxf(k, 0.f), (float)N);
+    return k;
+}
+
+// Per-depo geometry: widths and the patch's bin range clipped to the grid.
+struct Extent {
+    float mu_t, mu_x, st, sx;
+    int k0, k1, w0, w1;   // inclusive, clipped
+    bool point_t, point_x;
+};
+
+__device__ __forceinline__ bool axis_range(float mu, float sigma, float delta, float nsig, int nbins,
+                                           int* lo, int* hi, bool* point) {
+    float a, b;
+    *point = !(sigma > 1e-6f * delta);
+    if (*point) {
+        a = b = mu;
+    } else {
+        a = mu - nsig * sigma;
+        b = mu + nsig * sigma;
+    }
+    // Bins beyond the grid are clipped; clamp before converting to int.
+    const float fa = fminf(fmaxf(floorf(a / delta), -1.f), (float)nbins);
+    const float fb = fminf(fmaxf(floorf(b / delta), -1.f), (float)nbins);
+    int l = (int)fa, h = (int)fb;
+    if (l < 0) l = 0;
+    if (h > nbins - 1) h = nbins - 1;
+    *lo = l;
+    *hi = h;
+    return l <= h;
+}
+
+// Returns false if the depo has no in-grid bins or is invalid (then *bad).
+__device__ __forceinline__ bool depo_extent(const RasterArgs& a, int64_t i, Extent* e, float* q, bool* bad) {
+    *bad = false;
+    const float qi = __ldg(a.q + i), xi = __ldg(a.x + i), ti = __ldg(a.t + i);
+    float st, sx;
+    bool ok = isfinite(qi) && isfinite(xi) && isfinite(ti);
+    if (a.sig_t) {
+        st = __ldg(a.sig_t + i);
+        sx = __ldg(a.sig_x + i);
+    } else {
+        ok = ok && ti >= 0.f;
+        const float tt = fmaxf(ti, 0.f);
+        st = sqrtf(a.two_DL * tt) * a.inv_v;
+        sx = sqrtf(a.two_DT * tt);
+    }
+    ok = ok && isfinite(st) && isfinite(sx) && st >= 0.f && sx >= 0.f;
+    if (!ok) {
+        *bad = true;
+        return false;
+    }
+    *q = qi;
+    e->mu_t = ti; e->mu_x = xi; e->st = st; e->sx = sx;
+    if (!axis_range(ti, st, a.tick, a.nsig, a.nticks, &e->k0, &e->k1, &e->point_t)) return false;
+    if (!axis_range(xi, sx, a.pitch, a.nsig, a.nwires, &e->w0, &e->w1, &e->point_x)) return false;
+    return true;
+}
+
+// Weights of bins [first, first + nb) of one axis into w[0..nb) (warp-wide).
+// edge[] is per-warp scratch of kChunk + 1 floats (u) and cv[] (erfc(|u|)).
+__device__ __forceinline__ void axis_weights(float mu, float sigma, float delta, float nsig, bool point,
+                                             int first, int nb, float inv_norm, float* u_s, float* c_s,
+                                             float* w, int lane) {
+    if (point) {
+        // A point charge lands in one bin: the range has exactly that bin.
+        for (int b = lane; b < nb; b += 32) w[b] = 1.f;
+        __syncwarp();
+        return;
+    }
+    const float inv_s2 = 1.f / (1.41421356237309505f * sigma);
+    const float umax = nsig * 0.707106781186547524f;
+    for (int j = lane; j <= nb; j += 32) {
+        const float e = (float)(first + j) * delta;
+        float u = (e - mu) * inv_s2;
+        u = fminf(fmaxf(u, -umax), umax);
+        u_s[j] = u;
+        c_s[j] = erfcf(fabsf(u));
+    }
+    __syncwarp();
+    for (int b = lane; b < nb; b += 32) {
+        const float u0 = u_s[b], u1 = u_s[b + 1];
+        const float c0 = c_s[b], c1 = c_s[b + 1];
+        float m;
+        if (u0 >= 0.f) m = 0.5f * (c0 - c1);
+        else if (u1 <= 0.f) m = 0.5f * (c1 - c0);
+        else m = 1.f - 0.5f * (c0 + c1);
+        w[b] = m * inv_norm;
+    }
+    __syncwarp();
+}
+
+enum { EMIT_GRID = 0, EMIT_PATCH = 1 };
+
+template <int MODE>
+__global__ void __launch_bounds__(32 * kWarpsPerBlock)
+raster_kernel(RasterArgs a, float* __restrict__ grid, ws_patches pt, int64_t dummy) {
+    __shared__ float s_u[kWarpsPerBlock][kChunk + 1];
+    __shared__ float s_c[kWarpsPerBlock][kChunk + 1];
+    __shared__ float s_wt[kWarpsPerBlock][kChunk];
+    __shared__ float s_wx[kWarpsPerBlock][kChunk];
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    const int64_t nwarps = (int64_t)gridDim.x * kWarpsPerBlock;
+    const float inv_norm = 1.f / erff(a.nsig * 0.707106781186547524f);
+    for (int64_t i = (int64_t)blockIdx.x * kWarpsPerBlock + wib; i < a.n; i += nwarps) {
+        Extent e;
+        float q;
+        bool bad;
+        const bool any = depo_extent(a, i, &e, &q, &bad);
+        if (bad && lane == 0) atomicOr(a.status, WS_DEV_BAD_DEPO);
+        int64_t off = 0;
+        int ntf = 0;
+        if (MODE == EMIT_PATCH) {
+            const int nwf = any ? e.w1 - e.w0 + 1 : 0;
+            ntf = any ? e.k1 - e.k0 + 1 : 0;
+            off = pt.off[i];
+            const bool fits = off + (int64_t)nwf * ntf <= pt.capacity_bins;
+            if (lane == 0) {
+                pt.w0[i] = any ? e.w0 : 0;
+                pt.t0[i] = any ? e.k0 : 0;
+                pt.nw[i] = fits ? nwf : 0;
+                pt.nt[i] = fits ? ntf : 0;
+                if (!fits) atomicOr(a.status, WS_DEV_PATCH_OVERFLOW);
+            }
+            if (!fits) continue;
+        }
+        if (!any) continue;
+        const float scale = a.fluct ? 1.f : a.p * q;
+        for (int kc = e.k0; kc <= e.k1; kc += kChunk) {
+            const int ntc = min(kChunk, e.k1 - kc + 1);
+            axis_weights(e.mu_t, e.st, a.tick, a.nsig, e.point_t, kc, ntc, inv_norm, s_u[wib], s_c[wib],
+                         s_wt[wib], lane);
+            for (int wc = e.w0; wc <= e.w1; wc += kChunk) {
+                const int nxc = min(kChunk, e.w1 - wc + 1);
+                axis_weights(e.mu_x, e.sx, a.pitch, a.nsig, e.point_x, wc, nxc, inv_norm, s_u[wib],
+                             s_c[wib], s_wx[wib], lane);
+                const int nbin = nxc * ntc;
+                for (int idx = lane; idx < nbin; idx += 32) {
+                    const int ia = idx / ntc, ib = idx - ia * ntc;
+                    const int w = wc + ia, k = kc + ib;
+                    float v;
+                    if (a.fluct) {
+                        const float nexp = q * s_wx[wib][ia] * s_wt[wib][ib];
+                        const int N = (int)floorf(nexp + 0.5f);
+                        v = binomial_draw(N, a, (uint32_t)((int64_t)w * a.nticks + k), (uint32_t)i);
+                    } else {
+                        v = scale * s_wx[wib][ia] * s_wt[wib][ib];
+                    }
+                    if (MODE == EMIT_GRID) {
+                        if (v != 0.f) atomicAdd(grid + (int64_t)w * a.nticks + k, v);
+                    } else {
+                        pt.val[off + (int64_t)(w - e.w0) * ntf + (k - e.k0)] = v;
+                    }
+                }
+                __syncwarp();
+            }
+        }
+    }
+}
+
+__global__ void patch_sizes_kernel(RasterArgs a, int64_t* __restrict__ sizes,
+                                   unsigned long long* __restrict__ total) {
+    unsigned long long mine = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i <= a.n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        int64_t sz = 0;
+        if (i < a.n) {
+            Extent e;
+            float q;
+            bool bad;
+            if (depo_extent(a, i, &e, &q, &bad)) sz = (int64_t)(e.w1 - e.w0 + 1) * (e.k1 - e.k0 + 1);
+        }
+        if (sizes) sizes[i] = sz;
+        mine += (unsigned long long)sz;
+    }
+    if (total) {
+        for (int o = 16; o > 0; o >>= 1) mine += __shfl_down_sync(0xffffffffu, mine, o);
+        if ((threadIdx.x & 31) == 0 && mine) atomicAdd(total, mine);
+    }
+}
+
+// ---- exclusive scan (three phases: block scan, scan of block sums, add)
+constexpr int kScanThreads = 1024;
+constexpr int kScanItems = 4;
+constexpr int kScanTile = kScanThreads * kScanItems;
+
+__device__ __forceinline__ int64_t block_exclusive_scan(int64_t v, int64_t* s_warp, int64_t* total) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int64_t x = v;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int64_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) s_warp[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+        int64_t w = lane < (int)(blockDim.x >> 5) ? s_warp[lane] : 0;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int64_t y = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += y;
+        }
+        s_warp[lane] = w;  // inclusive warp totals
+    }
+    __syncthreads();
+    const int64_t before = wid > 0 ? s_warp[wid - 1] : 0;
+    *total = s_warp[(blockDim.x >> 5) - 1];
+    __syncthreads();
+    return before + x - v;
+}
+
+__global__ void __launch_bounds__(kScanThreads) scan_tiles_kernel(int64_t* v, int64_t n, int64_t* sums) {
+    __shared__ int64_t s_warp[32];
+    const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
+    int64_t loc[kScanItems];
+    int64_t sum = 0;
+#pragma unroll
+    for (int j = 0; j < kScanItems; ++j) {
+        loc[j] = base + j < n ? v[base + j] : 0;
+        sum += loc[j];
+    }
+    int64_t total;
+    int64_t run = block_exclusive_scan(sum, s_warp, &total);
+#pragma unroll
+    for (int j = 0; j < kScanItems; ++j) {
+        if (base + j < n) v[base + j] = run;
+        run += loc[j];
+    }
+    if (threadIdx.x == 0) sums[blockIdx.x] = total;
+}
+
+__global__ void __launch_bounds__(kScanThreads) scan_sums_kernel(int64_t* sums, int64_t nb) {
+    __shared__ int64_t s_warp[32];
+    int64_t carry = 0;
+    for (int64_t base = 0; base < nb; base += kScanThreads) {
+        const int64_t i = base + threadIdx.x;
+        const int64_t x = i < nb ? sums[i] : 0;
+        int64_t total;
+        const int64_t ex = block_exclusive_scan(x, s_warp, &total);
+        if (i < nb) sums[i] = carry + ex;
+        carry += total;
+    }
+}
+
+__global__ void scan_add_kernel(int64_t* v, int64_t n, const int64_t* sums) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        v[i] += sums[i / kScanTile];
+}
+
+// Warp per patch: grid[w0 + a][t0 + b] += val[off + a nt + b].
+__global__ void __launch_bounds__(256)
+scatter_patches_kernel(ws_patches p, float* __restrict__ grid, int nwires, int nticks) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < p.n; i += nwarps) {
+        const int nw = p.nw[i], nt = p.nt[i];
+        if (nw <= 0 || nt <= 0) continue;
+        const int w0 = p.w0[i], t0 = p.t0[i];
+        const int64_t off = p.off[i];
+        const int nbin = nw * nt;
+        for (int idx = lane; idx < nbin; idx += 32) {
+            const int ia = idx / nt, ib = idx - ia * nt;
+            const int w = w0 + ia, k = t0 + ib;
+            if (w < 0 || w >= nwires || k < 0 || k >= nticks) continue;
+            const float v = p.val[off + idx];
+            if (v != 0.f) atomicAdd(grid + (int64_t)w * nticks + k, v);
+        }
+    }
+}
+
+int grid_for(int64_t items, int per_block, int blocks_per_sm) {
+    int64_t need = (items + per_block - 1) / per_block;
+    const int64_t cap = (int64_t)num_sms() * blocks_per_sm;
+    if (need > cap) need = cap;
+    if (need < 1) need = 1;
+    return (int)need;
+}
+
+}  // namespace
+
+int num_sms() {
+    static int n = 0;
+    if (n == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 132;
+    }
+    return n;
+}
+
+cudaError_t launch_raster_scatter(const RasterArgs& a, float* grid, cudaStream_t s) {
+    if (a.n <= 0) return cudaSuccess;
+    ws_patches none{};
+    raster_kernel<EMIT_GRID><<<grid_for(a.n, kWarpsPerBlock, 8), 32 * kWarpsPerBlock, 0, s>>>(a, grid, none, 0);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_patch_sizes(const RasterArgs& a, int64_t* sizes, unsigned long long* total, cudaStream_t s) {
+    patch_sizes_kernel<<<grid_for(a.n + 1, 256, 8), 256, 0, s>>>(a, sizes, total);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scan_inplace(int64_t* v, int64_t n, int64_t* scratch, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    const int64_t nb = (n + kScanTile - 1) / kScanTile;
+    if (nb > kScanScratch) return cudaErrorInvalidValue;
+    scan_tiles_kernel<<<(unsigned)nb, kScanThreads, 0, s>>>(v, n, scratch);
+    scan_sums_kernel<<<1, kScanThreads, 0, s>>>(scratch, nb);
+    scan_add_kernel<<<grid_for(n, 256, 8), 256, 0, s>>>(v, n, scratch);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_raster_patches(const RasterArgs& a, const ws_patches& p, cudaStream_t s) {
+    if (a.n <= 0) return cudaSuccess;
+    raster_kernel<EMIT_PATCH><<<grid_for(a.n, kWarpsPerBlock, 8), 32 * kWarpsPerBlock, 0, s>>>(a, nullptr, p, 0);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scatter_patches(const ws_patches& p, float* grid, int nwires, int nticks, cudaStream_t s) {
+    if (p.n <= 0) return cudaSuccess;
+    scatter_patches_kernel<<<grid_for(p.n, 8, 8), 256, 0, s>>>(p, grid, nwires, nticks);
+    return cudaGetLastError();
+}
+
+}  // namespace ws

@@ -1,0 +1,431 @@
+// C ABI of the wiresim library (include/wiresim.h): argument checking, the
+// FFT planner, the workspace layout and the launch sequences of each entry
+// point.  No entry point allocates device memory; all device storage is the
+// caller's (the plane's workspace, depo arrays, grids, patch buffers).
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <new>
+#include <vector>
+
+#include "ws_internal.cuh"
+
+// Per-plane launch trace: a ring of (kernel, start event, end event) records
+// filled while tracing is on and aggregated by ws_plane_trace_read.
+struct ws_trace {
+    std::vector<cudaEvent_t> start, stop;
+    std::vector<int> kind;
+    int used = 0;
+    int64_t dropped = 0;
+};
+
+namespace {
+
+thread_local char g_last_error[256] = "";
+
+const char* const kKernelNames[] = {"memset_grid", "raster_scatter", "fwd_rows", "wire_conv", "inv_rows",
+                                    "patch_sizes", "scan", "raster_patches", "scatter_patches"};
+enum { K_MEMSET, K_RASTER_SCATTER, K_FWD, K_WCONV, K_INV, K_SIZES, K_SCAN, K_RPATCH, K_SCATTER, K_COUNT };
+
+// Record a start event for a traced launch; returns the record slot or -1.
+int trace_begin(ws_plane* pl, int kind, cudaStream_t s) {
+    ws_trace* t = pl->trace;
+    if (!t) return -1;
+    if (t->used >= (int)t->start.size()) { ++t->dropped; return -1; }
+    const int i = t->used++;
+    t->kind[i] = kind;
+    cudaEventRecord(t->start[i], s);
+    return i;
+}
+
+void trace_end(ws_plane* pl, int slot, cudaStream_t s) {
+    if (slot >= 0) cudaEventRecord(pl->trace->stop[slot], s);
+}
+
+
+ws_status cuda_fail(cudaError_t e, const char* where) {
+    snprintf(g_last_error, sizeof g_last_error, "%s: %s", where, cudaGetErrorString(e));
+    return WS_ERR_CUDA;
+}
+
+#define WS_CUDA(call)                                   \
+    do {                                                \
+        cudaError_t e_ = (call);                        \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
+    } while (0)
+
+// A launch bracketed by trace events when the plane is tracing.
+#define WS_LAUNCH(pl, kind, s, call)                    \
+    do {                                                \
+        const int slot_ = trace_begin((pl), (kind), (s)); \
+        cudaError_t e_ = (call);                        \
+        trace_end((pl), slot_, (s));                    \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
+    } while (0)
+
+bool smooth235(int n) {
+    if (n <= 0) return false;
+    for (int p : {2, 3, 5})
+        while (n % p == 0) n /= p;
+    return n == 1;
+}
+
+int next_smooth(int n) {
+    while (!smooth235(n)) ++n;
+    return n;
+}
+
+// Radix passes for L: fours first, then fives, threes and a last two.
+bool make_plan(int L, ws::FftPlan* p) {
+    if (!smooth235(L) || L < 2 || L > ws::kMaxFftLen) return false;
+    p->L = L;
+    p->npass = 0;
+    int n = L;
+    while (n % 4 == 0) { p->radix[p->npass++] = 4; n /= 4; }
+    while (n % 5 == 0) { p->radix[p->npass++] = 5; n /= 5; }
+    while (n % 3 == 0) { p->radix[p->npass++] = 3; n /= 3; }
+    while (n % 2 == 0) { p->radix[p->npass++] = 2; n /= 2; }
+    return p->npass <= ws::kMaxPasses && n == 1;
+}
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+struct Layout {
+    ws::FftPlan plan;
+    int nfreq, fstride;
+    size_t off_status, off_tw, off_rt, off_x, off_y, off_scan, total;
+};
+
+ws_status plan_layout(const ws_plane_desc* d, Layout* lay) {
+    if (!d) return WS_ERR_INVALID_ARG;
+    if (d->nwires <= 0 || d->nticks <= 0 || d->resp_nwires <= 0 || d->resp_nticks <= 0 ||
+        d->resp_wire_center < 0 || d->resp_wire_center >= d->resp_nwires || !(d->pitch_mm > 0) ||
+        !(d->tick_us > 0) || !(d->nsigma > 0) || d->plane_id < 0 || d->plane_id > 15 ||
+        (d->conv_mode != WS_CONV_LINEAR && d->conv_mode != WS_CONV_CIRCULAR) || d->fft_len_tick < 0)
+        return WS_ERR_INVALID_ARG;
+    if (d->resp_nwires > ws::kMaxRespWires) return WS_ERR_UNSUPPORTED_SIZE;
+    int L;
+    if (d->fft_len_tick > 0) {
+        L = d->fft_len_tick;
+        if (d->conv_mode == WS_CONV_LINEAR && L < d->nticks + d->resp_nticks - 1) return WS_ERR_INVALID_ARG;
+        if (d->conv_mode == WS_CONV_CIRCULAR && L != d->nticks) return WS_ERR_INVALID_ARG;
+    } else {
+        if (d->conv_mode == WS_CONV_LINEAR) {
+            L = next_smooth(d->nticks + d->resp_nticks - 1);
+            if (L < 2) L = 2;
+        } else {
+            L = d->nticks;
+        }
+    }
+    if (d->resp_nticks > L) return WS_ERR_UNSUPPORTED_SIZE;
+    if (!make_plan(L, &lay->plan)) return WS_ERR_UNSUPPORTED_SIZE;
+    lay->nfreq = L / 2 + 1;
+    lay->fstride = (lay->nfreq + 31) & ~31;
+    size_t o = 0;
+    lay->off_status = o; o = align256(o + 256);
+    lay->off_tw = o; o = align256(o + sizeof(float2) * (size_t)L);
+    lay->off_rt = o; o = align256(o + sizeof(float2) * (size_t)d->resp_nwires * lay->fstride);
+    lay->off_x = o; o = align256(o + sizeof(float2) * (size_t)d->nwires * lay->fstride);
+    lay->off_y = o; o = align256(o + sizeof(float2) * (size_t)d->nwires * lay->fstride);
+    lay->off_scan = o; o = align256(o + sizeof(int64_t) * (size_t)ws::kScanScratch);
+    lay->total = o;
+    return WS_OK;
+}
+
+bool aligned(const void* p, size_t a) { return ((uintptr_t)p & (a - 1)) == 0; }
+
+ws_status check_depos(const ws_depos* d) {
+    if (!d || d->n < 0) return WS_ERR_INVALID_ARG;
+    if (d->n == 0) return WS_OK;
+    if (!d->q || !d->x_mm || !d->t_us) return WS_ERR_INVALID_ARG;
+    if ((d->sigma_t_us == nullptr) != (d->sigma_x_mm == nullptr)) return WS_ERR_INVALID_ARG;
+    if (!aligned(d->q, 4) || !aligned(d->x_mm, 4) || !aligned(d->t_us, 4)) return WS_ERR_INVALID_ARG;
+    if (d->n > ((int64_t)1 << 32)) return WS_ERR_UNSUPPORTED_SIZE;  // depo index is a 32-bit counter word
+    return WS_OK;
+}
+
+ws_status check_params(const ws_params* p) {
+    if (!p) return WS_ERR_INVALID_ARG;
+    if (!(p->v_mm_us > 0) || !(p->DL_mm2_us >= 0) || !(p->DT_mm2_us >= 0)) return WS_ERR_INVALID_ARG;
+    if (!(p->p_survive >= 0) || !(p->p_survive <= 1)) return WS_ERR_INVALID_ARG;
+    if (p->event_id >= (1u << 28)) return WS_ERR_INVALID_ARG;
+    if (p->fluct_exact_max < 0) return WS_ERR_INVALID_ARG;
+    if (p->precision != WS_PREC_FP32 && p->precision != WS_PREC_FP32_COMP && p->precision != WS_PREC_FP64)
+        return WS_ERR_INVALID_ARG;
+    return WS_OK;
+}
+
+ws::RasterArgs raster_args(const ws_plane* pl, const ws_depos* d, const ws_params* p) {
+    ws::RasterArgs a;
+    a.q = d->q; a.x = d->x_mm; a.t = d->t_us;
+    a.sig_t = d->sigma_t_us; a.sig_x = d->sigma_x_mm;
+    a.n = d->n;
+    a.nwires = pl->desc.nwires; a.nticks = pl->desc.nticks;
+    a.pitch = (float)pl->desc.pitch_mm; a.tick = (float)pl->desc.tick_us;
+    a.nsig = (float)pl->desc.nsigma;
+    a.two_DL = (float)(2.0 * p->DL_mm2_us);
+    a.two_DT = (float)(2.0 * p->DT_mm2_us);
+    a.inv_v = (float)(1.0 / p->v_mm_us);
+    a.fluct = p->fluctuate ? 1 : 0;
+    a.p = (float)p->p_survive;
+    if (!(p->p_survive > 0)) a.T = 0u;
+    else if (p->p_survive >= 1.0) a.T = 0xFFFFFFFFu;
+    else a.T = (uint32_t)floor(p->p_survive * 4294967296.0);
+    a.key0 = (uint32_t)(p->seed & 0xFFFFFFFFu);
+    a.key1 = (uint32_t)(p->seed >> 32);
+    a.evpl = (p->event_id << 4) | ((uint32_t)pl->desc.plane_id & 15u);
+    a.exact_max = p->fluct_exact_max;
+    a.status = pl->status;
+    return a;
+}
+
+ws_status convolve_impl(ws_plane* pl, const float* grid, float* out, cudaStream_t s) {
+    const ws_plane_desc& d = pl->desc;
+    WS_LAUNCH(pl, K_FWD, s, ws::launch_fwd_rows(pl->plan, pl->tw, grid, d.nwires, d.nticks, d.nticks, pl->X,
+                                                pl->fstride, pl->nfreq, 1.0f, s));
+    WS_LAUNCH(pl, K_WCONV, s, ws::launch_wire_conv(pl->X, pl->Y, pl->Rt, d.nwires, pl->nfreq, pl->fstride,
+                                                   d.resp_nwires, d.resp_wire_center,
+                                                   d.conv_mode == WS_CONV_CIRCULAR, s));
+    WS_LAUNCH(pl, K_INV, s, ws::launch_inv_rows(pl->plan, pl->tw, pl->Y, d.nwires, pl->fstride, pl->nfreq, out,
+                                                d.nticks, d.nticks, s));
+    return WS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* ws_status_string(ws_status s) {
+    switch (s) {
+        case WS_OK: return "ok";
+        case WS_ERR_INVALID_ARG: return "invalid argument";
+        case WS_ERR_UNSUPPORTED_SIZE: return "unsupported size";
+        case WS_ERR_OOM: return "out of host memory";
+        case WS_ERR_CUDA: return "CUDA error";
+        case WS_ERR_TIMEOUT: return "device wait timed out";
+        case WS_ERR_WORKSPACE: return "workspace too small or misaligned";
+        case WS_ERR_BAD_INPUT: return "bad input data";
+    }
+    return "unknown status";
+}
+
+const char* ws_last_error(void) { return g_last_error; }
+
+ws_status ws_plane_workspace_bytes(const ws_plane_desc* desc, size_t* bytes) {
+    if (!bytes) return WS_ERR_INVALID_ARG;
+    Layout lay;
+    ws_status st = plan_layout(desc, &lay);
+    if (st != WS_OK) return st;
+    *bytes = lay.total;
+    return WS_OK;
+}
+
+ws_status ws_plane_create(const ws_plane_desc* desc, const float* response_dev, void* workspace_dev,
+                          size_t workspace_bytes, void* stream, ws_plane** out) {
+    if (!out || !response_dev) return WS_ERR_INVALID_ARG;
+    *out = nullptr;
+    Layout lay;
+    ws_status st = plan_layout(desc, &lay);
+    if (st != WS_OK) return st;
+    if (!workspace_dev || !aligned(workspace_dev, 256) || workspace_bytes < lay.total) return WS_ERR_WORKSPACE;
+    if (!aligned(response_dev, 4)) return WS_ERR_INVALID_ARG;
+    ws_plane* pl = new (std::nothrow) ws_plane;
+    if (!pl) return WS_ERR_OOM;
+    pl->trace = nullptr;
+    char* base = (char*)workspace_dev;
+    pl->desc = *desc;
+    pl->plan = lay.plan;
+    pl->nfreq = lay.nfreq;
+    pl->fstride = lay.fstride;
+    pl->ws_bytes = lay.total;
+    pl->status = (uint32_t*)(base + lay.off_status);
+    pl->counter = (unsigned long long*)(base + lay.off_status + 8);
+    pl->tw = (float2*)(base + lay.off_tw);
+    pl->Rt = (float2*)(base + lay.off_rt);
+    pl->X = (float2*)(base + lay.off_x);
+    pl->Y = (float2*)(base + lay.off_y);
+    pl->scan = (int64_t*)(base + lay.off_scan);
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = cudaMemsetAsync(base + lay.off_status, 0, 256, s);
+    if (e == cudaSuccess) e = ws::launch_twiddles(pl->tw, lay.plan.L, s);
+    // Response spectrum: per response row, the tick transform scaled by 1/L so
+    // that the inverse transform needs no scaling.
+    if (e == cudaSuccess)
+        e = ws::launch_fwd_rows(lay.plan, pl->tw, response_dev, desc->resp_nwires, desc->resp_nticks,
+                                desc->resp_nticks, pl->Rt, lay.fstride, lay.nfreq, 1.0f / (float)lay.plan.L, s);
+    if (e != cudaSuccess) {
+        delete pl;
+        return cuda_fail(e, "ws_plane_create");
+    }
+    *out = pl;
+    return WS_OK;
+}
+
+static void trace_free(ws_plane* pl) {
+    if (!pl->trace) return;
+    for (size_t i = 0; i < pl->trace->start.size(); ++i) {
+        cudaEventDestroy(pl->trace->start[i]);
+        cudaEventDestroy(pl->trace->stop[i]);
+    }
+    delete pl->trace;
+    pl->trace = nullptr;
+}
+
+ws_status ws_plane_destroy(ws_plane* plane) {
+    if (plane) trace_free(plane);
+    delete plane;
+    return WS_OK;
+}
+
+ws_status ws_plane_trace(ws_plane* pl, int max_records) {
+    if (!pl || max_records < 0) return WS_ERR_INVALID_ARG;
+    trace_free(pl);
+    if (max_records == 0) return WS_OK;
+    ws_trace* t = new (std::nothrow) ws_trace;
+    if (!t) return WS_ERR_OOM;
+    t->start.resize(max_records);
+    t->stop.resize(max_records);
+    t->kind.resize(max_records);
+    for (int i = 0; i < max_records; ++i) {
+        cudaError_t e = cudaEventCreate(&t->start[i]);
+        if (e == cudaSuccess) e = cudaEventCreate(&t->stop[i]);
+        if (e != cudaSuccess) {
+            t->start.resize(i);
+            t->stop.resize(i);
+            pl->trace = t;
+            trace_free(pl);
+            return cuda_fail(e, "ws_plane_trace");
+        }
+    }
+    pl->trace = t;
+    return WS_OK;
+}
+
+ws_status ws_plane_trace_read(ws_plane* pl, ws_trace_stat* stats, int max_stats, int* nstats) {
+    if (!pl || !nstats || (max_stats > 0 && !stats)) return WS_ERR_INVALID_ARG;
+    *nstats = 0;
+    ws_trace* t = pl->trace;
+    if (!t) return WS_OK;
+    double ms[K_COUNT] = {0};
+    int64_t cnt[K_COUNT] = {0};
+    for (int i = 0; i < t->used; ++i) {
+        WS_CUDA(cudaEventSynchronize(t->stop[i]));
+        float m = 0.f;
+        WS_CUDA(cudaEventElapsedTime(&m, t->start[i], t->stop[i]));
+        ms[t->kind[i]] += m;
+        cnt[t->kind[i]] += 1;
+    }
+    int n = 0;
+    for (int k = 0; k < K_COUNT; ++k) {
+        if (!cnt[k]) continue;
+        if (n < max_stats) {
+            stats[n].name = kKernelNames[k];
+            stats[n].launches = cnt[k];
+            stats[n].total_ms = ms[k];
+        }
+        ++n;
+    }
+    *nstats = n < max_stats ? n : max_stats;
+    t->used = 0;
+    t->dropped = 0;
+    return WS_OK;
+}
+
+ws_status ws_plane_get_info(const ws_plane* pl, ws_plane_info* info) {
+    if (!pl || !info) return WS_ERR_INVALID_ARG;
+    memset(info, 0, sizeof *info);
+    info->fft_len_tick = pl->plan.L;
+    info->nfreq = pl->nfreq;
+    info->nfreq_stride = pl->fstride;
+    info->npasses = pl->plan.npass;
+    for (int i = 0; i < pl->plan.npass; ++i) info->radices[i] = pl->plan.radix[i];
+    info->workspace_bytes = pl->ws_bytes;
+    return WS_OK;
+}
+
+ws_status ws_patch_capacity(ws_plane* pl, const ws_depos* depos, const ws_params* params, void* stream,
+                            int64_t* bins_out) {
+    if (!pl || !bins_out) return WS_ERR_INVALID_ARG;
+    ws_status st = check_depos(depos);
+    if (st == WS_OK) st = check_params(params);
+    if (st != WS_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    ws::RasterArgs a = raster_args(pl, depos, params);
+    WS_CUDA(cudaMemsetAsync(pl->counter, 0, sizeof(unsigned long long), s));
+    if (depos->n > 0) WS_CUDA(ws::launch_patch_sizes(a, nullptr, pl->counter, s));
+    unsigned long long total = 0;
+    WS_CUDA(cudaMemcpyAsync(&total, pl->counter, sizeof total, cudaMemcpyDeviceToHost, s));
+    WS_CUDA(cudaStreamSynchronize(s));
+    *bins_out = (int64_t)total;
+    return WS_OK;
+}
+
+ws_status ws_rasterize(ws_plane* pl, const ws_depos* depos, const ws_params* params, ws_patches* out,
+                       void* stream) {
+    if (!pl || !out) return WS_ERR_INVALID_ARG;
+    ws_status st = check_depos(depos);
+    if (st == WS_OK) st = check_params(params);
+    if (st != WS_OK) return st;
+    if (out->n != depos->n || out->capacity_bins < 0 || !out->off) return WS_ERR_INVALID_ARG;
+    if (depos->n > 0 && (!out->w0 || !out->t0 || !out->nw || !out->nt)) return WS_ERR_INVALID_ARG;
+    if (out->capacity_bins > 0 && !out->val) return WS_ERR_INVALID_ARG;
+    if ((depos->n + 1 + 4095) / 4096 > ws::kScanScratch) return WS_ERR_UNSUPPORTED_SIZE;
+    cudaStream_t s = (cudaStream_t)stream;
+    ws::RasterArgs a = raster_args(pl, depos, params);
+    WS_LAUNCH(pl, K_SIZES, s, ws::launch_patch_sizes(a, out->off, nullptr, s));
+    WS_LAUNCH(pl, K_SCAN, s, ws::launch_scan_inplace(out->off, depos->n + 1, pl->scan, s));
+    WS_LAUNCH(pl, K_RPATCH, s, ws::launch_raster_patches(a, *out, s));
+    return WS_OK;
+}
+
+ws_status ws_scatter(ws_plane* pl, const ws_patches* patches, float* grid_dev, void* stream) {
+    if (!pl || !patches || !grid_dev || patches->n < 0) return WS_ERR_INVALID_ARG;
+    if (patches->n > 0 && (!patches->off || !patches->w0 || !patches->t0 || !patches->nw || !patches->nt))
+        return WS_ERR_INVALID_ARG;
+    if (!aligned(grid_dev, 4)) return WS_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    WS_LAUNCH(pl, K_SCATTER, s, ws::launch_scatter_patches(*patches, grid_dev, pl->desc.nwires, pl->desc.nticks, s));
+    return WS_OK;
+}
+
+ws_status ws_convolve(ws_plane* pl, const float* grid_dev, float* out_dev, void* stream) {
+    if (!pl || !grid_dev || !out_dev) return WS_ERR_INVALID_ARG;
+    if (!aligned(grid_dev, 4) || !aligned(out_dev, 4)) return WS_ERR_INVALID_ARG;
+    return convolve_impl(pl, grid_dev, out_dev, (cudaStream_t)stream);
+}
+
+ws_status ws_simulate(ws_plane* pl, const ws_depos* depos, const ws_params* params, float* out_dev,
+                      void* stream) {
+    if (!pl || !out_dev || !aligned(out_dev, 4)) return WS_ERR_INVALID_ARG;
+    ws_status st = check_depos(depos);
+    if (st == WS_OK) st = check_params(params);
+    if (st != WS_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t grid_bytes = sizeof(float) * (size_t)pl->desc.nwires * pl->desc.nticks;
+    WS_LAUNCH(pl, K_MEMSET, s, cudaMemsetAsync(out_dev, 0, grid_bytes, s));
+    ws::RasterArgs a = raster_args(pl, depos, params);
+    WS_LAUNCH(pl, K_RASTER_SCATTER, s, ws::launch_raster_scatter(a, out_dev, s));
+    return convolve_impl(pl, out_dev, out_dev, s);
+}
+
+ws_status ws_plane_sync(ws_plane* pl, void* stream, uint32_t* bits) {
+    if (!pl || !bits) return WS_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    uint32_t v = 0;
+    WS_CUDA(cudaMemcpyAsync(&v, pl->status, sizeof v, cudaMemcpyDeviceToHost, s));
+    WS_CUDA(cudaStreamSynchronize(s));
+    *bits = v;
+    return WS_OK;
+}
+
+ws_status ws_plane_clear_status(ws_plane* pl, void* stream) {
+    if (!pl) return WS_ERR_INVALID_ARG;
+    WS_CUDA(cudaMemsetAsync(pl->status, 0, sizeof(uint32_t), (cudaStream_t)stream));
+    return WS_OK;
+}
+
+}  // extern "C"

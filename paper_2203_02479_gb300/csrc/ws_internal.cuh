@@ -1,0 +1,92 @@
+// Internal declarations shared by the wiresim translation units (never
+// installed; the public boundary is include/wiresim.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/wiresim.h"
+
+namespace ws {
+
+constexpr int kMaxPasses = 16;
+constexpr int kMaxFftLen = 14336;   // two complex64 buffers of this length fit in shared memory
+constexpr int kMaxRespWires = 21;   // wire taps of the register-blocked wire convolution
+constexpr int64_t kScanScratch = 65536;
+
+// Mixed-radix Stockham plan for one complex transform length.
+struct FftPlan {
+    int L;
+    int npass;
+    int radix[kMaxPasses];
+};
+
+// Launch geometry and constants of a raster pass.
+struct RasterArgs {
+    const float* q;
+    const float* x;
+    const float* t;
+    const float* sig_t;   // may be null (widths from diffusion)
+    const float* sig_x;
+    int64_t n;
+    int nwires, nticks;
+    float pitch, tick;
+    float nsig;
+    float two_DL, two_DT, inv_v;
+    int fluct;
+    float p;              // survival probability (expected-value scale)
+    uint32_t T;           // floor(p * 2^32), 0xFFFFFFFF for p >= 1
+    uint32_t key0, key1;  // Philox key from the seed
+    uint32_t evpl;        // (event_id << 4) | plane_id
+    int exact_max;
+    uint32_t* status;
+};
+
+// ---- FFT / convolution launchers (fft.cu)
+cudaError_t launch_twiddles(float2* tw, int L, cudaStream_t s);
+// Real rows -> half spectra: out[r][k] = scale * sum_n in[r][n] e^{-2 pi i k n / L}
+// for k < nfreq; rows shorter than L are zero padded.
+cudaError_t launch_fwd_rows(const FftPlan& plan, const float2* tw, const float* in, int nrows,
+                            int ncols, int64_t in_stride, float2* out, int64_t out_stride,
+                            int nfreq, float scale, cudaStream_t s);
+// Half spectra -> real rows: out[r][n] = sum_k Y[r][k] e^{+2 pi i k n / L} over the
+// Hermitian-extended spectrum, for n < ncols.
+cudaError_t launch_inv_rows(const FftPlan& plan, const float2* tw, const float2* in, int nrows,
+                            int64_t in_stride, int nfreq, float* out, int ncols,
+                            int64_t out_stride, cudaStream_t s);
+// Y[w][k] = sum_r Rt[r][k] * X[w + center - r][k]  (zero or wrapped outside).
+cudaError_t launch_wire_conv(const float2* X, float2* Y, const float2* Rt, int nwires,
+                             int nfreq, int64_t stride, int kw, int center, int circular,
+                             cudaStream_t s);
+
+// ---- raster / scatter launchers (raster.cu)
+cudaError_t launch_raster_scatter(const RasterArgs& a, float* grid, cudaStream_t s);
+cudaError_t launch_patch_sizes(const RasterArgs& a, int64_t* sizes, unsigned long long* total,
+                               cudaStream_t s);
+cudaError_t launch_scan_inplace(int64_t* v, int64_t n, int64_t* scratch, cudaStream_t s);
+cudaError_t launch_raster_patches(const RasterArgs& a, const ws_patches& p, cudaStream_t s);
+cudaError_t launch_scatter_patches(const ws_patches& p, float* grid, int nwires, int nticks,
+                                   cudaStream_t s);
+
+int num_sms();
+
+}  // namespace ws
+
+struct ws_trace;
+
+// The plane: host object pointing into the caller's workspace.
+struct ws_plane {
+    ws_trace* trace;    // launch trace, or null
+    ws_plane_desc desc;
+    ws::FftPlan plan;
+    int nfreq;          // L/2 + 1
+    int fstride;        // row stride of spectra (complex elements)
+    size_t ws_bytes;
+    uint32_t* status;   // device status word
+    unsigned long long* counter;
+    float2* tw;         // L twiddles e^{-2 pi i q / L}
+    float2* Rt;         // K_w x fstride response spectrum (scaled by 1/L)
+    float2* X;          // nwires x fstride
+    float2* Y;          // nwires x fstride
+    int64_t* scan;      // scan scratch
+};

@@ -1,0 +1,368 @@
+"""Python binding of the wiresim C ABI (``include/wiresim.h``).
+
+Argument marshalling only: every step of the path runs in the CUDA library.
+The ``ws_*`` functions mirror the C entry points one to one; ``Plane`` wraps
+them for torch tensors (PyTorch provides device memory and streams).  If the
+library has not been built, loading it raises ``WiresimError``: there is no
+fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import dataclasses
+import os
+import threading
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libwiresim.so")
+
+WS_OK = 0
+STATUS_NAMES = {0: "WS_OK", 1: "WS_ERR_INVALID_ARG", 2: "WS_ERR_UNSUPPORTED_SIZE", 3: "WS_ERR_OOM",
+                4: "WS_ERR_CUDA", 5: "WS_ERR_TIMEOUT", 6: "WS_ERR_WORKSPACE", 7: "WS_ERR_BAD_INPUT"}
+WS_DEV_BAD_DEPO = 0x1
+WS_DEV_PATCH_OVERFLOW = 0x2
+WS_DEV_TIMEOUT = 0x4
+WS_CONV_LINEAR, WS_CONV_CIRCULAR = 0, 1
+WS_PREC_FP32, WS_PREC_FP32_COMP, WS_PREC_FP64 = 0, 1, 2
+
+#: Every symbol include/wiresim.h declares.
+EXPORTED = ("ws_plane_workspace_bytes", "ws_plane_create", "ws_plane_destroy", "ws_plane_get_info",
+            "ws_patch_capacity", "ws_rasterize", "ws_scatter", "ws_convolve", "ws_simulate",
+            "ws_plane_sync", "ws_plane_clear_status", "ws_plane_trace", "ws_plane_trace_read",
+            "ws_status_string", "ws_last_error")
+
+
+class WiresimError(RuntimeError):
+    def __init__(self, status: int, where: str, detail: str = ""):
+        self.status = status
+        msg = f"{where}: {STATUS_NAMES.get(status, status)}"
+        if detail:
+            msg += f" ({detail})"
+        super().__init__(msg)
+
+
+class WsPlaneDesc(ctypes.Structure):
+    _fields_ = [("nwires", ctypes.c_int32), ("nticks", ctypes.c_int32),
+                ("pitch_mm", ctypes.c_double), ("tick_us", ctypes.c_double),
+                ("resp_nwires", ctypes.c_int32), ("resp_nticks", ctypes.c_int32),
+                ("resp_wire_center", ctypes.c_int32), ("conv_mode", ctypes.c_int32),
+                ("fft_len_tick", ctypes.c_int32), ("nsigma", ctypes.c_double),
+                ("plane_id", ctypes.c_int32)]
+
+
+class WsDepos(ctypes.Structure):
+    _fields_ = [("q", ctypes.c_void_p), ("x_mm", ctypes.c_void_p), ("t_us", ctypes.c_void_p),
+                ("sigma_t_us", ctypes.c_void_p), ("sigma_x_mm", ctypes.c_void_p),
+                ("n", ctypes.c_int64)]
+
+
+class WsParams(ctypes.Structure):
+    _fields_ = [("DL_mm2_us", ctypes.c_double), ("DT_mm2_us", ctypes.c_double),
+                ("v_mm_us", ctypes.c_double), ("fluctuate", ctypes.c_int32),
+                ("p_survive", ctypes.c_double), ("seed", ctypes.c_uint64),
+                ("event_id", ctypes.c_uint32), ("fluct_exact_max", ctypes.c_int32),
+                ("precision", ctypes.c_int32)]
+
+
+class WsPatches(ctypes.Structure):
+    _fields_ = [("val", ctypes.c_void_p), ("w0", ctypes.c_void_p), ("t0", ctypes.c_void_p),
+                ("nw", ctypes.c_void_p), ("nt", ctypes.c_void_p), ("off", ctypes.c_void_p),
+                ("capacity_bins", ctypes.c_int64), ("n", ctypes.c_int64)]
+
+
+class WsTraceStat(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char_p), ("launches", ctypes.c_int64), ("total_ms", ctypes.c_double)]
+
+
+class WsPlaneInfo(ctypes.Structure):
+    _fields_ = [("fft_len_tick", ctypes.c_int32), ("nfreq", ctypes.c_int32),
+                ("nfreq_stride", ctypes.c_int32), ("npasses", ctypes.c_int32),
+                ("radices", ctypes.c_int32 * 16), ("workspace_bytes", ctypes.c_size_t)]
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Load libwiresim.so (built by ``__graft_entry__.build()``); no fallback."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(path):
+            raise WiresimError(4, "load_library", f"{path} is missing: build it with "
+                               "paper_2203_02479_gb300.build.build()")
+        h = ctypes.CDLL(path)
+        P = ctypes.c_void_p
+        sig = {
+            "ws_plane_workspace_bytes": [ctypes.POINTER(WsPlaneDesc), ctypes.POINTER(ctypes.c_size_t)],
+            "ws_plane_create": [ctypes.POINTER(WsPlaneDesc), P, P, ctypes.c_size_t, P, ctypes.POINTER(P)],
+            "ws_plane_destroy": [P],
+            "ws_plane_get_info": [P, ctypes.POINTER(WsPlaneInfo)],
+            "ws_patch_capacity": [P, ctypes.POINTER(WsDepos), ctypes.POINTER(WsParams), P,
+                                  ctypes.POINTER(ctypes.c_int64)],
+            "ws_rasterize": [P, ctypes.POINTER(WsDepos), ctypes.POINTER(WsParams),
+                             ctypes.POINTER(WsPatches), P],
+            "ws_scatter": [P, ctypes.POINTER(WsPatches), P, P],
+            "ws_convolve": [P, P, P, P],
+            "ws_simulate": [P, ctypes.POINTER(WsDepos), ctypes.POINTER(WsParams), P, P],
+            "ws_plane_sync": [P, P, ctypes.POINTER(ctypes.c_uint32)],
+            "ws_plane_clear_status": [P, P],
+            "ws_plane_trace": [P, ctypes.c_int],
+            "ws_plane_trace_read": [P, ctypes.POINTER(WsTraceStat), ctypes.c_int,
+                                    ctypes.POINTER(ctypes.c_int)],
+        }
+        for name, args in sig.items():
+            fn = getattr(h, name)
+            fn.argtypes = args
+            fn.restype = ctypes.c_int
+        h.ws_status_string.argtypes = [ctypes.c_int]
+        h.ws_status_string.restype = ctypes.c_char_p
+        h.ws_last_error.argtypes = []
+        h.ws_last_error.restype = ctypes.c_char_p
+        _lib = h
+        return h
+
+
+def _check(status: int, where: str):
+    if status != WS_OK:
+        detail = ""
+        if status == 4:
+            detail = load_library().ws_last_error().decode(errors="replace")
+        raise WiresimError(status, where, detail)
+
+
+# ------------------------------------------------------------ thin wrappers
+def ws_plane_workspace_bytes(desc: WsPlaneDesc) -> int:
+    n = ctypes.c_size_t(0)
+    _check(load_library().ws_plane_workspace_bytes(ctypes.byref(desc), ctypes.byref(n)),
+           "ws_plane_workspace_bytes")
+    return int(n.value)
+
+
+def ws_plane_create(desc: WsPlaneDesc, response_dev: int, workspace_dev: int, workspace_bytes: int,
+                    stream: int) -> int:
+    h = ctypes.c_void_p(0)
+    _check(load_library().ws_plane_create(ctypes.byref(desc), response_dev, workspace_dev,
+                                          workspace_bytes, stream, ctypes.byref(h)), "ws_plane_create")
+    return int(h.value)
+
+
+def ws_plane_destroy(plane: int):
+    _check(load_library().ws_plane_destroy(plane), "ws_plane_destroy")
+
+
+def ws_plane_get_info(plane: int) -> WsPlaneInfo:
+    info = WsPlaneInfo()
+    _check(load_library().ws_plane_get_info(plane, ctypes.byref(info)), "ws_plane_get_info")
+    return info
+
+
+def ws_patch_capacity(plane: int, depos: WsDepos, params: WsParams, stream: int) -> int:
+    n = ctypes.c_int64(0)
+    _check(load_library().ws_patch_capacity(plane, ctypes.byref(depos), ctypes.byref(params), stream,
+                                            ctypes.byref(n)), "ws_patch_capacity")
+    return int(n.value)
+
+
+def ws_rasterize(plane: int, depos: WsDepos, params: WsParams, patches: WsPatches, stream: int):
+    _check(load_library().ws_rasterize(plane, ctypes.byref(depos), ctypes.byref(params),
+                                       ctypes.byref(patches), stream), "ws_rasterize")
+
+
+def ws_scatter(plane: int, patches: WsPatches, grid_dev: int, stream: int):
+    _check(load_library().ws_scatter(plane, ctypes.byref(patches), grid_dev, stream), "ws_scatter")
+
+
+def ws_convolve(plane: int, grid_dev: int, out_dev: int, stream: int):
+    _check(load_library().ws_convolve(plane, grid_dev, out_dev, stream), "ws_convolve")
+
+
+def ws_simulate(plane: int, depos: WsDepos, params: WsParams, out_dev: int, stream: int):
+    _check(load_library().ws_simulate(plane, ctypes.byref(depos), ctypes.byref(params), out_dev, stream),
+           "ws_simulate")
+
+
+def ws_plane_sync(plane: int, stream: int) -> int:
+    v = ctypes.c_uint32(0)
+    _check(load_library().ws_plane_sync(plane, stream, ctypes.byref(v)), "ws_plane_sync")
+    return int(v.value)
+
+
+def ws_plane_clear_status(plane: int, stream: int):
+    _check(load_library().ws_plane_clear_status(plane, stream), "ws_plane_clear_status")
+
+
+def ws_plane_trace(plane: int, max_records: int):
+    _check(load_library().ws_plane_trace(plane, max_records), "ws_plane_trace")
+
+
+def ws_plane_trace_read(plane: int) -> dict:
+    """{kernel name: (launches, total ms)} since tracing began or the last read."""
+    stats = (WsTraceStat * 32)()
+    n = ctypes.c_int(0)
+    _check(load_library().ws_plane_trace_read(plane, stats, 32, ctypes.byref(n)), "ws_plane_trace_read")
+    return {stats[i].name.decode(): (int(stats[i].launches), float(stats[i].total_ms))
+            for i in range(n.value)}
+
+
+# ---------------------------------------------------------- torch helpers
+def _torch():
+    import torch
+    return torch
+
+
+def _stream_handle(stream) -> int:
+    torch = _torch()
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return int(stream.cuda_stream)
+
+
+def _ptr(t) -> int:
+    return 0 if t is None else int(t.data_ptr())
+
+
+@dataclasses.dataclass
+class Params:
+    """Physics and numerics of a simulation call (mirrors ``ws_params``)."""
+    DL_mm2_us: float = 4.0e-4
+    DT_mm2_us: float = 8.8e-4
+    v_mm_us: float = 1.6
+    fluctuate: bool = False
+    p_survive: float = 1.0
+    seed: int = 0
+    event_id: int = 0
+    fluct_exact_max: int = 32
+    precision: int = WS_PREC_FP32
+
+    def c(self) -> WsParams:
+        return WsParams(self.DL_mm2_us, self.DT_mm2_us, self.v_mm_us, int(bool(self.fluctuate)),
+                        self.p_survive, self.seed & (2 ** 64 - 1), self.event_id, self.fluct_exact_max,
+                        self.precision)
+
+
+class DeviceDepos:
+    """Depo arrays resident on the device (float32, contiguous)."""
+
+    def __init__(self, q, x_mm, t_us, sigma_t_us=None, sigma_x_mm=None, device="cuda"):
+        torch = _torch()
+
+        def dev(a):
+            if a is None:
+                return None
+            if not hasattr(a, "data_ptr"):
+                a = torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32))
+            return a.to(device=device, dtype=torch.float32).contiguous()
+
+        self.q, self.x_mm, self.t_us = dev(q), dev(x_mm), dev(t_us)
+        self.sigma_t_us, self.sigma_x_mm = dev(sigma_t_us), dev(sigma_x_mm)
+        self.n = int(self.q.shape[0])
+        for a in (self.x_mm, self.t_us):
+            if int(a.shape[0]) != self.n:
+                raise ValueError("depo arrays differ in length")
+
+    @classmethod
+    def from_plane_depos(cls, d, device="cuda"):
+        return cls(d.q, d.x_mm, d.t_us, device=device)
+
+    def c(self) -> WsDepos:
+        return WsDepos(_ptr(self.q), _ptr(self.x_mm), _ptr(self.t_us), _ptr(self.sigma_t_us),
+                       _ptr(self.sigma_x_mm), self.n)
+
+
+class Plane:
+    """One wire plane with its response spectrum and workspace on the device."""
+
+    def __init__(self, nwires: int, nticks: int, response, *, pitch_mm: float = 5.0,
+                 tick_us: float = 0.5, wire_center: int = 10, circular: bool = False,
+                 fft_len_tick: int = 0, nsigma: float = 3.0, plane_id: int = 0, device="cuda",
+                 stream=None):
+        torch = _torch()
+        resp = response
+        if isinstance(resp, np.ndarray):
+            resp = torch.from_numpy(np.ascontiguousarray(resp, dtype=np.float32))
+        self.response = resp.to(device=device, dtype=torch.float32).contiguous()
+        kw, kt = int(self.response.shape[0]), int(self.response.shape[1])
+        self.desc = WsPlaneDesc(nwires, nticks, pitch_mm, tick_us, kw, kt, wire_center,
+                                WS_CONV_CIRCULAR if circular else WS_CONV_LINEAR, fft_len_tick,
+                                nsigma, plane_id)
+        self.nwires, self.nticks = nwires, nticks
+        nbytes = ws_plane_workspace_bytes(self.desc)
+        self.workspace = torch.empty(nbytes + 256, dtype=torch.uint8, device=device)
+        base = _ptr(self.workspace)
+        aligned = (base + 255) & ~255
+        self.handle = ws_plane_create(self.desc, _ptr(self.response), aligned, nbytes,
+                                      _stream_handle(stream))
+        self.info = ws_plane_get_info(self.handle)
+        self.device = device
+
+    def close(self):
+        if getattr(self, "handle", 0):
+            ws_plane_destroy(self.handle)
+            self.handle = 0
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def new_grid(self):
+        torch = _torch()
+        return torch.zeros((self.nwires, self.nticks), dtype=torch.float32, device=self.device)
+
+    def simulate(self, depos: DeviceDepos, params: Params, out=None, stream=None):
+        if out is None:
+            out = _torch().empty((self.nwires, self.nticks), dtype=_torch().float32, device=self.device)
+        ws_simulate(self.handle, depos.c(), params.c(), _ptr(out), _stream_handle(stream))
+        return out
+
+    def convolve(self, grid, out=None, stream=None):
+        if out is None:
+            out = _torch().empty_like(grid)
+        ws_convolve(self.handle, _ptr(grid), _ptr(out), _stream_handle(stream))
+        return out
+
+    def patch_capacity(self, depos: DeviceDepos, params: Params, stream=None) -> int:
+        return ws_patch_capacity(self.handle, depos.c(), params.c(), _stream_handle(stream))
+
+    def rasterize(self, depos: DeviceDepos, params: Params, capacity: int | None = None, stream=None):
+        torch = _torch()
+        if capacity is None:
+            capacity = self.patch_capacity(depos, params, stream)
+        n = depos.n
+        p = dict(val=torch.zeros(max(capacity, 1), dtype=torch.float32, device=self.device),
+                 w0=torch.zeros(max(n, 1), dtype=torch.int32, device=self.device),
+                 t0=torch.zeros(max(n, 1), dtype=torch.int32, device=self.device),
+                 nw=torch.zeros(max(n, 1), dtype=torch.int32, device=self.device),
+                 nt=torch.zeros(max(n, 1), dtype=torch.int32, device=self.device),
+                 off=torch.zeros(n + 1, dtype=torch.int64, device=self.device))
+        p["capacity"] = capacity
+        p["n"] = n
+        ws_rasterize(self.handle, depos.c(), params.c(), self.patches_c(p), _stream_handle(stream))
+        return p
+
+    @staticmethod
+    def patches_c(p) -> WsPatches:
+        return WsPatches(_ptr(p["val"]), _ptr(p["w0"]), _ptr(p["t0"]), _ptr(p["nw"]), _ptr(p["nt"]),
+                         _ptr(p["off"]), int(p["capacity"]), int(p["n"]))
+
+    def scatter(self, patches, grid, stream=None):
+        ws_scatter(self.handle, self.patches_c(patches), _ptr(grid), _stream_handle(stream))
+        return grid
+
+    def trace(self, max_records: int):
+        ws_plane_trace(self.handle, max_records)
+
+    def trace_read(self) -> dict:
+        return ws_plane_trace_read(self.handle)
+
+    def status(self, stream=None) -> int:
+        return ws_plane_sync(self.handle, _stream_handle(stream))
+
+    def clear_status(self, stream=None):
+        ws_plane_clear_status(self.handle, _stream_handle(stream))

@@ -1,0 +1,79 @@
+"""Host-side checks of the C ABI that need no GPU: the library builds and
+loads, exports every entry point include/wiresim.h declares, and the
+host-only planner answers workspace sizes and rejects bad descriptions."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2203_02479_gb300 import build, wiresim
+    build.build()
+    return wiresim.load_library()
+
+
+def _declared():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            txt = open(os.path.join(ROOT, "include", fn)).read()
+            names |= set(re.findall(r"^\s*(?:ws_status|const char\*)\s+(ws_\w+)\s*\(", txt, re.M))
+    return names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    from paper_2203_02479_gb300 import wiresim
+    declared = _declared()
+    assert declared, "no declarations parsed"
+    assert declared == set(wiresim.EXPORTED)
+    for name in declared:
+        assert hasattr(lib, name), name
+
+
+def _desc(**kw):
+    from paper_2203_02479_gb300 import wiresim
+    d = dict(nwires=960, nticks=6000, pitch_mm=5.0, tick_us=0.5, resp_nwires=21, resp_nticks=200,
+             resp_wire_center=10, conv_mode=0, fft_len_tick=0, nsigma=3.0, plane_id=0)
+    d.update(kw)
+    return wiresim.WsPlaneDesc(**d)
+
+
+def test_workspace_bytes_and_planner(lib):
+    from paper_2203_02479_gb300 import wiresim
+    n = wiresim.ws_plane_workspace_bytes(_desc())
+    # two nwires x round32(6250/2+1) complex64 spectra dominate
+    assert n >= 2 * 960 * 3136 * 8
+    assert n < 2 * 960 * 3136 * 8 + 2 * 1024 * 1024
+    assert n % 256 == 0
+    # circular mode: transform at the grid length itself
+    assert wiresim.ws_plane_workspace_bytes(_desc(conv_mode=1)) < n
+
+
+@pytest.mark.parametrize("kw,code", [
+    (dict(nwires=0), 1), (dict(resp_wire_center=21), 1), (dict(pitch_mm=0.0), 1),
+    (dict(conv_mode=3), 1), (dict(plane_id=16), 1), (dict(resp_nwires=23, resp_wire_center=11), 2),
+    (dict(conv_mode=1, nticks=6007), 2), (dict(fft_len_tick=7000), 2),
+    (dict(fft_len_tick=6000), 1), (dict(nticks=20000), 2)])
+def test_planner_rejects(lib, kw, code):
+    from paper_2203_02479_gb300 import wiresim
+    with pytest.raises(wiresim.WiresimError) as ei:
+        wiresim.ws_plane_workspace_bytes(_desc(**kw))
+    assert ei.value.status == code
+
+
+def test_null_arguments_rejected_without_device_work(lib):
+    from paper_2203_02479_gb300 import wiresim
+    assert lib.ws_simulate(None, None, None, None, None) == 1
+    assert lib.ws_convolve(None, None, None, None) == 1
+    assert lib.ws_plane_sync(None, None, None) == 1
+    assert lib.ws_plane_destroy(None) == 0
+    d = _desc()
+    h = ctypes.c_void_p(0)
+    # workspace missing -> WS_ERR_WORKSPACE before any CUDA call
+    assert lib.ws_plane_create(ctypes.byref(d), ctypes.c_void_p(256), None, 0, None, ctypes.byref(h)) == 6
+    assert lib.ws_status_string(2) == b"unsupported size"

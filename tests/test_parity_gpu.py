@@ -1,0 +1,316 @@
+"""CUDA path against the FP64 oracle, element by element, on seeded inputs.
+
+Tolerances:
+  * expected-value (deterministic) mode: relative L2 <= 1e-5 of the whole
+    grid, the bound the method is held to in FP32;
+  * binomial mode: bins drawn on the exact branch are bit-identical except
+    where FP32 and FP64 round q*w to different electron counts (those differ
+    by at most one electron); normal-branch bins differ by at most one
+    electron, in under 1% of bins; per-bin means and variances over seeds
+    match the binomial's.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2203_02479_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+REL_L2 = 1e-5
+
+
+@pytest.fixture(scope="module")
+def ws():
+    import torch
+    from paper_2203_02479_gb300 import build, wiresim
+    build.build()
+    wiresim.load_library()
+    torch.cuda.set_device(0)
+    return wiresim
+
+
+def rel_l2(a, b):
+    a = np.asarray(a, np.float64); b = np.asarray(b, np.float64)
+    nb = np.linalg.norm(b)
+    return np.linalg.norm(a - b) / (nb if nb > 0 else 1.0)
+
+
+def to_np(t):
+    import torch
+    torch.cuda.synchronize()
+    return t.detach().cpu().numpy().astype(np.float64)
+
+
+def gpu_grid_via_patches(ws, plane, d, params):
+    patches = plane.rasterize(d, params)
+    grid = plane.new_grid()
+    plane.scatter(patches, grid)
+    return patches, to_np(grid)
+
+
+# ------------------------------------------------------------ convolution
+@pytest.mark.parametrize("circular", [False, True])
+@pytest.mark.parametrize("nw,nt,kw,kt,c", [(37, 1000, 21, 200, 10), (8, 300, 5, 17, 2),
+                                           (30, 960, 21, 200, 10), (3, 125, 7, 11, 6),
+                                           (131, 2048, 21, 200, 3)])
+def test_convolve_matches_oracle(ws, circular, nw, nt, kw, kt, c):
+    import torch
+    rng = np.random.Generator(np.random.PCG64(nw * 1000 + nt + circular))
+    S = rng.standard_normal((nw, nt)).astype(np.float32)
+    R = rng.standard_normal((kw, kt)).astype(np.float32)
+    if circular and nt not in (960, 125, 300, 1000, 2048):
+        pytest.skip("circular needs a 2/3/5-smooth tick count")
+    plane = ws.Plane(nw, nt, R, wire_center=c, circular=circular)
+    out = plane.convolve(torch.from_numpy(S).cuda())
+    ref = oracle.convolve_fft(S.astype(np.float64), R, c, circular)
+    assert rel_l2(to_np(out), ref) <= REL_L2
+
+
+def test_convolve_in_place_and_delta_identity(ws):
+    import torch
+    rng = np.random.Generator(np.random.PCG64(3))
+    S = rng.standard_normal((40, 777)).astype(np.float32)
+    R = np.zeros((21, 200), np.float32); R[10, 0] = 1.0
+    plane = ws.Plane(40, 777, R)
+    g = torch.from_numpy(S).cuda()
+    plane.convolve(g, out=g)            # in place
+    assert rel_l2(to_np(g), S) <= 1e-6
+
+
+def test_convolve_full_size_sampled_outputs(ws):
+    """960 x 6000 plane: whole grid against Eq. 2 and sampled points against
+    Eq. 1's direct sum."""
+    import torch
+    rng = np.random.Generator(np.random.PCG64(4))
+    S = np.zeros((960, 6000), np.float32)
+    S[:, :] = rng.exponential(1.0, S.shape) * (rng.uniform(size=S.shape) < 0.05)
+    R = inputs.response("bipolar")
+    plane = ws.Plane(960, 6000, R)
+    out = to_np(plane.convolve(torch.from_numpy(S).cuda()))
+    S64 = S.astype(np.float64)
+    assert rel_l2(out, oracle.convolve_fft(S64, R, 10)) <= REL_L2
+    pw = np.concatenate([[0, 959, 0, 959, 480], rng.integers(0, 960, 200)])
+    pt = np.concatenate([[0, 0, 5999, 5999, 3000], rng.integers(0, 6000, 200)])
+    pts = oracle.convolve_points(S64, R, 10, pw, pt)
+    scale = np.abs(out).max()
+    assert np.abs(out[pw, pt] - pts).max() <= 1e-5 * scale
+
+
+# ------------------------------------------------------ raster + scatter
+def test_rasterize_patches_match_oracle(ws):
+    nw, nt = 70, 2500
+    d = inputs.uniform_depos(3000, nw, seed=21, nticks=nt)
+    plane = ws.Plane(nw, nt, inputs.response())
+    dd = ws.DeviceDepos.from_plane_depos(d)
+    params = ws.Params()
+    patches, S = gpu_grid_via_patches(ws, plane, dd, params)
+    ref = oracle.raster_scatter(d.q, d.x_mm, d.t_us, nw, nt)
+    assert rel_l2(S, ref) <= 1e-6
+    w0, nwv, t0, ntv, total = oracle.patch_extents(d.x_mm, d.t_us, nw, nt)
+    g_nw = patches["nw"].cpu().numpy(); g_nt = patches["nt"].cpu().numpy()
+    g_w0 = patches["w0"].cpu().numpy(); g_t0 = patches["t0"].cpu().numpy()
+    same = (g_nw == nwv) & (g_nt == ntv) & ((g_w0 == w0) | (nwv == 0)) & ((g_t0 == t0) | (ntv == 0))
+    # extents may differ only by a bin of zero weight where FP32 and FP64 put
+    # a window edge on different sides of a bin edge
+    assert same.mean() >= 0.995
+    off = patches["off"].cpu().numpy()
+    assert off[0] == 0 and (np.diff(off) == g_nw.astype(np.int64) * g_nt).all()
+    assert abs(int(off[-1]) - total) <= 0.005 * total
+    assert plane.status() == 0
+
+
+def test_simulate_small_plane_expected_mode(ws):
+    nw, nt = 48, 1500
+    d = inputs.uniform_depos(400, nw, seed=22, nticks=nt)
+    R = inputs.response("unipolar")
+    plane = ws.Plane(nw, nt, R)
+    out = to_np(plane.simulate(ws.DeviceDepos.from_plane_depos(d), ws.Params(p_survive=0.8)))
+    ref = oracle.simulate(d.q, d.x_mm, d.t_us, nw, nt, R, 10, p=0.8)
+    assert rel_l2(out, ref) <= REL_L2
+
+
+def test_simulate_full_single_plane(ws):
+    """960 wires x 6000 ticks, 1,000 uniform depos, bipolar response."""
+    w = inputs.single_plane()
+    sp = w.planes[0]; d = w.events[0][0]
+    plane = ws.Plane(sp.nwires, sp.nticks, sp.response)
+    out = to_np(plane.simulate(ws.DeviceDepos.from_plane_depos(d), ws.Params()))
+    S = oracle.raster_scatter(d.q, d.x_mm, d.t_us, sp.nwires, sp.nticks)
+    ref = oracle.convolve_fft(S, sp.response, 10)
+    assert rel_l2(out, ref) <= REL_L2
+    rng = np.random.Generator(np.random.PCG64(5))
+    pw = rng.integers(0, sp.nwires, 300); pt = rng.integers(0, sp.nticks, 300)
+    pts = oracle.convolve_points(S, sp.response, 10, pw, pt)
+    assert np.abs(out[pw, pt] - pts).max() <= 1e-5 * np.abs(out).max()
+
+
+def test_given_widths_and_large_patches(ws):
+    """Explicit sigmas, including patches wider than one 64-bin chunk on both
+    axes, point charges and depos straddling the grid edges."""
+    nw, nt = 150, 900
+    rng = np.random.Generator(np.random.PCG64(23))
+    n = 60
+    q = rng.exponential(3000, n).astype(np.float32)
+    x = rng.uniform(-20, nw * 5 + 20, n).astype(np.float32)
+    t = rng.uniform(-10, nt * 0.5 + 10, n).astype(np.float32)
+    st = rng.choice([0.0, 0.05, 0.7, 12.0, 30.0], n).astype(np.float32)
+    sx = rng.choice([0.0, 0.3, 2.0, 120.0], n).astype(np.float32)
+    plane = ws.Plane(nw, nt, inputs.response())
+    dd = ws.DeviceDepos(q, x, t, st, sx)
+    _, S = gpu_grid_via_patches(ws, plane, dd, ws.Params())
+    ref = oracle.raster_scatter(q, x, t, nw, nt, sig_t_us=st, sig_x_mm=sx)
+    assert rel_l2(S, ref) <= 1e-6
+    out = to_np(plane.simulate(dd, ws.Params()))
+    assert rel_l2(out, oracle.convolve_fft(ref, inputs.response(), 10)) <= REL_L2
+
+
+def test_edge_cases(ws):
+    import torch
+    nw, nt = 20, 400
+    plane = ws.Plane(nw, nt, inputs.response())
+    # no depos: all zeros
+    empty = ws.DeviceDepos(np.zeros(0, np.float32), np.zeros(0, np.float32), np.zeros(0, np.float32))
+    out = plane.simulate(empty, ws.Params())
+    assert float(out.abs().max()) == 0.0
+    # depos entirely off the grid: all zeros, no error
+    off = ws.DeviceDepos([100.0, 100.0], [-50.0, 500.0], [10.0, 10.0])
+    assert float(plane.simulate(off, ws.Params()).abs().max()) == 0.0
+    assert plane.status() == 0
+    # a NaN charge and a negative drift time are skipped and flagged
+    bad = ws.DeviceDepos([np.nan, 100.0, 50.0], [10.0, 12.0, 20.0], [10.0, 30.0, -1.0])
+    out = to_np(plane.simulate(bad, ws.Params()))
+    assert plane.status() & ws.WS_DEV_BAD_DEPO
+    ref = oracle.simulate([100.0], [12.0], [30.0], nw, nt, inputs.response(), 10)
+    assert rel_l2(out, ref) <= REL_L2
+    plane.clear_status()
+    assert plane.status() == 0
+    torch.cuda.synchronize()
+
+
+def test_patch_capacity_overflow_is_flagged(ws):
+    nw, nt = 30, 600
+    d = inputs.uniform_depos(50, nw, seed=24, nticks=nt)
+    plane = ws.Plane(nw, nt, inputs.response())
+    dd = ws.DeviceDepos.from_plane_depos(d)
+    need = plane.patch_capacity(dd, ws.Params())
+    p = plane.rasterize(dd, ws.Params(), capacity=need // 2)
+    assert plane.status() & 0x2
+    nwv = p["nw"].cpu().numpy(); off = p["off"].cpu().numpy()
+    written = nwv > 0
+    assert (off[:-1][written] + nwv[written] * p["nt"].cpu().numpy()[written] <= need // 2).all()
+
+
+def test_longest_transform(ws):
+    """13,000 ticks: the tick transform length is 13,500 = 2^2 3^3 5^3."""
+    nw, nt = 6, 13000
+    d = inputs.uniform_depos(100, nw, seed=25, nticks=nt)
+    R = inputs.response()
+    plane = ws.Plane(nw, nt, R)
+    assert plane.info.fft_len_tick == 13500
+    out = to_np(plane.simulate(ws.DeviceDepos.from_plane_depos(d), ws.Params()))
+    assert rel_l2(out, oracle.simulate(d.q, d.x_mm, d.t_us, nw, nt, R, 10)) <= REL_L2
+
+
+# ------------------------------------------------------------ fluctuation
+def _sparse_depos(n, nw, nt, seed, q_mean=400.0):
+    """Depos on a lattice of 4-wire x 40-tick cells, one per cell near its
+    centre, so no two patches (at most 13 ticks x 4 wires here) share a bin."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    cols, rows = nt // 40, nw // 4
+    idx = rng.permutation(cols * rows)[:n]
+    wi, ti = idx // cols, idx % cols
+    x = (wi * 4 + 2) * 5.0 + rng.uniform(-2, 2, len(idx))
+    t = (ti * 40 + 20) * 0.5 + rng.uniform(-3, 3, len(idx))
+    q = rng.exponential(q_mean, len(idx)) + 5
+    return q.astype(np.float32), x.astype(np.float32), np.maximum(t, 1.0).astype(np.float32)
+
+
+def _boundary_mask(qw):
+    """Bins whose expected electron count q*w lies within FP32 reach of
+    n + 1/2, where FP32 and FP64 may round to different counts."""
+    frac = qw - np.floor(qw)
+    return np.abs(frac - 0.5) < 2e-6 * qw + 1e-5
+
+
+def test_fluctuation_exact_branch_is_bit_exact(ws):
+    nw, nt = 64, 3000
+    q, x, t = _sparse_depos(300, nw, nt, 31)
+    plane = ws.Plane(nw, nt, inputs.response(), plane_id=2)
+    params = ws.Params(fluctuate=True, p_survive=0.7, seed=0xDEADBEEF12345, event_id=5,
+                       fluct_exact_max=1 << 30)
+    _, S = gpu_grid_via_patches(ws, plane, ws.DeviceDepos(q, x, t), params)
+    ref = oracle.raster_scatter(q, x, t, nw, nt, fluctuate=True, p=0.7, seed=0xDEADBEEF12345,
+                                event_id=5, plane_id=2, exact_max=1 << 30)
+    qw = oracle.raster_scatter(q, x, t, nw, nt)
+    amb = _boundary_mask(qw)
+    assert (S[~amb] == ref[~amb]).all()
+    assert np.abs(S[amb] - ref[amb]).max(initial=0) <= 1
+    assert (S > 0).sum() > 2000
+
+
+def test_fluctuation_normal_branch_within_one(ws):
+    nw, nt = 64, 3000
+    q, x, t = _sparse_depos(300, nw, nt, 32, q_mean=6000.0)
+    plane = ws.Plane(nw, nt, inputs.response())
+    params = ws.Params(fluctuate=True, p_survive=0.7, seed=99)
+    _, S = gpu_grid_via_patches(ws, plane, ws.DeviceDepos(q, x, t), params)
+    ref = oracle.raster_scatter(q, x, t, nw, nt, fluctuate=True, p=0.7, seed=99)
+    qw = oracle.raster_scatter(q, x, t, nw, nt)
+    amb = _boundary_mask(qw)
+    exact = (np.floor(qw + 0.5) <= 32) & ~amb
+    assert (S[exact] == ref[exact]).all()
+    normal = np.floor(qw + 0.5) > 32
+    diff = np.abs(S - ref)
+    assert diff.max() <= 1
+    assert (diff[normal] > 0).mean() < 0.01
+    assert normal.sum() > 1000
+
+
+def test_fluctuation_moments_over_seeds(ws):
+    """Per-bin mean and variance of the survivor counts over seeds against
+    p N and N p (1 - p) with N from the oracle's expected charges."""
+    nw, nt = 16, 800
+    q, x, t = _sparse_depos(20, nw, nt, 33, q_mean=2000.0)
+    plane = ws.Plane(nw, nt, inputs.response())
+    dd = ws.DeviceDepos(q, x, t)
+    qw = oracle.raster_scatter(q, x, t, nw, nt)
+    N = np.floor(qw + 0.5)
+    m = N > 0
+    K = 400
+    acc = np.zeros(m.sum()); acc2 = np.zeros(m.sum())
+    for s in range(K):
+        _, S = gpu_grid_via_patches(ws, plane, dd, ws.Params(fluctuate=True, p_survive=0.7, seed=s))
+        acc += S[m]; acc2 += S[m] ** 2
+    mean = acc / K
+    var = acc2 / K - mean ** 2
+    p = 0.7
+    z = (mean - N[m] * p) / np.sqrt(N[m] * p * (1 - p) / K)
+    assert np.abs(z).max() < 5.5
+    big = N[m] >= 20
+    ratio = var[big] / (N[m][big] * p * (1 - p))
+    assert abs(np.median(ratio) - 1) < 0.1
+
+
+def test_three_planes_fluctuated_full_size(ws):
+    """The three-plane workload at full size (100k track depos, binomial
+    fluctuation): raster S bin by bin, and the simulated waveforms."""
+    w = inputs.three_planes()
+    for sp, d in zip(w.planes, w.events[0]):
+        plane = ws.Plane(sp.nwires, sp.nticks, sp.response, plane_id=sp.plane_id)
+        dd = ws.DeviceDepos.from_plane_depos(d)
+        params = ws.Params(fluctuate=True, p_survive=w.p_survive, seed=w.seed)
+        _, S = gpu_grid_via_patches(ws, plane, dd, params)
+        ref = oracle.raster_scatter(d.q, d.x_mm, d.t_us, sp.nwires, sp.nticks, fluctuate=True,
+                                    p=w.p_survive, seed=w.seed, plane_id=sp.plane_id)
+        diff = np.abs(S - ref)
+        # overlapping patches: a bin sums several depos, each exact or off by one
+        assert (diff > 0).mean() < 0.01
+        assert diff.max() <= 4
+        assert abs(S.sum() - ref.sum()) <= 1e-4 * ref.sum()
+        out = to_np(plane.simulate(dd, params))
+        ref_m = oracle.convolve_fft(ref, sp.response, 10)
+        assert rel_l2(out, ref_m) <= 1e-3
+        assert plane.status() == 0
