@@ -375,7 +375,7 @@ def run_gpu(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=300)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="wiresim", choices=["wiresim", "reference"])
     ap.add_argument("--workload", default="three_planes", choices=["three_planes", "single_plane"])

@@ -112,7 +112,7 @@ typedef struct {
     uint32_t event_id;        /* < 2^28, part of the Philox counter         */
     int32_t fluct_exact_max;  /* bins with N <= this draw N Bernoulli trials
                                  exactly; larger N use the normal
-                                 approximation                              */
+                                 approximation; 0 .. 2^27                   */
     int32_t precision;        /* WS_PREC_*                                  */
 } ws_params;
 

@@ -10,22 +10,61 @@
 //                 transform carried out as the equivalent sum, so no
 //                 nwires x L_t response spectrum has to be streamed from HBM;
 //   3. inv_rows   inverse real FFT of every row, cropped to the grid.
-// Transforms are mixed-radix (2, 3, 4, 5) Stockham autosort passes in shared
-// memory with a table of L-th roots of unity.
+// Transforms are mixed-radix Stockham autosort passes in shared memory with
+// radices up to 25 (composites done as two register-level stages with
+// compile-time twiddles) and a per-pass table of inter-pass twiddles.
 #include <cuda_runtime.h>
 #include <stdint.h>
+
+#include <type_traits>
+#include <utility>
 
 #include "ws_internal.cuh"
 
 namespace ws {
 namespace {
 
-__global__ void twiddle_kernel(float2* tw, int L) {
-    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < L; q += gridDim.x * blockDim.x) {
-        double s, c;
-        sincospi(-2.0 * (double)q / (double)L, &s, &c);
-        tw[q] = make_float2((float)c, (float)s);
+// ---------------------------------------------------------------- helpers
+// Compile-time unrolled loop: f(integral_constant<int, i>) for i in [0, N).
+template <int... Is, class F>
+__device__ __forceinline__ void sfor_impl(std::integer_sequence<int, Is...>, F&& f) {
+    (f(std::integral_constant<int, Is>{}), ...);
+}
+template <int N, class F>
+__device__ __forceinline__ void sfor(F&& f) {
+    sfor_impl(std::make_integer_sequence<int, N>{}, f);
+}
+
+// cos and sin of 2 pi m / n in double at compile time: exact octant
+// reduction of the rational angle, then Taylor series on |a| <= pi/4.
+constexpr double kPi = 3.14159265358979323846264338327950288;
+__host__ __device__ constexpr double cx_sin_small(double a) {
+    double a2 = a * a, term = a, sum = a;
+    for (int i = 1; i < 14; ++i) { term *= -a2 / ((2.0 * i) * (2.0 * i + 1.0)); sum += term; }
+    return sum;
+}
+__host__ __device__ constexpr double cx_cos_small(double a) {
+    double a2 = a * a, term = 1.0, sum = 1.0;
+    for (int i = 1; i < 14; ++i) { term *= -a2 / ((2.0 * i - 1.0) * (2.0 * i)); sum += term; }
+    return sum;
+}
+// Returns cos (want_sin = false) or sin of 2 pi m / n.
+__host__ __device__ constexpr double cx_trig2pi(long m, long n, bool want_sin) {
+    long t = (8 * (m % n) + 8 * n) % (8 * n);   // angle in units of pi/(4n)
+    long o = t / n, r = t - o * n;               // octant and remainder
+    double a = 0.0;
+    long q = 0;
+    if (o % 2 == 0) { a = (kPi / 4.0) * (double)r / (double)n; q = o / 2; }
+    else { a = -(kPi / 4.0) * (double)(n - r) / (double)n; q = (o + 1) / 2; }
+    double c = cx_cos_small(a), s = cx_sin_small(a);
+    double cc = c, ss = s;
+    switch (q % 4) {
+        case 0: cc = c; ss = s; break;
+        case 1: cc = -s; ss = c; break;
+        case 2: cc = -c; ss = -s; break;
+        default: cc = s; ss = -c; break;
     }
+    return want_sin ? ss : cc;
 }
 
 __device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
@@ -43,7 +82,27 @@ __device__ __forceinline__ float2 mul_mi(float2 a) {
     return INV ? make_float2(-a.y, a.x) : make_float2(a.y, -a.x);
 }
 
-// Small DFTs, y_m = sum_n x_n e^{-+2 pi i m n / R}, in place.
+// x * e^{-+2 pi i M / N} with M, N compile-time.
+template <int N, int M, bool INV>
+__device__ __forceinline__ float2 rot(float2 x) {
+    constexpr int m = M % N;
+    if constexpr (m == 0) {
+        return x;
+    } else if constexpr (2 * m == N) {
+        return make_float2(-x.x, -x.y);
+    } else if constexpr (4 * m == N) {
+        return mul_mi<INV>(x);
+    } else if constexpr (4 * m == 3 * N) {
+        return mul_mi<!INV>(x);
+    } else {
+        constexpr float c = (float)cx_trig2pi(m, N, false);
+        constexpr float s = INV ? (float)cx_trig2pi(m, N, true) : -(float)cx_trig2pi(m, N, true);
+        return make_float2(fmaf(x.x, c, -x.y * s), fmaf(x.x, s, x.y * c));
+    }
+}
+
+// ------------------------------------------------------------ small DFTs
+// y_m = sum_n x_n e^{-+2 pi i m n / R}, in place, natural order.
 template <int R, bool INV> struct Dft;
 
 template <bool INV> struct Dft<2, INV> {
@@ -101,22 +160,72 @@ template <bool INV> struct Dft<5, INV> {
     }
 };
 
+// Composite N = N1 N2 (Cooley-Tukey in registers): with n = N2 n1 + n2 and
+// k = k1 + N1 k2, X[k] = sum_n2 W_N2^(n2 k2) W_N^(n2 k1) sum_n1 x[n] W_N1^(n1 k1).
+template <int N1, int N2, bool INV>
+__device__ __forceinline__ void dft_composite(float2* v) {
+    constexpr int N = N1 * N2;
+    sfor<N2>([&](auto n2c) {
+        constexpr int n2 = decltype(n2c)::value;
+        float2 t[N1];
+        sfor<N1>([&](auto n1c) { t[decltype(n1c)::value] = v[N2 * decltype(n1c)::value + n2]; });
+        Dft<N1, INV>::run(t);
+        sfor<N1>([&](auto k1c) {
+            constexpr int k1 = decltype(k1c)::value;
+            v[N2 * k1 + n2] = rot<N, n2 * k1, INV>(t[k1]);
+        });
+    });
+    float2 out[N];
+    sfor<N1>([&](auto k1c) {
+        constexpr int k1 = decltype(k1c)::value;
+        float2 t[N2];
+        sfor<N2>([&](auto n2c) { t[decltype(n2c)::value] = v[N2 * k1 + decltype(n2c)::value]; });
+        Dft<N2, INV>::run(t);
+        sfor<N2>([&](auto k2c) { out[k1 + N1 * decltype(k2c)::value] = t[decltype(k2c)::value]; });
+    });
+    sfor<N>([&](auto ic) { v[decltype(ic)::value] = out[decltype(ic)::value]; });
+}
+
+#define WS_COMPOSITE(R, A, B)                                                          \
+    template <bool INV> struct Dft<R, INV> {                                            \
+        __device__ __forceinline__ static void run(float2* v) { dft_composite<A, B, INV>(v); } \
+    };
+WS_COMPOSITE(6, 3, 2)
+WS_COMPOSITE(8, 4, 2)
+WS_COMPOSITE(9, 3, 3)
+WS_COMPOSITE(10, 5, 2)
+WS_COMPOSITE(12, 4, 3)
+WS_COMPOSITE(15, 5, 3)
+WS_COMPOSITE(16, 4, 4)
+WS_COMPOSITE(20, 5, 4)
+WS_COMPOSITE(25, 5, 5)
+#undef WS_COMPOSITE
+
+// ------------------------------------------------------- Stockham passes
+constexpr int kRowThreads = 256;
+
 // One Stockham pass of radix R over a length-L sequence: butterfly j reads
-// src[j + r L/R], twiddles by w^(r (j mod Ns)) with w the (Ns R)-th root,
-// and writes dst[(j - j mod Ns) R + j mod Ns + r Ns].
+// src[j + r L/R], multiplies input r by w^r with w = e^{-+2 pi i (j mod Ns) /
+// (Ns R)} (w from the pass's table of Ns base twiddles, its powers by a
+// multiply tree of depth <= 5), and writes dst[(j - j mod Ns) R + j mod Ns +
+// r Ns].
 template <int R, bool INV>
 __device__ __forceinline__ void stockham_pass(const float2* __restrict__ src, float2* __restrict__ dst,
                                               int L, int Ns, const float2* __restrict__ tw) {
     const int nb = L / R;
-    const int step = L / (Ns * R);
-    for (int j = threadIdx.x; j < nb; j += blockDim.x) {
+    for (int j = threadIdx.x; j < nb; j += kRowThreads) {
         const int k = j % Ns;
         float2 v[R];
 #pragma unroll
-        for (int r = 0; r < R; ++r) {
-            float2 x = src[j + r * nb];
-            if (r > 0) x = cmul_tw<INV>(x, __ldg(&tw[k * r * step]));
-            v[r] = x;
+        for (int r = 0; r < R; ++r) v[r] = src[j + r * nb];
+        if (Ns > 1) {
+            float2 wp[R];
+            wp[1] = __ldg(&tw[k]);
+            if (INV) wp[1].y = -wp[1].y;
+#pragma unroll
+            for (int r = 2; r < R; ++r) wp[r] = cmul_tw<false>(wp[r / 2], wp[r - r / 2]);
+#pragma unroll
+            for (int r = 1; r < R; ++r) v[r] = cmul_tw<false>(v[r], wp[r]);
         }
         Dft<R, INV>::run(v);
         const int d = (j - k) * R + k;
@@ -130,56 +239,88 @@ template <bool INV>
 __device__ float2* fft_smem(const FftPlan& plan, float2* a, float2* b, const float2* __restrict__ tw) {
     float2* src = a;
     float2* dst = b;
-    int Ns = 1;
     for (int p = 0; p < plan.npass; ++p) {
-        const int R = plan.radix[p];
-        switch (R) {
-            case 2: stockham_pass<2, INV>(src, dst, plan.L, Ns, tw); break;
-            case 3: stockham_pass<3, INV>(src, dst, plan.L, Ns, tw); break;
-            case 4: stockham_pass<4, INV>(src, dst, plan.L, Ns, tw); break;
-            default: stockham_pass<5, INV>(src, dst, plan.L, Ns, tw); break;
+        const int Ns = plan.ns[p];
+        const float2* t = tw + plan.twoff[p];
+        switch (plan.radix[p]) {
+            case 2: stockham_pass<2, INV>(src, dst, plan.L, Ns, t); break;
+            case 3: stockham_pass<3, INV>(src, dst, plan.L, Ns, t); break;
+            case 4: stockham_pass<4, INV>(src, dst, plan.L, Ns, t); break;
+            case 5: stockham_pass<5, INV>(src, dst, plan.L, Ns, t); break;
+            case 6: stockham_pass<6, INV>(src, dst, plan.L, Ns, t); break;
+            case 8: stockham_pass<8, INV>(src, dst, plan.L, Ns, t); break;
+            case 9: stockham_pass<9, INV>(src, dst, plan.L, Ns, t); break;
+            case 10: stockham_pass<10, INV>(src, dst, plan.L, Ns, t); break;
+            case 12: stockham_pass<12, INV>(src, dst, plan.L, Ns, t); break;
+            case 15: stockham_pass<15, INV>(src, dst, plan.L, Ns, t); break;
+            case 16: stockham_pass<16, INV>(src, dst, plan.L, Ns, t); break;
+            case 20: stockham_pass<20, INV>(src, dst, plan.L, Ns, t); break;
+            default: stockham_pass<25, INV>(src, dst, plan.L, Ns, t); break;
         }
         __syncthreads();
-        float2* t = src; src = dst; dst = t;
-        Ns *= R;
+        float2* tmp = src; src = dst; dst = tmp;
     }
     return src;
 }
 
-constexpr int kRowThreads = 512;
+// Pass twiddles: for pass p, tw[twoff[p] + k] = e^{-2 pi i k / (Ns R)}, k < Ns.
+__global__ void pass_twiddles_kernel(float2* tw, FftPlan plan) {
+    for (int p = 0; p < plan.npass; ++p) {
+        const int Ns = plan.ns[p], R = plan.radix[p];
+        for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < Ns; k += gridDim.x * blockDim.x) {
+            double s, c;
+            sincospi(-2.0 * (double)k / (double)((long long)Ns * R), &s, &c);
+            tw[plan.twoff[p] + k] = make_float2((float)c, (float)s);
+        }
+    }
+}
 
 // Two real rows (2 blockIdx.x, 2 blockIdx.x + 1) as one complex transform
 // z = a + i b; then A_k = (Z_k + conj Z_{L-k}) / 2, B_k = (Z_k - conj Z_{L-k}) / 2i.
-__global__ void __launch_bounds__(kRowThreads)
+__global__ void __launch_bounds__(kRowThreads, 2)
 fwd_rows_kernel(FftPlan plan, const float2* __restrict__ tw, const float* __restrict__ in,
                 int nrows, int ncols, int64_t in_stride, float2* __restrict__ out,
-                int64_t out_stride, int nfreq, float scale) {
-    extern __shared__ float2 smem[];
+                int64_t out_stride, int nfreq, float scale, int vec4) {
+    extern __shared__ __align__(16) float2 smem[];
     const int L = plan.L;
     float2* a = smem;
-    float2* b = smem + L;
+    float2* b = smem + ((L + 1) & ~1);  // both buffers 16-byte aligned
     const int r0 = 2 * blockIdx.x;
     const bool has_b = r0 + 1 < nrows;
     const float* pa = in + (int64_t)r0 * in_stride;
-    const float* pb = pa + in_stride;
+    const float* pb = has_b ? pa + in_stride : pa;
     const int nload = ncols < L ? ncols : L;
-    for (int n = threadIdx.x; n < L; n += blockDim.x) {
-        float xa = 0.f, xb = 0.f;
-        if (n < nload) {
-            xa = __ldg(pa + n);
-            if (has_b) xb = __ldg(pb + n);
+    if (vec4) {
+        // rows are 16-byte aligned and nload % 4 == 0
+        const float4* qa = reinterpret_cast<const float4*>(pa);
+        const float4* qb = reinterpret_cast<const float4*>(pb);
+        float4* a4 = reinterpret_cast<float4*>(a);
+        for (int n4 = threadIdx.x; n4 < nload / 4; n4 += kRowThreads) {
+            const float4 xa = __ldg(qa + n4);
+            float4 xb = __ldg(qb + n4);
+            if (!has_b) xb = make_float4(0.f, 0.f, 0.f, 0.f);
+            a4[2 * n4] = make_float4(xa.x, xb.x, xa.y, xb.y);
+            a4[2 * n4 + 1] = make_float4(xa.z, xb.z, xa.w, xb.w);
         }
-        a[n] = make_float2(xa, xb);
+        for (int n = nload + threadIdx.x; n < L; n += kRowThreads) a[n] = make_float2(0.f, 0.f);
+    } else {
+        for (int n = threadIdx.x; n < L; n += kRowThreads) {
+            float xa = 0.f, xb = 0.f;
+            if (n < nload) {
+                xa = __ldg(pa + n);
+                if (has_b) xb = __ldg(pb + n);
+            }
+            a[n] = make_float2(xa, xb);
+        }
     }
     __syncthreads();
     const float2* z = fft_smem<false>(plan, a, b, tw);
     float2* oa = out + (int64_t)r0 * out_stride;
     float2* ob = oa + out_stride;
     const float h = 0.5f * scale;
-    for (int k = threadIdx.x; k < nfreq; k += blockDim.x) {
+    for (int k = threadIdx.x; k < nfreq; k += kRowThreads) {
         const float2 zk = z[k];
         const float2 zm = z[k == 0 ? 0 : L - k];
-        // conj(zm) = (zm.x, -zm.y)
         oa[k] = make_float2(h * (zk.x + zm.x), h * (zk.y - zm.y));
         if (has_b) ob[k] = make_float2(h * (zk.y + zm.y), h * (zm.x - zk.x));
     }
@@ -187,20 +328,20 @@ fwd_rows_kernel(FftPlan plan, const float2* __restrict__ tw, const float* __rest
 
 // Two half spectra A (row r0) and B (row r0+1) -> Z = A + iB over the full
 // Hermitian extension, inverse transform, real part row r0, imaginary r0+1.
-__global__ void __launch_bounds__(kRowThreads)
+__global__ void __launch_bounds__(kRowThreads, 2)
 inv_rows_kernel(FftPlan plan, const float2* __restrict__ tw, const float2* __restrict__ in,
                 int nrows, int64_t in_stride, int nfreq, float* __restrict__ out, int ncols,
-                int64_t out_stride) {
-    extern __shared__ float2 smem[];
+                int64_t out_stride, int vec4) {
+    extern __shared__ __align__(16) float2 smem[];
     const int L = plan.L;
     float2* a = smem;
-    float2* b = smem + L;
+    float2* b = smem + ((L + 1) & ~1);  // both buffers 16-byte aligned
     const int r0 = 2 * blockIdx.x;
     const bool has_b = r0 + 1 < nrows;
     const float2* ya = in + (int64_t)r0 * in_stride;
-    const float2* yb = ya + in_stride;
+    const float2* yb = has_b ? ya + in_stride : ya;
     const bool even = (L & 1) == 0;
-    for (int k = threadIdx.x; k < L; k += blockDim.x) {
+    for (int k = threadIdx.x; k < L; k += kRowThreads) {
         const bool upper = k >= nfreq;
         const int kk = upper ? L - k : k;
         float2 A = __ldg(ya + kk);
@@ -214,22 +355,55 @@ inv_rows_kernel(FftPlan plan, const float2* __restrict__ tw, const float2* __res
     float* oa = out + (int64_t)r0 * out_stride;
     float* ob = oa + out_stride;
     const int nst = ncols < L ? ncols : L;
-    for (int n = threadIdx.x; n < nst; n += blockDim.x) {
-        const float2 v = z[n];
-        oa[n] = v.x;
-        if (has_b) ob[n] = v.y;
+    if (vec4) {
+        const float4* z4 = reinterpret_cast<const float4*>(z);
+        for (int n4 = threadIdx.x; n4 < nst / 4; n4 += kRowThreads) {
+            const float4 u = z4[2 * n4], w = z4[2 * n4 + 1];
+            reinterpret_cast<float4*>(oa)[n4] = make_float4(u.x, u.z, w.x, w.z);
+            if (has_b) reinterpret_cast<float4*>(ob)[n4] = make_float4(u.y, u.w, w.y, w.w);
+        }
+    } else {
+        for (int n = threadIdx.x; n < nst; n += kRowThreads) {
+            const float2 v = z[n];
+            oa[n] = v.x;
+            if (has_b) ob[n] = v.y;
+        }
     }
 }
 
-// Register-blocked wire convolution in the tick-frequency domain.  Thread
-// (k, block of B wires) keeps the K taps of column k in registers and
-// streams the B + K - 1 input rows its outputs need once each.
+// Register-blocked wire convolution in the tick-frequency domain.  A CTA
+// owns 128 frequency columns x B output wires; it stages the B + K - 1 input
+// rows those outputs need in shared memory with 16-byte loads (zeros outside
+// the grid in linear mode, wrapped rows in circular mode), then each thread
+// keeps its column's K taps and B accumulators in registers.
+constexpr int kConvCols = 128;
+
 template <int K, int B>
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(kConvCols)
 wire_conv_kernel(const float2* __restrict__ X, float2* __restrict__ Y, const float2* __restrict__ Rt,
                  int nwires, int nfreq, int64_t stride, int kw, int center, int circular) {
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    constexpr int ROWS = B + K - 1;
+    __shared__ float4 tile[ROWS][kConvCols / 2];
+    const int k0 = blockIdx.x * kConvCols;
     const int w0 = blockIdx.y * B;
+    const int ibase = w0 + center - (K - 1);
+    for (int e = threadIdx.x; e < ROWS * (kConvCols / 2); e += kConvCols) {
+        const int u = e / (kConvCols / 2), c2 = e - u * (kConvCols / 2);
+        int i = ibase + u;
+        const int kk = k0 + 2 * c2;
+        bool ok = kk < stride;
+        if (circular) {
+            i %= nwires;
+            if (i < 0) i += nwires;
+        } else {
+            ok = ok && i >= 0 && i < nwires;
+        }
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (ok) v = __ldg(reinterpret_cast<const float4*>(X + (int64_t)i * stride + kk));
+        tile[u][c2] = v;
+    }
+    __syncthreads();
+    const int k = k0 + threadIdx.x;
     if (k >= nfreq) return;
     float2 c[K];
 #pragma unroll
@@ -237,18 +411,10 @@ wire_conv_kernel(const float2* __restrict__ X, float2* __restrict__ Y, const flo
     float2 acc[B];
 #pragma unroll
     for (int b = 0; b < B; ++b) acc[b] = make_float2(0.f, 0.f);
-    const int ibase = w0 + center - (K - 1);
+    const float2* col = reinterpret_cast<const float2*>(&tile[0][0]) + threadIdx.x;
 #pragma unroll
-    for (int u = 0; u < B + K - 1; ++u) {
-        int i = ibase + u;
-        float2 x = make_float2(0.f, 0.f);
-        if (circular) {
-            i %= nwires;
-            if (i < 0) i += nwires;
-            x = __ldg(&X[(int64_t)i * stride + k]);
-        } else if (i >= 0 && i < nwires) {
-            x = __ldg(&X[(int64_t)i * stride + k]);
-        }
+    for (int u = 0; u < ROWS; ++u) {
+        const float2 x = col[u * kConvCols];
 #pragma unroll
         for (int b = 0; b < B; ++b) {
             const int r = b + K - 1 - u;
@@ -265,8 +431,8 @@ wire_conv_kernel(const float2* __restrict__ X, float2* __restrict__ Y, const flo
 
 }  // namespace
 
-cudaError_t launch_twiddles(float2* tw, int L, cudaStream_t s) {
-    twiddle_kernel<<<(L + 255) / 256, 256, 0, s>>>(tw, L);
+cudaError_t launch_twiddles(float2* tw, const FftPlan& plan, cudaStream_t s) {
+    pass_twiddles_kernel<<<(plan.L + 255) / 256, 256, 0, s>>>(tw, plan);
     return cudaGetLastError();
 }
 
@@ -278,11 +444,13 @@ cudaError_t launch_fwd_rows(const FftPlan& plan, const float2* tw, const float* 
                             int ncols, int64_t in_stride, float2* out, int64_t out_stride,
                             int nfreq, float scale, cudaStream_t s) {
     if (nrows <= 0) return cudaSuccess;
-    const int smem = 2 * plan.L * (int)sizeof(float2);
+    const int smem = 2 * ((plan.L + 1) & ~1) * (int)sizeof(float2);
     cudaError_t e = set_smem((const void*)fwd_rows_kernel, smem);
     if (e != cudaSuccess) return e;
+    const int nload = ncols < plan.L ? ncols : plan.L;
+    const int vec4 = ((uintptr_t)in % 16 == 0) && (in_stride % 4 == 0) && (nload % 4 == 0);
     fwd_rows_kernel<<<(nrows + 1) / 2, kRowThreads, smem, s>>>(plan, tw, in, nrows, ncols, in_stride,
-                                                               out, out_stride, nfreq, scale);
+                                                               out, out_stride, nfreq, scale, vec4);
     return cudaGetLastError();
 }
 
@@ -290,11 +458,13 @@ cudaError_t launch_inv_rows(const FftPlan& plan, const float2* tw, const float2*
                             int64_t in_stride, int nfreq, float* out, int ncols,
                             int64_t out_stride, cudaStream_t s) {
     if (nrows <= 0) return cudaSuccess;
-    const int smem = 2 * plan.L * (int)sizeof(float2);
+    const int smem = 2 * ((plan.L + 1) & ~1) * (int)sizeof(float2);
     cudaError_t e = set_smem((const void*)inv_rows_kernel, smem);
     if (e != cudaSuccess) return e;
+    const int nst = ncols < plan.L ? ncols : plan.L;
+    const int vec4 = ((uintptr_t)out % 16 == 0) && (out_stride % 4 == 0) && (nst % 4 == 0);
     inv_rows_kernel<<<(nrows + 1) / 2, kRowThreads, smem, s>>>(plan, tw, in, nrows, in_stride, nfreq,
-                                                               out, ncols, out_stride);
+                                                               out, ncols, out_stride, vec4);
     return cudaGetLastError();
 }
 
@@ -302,8 +472,8 @@ cudaError_t launch_wire_conv(const float2* X, float2* Y, const float2* Rt, int n
                              int64_t stride, int kw, int center, int circular, cudaStream_t s) {
     if (nwires <= 0 || nfreq <= 0) return cudaSuccess;
     constexpr int K = kMaxRespWires, B = 16;
-    dim3 grid((nfreq + 127) / 128, (nwires + B - 1) / B);
-    wire_conv_kernel<K, B><<<grid, 128, 0, s>>>(X, Y, Rt, nwires, nfreq, stride, kw, center, circular);
+    dim3 grid((nfreq + kConvCols - 1) / kConvCols, (nwires + B - 1) / B);
+    wire_conv_kernel<K, B><<<grid, kConvCols, 0, s>>>(X, Y, Rt, nwires, nfreq, stride, kw, center, circular);
     return cudaGetLastError();
 }
 

@@ -39,39 +39,39 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1
     return c;
 }
 
-// Survivors of N electrons with survival threshold T (p = T / 2^32).
-// N <= exact_max: count the first N Philox words below T (blocks j = 0..).
-// Otherwise the normal approximation from block 0 (Box-Muller), with the
-// integer part of N p taken exactly from the 64-bit product N T.
-__device__ float binomial_draw(int N, const RasterArgs& a, uint32_t bin, uint32_t depo) {
-    if (N <= 0 || a.T == 0u) return 0.f;
-    if (a.p >= 1.f) return (float)N;
+// Survivor count contributed by Philox block j of a bin holding N electrons
+// (the bin's binomial draw is the sum over its blocks):
+//   N <= exact_max: block j covers trials 4j .. 4j+3 (< N); a trial survives
+//     when its 32-bit word is below T (p = T / 2^32);
+//   N >  exact_max: one block, normal approximation by Box-Muller with the
+//     integer part of N p taken exactly from the 64-bit product N T.
+__device__ __forceinline__ int binomial_block(int N, int j, const RasterArgs& a, uint32_t bin, uint32_t depo) {
+    const uint4 x = philox4x32_10(make_uint4((uint32_t)j, bin, depo, a.evpl), a.key0, a.key1);
     if (N <= a.exact_max) {
-        int k = 0;
-        for (int j = 0; 4 * j < N; ++j) {
-            const uint4 x = philox4x32_10(make_uint4((uint32_t)j, bin, depo, a.evpl), a.key0, a.key1);
-            const int m = N - 4 * j;
-            k += (x.x < a.T);
-            if (m > 1) k += (x.y < a.T);
-            if (m > 2) k += (x.z < a.T);
-            if (m > 3) k += (x.w < a.T);
-        }
-        return (float)k;
+        const int m = N - 4 * j;
+        int k = (x.x < a.T);
+        if (m > 1) k += (x.y < a.T);
+        if (m > 2) k += (x.z < a.T);
+        if (m > 3) k += (x.w < a.T);
+        return k;
     }
-    const uint4 x = philox4x32_10(make_uint4(0u, bin, depo, a.evpl), a.key0, a.key1);
     const float two_m32 = 2.3283064365386963e-10f;  // 2^-32
     const float u1 = fmaf((float)x.x, two_m32, 0.5f * two_m32);
     const float u2 = fmaf((float)x.y, two_m32, 0.5f * two_m32);
     const float z = sqrtf(-2.f * logf(u1)) * cospif(2.f * u2);
     const uint64_t nt = (uint64_t)(uint32_t)N * (uint64_t)a.T;
-    const float ipart = (float)(uint32_t)(nt >> 32);
+    const int ipart = (int)(uint32_t)(nt >> 32);
     const float frac = (float)(uint32_t)nt * two_m32;
     const float pe = (float)a.T * two_m32;
-    const float mean = ipart + frac;
-    const float sd = sqrtf(mean * (1.f - pe));
-    float k = ipart + floorf(frac + z * sd + 0.5f);
-    k = fminf(fmaxf(k, 0.f), (float)N);
-    return k;
+    const float sd = sqrtf(((float)ipart + frac) * (1.f - pe));
+    int k = ipart + (int)floorf(frac + z * sd + 0.5f);
+    return k < 0 ? 0 : (k > N ? N : k);
+}
+
+// Philox blocks a bin of N electrons needs.
+__device__ __forceinline__ int binomial_items(int N, const RasterArgs& a) {
+    if (N <= 0 || a.T == 0u || a.keep_all) return 0;
+    return N <= a.exact_max ? (N + 3) >> 2 : 1;
 }
 
 // Per-depo geometry: widths and the patch's bin range clipped to the grid.
@@ -164,22 +164,42 @@ __device__ __forceinline__ void axis_weights(float mu, float sigma, float delta,
 
 enum { EMIT_GRID = 0, EMIT_PATCH = 1 };
 
+constexpr int kSmallT = 16;  // largest patch (ticks x wires) the lane-per-depo kernel takes
+constexpr int kSmallW = 8;
+
+__device__ __forceinline__ bool is_large(const Extent& e) {
+    return (e.k1 - e.k0 + 1) > kSmallT || (e.w1 - e.w0 + 1) > kSmallW;
+}
+
+// Warp per depo.  With list == nullptr every depo is processed; otherwise
+// only the large patches the lane-per-depo kernel handed over: the list's
+// entries if they fit in it, else every depo whose patch is large.  The
+// last block to finish resets the list counter for the next launch.
 template <int MODE>
 __global__ void __launch_bounds__(32 * kWarpsPerBlock)
-raster_kernel(RasterArgs a, float* __restrict__ grid, ws_patches pt, int64_t dummy) {
+raster_kernel(RasterArgs a, float* __restrict__ grid, ws_patches pt, const int* __restrict__ list,
+              unsigned* list_count, unsigned list_cap, unsigned* done) {
     __shared__ float s_u[kWarpsPerBlock][kChunk + 1];
     __shared__ float s_c[kWarpsPerBlock][kChunk + 1];
     __shared__ float s_wt[kWarpsPerBlock][kChunk];
     __shared__ float s_wx[kWarpsPerBlock][kChunk];
+    __shared__ int s_incl[kWarpsPerBlock][32];
+    __shared__ int s_n[kWarpsPerBlock][32];
+    __shared__ int s_cnt[kWarpsPerBlock][32];
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
     const int64_t nwarps = (int64_t)gridDim.x * kWarpsPerBlock;
     const float inv_norm = 1.f / erff(a.nsig * 0.707106781186547524f);
-    for (int64_t i = (int64_t)blockIdx.x * kWarpsPerBlock + wib; i < a.n; i += nwarps) {
+    const unsigned nlist = list ? *(volatile unsigned*)list_count : 0u;
+    const bool use_list = list != nullptr && nlist <= list_cap;
+    const int64_t nitems = list == nullptr ? a.n : (use_list ? (int64_t)nlist : a.n);
+    for (int64_t it = (int64_t)blockIdx.x * kWarpsPerBlock + wib; it < nitems; it += nwarps) {
+        const int64_t i = use_list ? (int64_t)list[it] : it;
         Extent e;
         float q;
         bool bad;
         const bool any = depo_extent(a, i, &e, &q, &bad);
+        if (list != nullptr && !(any && is_large(e))) continue;  // not handed over
         if (bad && lane == 0) atomicOr(a.status, WS_DEV_BAD_DEPO);
         int64_t off = 0;
         int ntf = 0;
@@ -208,26 +228,252 @@ raster_kernel(RasterArgs a, float* __restrict__ grid, ws_patches pt, int64_t dum
                 axis_weights(e.mu_x, e.sx, a.pitch, a.nsig, e.point_x, wc, nxc, inv_norm, s_u[wib],
                              s_c[wib], s_wx[wib], lane);
                 const int nbin = nxc * ntc;
-                for (int idx = lane; idx < nbin; idx += 32) {
-                    const int ia = idx / ntc, ib = idx - ia * ntc;
-                    const int w = wc + ia, k = kc + ib;
-                    float v;
-                    if (a.fluct) {
-                        const float nexp = q * s_wx[wib][ia] * s_wt[wib][ib];
-                        const int N = (int)floorf(nexp + 0.5f);
-                        v = binomial_draw(N, a, (uint32_t)((int64_t)w * a.nticks + k), (uint32_t)i);
-                    } else {
-                        v = scale * s_wx[wib][ia] * s_wt[wib][ib];
+                if (!a.fluct) {
+                    for (int idx = lane; idx < nbin; idx += 32) {
+                        const int ia = idx / ntc, ib = idx - ia * ntc;
+                        const int w = wc + ia, k = kc + ib;
+                        const float v = scale * s_wx[wib][ia] * s_wt[wib][ib];
+                        if (MODE == EMIT_GRID) {
+                            if (v != 0.f) atomicAdd(grid + (int64_t)w * a.nticks + k, v);
+                        } else {
+                            pt.val[off + (int64_t)(w - e.w0) * ntf + (k - e.k0)] = v;
+                        }
                     }
+                }
+                // Binomial mode: 32 bins per round; each (bin, Philox block)
+                // pair is one work item so the lanes share the draws evenly.
+                for (int base = 0; a.fluct && base < nbin; base += 32) {
+                    const int idx = base + lane;
+                    int N = 0, w = 0, k = 0;
+                    if (idx < nbin) {
+                        const int ia = idx / ntc, ib = idx - ia * ntc;
+                        w = wc + ia;
+                        k = kc + ib;
+                        const float nexp = fminf(q * s_wx[wib][ia] * s_wt[wib][ib], 1.0e9f);
+                        N = (int)floorf(nexp + 0.5f);
+                    }
+                    const int items = binomial_items(N, a);
+                    int incl = items;
+#pragma unroll
+                    for (int o = 1; o < 32; o <<= 1) {
+                        const int y = __shfl_up_sync(0xffffffffu, incl, o);
+                        if (lane >= o) incl += y;
+                    }
+                    const int total = __shfl_sync(0xffffffffu, incl, 31);
+                    s_incl[wib][lane] = incl;
+                    s_n[wib][lane] = N;
+                    s_cnt[wib][lane] = (N > 0 && a.keep_all) ? N : 0;
+                    __syncwarp();
+                    for (int it = lane; it < total; it += 32) {
+                        int lo = 0, hi = 31;  // first bin slot whose inclusive count exceeds it
+                        while (lo < hi) {
+                            const int mid = (lo + hi) >> 1;
+                            if (s_incl[wib][mid] > it) hi = mid; else lo = mid + 1;
+                        }
+                        const int first = lo > 0 ? s_incl[wib][lo - 1] : 0;
+                        const int bidx = base + lo;
+                        const int ia = bidx / ntc, ib = bidx - ia * ntc;
+                        const uint32_t gbin = (uint32_t)((int64_t)(wc + ia) * a.nticks + (kc + ib));
+                        const int c = binomial_block(s_n[wib][lo], it - first, a, gbin, (uint32_t)i);
+                        if (c) atomicAdd(&s_cnt[wib][lo], c);
+                    }
+                    __syncwarp();
+                    if (idx < nbin) {
+                        const float v = (float)s_cnt[wib][lane];
+                        if (MODE == EMIT_GRID) {
+                            if (v != 0.f) atomicAdd(grid + (int64_t)w * a.nticks + k, v);
+                        } else {
+                            pt.val[off + (int64_t)(w - e.w0) * ntf + (k - e.k0)] = v;
+                        }
+                    }
+                    __syncwarp();
+                }
+                __syncwarp();
+            }
+        }
+    }
+    if (list != nullptr) {
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            __threadfence();
+            if (atomicAdd(done, 1u) == gridDim.x - 1) {
+                *list_count = 0u;
+                *done = 0u;
+                __threadfence();
+            }
+        }
+    }
+}
+
+// Lane per depo for patches of at most kSmallT x kSmallW bins: each lane
+// computes its depo's widths, clipped bin range and the erfc edge tables of
+// both axes into shared memory; the warp then spreads the ~32 patches' bins
+// (and, with fluctuation, their Philox blocks) evenly over its lanes.
+// Larger patches are appended to a list for the warp-per-depo kernel.
+constexpr int kSmallWarpsPerBlock = 4;
+
+__device__ __forceinline__ void lane_axis_weights(float mu, float sigma, float delta, float nsig, bool point,
+                                                  int first, int nb, float inv_norm, float* w) {
+    if (point) {
+        w[0] = 1.f;
+        return;
+    }
+    const float inv_s2 = 1.f / (1.41421356237309505f * sigma);
+    const float umax = nsig * 0.707106781186547524f;
+    float u_prev = 0.f, c_prev = 0.f;
+    for (int j = 0; j <= nb; ++j) {
+        const float e = (float)(first + j) * delta;
+        float u = fminf(fmaxf((e - mu) * inv_s2, -umax), umax);
+        const float c = erfcf(fabsf(u));
+        if (j > 0) {
+            float m;
+            if (u_prev >= 0.f) m = 0.5f * (c_prev - c);
+            else if (u <= 0.f) m = 0.5f * (c - c_prev);
+            else m = 1.f - 0.5f * (c_prev + c);
+            w[j - 1] = m * inv_norm;
+        }
+        u_prev = u;
+        c_prev = c;
+    }
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(32 * kSmallWarpsPerBlock)
+raster_small_kernel(RasterArgs a, float* __restrict__ grid, ws_patches pt, int* __restrict__ list,
+                    unsigned* list_count, unsigned list_cap) {
+    constexpr int W = kSmallWarpsPerBlock;
+    __shared__ float s_wt[W][32][kSmallT + 1];
+    __shared__ float s_wx[W][32][kSmallW + 1];
+    __shared__ int s_off[W][32];
+    __shared__ int s_k0[W][32];
+    __shared__ int s_w0[W][32];
+    __shared__ int s_nt[W][32];
+    __shared__ float s_q[W][32];
+    __shared__ unsigned char s_own[W][32 * kSmallT * kSmallW];
+    __shared__ int s_incl[W][32];
+    __shared__ int s_cnt[W][32];
+    __shared__ int s_n[W][32];
+    __shared__ uint32_t s_gbin[W][32];
+    __shared__ uint32_t s_dep[W][32];
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    const int64_t nwarps = (int64_t)gridDim.x * W;
+    const float inv_norm = 1.f / erff(a.nsig * 0.707106781186547524f);
+    for (int64_t base = ((int64_t)blockIdx.x * W + wib) * 32; base < a.n; base += nwarps * 32) {
+        const int64_t i = base + lane;
+        Extent e;
+        float q = 0.f;
+        bool bad = false, any = false;
+        if (i < a.n) any = depo_extent(a, i, &e, &q, &bad);
+        if (bad) atomicOr(a.status, WS_DEV_BAD_DEPO);
+        const bool large = any && is_large(e);
+        if (large) {
+            const unsigned slot = atomicAdd(list_count, 1u);
+            if (slot < list_cap) list[slot] = (int)i;
+        }
+        const int ntc = any ? e.k1 - e.k0 + 1 : 0;
+        const int nxc = any ? e.w1 - e.w0 + 1 : 0;
+        int nb = (any && !large) ? ntc * nxc : 0;
+        if (MODE == EMIT_PATCH && i < a.n && !large) {
+            const int64_t off = pt.off[i];
+            const bool fits = off + nb <= pt.capacity_bins;
+            pt.w0[i] = any ? e.w0 : 0;
+            pt.t0[i] = any ? e.k0 : 0;
+            pt.nw[i] = fits ? nxc : 0;
+            pt.nt[i] = fits ? ntc : 0;
+            if (!fits) {
+                atomicOr(a.status, WS_DEV_PATCH_OVERFLOW);
+                nb = 0;
+            }
+        }
+        if (nb > 0) {
+            lane_axis_weights(e.mu_t, e.st, a.tick, a.nsig, e.point_t, e.k0, ntc, inv_norm, s_wt[wib][lane]);
+            lane_axis_weights(e.mu_x, e.sx, a.pitch, a.nsig, e.point_x, e.w0, nxc, inv_norm, s_wx[wib][lane]);
+        }
+        int incl = nb;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        const int total = __shfl_sync(0xffffffffu, incl, 31);
+        const int first = incl - nb;
+        s_off[wib][lane] = first;
+        s_k0[wib][lane] = any ? e.k0 : 0;
+        s_w0[wib][lane] = any ? e.w0 : 0;
+        s_nt[wib][lane] = ntc;
+        s_q[wib][lane] = a.fluct ? q : a.p * q;
+        for (int j = 0; j < nb; ++j) s_own[wib][first + j] = (unsigned char)lane;
+        __syncwarp();
+        if (!a.fluct) {
+            for (int g = lane; g < total; g += 32) {
+                const int d = s_own[wib][g];
+                const int local = g - s_off[wib][d];
+                const int nt = s_nt[wib][d];
+                const int ia = local / nt, ib = local - ia * nt;
+                const float v = s_q[wib][d] * s_wx[wib][d][ia] * s_wt[wib][d][ib];
+                if (MODE == EMIT_GRID) {
+                    if (v != 0.f) atomicAdd(grid + (int64_t)(s_w0[wib][d] + ia) * a.nticks + s_k0[wib][d] + ib, v);
+                } else {
+                    pt.val[pt.off[base + d] + local] = v;
+                }
+            }
+        } else {
+            for (int gb = 0; gb < total; gb += 32) {
+                const int g = gb + lane;
+                int N = 0, d = 0, local = 0, w = 0, k = 0;
+                if (g < total) {
+                    d = s_own[wib][g];
+                    local = g - s_off[wib][d];
+                    const int nt = s_nt[wib][d];
+                    const int ia = local / nt, ib = local - ia * nt;
+                    w = s_w0[wib][d] + ia;
+                    k = s_k0[wib][d] + ib;
+                    const float nexp = fminf(s_q[wib][d] * s_wx[wib][d][ia] * s_wt[wib][d][ib], 1.0e9f);
+                    N = (int)floorf(nexp + 0.5f);
+                }
+                const uint32_t gbin = (uint32_t)((int64_t)w * a.nticks + k);
+                const uint32_t dep = (uint32_t)(base + d);
+                const int items = binomial_items(N, a);
+                int cnt = (N > 0 && a.keep_all) ? N : 0;
+                if (items > 0 && N > a.exact_max) cnt = binomial_block(N, 0, a, gbin, dep);
+                const int ne = N <= a.exact_max ? items : 0;
+                int inc = ne;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int y = __shfl_up_sync(0xffffffffu, inc, o);
+                    if (lane >= o) inc += y;
+                }
+                const int tot = __shfl_sync(0xffffffffu, inc, 31);
+                s_incl[wib][lane] = inc;
+                s_cnt[wib][lane] = cnt;
+                s_n[wib][lane] = N;
+                s_gbin[wib][lane] = gbin;
+                s_dep[wib][lane] = dep;
+                __syncwarp();
+                for (int it = lane; it < tot; it += 32) {
+                    int lo = 0, hi = 31;  // first slot whose inclusive count exceeds it
+                    while (lo < hi) {
+                        const int mid = (lo + hi) >> 1;
+                        if (s_incl[wib][mid] > it) hi = mid; else lo = mid + 1;
+                    }
+                    const int j = it - (lo > 0 ? s_incl[wib][lo - 1] : 0);
+                    const int c = binomial_block(s_n[wib][lo], j, a, s_gbin[wib][lo], s_dep[wib][lo]);
+                    if (c) atomicAdd(&s_cnt[wib][lo], c);
+                }
+                __syncwarp();
+                if (g < total) {
+                    const float v = (float)s_cnt[wib][lane];
                     if (MODE == EMIT_GRID) {
                         if (v != 0.f) atomicAdd(grid + (int64_t)w * a.nticks + k, v);
                     } else {
-                        pt.val[off + (int64_t)(w - e.w0) * ntf + (k - e.k0)] = v;
+                        pt.val[pt.off[base + d] + local] = v;
                     }
                 }
                 __syncwarp();
             }
         }
+        __syncwarp();
     }
 }
 
@@ -360,10 +606,13 @@ int num_sms() {
     return n;
 }
 
-cudaError_t launch_raster_scatter(const RasterArgs& a, float* grid, cudaStream_t s) {
+cudaError_t launch_raster_scatter(const RasterArgs& a, float* grid, const LargeList& L, cudaStream_t s) {
     if (a.n <= 0) return cudaSuccess;
     ws_patches none{};
-    raster_kernel<EMIT_GRID><<<grid_for(a.n, kWarpsPerBlock, 8), 32 * kWarpsPerBlock, 0, s>>>(a, grid, none, 0);
+    raster_small_kernel<EMIT_GRID><<<grid_for(a.n, 32 * kSmallWarpsPerBlock, 16), 32 * kSmallWarpsPerBlock, 0, s>>>(
+        a, grid, none, L.list, L.count, L.cap);
+    raster_kernel<EMIT_GRID><<<num_sms() * 2, 32 * kWarpsPerBlock, 0, s>>>(a, grid, none, L.list, L.count, L.cap,
+                                                                          L.done);
     return cudaGetLastError();
 }
 
@@ -382,9 +631,12 @@ cudaError_t launch_scan_inplace(int64_t* v, int64_t n, int64_t* scratch, cudaStr
     return cudaGetLastError();
 }
 
-cudaError_t launch_raster_patches(const RasterArgs& a, const ws_patches& p, cudaStream_t s) {
+cudaError_t launch_raster_patches(const RasterArgs& a, const ws_patches& p, const LargeList& L, cudaStream_t s) {
     if (a.n <= 0) return cudaSuccess;
-    raster_kernel<EMIT_PATCH><<<grid_for(a.n, kWarpsPerBlock, 8), 32 * kWarpsPerBlock, 0, s>>>(a, nullptr, p, 0);
+    raster_small_kernel<EMIT_PATCH><<<grid_for(a.n, 32 * kSmallWarpsPerBlock, 16), 32 * kSmallWarpsPerBlock, 0, s>>>(
+        a, nullptr, p, L.list, L.count, L.cap);
+    raster_kernel<EMIT_PATCH><<<num_sms() * 2, 32 * kWarpsPerBlock, 0, s>>>(a, nullptr, p, L.list, L.count, L.cap,
+                                                                           L.done);
     return cudaGetLastError();
 }
 

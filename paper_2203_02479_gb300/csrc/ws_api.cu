@@ -79,17 +79,29 @@ int next_smooth(int n) {
     return n;
 }
 
-// Radix passes for L: fours first, then fives, threes and a last two.
+// Radix passes for L: greedily the largest supported radix that divides
+// what is left (25, 16, 20, 15, 12, 10, 9, 8, 6, 5, 4, 3, 2), so a 6250-point
+// transform is 25 x 25 x 10 and a 6000-point one 25 x 16 x 15.
 bool make_plan(int L, ws::FftPlan* p) {
     if (!smooth235(L) || L < 2 || L > ws::kMaxFftLen) return false;
+    static const int kRadices[] = {25, 16, 20, 15, 12, 10, 9, 8, 6, 5, 4, 3, 2};
     p->L = L;
     p->npass = 0;
-    int n = L;
-    while (n % 4 == 0) { p->radix[p->npass++] = 4; n /= 4; }
-    while (n % 5 == 0) { p->radix[p->npass++] = 5; n /= 5; }
-    while (n % 3 == 0) { p->radix[p->npass++] = 3; n /= 3; }
-    while (n % 2 == 0) { p->radix[p->npass++] = 2; n /= 2; }
-    return p->npass <= ws::kMaxPasses && n == 1;
+    int n = L, ns = 1, off = 0;
+    while (n > 1) {
+        int r = 0;
+        for (int c : kRadices)
+            if (n % c == 0) { r = c; break; }
+        if (r == 0 || p->npass >= ws::kMaxPasses) return false;
+        p->radix[p->npass] = r;
+        p->ns[p->npass] = ns;
+        p->twoff[p->npass] = off;
+        off += ns;
+        ns *= r;
+        n /= r;
+        ++p->npass;
+    }
+    return true;
 }
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -97,7 +109,7 @@ size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 struct Layout {
     ws::FftPlan plan;
     int nfreq, fstride;
-    size_t off_status, off_tw, off_rt, off_x, off_y, off_scan, total;
+    size_t off_status, off_tw, off_rt, off_x, off_y, off_scan, off_large, total;
 };
 
 ws_status plan_layout(const ws_plane_desc* d, Layout* lay) {
@@ -132,6 +144,7 @@ ws_status plan_layout(const ws_plane_desc* d, Layout* lay) {
     lay->off_x = o; o = align256(o + sizeof(float2) * (size_t)d->nwires * lay->fstride);
     lay->off_y = o; o = align256(o + sizeof(float2) * (size_t)d->nwires * lay->fstride);
     lay->off_scan = o; o = align256(o + sizeof(int64_t) * (size_t)ws::kScanScratch);
+    lay->off_large = o; o = align256(o + sizeof(int) * (size_t)ws::kLargeListCap);
     lay->total = o;
     return WS_OK;
 }
@@ -153,7 +166,7 @@ ws_status check_params(const ws_params* p) {
     if (!(p->v_mm_us > 0) || !(p->DL_mm2_us >= 0) || !(p->DT_mm2_us >= 0)) return WS_ERR_INVALID_ARG;
     if (!(p->p_survive >= 0) || !(p->p_survive <= 1)) return WS_ERR_INVALID_ARG;
     if (p->event_id >= (1u << 28)) return WS_ERR_INVALID_ARG;
-    if (p->fluct_exact_max < 0) return WS_ERR_INVALID_ARG;
+    if (p->fluct_exact_max < 0 || p->fluct_exact_max > (1 << 27)) return WS_ERR_INVALID_ARG;
     if (p->precision != WS_PREC_FP32 && p->precision != WS_PREC_FP32_COMP && p->precision != WS_PREC_FP64)
         return WS_ERR_INVALID_ARG;
     return WS_OK;
@@ -178,6 +191,7 @@ ws::RasterArgs raster_args(const ws_plane* pl, const ws_depos* d, const ws_param
     a.key0 = (uint32_t)(p->seed & 0xFFFFFFFFu);
     a.key1 = (uint32_t)(p->seed >> 32);
     a.evpl = (p->event_id << 4) | ((uint32_t)pl->desc.plane_id & 15u);
+    a.keep_all = p->p_survive >= 1.0 ? 1 : 0;
     a.exact_max = p->fluct_exact_max;
     a.status = pl->status;
     return a;
@@ -249,9 +263,13 @@ ws_status ws_plane_create(const ws_plane_desc* desc, const float* response_dev, 
     pl->X = (float2*)(base + lay.off_x);
     pl->Y = (float2*)(base + lay.off_y);
     pl->scan = (int64_t*)(base + lay.off_scan);
+    pl->large.list = (int*)(base + lay.off_large);
+    pl->large.count = (unsigned*)(base + lay.off_status + 16);
+    pl->large.done = (unsigned*)(base + lay.off_status + 20);
+    pl->large.cap = ws::kLargeListCap;
     cudaStream_t s = (cudaStream_t)stream;
     cudaError_t e = cudaMemsetAsync(base + lay.off_status, 0, 256, s);
-    if (e == cudaSuccess) e = ws::launch_twiddles(pl->tw, lay.plan.L, s);
+    if (e == cudaSuccess) e = ws::launch_twiddles(pl->tw, lay.plan, s);
     // Response spectrum: per response row, the tick transform scaled by 1/L so
     // that the inverse transform needs no scaling.
     if (e == cudaSuccess)
@@ -378,7 +396,7 @@ ws_status ws_rasterize(ws_plane* pl, const ws_depos* depos, const ws_params* par
     ws::RasterArgs a = raster_args(pl, depos, params);
     WS_LAUNCH(pl, K_SIZES, s, ws::launch_patch_sizes(a, out->off, nullptr, s));
     WS_LAUNCH(pl, K_SCAN, s, ws::launch_scan_inplace(out->off, depos->n + 1, pl->scan, s));
-    WS_LAUNCH(pl, K_RPATCH, s, ws::launch_raster_patches(a, *out, s));
+    WS_LAUNCH(pl, K_RPATCH, s, ws::launch_raster_patches(a, *out, pl->large, s));
     return WS_OK;
 }
 
@@ -408,7 +426,7 @@ ws_status ws_simulate(ws_plane* pl, const ws_depos* depos, const ws_params* para
     const size_t grid_bytes = sizeof(float) * (size_t)pl->desc.nwires * pl->desc.nticks;
     WS_LAUNCH(pl, K_MEMSET, s, cudaMemsetAsync(out_dev, 0, grid_bytes, s));
     ws::RasterArgs a = raster_args(pl, depos, params);
-    WS_LAUNCH(pl, K_RASTER_SCATTER, s, ws::launch_raster_scatter(a, out_dev, s));
+    WS_LAUNCH(pl, K_RASTER_SCATTER, s, ws::launch_raster_scatter(a, out_dev, pl->large, s));
     return convolve_impl(pl, out_dev, out_dev, s);
 }
 

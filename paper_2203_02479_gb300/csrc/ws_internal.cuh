@@ -19,6 +19,8 @@ struct FftPlan {
     int L;
     int npass;
     int radix[kMaxPasses];
+    int ns[kMaxPasses];     // product of the radices before pass p
+    int twoff[kMaxPasses];  // offset of pass p's Ns base twiddles
 };
 
 // Launch geometry and constants of a raster pass.
@@ -35,7 +37,8 @@ struct RasterArgs {
     float two_DL, two_DT, inv_v;
     int fluct;
     float p;              // survival probability (expected-value scale)
-    uint32_t T;           // floor(p * 2^32), 0xFFFFFFFF for p >= 1
+    uint32_t T;           // floor(p * 2^32), 0 for p <= 0
+    int keep_all;         // p >= 1: every electron survives
     uint32_t key0, key1;  // Philox key from the seed
     uint32_t evpl;        // (event_id << 4) | plane_id
     int exact_max;
@@ -43,7 +46,8 @@ struct RasterArgs {
 };
 
 // ---- FFT / convolution launchers (fft.cu)
-cudaError_t launch_twiddles(float2* tw, int L, cudaStream_t s);
+// Pass twiddle table: Ns base twiddles per pass (see FftPlan::twoff).
+cudaError_t launch_twiddles(float2* tw, const FftPlan& plan, cudaStream_t s);
 // Real rows -> half spectra: out[r][k] = scale * sum_n in[r][n] e^{-2 pi i k n / L}
 // for k < nfreq; rows shorter than L are zero padded.
 cudaError_t launch_fwd_rows(const FftPlan& plan, const float2* tw, const float* in, int nrows,
@@ -59,12 +63,23 @@ cudaError_t launch_wire_conv(const float2* X, float2* Y, const float2* Rt, int n
                              int nfreq, int64_t stride, int kw, int center, int circular,
                              cudaStream_t s);
 
+// Hand-over list of depos whose patches are too large for the lane-per-depo
+// raster kernel (workspace-resident; count and done must start at zero and
+// are reset by the second kernel).
+struct LargeList {
+    int* list;
+    unsigned* count;
+    unsigned* done;
+    unsigned cap;
+};
+constexpr unsigned kLargeListCap = 65536;
+
 // ---- raster / scatter launchers (raster.cu)
-cudaError_t launch_raster_scatter(const RasterArgs& a, float* grid, cudaStream_t s);
+cudaError_t launch_raster_scatter(const RasterArgs& a, float* grid, const LargeList& L, cudaStream_t s);
 cudaError_t launch_patch_sizes(const RasterArgs& a, int64_t* sizes, unsigned long long* total,
                                cudaStream_t s);
 cudaError_t launch_scan_inplace(int64_t* v, int64_t n, int64_t* scratch, cudaStream_t s);
-cudaError_t launch_raster_patches(const RasterArgs& a, const ws_patches& p, cudaStream_t s);
+cudaError_t launch_raster_patches(const RasterArgs& a, const ws_patches& p, const LargeList& L, cudaStream_t s);
 cudaError_t launch_scatter_patches(const ws_patches& p, float* grid, int nwires, int nticks,
                                    cudaStream_t s);
 
@@ -89,4 +104,5 @@ struct ws_plane {
     float2* X;          // nwires x fstride
     float2* Y;          // nwires x fstride
     int64_t* scan;      // scan scratch
+    ws::LargeList large;  // hand-over list of large patches
 };

@@ -240,10 +240,10 @@ def test_fluctuation_exact_branch_is_bit_exact(ws):
     q, x, t = _sparse_depos(300, nw, nt, 31)
     plane = ws.Plane(nw, nt, inputs.response(), plane_id=2)
     params = ws.Params(fluctuate=True, p_survive=0.7, seed=0xDEADBEEF12345, event_id=5,
-                       fluct_exact_max=1 << 30)
+                       fluct_exact_max=1 << 27)
     _, S = gpu_grid_via_patches(ws, plane, ws.DeviceDepos(q, x, t), params)
     ref = oracle.raster_scatter(q, x, t, nw, nt, fluctuate=True, p=0.7, seed=0xDEADBEEF12345,
-                                event_id=5, plane_id=2, exact_max=1 << 30)
+                                event_id=5, plane_id=2, exact_max=1 << 27)
     qw = oracle.raster_scatter(q, x, t, nw, nt)
     amb = _boundary_mask(qw)
     assert (S[~amb] == ref[~amb]).all()
