@@ -199,6 +199,28 @@ ws_status ws_convolve(ws_plane* plane, const float* grid_dev, float* out_dev, vo
 ws_status ws_simulate(ws_plane* plane, const ws_depos* depos, const ws_params* params,
                       float* out_dev, void* stream);
 
+/* The convolution of ws_convolve for callers that cannot allocate device
+ * memory (no cudaMalloc, no workspace to hand over): only the response,
+ * the input grid and the output grid are passed.  The paper has no
+ * counterpart; this is a deployment convenience.
+ *   - Scratch is one 16 MiB file-scope __device__ array inside the library,
+ *     held by every GPU that loads it until the process exits.  Planes whose
+ *     scratch (twiddles + response spectrum + two nwires x (L_t/2+1)
+ *     complex64 spectra, each rounded to 256 bytes) exceeds 16 MiB are
+ *     rejected with WS_ERR_WORKSPACE before anything is enqueued (e.g. up to
+ *     ~330 wires at 6000 ticks).
+ *   - The first call on a device, with that device current, looks up the
+ *     array's device address (cudaGetSymbolAddress); make that first call
+ *     before any stream capture.
+ *   - Every call shares the array and recomputes the response spectrum; it
+ *     keeps the last call's contents.  Calls that overlap on the GPU race on
+ *     it: order them on one stream.
+ *   - Allocates nothing (no cudaMalloc/cudaFree, no allocating library
+ *     call).  desc, grid_dev and out_dev as for ws_plane_create and
+ *     ws_convolve (grid and out may be the same buffer). */
+ws_status ws_convolve_noalloc(const ws_plane_desc* desc, const float* response_dev,
+                              const float* grid_dev, float* out_dev, void* stream);
+
 /* Copy the plane's device status word to *bits.  SYNCHRONISES `stream`. */
 ws_status ws_plane_sync(ws_plane* plane, void* stream, uint32_t* bits);
 

@@ -211,6 +211,21 @@ ws_status convolve_impl(ws_plane* pl, const float* grid, float* out, cudaStream_
 
 }  // namespace
 
+namespace ws {
+// Transform plan of a plane description (same planner as ws_plane_create).
+ws_status conv_plan(const ws_plane_desc* desc, FftPlan* plan, int* nfreq, int* fstride) {
+    Layout lay;
+    ws_status st = plan_layout(desc, &lay);
+    if (st != WS_OK) return st;
+    *plan = lay.plan;
+    *nfreq = lay.nfreq;
+    *fstride = lay.fstride;
+    return WS_OK;
+}
+
+ws_status record_cuda_error(cudaError_t e, const char* where) { return cuda_fail(e, where); }
+}  // namespace ws
+
 extern "C" {
 
 const char* ws_status_string(ws_status s) {

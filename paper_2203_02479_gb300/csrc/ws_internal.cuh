@@ -85,6 +85,10 @@ cudaError_t launch_scatter_patches(const ws_patches& p, float* grid, int nwires,
 
 int num_sms();
 
+// Planner and error recording shared with the allocation-free entry point.
+ws_status conv_plan(const ws_plane_desc* desc, FftPlan* plan, int* nfreq, int* fstride);
+ws_status record_cuda_error(cudaError_t e, const char* where);
+
 }  // namespace ws
 
 struct ws_trace;

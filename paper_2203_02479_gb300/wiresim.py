@@ -31,7 +31,7 @@ WS_PREC_FP32, WS_PREC_FP32_COMP, WS_PREC_FP64 = 0, 1, 2
 EXPORTED = ("ws_plane_workspace_bytes", "ws_plane_create", "ws_plane_destroy", "ws_plane_get_info",
             "ws_patch_capacity", "ws_rasterize", "ws_scatter", "ws_convolve", "ws_simulate",
             "ws_plane_sync", "ws_plane_clear_status", "ws_plane_trace", "ws_plane_trace_read",
-            "ws_status_string", "ws_last_error")
+            "ws_convolve_noalloc", "ws_status_string", "ws_last_error")
 
 
 class WiresimError(RuntimeError):
@@ -114,6 +114,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
             "ws_plane_trace": [P, ctypes.c_int],
             "ws_plane_trace_read": [P, ctypes.POINTER(WsTraceStat), ctypes.c_int,
                                     ctypes.POINTER(ctypes.c_int)],
+            "ws_convolve_noalloc": [ctypes.POINTER(WsPlaneDesc), P, P, P, P],
         }
         for name, args in sig.items():
             fn = getattr(h, name)
@@ -207,6 +208,13 @@ def ws_plane_trace_read(plane: int) -> dict:
     _check(load_library().ws_plane_trace_read(plane, stats, 32, ctypes.byref(n)), "ws_plane_trace_read")
     return {stats[i].name.decode(): (int(stats[i].launches), float(stats[i].total_ms))
             for i in range(n.value)}
+
+
+def ws_convolve_noalloc(desc: WsPlaneDesc, response_dev: int, grid_dev: int, out_dev: int, stream: int):
+    """Convolution without any device allocation (scratch is a 16 MiB array
+    inside the library, shared by all calls); see include/wiresim.h."""
+    _check(load_library().ws_convolve_noalloc(ctypes.byref(desc), response_dev, grid_dev, out_dev, stream),
+           "ws_convolve_noalloc")
 
 
 # ---------------------------------------------------------- torch helpers
