@@ -355,6 +355,7 @@ def run_gpu(args):
                    "wires": [sp.nwires for sp in w.planes], "nticks": w.planes[0].nticks,
                    "fluctuate": w.fluctuate, "p_survive": w.p_survive,
                    "fft_len_tick": planes[0].info.fft_len_tick,
+                   "wire_conv_variant": [pl.info.wire_conv_variant for pl in planes],
                    "l2": "flushed between timed steps (512 MiB write)"},
         "planes_per_s": all_planes / (total_ms * 1e-3),
         "raster_scatter_depos_per_s": all_depos / (raster_ms * 1e-3) if raster_ms > 0 else None,

@@ -140,6 +140,9 @@ typedef struct {
     int32_t npasses;          /* FFT radix passes                           */
     int32_t radices[16];
     size_t workspace_bytes;
+    int32_t wire_conv_variant;  /* autotuned wire-convolution kernel: wire
+                                   block 16 (0, 1) or 8 (2, 3), Karatsuba
+                                   three-product taps (1, 3)                */
 } ws_plane_info;
 
 typedef struct ws_plane ws_plane;
@@ -152,7 +155,9 @@ ws_status ws_plane_workspace_bytes(const ws_plane_desc* desc, size_t* bytes);
 
 /* Create a plane over a caller-owned device workspace (>= the size above,
  * 256-byte aligned) and compute the response spectrum once (the transform
- * of R in Eq. 2) on `stream`.  response_dev: K_w x K_t float32, row-major,
+ * of R in Eq. 2) on `stream`.  It also autotunes the wire-convolution
+ * kernel by timing its variants on the plane's buffers, which SYNCHRONISES
+ * `stream` once.  response_dev: K_w x K_t float32, row-major,
  * row r holding wire offset r - resp_wire_center, column j tick offset j
  * (causal).  The response is read during this call's stream work only.
  * The plane object itself is host memory, freed by ws_plane_destroy. */
@@ -226,6 +231,10 @@ ws_status ws_plane_sync(ws_plane* plane, void* stream, uint32_t* bits);
 
 /* Clear the plane's device status word (stream-ordered). */
 ws_status ws_plane_clear_status(ws_plane* plane, void* stream);
+
+/* Override the autotuned wire-convolution kernel (0..3, see
+ * ws_plane_info.wire_conv_variant); all variants compute the same sum. */
+ws_status ws_plane_set_wire_conv_variant(ws_plane* plane, int variant);
 
 /* Launch tracing (timing of each kernel with CUDA events).  With
  * max_records > 0, every later launch on this plane is bracketed by a pair

@@ -378,7 +378,10 @@ inv_rows_kernel(FftPlan plan, const float2* __restrict__ tw, const float2* __res
 // keeps its column's K taps and B accumulators in registers.
 constexpr int kConvCols = 128;
 
-template <int K, int B>
+// KARATSUBA: with r = c + i d (tap) and x = a + i b (input), r x =
+// [c (a + b) - b (c + d)] + i [c (a + b) + a (d - c)]: three real products
+// per tap into three accumulators instead of four.
+template <int K, int B, bool KARATSUBA>
 __global__ void __launch_bounds__(kConvCols)
 wire_conv_kernel(const float2* __restrict__ X, float2* __restrict__ Y, const float2* __restrict__ Rt,
                  int nwires, int nfreq, int64_t stride, int kw, int center, int circular) {
@@ -405,28 +408,67 @@ wire_conv_kernel(const float2* __restrict__ X, float2* __restrict__ Y, const flo
     __syncthreads();
     const int k = k0 + threadIdx.x;
     if (k >= nfreq) return;
-    float2 c[K];
-#pragma unroll
-    for (int r = 0; r < K; ++r) c[r] = r < kw ? __ldg(&Rt[(int64_t)r * stride + k]) : make_float2(0.f, 0.f);
-    float2 acc[B];
-#pragma unroll
-    for (int b = 0; b < B; ++b) acc[b] = make_float2(0.f, 0.f);
     const float2* col = reinterpret_cast<const float2*>(&tile[0][0]) + threadIdx.x;
+    if constexpr (KARATSUBA) {
+        float cc[K], cm[K], cp[K];   // c, d - c, c + d
 #pragma unroll
-    for (int u = 0; u < ROWS; ++u) {
-        const float2 x = col[u * kConvCols];
+        for (int r = 0; r < K; ++r) {
+            const float2 t = r < kw ? __ldg(&Rt[(int64_t)r * stride + k]) : make_float2(0.f, 0.f);
+            cc[r] = t.x;
+            cm[r] = t.y - t.x;
+            cp[r] = t.x + t.y;
+        }
+        float k1[B], k2[B], k3[B];
 #pragma unroll
-        for (int b = 0; b < B; ++b) {
-            const int r = b + K - 1 - u;
-            if (r >= 0 && r < K) {
-                acc[b].x = fmaf(c[r].x, x.x, fmaf(-c[r].y, x.y, acc[b].x));
-                acc[b].y = fmaf(c[r].x, x.y, fmaf(c[r].y, x.x, acc[b].y));
+        for (int b = 0; b < B; ++b) k1[b] = k2[b] = k3[b] = 0.f;
+#pragma unroll
+        for (int u = 0; u < ROWS; ++u) {
+            const float2 x = col[u * kConvCols];
+            const float sab = x.x + x.y;
+#pragma unroll
+            for (int b = 0; b < B; ++b) {
+                const int r = b + K - 1 - u;
+                if (r >= 0 && r < K) {
+                    k1[b] = fmaf(cc[r], sab, k1[b]);
+                    k2[b] = fmaf(cm[r], x.x, k2[b]);
+                    k3[b] = fmaf(cp[r], x.y, k3[b]);
+                }
             }
         }
-    }
 #pragma unroll
-    for (int b = 0; b < B; ++b)
-        if (w0 + b < nwires) Y[(int64_t)(w0 + b) * stride + k] = acc[b];
+        for (int b = 0; b < B; ++b)
+            if (w0 + b < nwires) Y[(int64_t)(w0 + b) * stride + k] = make_float2(k1[b] - k3[b], k1[b] + k2[b]);
+    } else {
+        float2 c[K];
+#pragma unroll
+        for (int r = 0; r < K; ++r) c[r] = r < kw ? __ldg(&Rt[(int64_t)r * stride + k]) : make_float2(0.f, 0.f);
+        float2 acc[B];
+#pragma unroll
+        for (int b = 0; b < B; ++b) acc[b] = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int u = 0; u < ROWS; ++u) {
+            const float2 x = col[u * kConvCols];
+#pragma unroll
+            for (int b = 0; b < B; ++b) {
+                const int r = b + K - 1 - u;
+                if (r >= 0 && r < K) {
+                    acc[b].x = fmaf(c[r].x, x.x, fmaf(-c[r].y, x.y, acc[b].x));
+                    acc[b].y = fmaf(c[r].x, x.y, fmaf(c[r].y, x.x, acc[b].y));
+                }
+            }
+        }
+#pragma unroll
+        for (int b = 0; b < B; ++b)
+            if (w0 + b < nwires) Y[(int64_t)(w0 + b) * stride + k] = acc[b];
+    }
+}
+
+template <int B, bool KS>
+void launch_wc(const float2* X, float2* Y, const float2* Rt, int nwires, int nfreq, int64_t stride, int kw,
+               int center, int circular, cudaStream_t s) {
+    constexpr int K = kMaxRespWires;
+    dim3 grid((nfreq + kConvCols - 1) / kConvCols, (nwires + B - 1) / B);
+    wire_conv_kernel<K, B, KS><<<grid, kConvCols, 0, s>>>(X, Y, Rt, nwires, nfreq, stride, kw, center, circular);
 }
 
 }  // namespace
@@ -469,11 +511,14 @@ cudaError_t launch_inv_rows(const FftPlan& plan, const float2* tw, const float2*
 }
 
 cudaError_t launch_wire_conv(const float2* X, float2* Y, const float2* Rt, int nwires, int nfreq,
-                             int64_t stride, int kw, int center, int circular, cudaStream_t s) {
+                             int64_t stride, int kw, int center, int circular, cudaStream_t s, int variant) {
     if (nwires <= 0 || nfreq <= 0) return cudaSuccess;
-    constexpr int K = kMaxRespWires, B = 16;
-    dim3 grid((nfreq + kConvCols - 1) / kConvCols, (nwires + B - 1) / B);
-    wire_conv_kernel<K, B><<<grid, kConvCols, 0, s>>>(X, Y, Rt, nwires, nfreq, stride, kw, center, circular);
+    switch (variant) {
+        case 1: launch_wc<16, true>(X, Y, Rt, nwires, nfreq, stride, kw, center, circular, s); break;
+        case 2: launch_wc<8, false>(X, Y, Rt, nwires, nfreq, stride, kw, center, circular, s); break;
+        case 3: launch_wc<8, true>(X, Y, Rt, nwires, nfreq, stride, kw, center, circular, s); break;
+        default: launch_wc<16, false>(X, Y, Rt, nwires, nfreq, stride, kw, center, circular, s); break;
+    }
     return cudaGetLastError();
 }
 

@@ -39,33 +39,43 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1
     return c;
 }
 
-// Survivor count contributed by Philox block j of a bin holding N electrons
-// (the bin's binomial draw is the sum over its blocks):
-//   N <= exact_max: block j covers trials 4j .. 4j+3 (< N); a trial survives
-//     when its 32-bit word is below T (p = T / 2^32);
-//   N >  exact_max: one block, normal approximation by Box-Muller with the
-//     integer part of N p taken exactly from the 64-bit product N T.
-__device__ __forceinline__ int binomial_block(int N, int j, const RasterArgs& a, uint32_t bin, uint32_t depo) {
-    const uint4 x = philox4x32_10(make_uint4((uint32_t)j, bin, depo, a.evpl), a.key0, a.key1);
-    if (N <= a.exact_max) {
-        const int m = N - 4 * j;
-        int k = (x.x < a.T);
-        if (m > 1) k += (x.y < a.T);
-        if (m > 2) k += (x.z < a.T);
-        if (m > 3) k += (x.w < a.T);
-        return k;
-    }
+// Survivors among trials 4j .. 4j + m - 1 of one Philox block: a trial
+// survives when its 32-bit word is below T (p = T / 2^32).
+__device__ __forceinline__ int exact_count(uint4 x, int m, uint32_t T) {
+    int k = (x.x < T);
+    if (m > 1) k += (x.y < T);
+    if (m > 2) k += (x.z < T);
+    if (m > 3) k += (x.w < T);
+    return k;
+}
+
+// Normal approximation of Binomial(N, p) from words 0, 1 of Philox block 0
+// (Box-Muller), with the integer part of N p taken exactly from the 64-bit
+// product N T.  The approximation itself is far coarser than single-precision
+// rounding, so the fast logarithm and cosine are used.
+__device__ __forceinline__ int normal_draw(uint4 x, int N, const RasterArgs& a) {
     const float two_m32 = 2.3283064365386963e-10f;  // 2^-32
     const float u1 = fmaf((float)x.x, two_m32, 0.5f * two_m32);
     const float u2 = fmaf((float)x.y, two_m32, 0.5f * two_m32);
-    const float z = sqrtf(-2.f * logf(u1)) * cospif(2.f * u2);
+    // cos(2 pi u2) = -cos(2 pi (u2 - 1/2)), argument within [-pi, pi]
+    const float r = sqrtf(fmaxf(-2.f * __logf(u1), 0.f));
+    const float z = -r * __cosf(6.28318530717958648f * (u2 - 0.5f));
     const uint64_t nt = (uint64_t)(uint32_t)N * (uint64_t)a.T;
     const int ipart = (int)(uint32_t)(nt >> 32);
     const float frac = (float)(uint32_t)nt * two_m32;
     const float pe = (float)a.T * two_m32;
     const float sd = sqrtf(((float)ipart + frac) * (1.f - pe));
-    int k = ipart + (int)floorf(frac + z * sd + 0.5f);
+    const int k = ipart + (int)floorf(frac + z * sd + 0.5f);
     return k < 0 ? 0 : (k > N ? N : k);
+}
+
+// Survivor count contributed by Philox block j of a bin holding N electrons
+// (the bin's binomial draw is the sum over its blocks): exact trials for
+// N <= exact_max, else the single normal-approximation block.
+__device__ __forceinline__ int binomial_block(int N, int j, const RasterArgs& a, uint32_t bin, uint32_t depo) {
+    const uint4 x = philox4x32_10(make_uint4((uint32_t)j, bin, depo, a.evpl), a.key0, a.key1);
+    if (N <= a.exact_max) return exact_count(x, N - 4 * j, a.T);
+    return normal_draw(x, N, a);
 }
 
 // Philox blocks a bin of N electrons needs.
@@ -305,12 +315,14 @@ raster_kernel(RasterArgs a, float* __restrict__ grid, ws_patches pt, const int* 
     }
 }
 
-// Lane per depo for patches of at most kSmallT x kSmallW bins: each lane
-// computes its depo's widths, clipped bin range and the erfc edge tables of
-// both axes into shared memory; the warp then spreads the ~32 patches' bins
-// (and, with fluctuation, their Philox blocks) evenly over its lanes.
-// Larger patches are appended to a list for the warp-per-depo kernel.
+// Lane pair per depo for patches of at most kSmallT x kSmallW bins: a warp
+// takes 16 depos; lane l computes depo l's widths, clipped bin range and tick
+// erfc edge table, lane l + 16 its wire edge table, into shared memory; the
+// warp then spreads the patches' bins (and, with fluctuation, their Philox
+// blocks) evenly over its 32 lanes.  Larger patches are appended to a list
+// for the warp-per-depo kernel.
 constexpr int kSmallWarpsPerBlock = 4;
+constexpr int kSmallGroup = 16;   // depos per warp (a lane pair per depo)
 
 __device__ __forceinline__ void lane_axis_weights(float mu, float sigma, float delta, float nsig, bool point,
                                                   int first, int nb, float inv_norm, float* w) {
@@ -337,37 +349,49 @@ __device__ __forceinline__ void lane_axis_weights(float mu, float sigma, float d
     }
 }
 
+// First slot of s[0..n) (inclusive prefix sums, nondecreasing) exceeding v.
+template <int N>
+__device__ __forceinline__ int find_slot(const int* s, int v) {
+    int lo = 0;
+#pragma unroll
+    for (int step = N / 2; step >= 1; step >>= 1)
+        if (s[lo + step - 1] <= v) lo += step;
+    return lo;
+}
+
 template <int MODE>
-__global__ void __launch_bounds__(32 * kSmallWarpsPerBlock)
+__global__ void __launch_bounds__(32 * kSmallWarpsPerBlock, 8)
 raster_small_kernel(RasterArgs a, float* __restrict__ grid, ws_patches pt, int* __restrict__ list,
                     unsigned* list_count, unsigned list_cap) {
     constexpr int W = kSmallWarpsPerBlock;
-    __shared__ float s_wt[W][32][kSmallT + 1];
-    __shared__ float s_wx[W][32][kSmallW + 1];
-    __shared__ int s_off[W][32];
-    __shared__ int s_k0[W][32];
-    __shared__ int s_w0[W][32];
-    __shared__ int s_nt[W][32];
-    __shared__ float s_q[W][32];
-    __shared__ unsigned char s_own[W][32 * kSmallT * kSmallW];
-    __shared__ int s_incl[W][32];
-    __shared__ int s_cnt[W][32];
-    __shared__ int s_n[W][32];
-    __shared__ uint32_t s_gbin[W][32];
-    __shared__ uint32_t s_dep[W][32];
+    constexpr int G = kSmallGroup;
+    __shared__ float s_wt[W][G][kSmallT + 1];
+    __shared__ float s_wx[W][G][kSmallW + 1];
+    __shared__ int s_off[W][G];     // inclusive scan of the depos' bin counts
+    __shared__ int s_k0[W][G];
+    __shared__ int s_w0[W][G];
+    __shared__ int s_nt[W][G];
+    __shared__ float s_q[W][G];
+    __shared__ int s_incl[W][64];   // inclusive scan of the round's exact items
+    __shared__ int s_cnt[W][64];
+    __shared__ int s_n[W][64];
+    __shared__ uint32_t s_gbin[W][64];
+    __shared__ uint32_t s_dep[W][64];
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
     const int64_t nwarps = (int64_t)gridDim.x * W;
     const float inv_norm = 1.f / erff(a.nsig * 0.707106781186547524f);
-    for (int64_t base = ((int64_t)blockIdx.x * W + wib) * 32; base < a.n; base += nwarps * 32) {
-        const int64_t i = base + lane;
+    const int dl = lane & (G - 1);      // depo slot of this lane
+    const bool tick_lane = lane < G;    // lane pair: tick edges on dl, wire edges on dl + G
+    for (int64_t base = ((int64_t)blockIdx.x * W + wib) * G; base < a.n; base += nwarps * G) {
+        const int64_t i = base + dl;
         Extent e;
         float q = 0.f;
         bool bad = false, any = false;
         if (i < a.n) any = depo_extent(a, i, &e, &q, &bad);
-        if (bad) atomicOr(a.status, WS_DEV_BAD_DEPO);
+        if (bad && tick_lane) atomicOr(a.status, WS_DEV_BAD_DEPO);
         const bool large = any && is_large(e);
-        if (large) {
+        if (large && tick_lane) {
             const unsigned slot = atomicAdd(list_count, 1u);
             if (slot < list_cap) list[slot] = (int)i;
         }
@@ -377,19 +401,22 @@ raster_small_kernel(RasterArgs a, float* __restrict__ grid, ws_patches pt, int* 
         if (MODE == EMIT_PATCH && i < a.n && !large) {
             const int64_t off = pt.off[i];
             const bool fits = off + nb <= pt.capacity_bins;
-            pt.w0[i] = any ? e.w0 : 0;
-            pt.t0[i] = any ? e.k0 : 0;
-            pt.nw[i] = fits ? nxc : 0;
-            pt.nt[i] = fits ? ntc : 0;
-            if (!fits) {
-                atomicOr(a.status, WS_DEV_PATCH_OVERFLOW);
-                nb = 0;
+            if (tick_lane) {
+                pt.w0[i] = any ? e.w0 : 0;
+                pt.t0[i] = any ? e.k0 : 0;
+                pt.nw[i] = fits ? nxc : 0;
+                pt.nt[i] = fits ? ntc : 0;
+                if (!fits) atomicOr(a.status, WS_DEV_PATCH_OVERFLOW);
             }
+            if (!fits) nb = 0;
         }
         if (nb > 0) {
-            lane_axis_weights(e.mu_t, e.st, a.tick, a.nsig, e.point_t, e.k0, ntc, inv_norm, s_wt[wib][lane]);
-            lane_axis_weights(e.mu_x, e.sx, a.pitch, a.nsig, e.point_x, e.w0, nxc, inv_norm, s_wx[wib][lane]);
+            if (tick_lane)
+                lane_axis_weights(e.mu_t, e.st, a.tick, a.nsig, e.point_t, e.k0, ntc, inv_norm, s_wt[wib][dl]);
+            else
+                lane_axis_weights(e.mu_x, e.sx, a.pitch, a.nsig, e.point_x, e.w0, nxc, inv_norm, s_wx[wib][dl]);
         }
+        if (!tick_lane) nb = 0;   // each depo counted once in the scan
         int incl = nb;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
@@ -397,18 +424,19 @@ raster_small_kernel(RasterArgs a, float* __restrict__ grid, ws_patches pt, int* 
             if (lane >= o) incl += y;
         }
         const int total = __shfl_sync(0xffffffffu, incl, 31);
-        const int first = incl - nb;
-        s_off[wib][lane] = first;
-        s_k0[wib][lane] = any ? e.k0 : 0;
-        s_w0[wib][lane] = any ? e.w0 : 0;
-        s_nt[wib][lane] = ntc;
-        s_q[wib][lane] = a.fluct ? q : a.p * q;
-        for (int j = 0; j < nb; ++j) s_own[wib][first + j] = (unsigned char)lane;
+        if (tick_lane) {
+            s_off[wib][dl] = incl;
+            s_k0[wib][dl] = any ? e.k0 : 0;
+            s_w0[wib][dl] = any ? e.w0 : 0;
+            s_nt[wib][dl] = ntc;
+            s_q[wib][dl] = a.fluct ? q : a.p * q;
+        }
         __syncwarp();
+        const int* off = s_off[wib];
         if (!a.fluct) {
             for (int g = lane; g < total; g += 32) {
-                const int d = s_own[wib][g];
-                const int local = g - s_off[wib][d];
+                const int d = find_slot<G>(off, g);
+                const int local = g - (d > 0 ? off[d - 1] : 0);
                 const int nt = s_nt[wib][d];
                 const int ia = local / nt, ib = local - ia * nt;
                 const float v = s_q[wib][d] * s_wx[wib][d][ia] * s_wt[wib][d][ib];
@@ -419,55 +447,95 @@ raster_small_kernel(RasterArgs a, float* __restrict__ grid, ws_patches pt, int* 
                 }
             }
         } else {
-            for (int gb = 0; gb < total; gb += 32) {
-                const int g = gb + lane;
-                int N = 0, d = 0, local = 0, w = 0, k = 0;
-                if (g < total) {
-                    d = s_own[wib][g];
-                    local = g - s_off[wib][d];
-                    const int nt = s_nt[wib][d];
-                    const int ia = local / nt, ib = local - ia * nt;
-                    w = s_w0[wib][d] + ia;
-                    k = s_k0[wib][d] + ib;
-                    const float nexp = fminf(s_q[wib][d] * s_wx[wib][d][ia] * s_wt[wib][d][ib], 1.0e9f);
-                    N = (int)floorf(nexp + 0.5f);
+            // Rounds of 64 bins, two per lane: the bin's electron count, its
+            // normal-branch draw if any, then the exact-branch Philox blocks
+            // of the round spread over the lanes two at a time.
+            for (int gb = 0; gb < total; gb += 64) {
+                int N[2], w[2], k[2], cnt[2], ne[2], local[2], d[2];
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int g = gb + 32 * h + lane;
+                    N[h] = 0; w[h] = 0; k[h] = 0; local[h] = 0; d[h] = 0;
+                    if (g < total) {
+                        d[h] = find_slot<G>(off, g);
+                        local[h] = g - (d[h] > 0 ? off[d[h] - 1] : 0);
+                        const int nt = s_nt[wib][d[h]];
+                        const int ia = local[h] / nt, ib = local[h] - ia * nt;
+                        w[h] = s_w0[wib][d[h]] + ia;
+                        k[h] = s_k0[wib][d[h]] + ib;
+                        const float nexp = fminf(s_q[wib][d[h]] * s_wx[wib][d[h]][ia] * s_wt[wib][d[h]][ib], 1.0e9f);
+                        N[h] = (int)floorf(nexp + 0.5f);
+                    }
                 }
-                const uint32_t gbin = (uint32_t)((int64_t)w * a.nticks + k);
-                const uint32_t dep = (uint32_t)(base + d);
-                const int items = binomial_items(N, a);
-                int cnt = (N > 0 && a.keep_all) ? N : 0;
-                if (items > 0 && N > a.exact_max) cnt = binomial_block(N, 0, a, gbin, dep);
-                const int ne = N <= a.exact_max ? items : 0;
-                int inc = ne;
+                uint32_t gbin[2], dep[2];
+                uint4 x[2];
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    gbin[h] = (uint32_t)((int64_t)w[h] * a.nticks + k[h]);
+                    dep[h] = (uint32_t)(base + d[h]);
+                    const int items = binomial_items(N[h], a);
+                    cnt[h] = (N[h] > 0 && a.keep_all) ? N[h] : 0;
+                    ne[h] = N[h] <= a.exact_max ? items : 0;
+                    x[h] = make_uint4(0u, 0u, 0u, 0u);
+                    if (items > 0 && N[h] > a.exact_max)
+                        x[h] = philox4x32_10(make_uint4(0u, gbin[h], dep[h], a.evpl), a.key0, a.key1);
+                }
+#pragma unroll
+                for (int h = 0; h < 2; ++h)
+                    if (binomial_items(N[h], a) > 0 && N[h] > a.exact_max) cnt[h] = normal_draw(x[h], N[h], a);
+                int inc0 = ne[0], inc1 = ne[1];
 #pragma unroll
                 for (int o = 1; o < 32; o <<= 1) {
-                    const int y = __shfl_up_sync(0xffffffffu, inc, o);
-                    if (lane >= o) inc += y;
+                    const int y0 = __shfl_up_sync(0xffffffffu, inc0, o);
+                    const int y1 = __shfl_up_sync(0xffffffffu, inc1, o);
+                    if (lane >= o) { inc0 += y0; inc1 += y1; }
                 }
-                const int tot = __shfl_sync(0xffffffffu, inc, 31);
-                s_incl[wib][lane] = inc;
-                s_cnt[wib][lane] = cnt;
-                s_n[wib][lane] = N;
-                s_gbin[wib][lane] = gbin;
-                s_dep[wib][lane] = dep;
+                const int tot0 = __shfl_sync(0xffffffffu, inc0, 31);
+                const int tot = tot0 + __shfl_sync(0xffffffffu, inc1, 31);
+                s_incl[wib][lane] = inc0;
+                s_incl[wib][32 + lane] = tot0 + inc1;
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    s_cnt[wib][32 * h + lane] = cnt[h];
+                    s_n[wib][32 * h + lane] = N[h];
+                    s_gbin[wib][32 * h + lane] = gbin[h];
+                    s_dep[wib][32 * h + lane] = dep[h];
+                }
                 __syncwarp();
-                for (int it = lane; it < tot; it += 32) {
-                    int lo = 0, hi = 31;  // first slot whose inclusive count exceeds it
-                    while (lo < hi) {
-                        const int mid = (lo + hi) >> 1;
-                        if (s_incl[wib][mid] > it) hi = mid; else lo = mid + 1;
+                const int* sinc = s_incl[wib];
+                for (int it0 = lane; it0 < tot; it0 += 64) {
+                    int sl[2], jj[2];
+                    bool ok[2];
+                    uint4 y[2];
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        const int it = it0 + 32 * h;
+                        ok[h] = it < tot;
+                        sl[h] = ok[h] ? find_slot<64>(sinc, it) : 0;
+                        jj[h] = it - (sl[h] > 0 ? sinc[sl[h] - 1] : 0);
                     }
-                    const int j = it - (lo > 0 ? s_incl[wib][lo - 1] : 0);
-                    const int c = binomial_block(s_n[wib][lo], j, a, s_gbin[wib][lo], s_dep[wib][lo]);
-                    if (c) atomicAdd(&s_cnt[wib][lo], c);
+#pragma unroll
+                    for (int h = 0; h < 2; ++h)
+                        y[h] = philox4x32_10(make_uint4((uint32_t)jj[h], s_gbin[wib][sl[h]], s_dep[wib][sl[h]], a.evpl),
+                                             a.key0, a.key1);
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        if (!ok[h]) continue;
+                        const int c = exact_count(y[h], s_n[wib][sl[h]] - 4 * jj[h], a.T);
+                        if (c) atomicAdd(&s_cnt[wib][sl[h]], c);
+                    }
                 }
                 __syncwarp();
-                if (g < total) {
-                    const float v = (float)s_cnt[wib][lane];
-                    if (MODE == EMIT_GRID) {
-                        if (v != 0.f) atomicAdd(grid + (int64_t)w * a.nticks + k, v);
-                    } else {
-                        pt.val[pt.off[base + d] + local] = v;
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int g = gb + 32 * h + lane;
+                    if (g < total) {
+                        const float v = (float)s_cnt[wib][32 * h + lane];
+                        if (MODE == EMIT_GRID) {
+                            if (v != 0.f) atomicAdd(grid + (int64_t)w[h] * a.nticks + k[h], v);
+                        } else {
+                            pt.val[pt.off[base + d[h]] + local[h]] = v;
+                        }
                     }
                 }
                 __syncwarp();
@@ -609,7 +677,7 @@ int num_sms() {
 cudaError_t launch_raster_scatter(const RasterArgs& a, float* grid, const LargeList& L, cudaStream_t s) {
     if (a.n <= 0) return cudaSuccess;
     ws_patches none{};
-    raster_small_kernel<EMIT_GRID><<<grid_for(a.n, 32 * kSmallWarpsPerBlock, 16), 32 * kSmallWarpsPerBlock, 0, s>>>(
+    raster_small_kernel<EMIT_GRID><<<grid_for(a.n, kSmallGroup * kSmallWarpsPerBlock, 16), 32 * kSmallWarpsPerBlock, 0, s>>>(
         a, grid, none, L.list, L.count, L.cap);
     raster_kernel<EMIT_GRID><<<num_sms() * 2, 32 * kWarpsPerBlock, 0, s>>>(a, grid, none, L.list, L.count, L.cap,
                                                                           L.done);
@@ -633,7 +701,7 @@ cudaError_t launch_scan_inplace(int64_t* v, int64_t n, int64_t* scratch, cudaStr
 
 cudaError_t launch_raster_patches(const RasterArgs& a, const ws_patches& p, const LargeList& L, cudaStream_t s) {
     if (a.n <= 0) return cudaSuccess;
-    raster_small_kernel<EMIT_PATCH><<<grid_for(a.n, 32 * kSmallWarpsPerBlock, 16), 32 * kSmallWarpsPerBlock, 0, s>>>(
+    raster_small_kernel<EMIT_PATCH><<<grid_for(a.n, kSmallGroup * kSmallWarpsPerBlock, 16), 32 * kSmallWarpsPerBlock, 0, s>>>(
         a, nullptr, p, L.list, L.count, L.cap);
     raster_kernel<EMIT_PATCH><<<num_sms() * 2, 32 * kWarpsPerBlock, 0, s>>>(a, nullptr, p, L.list, L.count, L.cap,
                                                                            L.done);

@@ -203,7 +203,7 @@ ws_status convolve_impl(ws_plane* pl, const float* grid, float* out, cudaStream_
                                                 pl->fstride, pl->nfreq, 1.0f, s));
     WS_LAUNCH(pl, K_WCONV, s, ws::launch_wire_conv(pl->X, pl->Y, pl->Rt, d.nwires, pl->nfreq, pl->fstride,
                                                    d.resp_nwires, d.resp_wire_center,
-                                                   d.conv_mode == WS_CONV_CIRCULAR, s));
+                                                   d.conv_mode == WS_CONV_CIRCULAR, s, pl->wconv_variant));
     WS_LAUNCH(pl, K_INV, s, ws::launch_inv_rows(pl->plan, pl->tw, pl->Y, d.nwires, pl->fstride, pl->nfreq, out,
                                                 d.nticks, d.nticks, s));
     return WS_OK;
@@ -290,6 +290,35 @@ ws_status ws_plane_create(const ws_plane_desc* desc, const float* response_dev, 
     if (e == cudaSuccess)
         e = ws::launch_fwd_rows(lay.plan, pl->tw, response_dev, desc->resp_nwires, desc->resp_nticks,
                                 desc->resp_nticks, pl->Rt, lay.fstride, lay.nfreq, 1.0f / (float)lay.plan.L, s);
+    // Autotune the wire convolution on this plane's own buffers: each variant
+    // once to warm up, then three timed launches; the fastest is kept.
+    pl->wconv_variant = 0;
+    if (e == cudaSuccess) e = cudaMemsetAsync(pl->X, 0, sizeof(float2) * (size_t)desc->nwires * lay.fstride, s);
+    if (e == cudaSuccess) {
+        cudaEvent_t t0 = nullptr, t1 = nullptr;
+        e = cudaEventCreate(&t0);
+        if (e == cudaSuccess) e = cudaEventCreate(&t1);
+        float best = 1e30f;
+        for (int v = 0; v < ws::kWireConvVariants && e == cudaSuccess; ++v) {
+            const int circ = desc->conv_mode == WS_CONV_CIRCULAR;
+            e = ws::launch_wire_conv(pl->X, pl->Y, pl->Rt, desc->nwires, lay.nfreq, lay.fstride, desc->resp_nwires,
+                                     desc->resp_wire_center, circ, s, v);
+            if (e == cudaSuccess) e = cudaEventRecord(t0, s);
+            for (int r = 0; r < 3 && e == cudaSuccess; ++r)
+                e = ws::launch_wire_conv(pl->X, pl->Y, pl->Rt, desc->nwires, lay.nfreq, lay.fstride,
+                                         desc->resp_nwires, desc->resp_wire_center, circ, s, v);
+            if (e == cudaSuccess) e = cudaEventRecord(t1, s);
+            if (e == cudaSuccess) e = cudaEventSynchronize(t1);
+            float ms = 0.f;
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, t0, t1);
+            if (e == cudaSuccess && ms < best) {
+                best = ms;
+                pl->wconv_variant = v;
+            }
+        }
+        if (t0) cudaEventDestroy(t0);
+        if (t1) cudaEventDestroy(t1);
+    }
     if (e != cudaSuccess) {
         delete pl;
         return cuda_fail(e, "ws_plane_create");
@@ -311,6 +340,12 @@ static void trace_free(ws_plane* pl) {
 ws_status ws_plane_destroy(ws_plane* plane) {
     if (plane) trace_free(plane);
     delete plane;
+    return WS_OK;
+}
+
+ws_status ws_plane_set_wire_conv_variant(ws_plane* pl, int variant) {
+    if (!pl || variant < 0 || variant >= ws::kWireConvVariants) return WS_ERR_INVALID_ARG;
+    pl->wconv_variant = variant;
     return WS_OK;
 }
 
@@ -377,6 +412,7 @@ ws_status ws_plane_get_info(const ws_plane* pl, ws_plane_info* info) {
     info->npasses = pl->plan.npass;
     for (int i = 0; i < pl->plan.npass; ++i) info->radices[i] = pl->plan.radix[i];
     info->workspace_bytes = pl->ws_bytes;
+    info->wire_conv_variant = pl->wconv_variant;
     return WS_OK;
 }
 

@@ -59,9 +59,11 @@ cudaError_t launch_inv_rows(const FftPlan& plan, const float2* tw, const float2*
                             int64_t in_stride, int nfreq, float* out, int ncols,
                             int64_t out_stride, cudaStream_t s);
 // Y[w][k] = sum_r Rt[r][k] * X[w + center - r][k]  (zero or wrapped outside).
+// variant: 0 = 16 wires per thread, 1 = 16 Karatsuba, 2 = 8, 3 = 8 Karatsuba.
+constexpr int kWireConvVariants = 4;
 cudaError_t launch_wire_conv(const float2* X, float2* Y, const float2* Rt, int nwires,
                              int nfreq, int64_t stride, int kw, int center, int circular,
-                             cudaStream_t s);
+                             cudaStream_t s, int variant = 0);
 
 // Hand-over list of depos whose patches are too large for the lane-per-depo
 // raster kernel (workspace-resident; count and done must start at zero and
@@ -96,6 +98,7 @@ struct ws_trace;
 // The plane: host object pointing into the caller's workspace.
 struct ws_plane {
     ws_trace* trace;    // launch trace, or null
+    int wconv_variant;  // wire-convolution kernel chosen by the autotuner
     ws_plane_desc desc;
     ws::FftPlan plan;
     int nfreq;          // L/2 + 1

@@ -31,7 +31,8 @@ WS_PREC_FP32, WS_PREC_FP32_COMP, WS_PREC_FP64 = 0, 1, 2
 EXPORTED = ("ws_plane_workspace_bytes", "ws_plane_create", "ws_plane_destroy", "ws_plane_get_info",
             "ws_patch_capacity", "ws_rasterize", "ws_scatter", "ws_convolve", "ws_simulate",
             "ws_plane_sync", "ws_plane_clear_status", "ws_plane_trace", "ws_plane_trace_read",
-            "ws_convolve_noalloc", "ws_status_string", "ws_last_error")
+            "ws_convolve_noalloc", "ws_plane_set_wire_conv_variant", "ws_status_string",
+            "ws_last_error")
 
 
 class WiresimError(RuntimeError):
@@ -79,7 +80,8 @@ class WsTraceStat(ctypes.Structure):
 class WsPlaneInfo(ctypes.Structure):
     _fields_ = [("fft_len_tick", ctypes.c_int32), ("nfreq", ctypes.c_int32),
                 ("nfreq_stride", ctypes.c_int32), ("npasses", ctypes.c_int32),
-                ("radices", ctypes.c_int32 * 16), ("workspace_bytes", ctypes.c_size_t)]
+                ("radices", ctypes.c_int32 * 16), ("workspace_bytes", ctypes.c_size_t),
+                ("wire_conv_variant", ctypes.c_int32)]
 
 
 _lock = threading.Lock()
@@ -115,6 +117,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
             "ws_plane_trace_read": [P, ctypes.POINTER(WsTraceStat), ctypes.c_int,
                                     ctypes.POINTER(ctypes.c_int)],
             "ws_convolve_noalloc": [ctypes.POINTER(WsPlaneDesc), P, P, P, P],
+            "ws_plane_set_wire_conv_variant": [P, ctypes.c_int],
         }
         for name, args in sig.items():
             fn = getattr(h, name)
@@ -362,6 +365,10 @@ class Plane:
     def scatter(self, patches, grid, stream=None):
         ws_scatter(self.handle, self.patches_c(patches), _ptr(grid), _stream_handle(stream))
         return grid
+
+    def set_wire_conv_variant(self, variant: int):
+        _check(load_library().ws_plane_set_wire_conv_variant(self.handle, variant),
+               "ws_plane_set_wire_conv_variant")
 
     def trace(self, max_records: int):
         ws_plane_trace(self.handle, max_records)

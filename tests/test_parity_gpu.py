@@ -69,6 +69,22 @@ def test_convolve_matches_oracle(ws, circular, nw, nt, kw, kt, c):
     assert rel_l2(to_np(out), ref) <= REL_L2
 
 
+@pytest.mark.parametrize("variant", [0, 1, 2, 3])
+@pytest.mark.parametrize("circular", [False, True])
+def test_every_wire_conv_variant(ws, variant, circular):
+    """Each wire-convolution kernel (wire blocks of 16 or 8, plain or
+    Karatsuba taps) gives the oracle's convolution, with a ragged wire tail."""
+    import torch
+    rng = np.random.Generator(np.random.PCG64(40 + variant))
+    nw, nt = 45, 1000
+    S = rng.standard_normal((nw, nt)).astype(np.float32)
+    R = rng.standard_normal((21, 200)).astype(np.float32)
+    plane = ws.Plane(nw, nt, R, circular=circular)
+    plane.set_wire_conv_variant(variant)
+    out = plane.convolve(torch.from_numpy(S).cuda())
+    assert rel_l2(to_np(out), oracle.convolve_fft(S.astype(np.float64), R, 10, circular)) <= REL_L2
+
+
 def test_convolve_in_place_and_delta_identity(ws):
     import torch
     rng = np.random.Generator(np.random.PCG64(3))
