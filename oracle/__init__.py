@@ -50,7 +50,7 @@ def _lib():
             h = ctypes.CDLL(_SO)
             h.wso_philox4x32_10.argtypes = [_u32p, _u32p, _u32p]
             h.wso_philox4x32_10.restype = None
-            h.wso_sigmas.argtypes = [ctypes.c_int64, _f32p, ctypes.c_double, ctypes.c_double,
+            h.wso_sigmas.argtypes = [ctypes.c_int64, _f64p, ctypes.c_double, ctypes.c_double,
                                      ctypes.c_double, _f64p, _f64p]
             h.wso_sigmas.restype = None
             h.wso_axis_weights.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_double,
@@ -64,14 +64,14 @@ def _lib():
             h.wso_binomial.restype = ctypes.c_int64
             opt_f32 = ctypes.c_void_p
             h.wso_raster_scatter.argtypes = [
-                ctypes.c_int64, _f32p, _f32p, _f32p, opt_f32, opt_f32,
+                ctypes.c_int64, _f64p, _f64p, _f64p, opt_f32, opt_f32,
                 ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
                 ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                 ctypes.c_int, ctypes.c_double, ctypes.c_uint64, ctypes.c_uint32,
                 ctypes.c_uint32, ctypes.c_int, _f64p]
             h.wso_raster_scatter.restype = ctypes.c_int64
             h.wso_patch_extents.argtypes = [
-                ctypes.c_int64, _f32p, _f32p, opt_f32, opt_f32,
+                ctypes.c_int64, _f64p, _f64p, opt_f32, opt_f32,
                 ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
                 ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                 _i32p, _i32p, _i32p, _i32p]
@@ -84,6 +84,12 @@ def _lib():
                                               ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                               ctypes.c_int, ctypes.c_int64, _i32p, _i32p, _f64p]
             h.wso_convolve_points.restype = None
+            h.wso_depo_grads.argtypes = [
+                ctypes.c_int64, _f64p, _f64p, _f64p, opt_f32, opt_f32, ctypes.c_int, ctypes.c_int,
+                ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                ctypes.c_double, ctypes.c_double, _f64p, _f64p, _f64p, _f64p,
+                ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
+            h.wso_depo_grads.restype = ctypes.c_int64
             _handle = h
     return _handle
 
@@ -100,6 +106,12 @@ EXACT_MAX = 32
 
 def _c32(a):
     return np.ascontiguousarray(np.asarray(a, dtype=np.float32))
+
+
+def _c64(a):
+    """Depo inputs in double: float32 arrays convert exactly, Python floats
+    and float64 arrays are kept as they are (finite differences need that)."""
+    return np.ascontiguousarray(np.asarray(a, dtype=np.float64))
 
 
 def _opt_ptr(a):
@@ -143,7 +155,7 @@ def sigmas(t_us, DL_: float = DL, DT_: float = DT, v: float = V):
     """sigma_L [us] = sqrt(2 D_L t)/v and sigma_T [mm] = sqrt(2 D_T t) (Sec. 2.2).
 
     Pinned by closed-form values."""
-    t = _c32(t_us)
+    t = _c64(t_us)
     st = np.zeros(t.shape[0]); sx = np.zeros(t.shape[0])
     _lib().wso_sigmas(t.shape[0], t, DL_, DT_, v, st, sx)
     return st, sx
@@ -173,9 +185,9 @@ def raster_scatter(q, x_mm, t_us, nwires: int, nticks: int, *, sig_t_us=None, si
 
     Sec. 2.2 (raster, scatter-add), Sec. 3.1 (binomial fluctuation).  Pinned
     by patch sums (closed form), linearity and the pins of its parts."""
-    q = _c32(q); x = _c32(x_mm); t = _c32(t_us)
-    st = None if sig_t_us is None else _c32(sig_t_us)
-    sx = None if sig_x_mm is None else _c32(sig_x_mm)
+    q = _c64(q); x = _c64(x_mm); t = _c64(t_us)
+    st = None if sig_t_us is None else _c64(sig_t_us)
+    sx = None if sig_x_mm is None else _c64(sig_x_mm)
     S = np.zeros((nwires, nticks))
     skipped = _lib().wso_raster_scatter(
         q.shape[0], q, x, t, _opt_ptr(st), _opt_ptr(sx), nwires, nticks, pitch_mm, tick_us,
@@ -188,10 +200,10 @@ def patch_extents(x_mm, t_us, nwires: int, nticks: int, *, sig_t_us=None, sig_x_
                   pitch_mm: float = PITCH_MM, tick_us: float = TICK_US, nsig: float = NSIGMA,
                   DL_: float = DL, DT_: float = DT, v: float = V):
     """Per-depo (w0, nw, t0, nt) of each patch clipped to the grid, and the bin total."""
-    x = _c32(x_mm); t = _c32(t_us)
+    x = _c64(x_mm); t = _c64(t_us)
     n = x.shape[0]
-    st = None if sig_t_us is None else _c32(sig_t_us)
-    sx = None if sig_x_mm is None else _c32(sig_x_mm)
+    st = None if sig_t_us is None else _c64(sig_t_us)
+    sx = None if sig_x_mm is None else _c64(sig_x_mm)
     w0 = np.zeros(n, np.int32); nw = np.zeros(n, np.int32)
     t0 = np.zeros(n, np.int32); nt = np.zeros(n, np.int32)
     total = _lib().wso_patch_extents(n, x, t, _opt_ptr(st), _opt_ptr(sx), nwires, nticks,
@@ -252,3 +264,81 @@ def simulate(q, x_mm, t_us, nwires: int, nticks: int, R, wire_center: int = 10, 
     """The whole hot path: raster, (fluctuate), scatter-add, convolve (Eq. 2)."""
     S = raster_scatter(q, x_mm, t_us, nwires, nticks, **kw)
     return convolve_fft(S, R, wire_center, circular)
+
+
+# ------------------------------------------------------------------ adjoint
+def convolve_adjoint(G, R, wire_center: int, circular: bool = False) -> np.ndarray:
+    """Adjoint of ``convolve_fft`` applied to G = dL/dM: dL/dS[w][t] =
+    sum_{r,j} R[r][j] G[w + r - c][t + j] (G zero outside the grid in linear
+    mode, indices wrapping in circular mode), via numpy's FFT.
+
+    Pinned by the dot-product identity <A S, G> = <S, A^T G>."""
+    G = np.asarray(G, dtype=np.float64)
+    R = np.asarray(R, dtype=np.float64)
+    nw, nt = G.shape
+    kw, kt = R.shape
+    if circular:
+        Rc = np.zeros((nw, nt))
+        for r in range(kw):
+            for j in range(kt):
+                Rc[(r - wire_center) % nw, j % nt] += R[r, j]
+        return np.fft.irfft2(np.fft.rfft2(G) * np.conj(np.fft.rfft2(Rc)), s=(nw, nt))
+    # correlation = convolution with the response flipped on both axes
+    Rf = R[::-1, ::-1]
+    lw, lt = nw + kw - 1, nt + kt - 1
+    full = np.fft.irfft2(np.fft.rfft2(G, s=(lw, lt)) * np.fft.rfft2(Rf, s=(lw, lt)), s=(lw, lt))
+    c2 = kw - 1 - wire_center
+    return np.ascontiguousarray(full[c2:c2 + nw, kt - 1:kt - 1 + nt])
+
+
+def response_grad(G, S, kw: int, kt: int, wire_center: int, circular: bool = False) -> np.ndarray:
+    """dL/dR[r][j] = sum_{w,t} G[w][t] S[w - (r - c)][t - j] (S zero outside
+    the grid, or wrapped), the cross-correlation of G and S at the response's
+    lags, via numpy's FFT.  Pinned by finite differences in R (L is linear
+    in R) and by the dot-product identity."""
+    G = np.asarray(G, dtype=np.float64)
+    S = np.asarray(S, dtype=np.float64)
+    nw, nt = G.shape
+    out = np.zeros((kw, kt))
+    if circular:
+        C = np.fft.irfft2(np.fft.rfft2(G) * np.conj(np.fft.rfft2(S)), s=(nw, nt))
+        for r in range(kw):
+            for j in range(kt):
+                out[r, j] = C[(r - wire_center) % nw, j % nt]
+        return out
+    lw, lt = nw + kw, nt + kt
+    C = np.fft.irfft2(np.fft.rfft2(G, s=(lw, lt)) * np.conj(np.fft.rfft2(S, s=(lw, lt))), s=(lw, lt))
+    for r in range(kw):
+        d = r - wire_center
+        out[r, :] = C[d % lw, :kt]
+    return out
+
+
+def depo_grads(q, x_mm, t_us, nwires: int, nticks: int, dS, *, sig_t_us=None, sig_x_mm=None,
+               pitch_mm: float = PITCH_MM, tick_us: float = TICK_US, nsig: float = NSIGMA,
+               DL_: float = DL, DT_: float = DT, v: float = V, p: float = 1.0):
+    """(gq, gx, gt, gDL, gDT): gradients of L through the expected-value
+    raster given dS = dL/dS (closed form in C).  Pinned by central finite
+    differences of ``raster_scatter``."""
+    q = _c64(q); x = _c64(x_mm); t = _c64(t_us)
+    n = q.shape[0]
+    st = None if sig_t_us is None else _c64(sig_t_us)
+    sx = None if sig_x_mm is None else _c64(sig_x_mm)
+    dS = np.ascontiguousarray(np.asarray(dS, dtype=np.float64))
+    gq = np.zeros(n); gx = np.zeros(n); gt = np.zeros(n)
+    gDL = ctypes.c_double(0.0); gDT = ctypes.c_double(0.0)
+    _lib().wso_depo_grads(n, q, x, t, _opt_ptr(st), _opt_ptr(sx), nwires, nticks, pitch_mm, tick_us, nsig,
+                          DL_, DT_, v, float(p), dS, gq, gx, gt, ctypes.byref(gDL), ctypes.byref(gDT))
+    return gq, gx, gt, float(gDL.value), float(gDT.value)
+
+
+def simulate_backward(q, x_mm, t_us, nwires: int, nticks: int, R, wire_center: int, G, *,
+                      circular: bool = False, **kw):
+    """All gradients of L given G = dL/dM: (gq, gx, gt, gDL, gDT, gR)."""
+    dS = convolve_adjoint(G, R, wire_center, circular)
+    rkw = {k: v for k, v in kw.items() if k in ("sig_t_us", "sig_x_mm", "pitch_mm", "tick_us", "nsig",
+                                                 "DL_", "DT_", "v", "p")}
+    gq, gx, gt, gDL, gDT = depo_grads(q, x_mm, t_us, nwires, nticks, dS, **rkw)
+    S = raster_scatter(q, x_mm, t_us, nwires, nticks, **rkw)
+    gR = response_grad(G, S, np.asarray(R).shape[0], np.asarray(R).shape[1], wire_center, circular)
+    return gq, gx, gt, gDL, gDT, gR

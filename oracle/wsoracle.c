@@ -68,11 +68,11 @@ void wso_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t ou
 /* Diffusion along the drift (Sec. 2.2): longitudinal width in time
  * sigma_L = sqrt(2 D_L t) / v, transverse width in pitch sigma_T =
  * sqrt(2 D_T t).  Units: mm, microseconds. */
-void wso_sigmas(int64_t n, const float* t_us, double DL, double DT, double v,
+void wso_sigmas(int64_t n, const double* t_us, double DL, double DT, double v,
                 double* sig_t_us, double* sig_x_mm)
 {
     for (int64_t i = 0; i < n; ++i) {
-        double t = (double)t_us[i];
+        double t = t_us[i];
         sig_t_us[i] = sqrt(2.0 * DL * t) / v;
         sig_x_mm[i] = sqrt(2.0 * DT * t);
     }
@@ -180,8 +180,8 @@ int64_t wso_binomial(int64_t N, double p, int exact_max, const uint32_t key[2],
  * receives a binomial count (see wso_binomial). */
 #define WSO_MAXBINS 65536
 
-int64_t wso_raster_scatter(int64_t n, const float* q, const float* x_mm, const float* t_us,
-                           const float* sig_t_us, const float* sig_x_mm,
+int64_t wso_raster_scatter(int64_t n, const double* q, const double* x_mm, const double* t_us,
+                           const double* sig_t_us, const double* sig_x_mm,
                            int nwires, int nticks, double pitch_mm, double tick_us,
                            double nsig, double DL, double DT, double v,
                            int fluctuate, double p, uint64_t seed, uint32_t event_id,
@@ -228,8 +228,8 @@ int64_t wso_raster_scatter(int64_t n, const float* q, const float* x_mm, const f
 /* Per-depo patch extents, clipped to the grid (for comparing patch lists).
  * Writes w0, nw, t0, nt per depo (nw = nt = 0 for an empty or skipped
  * patch).  Returns the total number of in-grid bins. */
-int64_t wso_patch_extents(int64_t n, const float* x_mm, const float* t_us,
-                          const float* sig_t_us, const float* sig_x_mm,
+int64_t wso_patch_extents(int64_t n, const double* x_mm, const double* t_us,
+                          const double* sig_t_us, const double* sig_x_mm,
                           int nwires, int nticks, double pitch_mm, double tick_us,
                           double nsig, double DL, double DT, double v,
                           int32_t* w0, int32_t* nw, int32_t* t0, int32_t* nt)
@@ -311,4 +311,106 @@ void wso_convolve_points(const double* S, int nwires, int nticks,
         }
         out[i] = acc;
     }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Adjoint of the expected-value raster (Sec. 2.2) for dL/dS given.
+ *
+ * With standardized clamped edges u_e = clamp((e - mu)/sigma, -n, n), a bin's
+ * weight is w = [Phi(u1) - Phi(u0)] / erf(n/sqrt 2).  An edge that sits on the
+ * window bound moves with mu and sigma, so its Phi stays at Phi(+-n) and it
+ * contributes nothing; an interior edge contributes
+ *   dPhi(u)/dmu = -phi(u)/sigma,  dPhi(u)/dsigma = -u phi(u)/sigma.
+ * The patch is p q w_t w_x, so per depo
+ *   dL/dq = p sum dS w_t w_x,  dL/dmu_t = p q sum dS w_x dw_t/dmu_t, ...
+ * and through diffusion sigma_L = sqrt(2 D_L t)/v, sigma_T = sqrt(2 D_T t):
+ *   dL/dt += dL/dsigma_t sigma_t/(2t) + dL/dsigma_x sigma_x/(2t),
+ *   dL/dD_L = sum dL/dsigma_t sigma_t/(2 D_L), dL/dD_T likewise.
+ * With given widths the sigma terms stay out of dL/dt and dL/dD are zero.
+ * A point-charge axis (sigma <= 1e-6 delta) has zero mu and sigma
+ * derivatives. */
+static int axis_weights_grad(double mu, double sigma, double delta, double nsig, int maxn, int64_t* lo,
+                             double* w, double* dmu, double* dsig)
+{
+    if (!(sigma > 1e-6 * delta)) {
+        *lo = (int64_t)floor(mu / delta);
+        w[0] = 1.0; dmu[0] = 0.0; dsig[0] = 0.0;
+        return 1;
+    }
+    double a = mu - nsig * sigma, b = mu + nsig * sigma;
+    int64_t klo = (int64_t)floor(a / delta), khi = (int64_t)floor(b / delta);
+    int64_t n = khi - klo + 1;
+    if (n > maxn) return -1;
+    double norm = erf(nsig / sqrt(2.0));
+    double inv_s2pi = 1.0 / sqrt(2.0 * M_PI);
+    for (int64_t k = klo; k <= khi; ++k) {
+        double e0 = (double)k * delta, e1 = (double)(k + 1) * delta;
+        int c0 = e0 <= a, c1 = e1 >= b;          /* edge clamped to the window bound */
+        double u0 = c0 ? -nsig : (e0 - mu) / sigma;
+        double u1 = c1 ? nsig : (e1 - mu) / sigma;
+        double p0 = c0 ? 0.0 : exp(-0.5 * u0 * u0) * inv_s2pi;
+        double p1 = c1 ? 0.0 : exp(-0.5 * u1 * u1) * inv_s2pi;
+        int64_t i = k - klo;
+        w[i] = 0.5 * (erf(u1 / sqrt(2.0)) - erf(u0 / sqrt(2.0))) / norm;
+        dmu[i] = -(p1 - p0) / (sigma * norm);
+        dsig[i] = -(u1 * p1 - u0 * p0) / (sigma * norm);
+    }
+    *lo = klo;
+    return (int)n;
+}
+
+int64_t wso_depo_grads(int64_t n, const double* q, const double* x_mm, const double* t_us,
+                       const double* sig_t_us, const double* sig_x_mm,
+                       int nwires, int nticks, double pitch_mm, double tick_us,
+                       double nsig, double DL, double DT, double v, double p,
+                       const double* dS, double* gq, double* gx, double* gt, double* gDL, double* gDT)
+{
+    double *wt = malloc(sizeof(double) * WSO_MAXBINS), *mt = malloc(sizeof(double) * WSO_MAXBINS),
+           *st_ = malloc(sizeof(double) * WSO_MAXBINS);
+    double *wx = malloc(sizeof(double) * WSO_MAXBINS), *mx = malloc(sizeof(double) * WSO_MAXBINS),
+           *sx_ = malloc(sizeof(double) * WSO_MAXBINS);
+    int64_t skipped = 0;
+    double sDL = 0.0, sDT = 0.0;
+    for (int64_t i = 0; i < n; ++i) {
+        double qi = q[i], xi = x_mm[i], ti = t_us[i];
+        double st, sx;
+        int given = sig_t_us != NULL;
+        if (given) { st = sig_t_us[i]; sx = sig_x_mm[i]; }
+        else { st = sqrt(2.0 * DL * ti) / v; sx = sqrt(2.0 * DT * ti); }
+        gq[i] = gx[i] = gt[i] = 0.0;
+        if (!isfinite(qi) || !isfinite(xi) || !isfinite(ti) || !isfinite(st) || !isfinite(sx) ||
+            st < 0.0 || sx < 0.0) { ++skipped; continue; }
+        int64_t klo, wlo;
+        int nt = axis_weights_grad(ti, st, tick_us, nsig, WSO_MAXBINS, &klo, wt, mt, st_);
+        int nw = axis_weights_grad(xi, sx, pitch_mm, nsig, WSO_MAXBINS, &wlo, wx, mx, sx_);
+        if (nt < 0 || nw < 0) { ++skipped; continue; }
+        double Sq = 0, Smt = 0, Sst = 0, Smx = 0, Ssx = 0;
+        for (int a = 0; a < nw; ++a) {
+            int64_t w = wlo + a;
+            if (w < 0 || w >= nwires) continue;
+            for (int b = 0; b < nt; ++b) {
+                int64_t k = klo + b;
+                if (k < 0 || k >= nticks) continue;
+                double g = dS[w * (int64_t)nticks + k];
+                Sq += g * wt[b] * wx[a];
+                Smt += g * mt[b] * wx[a];
+                Sst += g * st_[b] * wx[a];
+                Smx += g * wt[b] * mx[a];
+                Ssx += g * wt[b] * sx_[a];
+            }
+        }
+        double dq = p * Sq, dmt = p * qi * Smt, dst = p * qi * Sst, dmx = p * qi * Smx, dsx = p * qi * Ssx;
+        gq[i] = dq;
+        gx[i] = dmx;
+        gt[i] = dmt;
+        if (!given && ti > 0.0) {
+            gt[i] += dst * st / (2.0 * ti) + dsx * sx / (2.0 * ti);
+            if (DL > 0.0) sDL += dst * st / (2.0 * DL);
+            if (DT > 0.0) sDT += dsx * sx / (2.0 * DT);
+        }
+    }
+    *gDL = sDL;
+    *gDT = sDT;
+    free(wt); free(mt); free(st_); free(wx); free(mx); free(sx_);
+    return skipped;
 }

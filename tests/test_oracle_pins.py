@@ -159,10 +159,10 @@ def test_patch_is_outer_product_of_axis_weights():
     q, x, t = 4321.0, 1003.7, 1234.4
     st, sx = oracle.sigmas([t])
     S = oracle.raster_scatter([q], [x], [t], 300, 3000)
-    wlo, ww = oracle.axis_weights(np.float32(x), sx[0], 5.0)
-    tlo, wt = oracle.axis_weights(np.float32(t), st[0], 0.5)
+    wlo, ww = oracle.axis_weights(x, sx[0], 5.0)
+    tlo, wt = oracle.axis_weights(t, st[0], 0.5)
     ref = np.zeros_like(S)
-    ref[wlo:wlo + len(ww), tlo:tlo + len(wt)] = np.float32(q) * np.outer(ww, wt)
+    ref[wlo:wlo + len(ww), tlo:tlo + len(wt)] = q * np.outer(ww, wt)
     np.testing.assert_allclose(S, ref, rtol=0, atol=1e-12 * q)
     assert len(ww) != len(wt)
 
@@ -176,7 +176,7 @@ def test_patch_sum_equals_charge_for_interior_depos(p):
     x = rng.uniform(50, 4750, n)
     t = rng.uniform(20, 2990, n)
     S = oracle.raster_scatter(q, x, t, 960, 6000, p=p)
-    assert S.sum() == pytest.approx(p * np.float32(q).astype(np.float64).sum(), rel=1e-12)
+    assert S.sum() == pytest.approx(p * q.sum(), rel=1e-12)
 
 
 def test_point_charge_lands_in_one_bin():
@@ -201,7 +201,7 @@ def test_off_grid_charge_is_dropped_and_bad_depos_skipped():
     S, skipped = oracle.raster_scatter([100.0, 50.0, 50.0, 70.0], [-2.4, 5.0, np.nan, 5.0],
                                        [100.0, 100.0, 10.0, -5.0], 3, 400, return_skipped=True)
     assert skipped == 2
-    lo, ww = oracle.axis_weights(np.float32(-2.4), oracle.sigmas([100.0])[1][0], 5.0)
+    lo, ww = oracle.axis_weights(-2.4, oracle.sigmas([100.0])[1][0], 5.0)
     inside = sum(ww[i] for i in range(len(ww)) if lo + i >= 0)
     assert S.sum() == pytest.approx(50.0 + 100.0 * inside, rel=1e-12)
 
