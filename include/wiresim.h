@@ -226,6 +226,27 @@ ws_status ws_simulate(ws_plane* plane, const ws_depos* depos, const ws_params* p
 ws_status ws_convolve_noalloc(const ws_plane_desc* desc, const float* response_dev,
                               const float* grid_dev, float* out_dev, void* stream);
 
+/* Replace the plane's response (K_w x K_t float32 device array, same shape
+ * as at creation) and recompute its spectrum on `stream`. */
+ws_status ws_plane_set_response(ws_plane* plane, const float* response_dev, void* stream);
+
+/* Adjoint of ws_simulate in expected-value mode (fluctuate == 0): given
+ * grad_out_dev = dL/dM (nwires x nticks float32), computes
+ *   gq, gx, gt [n floats]: dL/dq, dL/dx, dL/dt per depo (t through the
+ *       Gaussian mean and, when widths come from diffusion, through
+ *       sigma_L = sqrt(2 D_L t)/v and sigma_T = sqrt(2 D_T t));
+ *   gDL, gDT [1 double each]: dL/dD_L, dL/dD_T (zero with given widths);
+ *   gR [K_w x K_t floats]: dL/dR.
+ * dL/dS is Eq. 2's adjoint (correlation with the response, by FFT); each
+ * patch is recomputed, not stored.  Derivatives of the clamped-edge bin
+ * weights hold everywhere except where a window bound crosses a bin edge.
+ * Any output pointer may be NULL to skip it (gR == NULL skips the
+ * response-gradient work).  All outputs are device pointers; uses the
+ * plane's workspace. */
+ws_status ws_simulate_backward(ws_plane* plane, const ws_depos* depos, const ws_params* params,
+                               const float* grad_out_dev, float* gq, float* gx, float* gt,
+                               double* gDL, double* gDT, float* gR, void* stream);
+
 /* Copy the plane's device status word to *bits.  SYNCHRONISES `stream`. */
 ws_status ws_plane_sync(ws_plane* plane, void* stream, uint32_t* bits);
 

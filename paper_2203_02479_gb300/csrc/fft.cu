@@ -471,7 +471,74 @@ void launch_wc(const float2* X, float2* Y, const float2* Rt, int nwires, int nfr
     wire_conv_kernel<K, B, KS><<<grid, kConvCols, 0, s>>>(X, Y, Rt, nwires, nfreq, stride, kw, center, circular);
 }
 
+// Adjoint coefficients: the wire correlation sum_r conj(Rt[r]) X[w + r - c]
+// is the wire convolution with taps A[kw-1-r] = conj(Rt[r]) and centre
+// kw-1-c.
+__global__ void adj_coeffs_kernel(const float2* __restrict__ Rt, float2* __restrict__ A, int kw, int64_t stride,
+                                  int nfreq) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < (int64_t)kw * nfreq;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int r = (int)(e / nfreq), k = (int)(e - (int64_t)r * nfreq);
+        const float2 v = Rt[(int64_t)r * stride + k];
+        A[(int64_t)(kw - 1 - r) * stride + k] = make_float2(v.x, -v.y);
+    }
+}
+
+// Response-gradient spectra: A[r][k] += scale * sum_w conj(XS[w - (r - c)][k])
+// XG[w][k] over this thread's chunk of wires (XS zero outside the grid, or
+// wrapped), accumulated into A with atomics.
+constexpr int kRespGradRows = 64;
+
+__global__ void __launch_bounds__(128)
+resp_grad_kernel(const float2* __restrict__ XG, const float2* __restrict__ XS, float2* __restrict__ A, int nwires,
+                 int nfreq, int64_t stride, int kw, int center, int circular, float scale) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nfreq) return;
+    const int w0 = blockIdx.y * kRespGradRows;
+    const int w1 = min(nwires, w0 + kRespGradRows);
+    float2 acc[kMaxRespWires];
+#pragma unroll
+    for (int r = 0; r < kMaxRespWires; ++r) acc[r] = make_float2(0.f, 0.f);
+    for (int w = w0; w < w1; ++w) {
+        const float2 xg = __ldg(&XG[(int64_t)w * stride + k]);
+#pragma unroll
+        for (int r = 0; r < kMaxRespWires; ++r) {
+            if (r >= kw) break;
+            int ws = w - (r - center);
+            if (circular) {
+                ws %= nwires;
+                if (ws < 0) ws += nwires;
+            } else if (ws < 0 || ws >= nwires) {
+                continue;
+            }
+            const float2 xs = __ldg(&XS[(int64_t)ws * stride + k]);
+            // conj(xs) * xg
+            acc[r].x = fmaf(xs.x, xg.x, fmaf(xs.y, xg.y, acc[r].x));
+            acc[r].y = fmaf(xs.x, xg.y, fmaf(-xs.y, xg.x, acc[r].y));
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < kMaxRespWires; ++r) {
+        if (r >= kw) break;
+        atomicAdd(&A[(int64_t)r * stride + k].x, scale * acc[r].x);
+        atomicAdd(&A[(int64_t)r * stride + k].y, scale * acc[r].y);
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_adj_coeffs(const float2* Rt, float2* A, int kw, int64_t stride, int nfreq, cudaStream_t s) {
+    adj_coeffs_kernel<<<(kw * nfreq + 255) / 256, 256, 0, s>>>(Rt, A, kw, stride, nfreq);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_resp_grad(const float2* XG, const float2* XS, float2* A, int nwires, int nfreq, int64_t stride,
+                             int kw, int center, int circular, float scale, cudaStream_t s) {
+    if (nwires <= 0 || nfreq <= 0) return cudaSuccess;
+    dim3 grid((nfreq + 127) / 128, (nwires + kRespGradRows - 1) / kRespGradRows);
+    resp_grad_kernel<<<grid, 128, 0, s>>>(XG, XS, A, nwires, nfreq, stride, kw, center, circular, scale);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_twiddles(float2* tw, const FftPlan& plan, cudaStream_t s) {
     pass_twiddles_kernel<<<(plan.L + 255) / 256, 256, 0, s>>>(tw, plan);

@@ -545,6 +545,146 @@ raster_small_kernel(RasterArgs a, float* __restrict__ grid, ws_patches pt, int* 
     }
 }
 
+// ---- adjoint of the expected-value raster (warp per depo)
+//
+// Patch = p q w_t w_x; with u = (e - mu)/sigma clamped to +-n at the window
+// bounds, w = [Phi(u1) - Phi(u0)] / erf(n/sqrt 2), and an interior edge
+// moves Phi by -phi(u)/sigma per unit mu and -u phi(u)/sigma per unit sigma
+// (an edge on the window bound moves with it and contributes nothing).
+struct GradArgs {
+    const float* dS;       // dL/dS, nwires x nticks
+    float* gq;
+    float* gx;
+    float* gt;
+    double* gDL;           // accumulated (caller zeroes), may be null
+    double* gDT;
+    double DL, DT;
+};
+
+// Per-axis weights and their mu / sigma derivatives for bins [first, first + nb).
+__device__ __forceinline__ void axis_weights_grad(float mu, float sigma, float delta, float nsig, bool point,
+                                                  int first, int nb, float inv_norm, float* u_s, float* c_s,
+                                                  float* w, float* dmu, float* dsig, int lane) {
+    if (point) {
+        for (int b = lane; b < nb; b += 32) { w[b] = 1.f; dmu[b] = 0.f; dsig[b] = 0.f; }
+        __syncwarp();
+        return;
+    }
+    const float inv_s = 1.f / sigma;
+    for (int j = lane; j <= nb; j += 32) {
+        const float e = (float)(first + j) * delta;
+        const float u = (e - mu) * inv_s;
+        const bool clamped = u <= -nsig || u >= nsig;
+        const float uc = fminf(fmaxf(u, -nsig), nsig);
+        u_s[j] = uc;
+        // phi(u) / sigma, or 0 on a window bound
+        c_s[j] = clamped ? 0.f : 0.398942280401432678f * __expf(-0.5f * uc * uc) * inv_s;
+    }
+    __syncwarp();
+    const float r2 = 0.707106781186547524f;
+    for (int b = lane; b < nb; b += 32) {
+        const float u0 = u_s[b], u1 = u_s[b + 1];
+        const float p0 = c_s[b], p1 = c_s[b + 1];
+        const float v0 = erfcf(fabsf(u0) * r2), v1 = erfcf(fabsf(u1) * r2);
+        float m;
+        if (u0 >= 0.f) m = 0.5f * (v0 - v1);
+        else if (u1 <= 0.f) m = 0.5f * (v1 - v0);
+        else m = 1.f - 0.5f * (v0 + v1);
+        w[b] = m * inv_norm;
+        dmu[b] = -(p1 - p0) * inv_norm;
+        dsig[b] = -(u1 * p1 - u0 * p0) * inv_norm;
+    }
+    __syncwarp();
+}
+
+__global__ void __launch_bounds__(32 * kWarpsPerBlock)
+depo_grad_kernel(RasterArgs a, GradArgs g) {
+    __shared__ float s_u[kWarpsPerBlock][kChunk + 1];
+    __shared__ float s_c[kWarpsPerBlock][kChunk + 1];
+    __shared__ float s_wt[kWarpsPerBlock][3][kChunk];
+    __shared__ float s_wx[kWarpsPerBlock][3][kChunk];
+    __shared__ double s_red[kWarpsPerBlock][2];
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    const int64_t nwarps = (int64_t)gridDim.x * kWarpsPerBlock;
+    const float inv_norm = 1.f / erff(a.nsig * 0.707106781186547524f);
+    double accL = 0.0, accT = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * kWarpsPerBlock + wib; i < a.n; i += nwarps) {
+        Extent e;
+        float q;
+        bool bad;
+        const bool any = depo_extent(a, i, &e, &q, &bad);
+        if (any) {
+            // One more bin on each side of a non-point axis: the FP32 bin
+            // range can drop a sliver bin whose edge lies within rounding of
+            // the window bound; bins wholly outside get both edges clamped
+            // (zero weight, zero derivative), so the clamp test on u alone
+            // decides which side of the kink the depo is on.
+            if (!e.point_t) { e.k0 = max(e.k0 - 1, 0); e.k1 = min(e.k1 + 1, a.nticks - 1); }
+            if (!e.point_x) { e.w0 = max(e.w0 - 1, 0); e.w1 = min(e.w1 + 1, a.nwires - 1); }
+        }
+        float Sq = 0.f, Smt = 0.f, Sst = 0.f, Smx = 0.f, Ssx = 0.f;
+        for (int kc = any ? e.k0 : 1; any && kc <= e.k1; kc += kChunk) {
+            const int ntc = min(kChunk, e.k1 - kc + 1);
+            axis_weights_grad(e.mu_t, e.st, a.tick, a.nsig, e.point_t, kc, ntc, inv_norm, s_u[wib], s_c[wib],
+                              s_wt[wib][0], s_wt[wib][1], s_wt[wib][2], lane);
+            for (int wc = e.w0; wc <= e.w1; wc += kChunk) {
+                const int nxc = min(kChunk, e.w1 - wc + 1);
+                axis_weights_grad(e.mu_x, e.sx, a.pitch, a.nsig, e.point_x, wc, nxc, inv_norm, s_u[wib],
+                                  s_c[wib], s_wx[wib][0], s_wx[wib][1], s_wx[wib][2], lane);
+                for (int idx = lane; idx < nxc * ntc; idx += 32) {
+                    const int ia = idx / ntc, ib = idx - ia * ntc;
+                    const float gv = __ldg(g.dS + (int64_t)(wc + ia) * a.nticks + kc + ib);
+                    const float wx = s_wx[wib][0][ia], wt = s_wt[wib][0][ib];
+                    Sq = fmaf(gv, wx * wt, Sq);
+                    Smt = fmaf(gv, wx * s_wt[wib][1][ib], Smt);
+                    Sst = fmaf(gv, wx * s_wt[wib][2][ib], Sst);
+                    Smx = fmaf(gv, s_wx[wib][1][ia] * wt, Smx);
+                    Ssx = fmaf(gv, s_wx[wib][2][ia] * wt, Ssx);
+                }
+                __syncwarp();
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            Sq += __shfl_down_sync(0xffffffffu, Sq, o);
+            Smt += __shfl_down_sync(0xffffffffu, Smt, o);
+            Sst += __shfl_down_sync(0xffffffffu, Sst, o);
+            Smx += __shfl_down_sync(0xffffffffu, Smx, o);
+            Ssx += __shfl_down_sync(0xffffffffu, Ssx, o);
+        }
+        if (lane == 0) {
+            const float pq = a.p * q;
+            float dq = 0.f, dx = 0.f, dt = 0.f;
+            if (any) {
+                dq = a.p * Sq;
+                dx = pq * Smx;
+                dt = pq * Smt;
+                const float dst = pq * Sst, dsx = pq * Ssx;
+                if (!a.sig_t && e.mu_t > 0.f) {
+                    dt += (dst * e.st + dsx * e.sx) / (2.f * e.mu_t);
+                    if (g.DL > 0.0) accL += (double)dst * e.st / (2.0 * g.DL);
+                    if (g.DT > 0.0) accT += (double)dsx * e.sx / (2.0 * g.DT);
+                }
+            }
+            if (g.gq) g.gq[i] = dq;
+            if (g.gx) g.gx[i] = dx;
+            if (g.gt) g.gt[i] = dt;
+        }
+    }
+    if (lane == 0) {
+        s_red[wib][0] = accL;
+        s_red[wib][1] = accT;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double L = 0.0, T = 0.0;
+        for (int w = 0; w < kWarpsPerBlock; ++w) { L += s_red[w][0]; T += s_red[w][1]; }
+        if (g.gDL && L != 0.0) atomicAdd(g.gDL, L);
+        if (g.gDT && T != 0.0) atomicAdd(g.gDT, T);
+    }
+}
+
 __global__ void patch_sizes_kernel(RasterArgs a, int64_t* __restrict__ sizes,
                                    unsigned long long* __restrict__ total) {
     unsigned long long mine = 0;
@@ -681,6 +821,14 @@ cudaError_t launch_raster_scatter(const RasterArgs& a, float* grid, const LargeL
         a, grid, none, L.list, L.count, L.cap);
     raster_kernel<EMIT_GRID><<<num_sms() * 2, 32 * kWarpsPerBlock, 0, s>>>(a, grid, none, L.list, L.count, L.cap,
                                                                           L.done);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_depo_grads(const RasterArgs& a, const float* dS, float* gq, float* gx, float* gt, double* gDL,
+                              double* gDT, double DL, double DT, cudaStream_t s) {
+    if (a.n <= 0) return cudaSuccess;
+    GradArgs g{dS, gq, gx, gt, gDL, gDT, DL, DT};
+    depo_grad_kernel<<<grid_for(a.n, kWarpsPerBlock, 8), 32 * kWarpsPerBlock, 0, s>>>(a, g);
     return cudaGetLastError();
 }
 

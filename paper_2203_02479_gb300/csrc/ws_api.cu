@@ -28,8 +28,10 @@ namespace {
 thread_local char g_last_error[256] = "";
 
 const char* const kKernelNames[] = {"memset_grid", "raster_scatter", "fwd_rows", "wire_conv", "inv_rows",
-                                    "patch_sizes", "scan", "raster_patches", "scatter_patches"};
-enum { K_MEMSET, K_RASTER_SCATTER, K_FWD, K_WCONV, K_INV, K_SIZES, K_SCAN, K_RPATCH, K_SCATTER, K_COUNT };
+                                    "patch_sizes", "scan", "raster_patches", "scatter_patches", "depo_grads",
+                                    "resp_grad"};
+enum { K_MEMSET, K_RASTER_SCATTER, K_FWD, K_WCONV, K_INV, K_SIZES, K_SCAN, K_RPATCH, K_SCATTER, K_DGRAD,
+       K_RGRAD, K_COUNT };
 
 // Record a start event for a traced launch; returns the record slot or -1.
 int trace_begin(ws_plane* pl, int kind, cudaStream_t s) {
@@ -109,7 +111,7 @@ size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 struct Layout {
     ws::FftPlan plan;
     int nfreq, fstride;
-    size_t off_status, off_tw, off_rt, off_x, off_y, off_scan, off_large, total;
+    size_t off_status, off_tw, off_rt, off_x, off_y, off_scan, off_large, off_radj, off_racc, off_grid2, total;
 };
 
 ws_status plan_layout(const ws_plane_desc* d, Layout* lay) {
@@ -145,6 +147,9 @@ ws_status plan_layout(const ws_plane_desc* d, Layout* lay) {
     lay->off_y = o; o = align256(o + sizeof(float2) * (size_t)d->nwires * lay->fstride);
     lay->off_scan = o; o = align256(o + sizeof(int64_t) * (size_t)ws::kScanScratch);
     lay->off_large = o; o = align256(o + sizeof(int) * (size_t)ws::kLargeListCap);
+    lay->off_radj = o; o = align256(o + sizeof(float2) * (size_t)d->resp_nwires * lay->fstride);
+    lay->off_racc = o; o = align256(o + sizeof(float2) * (size_t)d->resp_nwires * lay->fstride);
+    lay->off_grid2 = o; o = align256(o + sizeof(float) * (size_t)d->nwires * d->nticks);
     lay->total = o;
     return WS_OK;
 }
@@ -282,6 +287,9 @@ ws_status ws_plane_create(const ws_plane_desc* desc, const float* response_dev, 
     pl->large.count = (unsigned*)(base + lay.off_status + 16);
     pl->large.done = (unsigned*)(base + lay.off_status + 20);
     pl->large.cap = ws::kLargeListCap;
+    pl->Radj = (float2*)(base + lay.off_radj);
+    pl->Racc = (float2*)(base + lay.off_racc);
+    pl->grid2 = (float*)(base + lay.off_grid2);
     cudaStream_t s = (cudaStream_t)stream;
     cudaError_t e = cudaMemsetAsync(base + lay.off_status, 0, 256, s);
     if (e == cudaSuccess) e = ws::launch_twiddles(pl->tw, lay.plan, s);
@@ -290,6 +298,8 @@ ws_status ws_plane_create(const ws_plane_desc* desc, const float* response_dev, 
     if (e == cudaSuccess)
         e = ws::launch_fwd_rows(lay.plan, pl->tw, response_dev, desc->resp_nwires, desc->resp_nticks,
                                 desc->resp_nticks, pl->Rt, lay.fstride, lay.nfreq, 1.0f / (float)lay.plan.L, s);
+    if (e == cudaSuccess)
+        e = ws::launch_adj_coeffs(pl->Rt, pl->Radj, desc->resp_nwires, lay.fstride, lay.nfreq, s);
     // Autotune the wire convolution on this plane's own buffers: each variant
     // once to warm up, then three timed launches; the fastest is kept.
     pl->wconv_variant = 0;
@@ -479,6 +489,59 @@ ws_status ws_simulate(ws_plane* pl, const ws_depos* depos, const ws_params* para
     ws::RasterArgs a = raster_args(pl, depos, params);
     WS_LAUNCH(pl, K_RASTER_SCATTER, s, ws::launch_raster_scatter(a, out_dev, pl->large, s));
     return convolve_impl(pl, out_dev, out_dev, s);
+}
+
+ws_status ws_plane_set_response(ws_plane* pl, const float* response_dev, void* stream) {
+    if (!pl || !response_dev || !aligned(response_dev, 4)) return WS_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    const ws_plane_desc& d = pl->desc;
+    WS_CUDA(ws::launch_fwd_rows(pl->plan, pl->tw, response_dev, d.resp_nwires, d.resp_nticks, d.resp_nticks, pl->Rt,
+                                pl->fstride, pl->nfreq, 1.0f / (float)pl->plan.L, s));
+    WS_CUDA(ws::launch_adj_coeffs(pl->Rt, pl->Radj, d.resp_nwires, pl->fstride, pl->nfreq, s));
+    return WS_OK;
+}
+
+ws_status ws_simulate_backward(ws_plane* pl, const ws_depos* depos, const ws_params* params,
+                               const float* grad_out_dev, float* gq, float* gx, float* gt, double* gDL,
+                               double* gDT, float* gR, void* stream) {
+    if (!pl || !grad_out_dev || !aligned(grad_out_dev, 4)) return WS_ERR_INVALID_ARG;
+    ws_status st = check_depos(depos);
+    if (st == WS_OK) st = check_params(params);
+    if (st != WS_OK) return st;
+    if (params->fluctuate) return WS_ERR_INVALID_ARG;  // the adjoint is of the expected-value path
+    cudaStream_t s = (cudaStream_t)stream;
+    const ws_plane_desc& d = pl->desc;
+    const int circ = d.conv_mode == WS_CONV_CIRCULAR;
+    // dL/dS = adjoint convolution of G: tick transform, wire correlation with
+    // conj(R_hat), inverse transform.
+    WS_LAUNCH(pl, K_FWD, s, ws::launch_fwd_rows(pl->plan, pl->tw, grad_out_dev, d.nwires, d.nticks, d.nticks, pl->X,
+                                                pl->fstride, pl->nfreq, 1.0f, s));
+    WS_LAUNCH(pl, K_WCONV, s, ws::launch_wire_conv(pl->X, pl->Y, pl->Radj, d.nwires, pl->nfreq, pl->fstride,
+                                                   d.resp_nwires, d.resp_nwires - 1 - d.resp_wire_center, circ, s,
+                                                   pl->wconv_variant));
+    WS_LAUNCH(pl, K_INV, s, ws::launch_inv_rows(pl->plan, pl->tw, pl->Y, d.nwires, pl->fstride, pl->nfreq,
+                                                pl->grid2, d.nticks, d.nticks, s));
+    ws::RasterArgs a = raster_args(pl, depos, params);
+    if (gDL) WS_CUDA(cudaMemsetAsync(gDL, 0, sizeof(double), s));
+    if (gDT) WS_CUDA(cudaMemsetAsync(gDT, 0, sizeof(double), s));
+    WS_LAUNCH(pl, K_DGRAD, s, ws::launch_depo_grads(a, pl->grid2, gq, gx, gt, gDL, gDT, params->DL_mm2_us,
+                                                    params->DT_mm2_us, s));
+    if (gR) {
+        // dL/dR: recompute S, transform it, correlate with the transform of G
+        // (still in X) over wires, inverse transform, keep the response window.
+        const size_t grid_bytes = sizeof(float) * (size_t)d.nwires * d.nticks;
+        WS_LAUNCH(pl, K_MEMSET, s, cudaMemsetAsync(pl->grid2, 0, grid_bytes, s));
+        WS_LAUNCH(pl, K_RASTER_SCATTER, s, ws::launch_raster_scatter(a, pl->grid2, pl->large, s));
+        WS_LAUNCH(pl, K_FWD, s, ws::launch_fwd_rows(pl->plan, pl->tw, pl->grid2, d.nwires, d.nticks, d.nticks,
+                                                    pl->Y, pl->fstride, pl->nfreq, 1.0f, s));
+        WS_CUDA(cudaMemsetAsync(pl->Racc, 0, sizeof(float2) * (size_t)d.resp_nwires * pl->fstride, s));
+        WS_LAUNCH(pl, K_RGRAD, s, ws::launch_resp_grad(pl->X, pl->Y, pl->Racc, d.nwires, pl->nfreq, pl->fstride,
+                                                       d.resp_nwires, d.resp_wire_center, circ,
+                                                       1.0f / (float)pl->plan.L, s));
+        WS_LAUNCH(pl, K_INV, s, ws::launch_inv_rows(pl->plan, pl->tw, pl->Racc, d.resp_nwires, pl->fstride,
+                                                    pl->nfreq, gR, d.resp_nticks, d.resp_nticks, s));
+    }
+    return WS_OK;
 }
 
 ws_status ws_plane_sync(ws_plane* pl, void* stream, uint32_t* bits) {

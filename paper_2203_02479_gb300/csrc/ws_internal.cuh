@@ -76,10 +76,20 @@ struct LargeList {
 };
 constexpr unsigned kLargeListCap = 65536;
 
+// Adjoint helpers (fft.cu): flipped conjugate taps; response-gradient
+// spectra accumulated (A must start at zero).
+cudaError_t launch_adj_coeffs(const float2* Rt, float2* A, int kw, int64_t stride, int nfreq, cudaStream_t s);
+cudaError_t launch_resp_grad(const float2* XG, const float2* XS, float2* A, int nwires, int nfreq, int64_t stride,
+                             int kw, int center, int circular, float scale, cudaStream_t s);
+
 // ---- raster / scatter launchers (raster.cu)
 cudaError_t launch_raster_scatter(const RasterArgs& a, float* grid, const LargeList& L, cudaStream_t s);
 cudaError_t launch_patch_sizes(const RasterArgs& a, int64_t* sizes, unsigned long long* total,
                                cudaStream_t s);
+// Adjoint of the expected-value raster: per-depo dL/dq, dL/dx, dL/dt from
+// dS = dL/dS; dL/dD_L and dL/dD_T accumulated into gDL / gDT (FP64).
+cudaError_t launch_depo_grads(const RasterArgs& a, const float* dS, float* gq, float* gx, float* gt, double* gDL,
+                              double* gDT, double DL, double DT, cudaStream_t s);
 cudaError_t launch_scan_inplace(int64_t* v, int64_t n, int64_t* scratch, cudaStream_t s);
 cudaError_t launch_raster_patches(const RasterArgs& a, const ws_patches& p, const LargeList& L, cudaStream_t s);
 cudaError_t launch_scatter_patches(const ws_patches& p, float* grid, int nwires, int nticks,
@@ -112,4 +122,7 @@ struct ws_plane {
     float2* Y;          // nwires x fstride
     int64_t* scan;      // scan scratch
     ws::LargeList large;  // hand-over list of large patches
+    float2* Radj;       // K_w x fstride flipped conjugate taps (adjoint)
+    float2* Racc;       // K_w x fstride response-gradient spectra
+    float* grid2;       // nwires x nticks float scratch grid (adjoint)
 };

@@ -31,8 +31,8 @@ WS_PREC_FP32, WS_PREC_FP32_COMP, WS_PREC_FP64 = 0, 1, 2
 EXPORTED = ("ws_plane_workspace_bytes", "ws_plane_create", "ws_plane_destroy", "ws_plane_get_info",
             "ws_patch_capacity", "ws_rasterize", "ws_scatter", "ws_convolve", "ws_simulate",
             "ws_plane_sync", "ws_plane_clear_status", "ws_plane_trace", "ws_plane_trace_read",
-            "ws_convolve_noalloc", "ws_plane_set_wire_conv_variant", "ws_status_string",
-            "ws_last_error")
+            "ws_convolve_noalloc", "ws_plane_set_wire_conv_variant", "ws_plane_set_response",
+            "ws_simulate_backward", "ws_status_string", "ws_last_error")
 
 
 class WiresimError(RuntimeError):
@@ -118,6 +118,9 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
                                     ctypes.POINTER(ctypes.c_int)],
             "ws_convolve_noalloc": [ctypes.POINTER(WsPlaneDesc), P, P, P, P],
             "ws_plane_set_wire_conv_variant": [P, ctypes.c_int],
+            "ws_plane_set_response": [P, P, P],
+            "ws_simulate_backward": [P, ctypes.POINTER(WsDepos), ctypes.POINTER(WsParams), P, P, P, P, P, P,
+                                     P, P],
         }
         for name, args in sig.items():
             fn = getattr(h, name)
@@ -369,6 +372,30 @@ class Plane:
     def set_wire_conv_variant(self, variant: int):
         _check(load_library().ws_plane_set_wire_conv_variant(self.handle, variant),
                "ws_plane_set_wire_conv_variant")
+
+    def set_response(self, response, stream=None):
+        torch = _torch()
+        if not hasattr(response, "data_ptr"):
+            response = torch.from_numpy(np.ascontiguousarray(response, dtype=np.float32))
+        self.response = response.to(device=self.device, dtype=torch.float32).contiguous()
+        _check(load_library().ws_plane_set_response(self.handle, _ptr(self.response), _stream_handle(stream)),
+               "ws_plane_set_response")
+
+    def backward(self, depos: DeviceDepos, params: Params, grad_out, want_response: bool = True, stream=None):
+        """(gq, gx, gt, gDL, gDT, gR) as device tensors (gR None if not wanted)."""
+        torch = _torch()
+        dev = self.device
+        n = max(depos.n, 1)
+        gq = torch.empty(n, dtype=torch.float32, device=dev)
+        gx = torch.empty(n, dtype=torch.float32, device=dev)
+        gt = torch.empty(n, dtype=torch.float32, device=dev)
+        gD = torch.zeros(2, dtype=torch.float64, device=dev)
+        gR = torch.empty(tuple(self.response.shape), dtype=torch.float32, device=dev) if want_response else None
+        g = grad_out.contiguous()
+        _check(load_library().ws_simulate_backward(
+            self.handle, ctypes.byref(depos.c()), ctypes.byref(params.c()), _ptr(g), _ptr(gq), _ptr(gx), _ptr(gt),
+            _ptr(gD), _ptr(gD) + 8, _ptr(gR), _stream_handle(stream)), "ws_simulate_backward")
+        return gq[:depos.n], gx[:depos.n], gt[:depos.n], gD[0], gD[1], gR
 
     def trace(self, max_records: int):
         ws_plane_trace(self.handle, max_records)

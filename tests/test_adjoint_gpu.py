@@ -1,0 +1,142 @@
+"""GPU adjoint (ws_simulate_backward and the autograd wrapper) against the
+FP64 oracle's gradients, which tests/test_oracle_adjoint_pins.py ties to
+finite differences.
+
+Tolerance: relative L2 <= 1e-4 for each gradient vector (gq, gx, gt, gR)
+and for dL/dD_L, dL/dD_T.  The GPU chain runs in FP32 (FFT adjoint with
+relative error ~1e-6 of ||dS||, erfc/exp weight derivatives at ~1e-6, sums
+over ~25 bins per depo), so errors of a few 1e-6 are expected; 1e-4 leaves
+room for gradients that nearly cancel.
+
+Kinks: the raster's derivative jumps by about phi(3)/sigma where a window
+bound mu +- 3 sigma crosses a bin edge.  A depo whose bound lies within
+FP32 reach of an edge (1e-5 sigma here) has two valid one-sided
+derivatives, and FP32 and FP64 may pick different sides; such depos are
+checked for finiteness only and left out of the per-depo comparison.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2203_02479_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-4
+
+
+@pytest.fixture(scope="module")
+def ws():
+    import torch
+    from paper_2203_02479_gb300 import build, wiresim
+    build.build()
+    wiresim.load_library()
+    torch.cuda.set_device(0)
+    return wiresim
+
+
+def rel(a, b):
+    a = np.asarray(a, np.float64); b = np.asarray(b, np.float64)
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def kink_mask(d, nsig=3.0, reach=1e-5):
+    """Depos with a window bound within `reach` sigmas of a bin edge."""
+    t = d.t_us.astype(np.float64); x = d.x_mm.astype(np.float64)
+    st, sx = oracle.sigmas(t)
+    m = np.zeros(t.shape[0], bool)
+    for mu, sg, delta in ((t, st, oracle.TICK_US), (x, sx, oracle.PITCH_MM)):
+        for sign in (-1.0, 1.0):
+            b = (mu + sign * nsig * sg) / delta
+            m |= np.abs(b - np.round(b)) * delta < reach * np.maximum(sg, 1e-30)
+    return m
+
+
+def compare(got, ref, mask):
+    for name, g, r in zip(("gq", "gx", "gt"), got[:3], ref[:3]):
+        g = np.asarray(g, np.float64)
+        assert np.isfinite(g).all(), name
+        assert rel(g[~mask], r[~mask]) <= TOL, (name, rel(g[~mask], r[~mask]))
+    for name, g, r in zip(("gDL", "gDT", "gR"), got[3:], ref[3:]):
+        assert rel(g, r) <= TOL, (name, rel(g, r))
+
+
+def _case(ws, nw, nt, n, seed, circular=False, R=None, p=1.0):
+    import torch
+    d = inputs.uniform_depos(n, nw, seed, nticks=nt, t_min_us=1.0)
+    R = inputs.response("bipolar") if R is None else R
+    T = np.random.Generator(np.random.PCG64(seed + 1)).standard_normal((nw, nt)) * 20
+    M = oracle.simulate(d.q, d.x_mm, d.t_us, nw, nt, R, 10, circular=circular, p=p)
+    G = 2 * (M - T)
+    ref = oracle.simulate_backward(d.q, d.x_mm, d.t_us, nw, nt, R, 10, G, circular=circular, p=p)
+    plane = ws.Plane(nw, nt, R, circular=circular)
+    got = plane.backward(ws.DeviceDepos.from_plane_depos(d), ws.Params(p_survive=p),
+                         torch.from_numpy(G.astype(np.float32)).cuda())
+    torch.cuda.synchronize()
+    return [g.cpu().numpy() if hasattr(g, "cpu") else g for g in got], ref, kink_mask(d)
+
+
+@pytest.mark.parametrize("circular", [False, True])
+def test_backward_matches_oracle_small(ws, circular):
+    got, ref, mask = _case(ws, 40, 1200, 300, 51, circular=circular, p=0.9)
+    compare(got, ref, mask)
+
+
+def test_backward_full_plane_20k_depos(ws):
+    """960 x 6000 plane, 20,000 depos (t >= 1 us), loss sum (M - T)^2 with a
+    target simulated at shifted parameters (x + 1.5 mm, q x 1.1, D_L x 1.2,
+    D_T x 0.8, R x 0.9)."""
+    import torch
+    nw, nt = 960, 6000
+    d = inputs.uniform_depos(20000, nw, 1003, nticks=nt, t_min_us=1.0)
+    R = inputs.response("bipolar")
+    T = oracle.simulate(d.q * np.float32(1.1), d.x_mm + np.float32(1.5), d.t_us, nw, nt, R * np.float32(0.9), 10,
+                        DL_=oracle.DL * 1.2, DT_=oracle.DT * 0.8)
+    M = oracle.simulate(d.q, d.x_mm, d.t_us, nw, nt, R, 10)
+    G = 2 * (M - T)
+    ref = oracle.simulate_backward(d.q, d.x_mm, d.t_us, nw, nt, R, 10, G)
+    plane = ws.Plane(nw, nt, R)
+    got = plane.backward(ws.DeviceDepos.from_plane_depos(d), ws.Params(),
+                         torch.from_numpy(G.astype(np.float32)).cuda())
+    torch.cuda.synchronize()
+    got = [g.cpu().numpy() if hasattr(g, "cpu") else g for g in got]
+    mask = kink_mask(d)
+    assert mask.mean() < 1e-3
+    compare(got, ref, mask)
+
+
+def test_autograd_wrapper(ws):
+    """Gradients through torch.autograd equal the direct backward call, and
+    the forward equals ws_simulate."""
+    import torch
+    from paper_2203_02479_gb300 import autograd
+    nw, nt = 32, 900
+    d = inputs.uniform_depos(150, nw, 61, nticks=nt, t_min_us=1.0)
+    R = torch.from_numpy(inputs.response("unipolar")).cuda().requires_grad_(True)
+    plane = ws.Plane(nw, nt, R.detach())
+    q = torch.from_numpy(d.q).cuda().requires_grad_(True)
+    x = torch.from_numpy(d.x_mm).cuda().requires_grad_(True)
+    t = torch.from_numpy(d.t_us).cuda().requires_grad_(True)
+    DL = torch.tensor(4e-4, dtype=torch.float64, device="cuda", requires_grad=True)
+    DT = torch.tensor(8.8e-4, dtype=torch.float64, device="cuda", requires_grad=True)
+    target = torch.randn(nw, nt, device="cuda", generator=torch.Generator(device="cuda").manual_seed(3)) * 10
+    M = autograd.simulate(q, x, t, DL, DT, R, plane)
+    loss = ((M - target) ** 2).sum()
+    loss.backward()
+    G = (2 * (M.detach() - target)).contiguous()
+    gq, gx, gt, gDL, gDT, gR = plane.backward(ws.DeviceDepos.from_plane_depos(d), ws.Params(), G)
+    torch.cuda.synchronize()
+    for a, b in ((q.grad, gq), (x.grad, gx), (t.grad, gt), (R.grad, gR)):
+        assert rel(a.cpu().numpy(), b.cpu().numpy()) <= 1e-6
+    assert rel(DL.grad.cpu().numpy(), gDL.cpu().numpy()) <= 1e-6
+    assert rel(DT.grad.cpu().numpy(), gDT.cpu().numpy()) <= 1e-6
+    ref_m = oracle.simulate(d.q, d.x_mm, d.t_us, nw, nt, inputs.response("unipolar"), 10)
+    assert rel(M.detach().cpu().numpy(), ref_m) <= 1e-5
+
+
+def test_backward_rejects_fluctuation(ws):
+    import torch
+    plane = ws.Plane(8, 300, inputs.response())
+    d = ws.DeviceDepos([10.0], [12.0], [30.0])
+    with pytest.raises(ws.WiresimError):
+        plane.backward(d, ws.Params(fluctuate=True, p_survive=0.7), torch.zeros(8, 300, device="cuda"))
