@@ -226,6 +226,28 @@ ws_status ws_simulate(ws_plane* plane, const ws_depos* depos, const ws_params* p
 ws_status ws_convolve_noalloc(const ws_plane_desc* desc, const float* response_dev,
                               const float* grid_dev, float* out_dev, void* stream);
 
+/* Device workspace of ws_simulate_batch: a large-patch hand-over list and
+ * two spectra (max nwires x (L_t/2+1) complex64) per unit of a wave.
+ * units_per_wave: 1 .. 32. */
+ws_status ws_batch_workspace_bytes(ws_plane* const* planes, int nplanes, int units_per_wave,
+                                   size_t* bytes);
+
+/* Many events on a detector of nplanes planes in one call: the units
+ * (event e, plane p), in event-major order u = e * nplanes + p, run in waves
+ * of units_per_wave; each stage of a wave (grid clear, raster + fluctuation +
+ * scatter-add, tick transform, wire convolution, inverse transform) is ONE
+ * launch over all the wave's units, so events with very different depo
+ * counts share the GPU (the paper runs independent processes per GPU for
+ * throughput, Sec. 3.3).  depos[u] are unit u's depos; out_dev[u] its
+ * nwires(p) x nticks output (cleared, then simulated); event e uses
+ * event_id = params->event_id + e.  All planes must share the transform
+ * length, tick count and response shape (else WS_ERR_UNSUPPORTED_SIZE).
+ * Results equal ws_simulate unit by unit (up to summation order).  Makes no
+ * host synchronisation, so it can be captured into a CUDA graph. */
+ws_status ws_simulate_batch(ws_plane* const* planes, int nplanes, const ws_depos* depos, int nevents,
+                            const ws_params* params, float* const* out_dev, void* workspace_dev,
+                            size_t workspace_bytes, int units_per_wave, void* stream);
+
 /* Replace the plane's response (K_w x K_t float32 device array, same shape
  * as at creation) and recompute its spectrum on `stream`. */
 ws_status ws_plane_set_response(ws_plane* plane, const float* response_dev, void* stream);

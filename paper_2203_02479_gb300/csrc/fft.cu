@@ -204,6 +204,16 @@ WS_COMPOSITE(25, 5, 5)
 // ------------------------------------------------------- Stockham passes
 constexpr int kRowThreads = 256;
 
+// Unit owning global block b: the last u with prefix[u] <= b.
+__device__ __forceinline__ int find_unit(const int* prefix, int n, int b) {
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (prefix[mid] <= b) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
 // One Stockham pass of radix R over a length-L sequence: butterfly j reads
 // src[j + r L/R], multiplies input r by w^r with w = e^{-+2 pi i (j mod Ns) /
 // (Ns R)} (w from the pass's table of Ns base twiddles, its powers by a
@@ -278,14 +288,17 @@ __global__ void pass_twiddles_kernel(float2* tw, FftPlan plan) {
 // Two real rows (2 blockIdx.x, 2 blockIdx.x + 1) as one complex transform
 // z = a + i b; then A_k = (Z_k + conj Z_{L-k}) / 2, B_k = (Z_k - conj Z_{L-k}) / 2i.
 __global__ void __launch_bounds__(kRowThreads, 2)
-fwd_rows_kernel(FftPlan plan, const float2* __restrict__ tw, const float* __restrict__ in,
-                int nrows, int ncols, int64_t in_stride, float2* __restrict__ out,
-                int64_t out_stride, int nfreq, float scale, int vec4) {
+fwd_rows_kernel(FftPlan plan, const float2* __restrict__ tw, const __grid_constant__ RowUnits U, int ncols,
+                int64_t in_stride, int64_t out_stride, int nfreq, float scale, int vec4) {
     extern __shared__ __align__(16) float2 smem[];
     const int L = plan.L;
     float2* a = smem;
     float2* b = smem + ((L + 1) & ~1);  // both buffers 16-byte aligned
-    const int r0 = 2 * blockIdx.x;
+    const int u = find_unit(U.prefix, U.n, (int)blockIdx.x);
+    const float* __restrict__ in = static_cast<const float*>(U.in[u]);
+    float2* __restrict__ out = static_cast<float2*>(U.out[u]);
+    const int nrows = U.nrows[u];
+    const int r0 = 2 * ((int)blockIdx.x - U.prefix[u]);
     const bool has_b = r0 + 1 < nrows;
     const float* pa = in + (int64_t)r0 * in_stride;
     const float* pb = has_b ? pa + in_stride : pa;
@@ -329,14 +342,17 @@ fwd_rows_kernel(FftPlan plan, const float2* __restrict__ tw, const float* __rest
 // Two half spectra A (row r0) and B (row r0+1) -> Z = A + iB over the full
 // Hermitian extension, inverse transform, real part row r0, imaginary r0+1.
 __global__ void __launch_bounds__(kRowThreads, 2)
-inv_rows_kernel(FftPlan plan, const float2* __restrict__ tw, const float2* __restrict__ in,
-                int nrows, int64_t in_stride, int nfreq, float* __restrict__ out, int ncols,
-                int64_t out_stride, int vec4) {
+inv_rows_kernel(FftPlan plan, const float2* __restrict__ tw, const __grid_constant__ RowUnits U,
+                int64_t in_stride, int nfreq, int ncols, int64_t out_stride, int vec4) {
     extern __shared__ __align__(16) float2 smem[];
     const int L = plan.L;
     float2* a = smem;
     float2* b = smem + ((L + 1) & ~1);  // both buffers 16-byte aligned
-    const int r0 = 2 * blockIdx.x;
+    const int u = find_unit(U.prefix, U.n, (int)blockIdx.x);
+    const float2* __restrict__ in = static_cast<const float2*>(U.in[u]);
+    float* __restrict__ out = static_cast<float*>(U.out[u]);
+    const int nrows = U.nrows[u];
+    const int r0 = 2 * ((int)blockIdx.x - U.prefix[u]);
     const bool has_b = r0 + 1 < nrows;
     const float2* ya = in + (int64_t)r0 * in_stride;
     const float2* yb = has_b ? ya + in_stride : ya;
@@ -383,12 +399,16 @@ constexpr int kConvCols = 128;
 // per tap into three accumulators instead of four.
 template <int K, int B, bool KARATSUBA>
 __global__ void __launch_bounds__(kConvCols)
-wire_conv_kernel(const float2* __restrict__ X, float2* __restrict__ Y, const float2* __restrict__ Rt,
-                 int nwires, int nfreq, int64_t stride, int kw, int center, int circular) {
+wire_conv_kernel(const __grid_constant__ ConvUnits U, int nfreq, int64_t stride, int kw, int center, int circular) {
     constexpr int ROWS = B + K - 1;
     __shared__ float4 tile[ROWS][kConvCols / 2];
+    const int u = find_unit(U.prefix, U.n, (int)blockIdx.y);
+    const float2* __restrict__ X = U.X[u];
+    float2* __restrict__ Y = U.Y[u];
+    const float2* __restrict__ Rt = U.Rt[u];
+    const int nwires = U.nwires[u];
     const int k0 = blockIdx.x * kConvCols;
-    const int w0 = blockIdx.y * B;
+    const int w0 = ((int)blockIdx.y - U.prefix[u]) * B;
     const int ibase = w0 + center - (K - 1);
     for (int e = threadIdx.x; e < ROWS * (kConvCols / 2); e += kConvCols) {
         const int u = e / (kConvCols / 2), c2 = e - u * (kConvCols / 2);
@@ -464,11 +484,20 @@ wire_conv_kernel(const float2* __restrict__ X, float2* __restrict__ Y, const flo
 }
 
 template <int B, bool KS>
-void launch_wc(const float2* X, float2* Y, const float2* Rt, int nwires, int nfreq, int64_t stride, int kw,
-               int center, int circular, cudaStream_t s) {
+void launch_wc(const ConvBatch& cb, int nfreq, int64_t stride, int kw, int center, int circular, cudaStream_t s) {
     constexpr int K = kMaxRespWires;
-    dim3 grid((nfreq + kConvCols - 1) / kConvCols, (nwires + B - 1) / B);
-    wire_conv_kernel<K, B, KS><<<grid, kConvCols, 0, s>>>(X, Y, Rt, nwires, nfreq, stride, kw, center, circular);
+    ConvUnits U;
+    U.n = cb.n;
+    U.prefix[0] = 0;
+    for (int i = 0; i < cb.n; ++i) {
+        U.X[i] = cb.X[i];
+        U.Y[i] = cb.Y[i];
+        U.Rt[i] = cb.Rt[i];
+        U.nwires[i] = cb.nwires[i];
+        U.prefix[i + 1] = U.prefix[i] + (cb.nwires[i] + B - 1) / B;
+    }
+    dim3 grid((nfreq + kConvCols - 1) / kConvCols, U.prefix[cb.n]);
+    wire_conv_kernel<K, B, KS><<<grid, kConvCols, 0, s>>>(U, nfreq, stride, kw, center, circular);
 }
 
 // Adjoint coefficients: the wire correlation sum_r conj(Rt[r]) X[w + r - c]
@@ -549,17 +578,62 @@ static cudaError_t set_smem(const void* fn, int bytes) {
     return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
 }
 
+static RowUnits row_units(const RowBatch& rb, bool* aligned16) {
+    RowUnits U;
+    U.n = rb.n;
+    U.prefix[0] = 0;
+    *aligned16 = true;
+    for (int i = 0; i < rb.n; ++i) {
+        U.in[i] = rb.in[i];
+        U.out[i] = rb.out[i];
+        U.nrows[i] = rb.nrows[i];
+        U.prefix[i + 1] = U.prefix[i] + (rb.nrows[i] + 1) / 2;
+        *aligned16 = *aligned16 && ((uintptr_t)rb.in[i] % 16 == 0) && ((uintptr_t)rb.out[i] % 16 == 0);
+    }
+    return U;
+}
+
+cudaError_t launch_fwd_rows_batch(const FftPlan& plan, const float2* tw, const RowBatch& rb, int ncols,
+                                  int64_t in_stride, int64_t out_stride, int nfreq, float scale, cudaStream_t s) {
+    if (rb.n <= 0) return cudaSuccess;
+    const int smem = 2 * ((plan.L + 1) & ~1) * (int)sizeof(float2);
+    cudaError_t e = set_smem((const void*)fwd_rows_kernel, smem);
+    if (e != cudaSuccess) return e;
+    bool al = false;
+    const RowUnits U = row_units(rb, &al);
+    if (U.prefix[rb.n] <= 0) return cudaSuccess;
+    const int nload = ncols < plan.L ? ncols : plan.L;
+    const int vec4 = al && (in_stride % 4 == 0) && (nload % 4 == 0);
+    fwd_rows_kernel<<<U.prefix[rb.n], kRowThreads, smem, s>>>(plan, tw, U, ncols, in_stride, out_stride, nfreq,
+                                                              scale, vec4);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_fwd_rows(const FftPlan& plan, const float2* tw, const float* in, int nrows,
                             int ncols, int64_t in_stride, float2* out, int64_t out_stride,
                             int nfreq, float scale, cudaStream_t s) {
     if (nrows <= 0) return cudaSuccess;
+    RowBatch rb;
+    rb.n = 1;
+    rb.in[0] = in;
+    rb.out[0] = out;
+    rb.nrows[0] = nrows;
+    return launch_fwd_rows_batch(plan, tw, rb, ncols, in_stride, out_stride, nfreq, scale, s);
+}
+
+cudaError_t launch_inv_rows_batch(const FftPlan& plan, const float2* tw, const RowBatch& rb, int64_t in_stride,
+                                  int nfreq, int ncols, int64_t out_stride, cudaStream_t s) {
+    if (rb.n <= 0) return cudaSuccess;
     const int smem = 2 * ((plan.L + 1) & ~1) * (int)sizeof(float2);
-    cudaError_t e = set_smem((const void*)fwd_rows_kernel, smem);
+    cudaError_t e = set_smem((const void*)inv_rows_kernel, smem);
     if (e != cudaSuccess) return e;
-    const int nload = ncols < plan.L ? ncols : plan.L;
-    const int vec4 = ((uintptr_t)in % 16 == 0) && (in_stride % 4 == 0) && (nload % 4 == 0);
-    fwd_rows_kernel<<<(nrows + 1) / 2, kRowThreads, smem, s>>>(plan, tw, in, nrows, ncols, in_stride,
-                                                               out, out_stride, nfreq, scale, vec4);
+    bool al = false;
+    const RowUnits U = row_units(rb, &al);
+    if (U.prefix[rb.n] <= 0) return cudaSuccess;
+    const int nst = ncols < plan.L ? ncols : plan.L;
+    const int vec4 = al && (out_stride % 4 == 0) && (nst % 4 == 0);
+    inv_rows_kernel<<<U.prefix[rb.n], kRowThreads, smem, s>>>(plan, tw, U, in_stride, nfreq, ncols, out_stride,
+                                                              vec4);
     return cudaGetLastError();
 }
 
@@ -567,26 +641,36 @@ cudaError_t launch_inv_rows(const FftPlan& plan, const float2* tw, const float2*
                             int64_t in_stride, int nfreq, float* out, int ncols,
                             int64_t out_stride, cudaStream_t s) {
     if (nrows <= 0) return cudaSuccess;
-    const int smem = 2 * ((plan.L + 1) & ~1) * (int)sizeof(float2);
-    cudaError_t e = set_smem((const void*)inv_rows_kernel, smem);
-    if (e != cudaSuccess) return e;
-    const int nst = ncols < plan.L ? ncols : plan.L;
-    const int vec4 = ((uintptr_t)out % 16 == 0) && (out_stride % 4 == 0) && (nst % 4 == 0);
-    inv_rows_kernel<<<(nrows + 1) / 2, kRowThreads, smem, s>>>(plan, tw, in, nrows, in_stride, nfreq,
-                                                               out, ncols, out_stride, vec4);
+    RowBatch rb;
+    rb.n = 1;
+    rb.in[0] = in;
+    rb.out[0] = out;
+    rb.nrows[0] = nrows;
+    return launch_inv_rows_batch(plan, tw, rb, in_stride, nfreq, ncols, out_stride, s);
+}
+
+cudaError_t launch_wire_conv_batch(const ConvBatch& cb, int nfreq, int64_t stride, int kw, int center, int circular,
+                                   cudaStream_t s, int variant) {
+    if (cb.n <= 0 || nfreq <= 0) return cudaSuccess;
+    switch (variant) {
+        case 1: launch_wc<16, true>(cb, nfreq, stride, kw, center, circular, s); break;
+        case 2: launch_wc<8, false>(cb, nfreq, stride, kw, center, circular, s); break;
+        case 3: launch_wc<8, true>(cb, nfreq, stride, kw, center, circular, s); break;
+        default: launch_wc<16, false>(cb, nfreq, stride, kw, center, circular, s); break;
+    }
     return cudaGetLastError();
 }
 
 cudaError_t launch_wire_conv(const float2* X, float2* Y, const float2* Rt, int nwires, int nfreq,
                              int64_t stride, int kw, int center, int circular, cudaStream_t s, int variant) {
     if (nwires <= 0 || nfreq <= 0) return cudaSuccess;
-    switch (variant) {
-        case 1: launch_wc<16, true>(X, Y, Rt, nwires, nfreq, stride, kw, center, circular, s); break;
-        case 2: launch_wc<8, false>(X, Y, Rt, nwires, nfreq, stride, kw, center, circular, s); break;
-        case 3: launch_wc<8, true>(X, Y, Rt, nwires, nfreq, stride, kw, center, circular, s); break;
-        default: launch_wc<16, false>(X, Y, Rt, nwires, nfreq, stride, kw, center, circular, s); break;
-    }
-    return cudaGetLastError();
+    ConvBatch cb;
+    cb.n = 1;
+    cb.X[0] = X;
+    cb.Y[0] = Y;
+    cb.Rt[0] = Rt;
+    cb.nwires[0] = nwires;
+    return launch_wire_conv_batch(cb, nfreq, stride, kw, center, circular, s, variant);
 }
 
 }  // namespace ws

@@ -174,6 +174,16 @@ __device__ __forceinline__ void axis_weights(float mu, float sigma, float delta,
 
 enum { EMIT_GRID = 0, EMIT_PATCH = 1 };
 
+// Unit owning global item b: the last u with prefix[u] <= b.
+__device__ __forceinline__ int find_unit64(const long long* prefix, int n, long long b) {
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (prefix[mid] <= b) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
 constexpr int kSmallT = 16;  // largest patch (ticks x wires) the lane-per-depo kernel takes
 constexpr int kSmallW = 8;
 
@@ -181,13 +191,13 @@ __device__ __forceinline__ bool is_large(const Extent& e) {
     return (e.k1 - e.k0 + 1) > kSmallT || (e.w1 - e.w0 + 1) > kSmallW;
 }
 
-// Warp per depo.  With list == nullptr every depo is processed; otherwise
-// only the large patches the lane-per-depo kernel handed over: the list's
-// entries if they fit in it, else every depo whose patch is large.  The
-// last block to finish resets the list counter for the next launch.
+// Warp per depo for the large patches the lane-pair kernel handed over:
+// the list's (unit, depo) entries if they fit in it, else every depo of
+// every unit whose patch is large.  The last block to finish resets the
+// list counter for the next launch.
 template <int MODE>
 __global__ void __launch_bounds__(32 * kWarpsPerBlock)
-raster_kernel(RasterArgs a, float* __restrict__ grid, ws_patches pt, const int* __restrict__ list,
+raster_kernel(const __grid_constant__ RasterUnits U, ws_patches pt, const long long* __restrict__ list,
               unsigned* list_count, unsigned list_cap, unsigned* done) {
     __shared__ float s_u[kWarpsPerBlock][kChunk + 1];
     __shared__ float s_c[kWarpsPerBlock][kChunk + 1];
@@ -199,18 +209,27 @@ raster_kernel(RasterArgs a, float* __restrict__ grid, ws_patches pt, const int* 
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
     const int64_t nwarps = (int64_t)gridDim.x * kWarpsPerBlock;
-    const float inv_norm = 1.f / erff(a.nsig * 0.707106781186547524f);
-    const unsigned nlist = list ? *(volatile unsigned*)list_count : 0u;
-    const bool use_list = list != nullptr && nlist <= list_cap;
-    const int64_t nitems = list == nullptr ? a.n : (use_list ? (int64_t)nlist : a.n);
+    const unsigned nlist = *(volatile unsigned*)list_count;
+    const bool use_list = nlist <= list_cap;
+    const int64_t nitems = use_list ? (int64_t)nlist : U.dprefix[U.n];
     for (int64_t it = (int64_t)blockIdx.x * kWarpsPerBlock + wib; it < nitems; it += nwarps) {
-        const int64_t i = use_list ? (int64_t)list[it] : it;
+        int u;
+        int64_t i;
+        if (use_list) {
+            const long long entry = list[it];
+            u = (int)(entry >> 40);
+            i = entry & ((1ll << 40) - 1);
+        } else {
+            u = find_unit64(U.dprefix, U.n, it);
+            i = it - U.dprefix[u];
+        }
+        const RasterArgs& a = U.a[u];
+        float* __restrict__ grid = U.grid[u];
         Extent e;
         float q;
         bool bad;
         const bool any = depo_extent(a, i, &e, &q, &bad);
-        if (list != nullptr && !(any && is_large(e))) continue;  // not handed over
-        if (bad && lane == 0) atomicOr(a.status, WS_DEV_BAD_DEPO);
+        if (!(any && is_large(e))) continue;  // not handed over
         int64_t off = 0;
         int ntf = 0;
         if (MODE == EMIT_PATCH) {
@@ -228,6 +247,7 @@ raster_kernel(RasterArgs a, float* __restrict__ grid, ws_patches pt, const int* 
             if (!fits) continue;
         }
         if (!any) continue;
+        const float inv_norm = 1.f / erff(a.nsig * 0.707106781186547524f);
         const float scale = a.fluct ? 1.f : a.p * q;
         for (int kc = e.k0; kc <= e.k1; kc += kChunk) {
             const int ntc = min(kChunk, e.k1 - kc + 1);
@@ -302,15 +322,13 @@ raster_kernel(RasterArgs a, float* __restrict__ grid, ws_patches pt, const int* 
             }
         }
     }
-    if (list != nullptr) {
-        __syncthreads();
-        if (threadIdx.x == 0) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        if (atomicAdd(done, 1u) == gridDim.x - 1) {
+            *list_count = 0u;
+            *done = 0u;
             __threadfence();
-            if (atomicAdd(done, 1u) == gridDim.x - 1) {
-                *list_count = 0u;
-                *done = 0u;
-                __threadfence();
-            }
         }
     }
 }
@@ -361,7 +379,7 @@ __device__ __forceinline__ int find_slot(const int* s, int v) {
 
 template <int MODE>
 __global__ void __launch_bounds__(32 * kSmallWarpsPerBlock, 8)
-raster_small_kernel(RasterArgs a, float* __restrict__ grid, ws_patches pt, int* __restrict__ list,
+raster_small_kernel(const __grid_constant__ RasterUnits U, ws_patches pt, long long* __restrict__ list,
                     unsigned* list_count, unsigned list_cap) {
     constexpr int W = kSmallWarpsPerBlock;
     constexpr int G = kSmallGroup;
@@ -380,10 +398,15 @@ raster_small_kernel(RasterArgs a, float* __restrict__ grid, ws_patches pt, int* 
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
     const int64_t nwarps = (int64_t)gridDim.x * W;
-    const float inv_norm = 1.f / erff(a.nsig * 0.707106781186547524f);
     const int dl = lane & (G - 1);      // depo slot of this lane
     const bool tick_lane = lane < G;    // lane pair: tick edges on dl, wire edges on dl + G
-    for (int64_t base = ((int64_t)blockIdx.x * W + wib) * G; base < a.n; base += nwarps * G) {
+    const int64_t ngroups = U.gprefix[U.n];
+    for (int64_t grp = (int64_t)blockIdx.x * W + wib; grp < ngroups; grp += nwarps) {
+        const int uu = find_unit64(U.gprefix, U.n, grp);
+        const RasterArgs& a = U.a[uu];
+        float* __restrict__ grid = U.grid[uu];
+        const float inv_norm = 1.f / erff(a.nsig * 0.707106781186547524f);
+        const int64_t base = (grp - U.gprefix[uu]) * G;
         const int64_t i = base + dl;
         Extent e;
         float q = 0.f;
@@ -393,7 +416,7 @@ raster_small_kernel(RasterArgs a, float* __restrict__ grid, ws_patches pt, int* 
         const bool large = any && is_large(e);
         if (large && tick_lane) {
             const unsigned slot = atomicAdd(list_count, 1u);
-            if (slot < list_cap) list[slot] = (int)i;
+            if (slot < list_cap) list[slot] = ((long long)uu << 40) | (long long)i;
         }
         const int ntc = any ? e.k1 - e.k0 + 1 : 0;
         const int nxc = any ? e.w1 - e.w0 + 1 : 0;
@@ -814,22 +837,42 @@ int num_sms() {
     return n;
 }
 
-cudaError_t launch_raster_scatter(const RasterArgs& a, float* grid, const LargeList& L, cudaStream_t s) {
-    if (a.n <= 0) return cudaSuccess;
-    ws_patches none{};
-    raster_small_kernel<EMIT_GRID><<<grid_for(a.n, kSmallGroup * kSmallWarpsPerBlock, 16), 32 * kSmallWarpsPerBlock, 0, s>>>(
-        a, grid, none, L.list, L.count, L.cap);
-    raster_kernel<EMIT_GRID><<<num_sms() * 2, 32 * kWarpsPerBlock, 0, s>>>(a, grid, none, L.list, L.count, L.cap,
-                                                                          L.done);
+static RasterUnits raster_units(const RasterBatch& rb) {
+    RasterUnits U;
+    U.n = rb.n;
+    U.gprefix[0] = 0;
+    U.dprefix[0] = 0;
+    for (int i = 0; i < rb.n; ++i) {
+        U.a[i] = rb.a[i];
+        U.grid[i] = rb.grid[i];
+        U.gprefix[i + 1] = U.gprefix[i] + (rb.a[i].n + kSmallGroup - 1) / kSmallGroup;
+        U.dprefix[i + 1] = U.dprefix[i] + rb.a[i].n;
+    }
+    return U;
+}
+
+template <int MODE>
+static cudaError_t launch_raster_units(const RasterUnits& U, const ws_patches& p, const LargeList& L,
+                                       cudaStream_t s) {
+    if (U.dprefix[U.n] <= 0) return cudaSuccess;
+    const int64_t groups = U.gprefix[U.n];
+    int blocks = grid_for(groups * 32, 32 * kSmallWarpsPerBlock, 16);
+    raster_small_kernel<MODE><<<blocks, 32 * kSmallWarpsPerBlock, 0, s>>>(U, p, L.list, L.count, L.cap);
+    raster_kernel<MODE><<<num_sms() * 2, 32 * kWarpsPerBlock, 0, s>>>(U, p, L.list, L.count, L.cap, L.done);
     return cudaGetLastError();
 }
 
-cudaError_t launch_depo_grads(const RasterArgs& a, const float* dS, float* gq, float* gx, float* gt, double* gDL,
-                              double* gDT, double DL, double DT, cudaStream_t s) {
-    if (a.n <= 0) return cudaSuccess;
-    GradArgs g{dS, gq, gx, gt, gDL, gDT, DL, DT};
-    depo_grad_kernel<<<grid_for(a.n, kWarpsPerBlock, 8), 32 * kWarpsPerBlock, 0, s>>>(a, g);
-    return cudaGetLastError();
+cudaError_t launch_raster_scatter_batch(const RasterBatch& rb, const LargeList& L, cudaStream_t s) {
+    ws_patches none{};
+    return launch_raster_units<EMIT_GRID>(raster_units(rb), none, L, s);
+}
+
+cudaError_t launch_raster_scatter(const RasterArgs& a, float* grid, const LargeList& L, cudaStream_t s) {
+    RasterBatch rb;
+    rb.n = 1;
+    rb.a[0] = a;
+    rb.grid[0] = grid;
+    return launch_raster_scatter_batch(rb, L, s);
 }
 
 cudaError_t launch_patch_sizes(const RasterArgs& a, int64_t* sizes, unsigned long long* total, cudaStream_t s) {
@@ -848,17 +891,48 @@ cudaError_t launch_scan_inplace(int64_t* v, int64_t n, int64_t* scratch, cudaStr
 }
 
 cudaError_t launch_raster_patches(const RasterArgs& a, const ws_patches& p, const LargeList& L, cudaStream_t s) {
-    if (a.n <= 0) return cudaSuccess;
-    raster_small_kernel<EMIT_PATCH><<<grid_for(a.n, kSmallGroup * kSmallWarpsPerBlock, 16), 32 * kSmallWarpsPerBlock, 0, s>>>(
-        a, nullptr, p, L.list, L.count, L.cap);
-    raster_kernel<EMIT_PATCH><<<num_sms() * 2, 32 * kWarpsPerBlock, 0, s>>>(a, nullptr, p, L.list, L.count, L.cap,
-                                                                           L.done);
-    return cudaGetLastError();
+    RasterBatch rb;
+    rb.n = 1;
+    rb.a[0] = a;
+    rb.grid[0] = nullptr;
+    return launch_raster_units<EMIT_PATCH>(raster_units(rb), p, L, s);
 }
 
 cudaError_t launch_scatter_patches(const ws_patches& p, float* grid, int nwires, int nticks, cudaStream_t s) {
     if (p.n <= 0) return cudaSuccess;
     scatter_patches_kernel<<<grid_for(p.n, 8, 8), 256, 0, s>>>(p, grid, nwires, nticks);
+    return cudaGetLastError();
+}
+
+// Zero every unit's grid (float4 stores; grids are 16-byte aligned and a
+// multiple of 4 floats, else the tail is done with scalar stores).
+__global__ void zero_grids_kernel(const __grid_constant__ RasterUnits U, const __grid_constant__ ZeroSizes Z) {
+    for (int u = 0; u < U.n; ++u) {
+        float* g = U.grid[u];
+        const int64_t n = Z.count[u];
+        const int64_t n4 = ((uintptr_t)g % 16 == 0) ? n / 4 : 0;
+        float4* g4 = reinterpret_cast<float4*>(g);
+        for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += (int64_t)gridDim.x * blockDim.x)
+            g4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int64_t i = 4 * n4 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+             i += (int64_t)gridDim.x * blockDim.x)
+            g[i] = 0.f;
+    }
+}
+
+cudaError_t launch_zero_grids(const RasterBatch& rb, const int64_t* counts, cudaStream_t s) {
+    RasterUnits U = raster_units(rb);
+    ZeroSizes Z;
+    for (int i = 0; i < rb.n; ++i) Z.count[i] = counts[i];
+    zero_grids_kernel<<<num_sms() * 4, 256, 0, s>>>(U, Z);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_depo_grads(const RasterArgs& a, const float* dS, float* gq, float* gx, float* gt, double* gDL,
+                              double* gDT, double DL, double DT, cudaStream_t s) {
+    if (a.n <= 0) return cudaSuccess;
+    GradArgs g{dS, gq, gx, gt, gDL, gDT, DL, DT};
+    depo_grad_kernel<<<grid_for(a.n, kWarpsPerBlock, 8), 32 * kWarpsPerBlock, 0, s>>>(a, g);
     return cudaGetLastError();
 }
 

@@ -146,7 +146,7 @@ ws_status plan_layout(const ws_plane_desc* d, Layout* lay) {
     lay->off_x = o; o = align256(o + sizeof(float2) * (size_t)d->nwires * lay->fstride);
     lay->off_y = o; o = align256(o + sizeof(float2) * (size_t)d->nwires * lay->fstride);
     lay->off_scan = o; o = align256(o + sizeof(int64_t) * (size_t)ws::kScanScratch);
-    lay->off_large = o; o = align256(o + sizeof(int) * (size_t)ws::kLargeListCap);
+    lay->off_large = o; o = align256(o + sizeof(long long) * (size_t)ws::kLargeListCap);
     lay->off_radj = o; o = align256(o + sizeof(float2) * (size_t)d->resp_nwires * lay->fstride);
     lay->off_racc = o; o = align256(o + sizeof(float2) * (size_t)d->resp_nwires * lay->fstride);
     lay->off_grid2 = o; o = align256(o + sizeof(float) * (size_t)d->nwires * d->nticks);
@@ -283,7 +283,7 @@ ws_status ws_plane_create(const ws_plane_desc* desc, const float* response_dev, 
     pl->X = (float2*)(base + lay.off_x);
     pl->Y = (float2*)(base + lay.off_y);
     pl->scan = (int64_t*)(base + lay.off_scan);
-    pl->large.list = (int*)(base + lay.off_large);
+    pl->large.list = (long long*)(base + lay.off_large);
     pl->large.count = (unsigned*)(base + lay.off_status + 16);
     pl->large.done = (unsigned*)(base + lay.off_status + 20);
     pl->large.cap = ws::kLargeListCap;
@@ -543,6 +543,125 @@ ws_status ws_simulate_backward(ws_plane* pl, const ws_depos* depos, const ws_par
     }
     return WS_OK;
 }
+
+}  // extern "C"
+
+namespace {
+
+struct BatchLayout {
+    size_t off_counters, off_list, off_spec, spec_bytes, total;
+};
+
+ws_status batch_layout(ws_plane* const* planes, int nplanes, int units_per_wave, BatchLayout* lay) {
+    if (!planes || nplanes <= 0 || units_per_wave <= 0 || units_per_wave > ws::kMaxUnits) return WS_ERR_INVALID_ARG;
+    int maxw = 0;
+    const ws_plane* p0 = planes[0];
+    if (!p0) return WS_ERR_INVALID_ARG;
+    for (int i = 0; i < nplanes; ++i) {
+        const ws_plane* p = planes[i];
+        if (!p) return WS_ERR_INVALID_ARG;
+        // one launch per stage needs one transform plan and one response shape
+        if (p->plan.L != p0->plan.L || p->plan.npass != p0->plan.npass || p->fstride != p0->fstride ||
+            p->desc.nticks != p0->desc.nticks || p->desc.resp_nwires != p0->desc.resp_nwires ||
+            p->desc.resp_wire_center != p0->desc.resp_wire_center || p->desc.conv_mode != p0->desc.conv_mode)
+            return WS_ERR_UNSUPPORTED_SIZE;
+        for (int j = 0; j < p->plan.npass; ++j)
+            if (p->plan.radix[j] != p0->plan.radix[j]) return WS_ERR_UNSUPPORTED_SIZE;
+        if (p->desc.nwires > maxw) maxw = p->desc.nwires;
+    }
+    size_t o = 0;
+    lay->off_counters = o; o = align256(o + 256);
+    lay->off_list = o; o = align256(o + sizeof(long long) * (size_t)ws::kLargeListCap);
+    lay->spec_bytes = align256(sizeof(float2) * (size_t)maxw * p0->fstride);
+    lay->off_spec = o; o += 2 * (size_t)units_per_wave * lay->spec_bytes;
+    lay->total = o;
+    return WS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+ws_status ws_batch_workspace_bytes(ws_plane* const* planes, int nplanes, int units_per_wave, size_t* bytes) {
+    if (!bytes) return WS_ERR_INVALID_ARG;
+    BatchLayout lay;
+    ws_status st = batch_layout(planes, nplanes, units_per_wave, &lay);
+    if (st != WS_OK) return st;
+    *bytes = lay.total;
+    return WS_OK;
+}
+
+ws_status ws_simulate_batch(ws_plane* const* planes, int nplanes, const ws_depos* depos, int nevents,
+                            const ws_params* params, float* const* out_dev, void* workspace_dev,
+                            size_t workspace_bytes, int units_per_wave, void* stream) {
+    BatchLayout lay;
+    ws_status st = batch_layout(planes, nplanes, units_per_wave, &lay);
+    if (st != WS_OK) return st;
+    if (!depos || !out_dev || nevents < 0) return WS_ERR_INVALID_ARG;
+    st = check_params(params);
+    if (st != WS_OK) return st;
+    if (!workspace_dev || !aligned(workspace_dev, 256) || workspace_bytes < lay.total) return WS_ERR_WORKSPACE;
+    if (params->event_id + (uint64_t)nevents > (1u << 28)) return WS_ERR_INVALID_ARG;
+    const int nunits = nevents * nplanes;
+    for (int u = 0; u < nunits; ++u) {
+        st = check_depos(&depos[u]);
+        if (st != WS_OK) return st;
+        if (!out_dev[u] || !aligned(out_dev[u], 4)) return WS_ERR_INVALID_ARG;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    char* base = (char*)workspace_dev;
+    ws::LargeList L;
+    L.list = (long long*)(base + lay.off_list);
+    L.count = (unsigned*)(base + lay.off_counters);
+    L.done = (unsigned*)(base + lay.off_counters + 4);
+    L.cap = ws::kLargeListCap;
+    WS_CUDA(cudaMemsetAsync(base + lay.off_counters, 0, 256, s));
+    ws_plane* p0 = planes[0];
+    const ws_plane_desc& d0 = p0->desc;
+    const int circ = d0.conv_mode == WS_CONV_CIRCULAR;
+    for (int u0 = 0; u0 < nunits; u0 += units_per_wave) {
+        const int nu = nunits - u0 < units_per_wave ? nunits - u0 : units_per_wave;
+        ws::RasterBatch rb;
+        ws::RowBatch fb, ib;
+        ws::ConvBatch cb;
+        int64_t counts[ws::kMaxUnits];
+        rb.n = fb.n = ib.n = cb.n = nu;
+        for (int j = 0; j < nu; ++j) {
+            const int u = u0 + j, e = u / nplanes, pi = u % nplanes;
+            ws_plane* pl = planes[pi];
+            ws_params pe = *params;
+            pe.event_id = params->event_id + (uint32_t)e;
+            float2* X = (float2*)(base + lay.off_spec + (size_t)(2 * j) * lay.spec_bytes);
+            float2* Y = (float2*)(base + lay.off_spec + (size_t)(2 * j + 1) * lay.spec_bytes);
+            rb.a[j] = raster_args(pl, &depos[u], &pe);
+            rb.grid[j] = out_dev[u];
+            counts[j] = (int64_t)pl->desc.nwires * pl->desc.nticks;
+            fb.in[j] = out_dev[u];
+            fb.out[j] = X;
+            fb.nrows[j] = pl->desc.nwires;
+            cb.X[j] = X;
+            cb.Y[j] = Y;
+            cb.Rt[j] = pl->Rt;
+            cb.nwires[j] = pl->desc.nwires;
+            ib.in[j] = Y;
+            ib.out[j] = out_dev[u];
+            ib.nrows[j] = pl->desc.nwires;
+        }
+        WS_LAUNCH(p0, K_MEMSET, s, ws::launch_zero_grids(rb, counts, s));
+        WS_LAUNCH(p0, K_RASTER_SCATTER, s, ws::launch_raster_scatter_batch(rb, L, s));
+        WS_LAUNCH(p0, K_FWD, s, ws::launch_fwd_rows_batch(p0->plan, p0->tw, fb, d0.nticks, d0.nticks, p0->fstride,
+                                                          p0->nfreq, 1.0f, s));
+        WS_LAUNCH(p0, K_WCONV, s, ws::launch_wire_conv_batch(cb, p0->nfreq, p0->fstride, d0.resp_nwires,
+                                                             d0.resp_wire_center, circ, s, p0->wconv_variant));
+        WS_LAUNCH(p0, K_INV, s, ws::launch_inv_rows_batch(p0->plan, p0->tw, ib, p0->fstride, p0->nfreq, d0.nticks,
+                                                          d0.nticks, s));
+    }
+    return WS_OK;
+}
+
+}  // extern "C"
+
+extern "C" {
 
 ws_status ws_plane_sync(ws_plane* pl, void* stream, uint32_t* bits) {
     if (!pl || !bits) return WS_ERR_INVALID_ARG;

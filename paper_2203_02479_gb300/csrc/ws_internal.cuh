@@ -45,6 +45,40 @@ struct RasterArgs {
     uint32_t* status;
 };
 
+// ---- unit tables for launches that cover several (event, plane) units
+constexpr int kMaxUnits = 32;
+
+// Host-side batch descriptions.
+struct RowBatch {          // row transforms: unit i has nrows[i] rows in[i] -> out[i]
+    int n;
+    const void* in[kMaxUnits];
+    void* out[kMaxUnits];
+    int nrows[kMaxUnits];
+};
+struct ConvBatch {         // wire convolutions: unit i maps X[i] -> Y[i] with taps Rt[i]
+    int n;
+    const float2* X[kMaxUnits];
+    float2* Y[kMaxUnits];
+    const float2* Rt[kMaxUnits];
+    int nwires[kMaxUnits];
+};
+// Device-side tables (kernel parameters, read in place as __grid_constant__).
+struct RowUnits {
+    int n;
+    int prefix[kMaxUnits + 1];   // cumulative row pairs
+    const void* in[kMaxUnits];
+    void* out[kMaxUnits];
+    int nrows[kMaxUnits];
+};
+struct ConvUnits {
+    int n;
+    int prefix[kMaxUnits + 1];   // cumulative wire blocks
+    const float2* X[kMaxUnits];
+    float2* Y[kMaxUnits];
+    const float2* Rt[kMaxUnits];
+    int nwires[kMaxUnits];
+};
+
 // ---- FFT / convolution launchers (fft.cu)
 // Pass twiddle table: Ns base twiddles per pass (see FftPlan::twoff).
 cudaError_t launch_twiddles(float2* tw, const FftPlan& plan, cudaStream_t s);
@@ -59,6 +93,14 @@ cudaError_t launch_inv_rows(const FftPlan& plan, const float2* tw, const float2*
                             int64_t in_stride, int nfreq, float* out, int ncols,
                             int64_t out_stride, cudaStream_t s);
 // Y[w][k] = sum_r Rt[r][k] * X[w + center - r][k]  (zero or wrapped outside).
+// Batched forms: one launch over every unit (all units share plan, strides,
+// response shape and wire-convolution variant).
+cudaError_t launch_fwd_rows_batch(const FftPlan& plan, const float2* tw, const RowBatch& rb, int ncols,
+                                  int64_t in_stride, int64_t out_stride, int nfreq, float scale, cudaStream_t s);
+cudaError_t launch_inv_rows_batch(const FftPlan& plan, const float2* tw, const RowBatch& rb, int64_t in_stride,
+                                  int nfreq, int ncols, int64_t out_stride, cudaStream_t s);
+cudaError_t launch_wire_conv_batch(const ConvBatch& cb, int nfreq, int64_t stride, int kw, int center, int circular,
+                                   cudaStream_t s, int variant);
 // variant: 0 = 16 wires per thread, 1 = 16 Karatsuba, 2 = 8, 3 = 8 Karatsuba.
 constexpr int kWireConvVariants = 4;
 cudaError_t launch_wire_conv(const float2* X, float2* Y, const float2* Rt, int nwires,
@@ -69,7 +111,7 @@ cudaError_t launch_wire_conv(const float2* X, float2* Y, const float2* Rt, int n
 // raster kernel (workspace-resident; count and done must start at zero and
 // are reset by the second kernel).
 struct LargeList {
-    int* list;
+    long long* list;      // entries (unit << 40) | depo index
     unsigned* count;
     unsigned* done;
     unsigned cap;
@@ -84,6 +126,24 @@ cudaError_t launch_resp_grad(const float2* XG, const float2* XS, float2* A, int 
 
 // ---- raster / scatter launchers (raster.cu)
 cudaError_t launch_raster_scatter(const RasterArgs& a, float* grid, const LargeList& L, cudaStream_t s);
+// Batched raster: unit i rasterises a[i] into grid[i]; one launch pair for all.
+struct RasterBatch {
+    int n;
+    RasterArgs a[kMaxUnits];
+    float* grid[kMaxUnits];
+};
+struct RasterUnits {
+    int n;
+    long long gprefix[kMaxUnits + 1];   // cumulative 16-depo groups
+    long long dprefix[kMaxUnits + 1];   // cumulative depos
+    RasterArgs a[kMaxUnits];
+    float* grid[kMaxUnits];
+};
+struct ZeroSizes {
+    long long count[kMaxUnits];
+};
+cudaError_t launch_raster_scatter_batch(const RasterBatch& rb, const LargeList& L, cudaStream_t s);
+cudaError_t launch_zero_grids(const RasterBatch& rb, const int64_t* counts, cudaStream_t s);
 cudaError_t launch_patch_sizes(const RasterArgs& a, int64_t* sizes, unsigned long long* total,
                                cudaStream_t s);
 // Adjoint of the expected-value raster: per-depo dL/dq, dL/dx, dL/dt from

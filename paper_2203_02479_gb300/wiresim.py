@@ -32,7 +32,8 @@ EXPORTED = ("ws_plane_workspace_bytes", "ws_plane_create", "ws_plane_destroy", "
             "ws_patch_capacity", "ws_rasterize", "ws_scatter", "ws_convolve", "ws_simulate",
             "ws_plane_sync", "ws_plane_clear_status", "ws_plane_trace", "ws_plane_trace_read",
             "ws_convolve_noalloc", "ws_plane_set_wire_conv_variant", "ws_plane_set_response",
-            "ws_simulate_backward", "ws_status_string", "ws_last_error")
+            "ws_simulate_backward", "ws_batch_workspace_bytes", "ws_simulate_batch", "ws_status_string",
+            "ws_last_error")
 
 
 class WiresimError(RuntimeError):
@@ -119,6 +120,10 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
             "ws_convolve_noalloc": [ctypes.POINTER(WsPlaneDesc), P, P, P, P],
             "ws_plane_set_wire_conv_variant": [P, ctypes.c_int],
             "ws_plane_set_response": [P, P, P],
+            "ws_batch_workspace_bytes": [ctypes.POINTER(P), ctypes.c_int, ctypes.c_int,
+                                         ctypes.POINTER(ctypes.c_size_t)],
+            "ws_simulate_batch": [ctypes.POINTER(P), ctypes.c_int, ctypes.POINTER(WsDepos), ctypes.c_int,
+                                  ctypes.POINTER(WsParams), ctypes.POINTER(P), P, ctypes.c_size_t, ctypes.c_int, P],
             "ws_simulate_backward": [P, ctypes.POINTER(WsDepos), ctypes.POINTER(WsParams), P, P, P, P, P, P,
                                      P, P],
         }
@@ -408,3 +413,61 @@ class Plane:
 
     def clear_status(self, stream=None):
         ws_plane_clear_status(self.handle, _stream_handle(stream))
+
+
+class Batch:
+    """Many events x planes through ``ws_simulate_batch``.
+
+    ``events[e][p]`` are DeviceDepos of event e seen by plane p; outputs are
+    allocated per unit.  ``run()`` enqueues the batch; ``capture()`` records
+    it once into a CUDA graph that ``replay()`` relaunches (the buffers stay
+    fixed, so refill the depo tensors in place between replays)."""
+
+    def __init__(self, planes, events, params: Params, units_per_wave: int = 6, device="cuda"):
+        torch = _torch()
+        self.planes = list(planes)
+        self.events = events
+        self.params = params
+        self.units_per_wave = units_per_wave
+        self.nplanes = len(self.planes)
+        self.nevents = len(events)
+        P = ctypes.c_void_p
+        self._planes_c = (P * self.nplanes)(*[pl.handle for pl in self.planes])
+        units = [events[e][p] for e in range(self.nevents) for p in range(self.nplanes)]
+        self._depos_c = (WsDepos * len(units))(*[d.c() for d in units])
+        self.outs = [torch.empty((self.planes[u % self.nplanes].nwires, self.planes[u % self.nplanes].nticks),
+                                 dtype=torch.float32, device=device) for u in range(len(units))]
+        self._outs_c = (P * len(units))(*[o.data_ptr() for o in self.outs])
+        n = ctypes.c_size_t(0)
+        _check(load_library().ws_batch_workspace_bytes(self._planes_c, self.nplanes, units_per_wave,
+                                                        ctypes.byref(n)), "ws_batch_workspace_bytes")
+        self.workspace = torch.empty(int(n.value) + 256, dtype=torch.uint8, device=device)
+        self._ws_ptr = (self.workspace.data_ptr() + 255) & ~255
+        self._ws_bytes = int(n.value)
+        self._params_c = params.c()
+        self.graph = None
+
+    def run(self, stream=None):
+        _check(load_library().ws_simulate_batch(self._planes_c, self.nplanes, self._depos_c, self.nevents,
+                                                ctypes.byref(self._params_c), self._outs_c, self._ws_ptr,
+                                                self._ws_bytes, self.units_per_wave, _stream_handle(stream)),
+               "ws_simulate_batch")
+        return self.outs
+
+    def capture(self):
+        torch = _torch()
+        s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(s):
+            self.run(s)          # warm-up outside the graph (kernel attributes, lazy loading)
+        torch.cuda.current_stream().wait_stream(s)
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            self.run()
+        self.graph = g
+        return g
+
+    def replay(self):
+        self.graph.replay()
+        return self.outs
