@@ -233,6 +233,78 @@ def run_reference(args):
 
 
 # -------------------------------------------------------------------- main
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # 152 SMs x 128 FP32 lanes x FMA x max SM clock
+
+
+def algorithmic_flops(kernel: str, nw: int, nt: int, L: int, nfreq: int, kw: int) -> float:
+    """FP32 flops a kernel's step needs by the usual count, per launch on one
+    plane: 5 L log2 L per complex L-point FFT (two real rows per transform),
+    8 per complex multiply-add of the wire-axis sum."""
+    import math
+    if kernel in ("fwd_rows", "inv_rows"):
+        return (nw + 1) // 2 * 5.0 * L * math.log2(L)
+    if kernel == "wire_conv":
+        return 8.0 * kw * nfreq * nw
+    return 0.0
+
+
+def _time_steps(step, steps, stream, flush):
+    import torch
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    for i in range(steps):
+        flush.zero_()
+        starts[i].record(stream)
+        step()
+        ends[i].record(stream)
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) for a, b in zip(starts, ends)]
+
+
+def batched_workload_comparison(wiresim, dev, stream, flush, steps: int):
+    """64 events x 3 planes with log-uniform depo counts: the batched path
+    (one launch per stage per wave, replayed from a CUDA graph; wave size
+    picked by timing) against one ws_simulate call per (event, plane)."""
+    import torch
+    w = inputs.batched_events()
+    planes = [wiresim.Plane(sp.nwires, sp.nticks, sp.response, plane_id=sp.plane_id, device=dev) for sp in w.planes]
+    events = [[wiresim.DeviceDepos.from_plane_depos(d, device=dev) for d in ev] for ev in w.events]
+    params = wiresim.Params(fluctuate=w.fluctuate, p_survive=w.p_survive, seed=w.seed)
+    ndp = sum(d.n for ev in w.events for d in ev)
+    best = None
+    for upw in (3, 6, 12, 24):
+        b = wiresim.Batch(planes, events, params, units_per_wave=upw, device=dev)
+        b.run(stream)
+        torch.cuda.synchronize()
+        ms = sum(_time_steps(lambda: b.run(stream), 2, stream, flush)) / 2
+        if best is None or ms < best[0]:
+            best = (ms, upw, b)
+        else:
+            del b
+    _, upw, b = best
+    b.capture()
+    b.replay()
+    torch.cuda.synchronize()
+    graph_ms = _time_steps(b.replay, steps, stream, flush)
+    outs = [torch.empty((pl.nwires, pl.nticks), dtype=torch.float32, device=dev) for pl in planes]
+
+    def per_plane():
+        for e, ev in enumerate(events):
+            pe = wiresim.Params(**{**params.__dict__, "event_id": e})
+            for pl, d, o in zip(planes, ev, outs):
+                pl.simulate(d, pe, out=o, stream=stream)
+
+    per_plane()
+    torch.cuda.synchronize()
+    pp_ms = _time_steps(per_plane, steps, stream, flush)
+    g = sum(graph_ms) / len(graph_ms)
+    pp = sum(pp_ms) / len(pp_ms)
+    return {"workload": w.name, "events": len(w.events), "depo_planes": ndp,
+            "units_per_wave": upw, "batched_graph_depos_per_s": ndp / (g * 1e-3),
+            "per_plane_depos_per_s": ndp / (pp * 1e-3), "speedup": pp / g,
+            "batched_ms": g, "per_plane_ms": pp}
+
+
 def run_gpu(args):
     import torch
     from paper_2203_02479_gb300 import wiresim
@@ -248,56 +320,82 @@ def run_gpu(args):
     planes = [wiresim.Plane(sp.nwires, sp.nticks, sp.response, plane_id=sp.plane_id, device=dev)
               for sp in w.planes]
     depos = [wiresim.DeviceDepos.from_plane_depos(d, device=dev) for d in ev]
-    outs = [torch.empty((sp.nwires, sp.nticks), dtype=torch.float32, device=dev) for sp in w.planes]
     params = wiresim.Params(fluctuate=w.fluctuate, p_survive=w.p_survive, seed=w.seed, event_id=rank)
+    batch = wiresim.Batch(planes, [depos], params, units_per_wave=len(planes), device=dev)
+    outs = [torch.empty((sp.nwires, sp.nticks), dtype=torch.float32, device=dev) for sp in w.planes]
     ndepo_planes = sum(d.n for d in ev)
     stream = torch.cuda.current_stream(dev)
     flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device=dev)
 
     def step():
+        batch.run(stream)
+
+    def step_per_plane():
         for pl, dd, o in zip(planes, depos, outs):
             pl.simulate(dd, params, out=o, stream=stream)
 
     for _ in range(max(args.warmup, 0)):
         step()
+        step_per_plane()
     torch.cuda.synchronize(dev)
 
-    for pl in planes:
-        pl.trace(args.steps * 8 + 16)
+    # timed region: the batched path (all planes of the event per launch),
+    # with the library's launch trace on the stream
+    planes[0].trace(args.steps * 8 + 16)
     sampler = ClockSampler(local) if local == 0 else None
-    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     _barrier(dist)
     torch.cuda.synchronize(dev)
-    for i in range(args.steps):
-        flush.zero_()
-        starts[i].record(stream)
-        step()
-        ends[i].record(stream)
-    torch.cuda.synchronize(dev)
+    step_ms = _time_steps(step, args.steps, stream, flush)
     _barrier(dist)
     clocks = sampler.stop() if sampler else None
-    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
     total_ms = _max_over_ranks(dist, float(sum(step_ms)), dev)
+    stats = planes[0].trace_read()
+    planes[0].trace(0)
 
-    # per-kernel device times from the launch trace over the timed steps
-    kern = {}
-    kbytes = {}
-    for pl, sp, d in zip(planes, w.planes, ev):
-        stats = pl.trace_read()
-        pl.trace(0)
-        for name, (n, ms) in stats.items():
-            a = kern.setdefault(name, [0, 0.0])
-            a[0] += n
-            a[1] += ms
-            kbytes[name] = kbytes.get(name, 0.0) + n * algorithmic_bytes(
-                name, sp.nwires, sp.nticks, pl.info.nfreq, sp.response.shape[0], d.n)
-    launches = sum(n for name, (n, _) in kern.items() if name != "memset_grid")
-    dominant = max((k for k in kern if k != "memset_grid"), key=lambda k: kern[k][1])
+    # per-kernel algorithmic work (sum over the event's planes per launch)
+    kern = {name: [n, ms] for name, (n, ms) in stats.items()}
+    # each traced raster_scatter entry is two kernels (lane-pair + large-patch)
+    launches = sum(n * (2 if name == "raster_scatter" else 1) for name, (n, _) in kern.items())
+    per_launch_bytes, per_launch_flops = {}, {}
+    for name in kern:
+        per_launch_bytes[name] = sum(algorithmic_bytes(name, sp.nwires, sp.nticks, pl.info.nfreq,
+                                                       sp.response.shape[0], d.n)
+                                     for pl, sp, d in zip(planes, w.planes, ev))
+        per_launch_flops[name] = sum(algorithmic_flops(name, sp.nwires, sp.nticks, pl.info.fft_len_tick,
+                                                       pl.info.nfreq, sp.response.shape[0])
+                                     for pl, sp in zip(planes, w.planes))
+    dominant = max(kern, key=lambda k: kern[k][1])
     dn, dms = kern[dominant]
+    avg_s = dms / dn * 1e-3
     peak_gbs, sm_max, peak_src = _peaks()
-    achieved = kbytes[dominant] / dn / (dms / dn * 1e-3) / 1e9
-    raster_ms = kern.get("raster_scatter", [0, 0.0])[1] + kern.get("memset_grid", [0, 0.0])[1]
+    bw = per_launch_bytes[dominant] / avg_s / 1e9
+    fl = per_launch_flops[dominant] / avg_s / 1e12
+    t_hbm = per_launch_bytes[dominant] / (peak_gbs * 1e9)
+    t_alu = per_launch_flops[dominant] / (FP32_PEAK_TFLOPS * 1e12)
+    if t_alu > t_hbm:
+        roof = {"kernel": dominant, "bound": "alu", "achieved": fl, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": fl / FP32_PEAK_TFLOPS, "traffic": None,
+                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz",
+                "hbm_frac_of_measured": bw / peak_gbs}
+    else:
+        roof = {"kernel": dominant, "bound": "hbm", "achieved": bw, "peak": peak_gbs, "unit": "GB/s",
+                "frac": bw / peak_gbs, "traffic": None, "peak_source": f"{peak_src} hbm_gbs",
+                "alu_frac_of_derived": fl / FP32_PEAK_TFLOPS}
+    kernels = {}
+    for name, (n, ms) in sorted(kern.items()):
+        a = ms / n * 1e-3
+        kernels[name] = {"ms_per_step": ms / args.steps, "launches_per_step": n / args.steps,
+                         "hbm_gbs": per_launch_bytes[name] / a / 1e9,
+                         "hbm_frac": per_launch_bytes[name] / a / 1e9 / peak_gbs,
+                         "fp32_tflops": per_launch_flops[name] / a / 1e12,
+                         "fp32_frac": per_launch_flops[name] / a / 1e12 / FP32_PEAK_TFLOPS}
+
+    # the same event one plane at a time, and replayed from a CUDA graph
+    pp_ms = _time_steps(step_per_plane, args.steps, stream, flush)
+    batch.capture()
+    batch.replay()
+    torch.cuda.synchronize(dev)
+    graph_ms = _time_steps(batch.replay, args.steps, stream, flush)
 
     # end to end through the public API with host buffers
     e2e = None
@@ -306,14 +404,16 @@ def run_gpu(args):
         host_out = [torch.empty((sp.nwires, sp.nticks), dtype=torch.float32).pin_memory() for sp in w.planes]
         dev_in = [[torch.empty_like(a, device=dev) for a in trip] for trip in host_in]
         dd_e2e = [wiresim.DeviceDepos(*trip, device=dev) for trip in dev_in]
+        b2 = wiresim.Batch(planes, [dd_e2e], params, units_per_wave=len(planes), device=dev)
         h2d = sum(a.numel() * 4 for trip in host_in for a in trip)
         d2h = sum(o.numel() * 4 for o in host_out)
 
         def e2e_step():
-            for trip_h, trip_d, dd, pl, o, oh in zip(host_in, dev_in, dd_e2e, planes, outs, host_out):
+            for trip_h, trip_d in zip(host_in, dev_in):
                 for a_h, a_d in zip(trip_h, trip_d):
                     a_d.copy_(a_h, non_blocking=True)
-                pl.simulate(dd, params, out=o, stream=stream)
+            b2.run(stream)
+            for o, oh in zip(b2.outs, host_out):
                 oh.copy_(o, non_blocking=True)
 
         for _ in range(max(args.warmup, 1)):
@@ -337,16 +437,22 @@ def run_gpu(args):
 
     all_depos = _sum_over_ranks(dist, float(ndepo_planes * args.steps), dev)
     all_planes = _sum_over_ranks(dist, float(len(planes) * args.steps), dev)
+    batched = None
+    if rank == 0 and world == 1 and not args.no_batched_workload:
+        batched = batched_workload_comparison(wiresim, dev, stream, flush, max(3, min(args.steps, 10)))
     if rank != 0:
         if dist is not None:
             dist.destroy_process_group()
         return
     value = all_depos / (total_ms * 1e-3)
+    raster_ms = kern.get("raster_scatter", [0, 0.0])[1] + kern.get("memset_grid", [0, 0.0])[1]
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
         done, secs, nplanes = oracle_sample(w, args.cpu_seconds)
         cpu = {"value": done / secs, "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": f"{nplanes} planes of this event ({done} depo-planes), FP64, single thread"}
+    pp = sum(pp_ms) / len(pp_ms)
+    gr = sum(graph_ms) / len(graph_ms)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
@@ -356,17 +462,19 @@ def run_gpu(args):
                    "fluctuate": w.fluctuate, "p_survive": w.p_survive,
                    "fft_len_tick": planes[0].info.fft_len_tick,
                    "wire_conv_variant": [pl.info.wire_conv_variant for pl in planes],
+                   "path": "ws_simulate_batch over the event's planes (one launch per stage)",
                    "l2": "flushed between timed steps (512 MiB write)"},
         "planes_per_s": all_planes / (total_ms * 1e-3),
         "raster_scatter_depos_per_s": all_depos / (raster_ms * 1e-3) if raster_ms > 0 else None,
-        "kernels_ms_per_step": {k: v[1] / args.steps for k, v in sorted(kern.items())},
-        "roofline": {"kernel": dominant, "bound": "hbm", "achieved": achieved, "peak": peak_gbs,
-                     "unit": "GB/s", "frac": achieved / peak_gbs, "traffic": None,
-                     "peak_source": f"{peak_src} hbm_gbs"},
+        "per_plane_path": {"ms_per_step": pp, "value": ndepo_planes / (pp * 1e-3)},
+        "graph_replay": {"ms_per_step": gr, "value": ndepo_planes / (gr * 1e-3)},
+        "kernels": kernels,
+        "roofline": roof,
         "gpu_launches": launches,
         "clocks": clocks,
         "e2e": e2e,
         "cpu_baseline": cpu,
+        "batched_workload": batched,
     }
     print(json.dumps(line), flush=True)
     if dist is not None:
@@ -382,6 +490,7 @@ def main():
     ap.add_argument("--workload", default="three_planes", choices=["three_planes", "single_plane"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batched-workload", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "wiresim":
