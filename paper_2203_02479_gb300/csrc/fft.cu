@@ -67,69 +67,82 @@ __host__ __device__ constexpr double cx_trig2pi(long m, long n, bool want_sin) {
     return want_sin ? ss : cc;
 }
 
-__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
-__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
-__device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+// Complex arithmetic on float2 (FP32 path) or double2 (FP64 path).
+template <typename S> struct CplxOf;
+template <> struct CplxOf<float> { using type = float2; };
+template <> struct CplxOf<double> { using type = double2; };
+template <typename S> using cplx = typename CplxOf<S>::type;
+
+__device__ __forceinline__ float2 mkc(float a, float b) { return make_float2(a, b); }
+__device__ __forceinline__ double2 mkc(double a, double b) { return make_double2(a, b); }
+__device__ __forceinline__ float fmx(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ double fmx(double a, double b, double c) { return fma(a, b, c); }
+
+template <typename C> __device__ __forceinline__ C cadd(C a, C b) { return mkc(a.x + b.x, a.y + b.y); }
+template <typename C> __device__ __forceinline__ C csub(C a, C b) { return mkc(a.x - b.x, a.y - b.y); }
+template <typename C, typename S> __device__ __forceinline__ C cscale(C a, S s) { return mkc(a.x * s, a.y * s); }
 // a * w (forward) or a * conj(w) (inverse)
-template <bool INV>
-__device__ __forceinline__ float2 cmul_tw(float2 a, float2 w) {
+template <bool INV, typename C>
+__device__ __forceinline__ C cmul_tw(C a, C w) {
     if (INV) w.y = -w.y;
-    return make_float2(fmaf(a.x, w.x, -a.y * w.y), fmaf(a.x, w.y, a.y * w.x));
+    return mkc(fmx(a.x, w.x, -a.y * w.y), fmx(a.x, w.y, a.y * w.x));
 }
 // -i*a (forward) or +i*a (inverse)
-template <bool INV>
-__device__ __forceinline__ float2 mul_mi(float2 a) {
-    return INV ? make_float2(-a.y, a.x) : make_float2(a.y, -a.x);
+template <bool INV, typename C>
+__device__ __forceinline__ C mul_mi(C a) {
+    return INV ? mkc(-a.y, a.x) : mkc(a.y, -a.x);
 }
 
 // x * e^{-+2 pi i M / N} with M, N compile-time.
-template <int N, int M, bool INV>
-__device__ __forceinline__ float2 rot(float2 x) {
+template <int N, int M, bool INV, typename C>
+__device__ __forceinline__ C rot(C x) {
+    using S = decltype(x.x);
     constexpr int m = M % N;
     if constexpr (m == 0) {
         return x;
     } else if constexpr (2 * m == N) {
-        return make_float2(-x.x, -x.y);
+        return mkc(-x.x, -x.y);
     } else if constexpr (4 * m == N) {
         return mul_mi<INV>(x);
     } else if constexpr (4 * m == 3 * N) {
         return mul_mi<!INV>(x);
     } else {
-        constexpr float c = (float)cx_trig2pi(m, N, false);
-        constexpr float s = INV ? (float)cx_trig2pi(m, N, true) : -(float)cx_trig2pi(m, N, true);
-        return make_float2(fmaf(x.x, c, -x.y * s), fmaf(x.x, s, x.y * c));
+        constexpr S c = (S)cx_trig2pi(m, N, false);
+        constexpr S s = INV ? (S)cx_trig2pi(m, N, true) : -(S)cx_trig2pi(m, N, true);
+        return mkc(fmx(x.x, c, -x.y * s), fmx(x.x, s, x.y * c));
     }
 }
 
 // ------------------------------------------------------------ small DFTs
 // y_m = sum_n x_n e^{-+2 pi i m n / R}, in place, natural order.
-template <int R, bool INV> struct Dft;
+template <int R, bool INV, typename C> struct Dft;
 
-template <bool INV> struct Dft<2, INV> {
-    __device__ __forceinline__ static void run(float2* v) {
-        float2 a = v[0], b = v[1];
+template <bool INV, typename C> struct Dft<2, INV, C> {
+    __device__ __forceinline__ static void run(C* v) {
+        C a = v[0], b = v[1];
         v[0] = cadd(a, b);
         v[1] = csub(a, b);
     }
 };
 
-template <bool INV> struct Dft<3, INV> {
-    __device__ __forceinline__ static void run(float2* v) {
-        const float s3 = 0.866025403784438647f;  // sin(2 pi / 3)
-        float2 t1 = cadd(v[1], v[2]);
-        float2 t2 = csub(v[1], v[2]);
-        float2 a = make_float2(fmaf(-0.5f, t1.x, v[0].x), fmaf(-0.5f, t1.y, v[0].y));
-        float2 b = mul_mi<INV>(cscale(t2, s3));
+template <bool INV, typename C> struct Dft<3, INV, C> {
+    __device__ __forceinline__ static void run(C* v) {
+        using S = decltype(v[0].x);
+        const S s3 = (S)0.866025403784438646763723170752936183;  // sin(2 pi / 3)
+        C t1 = cadd(v[1], v[2]);
+        C t2 = csub(v[1], v[2]);
+        C a = mkc(fmx((S)-0.5, t1.x, v[0].x), fmx((S)-0.5, t1.y, v[0].y));
+        C b = mul_mi<INV>(cscale(t2, s3));
         v[0] = cadd(v[0], t1);
         v[1] = cadd(a, b);
         v[2] = csub(a, b);
     }
 };
 
-template <bool INV> struct Dft<4, INV> {
-    __device__ __forceinline__ static void run(float2* v) {
-        float2 s02 = cadd(v[0], v[2]), d02 = csub(v[0], v[2]);
-        float2 s13 = cadd(v[1], v[3]), d13 = mul_mi<INV>(csub(v[1], v[3]));
+template <bool INV, typename C> struct Dft<4, INV, C> {
+    __device__ __forceinline__ static void run(C* v) {
+        C s02 = cadd(v[0], v[2]), d02 = csub(v[0], v[2]);
+        C s13 = cadd(v[1], v[3]), d13 = mul_mi<INV>(csub(v[1], v[3]));
         v[0] = cadd(s02, s13);
         v[2] = csub(s02, s13);
         v[1] = cadd(d02, d13);
@@ -137,19 +150,20 @@ template <bool INV> struct Dft<4, INV> {
     }
 };
 
-template <bool INV> struct Dft<5, INV> {
-    __device__ __forceinline__ static void run(float2* v) {
-        const float c1 = 0.309016994374947424f;   // cos(2 pi / 5)
-        const float c2 = -0.809016994374947424f;  // cos(4 pi / 5)
-        const float s1 = 0.951056516295153572f;   // sin(2 pi / 5)
-        const float s2 = 0.587785252292473129f;   // sin(4 pi / 5)
-        float2 t1 = cadd(v[1], v[4]), t3 = csub(v[1], v[4]);
-        float2 t2 = cadd(v[2], v[3]), t4 = csub(v[2], v[3]);
-        float2 x0 = v[0];
-        float2 a1 = make_float2(fmaf(c1, t1.x, fmaf(c2, t2.x, x0.x)), fmaf(c1, t1.y, fmaf(c2, t2.y, x0.y)));
-        float2 a2 = make_float2(fmaf(c2, t1.x, fmaf(c1, t2.x, x0.x)), fmaf(c2, t1.y, fmaf(c1, t2.y, x0.y)));
-        float2 b1 = make_float2(fmaf(s1, t3.x, s2 * t4.x), fmaf(s1, t3.y, s2 * t4.y));
-        float2 b2 = make_float2(fmaf(s2, t3.x, -s1 * t4.x), fmaf(s2, t3.y, -s1 * t4.y));
+template <bool INV, typename C> struct Dft<5, INV, C> {
+    __device__ __forceinline__ static void run(C* v) {
+        using S = decltype(v[0].x);
+        const S c1 = (S)0.309016994374947424102293417182819059;   // cos(2 pi / 5)
+        const S c2 = (S)-0.809016994374947424102293417182819059;  // cos(4 pi / 5)
+        const S s1 = (S)0.951056516295153572116439333379382143;   // sin(2 pi / 5)
+        const S s2 = (S)0.587785252292473129168705954639072769;   // sin(4 pi / 5)
+        C t1 = cadd(v[1], v[4]), t3 = csub(v[1], v[4]);
+        C t2 = cadd(v[2], v[3]), t4 = csub(v[2], v[3]);
+        C x0 = v[0];
+        C a1 = mkc(fmx(c1, t1.x, fmx(c2, t2.x, x0.x)), fmx(c1, t1.y, fmx(c2, t2.y, x0.y)));
+        C a2 = mkc(fmx(c2, t1.x, fmx(c1, t2.x, x0.x)), fmx(c2, t1.y, fmx(c1, t2.y, x0.y)));
+        C b1 = mkc(fmx(s1, t3.x, s2 * t4.x), fmx(s1, t3.y, s2 * t4.y));
+        C b2 = mkc(fmx(s2, t3.x, -s1 * t4.x), fmx(s2, t3.y, -s1 * t4.y));
         b1 = mul_mi<INV>(b1);
         b2 = mul_mi<INV>(b2);
         v[0] = cadd(x0, cadd(t1, t2));
@@ -162,33 +176,33 @@ template <bool INV> struct Dft<5, INV> {
 
 // Composite N = N1 N2 (Cooley-Tukey in registers): with n = N2 n1 + n2 and
 // k = k1 + N1 k2, X[k] = sum_n2 W_N2^(n2 k2) W_N^(n2 k1) sum_n1 x[n] W_N1^(n1 k1).
-template <int N1, int N2, bool INV>
-__device__ __forceinline__ void dft_composite(float2* v) {
+template <int N1, int N2, bool INV, typename C>
+__device__ __forceinline__ void dft_composite(C* v) {
     constexpr int N = N1 * N2;
     sfor<N2>([&](auto n2c) {
         constexpr int n2 = decltype(n2c)::value;
-        float2 t[N1];
+        C t[N1];
         sfor<N1>([&](auto n1c) { t[decltype(n1c)::value] = v[N2 * decltype(n1c)::value + n2]; });
-        Dft<N1, INV>::run(t);
+        Dft<N1, INV, C>::run(t);
         sfor<N1>([&](auto k1c) {
             constexpr int k1 = decltype(k1c)::value;
             v[N2 * k1 + n2] = rot<N, n2 * k1, INV>(t[k1]);
         });
     });
-    float2 out[N];
+    C out[N];
     sfor<N1>([&](auto k1c) {
         constexpr int k1 = decltype(k1c)::value;
-        float2 t[N2];
+        C t[N2];
         sfor<N2>([&](auto n2c) { t[decltype(n2c)::value] = v[N2 * k1 + decltype(n2c)::value]; });
-        Dft<N2, INV>::run(t);
+        Dft<N2, INV, C>::run(t);
         sfor<N2>([&](auto k2c) { out[k1 + N1 * decltype(k2c)::value] = t[decltype(k2c)::value]; });
     });
     sfor<N>([&](auto ic) { v[decltype(ic)::value] = out[decltype(ic)::value]; });
 }
 
-#define WS_COMPOSITE(R, A, B)                                                          \
-    template <bool INV> struct Dft<R, INV> {                                            \
-        __device__ __forceinline__ static void run(float2* v) { dft_composite<A, B, INV>(v); } \
+#define WS_COMPOSITE(R, A, B)                                                             \
+    template <bool INV, typename C> struct Dft<R, INV, C> {                                \
+        __device__ __forceinline__ static void run(C* v) { dft_composite<A, B, INV>(v); } \
     };
 WS_COMPOSITE(6, 3, 2)
 WS_COMPOSITE(8, 4, 2)
@@ -219,25 +233,25 @@ __device__ __forceinline__ int find_unit(const int* prefix, int n, int b) {
 // (Ns R)} (w from the pass's table of Ns base twiddles, its powers by a
 // multiply tree of depth <= 5), and writes dst[(j - j mod Ns) R + j mod Ns +
 // r Ns].
-template <int R, bool INV>
-__device__ __forceinline__ void stockham_pass(const float2* __restrict__ src, float2* __restrict__ dst,
-                                              int L, int Ns, const float2* __restrict__ tw) {
+template <int R, bool INV, typename C>
+__device__ __forceinline__ void stockham_pass(const C* __restrict__ src, C* __restrict__ dst,
+                                              int L, int Ns, const C* __restrict__ tw) {
     const int nb = L / R;
     for (int j = threadIdx.x; j < nb; j += kRowThreads) {
         const int k = j % Ns;
-        float2 v[R];
+        C v[R];
 #pragma unroll
         for (int r = 0; r < R; ++r) v[r] = src[j + r * nb];
         if (Ns > 1) {
-            float2 wp[R];
-            wp[1] = __ldg(&tw[k]);
+            C wp[R];
+            wp[1] = tw[k];
             if (INV) wp[1].y = -wp[1].y;
 #pragma unroll
             for (int r = 2; r < R; ++r) wp[r] = cmul_tw<false>(wp[r / 2], wp[r - r / 2]);
 #pragma unroll
             for (int r = 1; r < R; ++r) v[r] = cmul_tw<false>(v[r], wp[r]);
         }
-        Dft<R, INV>::run(v);
+        Dft<R, INV, C>::run(v);
         const int d = (j - k) * R + k;
 #pragma unroll
         for (int r = 0; r < R; ++r) dst[d + r * Ns] = v[r];
@@ -245,13 +259,13 @@ __device__ __forceinline__ void stockham_pass(const float2* __restrict__ src, fl
 }
 
 // Full transform in shared memory; returns the buffer holding the result.
-template <bool INV>
-__device__ float2* fft_smem(const FftPlan& plan, float2* a, float2* b, const float2* __restrict__ tw) {
-    float2* src = a;
-    float2* dst = b;
+template <bool INV, typename C>
+__device__ C* fft_smem(const FftPlan& plan, C* a, C* b, const C* __restrict__ tw) {
+    C* src = a;
+    C* dst = b;
     for (int p = 0; p < plan.npass; ++p) {
         const int Ns = plan.ns[p];
-        const float2* t = tw + plan.twoff[p];
+        const C* t = tw + plan.twoff[p];
         switch (plan.radix[p]) {
             case 2: stockham_pass<2, INV>(src, dst, plan.L, Ns, t); break;
             case 3: stockham_pass<3, INV>(src, dst, plan.L, Ns, t); break;
@@ -268,42 +282,49 @@ __device__ float2* fft_smem(const FftPlan& plan, float2* a, float2* b, const flo
             default: stockham_pass<25, INV>(src, dst, plan.L, Ns, t); break;
         }
         __syncthreads();
-        float2* tmp = src; src = dst; dst = tmp;
+        C* tmp = src; src = dst; dst = tmp;
     }
     return src;
 }
 
 // Pass twiddles: for pass p, tw[twoff[p] + k] = e^{-2 pi i k / (Ns R)}, k < Ns.
-__global__ void pass_twiddles_kernel(float2* tw, FftPlan plan) {
+template <typename C>
+__global__ void pass_twiddles_kernel(C* tw, FftPlan plan) {
     for (int p = 0; p < plan.npass; ++p) {
         const int Ns = plan.ns[p], R = plan.radix[p];
         for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < Ns; k += gridDim.x * blockDim.x) {
             double s, c;
             sincospi(-2.0 * (double)k / (double)((long long)Ns * R), &s, &c);
-            tw[plan.twoff[p] + k] = make_float2((float)c, (float)s);
+            tw[plan.twoff[p] + k] = mkc((decltype(tw[0].x))c, (decltype(tw[0].x))s);
         }
     }
 }
 
-// Two real rows (2 blockIdx.x, 2 blockIdx.x + 1) as one complex transform
-// z = a + i b; then A_k = (Z_k + conj Z_{L-k}) / 2, B_k = (Z_k - conj Z_{L-k}) / 2i.
-__global__ void __launch_bounds__(kRowThreads, 2)
-fwd_rows_kernel(FftPlan plan, const float2* __restrict__ tw, const __grid_constant__ RowUnits U, int ncols,
+// Two real rows of unit u as one complex transform z = a + i b, then
+// A_k = (Z_k + conj Z_{L-k}) / 2, B_k = (Z_k - conj Z_{L-k}) / 2i.  Input rows
+// are TIN (float, or double for the FP64 path); with U.in2 set (float
+// inputs) a row is in + in2 (the compensated hi + lo pair).
+template <typename S, typename TIN>
+__global__ void __launch_bounds__(kRowThreads, sizeof(S) == 4 ? 2 : 1)
+fwd_rows_kernel(FftPlan plan, const cplx<S>* __restrict__ tw, const __grid_constant__ RowUnits U, int ncols,
                 int64_t in_stride, int64_t out_stride, int nfreq, float scale, int vec4) {
-    extern __shared__ __align__(16) float2 smem[];
+    using C = cplx<S>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* smem = reinterpret_cast<C*>(smem_raw);
     const int L = plan.L;
-    float2* a = smem;
-    float2* b = smem + ((L + 1) & ~1);  // both buffers 16-byte aligned
+    C* a = smem;
+    C* b = smem + ((L + 1) & ~1);  // both buffers 16-byte aligned
     const int u = find_unit(U.prefix, U.n, (int)blockIdx.x);
-    const float* __restrict__ in = static_cast<const float*>(U.in[u]);
-    float2* __restrict__ out = static_cast<float2*>(U.out[u]);
+    const TIN* __restrict__ in = static_cast<const TIN*>(U.in[u]);
+    const float* __restrict__ in2 = static_cast<const float*>(U.in2[u]);
+    C* __restrict__ out = static_cast<C*>(U.out[u]);
     const int nrows = U.nrows[u];
     const int r0 = 2 * ((int)blockIdx.x - U.prefix[u]);
     const bool has_b = r0 + 1 < nrows;
-    const float* pa = in + (int64_t)r0 * in_stride;
-    const float* pb = has_b ? pa + in_stride : pa;
+    const TIN* pa = in + (int64_t)r0 * in_stride;
+    const TIN* pb = has_b ? pa + in_stride : pa;
     const int nload = ncols < L ? ncols : L;
-    if (vec4) {
+    if (std::is_same<S, float>::value && std::is_same<TIN, float>::value && vec4 && !in2) {
         // rows are 16-byte aligned and nload % 4 == 0
         const float4* qa = reinterpret_cast<const float4*>(pa);
         const float4* qb = reinterpret_cast<const float4*>(pb);
@@ -315,74 +336,84 @@ fwd_rows_kernel(FftPlan plan, const float2* __restrict__ tw, const __grid_consta
             a4[2 * n4] = make_float4(xa.x, xb.x, xa.y, xb.y);
             a4[2 * n4 + 1] = make_float4(xa.z, xb.z, xa.w, xb.w);
         }
-        for (int n = nload + threadIdx.x; n < L; n += kRowThreads) a[n] = make_float2(0.f, 0.f);
+        for (int n = nload + threadIdx.x; n < L; n += kRowThreads) a[n] = mkc((S)0, (S)0);
     } else {
+        const float* la = in2 ? in2 + (int64_t)r0 * in_stride : nullptr;
+        const float* lb = (in2 && has_b) ? la + in_stride : la;
         for (int n = threadIdx.x; n < L; n += kRowThreads) {
-            float xa = 0.f, xb = 0.f;
+            S xa = 0, xb = 0;
             if (n < nload) {
-                xa = __ldg(pa + n);
-                if (has_b) xb = __ldg(pb + n);
+                xa = (S)pa[n];
+                if (has_b) xb = (S)pb[n];
+                if (in2) {
+                    xa += (S)la[n];
+                    if (has_b) xb += (S)lb[n];
+                }
             }
-            a[n] = make_float2(xa, xb);
+            a[n] = mkc(xa, xb);
         }
     }
     __syncthreads();
-    const float2* z = fft_smem<false>(plan, a, b, tw);
-    float2* oa = out + (int64_t)r0 * out_stride;
-    float2* ob = oa + out_stride;
-    const float h = 0.5f * scale;
+    const C* z = fft_smem<false>(plan, a, b, tw);
+    C* oa = out + (int64_t)r0 * out_stride;
+    C* ob = oa + out_stride;
+    const S h = (S)0.5 * (S)scale;
     for (int k = threadIdx.x; k < nfreq; k += kRowThreads) {
-        const float2 zk = z[k];
-        const float2 zm = z[k == 0 ? 0 : L - k];
-        oa[k] = make_float2(h * (zk.x + zm.x), h * (zk.y - zm.y));
-        if (has_b) ob[k] = make_float2(h * (zk.y + zm.y), h * (zm.x - zk.x));
+        const C zk = z[k];
+        const C zm = z[k == 0 ? 0 : L - k];
+        oa[k] = mkc(h * (zk.x + zm.x), h * (zk.y - zm.y));
+        if (has_b) ob[k] = mkc(h * (zk.y + zm.y), h * (zm.x - zk.x));
     }
 }
 
 // Two half spectra A (row r0) and B (row r0+1) -> Z = A + iB over the full
-// Hermitian extension, inverse transform, real part row r0, imaginary r0+1.
-__global__ void __launch_bounds__(kRowThreads, 2)
-inv_rows_kernel(FftPlan plan, const float2* __restrict__ tw, const __grid_constant__ RowUnits U,
+// Hermitian extension, inverse transform, real part row r0, imaginary r0+1,
+// stored as float.
+template <typename S>
+__global__ void __launch_bounds__(kRowThreads, sizeof(S) == 4 ? 2 : 1)
+inv_rows_kernel(FftPlan plan, const cplx<S>* __restrict__ tw, const __grid_constant__ RowUnits U,
                 int64_t in_stride, int nfreq, int ncols, int64_t out_stride, int vec4) {
-    extern __shared__ __align__(16) float2 smem[];
+    using C = cplx<S>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* smem = reinterpret_cast<C*>(smem_raw);
     const int L = plan.L;
-    float2* a = smem;
-    float2* b = smem + ((L + 1) & ~1);  // both buffers 16-byte aligned
+    C* a = smem;
+    C* b = smem + ((L + 1) & ~1);  // both buffers 16-byte aligned
     const int u = find_unit(U.prefix, U.n, (int)blockIdx.x);
-    const float2* __restrict__ in = static_cast<const float2*>(U.in[u]);
+    const C* __restrict__ in = static_cast<const C*>(U.in[u]);
     float* __restrict__ out = static_cast<float*>(U.out[u]);
     const int nrows = U.nrows[u];
     const int r0 = 2 * ((int)blockIdx.x - U.prefix[u]);
     const bool has_b = r0 + 1 < nrows;
-    const float2* ya = in + (int64_t)r0 * in_stride;
-    const float2* yb = has_b ? ya + in_stride : ya;
+    const C* ya = in + (int64_t)r0 * in_stride;
+    const C* yb = has_b ? ya + in_stride : ya;
     const bool even = (L & 1) == 0;
     for (int k = threadIdx.x; k < L; k += kRowThreads) {
         const bool upper = k >= nfreq;
         const int kk = upper ? L - k : k;
-        float2 A = __ldg(ya + kk);
-        float2 B = has_b ? __ldg(yb + kk) : make_float2(0.f, 0.f);
-        if (kk == 0 || (even && 2 * kk == L)) { A.y = 0.f; B.y = 0.f; }
+        C A = ya[kk];
+        C B = has_b ? yb[kk] : mkc((S)0, (S)0);
+        if (kk == 0 || (even && 2 * kk == L)) { A.y = 0; B.y = 0; }
         if (upper) { A.y = -A.y; B.y = -B.y; }
-        a[k] = make_float2(A.x - B.y, A.y + B.x);
+        a[k] = mkc(A.x - B.y, A.y + B.x);
     }
     __syncthreads();
-    const float2* z = fft_smem<true>(plan, a, b, tw);
+    const C* z = fft_smem<true>(plan, a, b, tw);
     float* oa = out + (int64_t)r0 * out_stride;
     float* ob = oa + out_stride;
     const int nst = ncols < L ? ncols : L;
-    if (vec4) {
+    if (std::is_same<S, float>::value && vec4) {
         const float4* z4 = reinterpret_cast<const float4*>(z);
         for (int n4 = threadIdx.x; n4 < nst / 4; n4 += kRowThreads) {
-            const float4 u = z4[2 * n4], w = z4[2 * n4 + 1];
-            reinterpret_cast<float4*>(oa)[n4] = make_float4(u.x, u.z, w.x, w.z);
-            if (has_b) reinterpret_cast<float4*>(ob)[n4] = make_float4(u.y, u.w, w.y, w.w);
+            const float4 u4 = z4[2 * n4], w4 = z4[2 * n4 + 1];
+            reinterpret_cast<float4*>(oa)[n4] = make_float4(u4.x, u4.z, w4.x, w4.z);
+            if (has_b) reinterpret_cast<float4*>(ob)[n4] = make_float4(u4.y, u4.w, w4.y, w4.w);
         }
     } else {
         for (int n = threadIdx.x; n < nst; n += kRowThreads) {
-            const float2 v = z[n];
-            oa[n] = v.x;
-            if (has_b) ob[n] = v.y;
+            const C v = z[n];
+            oa[n] = (float)v.x;
+            if (has_b) ob[n] = (float)v.y;
         }
     }
 }
@@ -397,23 +428,25 @@ constexpr int kConvCols = 128;
 // KARATSUBA: with r = c + i d (tap) and x = a + i b (input), r x =
 // [c (a + b) - b (c + d)] + i [c (a + b) + a (d - c)]: three real products
 // per tap into three accumulators instead of four.
-template <int K, int B, bool KARATSUBA>
+template <int K, int B, bool KARATSUBA, typename S>
 __global__ void __launch_bounds__(kConvCols)
 wire_conv_kernel(const __grid_constant__ ConvUnits U, int nfreq, int64_t stride, int kw, int center, int circular) {
+    using C = cplx<S>;
     constexpr int ROWS = B + K - 1;
-    __shared__ float4 tile[ROWS][kConvCols / 2];
+    __shared__ __align__(16) C tile[ROWS][kConvCols];
     const int u = find_unit(U.prefix, U.n, (int)blockIdx.y);
-    const float2* __restrict__ X = U.X[u];
-    float2* __restrict__ Y = U.Y[u];
-    const float2* __restrict__ Rt = U.Rt[u];
+    const C* __restrict__ X = static_cast<const C*>(U.X[u]);
+    C* __restrict__ Y = static_cast<C*>(U.Y[u]);
+    const C* __restrict__ Rt = static_cast<const C*>(U.Rt[u]);
     const int nwires = U.nwires[u];
     const int k0 = blockIdx.x * kConvCols;
     const int w0 = ((int)blockIdx.y - U.prefix[u]) * B;
     const int ibase = w0 + center - (K - 1);
-    for (int e = threadIdx.x; e < ROWS * (kConvCols / 2); e += kConvCols) {
-        const int u = e / (kConvCols / 2), c2 = e - u * (kConvCols / 2);
-        int i = ibase + u;
-        const int kk = k0 + 2 * c2;
+    constexpr int PER = std::is_same<S, float>::value ? 2 : 1;   // complex values per 16-byte load
+    for (int e = threadIdx.x; e < ROWS * (kConvCols / PER); e += kConvCols) {
+        const int uu = e / (kConvCols / PER), c2 = e - uu * (kConvCols / PER);
+        int i = ibase + uu;
+        const int kk = k0 + PER * c2;
         bool ok = kk < stride;
         if (circular) {
             i %= nwires;
@@ -421,59 +454,64 @@ wire_conv_kernel(const __grid_constant__ ConvUnits U, int nfreq, int64_t stride,
         } else {
             ok = ok && i >= 0 && i < nwires;
         }
-        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (ok) v = __ldg(reinterpret_cast<const float4*>(X + (int64_t)i * stride + kk));
-        tile[u][c2] = v;
+        if constexpr (PER == 2) {
+            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (ok) v = __ldg(reinterpret_cast<const float4*>(X + (int64_t)i * stride + kk));
+            reinterpret_cast<float4*>(&tile[uu][0])[c2] = v;
+        } else {
+            C v = mkc((S)0, (S)0);
+            if (ok) v = X[(int64_t)i * stride + kk];
+            tile[uu][c2] = v;
+        }
     }
     __syncthreads();
     const int k = k0 + threadIdx.x;
     if (k >= nfreq) return;
-    const float2* col = reinterpret_cast<const float2*>(&tile[0][0]) + threadIdx.x;
     if constexpr (KARATSUBA) {
-        float cc[K], cm[K], cp[K];   // c, d - c, c + d
+        S cc[K], cm[K], cp[K];   // c, d - c, c + d
 #pragma unroll
         for (int r = 0; r < K; ++r) {
-            const float2 t = r < kw ? __ldg(&Rt[(int64_t)r * stride + k]) : make_float2(0.f, 0.f);
+            const C t = r < kw ? Rt[(int64_t)r * stride + k] : mkc((S)0, (S)0);
             cc[r] = t.x;
             cm[r] = t.y - t.x;
             cp[r] = t.x + t.y;
         }
-        float k1[B], k2[B], k3[B];
+        S k1[B], k2[B], k3[B];
 #pragma unroll
-        for (int b = 0; b < B; ++b) k1[b] = k2[b] = k3[b] = 0.f;
+        for (int b = 0; b < B; ++b) k1[b] = k2[b] = k3[b] = 0;
 #pragma unroll
-        for (int u = 0; u < ROWS; ++u) {
-            const float2 x = col[u * kConvCols];
-            const float sab = x.x + x.y;
+        for (int uu = 0; uu < ROWS; ++uu) {
+            const C x = tile[uu][threadIdx.x];
+            const S sab = x.x + x.y;
 #pragma unroll
             for (int b = 0; b < B; ++b) {
-                const int r = b + K - 1 - u;
+                const int r = b + K - 1 - uu;
                 if (r >= 0 && r < K) {
-                    k1[b] = fmaf(cc[r], sab, k1[b]);
-                    k2[b] = fmaf(cm[r], x.x, k2[b]);
-                    k3[b] = fmaf(cp[r], x.y, k3[b]);
+                    k1[b] = fmx(cc[r], sab, k1[b]);
+                    k2[b] = fmx(cm[r], x.x, k2[b]);
+                    k3[b] = fmx(cp[r], x.y, k3[b]);
                 }
             }
         }
 #pragma unroll
         for (int b = 0; b < B; ++b)
-            if (w0 + b < nwires) Y[(int64_t)(w0 + b) * stride + k] = make_float2(k1[b] - k3[b], k1[b] + k2[b]);
+            if (w0 + b < nwires) Y[(int64_t)(w0 + b) * stride + k] = mkc(k1[b] - k3[b], k1[b] + k2[b]);
     } else {
-        float2 c[K];
+        C c[K];
 #pragma unroll
-        for (int r = 0; r < K; ++r) c[r] = r < kw ? __ldg(&Rt[(int64_t)r * stride + k]) : make_float2(0.f, 0.f);
-        float2 acc[B];
+        for (int r = 0; r < K; ++r) c[r] = r < kw ? Rt[(int64_t)r * stride + k] : mkc((S)0, (S)0);
+        C acc[B];
 #pragma unroll
-        for (int b = 0; b < B; ++b) acc[b] = make_float2(0.f, 0.f);
+        for (int b = 0; b < B; ++b) acc[b] = mkc((S)0, (S)0);
 #pragma unroll
-        for (int u = 0; u < ROWS; ++u) {
-            const float2 x = col[u * kConvCols];
+        for (int uu = 0; uu < ROWS; ++uu) {
+            const C x = tile[uu][threadIdx.x];
 #pragma unroll
             for (int b = 0; b < B; ++b) {
-                const int r = b + K - 1 - u;
+                const int r = b + K - 1 - uu;
                 if (r >= 0 && r < K) {
-                    acc[b].x = fmaf(c[r].x, x.x, fmaf(-c[r].y, x.y, acc[b].x));
-                    acc[b].y = fmaf(c[r].x, x.y, fmaf(c[r].y, x.x, acc[b].y));
+                    acc[b].x = fmx(c[r].x, x.x, fmx(-c[r].y, x.y, acc[b].x));
+                    acc[b].y = fmx(c[r].x, x.y, fmx(c[r].y, x.x, acc[b].y));
                 }
             }
         }
@@ -483,7 +521,7 @@ wire_conv_kernel(const __grid_constant__ ConvUnits U, int nfreq, int64_t stride,
     }
 }
 
-template <int B, bool KS>
+template <int B, bool KS, typename S>
 void launch_wc(const ConvBatch& cb, int nfreq, int64_t stride, int kw, int center, int circular, cudaStream_t s) {
     constexpr int K = kMaxRespWires;
     ConvUnits U;
@@ -497,7 +535,7 @@ void launch_wc(const ConvBatch& cb, int nfreq, int64_t stride, int kw, int cente
         U.prefix[i + 1] = U.prefix[i] + (cb.nwires[i] + B - 1) / B;
     }
     dim3 grid((nfreq + kConvCols - 1) / kConvCols, U.prefix[cb.n]);
-    wire_conv_kernel<K, B, KS><<<grid, kConvCols, 0, s>>>(U, nfreq, stride, kw, center, circular);
+    wire_conv_kernel<K, B, KS, S><<<grid, kConvCols, 0, s>>>(U, nfreq, stride, kw, center, circular);
 }
 
 // Adjoint coefficients: the wire correlation sum_r conj(Rt[r]) X[w + r - c]
@@ -570,7 +608,12 @@ cudaError_t launch_resp_grad(const float2* XG, const float2* XS, float2* A, int 
 }
 
 cudaError_t launch_twiddles(float2* tw, const FftPlan& plan, cudaStream_t s) {
-    pass_twiddles_kernel<<<(plan.L + 255) / 256, 256, 0, s>>>(tw, plan);
+    pass_twiddles_kernel<float2><<<(plan.L + 255) / 256, 256, 0, s>>>(tw, plan);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_twiddles64(double2* tw, const FftPlan& plan, cudaStream_t s) {
+    pass_twiddles_kernel<double2><<<(plan.L + 255) / 256, 256, 0, s>>>(tw, plan);
     return cudaGetLastError();
 }
 
@@ -585,6 +628,7 @@ static RowUnits row_units(const RowBatch& rb, bool* aligned16) {
     *aligned16 = true;
     for (int i = 0; i < rb.n; ++i) {
         U.in[i] = rb.in[i];
+        U.in2[i] = rb.in2[i];
         U.out[i] = rb.out[i];
         U.nrows[i] = rb.nrows[i];
         U.prefix[i + 1] = U.prefix[i] + (rb.nrows[i] + 1) / 2;
@@ -593,84 +637,131 @@ static RowUnits row_units(const RowBatch& rb, bool* aligned16) {
     return U;
 }
 
-cudaError_t launch_fwd_rows_batch(const FftPlan& plan, const float2* tw, const RowBatch& rb, int ncols,
-                                  int64_t in_stride, int64_t out_stride, int nfreq, float scale, cudaStream_t s) {
+template <typename S, typename TIN>
+static cudaError_t fwd_rows_t(const FftPlan& plan, const cplx<S>* tw, const RowBatch& rb, int ncols,
+                              int64_t in_stride, int64_t out_stride, int nfreq, float scale, cudaStream_t s) {
     if (rb.n <= 0) return cudaSuccess;
-    const int smem = 2 * ((plan.L + 1) & ~1) * (int)sizeof(float2);
-    cudaError_t e = set_smem((const void*)fwd_rows_kernel, smem);
+    const int smem = 2 * ((plan.L + 1) & ~1) * (int)sizeof(cplx<S>);
+    cudaError_t e = set_smem((const void*)fwd_rows_kernel<S, TIN>, smem);
     if (e != cudaSuccess) return e;
     bool al = false;
     const RowUnits U = row_units(rb, &al);
     if (U.prefix[rb.n] <= 0) return cudaSuccess;
     const int nload = ncols < plan.L ? ncols : plan.L;
     const int vec4 = al && (in_stride % 4 == 0) && (nload % 4 == 0);
-    fwd_rows_kernel<<<U.prefix[rb.n], kRowThreads, smem, s>>>(plan, tw, U, ncols, in_stride, out_stride, nfreq,
-                                                              scale, vec4);
+    fwd_rows_kernel<S, TIN><<<U.prefix[rb.n], kRowThreads, smem, s>>>(plan, tw, U, ncols, in_stride, out_stride,
+                                                                      nfreq, scale, vec4);
     return cudaGetLastError();
 }
 
-cudaError_t launch_fwd_rows(const FftPlan& plan, const float2* tw, const float* in, int nrows,
-                            int ncols, int64_t in_stride, float2* out, int64_t out_stride,
-                            int nfreq, float scale, cudaStream_t s) {
-    if (nrows <= 0) return cudaSuccess;
-    RowBatch rb;
-    rb.n = 1;
-    rb.in[0] = in;
-    rb.out[0] = out;
-    rb.nrows[0] = nrows;
-    return launch_fwd_rows_batch(plan, tw, rb, ncols, in_stride, out_stride, nfreq, scale, s);
-}
-
-cudaError_t launch_inv_rows_batch(const FftPlan& plan, const float2* tw, const RowBatch& rb, int64_t in_stride,
-                                  int nfreq, int ncols, int64_t out_stride, cudaStream_t s) {
+template <typename S>
+static cudaError_t inv_rows_t(const FftPlan& plan, const cplx<S>* tw, const RowBatch& rb, int64_t in_stride,
+                              int nfreq, int ncols, int64_t out_stride, cudaStream_t s) {
     if (rb.n <= 0) return cudaSuccess;
-    const int smem = 2 * ((plan.L + 1) & ~1) * (int)sizeof(float2);
-    cudaError_t e = set_smem((const void*)inv_rows_kernel, smem);
+    const int smem = 2 * ((plan.L + 1) & ~1) * (int)sizeof(cplx<S>);
+    cudaError_t e = set_smem((const void*)inv_rows_kernel<S>, smem);
     if (e != cudaSuccess) return e;
     bool al = false;
     const RowUnits U = row_units(rb, &al);
     if (U.prefix[rb.n] <= 0) return cudaSuccess;
     const int nst = ncols < plan.L ? ncols : plan.L;
     const int vec4 = al && (out_stride % 4 == 0) && (nst % 4 == 0);
-    inv_rows_kernel<<<U.prefix[rb.n], kRowThreads, smem, s>>>(plan, tw, U, in_stride, nfreq, ncols, out_stride,
-                                                              vec4);
+    inv_rows_kernel<S><<<U.prefix[rb.n], kRowThreads, smem, s>>>(plan, tw, U, in_stride, nfreq, ncols, out_stride,
+                                                                 vec4);
     return cudaGetLastError();
+}
+
+static RowBatch one_row(const void* in, const void* in2, void* out, int nrows) {
+    RowBatch rb;
+    rb.n = 1;
+    rb.in[0] = in;
+    rb.in2[0] = in2;
+    rb.out[0] = out;
+    rb.nrows[0] = nrows;
+    return rb;
+}
+
+cudaError_t launch_fwd_rows_batch(const FftPlan& plan, const float2* tw, const RowBatch& rb, int ncols,
+                                  int64_t in_stride, int64_t out_stride, int nfreq, float scale, cudaStream_t s) {
+    return fwd_rows_t<float, float>(plan, tw, rb, ncols, in_stride, out_stride, nfreq, scale, s);
+}
+
+cudaError_t launch_fwd_rows(const FftPlan& plan, const float2* tw, const float* in, int nrows,
+                            int ncols, int64_t in_stride, float2* out, int64_t out_stride,
+                            int nfreq, float scale, cudaStream_t s) {
+    if (nrows <= 0) return cudaSuccess;
+    return launch_fwd_rows_batch(plan, tw, one_row(in, nullptr, out, nrows), ncols, in_stride, out_stride, nfreq,
+                                 scale, s);
+}
+
+cudaError_t launch_fwd_rows_comp(const FftPlan& plan, const float2* tw, const float* hi, const float* lo, int nrows,
+                                 int ncols, int64_t in_stride, float2* out, int64_t out_stride, int nfreq,
+                                 cudaStream_t s) {
+    if (nrows <= 0) return cudaSuccess;
+    return fwd_rows_t<float, float>(plan, tw, one_row(hi, lo, out, nrows), ncols, in_stride, out_stride, nfreq,
+                                    1.0f, s);
+}
+
+cudaError_t launch_fwd_rows64(const FftPlan& plan, const double2* tw, const void* in, bool in_double, int nrows,
+                              int ncols, int64_t in_stride, double2* out, int64_t out_stride, int nfreq, float scale,
+                              cudaStream_t s) {
+    if (nrows <= 0) return cudaSuccess;
+    const RowBatch rb = one_row(in, nullptr, out, nrows);
+    if (in_double) return fwd_rows_t<double, double>(plan, tw, rb, ncols, in_stride, out_stride, nfreq, scale, s);
+    return fwd_rows_t<double, float>(plan, tw, rb, ncols, in_stride, out_stride, nfreq, scale, s);
+}
+
+cudaError_t launch_inv_rows_batch(const FftPlan& plan, const float2* tw, const RowBatch& rb, int64_t in_stride,
+                                  int nfreq, int ncols, int64_t out_stride, cudaStream_t s) {
+    return inv_rows_t<float>(plan, tw, rb, in_stride, nfreq, ncols, out_stride, s);
 }
 
 cudaError_t launch_inv_rows(const FftPlan& plan, const float2* tw, const float2* in, int nrows,
                             int64_t in_stride, int nfreq, float* out, int ncols,
                             int64_t out_stride, cudaStream_t s) {
     if (nrows <= 0) return cudaSuccess;
-    RowBatch rb;
-    rb.n = 1;
-    rb.in[0] = in;
-    rb.out[0] = out;
-    rb.nrows[0] = nrows;
-    return launch_inv_rows_batch(plan, tw, rb, in_stride, nfreq, ncols, out_stride, s);
+    return launch_inv_rows_batch(plan, tw, one_row(in, nullptr, out, nrows), in_stride, nfreq, ncols, out_stride, s);
+}
+
+cudaError_t launch_inv_rows64(const FftPlan& plan, const double2* tw, const double2* in, int nrows, int64_t in_stride,
+                              int nfreq, float* out, int ncols, int64_t out_stride, cudaStream_t s) {
+    if (nrows <= 0) return cudaSuccess;
+    return inv_rows_t<double>(plan, tw, one_row(in, nullptr, out, nrows), in_stride, nfreq, ncols, out_stride, s);
 }
 
 cudaError_t launch_wire_conv_batch(const ConvBatch& cb, int nfreq, int64_t stride, int kw, int center, int circular,
                                    cudaStream_t s, int variant) {
     if (cb.n <= 0 || nfreq <= 0) return cudaSuccess;
     switch (variant) {
-        case 1: launch_wc<16, true>(cb, nfreq, stride, kw, center, circular, s); break;
-        case 2: launch_wc<8, false>(cb, nfreq, stride, kw, center, circular, s); break;
-        case 3: launch_wc<8, true>(cb, nfreq, stride, kw, center, circular, s); break;
-        default: launch_wc<16, false>(cb, nfreq, stride, kw, center, circular, s); break;
+        case 1: launch_wc<16, true, float>(cb, nfreq, stride, kw, center, circular, s); break;
+        case 2: launch_wc<8, false, float>(cb, nfreq, stride, kw, center, circular, s); break;
+        case 3: launch_wc<8, true, float>(cb, nfreq, stride, kw, center, circular, s); break;
+        default: launch_wc<16, false, float>(cb, nfreq, stride, kw, center, circular, s); break;
     }
     return cudaGetLastError();
 }
 
-cudaError_t launch_wire_conv(const float2* X, float2* Y, const float2* Rt, int nwires, int nfreq,
-                             int64_t stride, int kw, int center, int circular, cudaStream_t s, int variant) {
-    if (nwires <= 0 || nfreq <= 0) return cudaSuccess;
+static ConvBatch one_conv(const void* X, void* Y, const void* Rt, int nwires) {
     ConvBatch cb;
     cb.n = 1;
     cb.X[0] = X;
     cb.Y[0] = Y;
     cb.Rt[0] = Rt;
     cb.nwires[0] = nwires;
-    return launch_wire_conv_batch(cb, nfreq, stride, kw, center, circular, s, variant);
+    return cb;
+}
+
+cudaError_t launch_wire_conv(const float2* X, float2* Y, const float2* Rt, int nwires, int nfreq,
+                             int64_t stride, int kw, int center, int circular, cudaStream_t s, int variant) {
+    if (nwires <= 0 || nfreq <= 0) return cudaSuccess;
+    return launch_wire_conv_batch(one_conv(X, Y, Rt, nwires), nfreq, stride, kw, center, circular, s, variant);
+}
+
+cudaError_t launch_wire_conv64(const double2* X, double2* Y, const double2* Rt, int nwires, int nfreq, int64_t stride,
+                               int kw, int center, int circular, cudaStream_t s) {
+    if (nwires <= 0 || nfreq <= 0) return cudaSuccess;
+    launch_wc<4, false, double>(one_conv(X, Y, Rt, nwires), nfreq, stride, kw, center, circular, s);
+    return cudaGetLastError();
 }
 
 }  // namespace ws

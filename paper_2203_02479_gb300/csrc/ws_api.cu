@@ -637,6 +637,7 @@ ws_status ws_simulate_batch(ws_plane* const* planes, int nplanes, const ws_depos
             rb.grid[j] = out_dev[u];
             counts[j] = (int64_t)pl->desc.nwires * pl->desc.nticks;
             fb.in[j] = out_dev[u];
+            fb.in2[j] = nullptr;
             fb.out[j] = X;
             fb.nrows[j] = pl->desc.nwires;
             cb.X[j] = X;
@@ -644,6 +645,7 @@ ws_status ws_simulate_batch(ws_plane* const* planes, int nplanes, const ws_depos
             cb.Rt[j] = pl->Rt;
             cb.nwires[j] = pl->desc.nwires;
             ib.in[j] = Y;
+            ib.in2[j] = nullptr;
             ib.out[j] = out_dev[u];
             ib.nrows[j] = pl->desc.nwires;
         }

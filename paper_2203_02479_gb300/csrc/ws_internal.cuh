@@ -52,14 +52,15 @@ constexpr int kMaxUnits = 32;
 struct RowBatch {          // row transforms: unit i has nrows[i] rows in[i] -> out[i]
     int n;
     const void* in[kMaxUnits];
+    const void* in2[kMaxUnits];   // optional float low parts added to in (compensated grids)
     void* out[kMaxUnits];
     int nrows[kMaxUnits];
 };
 struct ConvBatch {         // wire convolutions: unit i maps X[i] -> Y[i] with taps Rt[i]
     int n;
-    const float2* X[kMaxUnits];
-    float2* Y[kMaxUnits];
-    const float2* Rt[kMaxUnits];
+    const void* X[kMaxUnits];
+    void* Y[kMaxUnits];
+    const void* Rt[kMaxUnits];
     int nwires[kMaxUnits];
 };
 // Device-side tables (kernel parameters, read in place as __grid_constant__).
@@ -67,15 +68,16 @@ struct RowUnits {
     int n;
     int prefix[kMaxUnits + 1];   // cumulative row pairs
     const void* in[kMaxUnits];
+    const void* in2[kMaxUnits];
     void* out[kMaxUnits];
     int nrows[kMaxUnits];
 };
 struct ConvUnits {
     int n;
     int prefix[kMaxUnits + 1];   // cumulative wire blocks
-    const float2* X[kMaxUnits];
-    float2* Y[kMaxUnits];
-    const float2* Rt[kMaxUnits];
+    const void* X[kMaxUnits];
+    void* Y[kMaxUnits];
+    const void* Rt[kMaxUnits];
     int nwires[kMaxUnits];
 };
 
@@ -101,6 +103,20 @@ cudaError_t launch_inv_rows_batch(const FftPlan& plan, const float2* tw, const R
                                   int nfreq, int ncols, int64_t out_stride, cudaStream_t s);
 cudaError_t launch_wire_conv_batch(const ConvBatch& cb, int nfreq, int64_t stride, int kw, int center, int circular,
                                    cudaStream_t s, int variant);
+// FP64 path (precision WS_PREC_FP64): double twiddles, spectra and sums;
+// the forward transform reads float or double rows, the inverse writes float.
+cudaError_t launch_twiddles64(double2* tw, const FftPlan& plan, cudaStream_t s);
+cudaError_t launch_fwd_rows64(const FftPlan& plan, const double2* tw, const void* in, bool in_double, int nrows,
+                              int ncols, int64_t in_stride, double2* out, int64_t out_stride, int nfreq, float scale,
+                              cudaStream_t s);
+cudaError_t launch_inv_rows64(const FftPlan& plan, const double2* tw, const double2* in, int nrows, int64_t in_stride,
+                              int nfreq, float* out, int ncols, int64_t out_stride, cudaStream_t s);
+cudaError_t launch_wire_conv64(const double2* X, double2* Y, const double2* Rt, int nwires, int nfreq, int64_t stride,
+                               int kw, int center, int circular, cudaStream_t s);
+// Compensated input: rows are hi + lo (two float grids).
+cudaError_t launch_fwd_rows_comp(const FftPlan& plan, const float2* tw, const float* hi, const float* lo, int nrows,
+                                 int ncols, int64_t in_stride, float2* out, int64_t out_stride, int nfreq,
+                                 cudaStream_t s);
 // variant: 0 = 16 wires per thread, 1 = 16 Karatsuba, 2 = 8, 3 = 8 Karatsuba.
 constexpr int kWireConvVariants = 4;
 cudaError_t launch_wire_conv(const float2* X, float2* Y, const float2* Rt, int nwires,
