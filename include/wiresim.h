@@ -85,6 +85,9 @@ typedef struct {
                                  (circular); else that length               */
     double nsigma;            /* Gaussian truncation in sigmas (3.0)        */
     int32_t plane_id;         /* 0..15, part of the random-stream key       */
+    int32_t fp64;             /* nonzero: also hold the FP64 tables and
+                                 buffers that WS_PREC_FP64 needs (about
+                                 2x the workspace)                          */
 } ws_plane_desc;
 
 /* Depos of one event as seen by one plane: structure of arrays of float32
@@ -113,7 +116,14 @@ typedef struct {
     int32_t fluct_exact_max;  /* bins with N <= this draw N Bernoulli trials
                                  exactly; larger N use the normal
                                  approximation; 0 .. 2^27                   */
-    int32_t precision;        /* WS_PREC_*                                  */
+    int32_t precision;        /* WS_PREC_FP32: float throughout;
+                                 WS_PREC_FP32_COMP: float with compensated
+                                 (TwoSum) scatter-add and FP64 edge weights
+                                 for axes narrower than 1/8 bin;
+                                 WS_PREC_FP64: double throughout (needs a
+                                 plane created with fp64 != 0).  Only
+                                 ws_simulate honours it; the batch, patch
+                                 and adjoint entry points run FP32.         */
 } ws_params;
 
 /* Patches as produced by ws_rasterize: caller-allocated device arrays.

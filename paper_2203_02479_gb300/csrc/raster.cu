@@ -1,18 +1,26 @@
 // Diffusion, raster, binomial fluctuation and scatter-add (Sec. 2.2, Sec. 3.1).
 //
-// One warp per depo (Sec. 2.3: parallelism at the level of individual
-// ionization electron groups).  The lanes evaluate the complementary error
-// function at the patch's bin edges into a per-warp shared-memory edge
-// table, difference neighbouring edges into 1D bin weights for each axis,
-// and then emit the outer product, one bin per lane, either straight into
-// the grid with red.global.add (fused raster + scatter) or into a patch
-// buffer.
+// Parallel over depos (Sec. 2.3: parallelism at the level of individual
+// ionization electron groups).  The erfc of the standardized bin edges of a
+// patch go into per-warp shared-memory tables, neighbouring edges are
+// differenced into 1D bin weights for each axis, and the outer product is
+// emitted bin by bin, either straight into the grid with atomics (fused
+// raster + scatter) or into a patch buffer.
 //
 // Bin weight of bin [e0, e1] clipped to mu +- n sigma: with u = (e - mu) /
 // (sqrt 2 sigma) clamped to +-n/sqrt 2 and c = erfc(|u|), the mass is
 //   (c0 - c1)/2 if u0 >= 0,  (c1 - c0)/2 if u1 <= 0,  1 - (c0 + c1)/2 else,
 // which equals (erf(u1) - erf(u0))/2 without cancelling in the tails; it is
 // divided by the window mass erf(n / sqrt 2).
+//
+// Precision P (template parameter, from ws_params.precision):
+//   0  FP32: weights, values and grid in float;
+//   1  FP32 with compensated scatter: each atomicAdd's returned old value
+//      gives the exact rounding error of the addition (TwoSum), added to a
+//      second float grid that the forward transform adds back; axes
+//      narrower than an eighth of a bin take their edge differences in FP64;
+//   2  FP64: widths, bin ranges, weights, values, binomial tail and the grid
+//      in double.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -23,6 +31,16 @@ namespace {
 
 constexpr int kChunk = 64;        // bins per axis held in the per-warp tables
 constexpr int kWarpsPerBlock = 8;
+
+template <int P> struct PrecT { using W = float; };
+template <> struct PrecT<2> { using W = double; };
+
+__device__ __forceinline__ float erfc_t(float x) { return erfcf(x); }
+__device__ __forceinline__ double erfc_t(double x) { return erfc(x); }
+__device__ __forceinline__ float erf_t(float x) { return erff(x); }
+__device__ __forceinline__ double erf_t(double x) { return erf(x); }
+__device__ __forceinline__ float sqrt_t(float x) { return sqrtf(x); }
+__device__ __forceinline__ double sqrt_t(double x) { return sqrt(x); }
 
 // Philox4x32-10 (Salmon et al., SC'11): ten rounds of two 32x32 multiplies
 // whose high halves are mixed with the other counter words and the key; the
@@ -51,31 +69,46 @@ __device__ __forceinline__ int exact_count(uint4 x, int m, uint32_t T) {
 
 // Normal approximation of Binomial(N, p) from words 0, 1 of Philox block 0
 // (Box-Muller), with the integer part of N p taken exactly from the 64-bit
-// product N T.  The approximation itself is far coarser than single-precision
-// rounding, so the fast logarithm and cosine are used.
+// product N T.  In single precision the approximation itself is far coarser
+// than the rounding, so the fast logarithm and cosine are used; the FP64
+// path uses the double-precision functions.
+template <int P>
 __device__ __forceinline__ int normal_draw(uint4 x, int N, const RasterArgs& a) {
-    const float two_m32 = 2.3283064365386963e-10f;  // 2^-32
-    const float u1 = fmaf((float)x.x, two_m32, 0.5f * two_m32);
-    const float u2 = fmaf((float)x.y, two_m32, 0.5f * two_m32);
-    // cos(2 pi u2) = -cos(2 pi (u2 - 1/2)), argument within [-pi, pi]
-    const float r = sqrtf(fmaxf(-2.f * __logf(u1), 0.f));
-    const float z = -r * __cosf(6.28318530717958648f * (u2 - 0.5f));
     const uint64_t nt = (uint64_t)(uint32_t)N * (uint64_t)a.T;
     const int ipart = (int)(uint32_t)(nt >> 32);
-    const float frac = (float)(uint32_t)nt * two_m32;
-    const float pe = (float)a.T * two_m32;
-    const float sd = sqrtf(((float)ipart + frac) * (1.f - pe));
-    const int k = ipart + (int)floorf(frac + z * sd + 0.5f);
-    return k < 0 ? 0 : (k > N ? N : k);
+    if constexpr (P == 2) {
+        const double two_m32 = 2.3283064365386962890625e-10;
+        const double u1 = ((double)x.x + 0.5) * two_m32;
+        const double u2 = ((double)x.y + 0.5) * two_m32;
+        const double z = sqrt(-2.0 * log(u1)) * cospi(2.0 * u2);
+        const double frac = (double)(uint32_t)nt * two_m32;
+        const double pe = (double)a.T * two_m32;
+        const double sd = sqrt(((double)ipart + frac) * (1.0 - pe));
+        const int k = ipart + (int)floor(frac + z * sd + 0.5);
+        return k < 0 ? 0 : (k > N ? N : k);
+    } else {
+        const float two_m32 = 2.3283064365386963e-10f;  // 2^-32
+        const float u1 = fmaf((float)x.x, two_m32, 0.5f * two_m32);
+        const float u2 = fmaf((float)x.y, two_m32, 0.5f * two_m32);
+        // cos(2 pi u2) = -cos(2 pi (u2 - 1/2)), argument within [-pi, pi]
+        const float r = sqrtf(fmaxf(-2.f * __logf(u1), 0.f));
+        const float z = -r * __cosf(6.28318530717958648f * (u2 - 0.5f));
+        const float frac = (float)(uint32_t)nt * two_m32;
+        const float pe = (float)a.T * two_m32;
+        const float sd = sqrtf(((float)ipart + frac) * (1.f - pe));
+        const int k = ipart + (int)floorf(frac + z * sd + 0.5f);
+        return k < 0 ? 0 : (k > N ? N : k);
+    }
 }
 
 // Survivor count contributed by Philox block j of a bin holding N electrons
 // (the bin's binomial draw is the sum over its blocks): exact trials for
 // N <= exact_max, else the single normal-approximation block.
+template <int P>
 __device__ __forceinline__ int binomial_block(int N, int j, const RasterArgs& a, uint32_t bin, uint32_t depo) {
     const uint4 x = philox4x32_10(make_uint4((uint32_t)j, bin, depo, a.evpl), a.key0, a.key1);
     if (N <= a.exact_max) return exact_count(x, N - 4 * j, a.T);
-    return normal_draw(x, N, a);
+    return normal_draw<P>(x, N, a);
 }
 
 // Philox blocks a bin of N electrons needs.
@@ -84,26 +117,53 @@ __device__ __forceinline__ int binomial_items(int N, const RasterArgs& a) {
     return N <= a.exact_max ? (N + 3) >> 2 : 1;
 }
 
+// Electrons in a bin of expected charge v (saturating at 1e9).
+__device__ __forceinline__ int electrons(float v) { return (int)floorf(fminf(v, 1.0e9f) + 0.5f); }
+__device__ __forceinline__ int electrons(double v) { return (int)floor(fmin(v, 1.0e9) + 0.5); }
+
+// Scatter-add of one bin value into the grid at the unit's precision.
+__device__ __forceinline__ float two_sum_err(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    return __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+template <int P>
+__device__ __forceinline__ void emit(const RasterArgs& a, float* grid, int64_t idx, typename PrecT<P>::W v) {
+    if (v == 0) return;
+    if constexpr (P == 0) {
+        atomicAdd(grid + idx, v);
+    } else if constexpr (P == 1) {
+        const float old = atomicAdd(grid + idx, v);
+        const float err = two_sum_err(old, v);
+        if (err != 0.f) atomicAdd(a.lo + idx, err);
+    } else {
+        atomicAdd(a.grid64 + idx, v);
+    }
+}
+
 // Per-depo geometry: widths and the patch's bin range clipped to the grid.
-struct Extent {
-    float mu_t, mu_x, st, sx;
+template <typename W>
+struct ExtentT {
+    W mu_t, mu_x, st, sx;
     int k0, k1, w0, w1;   // inclusive, clipped
     bool point_t, point_x;
 };
+using Extent = ExtentT<float>;
 
-__device__ __forceinline__ bool axis_range(float mu, float sigma, float delta, float nsig, int nbins,
-                                           int* lo, int* hi, bool* point) {
-    float a, b;
-    *point = !(sigma > 1e-6f * delta);
+template <typename W>
+__device__ __forceinline__ bool axis_range(W mu, W sigma, W delta, W nsig, int nbins, int* lo, int* hi, bool* point) {
+    W lo_e, hi_e;
+    *point = !(sigma > (W)1e-6 * delta);
     if (*point) {
-        a = b = mu;
+        lo_e = hi_e = mu;
     } else {
-        a = mu - nsig * sigma;
-        b = mu + nsig * sigma;
+        lo_e = mu - nsig * sigma;
+        hi_e = mu + nsig * sigma;
     }
     // Bins beyond the grid are clipped; clamp before converting to int.
-    const float fa = fminf(fmaxf(floorf(a / delta), -1.f), (float)nbins);
-    const float fb = fminf(fmaxf(floorf(b / delta), -1.f), (float)nbins);
+    const W fa = fmin(fmax(floor(lo_e / delta), (W)-1), (W)nbins);
+    const W fb = fmin(fmax(floor(hi_e / delta), (W)-1), (W)nbins);
     int l = (int)fa, h = (int)fb;
     if (l < 0) l = 0;
     if (h > nbins - 1) h = nbins - 1;
@@ -113,63 +173,93 @@ __device__ __forceinline__ bool axis_range(float mu, float sigma, float delta, f
 }
 
 // Returns false if the depo has no in-grid bins or is invalid (then *bad).
-__device__ __forceinline__ bool depo_extent(const RasterArgs& a, int64_t i, Extent* e, float* q, bool* bad) {
+template <typename W>
+__device__ __forceinline__ bool depo_extent(const RasterArgs& a, int64_t i, ExtentT<W>* e, W* q, bool* bad) {
     *bad = false;
-    const float qi = __ldg(a.q + i), xi = __ldg(a.x + i), ti = __ldg(a.t + i);
-    float st, sx;
-    bool ok = isfinite(qi) && isfinite(xi) && isfinite(ti);
+    const float qf = __ldg(a.q + i), xf = __ldg(a.x + i), tf = __ldg(a.t + i);
+    bool ok = isfinite(qf) && isfinite(xf) && isfinite(tf);
+    const W ti = (W)tf;
+    W st, sx;
     if (a.sig_t) {
-        st = __ldg(a.sig_t + i);
-        sx = __ldg(a.sig_x + i);
+        st = (W)__ldg(a.sig_t + i);
+        sx = (W)__ldg(a.sig_x + i);
     } else {
-        ok = ok && ti >= 0.f;
-        const float tt = fmaxf(ti, 0.f);
-        st = sqrtf(a.two_DL * tt) * a.inv_v;
-        sx = sqrtf(a.two_DT * tt);
+        ok = ok && tf >= 0.f;
+        const W tt = ti > (W)0 ? ti : (W)0;
+        if constexpr (sizeof(W) == 8) {
+            st = sqrt(a.two_DL64 * tt) / a.v64;
+            sx = sqrt(a.two_DT64 * tt);
+        } else {
+            st = sqrtf(a.two_DL * tt) * a.inv_v;
+            sx = sqrtf(a.two_DT * tt);
+        }
     }
-    ok = ok && isfinite(st) && isfinite(sx) && st >= 0.f && sx >= 0.f;
+    ok = ok && isfinite(st) && isfinite(sx) && st >= (W)0 && sx >= (W)0;
     if (!ok) {
         *bad = true;
         return false;
     }
-    *q = qi;
-    e->mu_t = ti; e->mu_x = xi; e->st = st; e->sx = sx;
-    if (!axis_range(ti, st, a.tick, a.nsig, a.nticks, &e->k0, &e->k1, &e->point_t)) return false;
-    if (!axis_range(xi, sx, a.pitch, a.nsig, a.nwires, &e->w0, &e->w1, &e->point_x)) return false;
+    *q = (W)qf;
+    e->mu_t = ti; e->mu_x = (W)xf; e->st = st; e->sx = sx;
+    const W tick = sizeof(W) == 8 ? (W)a.tick64 : (W)a.tick;
+    const W pitch = sizeof(W) == 8 ? (W)a.pitch64 : (W)a.pitch;
+    const W nsig = sizeof(W) == 8 ? (W)a.nsig64 : (W)a.nsig;
+    if (!axis_range<W>(ti, st, tick, nsig, a.nticks, &e->k0, &e->k1, &e->point_t)) return false;
+    if (!axis_range<W>((W)xf, sx, pitch, nsig, a.nwires, &e->w0, &e->w1, &e->point_x)) return false;
     return true;
 }
 
+// Weight of a bin from its two clamped standardized edges u and erfc(|u|).
+template <typename W>
+__device__ __forceinline__ W bin_mass(W u0, W u1, W c0, W c1) {
+    if (u0 >= (W)0) return (W)0.5 * (c0 - c1);
+    if (u1 <= (W)0) return (W)0.5 * (c1 - c0);
+    return (W)1 - (W)0.5 * (c0 + c1);
+}
+
 // Weights of bins [first, first + nb) of one axis into w[0..nb) (warp-wide).
-// edge[] is per-warp scratch of kChunk + 1 floats (u) and cv[] (erfc(|u|)).
-__device__ __forceinline__ void axis_weights(float mu, float sigma, float delta, float nsig, bool point,
-                                             int first, int nb, float inv_norm, float* u_s, float* c_s,
-                                             float* w, int lane) {
+template <typename W>
+__device__ __forceinline__ void axis_weights(W mu, W sigma, W delta, W nsig, bool point, int first, int nb,
+                                             W inv_norm, W* u_s, W* c_s, W* w, int lane) {
     if (point) {
         // A point charge lands in one bin: the range has exactly that bin.
-        for (int b = lane; b < nb; b += 32) w[b] = 1.f;
+        for (int b = lane; b < nb; b += 32) w[b] = (W)1;
         __syncwarp();
         return;
     }
-    const float inv_s2 = 1.f / (1.41421356237309505f * sigma);
-    const float umax = nsig * 0.707106781186547524f;
+    const W inv_s2 = (W)1 / ((W)1.41421356237309504880 * sigma);
+    const W umax = nsig * (W)0.70710678118654752440;
     for (int j = lane; j <= nb; j += 32) {
-        const float e = (float)(first + j) * delta;
-        float u = (e - mu) * inv_s2;
-        u = fminf(fmaxf(u, -umax), umax);
+        const W e = (W)(first + j) * delta;
+        W u = (e - mu) * inv_s2;
+        u = fmin(fmax(u, -umax), umax);
         u_s[j] = u;
-        c_s[j] = erfcf(fabsf(u));
+        c_s[j] = erfc_t(fabs(u));
     }
     __syncwarp();
-    for (int b = lane; b < nb; b += 32) {
-        const float u0 = u_s[b], u1 = u_s[b + 1];
-        const float c0 = c_s[b], c1 = c_s[b + 1];
-        float m;
-        if (u0 >= 0.f) m = 0.5f * (c0 - c1);
-        else if (u1 <= 0.f) m = 0.5f * (c1 - c0);
-        else m = 1.f - 0.5f * (c0 + c1);
-        w[b] = m * inv_norm;
-    }
+    for (int b = lane; b < nb; b += 32) w[b] = bin_mass(u_s[b], u_s[b + 1], c_s[b], c_s[b + 1]) * inv_norm;
     __syncwarp();
+}
+
+// Same, computed by one lane for its own depo (WC: arithmetic, WO: output).
+template <typename WC, typename WO>
+__device__ __forceinline__ void lane_axis_weights(WC mu, WC sigma, WC delta, WC nsig, bool point, int first, int nb,
+                                                  WC inv_norm, WO* w) {
+    if (point) {
+        w[0] = (WO)1;
+        return;
+    }
+    const WC inv_s2 = (WC)1 / ((WC)1.41421356237309504880 * sigma);
+    const WC umax = nsig * (WC)0.70710678118654752440;
+    WC u_prev = 0, c_prev = 0;
+    for (int j = 0; j <= nb; ++j) {
+        const WC e = (WC)(first + j) * delta;
+        const WC u = fmin(fmax((e - mu) * inv_s2, -umax), umax);
+        const WC c = erfc_t(fabs(u));
+        if (j > 0) w[j - 1] = (WO)(bin_mass(u_prev, u, c_prev, c) * inv_norm);
+        u_prev = u;
+        c_prev = c;
+    }
 }
 
 enum { EMIT_GRID = 0, EMIT_PATCH = 1 };
@@ -187,22 +277,30 @@ __device__ __forceinline__ int find_unit64(const long long* prefix, int n, long 
 constexpr int kSmallT = 16;  // largest patch (ticks x wires) the lane-per-depo kernel takes
 constexpr int kSmallW = 8;
 
-__device__ __forceinline__ bool is_large(const Extent& e) {
+template <typename W>
+__device__ __forceinline__ bool is_large(const ExtentT<W>& e) {
     return (e.k1 - e.k0 + 1) > kSmallT || (e.w1 - e.w0 + 1) > kSmallW;
+}
+
+template <typename W>
+__device__ __forceinline__ W window_norm(const RasterArgs& a) {
+    if constexpr (sizeof(W) == 8) return 1.0 / erf(a.nsig64 * 0.70710678118654752440);
+    else return 1.f / erff(a.nsig * 0.707106781186547524f);
 }
 
 // Warp per depo for the large patches the lane-pair kernel handed over:
 // the list's (unit, depo) entries if they fit in it, else every depo of
 // every unit whose patch is large.  The last block to finish resets the
 // list counter for the next launch.
-template <int MODE>
+template <int MODE, int P>
 __global__ void __launch_bounds__(32 * kWarpsPerBlock)
 raster_kernel(const __grid_constant__ RasterUnits U, ws_patches pt, const long long* __restrict__ list,
               unsigned* list_count, unsigned list_cap, unsigned* done) {
-    __shared__ float s_u[kWarpsPerBlock][kChunk + 1];
-    __shared__ float s_c[kWarpsPerBlock][kChunk + 1];
-    __shared__ float s_wt[kWarpsPerBlock][kChunk];
-    __shared__ float s_wx[kWarpsPerBlock][kChunk];
+    using W = typename PrecT<P>::W;
+    __shared__ W s_u[kWarpsPerBlock][kChunk + 1];
+    __shared__ W s_c[kWarpsPerBlock][kChunk + 1];
+    __shared__ W s_wt[kWarpsPerBlock][kChunk];
+    __shared__ W s_wx[kWarpsPerBlock][kChunk];
     __shared__ int s_incl[kWarpsPerBlock][32];
     __shared__ int s_n[kWarpsPerBlock][32];
     __shared__ int s_cnt[kWarpsPerBlock][32];
@@ -225,49 +323,48 @@ raster_kernel(const __grid_constant__ RasterUnits U, ws_patches pt, const long l
         }
         const RasterArgs& a = U.a[u];
         float* __restrict__ grid = U.grid[u];
-        Extent e;
-        float q;
+        ExtentT<W> e;
+        W q;
         bool bad;
-        const bool any = depo_extent(a, i, &e, &q, &bad);
+        const bool any = depo_extent<W>(a, i, &e, &q, &bad);
         if (!(any && is_large(e))) continue;  // not handed over
         int64_t off = 0;
         int ntf = 0;
         if (MODE == EMIT_PATCH) {
-            const int nwf = any ? e.w1 - e.w0 + 1 : 0;
-            ntf = any ? e.k1 - e.k0 + 1 : 0;
+            const int nwf = e.w1 - e.w0 + 1;
+            ntf = e.k1 - e.k0 + 1;
             off = pt.off[i];
             const bool fits = off + (int64_t)nwf * ntf <= pt.capacity_bins;
             if (lane == 0) {
-                pt.w0[i] = any ? e.w0 : 0;
-                pt.t0[i] = any ? e.k0 : 0;
+                pt.w0[i] = e.w0;
+                pt.t0[i] = e.k0;
                 pt.nw[i] = fits ? nwf : 0;
                 pt.nt[i] = fits ? ntf : 0;
                 if (!fits) atomicOr(a.status, WS_DEV_PATCH_OVERFLOW);
             }
             if (!fits) continue;
         }
-        if (!any) continue;
-        const float inv_norm = 1.f / erff(a.nsig * 0.707106781186547524f);
-        const float scale = a.fluct ? 1.f : a.p * q;
+        const W inv_norm = window_norm<W>(a);
+        const W tick = sizeof(W) == 8 ? (W)a.tick64 : (W)a.tick;
+        const W pitch = sizeof(W) == 8 ? (W)a.pitch64 : (W)a.pitch;
+        const W nsig = sizeof(W) == 8 ? (W)a.nsig64 : (W)a.nsig;
+        const W scale = a.fluct ? (W)1 : (sizeof(W) == 8 ? (W)a.p64 : (W)a.p) * q;
         for (int kc = e.k0; kc <= e.k1; kc += kChunk) {
             const int ntc = min(kChunk, e.k1 - kc + 1);
-            axis_weights(e.mu_t, e.st, a.tick, a.nsig, e.point_t, kc, ntc, inv_norm, s_u[wib], s_c[wib],
-                         s_wt[wib], lane);
+            axis_weights<W>(e.mu_t, e.st, tick, nsig, e.point_t, kc, ntc, inv_norm, s_u[wib], s_c[wib], s_wt[wib],
+                            lane);
             for (int wc = e.w0; wc <= e.w1; wc += kChunk) {
                 const int nxc = min(kChunk, e.w1 - wc + 1);
-                axis_weights(e.mu_x, e.sx, a.pitch, a.nsig, e.point_x, wc, nxc, inv_norm, s_u[wib],
-                             s_c[wib], s_wx[wib], lane);
+                axis_weights<W>(e.mu_x, e.sx, pitch, nsig, e.point_x, wc, nxc, inv_norm, s_u[wib], s_c[wib],
+                                s_wx[wib], lane);
                 const int nbin = nxc * ntc;
                 if (!a.fluct) {
                     for (int idx = lane; idx < nbin; idx += 32) {
                         const int ia = idx / ntc, ib = idx - ia * ntc;
                         const int w = wc + ia, k = kc + ib;
-                        const float v = scale * s_wx[wib][ia] * s_wt[wib][ib];
-                        if (MODE == EMIT_GRID) {
-                            if (v != 0.f) atomicAdd(grid + (int64_t)w * a.nticks + k, v);
-                        } else {
-                            pt.val[off + (int64_t)(w - e.w0) * ntf + (k - e.k0)] = v;
-                        }
+                        const W v = scale * s_wx[wib][ia] * s_wt[wib][ib];
+                        if (MODE == EMIT_GRID) emit<P>(a, grid, (int64_t)w * a.nticks + k, v);
+                        else pt.val[off + (int64_t)(w - e.w0) * ntf + (k - e.k0)] = (float)v;
                     }
                 }
                 // Binomial mode: 32 bins per round; each (bin, Philox block)
@@ -279,8 +376,7 @@ raster_kernel(const __grid_constant__ RasterUnits U, ws_patches pt, const long l
                         const int ia = idx / ntc, ib = idx - ia * ntc;
                         w = wc + ia;
                         k = kc + ib;
-                        const float nexp = fminf(q * s_wx[wib][ia] * s_wt[wib][ib], 1.0e9f);
-                        N = (int)floorf(nexp + 0.5f);
+                        N = electrons(q * s_wx[wib][ia] * s_wt[wib][ib]);
                     }
                     const int items = binomial_items(N, a);
                     int incl = items;
@@ -294,27 +390,24 @@ raster_kernel(const __grid_constant__ RasterUnits U, ws_patches pt, const long l
                     s_n[wib][lane] = N;
                     s_cnt[wib][lane] = (N > 0 && a.keep_all) ? N : 0;
                     __syncwarp();
-                    for (int it = lane; it < total; it += 32) {
-                        int lo = 0, hi = 31;  // first bin slot whose inclusive count exceeds it
+                    for (int it2 = lane; it2 < total; it2 += 32) {
+                        int lo = 0, hi = 31;  // first bin slot whose inclusive count exceeds it2
                         while (lo < hi) {
                             const int mid = (lo + hi) >> 1;
-                            if (s_incl[wib][mid] > it) hi = mid; else lo = mid + 1;
+                            if (s_incl[wib][mid] > it2) hi = mid; else lo = mid + 1;
                         }
                         const int first = lo > 0 ? s_incl[wib][lo - 1] : 0;
                         const int bidx = base + lo;
                         const int ia = bidx / ntc, ib = bidx - ia * ntc;
                         const uint32_t gbin = (uint32_t)((int64_t)(wc + ia) * a.nticks + (kc + ib));
-                        const int c = binomial_block(s_n[wib][lo], it - first, a, gbin, (uint32_t)i);
+                        const int c = binomial_block<P>(s_n[wib][lo], it2 - first, a, gbin, (uint32_t)i);
                         if (c) atomicAdd(&s_cnt[wib][lo], c);
                     }
                     __syncwarp();
                     if (idx < nbin) {
-                        const float v = (float)s_cnt[wib][lane];
-                        if (MODE == EMIT_GRID) {
-                            if (v != 0.f) atomicAdd(grid + (int64_t)w * a.nticks + k, v);
-                        } else {
-                            pt.val[off + (int64_t)(w - e.w0) * ntf + (k - e.k0)] = v;
-                        }
+                        const W v = (W)s_cnt[wib][lane];
+                        if (MODE == EMIT_GRID) emit<P>(a, grid, (int64_t)w * a.nticks + k, v);
+                        else pt.val[off + (int64_t)(w - e.w0) * ntf + (k - e.k0)] = (float)v;
                     }
                     __syncwarp();
                 }
@@ -342,31 +435,6 @@ raster_kernel(const __grid_constant__ RasterUnits U, ws_patches pt, const long l
 constexpr int kSmallWarpsPerBlock = 4;
 constexpr int kSmallGroup = 16;   // depos per warp (a lane pair per depo)
 
-__device__ __forceinline__ void lane_axis_weights(float mu, float sigma, float delta, float nsig, bool point,
-                                                  int first, int nb, float inv_norm, float* w) {
-    if (point) {
-        w[0] = 1.f;
-        return;
-    }
-    const float inv_s2 = 1.f / (1.41421356237309505f * sigma);
-    const float umax = nsig * 0.707106781186547524f;
-    float u_prev = 0.f, c_prev = 0.f;
-    for (int j = 0; j <= nb; ++j) {
-        const float e = (float)(first + j) * delta;
-        float u = fminf(fmaxf((e - mu) * inv_s2, -umax), umax);
-        const float c = erfcf(fabsf(u));
-        if (j > 0) {
-            float m;
-            if (u_prev >= 0.f) m = 0.5f * (c_prev - c);
-            else if (u <= 0.f) m = 0.5f * (c - c_prev);
-            else m = 1.f - 0.5f * (c_prev + c);
-            w[j - 1] = m * inv_norm;
-        }
-        u_prev = u;
-        c_prev = c;
-    }
-}
-
 // First slot of s[0..n) (inclusive prefix sums, nondecreasing) exceeding v.
 template <int N>
 __device__ __forceinline__ int find_slot(const int* s, int v) {
@@ -377,41 +445,57 @@ __device__ __forceinline__ int find_slot(const int* s, int v) {
     return lo;
 }
 
-template <int MODE>
+// One axis of a lane's depo: FP32, or FP64 for the whole FP64 path and for
+// axes narrower than an eighth of a bin in the compensated path.
+template <int P, typename W>
+__device__ __forceinline__ void lane_weights(const RasterArgs& a, W mu, W sigma, bool tick_axis, bool point, int first,
+                                             int nb, W inv_norm, W* w) {
+    const W delta = tick_axis ? (sizeof(W) == 8 ? (W)a.tick64 : (W)a.tick) : (sizeof(W) == 8 ? (W)a.pitch64 : (W)a.pitch);
+    const W nsig = sizeof(W) == 8 ? (W)a.nsig64 : (W)a.nsig;
+    if (P == 1 && !point && sigma < delta * (W)0.125) {
+        lane_axis_weights<double, W>((double)mu, (double)sigma, tick_axis ? a.tick64 : a.pitch64, a.nsig64, point, first,
+                                     nb, 1.0 / erf(a.nsig64 * 0.70710678118654752440), w);
+        return;
+    }
+    lane_axis_weights<W, W>(mu, sigma, delta, nsig, point, first, nb, inv_norm, w);
+}
+
+template <int MODE, int P>
 __global__ void __launch_bounds__(32 * kSmallWarpsPerBlock, 8)
 raster_small_kernel(const __grid_constant__ RasterUnits U, ws_patches pt, long long* __restrict__ list,
                     unsigned* list_count, unsigned list_cap) {
-    constexpr int W = kSmallWarpsPerBlock;
+    using W = typename PrecT<P>::W;
+    constexpr int NW = kSmallWarpsPerBlock;
     constexpr int G = kSmallGroup;
-    __shared__ float s_wt[W][G][kSmallT + 1];
-    __shared__ float s_wx[W][G][kSmallW + 1];
-    __shared__ int s_off[W][G];     // inclusive scan of the depos' bin counts
-    __shared__ int s_k0[W][G];
-    __shared__ int s_w0[W][G];
-    __shared__ int s_nt[W][G];
-    __shared__ float s_q[W][G];
-    __shared__ int s_incl[W][64];   // inclusive scan of the round's exact items
-    __shared__ int s_cnt[W][64];
-    __shared__ int s_n[W][64];
-    __shared__ uint32_t s_gbin[W][64];
-    __shared__ uint32_t s_dep[W][64];
+    __shared__ W s_wt[NW][G][kSmallT + 1];
+    __shared__ W s_wx[NW][G][kSmallW + 1];
+    __shared__ int s_off[NW][G];     // inclusive scan of the depos' bin counts
+    __shared__ int s_k0[NW][G];
+    __shared__ int s_w0[NW][G];
+    __shared__ int s_nt[NW][G];
+    __shared__ W s_q[NW][G];
+    __shared__ int s_incl[NW][64];   // inclusive scan of the round's exact items
+    __shared__ int s_cnt[NW][64];
+    __shared__ int s_n[NW][64];
+    __shared__ uint32_t s_gbin[NW][64];
+    __shared__ uint32_t s_dep[NW][64];
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
-    const int64_t nwarps = (int64_t)gridDim.x * W;
+    const int64_t nwarps = (int64_t)gridDim.x * NW;
     const int dl = lane & (G - 1);      // depo slot of this lane
     const bool tick_lane = lane < G;    // lane pair: tick edges on dl, wire edges on dl + G
     const int64_t ngroups = U.gprefix[U.n];
-    for (int64_t grp = (int64_t)blockIdx.x * W + wib; grp < ngroups; grp += nwarps) {
+    for (int64_t grp = (int64_t)blockIdx.x * NW + wib; grp < ngroups; grp += nwarps) {
         const int uu = find_unit64(U.gprefix, U.n, grp);
         const RasterArgs& a = U.a[uu];
         float* __restrict__ grid = U.grid[uu];
-        const float inv_norm = 1.f / erff(a.nsig * 0.707106781186547524f);
+        const W inv_norm = window_norm<W>(a);
         const int64_t base = (grp - U.gprefix[uu]) * G;
         const int64_t i = base + dl;
-        Extent e;
-        float q = 0.f;
+        ExtentT<W> e;
+        W q = 0;
         bool bad = false, any = false;
-        if (i < a.n) any = depo_extent(a, i, &e, &q, &bad);
+        if (i < a.n) any = depo_extent<W>(a, i, &e, &q, &bad);
         if (bad && tick_lane) atomicOr(a.status, WS_DEV_BAD_DEPO);
         const bool large = any && is_large(e);
         if (large && tick_lane) {
@@ -434,10 +518,8 @@ raster_small_kernel(const __grid_constant__ RasterUnits U, ws_patches pt, long l
             if (!fits) nb = 0;
         }
         if (nb > 0) {
-            if (tick_lane)
-                lane_axis_weights(e.mu_t, e.st, a.tick, a.nsig, e.point_t, e.k0, ntc, inv_norm, s_wt[wib][dl]);
-            else
-                lane_axis_weights(e.mu_x, e.sx, a.pitch, a.nsig, e.point_x, e.w0, nxc, inv_norm, s_wx[wib][dl]);
+            if (tick_lane) lane_weights<P, W>(a, e.mu_t, e.st, true, e.point_t, e.k0, ntc, inv_norm, s_wt[wib][dl]);
+            else lane_weights<P, W>(a, e.mu_x, e.sx, false, e.point_x, e.w0, nxc, inv_norm, s_wx[wib][dl]);
         }
         if (!tick_lane) nb = 0;   // each depo counted once in the scan
         int incl = nb;
@@ -452,7 +534,7 @@ raster_small_kernel(const __grid_constant__ RasterUnits U, ws_patches pt, long l
             s_k0[wib][dl] = any ? e.k0 : 0;
             s_w0[wib][dl] = any ? e.w0 : 0;
             s_nt[wib][dl] = ntc;
-            s_q[wib][dl] = a.fluct ? q : a.p * q;
+            s_q[wib][dl] = a.fluct ? q : (sizeof(W) == 8 ? (W)a.p64 : (W)a.p) * q;
         }
         __syncwarp();
         const int* off = s_off[wib];
@@ -462,12 +544,9 @@ raster_small_kernel(const __grid_constant__ RasterUnits U, ws_patches pt, long l
                 const int local = g - (d > 0 ? off[d - 1] : 0);
                 const int nt = s_nt[wib][d];
                 const int ia = local / nt, ib = local - ia * nt;
-                const float v = s_q[wib][d] * s_wx[wib][d][ia] * s_wt[wib][d][ib];
-                if (MODE == EMIT_GRID) {
-                    if (v != 0.f) atomicAdd(grid + (int64_t)(s_w0[wib][d] + ia) * a.nticks + s_k0[wib][d] + ib, v);
-                } else {
-                    pt.val[pt.off[base + d] + local] = v;
-                }
+                const W v = s_q[wib][d] * s_wx[wib][d][ia] * s_wt[wib][d][ib];
+                if (MODE == EMIT_GRID) emit<P>(a, grid, (int64_t)(s_w0[wib][d] + ia) * a.nticks + s_k0[wib][d] + ib, v);
+                else pt.val[pt.off[base + d] + local] = (float)v;
             }
         } else {
             // Rounds of 64 bins, two per lane: the bin's electron count, its
@@ -486,8 +565,7 @@ raster_small_kernel(const __grid_constant__ RasterUnits U, ws_patches pt, long l
                         const int ia = local[h] / nt, ib = local[h] - ia * nt;
                         w[h] = s_w0[wib][d[h]] + ia;
                         k[h] = s_k0[wib][d[h]] + ib;
-                        const float nexp = fminf(s_q[wib][d[h]] * s_wx[wib][d[h]][ia] * s_wt[wib][d[h]][ib], 1.0e9f);
-                        N[h] = (int)floorf(nexp + 0.5f);
+                        N[h] = electrons(s_q[wib][d[h]] * s_wx[wib][d[h]][ia] * s_wt[wib][d[h]][ib]);
                     }
                 }
                 uint32_t gbin[2], dep[2];
@@ -505,7 +583,7 @@ raster_small_kernel(const __grid_constant__ RasterUnits U, ws_patches pt, long l
                 }
 #pragma unroll
                 for (int h = 0; h < 2; ++h)
-                    if (binomial_items(N[h], a) > 0 && N[h] > a.exact_max) cnt[h] = normal_draw(x[h], N[h], a);
+                    if (binomial_items(N[h], a) > 0 && N[h] > a.exact_max) cnt[h] = normal_draw<P>(x[h], N[h], a);
                 int inc0 = ne[0], inc1 = ne[1];
 #pragma unroll
                 for (int o = 1; o < 32; o <<= 1) {
@@ -553,12 +631,9 @@ raster_small_kernel(const __grid_constant__ RasterUnits U, ws_patches pt, long l
                 for (int h = 0; h < 2; ++h) {
                     const int g = gb + 32 * h + lane;
                     if (g < total) {
-                        const float v = (float)s_cnt[wib][32 * h + lane];
-                        if (MODE == EMIT_GRID) {
-                            if (v != 0.f) atomicAdd(grid + (int64_t)w[h] * a.nticks + k[h], v);
-                        } else {
-                            pt.val[pt.off[base + d[h]] + local[h]] = v;
-                        }
+                        const W v = (W)s_cnt[wib][32 * h + lane];
+                        if (MODE == EMIT_GRID) emit<P>(a, grid, (int64_t)w[h] * a.nticks + k[h], v);
+                        else pt.val[pt.off[base + d[h]] + local[h]] = (float)v;
                     }
                 }
                 __syncwarp();
@@ -636,7 +711,7 @@ depo_grad_kernel(RasterArgs a, GradArgs g) {
         Extent e;
         float q;
         bool bad;
-        const bool any = depo_extent(a, i, &e, &q, &bad);
+        const bool any = depo_extent<float>(a, i, &e, &q, &bad);
         if (any) {
             // One more bin on each side of a non-point axis: the FP32 bin
             // range can drop a sliver bin whose edge lies within rounding of
@@ -718,7 +793,7 @@ __global__ void patch_sizes_kernel(RasterArgs a, int64_t* __restrict__ sizes,
             Extent e;
             float q;
             bool bad;
-            if (depo_extent(a, i, &e, &q, &bad)) sz = (int64_t)(e.w1 - e.w0 + 1) * (e.k1 - e.k0 + 1);
+            if (depo_extent<float>(a, i, &e, &q, &bad)) sz = (int64_t)(e.w1 - e.w0 + 1) * (e.k1 - e.k0 + 1);
         }
         if (sizes) sizes[i] = sz;
         mine += (unsigned long long)sz;
@@ -851,25 +926,30 @@ static RasterUnits raster_units(const RasterBatch& rb) {
     return U;
 }
 
-template <int MODE>
+template <int MODE, int P>
 static cudaError_t launch_raster_units(const RasterUnits& U, const ws_patches& p, const LargeList& L,
                                        cudaStream_t s) {
     if (U.dprefix[U.n] <= 0) return cudaSuccess;
     const int64_t groups = U.gprefix[U.n];
     int blocks = grid_for(groups * 32, 32 * kSmallWarpsPerBlock, 16);
-    raster_small_kernel<MODE><<<blocks, 32 * kSmallWarpsPerBlock, 0, s>>>(U, p, L.list, L.count, L.cap);
-    raster_kernel<MODE><<<num_sms() * 2, 32 * kWarpsPerBlock, 0, s>>>(U, p, L.list, L.count, L.cap, L.done);
+    raster_small_kernel<MODE, P><<<blocks, 32 * kSmallWarpsPerBlock, 0, s>>>(U, p, L.list, L.count, L.cap);
+    raster_kernel<MODE, P><<<num_sms() * 2, 32 * kWarpsPerBlock, 0, s>>>(U, p, L.list, L.count, L.cap, L.done);
     return cudaGetLastError();
 }
 
 cudaError_t launch_raster_scatter_batch(const RasterBatch& rb, const LargeList& L, cudaStream_t s) {
     ws_patches none{};
-    return launch_raster_units<EMIT_GRID>(raster_units(rb), none, L, s);
+    switch (rb.prec) {
+        case WS_PREC_FP32_COMP: return launch_raster_units<EMIT_GRID, 1>(raster_units(rb), none, L, s);
+        case WS_PREC_FP64: return launch_raster_units<EMIT_GRID, 2>(raster_units(rb), none, L, s);
+        default: return launch_raster_units<EMIT_GRID, 0>(raster_units(rb), none, L, s);
+    }
 }
 
 cudaError_t launch_raster_scatter(const RasterArgs& a, float* grid, const LargeList& L, cudaStream_t s) {
     RasterBatch rb;
     rb.n = 1;
+    rb.prec = a.prec;
     rb.a[0] = a;
     rb.grid[0] = grid;
     return launch_raster_scatter_batch(rb, L, s);
@@ -893,9 +973,10 @@ cudaError_t launch_scan_inplace(int64_t* v, int64_t n, int64_t* scratch, cudaStr
 cudaError_t launch_raster_patches(const RasterArgs& a, const ws_patches& p, const LargeList& L, cudaStream_t s) {
     RasterBatch rb;
     rb.n = 1;
+    rb.prec = WS_PREC_FP32;
     rb.a[0] = a;
     rb.grid[0] = nullptr;
-    return launch_raster_units<EMIT_PATCH>(raster_units(rb), p, L, s);
+    return launch_raster_units<EMIT_PATCH, 0>(raster_units(rb), p, L, s);
 }
 
 cudaError_t launch_scatter_patches(const ws_patches& p, float* grid, int nwires, int nticks, cudaStream_t s) {

@@ -111,7 +111,8 @@ size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 struct Layout {
     ws::FftPlan plan;
     int nfreq, fstride;
-    size_t off_status, off_tw, off_rt, off_x, off_y, off_scan, off_large, off_radj, off_racc, off_grid2, total;
+    size_t off_status, off_tw, off_rt, off_x, off_y, off_scan, off_large, off_radj, off_racc, off_grid2;
+    size_t off_tw64, off_rt64, off_x64, off_y64, off_g64, total;
 };
 
 ws_status plan_layout(const ws_plane_desc* d, Layout* lay) {
@@ -150,6 +151,14 @@ ws_status plan_layout(const ws_plane_desc* d, Layout* lay) {
     lay->off_radj = o; o = align256(o + sizeof(float2) * (size_t)d->resp_nwires * lay->fstride);
     lay->off_racc = o; o = align256(o + sizeof(float2) * (size_t)d->resp_nwires * lay->fstride);
     lay->off_grid2 = o; o = align256(o + sizeof(float) * (size_t)d->nwires * d->nticks);
+    lay->off_tw64 = lay->off_rt64 = lay->off_x64 = lay->off_y64 = lay->off_g64 = 0;
+    if (d->fp64) {
+        lay->off_tw64 = o; o = align256(o + sizeof(double2) * (size_t)L);
+        lay->off_rt64 = o; o = align256(o + sizeof(double2) * (size_t)d->resp_nwires * lay->fstride);
+        lay->off_x64 = o; o = align256(o + sizeof(double2) * (size_t)d->nwires * lay->fstride);
+        lay->off_y64 = o; o = align256(o + sizeof(double2) * (size_t)d->nwires * lay->fstride);
+        lay->off_g64 = o; o = align256(o + sizeof(double) * (size_t)d->nwires * d->nticks);
+    }
     lay->total = o;
     return WS_OK;
 }
@@ -199,6 +208,16 @@ ws::RasterArgs raster_args(const ws_plane* pl, const ws_depos* d, const ws_param
     a.keep_all = p->p_survive >= 1.0 ? 1 : 0;
     a.exact_max = p->fluct_exact_max;
     a.status = pl->status;
+    a.prec = p->precision;
+    a.lo = nullptr;
+    a.grid64 = nullptr;
+    a.two_DL64 = 2.0 * p->DL_mm2_us;
+    a.two_DT64 = 2.0 * p->DT_mm2_us;
+    a.v64 = p->v_mm_us;
+    a.pitch64 = pl->desc.pitch_mm;
+    a.tick64 = pl->desc.tick_us;
+    a.nsig64 = pl->desc.nsigma;
+    a.p64 = p->p_survive;
     return a;
 }
 
@@ -290,6 +309,12 @@ ws_status ws_plane_create(const ws_plane_desc* desc, const float* response_dev, 
     pl->Radj = (float2*)(base + lay.off_radj);
     pl->Racc = (float2*)(base + lay.off_racc);
     pl->grid2 = (float*)(base + lay.off_grid2);
+    pl->fp64 = desc->fp64 != 0;
+    pl->tw64 = pl->fp64 ? (double2*)(base + lay.off_tw64) : nullptr;
+    pl->Rt64 = pl->fp64 ? (double2*)(base + lay.off_rt64) : nullptr;
+    pl->X64 = pl->fp64 ? (double2*)(base + lay.off_x64) : nullptr;
+    pl->Y64 = pl->fp64 ? (double2*)(base + lay.off_y64) : nullptr;
+    pl->g64 = pl->fp64 ? (double*)(base + lay.off_g64) : nullptr;
     cudaStream_t s = (cudaStream_t)stream;
     cudaError_t e = cudaMemsetAsync(base + lay.off_status, 0, 256, s);
     if (e == cudaSuccess) e = ws::launch_twiddles(pl->tw, lay.plan, s);
@@ -300,6 +325,10 @@ ws_status ws_plane_create(const ws_plane_desc* desc, const float* response_dev, 
                                 desc->resp_nticks, pl->Rt, lay.fstride, lay.nfreq, 1.0f / (float)lay.plan.L, s);
     if (e == cudaSuccess)
         e = ws::launch_adj_coeffs(pl->Rt, pl->Radj, desc->resp_nwires, lay.fstride, lay.nfreq, s);
+    if (e == cudaSuccess && pl->fp64) e = ws::launch_twiddles64(pl->tw64, lay.plan, s);
+    if (e == cudaSuccess && pl->fp64)
+        e = ws::launch_fwd_rows64(lay.plan, pl->tw64, response_dev, false, desc->resp_nwires, desc->resp_nticks,
+                                  desc->resp_nticks, pl->Rt64, lay.fstride, lay.nfreq, 1.0f / (float)lay.plan.L, s);
     // Autotune the wire convolution on this plane's own buffers: each variant
     // once to warm up, then three timed launches; the fastest is kept.
     pl->wconv_variant = 0;
@@ -484,9 +513,40 @@ ws_status ws_simulate(ws_plane* pl, const ws_depos* depos, const ws_params* para
     if (st == WS_OK) st = check_params(params);
     if (st != WS_OK) return st;
     cudaStream_t s = (cudaStream_t)stream;
-    const size_t grid_bytes = sizeof(float) * (size_t)pl->desc.nwires * pl->desc.nticks;
-    WS_LAUNCH(pl, K_MEMSET, s, cudaMemsetAsync(out_dev, 0, grid_bytes, s));
+    const ws_plane_desc& d = pl->desc;
+    const size_t grid_bytes = sizeof(float) * (size_t)d.nwires * d.nticks;
     ws::RasterArgs a = raster_args(pl, depos, params);
+    if (params->precision == WS_PREC_FP64) {
+        if (!pl->fp64) return WS_ERR_WORKSPACE;
+        // FP64 throughout: double grid, double transforms, float output.
+        WS_LAUNCH(pl, K_MEMSET, s, cudaMemsetAsync(pl->g64, 0, 2 * grid_bytes, s));
+        a.grid64 = pl->g64;
+        WS_LAUNCH(pl, K_RASTER_SCATTER, s, ws::launch_raster_scatter(a, out_dev, pl->large, s));
+        WS_LAUNCH(pl, K_FWD, s, ws::launch_fwd_rows64(pl->plan, pl->tw64, pl->g64, true, d.nwires, d.nticks, d.nticks,
+                                                      pl->X64, pl->fstride, pl->nfreq, 1.0f, s));
+        WS_LAUNCH(pl, K_WCONV, s, ws::launch_wire_conv64(pl->X64, pl->Y64, pl->Rt64, d.nwires, pl->nfreq, pl->fstride,
+                                                         d.resp_nwires, d.resp_wire_center,
+                                                         d.conv_mode == WS_CONV_CIRCULAR, s));
+        WS_LAUNCH(pl, K_INV, s, ws::launch_inv_rows64(pl->plan, pl->tw64, pl->Y64, d.nwires, pl->fstride, pl->nfreq,
+                                                      out_dev, d.nticks, d.nticks, s));
+        return WS_OK;
+    }
+    WS_LAUNCH(pl, K_MEMSET, s, cudaMemsetAsync(out_dev, 0, grid_bytes, s));
+    if (params->precision == WS_PREC_FP32_COMP) {
+        // Compensated scatter: the grid's low parts go to grid2 and are added
+        // back by the forward transform.
+        WS_CUDA(cudaMemsetAsync(pl->grid2, 0, grid_bytes, s));
+        a.lo = pl->grid2;
+        WS_LAUNCH(pl, K_RASTER_SCATTER, s, ws::launch_raster_scatter(a, out_dev, pl->large, s));
+        WS_LAUNCH(pl, K_FWD, s, ws::launch_fwd_rows_comp(pl->plan, pl->tw, out_dev, pl->grid2, d.nwires, d.nticks,
+                                                         d.nticks, pl->X, pl->fstride, pl->nfreq, s));
+        WS_LAUNCH(pl, K_WCONV, s, ws::launch_wire_conv(pl->X, pl->Y, pl->Rt, d.nwires, pl->nfreq, pl->fstride,
+                                                       d.resp_nwires, d.resp_wire_center,
+                                                       d.conv_mode == WS_CONV_CIRCULAR, s, pl->wconv_variant));
+        WS_LAUNCH(pl, K_INV, s, ws::launch_inv_rows(pl->plan, pl->tw, pl->Y, d.nwires, pl->fstride, pl->nfreq, out_dev,
+                                                    d.nticks, d.nticks, s));
+        return WS_OK;
+    }
     WS_LAUNCH(pl, K_RASTER_SCATTER, s, ws::launch_raster_scatter(a, out_dev, pl->large, s));
     return convolve_impl(pl, out_dev, out_dev, s);
 }
@@ -498,6 +558,9 @@ ws_status ws_plane_set_response(ws_plane* pl, const float* response_dev, void* s
     WS_CUDA(ws::launch_fwd_rows(pl->plan, pl->tw, response_dev, d.resp_nwires, d.resp_nticks, d.resp_nticks, pl->Rt,
                                 pl->fstride, pl->nfreq, 1.0f / (float)pl->plan.L, s));
     WS_CUDA(ws::launch_adj_coeffs(pl->Rt, pl->Radj, d.resp_nwires, pl->fstride, pl->nfreq, s));
+    if (pl->fp64)
+        WS_CUDA(ws::launch_fwd_rows64(pl->plan, pl->tw64, response_dev, false, d.resp_nwires, d.resp_nticks,
+                                      d.resp_nticks, pl->Rt64, pl->fstride, pl->nfreq, 1.0f / (float)pl->plan.L, s));
     return WS_OK;
 }
 
@@ -600,6 +663,7 @@ ws_status ws_simulate_batch(ws_plane* const* planes, int nplanes, const ws_depos
     if (!depos || !out_dev || nevents < 0) return WS_ERR_INVALID_ARG;
     st = check_params(params);
     if (st != WS_OK) return st;
+    if (params->precision != WS_PREC_FP32) return WS_ERR_UNSUPPORTED_SIZE;
     if (!workspace_dev || !aligned(workspace_dev, 256) || workspace_bytes < lay.total) return WS_ERR_WORKSPACE;
     if (params->event_id + (uint64_t)nevents > (1u << 28)) return WS_ERR_INVALID_ARG;
     const int nunits = nevents * nplanes;
@@ -626,6 +690,7 @@ ws_status ws_simulate_batch(ws_plane* const* planes, int nplanes, const ws_depos
         ws::ConvBatch cb;
         int64_t counts[ws::kMaxUnits];
         rb.n = fb.n = ib.n = cb.n = nu;
+        rb.prec = WS_PREC_FP32;
         for (int j = 0; j < nu; ++j) {
             const int u = u0 + j, e = u / nplanes, pi = u % nplanes;
             ws_plane* pl = planes[pi];

@@ -43,6 +43,11 @@ struct RasterArgs {
     uint32_t evpl;        // (event_id << 4) | plane_id
     int exact_max;
     uint32_t* status;
+    // precision path (WS_PREC_*) and its extra state
+    int prec;
+    float* lo;            // compensated path: low parts of the grid
+    double* grid64;       // FP64 path: the grid in double
+    double two_DL64, two_DT64, v64, pitch64, tick64, nsig64, p64;
 };
 
 // ---- unit tables for launches that cover several (event, plane) units
@@ -145,6 +150,7 @@ cudaError_t launch_raster_scatter(const RasterArgs& a, float* grid, const LargeL
 // Batched raster: unit i rasterises a[i] into grid[i]; one launch pair for all.
 struct RasterBatch {
     int n;
+    int prec;             // one precision for the whole batch
     RasterArgs a[kMaxUnits];
     float* grid[kMaxUnits];
 };
@@ -200,5 +206,11 @@ struct ws_plane {
     ws::LargeList large;  // hand-over list of large patches
     float2* Radj;       // K_w x fstride flipped conjugate taps (adjoint)
     float2* Racc;       // K_w x fstride response-gradient spectra
-    float* grid2;       // nwires x nticks float scratch grid (adjoint)
+    float* grid2;       // nwires x nticks float scratch grid (adjoint, compensated low parts)
+    bool fp64;          // FP64 buffers present
+    double2* tw64;      // FP64 pass twiddles
+    double2* Rt64;      // FP64 response spectrum
+    double2* X64;       // FP64 spectra
+    double2* Y64;
+    double* g64;        // FP64 grid
 };

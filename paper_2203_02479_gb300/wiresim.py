@@ -51,7 +51,7 @@ class WsPlaneDesc(ctypes.Structure):
                 ("resp_nwires", ctypes.c_int32), ("resp_nticks", ctypes.c_int32),
                 ("resp_wire_center", ctypes.c_int32), ("conv_mode", ctypes.c_int32),
                 ("fft_len_tick", ctypes.c_int32), ("nsigma", ctypes.c_double),
-                ("plane_id", ctypes.c_int32)]
+                ("plane_id", ctypes.c_int32), ("fp64", ctypes.c_int32)]
 
 
 class WsDepos(ctypes.Structure):
@@ -298,8 +298,8 @@ class Plane:
 
     def __init__(self, nwires: int, nticks: int, response, *, pitch_mm: float = 5.0,
                  tick_us: float = 0.5, wire_center: int = 10, circular: bool = False,
-                 fft_len_tick: int = 0, nsigma: float = 3.0, plane_id: int = 0, device="cuda",
-                 stream=None):
+                 fft_len_tick: int = 0, nsigma: float = 3.0, plane_id: int = 0, fp64: bool = False,
+                 device="cuda", stream=None):
         torch = _torch()
         resp = response
         if isinstance(resp, np.ndarray):
@@ -308,7 +308,7 @@ class Plane:
         kw, kt = int(self.response.shape[0]), int(self.response.shape[1])
         self.desc = WsPlaneDesc(nwires, nticks, pitch_mm, tick_us, kw, kt, wire_center,
                                 WS_CONV_CIRCULAR if circular else WS_CONV_LINEAR, fft_len_tick,
-                                nsigma, plane_id)
+                                nsigma, plane_id, int(bool(fp64)))
         self.nwires, self.nticks = nwires, nticks
         nbytes = ws_plane_workspace_bytes(self.desc)
         self.workspace = torch.empty(nbytes + 256, dtype=torch.uint8, device=device)
