@@ -460,8 +460,14 @@ __device__ __forceinline__ void lane_weights(const RasterArgs& a, W mu, W sigma,
     lane_axis_weights<W, W>(mu, sigma, delta, nsig, point, first, nb, inv_norm, w);
 }
 
+// Binomial work items of one round are addressed through a byte map when
+// every bin needs at most 8 Philox blocks (exact_max <= 32).
+constexpr int kRoundBins = 64;
+constexpr int kItemMap = kRoundBins * 9;
+constexpr int kBinMap = 1024;    // bins of a 16-depo group addressed through a byte map
+
 template <int MODE, int P>
-__global__ void __launch_bounds__(32 * kSmallWarpsPerBlock, 8)
+__global__ void __launch_bounds__(32 * kSmallWarpsPerBlock, 6)
 raster_small_kernel(const __grid_constant__ RasterUnits U, ws_patches pt, long long* __restrict__ list,
                     unsigned* list_count, unsigned list_cap) {
     using W = typename PrecT<P>::W;
@@ -473,17 +479,22 @@ raster_small_kernel(const __grid_constant__ RasterUnits U, ws_patches pt, long l
     __shared__ int s_k0[NW][G];
     __shared__ int s_w0[NW][G];
     __shared__ int s_nt[NW][G];
+    __shared__ float s_rnt[NW][G];   // 1 / nt
     __shared__ W s_q[NW][G];
-    __shared__ int s_incl[NW][64];   // inclusive scan of the round's exact items
-    __shared__ int s_cnt[NW][64];
-    __shared__ int s_n[NW][64];
-    __shared__ uint32_t s_gbin[NW][64];
-    __shared__ uint32_t s_dep[NW][64];
+    __shared__ unsigned char s_bdep[NW][kBinMap];   // bin -> depo slot
+    __shared__ int s_start[NW][kRoundBins];         // first item of each bin slot
+    __shared__ int s_incl[NW][kRoundBins];          // inclusive item scan (fallback search)
+    __shared__ unsigned char s_item[NW][kItemMap];  // item -> bin slot
+    __shared__ int s_cnt[NW][kRoundBins];
+    __shared__ int s_n[NW][kRoundBins];
+    __shared__ uint32_t s_gbin[NW][kRoundBins];
+    __shared__ uint32_t s_dep[NW][kRoundBins];
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
     const int64_t nwarps = (int64_t)gridDim.x * NW;
     const int dl = lane & (G - 1);      // depo slot of this lane
     const bool tick_lane = lane < G;    // lane pair: tick edges on dl, wire edges on dl + G
+    const unsigned lt_mask = (1u << lane) - 1u;
     const int64_t ngroups = U.gprefix[U.n];
     for (int64_t grp = (int64_t)blockIdx.x * NW + wib; grp < ngroups; grp += nwarps) {
         const int uu = find_unit64(U.gprefix, U.n, grp);
@@ -529,61 +540,67 @@ raster_small_kernel(const __grid_constant__ RasterUnits U, ws_patches pt, long l
             if (lane >= o) incl += y;
         }
         const int total = __shfl_sync(0xffffffffu, incl, 31);
+        const bool use_bmap = total <= kBinMap;
         if (tick_lane) {
             s_off[wib][dl] = incl;
             s_k0[wib][dl] = any ? e.k0 : 0;
             s_w0[wib][dl] = any ? e.w0 : 0;
             s_nt[wib][dl] = ntc;
+            s_rnt[wib][dl] = ntc > 0 ? 1.f / (float)ntc : 0.f;
             s_q[wib][dl] = a.fluct ? q : (sizeof(W) == 8 ? (W)a.p64 : (W)a.p) * q;
+            if (use_bmap)
+                for (int j = incl - nb; j < incl; ++j) s_bdep[wib][j] = (unsigned char)dl;
         }
         __syncwarp();
         const int* off = s_off[wib];
+        // bin g of the group -> depo slot d, index inside its patch, (wire, tick)
+        auto locate = [&](int g, int& d, int& local, int& ia, int& ib) {
+            d = use_bmap ? (int)s_bdep[wib][g] : find_slot<G>(off, g);
+            local = g - (d > 0 ? off[d - 1] : 0);
+            ia = (int)(((float)local + 0.5f) * s_rnt[wib][d]);
+            ib = local - ia * s_nt[wib][d];
+        };
         if (!a.fluct) {
             for (int g = lane; g < total; g += 32) {
-                const int d = find_slot<G>(off, g);
-                const int local = g - (d > 0 ? off[d - 1] : 0);
-                const int nt = s_nt[wib][d];
-                const int ia = local / nt, ib = local - ia * nt;
+                int d, local, ia, ib;
+                locate(g, d, local, ia, ib);
                 const W v = s_q[wib][d] * s_wx[wib][d][ia] * s_wt[wib][d][ib];
                 if (MODE == EMIT_GRID) emit<P>(a, grid, (int64_t)(s_w0[wib][d] + ia) * a.nticks + s_k0[wib][d] + ib, v);
                 else pt.val[pt.off[base + d] + local] = (float)v;
             }
         } else {
-            // Rounds of 64 bins, two per lane: the bin's electron count, its
-            // normal-branch draw if any, then the exact-branch Philox blocks
-            // of the round spread over the lanes two at a time.
-            for (int gb = 0; gb < total; gb += 64) {
-                int N[2], w[2], k[2], cnt[2], ne[2], local[2], d[2];
+            const bool use_imap = a.exact_max <= 32;
+            // Rounds of 64 bins, two per lane.  Each bin's Philox blocks are
+            // work items (one for a normal-approximation bin, ceil(N/4) for
+            // an exact bin), normal ones first, spread over the lanes two at
+            // a time; exact counts add up in shared memory.
+            for (int gb = 0; gb < total; gb += kRoundBins) {
+                int N[2], w[2], k[2], local[2], d[2], ne[2];
+                bool nrm[2];
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
                     const int g = gb + 32 * h + lane;
                     N[h] = 0; w[h] = 0; k[h] = 0; local[h] = 0; d[h] = 0;
                     if (g < total) {
-                        d[h] = find_slot<G>(off, g);
-                        local[h] = g - (d[h] > 0 ? off[d[h] - 1] : 0);
-                        const int nt = s_nt[wib][d[h]];
-                        const int ia = local[h] / nt, ib = local[h] - ia * nt;
+                        int ia, ib;
+                        locate(g, d[h], local[h], ia, ib);
                         w[h] = s_w0[wib][d[h]] + ia;
                         k[h] = s_k0[wib][d[h]] + ib;
                         N[h] = electrons(s_q[wib][d[h]] * s_wx[wib][d[h]][ia] * s_wt[wib][d[h]][ib]);
                     }
-                }
-                uint32_t gbin[2], dep[2];
-                uint4 x[2];
-#pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    gbin[h] = (uint32_t)((int64_t)w[h] * a.nticks + k[h]);
-                    dep[h] = (uint32_t)(base + d[h]);
                     const int items = binomial_items(N[h], a);
-                    cnt[h] = (N[h] > 0 && a.keep_all) ? N[h] : 0;
-                    ne[h] = N[h] <= a.exact_max ? items : 0;
-                    x[h] = make_uint4(0u, 0u, 0u, 0u);
-                    if (items > 0 && N[h] > a.exact_max)
-                        x[h] = philox4x32_10(make_uint4(0u, gbin[h], dep[h], a.evpl), a.key0, a.key1);
+                    nrm[h] = items > 0 && N[h] > a.exact_max;
+                    ne[h] = nrm[h] ? 0 : items;
+                    const int slot = 32 * h + lane;
+                    s_cnt[wib][slot] = (N[h] > 0 && a.keep_all) ? N[h] : 0;
+                    s_n[wib][slot] = N[h];
+                    s_gbin[wib][slot] = (uint32_t)((int64_t)w[h] * a.nticks + k[h]);
+                    s_dep[wib][slot] = (uint32_t)(base + d[h]);
                 }
-#pragma unroll
-                for (int h = 0; h < 2; ++h)
-                    if (binomial_items(N[h], a) > 0 && N[h] > a.exact_max) cnt[h] = normal_draw<P>(x[h], N[h], a);
+                // normal items first (one per bin), then the exact items
+                const unsigned b0 = __ballot_sync(0xffffffffu, nrm[0]);
+                const unsigned b1 = __ballot_sync(0xffffffffu, nrm[1]);
+                const int nn0 = __popc(b0), nn = nn0 + __popc(b1);
                 int inc0 = ne[0], inc1 = ne[1];
 #pragma unroll
                 for (int o = 1; o < 32; o <<= 1) {
@@ -592,18 +609,20 @@ raster_small_kernel(const __grid_constant__ RasterUnits U, ws_patches pt, long l
                     if (lane >= o) { inc0 += y0; inc1 += y1; }
                 }
                 const int tot0 = __shfl_sync(0xffffffffu, inc0, 31);
-                const int tot = tot0 + __shfl_sync(0xffffffffu, inc1, 31);
-                s_incl[wib][lane] = inc0;
-                s_incl[wib][32 + lane] = tot0 + inc1;
-#pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    s_cnt[wib][32 * h + lane] = cnt[h];
-                    s_n[wib][32 * h + lane] = N[h];
-                    s_gbin[wib][32 * h + lane] = gbin[h];
-                    s_dep[wib][32 * h + lane] = dep[h];
+                const int tot = nn + tot0 + __shfl_sync(0xffffffffu, inc1, 31);
+                const int st0 = nrm[0] ? __popc(b0 & lt_mask) : nn + inc0 - ne[0];
+                const int st1 = nrm[1] ? nn0 + __popc(b1 & lt_mask) : nn + tot0 + inc1 - ne[1];
+                s_start[wib][lane] = st0;
+                s_start[wib][32 + lane] = st1;
+                s_incl[wib][lane] = nrm[0] ? 0 : nn + inc0;
+                s_incl[wib][32 + lane] = nrm[1] ? 0 : nn + tot0 + inc1;
+                if (use_imap) {
+                    if (nrm[0]) s_item[wib][st0] = (unsigned char)lane;
+                    if (nrm[1]) s_item[wib][st1] = (unsigned char)(32 + lane);
+                    for (int j = 0; j < ne[0]; ++j) s_item[wib][st0 + j] = (unsigned char)lane;
+                    for (int j = 0; j < ne[1]; ++j) s_item[wib][st1 + j] = (unsigned char)(32 + lane);
                 }
                 __syncwarp();
-                const int* sinc = s_incl[wib];
                 for (int it0 = lane; it0 < tot; it0 += 64) {
                     int sl[2], jj[2];
                     bool ok[2];
@@ -612,8 +631,22 @@ raster_small_kernel(const __grid_constant__ RasterUnits U, ws_patches pt, long l
                     for (int h = 0; h < 2; ++h) {
                         const int it = it0 + 32 * h;
                         ok[h] = it < tot;
-                        sl[h] = ok[h] ? find_slot<64>(sinc, it) : 0;
-                        jj[h] = it - (sl[h] > 0 ? sinc[sl[h] - 1] : 0);
+                        if (!ok[h]) {
+                            sl[h] = 0;
+                        } else if (use_imap) {
+                            sl[h] = s_item[wib][it];
+                        } else if (it < nn) {
+                            // it-th normal bin: position of the it-th set bit
+                            sl[h] = it < nn0 ? (int)__fns(b0, 0, it + 1) : 32 + (int)__fns(b1, 0, it - nn0 + 1);
+                        } else {
+                            // exact items: first slot whose inclusive end exceeds it
+                            int lo = 0;
+#pragma unroll
+                            for (int step = 32; step >= 1; step >>= 1)
+                                if (lo + step - 1 < kRoundBins && s_incl[wib][lo + step - 1] <= it) lo += step;
+                            sl[h] = lo;
+                        }
+                        jj[h] = it - s_start[wib][sl[h]];
                     }
 #pragma unroll
                     for (int h = 0; h < 2; ++h)
@@ -622,8 +655,13 @@ raster_small_kernel(const __grid_constant__ RasterUnits U, ws_patches pt, long l
 #pragma unroll
                     for (int h = 0; h < 2; ++h) {
                         if (!ok[h]) continue;
-                        const int c = exact_count(y[h], s_n[wib][sl[h]] - 4 * jj[h], a.T);
-                        if (c) atomicAdd(&s_cnt[wib][sl[h]], c);
+                        const int n = s_n[wib][sl[h]];
+                        if (n > a.exact_max) {
+                            s_cnt[wib][sl[h]] = normal_draw<P>(y[h], n, a);
+                        } else {
+                            const int c = exact_count(y[h], n - 4 * jj[h], a.T);
+                            if (c) atomicAdd(&s_cnt[wib][sl[h]], c);
+                        }
                     }
                 }
                 __syncwarp();
