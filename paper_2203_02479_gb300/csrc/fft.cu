@@ -730,8 +730,12 @@ cudaError_t launch_inv_rows64(const FftPlan& plan, const double2* tw, const doub
 }
 
 cudaError_t launch_wire_conv_batch(const ConvBatch& cb, int nfreq, int64_t stride, int kw, int center, int circular,
-                                   cudaStream_t s, int variant) {
+                                   cudaStream_t s, int variant, uint32_t* status) {
     if (cb.n <= 0 || nfreq <= 0) return cudaSuccess;
+    if (variant >= 4) {
+        if (circular || !status) return cudaErrorInvalidValue;
+        return launch_wire_conv_tma(cb, nfreq, stride, kw, center, variant - 4, status, s);
+    }
     switch (variant) {
         case 1: launch_wc<16, true, float>(cb, nfreq, stride, kw, center, circular, s); break;
         case 2: launch_wc<8, false, float>(cb, nfreq, stride, kw, center, circular, s); break;
@@ -752,9 +756,11 @@ static ConvBatch one_conv(const void* X, void* Y, const void* Rt, int nwires) {
 }
 
 cudaError_t launch_wire_conv(const float2* X, float2* Y, const float2* Rt, int nwires, int nfreq,
-                             int64_t stride, int kw, int center, int circular, cudaStream_t s, int variant) {
+                             int64_t stride, int kw, int center, int circular, cudaStream_t s, int variant,
+                             uint32_t* status) {
     if (nwires <= 0 || nfreq <= 0) return cudaSuccess;
-    return launch_wire_conv_batch(one_conv(X, Y, Rt, nwires), nfreq, stride, kw, center, circular, s, variant);
+    return launch_wire_conv_batch(one_conv(X, Y, Rt, nwires), nfreq, stride, kw, center, circular, s, variant,
+                                  status);
 }
 
 cudaError_t launch_wire_conv64(const double2* X, double2* Y, const double2* Rt, int nwires, int nfreq, int64_t stride,

@@ -37,10 +37,6 @@ template <> struct PrecT<2> { using W = double; };
 
 __device__ __forceinline__ float erfc_t(float x) { return erfcf(x); }
 __device__ __forceinline__ double erfc_t(double x) { return erfc(x); }
-__device__ __forceinline__ float erf_t(float x) { return erff(x); }
-__device__ __forceinline__ double erf_t(double x) { return erf(x); }
-__device__ __forceinline__ float sqrt_t(float x) { return sqrtf(x); }
-__device__ __forceinline__ double sqrt_t(double x) { return sqrt(x); }
 
 // Philox4x32-10 (Salmon et al., SC'11): ten rounds of two 32x32 multiplies
 // whose high halves are mixed with the other counter words and the key; the

@@ -1,0 +1,259 @@
+// Wire convolution fed by the tensor memory accelerator (linear mode).
+//
+// Same sum as wire_conv_kernel in fft.cu (Y[w][k] = sum_r Rt[r][k]
+// X[w + c - r][k], the wire axis of Eq. 2's product in the tick-frequency
+// domain), but the (B + K - 1) x 128-column input tiles arrive by 2D TMA
+// copies (cp.async.bulk.tensor) that complete on shared-memory mbarriers:
+// persistent CTAs double-buffer, issuing tile t + 1 while computing tile t.
+// Rows outside the grid come back as zeros from the copy engine's
+// out-of-bounds fill, which is exactly linear mode's zero padding.
+//
+// Every mbarrier wait is bounded: if a copy never lands, the CTA sets
+// WS_DEV_TIMEOUT in the plane's status word, waits (bounded) for its other
+// copy in flight and returns; it never spins forever.
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <cudaTypedefs.h>
+#include <stdint.h>
+
+#include <mutex>
+
+#include "ws_internal.cuh"
+
+namespace ws {
+namespace {
+
+constexpr int kCols = 128;                 // complex columns per tile (one thread each)
+constexpr int kWaitIters = 1 << 20;        // try_wait attempts before giving up
+
+struct TmaConvUnits {
+    CUtensorMap map[kMaxUnits];            // X of each unit: {2 * stride floats, nwires rows}
+    int n;
+    int prefix[kMaxUnits + 1];             // cumulative tiles
+    int nwires[kMaxUnits];
+    void* Y[kMaxUnits];
+    const void* Rt[kMaxUnits];
+};
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(bar)) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+    const uint32_t b = smem_addr(bar);
+    for (int it = 0; it < kWaitIters; ++it) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(done)
+            : "r"(b), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+// 2D tile copy of the box at (x, y) into dst, completing on bar.
+__device__ __forceinline__ void tma_load_tile(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar,
+                                              uint32_t bytes) {
+    const uint32_t b = smem_addr(bar);
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(b), "r"(bytes) : "memory");
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+        ::"r"(smem_addr(dst)), "l"(map), "r"(x), "r"(y), "r"(b)
+        : "memory");
+}
+
+template <int K, int B, bool KARATSUBA>
+__global__ void __launch_bounds__(kCols)
+wire_conv_tma_kernel(const __grid_constant__ TmaConvUnits U, int nfreq, int64_t stride, int kw, int center,
+                     int nkblocks, uint32_t* status) {
+    constexpr int ROWS = B + K - 1;
+    constexpr uint32_t TILE_BYTES = ROWS * kCols * sizeof(float2);
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ __align__(8) uint64_t bar[2];
+    auto buf = [&](int st) { return reinterpret_cast<float2*>(smem + (st ? TILE_BYTES : 0u)); };
+    const int total = U.prefix[U.n];
+    auto tile_of = [&](int t, int& u, int& k0, int& w0) {
+        int lo = 0, hi = U.n - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (U.prefix[mid] <= t) lo = mid; else hi = mid - 1;
+        }
+        u = lo;
+        const int tt = t - U.prefix[u];
+        k0 = (tt % nkblocks) * kCols;
+        w0 = (tt / nkblocks) * B;
+    };
+    auto issue = [&](int t, int st) {
+        int u, k0, w0;
+        tile_of(t, u, k0, w0);
+        tma_load_tile(buf(st), &U.map[u], 2 * k0, w0 + center - (K - 1), &bar[st], TILE_BYTES);
+    };
+    if (threadIdx.x == 0) {
+        mbar_init(&bar[0]);
+        mbar_init(&bar[1]);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    int t = blockIdx.x;
+    if (t < total && threadIdx.x == 0) issue(t, 0);
+    uint32_t parity[2] = {0u, 0u};
+    bool inflight_next = false;
+    for (int i = 0; t < total; ++i, t += gridDim.x) {
+        const int st = i & 1;
+        const int tn = t + gridDim.x;
+        inflight_next = tn < total;
+        if (inflight_next && threadIdx.x == 0) issue(tn, st ^ 1);
+        const bool ok = mbar_wait(&bar[st], parity[st]);
+        parity[st] ^= 1u;
+        if (__syncthreads_or(!ok)) {
+            // A copy never landed: flag it, let the other copy (if any) drain,
+            // and leave without touching the buffers again.
+            if (threadIdx.x == 0) atomicOr(status, WS_DEV_TIMEOUT);
+            if (inflight_next) mbar_wait(&bar[st ^ 1], parity[st ^ 1]);
+            return;
+        }
+        int u, k0, w0;
+        tile_of(t, u, k0, w0);
+        const int k = k0 + threadIdx.x;
+        const int nwires = U.nwires[u];
+        float2* __restrict__ Y = static_cast<float2*>(U.Y[u]);
+        const float2* __restrict__ Rt = static_cast<const float2*>(U.Rt[u]);
+        const float2* col = buf(st) + threadIdx.x;
+        if (k < nfreq) {
+            if constexpr (KARATSUBA) {
+                float cc[K], cm[K], cp[K];
+#pragma unroll
+                for (int r = 0; r < K; ++r) {
+                    const float2 v = r < kw ? __ldg(&Rt[(int64_t)r * stride + k]) : make_float2(0.f, 0.f);
+                    cc[r] = v.x;
+                    cm[r] = v.y - v.x;
+                    cp[r] = v.x + v.y;
+                }
+                float k1[B], k2[B], k3[B];
+#pragma unroll
+                for (int b = 0; b < B; ++b) k1[b] = k2[b] = k3[b] = 0.f;
+#pragma unroll
+                for (int uu = 0; uu < ROWS; ++uu) {
+                    const float2 x = col[uu * kCols];
+                    const float sab = x.x + x.y;
+#pragma unroll
+                    for (int b = 0; b < B; ++b) {
+                        const int r = b + K - 1 - uu;
+                        if (r >= 0 && r < K) {
+                            k1[b] = fmaf(cc[r], sab, k1[b]);
+                            k2[b] = fmaf(cm[r], x.x, k2[b]);
+                            k3[b] = fmaf(cp[r], x.y, k3[b]);
+                        }
+                    }
+                }
+#pragma unroll
+                for (int b = 0; b < B; ++b)
+                    if (w0 + b < nwires) Y[(int64_t)(w0 + b) * stride + k] = make_float2(k1[b] - k3[b], k1[b] + k2[b]);
+            } else {
+                float2 c[K];
+#pragma unroll
+                for (int r = 0; r < K; ++r) c[r] = r < kw ? __ldg(&Rt[(int64_t)r * stride + k]) : make_float2(0.f, 0.f);
+                float2 acc[B];
+#pragma unroll
+                for (int b = 0; b < B; ++b) acc[b] = make_float2(0.f, 0.f);
+#pragma unroll
+                for (int uu = 0; uu < ROWS; ++uu) {
+                    const float2 x = col[uu * kCols];
+#pragma unroll
+                    for (int b = 0; b < B; ++b) {
+                        const int r = b + K - 1 - uu;
+                        if (r >= 0 && r < K) {
+                            acc[b].x = fmaf(c[r].x, x.x, fmaf(-c[r].y, x.y, acc[b].x));
+                            acc[b].y = fmaf(c[r].x, x.y, fmaf(c[r].y, x.x, acc[b].y));
+                        }
+                    }
+                }
+#pragma unroll
+                for (int b = 0; b < B; ++b)
+                    if (w0 + b < nwires) Y[(int64_t)(w0 + b) * stride + k] = acc[b];
+            }
+        }
+        __syncthreads();   // buffer st is free for the copy issued next iteration
+    }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+    static std::once_flag once;
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    });
+    return fn;
+}
+
+template <int B, bool KS>
+cudaError_t launch_tma(const ConvBatch& cb, int nfreq, int64_t stride, int kw, int center, uint32_t* status,
+                       cudaStream_t s) {
+    constexpr int K = kMaxRespWires;
+    constexpr int ROWS = B + K - 1;
+    const PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
+    if (!enc) return cudaErrorNotSupported;
+    TmaConvUnits U;
+    const int nkblocks = (nfreq + kCols - 1) / kCols;
+    U.n = cb.n;
+    U.prefix[0] = 0;
+    for (int i = 0; i < cb.n; ++i) {
+        const cuuint64_t dims[2] = {(cuuint64_t)(2 * stride), (cuuint64_t)cb.nwires[i]};
+        const cuuint64_t strides[1] = {(cuuint64_t)(2 * stride * sizeof(float))};
+        const cuuint32_t box[2] = {2 * kCols, ROWS};
+        const cuuint32_t estr[2] = {1, 1};
+        const CUresult r = enc(&U.map[i], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void*>(cb.X[i]), dims,
+                               strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+        U.nwires[i] = cb.nwires[i];
+        U.Y[i] = cb.Y[i];
+        U.Rt[i] = cb.Rt[i];
+        U.prefix[i + 1] = U.prefix[i] + nkblocks * ((cb.nwires[i] + B - 1) / B);
+    }
+    const int total = U.prefix[cb.n];
+    if (total <= 0) return cudaSuccess;
+    const int smem = 2 * ROWS * kCols * (int)sizeof(float2);
+    cudaError_t e = cudaFuncSetAttribute((const void*)wire_conv_tma_kernel<K, B, KS>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, wire_conv_tma_kernel<K, B, KS>, kCols, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) per_sm = 1;
+    int grid = num_sms() * per_sm;
+    if (grid > total) grid = total;
+    wire_conv_tma_kernel<K, B, KS><<<grid, kCols, smem, s>>>(U, nfreq, stride, kw, center, nkblocks, status);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+bool tma_available() { return encode_fn() != nullptr; }
+
+cudaError_t launch_wire_conv_tma(const ConvBatch& cb, int nfreq, int64_t stride, int kw, int center, int variant,
+                                 uint32_t* status, cudaStream_t s) {
+    if (cb.n <= 0 || nfreq <= 0) return cudaSuccess;
+    switch (variant) {
+        case 1: return launch_tma<16, true>(cb, nfreq, stride, kw, center, status, s);
+        case 2: return launch_tma<8, false>(cb, nfreq, stride, kw, center, status, s);
+        case 3: return launch_tma<8, true>(cb, nfreq, stride, kw, center, status, s);
+        default: return launch_tma<16, false>(cb, nfreq, stride, kw, center, status, s);
+    }
+}
+
+}  // namespace ws

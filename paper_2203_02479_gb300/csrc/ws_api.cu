@@ -227,7 +227,7 @@ ws_status convolve_impl(ws_plane* pl, const float* grid, float* out, cudaStream_
                                                 pl->fstride, pl->nfreq, 1.0f, s));
     WS_LAUNCH(pl, K_WCONV, s, ws::launch_wire_conv(pl->X, pl->Y, pl->Rt, d.nwires, pl->nfreq, pl->fstride,
                                                    d.resp_nwires, d.resp_wire_center,
-                                                   d.conv_mode == WS_CONV_CIRCULAR, s, pl->wconv_variant));
+                                                   d.conv_mode == WS_CONV_CIRCULAR, s, pl->wconv_variant, pl->status));
     WS_LAUNCH(pl, K_INV, s, ws::launch_inv_rows(pl->plan, pl->tw, pl->Y, d.nwires, pl->fstride, pl->nfreq, out,
                                                 d.nticks, d.nticks, s));
     return WS_OK;
@@ -338,14 +338,15 @@ ws_status ws_plane_create(const ws_plane_desc* desc, const float* response_dev, 
         e = cudaEventCreate(&t0);
         if (e == cudaSuccess) e = cudaEventCreate(&t1);
         float best = 1e30f;
-        for (int v = 0; v < ws::kWireConvVariants && e == cudaSuccess; ++v) {
-            const int circ = desc->conv_mode == WS_CONV_CIRCULAR;
+        const int circ = desc->conv_mode == WS_CONV_CIRCULAR;
+        const int nvar = (circ || !ws::tma_available()) ? 4 : ws::kWireConvVariants;
+        for (int v = 0; v < nvar && e == cudaSuccess; ++v) {
             e = ws::launch_wire_conv(pl->X, pl->Y, pl->Rt, desc->nwires, lay.nfreq, lay.fstride, desc->resp_nwires,
-                                     desc->resp_wire_center, circ, s, v);
+                                     desc->resp_wire_center, circ, s, v, pl->status);
             if (e == cudaSuccess) e = cudaEventRecord(t0, s);
             for (int r = 0; r < 3 && e == cudaSuccess; ++r)
                 e = ws::launch_wire_conv(pl->X, pl->Y, pl->Rt, desc->nwires, lay.nfreq, lay.fstride,
-                                         desc->resp_nwires, desc->resp_wire_center, circ, s, v);
+                                         desc->resp_nwires, desc->resp_wire_center, circ, s, v, pl->status);
             if (e == cudaSuccess) e = cudaEventRecord(t1, s);
             if (e == cudaSuccess) e = cudaEventSynchronize(t1);
             float ms = 0.f;
@@ -384,6 +385,7 @@ ws_status ws_plane_destroy(ws_plane* plane) {
 
 ws_status ws_plane_set_wire_conv_variant(ws_plane* pl, int variant) {
     if (!pl || variant < 0 || variant >= ws::kWireConvVariants) return WS_ERR_INVALID_ARG;
+    if (variant >= 4 && (pl->desc.conv_mode == WS_CONV_CIRCULAR || !ws::tma_available())) return WS_ERR_UNSUPPORTED_SIZE;
     pl->wconv_variant = variant;
     return WS_OK;
 }
@@ -542,7 +544,7 @@ ws_status ws_simulate(ws_plane* pl, const ws_depos* depos, const ws_params* para
                                                          d.nticks, pl->X, pl->fstride, pl->nfreq, s));
         WS_LAUNCH(pl, K_WCONV, s, ws::launch_wire_conv(pl->X, pl->Y, pl->Rt, d.nwires, pl->nfreq, pl->fstride,
                                                        d.resp_nwires, d.resp_wire_center,
-                                                       d.conv_mode == WS_CONV_CIRCULAR, s, pl->wconv_variant));
+                                                       d.conv_mode == WS_CONV_CIRCULAR, s, pl->wconv_variant, pl->status));
         WS_LAUNCH(pl, K_INV, s, ws::launch_inv_rows(pl->plan, pl->tw, pl->Y, d.nwires, pl->fstride, pl->nfreq, out_dev,
                                                     d.nticks, d.nticks, s));
         return WS_OK;
@@ -581,7 +583,7 @@ ws_status ws_simulate_backward(ws_plane* pl, const ws_depos* depos, const ws_par
                                                 pl->fstride, pl->nfreq, 1.0f, s));
     WS_LAUNCH(pl, K_WCONV, s, ws::launch_wire_conv(pl->X, pl->Y, pl->Radj, d.nwires, pl->nfreq, pl->fstride,
                                                    d.resp_nwires, d.resp_nwires - 1 - d.resp_wire_center, circ, s,
-                                                   pl->wconv_variant));
+                                                   pl->wconv_variant, pl->status));
     WS_LAUNCH(pl, K_INV, s, ws::launch_inv_rows(pl->plan, pl->tw, pl->Y, d.nwires, pl->fstride, pl->nfreq,
                                                 pl->grid2, d.nticks, d.nticks, s));
     ws::RasterArgs a = raster_args(pl, depos, params);
@@ -719,7 +721,8 @@ ws_status ws_simulate_batch(ws_plane* const* planes, int nplanes, const ws_depos
         WS_LAUNCH(p0, K_FWD, s, ws::launch_fwd_rows_batch(p0->plan, p0->tw, fb, d0.nticks, d0.nticks, p0->fstride,
                                                           p0->nfreq, 1.0f, s));
         WS_LAUNCH(p0, K_WCONV, s, ws::launch_wire_conv_batch(cb, p0->nfreq, p0->fstride, d0.resp_nwires,
-                                                             d0.resp_wire_center, circ, s, p0->wconv_variant));
+                                                             d0.resp_wire_center, circ, s, p0->wconv_variant,
+                                                             p0->status));
         WS_LAUNCH(p0, K_INV, s, ws::launch_inv_rows_batch(p0->plan, p0->tw, ib, p0->fstride, p0->nfreq, d0.nticks,
                                                           d0.nticks, s));
     }

@@ -107,7 +107,7 @@ cudaError_t launch_fwd_rows_batch(const FftPlan& plan, const float2* tw, const R
 cudaError_t launch_inv_rows_batch(const FftPlan& plan, const float2* tw, const RowBatch& rb, int64_t in_stride,
                                   int nfreq, int ncols, int64_t out_stride, cudaStream_t s);
 cudaError_t launch_wire_conv_batch(const ConvBatch& cb, int nfreq, int64_t stride, int kw, int center, int circular,
-                                   cudaStream_t s, int variant);
+                                   cudaStream_t s, int variant, uint32_t* status = nullptr);
 // FP64 path (precision WS_PREC_FP64): double twiddles, spectra and sums;
 // the forward transform reads float or double rows, the inverse writes float.
 cudaError_t launch_twiddles64(double2* tw, const FftPlan& plan, cudaStream_t s);
@@ -122,11 +122,17 @@ cudaError_t launch_wire_conv64(const double2* X, double2* Y, const double2* Rt, 
 cudaError_t launch_fwd_rows_comp(const FftPlan& plan, const float2* tw, const float* hi, const float* lo, int nrows,
                                  int ncols, int64_t in_stride, float2* out, int64_t out_stride, int nfreq,
                                  cudaStream_t s);
-// variant: 0 = 16 wires per thread, 1 = 16 Karatsuba, 2 = 8, 3 = 8 Karatsuba.
-constexpr int kWireConvVariants = 4;
+// variant: 0 = 16 wires per thread, 1 = 16 Karatsuba, 2 = 8, 3 = 8 Karatsuba,
+// with plain loads; 4..7 the same four fed by TMA tile copies (linear mode
+// only; they report a copy that never lands in *status).
+constexpr int kWireConvVariants = 8;
 cudaError_t launch_wire_conv(const float2* X, float2* Y, const float2* Rt, int nwires,
                              int nfreq, int64_t stride, int kw, int center, int circular,
-                             cudaStream_t s, int variant = 0);
+                             cudaStream_t s, int variant = 0, uint32_t* status = nullptr);
+// TMA-fed wire convolution (wconv_tma.cu), variant 0..3 as above.
+bool tma_available();
+cudaError_t launch_wire_conv_tma(const ConvBatch& cb, int nfreq, int64_t stride, int kw, int center, int variant,
+                                 uint32_t* status, cudaStream_t s);
 
 // Hand-over list of depos whose patches are too large for the lane-per-depo
 // raster kernel (workspace-resident; count and done must start at zero and
