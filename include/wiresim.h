@@ -151,8 +151,13 @@ typedef struct {
     int32_t radices[16];
     size_t workspace_bytes;
     int32_t wire_conv_variant;  /* autotuned wire-convolution kernel: wire
-                                   block 16 (0, 1) or 8 (2, 3), Karatsuba
-                                   three-product taps (1, 3)                */
+                                   block 16 (0, 1, 4, 5) or 8 (2, 3, 6, 7),
+                                   Karatsuba three-product taps (odd), tiles
+                                   by TMA (4..7, linear mode only)          */
+    int32_t row_fft_fixed_shape; /* 1: this L_t's FP32 tick-axis transforms
+                                   run kernels compiled for its radix plan
+                                   (first and last passes on global memory);
+                                   0: the generic kernels                   */
 } ws_plane_info;
 
 typedef struct ws_plane ws_plane;

@@ -418,6 +418,199 @@ inv_rows_kernel(FftPlan plan, const cplx<S>* __restrict__ tw, const __grid_const
     }
 }
 
+// ------------------------------------------- row transforms of fixed shape
+// For the common transform lengths the radix sequence, L and every pass's
+// Ns are template constants: index arithmetic folds, each kernel holds only
+// its own passes (the generic kernels above carry all thirteen radices and
+// their code outgrows the instruction cache when edge passes are fused), and
+// the first and last passes talk to global memory directly:
+//   forward: pass 0 loads the two input rows; the last pass pairs butterflies
+//            j and Ns - j so that each thread holds Z_k and Z_{L-k} and
+//            writes the split spectra A_k, B_k;
+//   inverse: pass 0 reads the Hermitian extension of both half spectra; the
+//            last pass stores the real and imaginary rows.
+// Only the middle passes go through shared memory.
+template <int NT, int... Rs>
+struct Shape {
+    static constexpr int threads = NT;
+    static constexpr int npass = sizeof...(Rs);
+    static constexpr int radix[npass] = {Rs...};
+    static constexpr int L = (Rs * ...);
+    static constexpr int ns(int p) {
+        int n = 1;
+        for (int i = 0; i < p; ++i) n *= radix[i];
+        return n;
+    }
+};
+
+template <int R, bool INV, typename C>
+__device__ __forceinline__ void twiddle_inputs(C* v, C w) {
+    C wp[R];
+    wp[1] = w;
+    if (INV) wp[1].y = -wp[1].y;
+#pragma unroll
+    for (int r = 2; r < R; ++r) wp[r] = cmul_tw<false>(wp[r / 2], wp[r - r / 2]);
+#pragma unroll
+    for (int r = 1; r < R; ++r) v[r] = cmul_tw<false>(v[r], wp[r]);
+}
+
+// One Stockham pass (same butterfly as stockham_pass) reading ld(i) and
+// writing st(i, value).
+template <int R, int Ns, int L, int NT, bool INV, typename C, typename Ld, typename St>
+__device__ __forceinline__ void io_pass(const C* __restrict__ tw, Ld ld, St st) {
+    constexpr int nb = L / R;
+#pragma unroll 1
+    for (int j = threadIdx.x; j < nb; j += NT) {
+        const int k = j % Ns;
+        C v[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[r] = ld(j + r * nb);
+        if (Ns > 1) twiddle_inputs<R, INV>(v, tw[k]);
+        Dft<R, INV, C>::run(v);
+        const int d = (j - k) * R + k;
+#pragma unroll
+        for (int r = 0; r < R; ++r) st(d + r * Ns, v[r]);
+    }
+}
+
+// Last forward pass (Ns R = L: butterfly j yields Z[j + r Ns]).  Z[L - k]
+// for k = j + r Ns is output R-1-r of butterfly Ns - j, or output (R-r) mod R
+// of butterfly 0 when j = 0; out(k, Z_k, Z_{L-k}) for every k < nfreq.
+template <int R, int Ns, int L, int NT, typename C, typename Ld, typename Out>
+__device__ __forceinline__ void fwd_last_pass(const C* __restrict__ tw, Ld ld, int nfreq, Out out) {
+    static_assert(Ns * R == L, "last pass");
+    constexpr int ntask = Ns / 2 + 1;
+#pragma unroll 1
+    for (int j = threadIdx.x; j < ntask; j += NT) {
+        const int jm = Ns - j;
+        const bool two = j > 0 && jm != j;
+        C v[R], w[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[r] = ld(j + r * Ns);
+        if (Ns > 1) twiddle_inputs<R, false>(v, tw[j]);
+        Dft<R, false, C>::run(v);
+        if (two) {
+#pragma unroll
+            for (int r = 0; r < R; ++r) w[r] = ld(jm + r * Ns);
+            twiddle_inputs<R, false>(w, tw[jm]);
+            Dft<R, false, C>::run(w);
+        }
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int k = j + r * Ns;
+            if (k < nfreq) out(k, v[r], j == 0 ? v[(R - r) % R] : (two ? w[R - 1 - r] : v[R - 1 - r]));
+        }
+        if (two) {
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                const int k = jm + r * Ns;
+                if (k < nfreq) out(k, w[r], v[R - 1 - r]);
+            }
+        }
+    }
+}
+
+// Passes 1 .. npass-2 of shape SH in shared memory, pass p reading buf[(p-1)&1]
+// and writing buf[p&1].
+template <typename SH, bool INV, typename C>
+__device__ __forceinline__ void shape_middle(const FftPlan& plan, C* buf0, C* buf1, const C* __restrict__ tw) {
+    sfor<SH::npass>([&](auto pc) {
+        constexpr int p = decltype(pc)::value;
+        if constexpr (p > 0 && p + 1 < SH::npass) {
+            constexpr int R = SH::radix[p], Ns = SH::ns(p);
+            C* src = (p - 1) & 1 ? buf1 : buf0;
+            C* dst = p & 1 ? buf1 : buf0;
+            io_pass<R, Ns, SH::L, SH::threads, INV>(tw + plan.twoff[p], [&](int i) { return src[i]; },
+                                       [&](int i, C v) { dst[i] = v; });
+            __syncthreads();
+        }
+    });
+}
+
+template <typename SH>
+__global__ void __launch_bounds__(SH::threads, 2)
+fwd_rows_shape_kernel(FftPlan plan, const float2* __restrict__ tw, const __grid_constant__ RowUnits U, int ncols,
+                      int64_t in_stride, int64_t out_stride, int nfreq, float scale) {
+    using C = float2;
+    constexpr int L = SH::L, last = SH::npass - 1;
+    static_assert(SH::npass >= 2, "edge passes");
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* buf0 = reinterpret_cast<C*>(smem_raw);
+    C* buf1 = buf0 + ((L + 1) & ~1);
+    const int u = find_unit(U.prefix, U.n, (int)blockIdx.x);
+    const float* __restrict__ in = static_cast<const float*>(U.in[u]);
+    const float* __restrict__ in2 = static_cast<const float*>(U.in2[u]);
+    const int r0 = 2 * ((int)blockIdx.x - U.prefix[u]);
+    const bool has_b = r0 + 1 < U.nrows[u];
+    const float* __restrict__ pa = in + (int64_t)r0 * in_stride;
+    const float* __restrict__ pb = has_b ? pa + in_stride : pa;
+    const float* __restrict__ la = in2 ? in2 + (int64_t)r0 * in_stride : nullptr;
+    const float* __restrict__ lb = (in2 && has_b) ? la + in_stride : la;
+    const int nload = ncols < L ? ncols : L;
+    io_pass<SH::radix[0], 1, L, SH::threads, false>(tw, [&](int n) {
+        float xa = 0.f, xb = 0.f;
+        if (n < nload) {
+            xa = __ldg(pa + n);
+            if (has_b) xb = __ldg(pb + n);
+            if (in2) {
+                xa += __ldg(la + n);
+                if (has_b) xb += __ldg(lb + n);
+            }
+        }
+        return make_float2(xa, xb);
+    }, [&](int i, C v) { buf0[i] = v; });
+    __syncthreads();
+    shape_middle<SH, false>(plan, buf0, buf1, tw);
+    const C* z = (last - 1) & 1 ? buf1 : buf0;
+    C* oa = static_cast<C*>(U.out[u]) + (int64_t)r0 * out_stride;
+    C* ob = oa + out_stride;
+    const float h = 0.5f * scale;
+    fwd_last_pass<SH::radix[last], SH::ns(last), L, SH::threads>(tw + plan.twoff[last], [&](int i) { return z[i]; }, nfreq,
+                                                    [&](int k, C zk, C zm) {
+        oa[k] = make_float2(h * (zk.x + zm.x), h * (zk.y - zm.y));
+        if (has_b) ob[k] = make_float2(h * (zk.y + zm.y), h * (zm.x - zk.x));
+    });
+}
+
+template <typename SH>
+__global__ void __launch_bounds__(SH::threads, 2)
+inv_rows_shape_kernel(FftPlan plan, const float2* __restrict__ tw, const __grid_constant__ RowUnits U,
+                      int64_t in_stride, int nfreq, int ncols, int64_t out_stride) {
+    using C = float2;
+    constexpr int L = SH::L, last = SH::npass - 1;
+    static_assert(SH::npass >= 2, "edge passes");
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* buf0 = reinterpret_cast<C*>(smem_raw);
+    C* buf1 = buf0 + ((L + 1) & ~1);
+    const int u = find_unit(U.prefix, U.n, (int)blockIdx.x);
+    const int r0 = 2 * ((int)blockIdx.x - U.prefix[u]);
+    const bool has_b = r0 + 1 < U.nrows[u];
+    const C* __restrict__ ya = static_cast<const C*>(U.in[u]) + (int64_t)r0 * in_stride;
+    const C* __restrict__ yb = has_b ? ya + in_stride : ya;
+    io_pass<SH::radix[0], 1, L, SH::threads, true>(tw, [&](int k) {
+        const bool upper = k >= nfreq;
+        const int kk = upper ? L - k : k;
+        C A = __ldg(ya + kk);
+        C B = has_b ? __ldg(yb + kk) : make_float2(0.f, 0.f);
+        if (kk == 0 || (L % 2 == 0 && 2 * kk == L)) { A.y = 0.f; B.y = 0.f; }
+        if (upper) { A.y = -A.y; B.y = -B.y; }
+        return make_float2(A.x - B.y, A.y + B.x);
+    }, [&](int i, C v) { buf0[i] = v; });
+    __syncthreads();
+    shape_middle<SH, true>(plan, buf0, buf1, tw);
+    const C* z = (last - 1) & 1 ? buf1 : buf0;
+    float* oa = static_cast<float*>(U.out[u]) + (int64_t)r0 * out_stride;
+    float* ob = oa + out_stride;
+    const int nst = ncols < L ? ncols : L;
+    io_pass<SH::radix[last], SH::ns(last), L, SH::threads, true>(tw + plan.twoff[last], [&](int i) { return z[i]; },
+                                                    [&](int n, C v) {
+        if (n < nst) {
+            oa[n] = v.x;
+            if (has_b) ob[n] = v.y;
+        }
+    });
+}
+
 // Register-blocked wire convolution in the tick-frequency domain.  A CTA
 // owns 128 frequency columns x B output wires; it stages the B + K - 1 input
 // rows those outputs need in shared memory with 16-byte loads (zeros outside
@@ -637,10 +830,59 @@ static RowUnits row_units(const RowBatch& rb, bool* aligned16) {
     return U;
 }
 
+// Fixed-shape kernels for the FP32 transforms (greedy radix plans of the
+// lengths below); other plans run the generic kernels.
+using FwdShapeFn = void (*)(FftPlan, const float2*, const RowUnits, int, int64_t, int64_t, int, float);
+using InvShapeFn = void (*)(FftPlan, const float2*, const RowUnits, int64_t, int, int, int64_t);
+struct ShapeKernels {
+    int npass;
+    int radix[4];
+    FwdShapeFn fwd;
+    int fwd_threads;
+    InvShapeFn inv;
+    int inv_threads;
+};
+constexpr int kFwdShapeThreads = 320;
+constexpr int kInvShapeThreads = 320;
+#define WS_SHAPE3(A, B, C)                                                                                  \
+    {3, {A, B, C}, fwd_rows_shape_kernel<Shape<kFwdShapeThreads, A, B, C>>, kFwdShapeThreads,                \
+     inv_rows_shape_kernel<Shape<kInvShapeThreads, A, B, C>>, kInvShapeThreads}
+static const ShapeKernels kShapes[] = {
+    WS_SHAPE3(25, 25, 10),  // 6250: linear convolution of 6000 ticks with a 200-tick response
+    WS_SHAPE3(25, 16, 15),  // 6000: circular convolution of 6000 ticks
+    WS_SHAPE3(25, 16, 16),  // 6400
+    WS_SHAPE3(25, 16, 8),   // 3200
+    WS_SHAPE3(25, 16, 3),   // 1200
+};
+#undef WS_SHAPE3
+
+static const ShapeKernels* shape_kernels(const FftPlan& plan) {
+    for (const ShapeKernels& k : kShapes) {
+        bool eq = k.npass == plan.npass;
+        for (int p = 0; eq && p < plan.npass; ++p) eq = k.radix[p] == plan.radix[p];
+        if (eq) return &k;
+    }
+    return nullptr;
+}
+
+bool row_fft_fixed_shape(const FftPlan& plan) { return shape_kernels(plan) != nullptr; }
+
 template <typename S, typename TIN>
 static cudaError_t fwd_rows_t(const FftPlan& plan, const cplx<S>* tw, const RowBatch& rb, int ncols,
                               int64_t in_stride, int64_t out_stride, int nfreq, float scale, cudaStream_t s) {
     if (rb.n <= 0) return cudaSuccess;
+    if constexpr (std::is_same<S, float>::value && std::is_same<TIN, float>::value) {
+        if (const ShapeKernels* k = shape_kernels(plan)) {
+            const int smem = 2 * ((plan.L + 1) & ~1) * (int)sizeof(float2);
+            cudaError_t e = set_smem((const void*)k->fwd, smem);
+            if (e != cudaSuccess) return e;
+            bool al = false;
+            const RowUnits U = row_units(rb, &al);
+            if (U.prefix[rb.n] <= 0) return cudaSuccess;
+            k->fwd<<<U.prefix[rb.n], k->fwd_threads, smem, s>>>(plan, tw, U, ncols, in_stride, out_stride, nfreq, scale);
+            return cudaGetLastError();
+        }
+    }
     const int smem = 2 * ((plan.L + 1) & ~1) * (int)sizeof(cplx<S>);
     cudaError_t e = set_smem((const void*)fwd_rows_kernel<S, TIN>, smem);
     if (e != cudaSuccess) return e;
@@ -658,6 +900,18 @@ template <typename S>
 static cudaError_t inv_rows_t(const FftPlan& plan, const cplx<S>* tw, const RowBatch& rb, int64_t in_stride,
                               int nfreq, int ncols, int64_t out_stride, cudaStream_t s) {
     if (rb.n <= 0) return cudaSuccess;
+    if constexpr (std::is_same<S, float>::value) {
+        if (const ShapeKernels* k = shape_kernels(plan)) {
+            const int smem = 2 * ((plan.L + 1) & ~1) * (int)sizeof(float2);
+            cudaError_t e = set_smem((const void*)k->inv, smem);
+            if (e != cudaSuccess) return e;
+            bool al = false;
+            const RowUnits U = row_units(rb, &al);
+            if (U.prefix[rb.n] <= 0) return cudaSuccess;
+            k->inv<<<U.prefix[rb.n], k->inv_threads, smem, s>>>(plan, tw, U, in_stride, nfreq, ncols, out_stride);
+            return cudaGetLastError();
+        }
+    }
     const int smem = 2 * ((plan.L + 1) & ~1) * (int)sizeof(cplx<S>);
     cudaError_t e = set_smem((const void*)inv_rows_kernel<S>, smem);
     if (e != cudaSuccess) return e;

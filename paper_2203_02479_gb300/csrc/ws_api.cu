@@ -454,6 +454,7 @@ ws_status ws_plane_get_info(const ws_plane* pl, ws_plane_info* info) {
     for (int i = 0; i < pl->plan.npass; ++i) info->radices[i] = pl->plan.radix[i];
     info->workspace_bytes = pl->ws_bytes;
     info->wire_conv_variant = pl->wconv_variant;
+    info->row_fft_fixed_shape = ws::row_fft_fixed_shape(pl->plan) ? 1 : 0;
     return WS_OK;
 }
 

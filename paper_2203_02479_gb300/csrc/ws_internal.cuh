@@ -102,6 +102,8 @@ cudaError_t launch_inv_rows(const FftPlan& plan, const float2* tw, const float2*
 // Y[w][k] = sum_r Rt[r][k] * X[w + center - r][k]  (zero or wrapped outside).
 // Batched forms: one launch over every unit (all units share plan, strides,
 // response shape and wire-convolution variant).
+// True when the plan's radix sequence has fixed-shape FP32 row kernels.
+bool row_fft_fixed_shape(const FftPlan& plan);
 cudaError_t launch_fwd_rows_batch(const FftPlan& plan, const float2* tw, const RowBatch& rb, int ncols,
                                   int64_t in_stride, int64_t out_stride, int nfreq, float scale, cudaStream_t s);
 cudaError_t launch_inv_rows_batch(const FftPlan& plan, const float2* tw, const RowBatch& rb, int64_t in_stride,

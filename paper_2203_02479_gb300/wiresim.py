@@ -82,7 +82,7 @@ class WsPlaneInfo(ctypes.Structure):
     _fields_ = [("fft_len_tick", ctypes.c_int32), ("nfreq", ctypes.c_int32),
                 ("nfreq_stride", ctypes.c_int32), ("npasses", ctypes.c_int32),
                 ("radices", ctypes.c_int32 * 16), ("workspace_bytes", ctypes.c_size_t),
-                ("wire_conv_variant", ctypes.c_int32)]
+                ("wire_conv_variant", ctypes.c_int32), ("row_fft_fixed_shape", ctypes.c_int32)]
 
 
 _lock = threading.Lock()

@@ -333,3 +333,22 @@ def test_three_planes_fluctuated_full_size(ws):
         ref_m = oracle.convolve_fft(ref, sp.response, 10)
         assert rel_l2(out, ref_m) <= 1e-3
         assert plane.status() == 0
+
+
+@pytest.mark.parametrize("nw,nt,kt,circular,L,fixed", [
+    (311, 6000, 200, False, 6250, 1), (7, 6000, 200, True, 6000, 1), (160, 6300, 101, False, 6400, 1),
+    (305, 3000, 200, False, 3200, 1), (1, 1000, 200, False, 1200, 1), (33, 1900, 200, False, 2160, 0)])
+def test_fixed_shape_row_transforms(ws, nw, nt, kt, circular, L, fixed):
+    """Row kernels compiled for one radix plan (25.25.10, 25.16.15, 25.16.16,
+    25.16.8, 25.16.3) and the generic kernels: odd wire counts leave a lone
+    last row; more row pairs than resident CTAs."""
+    import torch
+    rng = np.random.Generator(np.random.PCG64(nw + nt))
+    S = rng.standard_normal((nw, nt)).astype(np.float32)
+    R = rng.standard_normal((21, kt)).astype(np.float32)
+    plane = ws.Plane(nw, nt, R, circular=circular)
+    assert plane.info.fft_len_tick == L
+    assert plane.info.row_fft_fixed_shape == fixed
+    out = plane.convolve(torch.from_numpy(S).cuda())
+    assert rel_l2(to_np(out), oracle.convolve_fft(S.astype(np.float64), R, 10, circular)) <= REL_L2
+    assert plane.status() == 0
