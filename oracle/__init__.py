@@ -62,6 +62,9 @@ def _lib():
             h.wso_binomial.argtypes = [ctypes.c_int64, ctypes.c_double, ctypes.c_int, _u32p,
                                        ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32]
             h.wso_binomial.restype = ctypes.c_int64
+            h.wso_binomial_invert_many.argtypes = [ctypes.c_int64, ctypes.c_double, ctypes.c_int64, _u32p,
+                                                   np.ctypeslib.ndpointer(np.int64, flags="C_CONTIGUOUS")]
+            h.wso_binomial_invert_many.restype = None
             opt_f32 = ctypes.c_void_p
             h.wso_raster_scatter.argtypes = [
                 ctypes.c_int64, _f64p, _f64p, _f64p, opt_f32, opt_f32,
@@ -102,6 +105,7 @@ DL = 4.0e-4
 DT = 8.8e-4
 V = 1.6
 EXACT_MAX = 32
+EXACT_CAP = 64     # largest exact_max: keeps (1 - s)^N a normal float
 
 
 def _c32(a):
@@ -142,12 +146,27 @@ def binomial(N: int, p: float, seed: int, bin_index: int, depo: int, event_id: i
              plane_id: int = 0, exact_max: int = EXACT_MAX) -> int:
     """Binomial(N, p) survivor count of one bin (Sec. 3.1 reading).
 
-    Pinned by chi-square against scipy.stats.binom (exact branch) and by the
-    first two moments (normal branch)."""
+    Pinned by the exact pmf over every value of the inversion's random word
+    (exact branch), chi-square against scipy.stats.binom over many bins, and
+    the first two moments (normal branch)."""
+    if exact_max > EXACT_CAP:
+        raise ValueError(f"exact_max above {EXACT_CAP}")
     key = seed_key(seed)
     evpl = ((event_id << 4) | (plane_id & 15)) & 0xFFFFFFFF
     return int(_lib().wso_binomial(int(N), float(p), int(exact_max), key,
                                    bin_index & 0xFFFFFFFF, depo & 0xFFFFFFFF, evpl))
+
+
+def binomial_invert(N: int, p: float, x0) -> np.ndarray:
+    """Exact-branch survivor counts for Philox words x0 (the CDF inversion of
+    the Sec. 3.1 reading), vectorised over x0.
+
+    Pinned exhaustively against the Binomial pmf over all 2^24 values of
+    the word's top 24 bits."""
+    x = np.ascontiguousarray(np.asarray(x0, dtype=np.uint32).ravel())
+    k = np.zeros(x.shape[0], dtype=np.int64)
+    _lib().wso_binomial_invert_many(int(N), float(p), x.shape[0], x, k)
+    return k
 
 
 # ---------------------------------------------------------------- diffusion
@@ -188,6 +207,8 @@ def raster_scatter(q, x_mm, t_us, nwires: int, nticks: int, *, sig_t_us=None, si
     q = _c64(q); x = _c64(x_mm); t = _c64(t_us)
     st = None if sig_t_us is None else _c64(sig_t_us)
     sx = None if sig_x_mm is None else _c64(sig_x_mm)
+    if fluctuate and exact_max > EXACT_CAP:
+        raise ValueError(f"exact_max above {EXACT_CAP}")
     S = np.zeros((nwires, nticks))
     skipped = _lib().wso_raster_scatter(
         q.shape[0], q, x, t, _opt_ptr(st), _opt_ptr(sx), nwires, nticks, pitch_mm, tick_us,

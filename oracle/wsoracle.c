@@ -22,7 +22,8 @@
  * Every function below is pinned by tests against something other than
  * itself: Gauss-Legendre quadrature of the Gaussian (bin weights), closed
  * forms (patch sums, delta response), cuRAND's host Philox generator (the
- * random stream), binomial moments (the sampler) and scipy's convolve2d
+ * random stream), the exact binomial pmf (the sampler, over every value of
+ * its random word), binomial moments, and scipy's convolve2d
  * (the convolution).
  */
 #include <math.h>
@@ -117,22 +118,68 @@ int wso_axis_weights(double mu, double sigma, double delta, double nsig,
 
 /* ------------------------------------------------------------------------ */
 /* Binomial charge fluctuation (Sec. 3.1: the CPU reference draws binomial
- * numbers).  Reading: each bin holds N = floor(q*w + 1/2) electrons, each
- * surviving independently with probability p; the bins draw independently
- * from Philox keyed by the seed, with the counter (block j, global bin,
- * depo index, event << 4 | plane).
- *   - N <= exact_max: k = number of i < N whose 32-bit word i (word i%4 of
- *     block i/4) is below T = floor(p * 2^32); integer-only.
- *   - N > exact_max: normal approximation from block 0,
+ * numbers; the sampler itself is not given).  Reading: each bin holds
+ * N = floor(q*w + 1/2) electrons, each surviving independently with
+ * probability p; the bins draw independently from Philox block 0 keyed by
+ * the seed, with the counter (0, global bin, depo index, event << 4 | plane).
+ *   - N <= exact_max (at most WSO_EXACT_CAP): inversion of the Binomial CDF
+ *     in single precision from word 0 (see wso_binomial_invert).
+ *   - N > exact_max: normal approximation from words 0 and 1,
  *     u1 = (x0 + 1/2)/2^32, u2 = (x1 + 1/2)/2^32,
  *     z = sqrt(-2 ln u1) cos(2 pi u2),
- *     k = clamp(floor(N p + z sqrt(N p (1 - p)) + 1/2), 0, N), p = T/2^32.
+ *     k = clamp(floor(N p + z sqrt(N p (1 - p)) + 1/2), 0, N), p = T/2^32
+ *     with T = floor(p * 2^32).
  *   - p >= 1 keeps every electron, p <= 0 none. */
+#define WSO_EXACT_CAP 64
+
 uint32_t wso_survive_threshold(double p)
 {
     if (!(p > 0.0)) return 0u;
     if (p >= 1.0) return 0xFFFFFFFFu;
     return (uint32_t)floor(p * 4294967296.0);
+}
+
+/* Sequential-search inversion of the Binomial(N, p) CDF, every step a
+ * single-precision operation in a fixed order (so that any IEEE-754 machine
+ * takes the same decisions):
+ *   pf = (float)p; the search runs on s = min(pf, 1 - pf) and the count is
+ *   mirrored (N - k) when pf > 1/2;
+ *   f_0 = (1 - s)^N by binary powering over the bits of N, low bit first;
+ *   r = s / (1 - s);  f_{k+1} = ((f_k r) (N - k)) (1/(k+1)), where 1/(k+1) is
+ *   the float reciprocal;  F_k = F_{k-1} + f_k;
+ *   u = (x0 >> 8) 2^-24;  k = the first k with u < F_k, else N.
+ * The probability of each k is F_k - F_{k-1} over the 2^24 values of u,
+ * Binomial(N, s) up to float rounding.  N <= WSO_EXACT_CAP keeps f_0 above
+ * 2^-64, a normal float. */
+int64_t wso_binomial_invert(int64_t N, double p, uint32_t x0)
+{
+    const float pf = (float)p;
+    const int flip = pf > 0.5f;
+    const float s = flip ? 1.0f - pf : pf;
+    const float r = s / (1.0f - s);
+    float base = 1.0f - s, f = 1.0f;
+    for (int64_t n = N; n > 0; n >>= 1) {
+        if (n & 1) f = f * base;
+        base = base * base;
+    }
+    const float u = (float)(x0 >> 8) * 5.9604644775390625e-8f;
+    float F = f;
+    int64_t k = 0;
+    while (!(u < F) && k < N) {
+        const float inv = 1.0f / (float)(k + 1);
+        f = f * r;
+        f = f * (float)(N - k);
+        f = f * inv;
+        F = F + f;
+        ++k;
+    }
+    return flip ? N - k : k;
+}
+
+/* wso_binomial_invert over an array of words (for the exhaustive pin). */
+void wso_binomial_invert_many(int64_t N, double p, int64_t n, const uint32_t* x0, int64_t* k)
+{
+    for (int64_t i = 0; i < n; ++i) k[i] = wso_binomial_invert(N, p, x0[i]);
 }
 
 int64_t wso_binomial(int64_t N, double p, int exact_max, const uint32_t key[2],
@@ -141,21 +188,12 @@ int64_t wso_binomial(int64_t N, double p, int exact_max, const uint32_t key[2],
     if (N <= 0) return 0;
     if (!(p > 0.0)) return 0;
     if (p >= 1.0) return N;
+    if (exact_max > WSO_EXACT_CAP) return -1;
     uint32_t T = wso_survive_threshold(p);
     uint32_t ctr[4], x[4];
-    if (N <= exact_max) {
-        int64_t k = 0;
-        for (int64_t i = 0; i < N; ++i) {
-            if (i % 4 == 0) {
-                ctr[0] = (uint32_t)(i / 4); ctr[1] = bin; ctr[2] = depo; ctr[3] = evpl;
-                wso_philox4x32_10(ctr, key, x);
-            }
-            if (x[i % 4] < T) ++k;
-        }
-        return k;
-    }
     ctr[0] = 0; ctr[1] = bin; ctr[2] = depo; ctr[3] = evpl;
     wso_philox4x32_10(ctr, key, x);
+    if (N <= exact_max) return wso_binomial_invert(N, p, x[0]);
     double u1 = ((double)x[0] + 0.5) / 4294967296.0;
     double u2 = ((double)x[1] + 0.5) / 4294967296.0;
     double z = sqrt(-2.0 * log(u1)) * cos(2.0 * M_PI * u2);
@@ -187,6 +225,7 @@ int64_t wso_raster_scatter(int64_t n, const double* q, const double* x_mm, const
                            int fluctuate, double p, uint64_t seed, uint32_t event_id,
                            uint32_t plane_id, int exact_max, double* S)
 {
+    if (fluctuate && exact_max > WSO_EXACT_CAP) return -1;
     double* wt = (double*)malloc(sizeof(double) * WSO_MAXBINS);
     double* wx = (double*)malloc(sizeof(double) * WSO_MAXBINS);
     uint32_t key[2] = {(uint32_t)(seed & 0xFFFFFFFFu), (uint32_t)(seed >> 32)};

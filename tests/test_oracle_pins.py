@@ -231,6 +231,51 @@ def test_binomial_exact_branch_matches_binomial_pmf():
     assert k.mean() == pytest.approx(N * p, abs=4 * math.sqrt(N * p * (1 - p) / m))
 
 
+_ALL_WORDS = None
+
+
+def _all_words():
+    """Every value of a word's top 24 bits (the inversion's uniform u)."""
+    global _ALL_WORDS
+    if _ALL_WORDS is None:
+        _ALL_WORDS = (np.arange(1 << 24, dtype=np.uint32) << np.uint32(8))
+    return _ALL_WORDS
+
+
+@pytest.mark.parametrize("N,p", [(1, 0.7), (5, 0.7), (20, 0.7), (32, 0.3), (64, 0.5), (13, 0.999),
+                                 (9, 0.01), (40, 0.62)])
+def test_binomial_inversion_is_the_pmf_over_every_word(N, p):
+    """Exact branch: over all 2^24 values of u the inversion returns k with
+    frequency Binomial(N, float(p)).pmf(k), up to the float rounding of the
+    running CDF (a few ulps per step) and the 2^-24 spacing of u."""
+    stats = pytest.importorskip("scipy.stats")
+    k = oracle.binomial_invert(N, p, _all_words())
+    freq = np.bincount(k, minlength=N + 1) / float(1 << 24)
+    pmf = stats.binom.pmf(np.arange(N + 1), N, float(np.float32(p)))
+    assert np.abs(freq - pmf).max() <= 1e-7 * (N + 2) + 2.0 ** -24
+    # u nondecreasing gives k nondecreasing (mirrored for p > 1/2)
+    d = np.diff(k)
+    assert (d >= 0).all() if np.float32(p) <= 0.5 else (d <= 0).all()
+
+
+def test_binomial_inversion_edges():
+    """u = 0 gives the smallest count, the largest u the largest reachable;
+    N = 1 is a Bernoulli trial with P(k = 1) = float(p)."""
+    lo, hi = np.uint32(0), np.uint32(0xFFFFFFFF)
+    assert oracle.binomial_invert(10, 0.3, [lo])[0] == 0
+    assert oracle.binomial_invert(10, 0.7, [lo])[0] == 10
+    assert oracle.binomial_invert(10, 0.3, [hi])[0] == 10
+    k = oracle.binomial_invert(1, 0.7, _all_words())
+    assert abs(k.mean() - float(np.float32(0.7))) <= 2 ** -23
+
+
+def test_binomial_exact_max_is_capped():
+    with pytest.raises(ValueError):
+        oracle.binomial(10, 0.7, 1, 2, 3, exact_max=oracle.EXACT_CAP + 1)
+    with pytest.raises(ValueError):
+        oracle.raster_scatter([1.0], [2.0], [3.0], 4, 10, fluctuate=True, p=0.7, exact_max=100)
+
+
 def test_binomial_normal_branch_moments():
     """Normal branch (N > exact_max): mean N p and variance N p (1 - p)."""
     N, p, m = 5000, 0.7, 20000
