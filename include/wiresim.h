@@ -113,9 +113,10 @@ typedef struct {
     double p_survive;         /* electron survival probability p            */
     uint64_t seed;            /* Philox key                                 */
     uint32_t event_id;        /* < 2^28, part of the Philox counter         */
-    int32_t fluct_exact_max;  /* bins with N <= this draw N Bernoulli trials
-                                 exactly; larger N use the normal
-                                 approximation; 0 .. 2^27                   */
+    int32_t fluct_exact_max;  /* bins with N <= this sample Binomial(N, p)
+                                 by inversion of its CDF (single precision,
+                                 one Philox word); larger N use the normal
+                                 approximation; 0 .. 64                     */
     int32_t precision;        /* WS_PREC_FP32: float throughout;
                                  WS_PREC_FP32_COMP: float with compensated
                                  (TwoSum) scatter-add and FP64 edge weights

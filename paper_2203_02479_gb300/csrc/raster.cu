@@ -53,14 +53,31 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1
     return c;
 }
 
-// Survivors among trials 4j .. 4j + m - 1 of one Philox block: a trial
-// survives when its 32-bit word is below T (p = T / 2^32).
-__device__ __forceinline__ int exact_count(uint4 x, int m, uint32_t T) {
-    int k = (x.x < T);
-    if (m > 1) k += (x.y < T);
-    if (m > 2) k += (x.z < T);
-    if (m > 3) k += (x.w < T);
-    return k;
+// Exact branch: sequential-search inversion of the Binomial(N, s) CDF,
+// s = min(p, 1 - p), in single precision with every operation rounded in a
+// fixed order (f_0 = (1 - s)^N by binary powering over the bits of N, low
+// bit first; f_{k+1} = ((f_k r) (N - k)) / (k + 1) with r = s / (1 - s) and
+// the correctly rounded reciprocal of k + 1; F_k = F_{k-1} + f_k), u the top
+// 24 bits of the word over 2^24; k = the first k with u < F_k (N if none),
+// mirrored to N - k for p > 1/2.  Any IEEE-754 machine doing these steps
+// takes the same decisions.  recip[i] holds 1/i.
+__device__ __forceinline__ int invert_binomial(int N, uint32_t x0, const RasterArgs& a, const float* recip) {
+    float f = 1.0f, base = a.inv_base;
+    for (int n = N; n > 0; n >>= 1) {
+        if (n & 1) f = __fmul_rn(f, base);
+        base = __fmul_rn(base, base);
+    }
+    const float u = __fmul_rn(__uint2float_rn(x0 >> 8), 5.9604644775390625e-8f);
+    float F = f;
+    int k = 0;
+    while (!(u < F) && k < N) {
+        f = __fmul_rn(f, a.inv_r);
+        f = __fmul_rn(f, __int2float_rn(N - k));
+        f = __fmul_rn(f, recip[k + 1]);
+        F = __fadd_rn(F, f);
+        ++k;
+    }
+    return a.inv_flip ? N - k : k;
 }
 
 // Normal approximation of Binomial(N, p) from words 0, 1 of Philox block 0
@@ -97,20 +114,24 @@ __device__ __forceinline__ int normal_draw(uint4 x, int N, const RasterArgs& a) 
     }
 }
 
-// Survivor count contributed by Philox block j of a bin holding N electrons
-// (the bin's binomial draw is the sum over its blocks): exact trials for
-// N <= exact_max, else the single normal-approximation block.
+// Survivor count of a bin holding N electrons: one Philox block with counter
+// (0, global bin, depo, event << 4 | plane); CDF inversion of its word 0 for
+// N <= exact_max, else the normal approximation from words 0 and 1.
 template <int P>
-__device__ __forceinline__ int binomial_block(int N, int j, const RasterArgs& a, uint32_t bin, uint32_t depo) {
-    const uint4 x = philox4x32_10(make_uint4((uint32_t)j, bin, depo, a.evpl), a.key0, a.key1);
-    if (N <= a.exact_max) return exact_count(x, N - 4 * j, a.T);
+__device__ __forceinline__ int binomial_bin(int N, const RasterArgs& a, uint32_t bin, uint32_t depo,
+                                            const float* recip) {
+    if (N <= 0 || a.T == 0u) return 0;
+    if (a.keep_all) return N;
+    const uint4 x = philox4x32_10(make_uint4(0u, bin, depo, a.evpl), a.key0, a.key1);
+    if (N <= a.exact_max) return invert_binomial(N, x.x, a, recip);
     return normal_draw<P>(x, N, a);
 }
 
-// Philox blocks a bin of N electrons needs.
-__device__ __forceinline__ int binomial_items(int N, const RasterArgs& a) {
-    if (N <= 0 || a.T == 0u || a.keep_all) return 0;
-    return N <= a.exact_max ? (N + 3) >> 2 : 1;
+// Reciprocals 1/i, i = 0 .. kExactCap, correctly rounded, into shared memory
+// (entry 0 unused).
+__device__ __forceinline__ void fill_recip(float* recip) {
+    for (int i = threadIdx.x; i <= kExactCap; i += blockDim.x) recip[i] = i > 0 ? __frcp_rn((float)i) : 0.f;
+    __syncthreads();
 }
 
 // Electrons in a bin of expected charge v (saturating at 1e9).
@@ -297,9 +318,8 @@ raster_kernel(const __grid_constant__ RasterUnits U, ws_patches pt, const long l
     __shared__ W s_c[kWarpsPerBlock][kChunk + 1];
     __shared__ W s_wt[kWarpsPerBlock][kChunk];
     __shared__ W s_wx[kWarpsPerBlock][kChunk];
-    __shared__ int s_incl[kWarpsPerBlock][32];
-    __shared__ int s_n[kWarpsPerBlock][32];
-    __shared__ int s_cnt[kWarpsPerBlock][32];
+    __shared__ float s_recip[kExactCap + 1];
+    fill_recip(s_recip);
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
     const int64_t nwarps = (int64_t)gridDim.x * kWarpsPerBlock;
@@ -354,58 +374,18 @@ raster_kernel(const __grid_constant__ RasterUnits U, ws_patches pt, const long l
                 axis_weights<W>(e.mu_x, e.sx, pitch, nsig, e.point_x, wc, nxc, inv_norm, s_u[wib], s_c[wib],
                                 s_wx[wib], lane);
                 const int nbin = nxc * ntc;
-                if (!a.fluct) {
-                    for (int idx = lane; idx < nbin; idx += 32) {
-                        const int ia = idx / ntc, ib = idx - ia * ntc;
-                        const int w = wc + ia, k = kc + ib;
-                        const W v = scale * s_wx[wib][ia] * s_wt[wib][ib];
-                        if (MODE == EMIT_GRID) emit<P>(a, grid, (int64_t)w * a.nticks + k, v);
-                        else pt.val[off + (int64_t)(w - e.w0) * ntf + (k - e.k0)] = (float)v;
+                for (int idx = lane; idx < nbin; idx += 32) {
+                    const int ia = idx / ntc, ib = idx - ia * ntc;
+                    const int w = wc + ia, k = kc + ib;
+                    W v;
+                    if (!a.fluct) {
+                        v = scale * s_wx[wib][ia] * s_wt[wib][ib];
+                    } else {
+                        const int N = electrons(q * s_wx[wib][ia] * s_wt[wib][ib]);
+                        v = (W)binomial_bin<P>(N, a, (uint32_t)((int64_t)w * a.nticks + k), (uint32_t)i, s_recip);
                     }
-                }
-                // Binomial mode: 32 bins per round; each (bin, Philox block)
-                // pair is one work item so the lanes share the draws evenly.
-                for (int base = 0; a.fluct && base < nbin; base += 32) {
-                    const int idx = base + lane;
-                    int N = 0, w = 0, k = 0;
-                    if (idx < nbin) {
-                        const int ia = idx / ntc, ib = idx - ia * ntc;
-                        w = wc + ia;
-                        k = kc + ib;
-                        N = electrons(q * s_wx[wib][ia] * s_wt[wib][ib]);
-                    }
-                    const int items = binomial_items(N, a);
-                    int incl = items;
-#pragma unroll
-                    for (int o = 1; o < 32; o <<= 1) {
-                        const int y = __shfl_up_sync(0xffffffffu, incl, o);
-                        if (lane >= o) incl += y;
-                    }
-                    const int total = __shfl_sync(0xffffffffu, incl, 31);
-                    s_incl[wib][lane] = incl;
-                    s_n[wib][lane] = N;
-                    s_cnt[wib][lane] = (N > 0 && a.keep_all) ? N : 0;
-                    __syncwarp();
-                    for (int it2 = lane; it2 < total; it2 += 32) {
-                        int lo = 0, hi = 31;  // first bin slot whose inclusive count exceeds it2
-                        while (lo < hi) {
-                            const int mid = (lo + hi) >> 1;
-                            if (s_incl[wib][mid] > it2) hi = mid; else lo = mid + 1;
-                        }
-                        const int first = lo > 0 ? s_incl[wib][lo - 1] : 0;
-                        const int bidx = base + lo;
-                        const int ia = bidx / ntc, ib = bidx - ia * ntc;
-                        const uint32_t gbin = (uint32_t)((int64_t)(wc + ia) * a.nticks + (kc + ib));
-                        const int c = binomial_block<P>(s_n[wib][lo], it2 - first, a, gbin, (uint32_t)i);
-                        if (c) atomicAdd(&s_cnt[wib][lo], c);
-                    }
-                    __syncwarp();
-                    if (idx < nbin) {
-                        const W v = (W)s_cnt[wib][lane];
-                        if (MODE == EMIT_GRID) emit<P>(a, grid, (int64_t)w * a.nticks + k, v);
-                        else pt.val[off + (int64_t)(w - e.w0) * ntf + (k - e.k0)] = (float)v;
-                    }
-                    __syncwarp();
+                    if (MODE == EMIT_GRID) emit<P>(a, grid, (int64_t)w * a.nticks + k, v);
+                    else pt.val[off + (int64_t)(w - e.w0) * ntf + (k - e.k0)] = (float)v;
                 }
                 __syncwarp();
             }
@@ -456,10 +436,6 @@ __device__ __forceinline__ void lane_weights(const RasterArgs& a, W mu, W sigma,
     lane_axis_weights<W, W>(mu, sigma, delta, nsig, point, first, nb, inv_norm, w);
 }
 
-// Binomial work items of one round are addressed through a byte map when
-// every bin needs at most 8 Philox blocks (exact_max <= 32).
-constexpr int kRoundBins = 64;
-constexpr int kItemMap = kRoundBins * 9;
 constexpr int kBinMap = 1024;    // bins of a 16-depo group addressed through a byte map
 
 template <int MODE, int P>
@@ -478,19 +454,13 @@ raster_small_kernel(const __grid_constant__ RasterUnits U, ws_patches pt, long l
     __shared__ float s_rnt[NW][G];   // 1 / nt
     __shared__ W s_q[NW][G];
     __shared__ unsigned char s_bdep[NW][kBinMap];   // bin -> depo slot
-    __shared__ int s_start[NW][kRoundBins];         // first item of each bin slot
-    __shared__ int s_incl[NW][kRoundBins];          // inclusive item scan (fallback search)
-    __shared__ unsigned char s_item[NW][kItemMap];  // item -> bin slot
-    __shared__ int s_cnt[NW][kRoundBins];
-    __shared__ int s_n[NW][kRoundBins];
-    __shared__ uint32_t s_gbin[NW][kRoundBins];
-    __shared__ uint32_t s_dep[NW][kRoundBins];
+    __shared__ float s_recip[kExactCap + 1];
+    fill_recip(s_recip);
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
     const int64_t nwarps = (int64_t)gridDim.x * NW;
     const int dl = lane & (G - 1);      // depo slot of this lane
     const bool tick_lane = lane < G;    // lane pair: tick edges on dl, wire edges on dl + G
-    const unsigned lt_mask = (1u << lane) - 1u;
     const int64_t ngroups = U.gprefix[U.n];
     for (int64_t grp = (int64_t)blockIdx.x * NW + wib; grp < ngroups; grp += nwarps) {
         const int uu = find_unit64(U.gprefix, U.n, grp);
@@ -556,122 +526,16 @@ raster_small_kernel(const __grid_constant__ RasterUnits U, ws_patches pt, long l
             ia = (int)(((float)local + 0.5f) * s_rnt[wib][d]);
             ib = local - ia * s_nt[wib][d];
         };
-        if (!a.fluct) {
-            for (int g = lane; g < total; g += 32) {
-                int d, local, ia, ib;
-                locate(g, d, local, ia, ib);
-                const W v = s_q[wib][d] * s_wx[wib][d][ia] * s_wt[wib][d][ib];
-                if (MODE == EMIT_GRID) emit<P>(a, grid, (int64_t)(s_w0[wib][d] + ia) * a.nticks + s_k0[wib][d] + ib, v);
-                else pt.val[pt.off[base + d] + local] = (float)v;
-            }
-        } else {
-            const bool use_imap = a.exact_max <= 32;
-            // Rounds of 64 bins, two per lane.  Each bin's Philox blocks are
-            // work items (one for a normal-approximation bin, ceil(N/4) for
-            // an exact bin), normal ones first, spread over the lanes two at
-            // a time; exact counts add up in shared memory.
-            for (int gb = 0; gb < total; gb += kRoundBins) {
-                int N[2], w[2], k[2], local[2], d[2], ne[2];
-                bool nrm[2];
-#pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    const int g = gb + 32 * h + lane;
-                    N[h] = 0; w[h] = 0; k[h] = 0; local[h] = 0; d[h] = 0;
-                    if (g < total) {
-                        int ia, ib;
-                        locate(g, d[h], local[h], ia, ib);
-                        w[h] = s_w0[wib][d[h]] + ia;
-                        k[h] = s_k0[wib][d[h]] + ib;
-                        N[h] = electrons(s_q[wib][d[h]] * s_wx[wib][d[h]][ia] * s_wt[wib][d[h]][ib]);
-                    }
-                    const int items = binomial_items(N[h], a);
-                    nrm[h] = items > 0 && N[h] > a.exact_max;
-                    ne[h] = nrm[h] ? 0 : items;
-                    const int slot = 32 * h + lane;
-                    s_cnt[wib][slot] = (N[h] > 0 && a.keep_all) ? N[h] : 0;
-                    s_n[wib][slot] = N[h];
-                    s_gbin[wib][slot] = (uint32_t)((int64_t)w[h] * a.nticks + k[h]);
-                    s_dep[wib][slot] = (uint32_t)(base + d[h]);
-                }
-                // normal items first (one per bin), then the exact items
-                const unsigned b0 = __ballot_sync(0xffffffffu, nrm[0]);
-                const unsigned b1 = __ballot_sync(0xffffffffu, nrm[1]);
-                const int nn0 = __popc(b0), nn = nn0 + __popc(b1);
-                int inc0 = ne[0], inc1 = ne[1];
-#pragma unroll
-                for (int o = 1; o < 32; o <<= 1) {
-                    const int y0 = __shfl_up_sync(0xffffffffu, inc0, o);
-                    const int y1 = __shfl_up_sync(0xffffffffu, inc1, o);
-                    if (lane >= o) { inc0 += y0; inc1 += y1; }
-                }
-                const int tot0 = __shfl_sync(0xffffffffu, inc0, 31);
-                const int tot = nn + tot0 + __shfl_sync(0xffffffffu, inc1, 31);
-                const int st0 = nrm[0] ? __popc(b0 & lt_mask) : nn + inc0 - ne[0];
-                const int st1 = nrm[1] ? nn0 + __popc(b1 & lt_mask) : nn + tot0 + inc1 - ne[1];
-                s_start[wib][lane] = st0;
-                s_start[wib][32 + lane] = st1;
-                s_incl[wib][lane] = nrm[0] ? 0 : nn + inc0;
-                s_incl[wib][32 + lane] = nrm[1] ? 0 : nn + tot0 + inc1;
-                if (use_imap) {
-                    if (nrm[0]) s_item[wib][st0] = (unsigned char)lane;
-                    if (nrm[1]) s_item[wib][st1] = (unsigned char)(32 + lane);
-                    for (int j = 0; j < ne[0]; ++j) s_item[wib][st0 + j] = (unsigned char)lane;
-                    for (int j = 0; j < ne[1]; ++j) s_item[wib][st1 + j] = (unsigned char)(32 + lane);
-                }
-                __syncwarp();
-                for (int it0 = lane; it0 < tot; it0 += 64) {
-                    int sl[2], jj[2];
-                    bool ok[2];
-                    uint4 y[2];
-#pragma unroll
-                    for (int h = 0; h < 2; ++h) {
-                        const int it = it0 + 32 * h;
-                        ok[h] = it < tot;
-                        if (!ok[h]) {
-                            sl[h] = 0;
-                        } else if (use_imap) {
-                            sl[h] = s_item[wib][it];
-                        } else if (it < nn) {
-                            // it-th normal bin: position of the it-th set bit
-                            sl[h] = it < nn0 ? (int)__fns(b0, 0, it + 1) : 32 + (int)__fns(b1, 0, it - nn0 + 1);
-                        } else {
-                            // exact items: first slot whose inclusive end exceeds it
-                            int lo = 0;
-#pragma unroll
-                            for (int step = 32; step >= 1; step >>= 1)
-                                if (lo + step - 1 < kRoundBins && s_incl[wib][lo + step - 1] <= it) lo += step;
-                            sl[h] = lo;
-                        }
-                        jj[h] = it - s_start[wib][sl[h]];
-                    }
-#pragma unroll
-                    for (int h = 0; h < 2; ++h)
-                        y[h] = philox4x32_10(make_uint4((uint32_t)jj[h], s_gbin[wib][sl[h]], s_dep[wib][sl[h]], a.evpl),
-                                             a.key0, a.key1);
-#pragma unroll
-                    for (int h = 0; h < 2; ++h) {
-                        if (!ok[h]) continue;
-                        const int n = s_n[wib][sl[h]];
-                        if (n > a.exact_max) {
-                            s_cnt[wib][sl[h]] = normal_draw<P>(y[h], n, a);
-                        } else {
-                            const int c = exact_count(y[h], n - 4 * jj[h], a.T);
-                            if (c) atomicAdd(&s_cnt[wib][sl[h]], c);
-                        }
-                    }
-                }
-                __syncwarp();
-#pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    const int g = gb + 32 * h + lane;
-                    if (g < total) {
-                        const W v = (W)s_cnt[wib][32 * h + lane];
-                        if (MODE == EMIT_GRID) emit<P>(a, grid, (int64_t)w[h] * a.nticks + k[h], v);
-                        else pt.val[pt.off[base + d[h]] + local[h]] = (float)v;
-                    }
-                }
-                __syncwarp();
-            }
+        for (int g = lane; g < total; g += 32) {
+            int d, local, ia, ib;
+            locate(g, d, local, ia, ib);
+            const int w = s_w0[wib][d] + ia, k = s_k0[wib][d] + ib;
+            W v = s_q[wib][d] * s_wx[wib][d][ia] * s_wt[wib][d][ib];
+            if (a.fluct)
+                v = (W)binomial_bin<P>(electrons(v), a, (uint32_t)((int64_t)w * a.nticks + k), (uint32_t)(base + d),
+                                       s_recip);
+            if (MODE == EMIT_GRID) emit<P>(a, grid, (int64_t)w * a.nticks + k, v);
+            else pt.val[pt.off[base + d] + local] = (float)v;
         }
         __syncwarp();
     }

@@ -180,7 +180,7 @@ ws_status check_params(const ws_params* p) {
     if (!(p->v_mm_us > 0) || !(p->DL_mm2_us >= 0) || !(p->DT_mm2_us >= 0)) return WS_ERR_INVALID_ARG;
     if (!(p->p_survive >= 0) || !(p->p_survive <= 1)) return WS_ERR_INVALID_ARG;
     if (p->event_id >= (1u << 28)) return WS_ERR_INVALID_ARG;
-    if (p->fluct_exact_max < 0 || p->fluct_exact_max > (1 << 27)) return WS_ERR_INVALID_ARG;
+    if (p->fluct_exact_max < 0 || p->fluct_exact_max > ws::kExactCap) return WS_ERR_INVALID_ARG;
     if (p->precision != WS_PREC_FP32 && p->precision != WS_PREC_FP32_COMP && p->precision != WS_PREC_FP64)
         return WS_ERR_INVALID_ARG;
     return WS_OK;
@@ -207,6 +207,13 @@ ws::RasterArgs raster_args(const ws_plane* pl, const ws_depos* d, const ws_param
     a.evpl = (p->event_id << 4) | ((uint32_t)pl->desc.plane_id & 15u);
     a.keep_all = p->p_survive >= 1.0 ? 1 : 0;
     a.exact_max = p->fluct_exact_max;
+    {
+        const float pf = a.p;
+        a.inv_flip = pf > 0.5f ? 1 : 0;
+        const float sv = a.inv_flip ? 1.0f - pf : pf;
+        a.inv_base = 1.0f - sv;
+        a.inv_r = sv / a.inv_base;
+    }
     a.status = pl->status;
     a.prec = p->precision;
     a.lo = nullptr;

@@ -24,6 +24,8 @@ struct FftPlan {
 };
 
 // Launch geometry and constants of a raster pass.
+constexpr int kExactCap = 64;   // largest fluct_exact_max ((1 - s)^N stays a normal float)
+
 struct RasterArgs {
     const float* q;
     const float* x;
@@ -41,7 +43,10 @@ struct RasterArgs {
     int keep_all;         // p >= 1: every electron survives
     uint32_t key0, key1;  // Philox key from the seed
     uint32_t evpl;        // (event_id << 4) | plane_id
-    int exact_max;
+    int exact_max;        // N <= exact_max: CDF inversion; above: normal approximation
+    // CDF inversion on s = min(p, 1-p) (float): r = s / (1 - s), base = 1 - s
+    float inv_r, inv_base;
+    int inv_flip;         // p > 1/2: the search counts losses, k = N - k'
     uint32_t* status;
     // precision path (WS_PREC_*) and its extra state
     int prec;
