@@ -114,16 +114,60 @@ __device__ __forceinline__ int normal_draw(uint4 x, int N, const RasterArgs& a) 
     }
 }
 
+// The same search on a table: row N (N = 1 .. kExactCap, at offset
+// N (N - 1) / 2) holds F_0 .. F_{N-1} built by invert_binomial's operations
+// for one (r, 1 - s), so the first k with u < F_k is a binary search with the
+// same result.
+constexpr int kCdfTable = kExactCap * (kExactCap + 1) / 2;
+
+__device__ void fill_cdf(float* cdf, const float* recip, const RasterArgs& a) {
+    for (int N = threadIdx.x + 1; N <= kExactCap; N += blockDim.x) {
+        float f = 1.0f, base = a.inv_base;
+        for (int n = N; n > 0; n >>= 1) {
+            if (n & 1) f = __fmul_rn(f, base);
+            base = __fmul_rn(base, base);
+        }
+        float* row = cdf + N * (N - 1) / 2;
+        float F = f;
+        row[0] = F;
+        for (int k = 0; k + 1 < N; ++k) {
+            f = __fmul_rn(f, a.inv_r);
+            f = __fmul_rn(f, __int2float_rn(N - k));
+            f = __fmul_rn(f, recip[k + 1]);
+            F = __fadd_rn(F, f);
+            row[k + 1] = F;
+        }
+    }
+    __syncthreads();
+}
+
+__device__ __forceinline__ int invert_binomial_table(int N, uint32_t x0, const RasterArgs& a, const float* cdf) {
+    const float u = __fmul_rn(__uint2float_rn(x0 >> 8), 5.9604644775390625e-8f);
+    const float* row = cdf + N * (N - 1) / 2;
+    int k = 0, len = N;
+    while (len > 0) {
+        const int half = len >> 1;
+        if (u < row[k + half]) {
+            len = half;
+        } else {
+            k += half + 1;
+            len -= half + 1;
+        }
+    }
+    return a.inv_flip ? N - k : k;
+}
+
 // Survivor count of a bin holding N electrons: one Philox block with counter
 // (0, global bin, depo, event << 4 | plane); CDF inversion of its word 0 for
 // N <= exact_max, else the normal approximation from words 0 and 1.
+// cdf: the table for this unit's (r, 1 - s), or null for the direct search.
 template <int P>
 __device__ __forceinline__ int binomial_bin(int N, const RasterArgs& a, uint32_t bin, uint32_t depo,
-                                            const float* recip) {
+                                            const float* recip, const float* cdf) {
     if (N <= 0 || a.T == 0u) return 0;
     if (a.keep_all) return N;
     const uint4 x = philox4x32_10(make_uint4(0u, bin, depo, a.evpl), a.key0, a.key1);
-    if (N <= a.exact_max) return invert_binomial(N, x.x, a, recip);
+    if (N <= a.exact_max) return cdf ? invert_binomial_table(N, x.x, a, cdf) : invert_binomial(N, x.x, a, recip);
     return normal_draw<P>(x, N, a);
 }
 
@@ -382,7 +426,8 @@ raster_kernel(const __grid_constant__ RasterUnits U, ws_patches pt, const long l
                         v = scale * s_wx[wib][ia] * s_wt[wib][ib];
                     } else {
                         const int N = electrons(q * s_wx[wib][ia] * s_wt[wib][ib]);
-                        v = (W)binomial_bin<P>(N, a, (uint32_t)((int64_t)w * a.nticks + k), (uint32_t)i, s_recip);
+                        v = (W)binomial_bin<P>(N, a, (uint32_t)((int64_t)w * a.nticks + k), (uint32_t)i, s_recip,
+                                               nullptr);
                     }
                     if (MODE == EMIT_GRID) emit<P>(a, grid, (int64_t)w * a.nticks + k, v);
                     else pt.val[off + (int64_t)(w - e.w0) * ntf + (k - e.k0)] = (float)v;
@@ -455,7 +500,10 @@ raster_small_kernel(const __grid_constant__ RasterUnits U, ws_patches pt, long l
     __shared__ W s_q[NW][G];
     __shared__ unsigned char s_bdep[NW][kBinMap];   // bin -> depo slot
     __shared__ float s_recip[kExactCap + 1];
+    __shared__ float s_cdf[kCdfTable];   // exact-branch CDF rows for unit 0's survival probability
     fill_recip(s_recip);
+    const RasterArgs& a0 = U.a[0];
+    if (a0.fluct) fill_cdf(s_cdf, s_recip, a0);
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
     const int64_t nwarps = (int64_t)gridDim.x * NW;
@@ -467,6 +515,7 @@ raster_small_kernel(const __grid_constant__ RasterUnits U, ws_patches pt, long l
         const RasterArgs& a = U.a[uu];
         float* __restrict__ grid = U.grid[uu];
         const W inv_norm = window_norm<W>(a);
+        const float* cdf = (a0.fluct && a.inv_r == a0.inv_r && a.inv_base == a0.inv_base) ? s_cdf : nullptr;
         const int64_t base = (grp - U.gprefix[uu]) * G;
         const int64_t i = base + dl;
         ExtentT<W> e;
@@ -533,7 +582,7 @@ raster_small_kernel(const __grid_constant__ RasterUnits U, ws_patches pt, long l
             W v = s_q[wib][d] * s_wx[wib][d][ia] * s_wt[wib][d][ib];
             if (a.fluct)
                 v = (W)binomial_bin<P>(electrons(v), a, (uint32_t)((int64_t)w * a.nticks + k), (uint32_t)(base + d),
-                                       s_recip);
+                                       s_recip, cdf);
             if (MODE == EMIT_GRID) emit<P>(a, grid, (int64_t)w * a.nticks + k, v);
             else pt.val[pt.off[base + d] + local] = (float)v;
         }
