@@ -447,14 +447,13 @@ raster_kernel(const __grid_constant__ RasterUnits U, ws_patches pt, const long l
     }
 }
 
-// Lane pair per depo for patches of at most kSmallT x kSmallW bins: a warp
-// takes 16 depos; lane l computes depo l's widths, clipped bin range and tick
-// erfc edge table, lane l + 16 its wire edge table, into shared memory; the
-// warp then spreads the patches' bins (and, with fluctuation, their Philox
-// blocks) evenly over its 32 lanes.  Larger patches are appended to a list
-// for the warp-per-depo kernel.
+// Lane per depo for patches of at most kSmallT x kSmallW bins: a warp takes
+// 32 depos; lane l computes depo l's widths, clipped bin range and both erfc
+// edge tables into shared memory; the warp then spreads the patches' bins
+// (each with its own binomial draw when fluctuating) evenly over its lanes.
+// Larger patches are appended to a list for the warp-per-depo kernel.
 constexpr int kSmallWarpsPerBlock = 4;
-constexpr int kSmallGroup = 16;   // depos per warp (a lane pair per depo)
+constexpr int kSmallGroup = 32;   // depos per warp (a lane per depo)
 
 // First slot of s[0..n) (inclusive prefix sums, nondecreasing) exceeding v.
 template <int N>
@@ -481,7 +480,7 @@ __device__ __forceinline__ void lane_weights(const RasterArgs& a, W mu, W sigma,
     lane_axis_weights<W, W>(mu, sigma, delta, nsig, point, first, nb, inv_norm, w);
 }
 
-constexpr int kBinMap = 1024;    // bins of a 16-depo group addressed through a byte map
+constexpr int kBinMap = 1024;    // bins of a depo group addressed through a byte map (else a search)
 
 template <int MODE, int P>
 __global__ void __launch_bounds__(32 * kSmallWarpsPerBlock, 6)
@@ -507,8 +506,7 @@ raster_small_kernel(const __grid_constant__ RasterUnits U, ws_patches pt, long l
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
     const int64_t nwarps = (int64_t)gridDim.x * NW;
-    const int dl = lane & (G - 1);      // depo slot of this lane
-    const bool tick_lane = lane < G;    // lane pair: tick edges on dl, wire edges on dl + G
+    const int dl = lane;                // depo slot of this lane
     const int64_t ngroups = U.gprefix[U.n];
     for (int64_t grp = (int64_t)blockIdx.x * NW + wib; grp < ngroups; grp += nwarps) {
         const int uu = find_unit64(U.gprefix, U.n, grp);
@@ -522,9 +520,9 @@ raster_small_kernel(const __grid_constant__ RasterUnits U, ws_patches pt, long l
         W q = 0;
         bool bad = false, any = false;
         if (i < a.n) any = depo_extent<W>(a, i, &e, &q, &bad);
-        if (bad && tick_lane) atomicOr(a.status, WS_DEV_BAD_DEPO);
+        if (bad) atomicOr(a.status, WS_DEV_BAD_DEPO);
         const bool large = any && is_large(e);
-        if (large && tick_lane) {
+        if (large) {
             const unsigned slot = atomicAdd(list_count, 1u);
             if (slot < list_cap) list[slot] = ((long long)uu << 40) | (long long)i;
         }
@@ -534,20 +532,17 @@ raster_small_kernel(const __grid_constant__ RasterUnits U, ws_patches pt, long l
         if (MODE == EMIT_PATCH && i < a.n && !large) {
             const int64_t off = pt.off[i];
             const bool fits = off + nb <= pt.capacity_bins;
-            if (tick_lane) {
-                pt.w0[i] = any ? e.w0 : 0;
-                pt.t0[i] = any ? e.k0 : 0;
-                pt.nw[i] = fits ? nxc : 0;
-                pt.nt[i] = fits ? ntc : 0;
-                if (!fits) atomicOr(a.status, WS_DEV_PATCH_OVERFLOW);
-            }
+            pt.w0[i] = any ? e.w0 : 0;
+            pt.t0[i] = any ? e.k0 : 0;
+            pt.nw[i] = fits ? nxc : 0;
+            pt.nt[i] = fits ? ntc : 0;
+            if (!fits) atomicOr(a.status, WS_DEV_PATCH_OVERFLOW);
             if (!fits) nb = 0;
         }
         if (nb > 0) {
-            if (tick_lane) lane_weights<P, W>(a, e.mu_t, e.st, true, e.point_t, e.k0, ntc, inv_norm, s_wt[wib][dl]);
-            else lane_weights<P, W>(a, e.mu_x, e.sx, false, e.point_x, e.w0, nxc, inv_norm, s_wx[wib][dl]);
+            lane_weights<P, W>(a, e.mu_t, e.st, true, e.point_t, e.k0, ntc, inv_norm, s_wt[wib][dl]);
+            lane_weights<P, W>(a, e.mu_x, e.sx, false, e.point_x, e.w0, nxc, inv_norm, s_wx[wib][dl]);
         }
-        if (!tick_lane) nb = 0;   // each depo counted once in the scan
         int incl = nb;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
@@ -556,16 +551,14 @@ raster_small_kernel(const __grid_constant__ RasterUnits U, ws_patches pt, long l
         }
         const int total = __shfl_sync(0xffffffffu, incl, 31);
         const bool use_bmap = total <= kBinMap;
-        if (tick_lane) {
-            s_off[wib][dl] = incl;
-            s_k0[wib][dl] = any ? e.k0 : 0;
-            s_w0[wib][dl] = any ? e.w0 : 0;
-            s_nt[wib][dl] = ntc;
-            s_rnt[wib][dl] = ntc > 0 ? 1.f / (float)ntc : 0.f;
-            s_q[wib][dl] = a.fluct ? q : (sizeof(W) == 8 ? (W)a.p64 : (W)a.p) * q;
-            if (use_bmap)
-                for (int j = incl - nb; j < incl; ++j) s_bdep[wib][j] = (unsigned char)dl;
-        }
+        s_off[wib][dl] = incl;
+        s_k0[wib][dl] = any ? e.k0 : 0;
+        s_w0[wib][dl] = any ? e.w0 : 0;
+        s_nt[wib][dl] = ntc;
+        s_rnt[wib][dl] = ntc > 0 ? 1.f / (float)ntc : 0.f;
+        s_q[wib][dl] = a.fluct ? q : (sizeof(W) == 8 ? (W)a.p64 : (W)a.p) * q;
+        if (use_bmap)
+            for (int j = incl - nb; j < incl; ++j) s_bdep[wib][j] = (unsigned char)dl;
         __syncwarp();
         const int* off = s_off[wib];
         // bin g of the group -> depo slot d, index inside its patch, (wire, tick)
