@@ -500,6 +500,7 @@ raster_small_kernel(const __grid_constant__ RasterUnits U, ws_patches pt, long l
     __shared__ unsigned char s_bdep[NW][kBinMap];   // bin -> depo slot
     __shared__ float s_recip[kExactCap + 1];
     __shared__ float s_cdf[kCdfTable];   // exact-branch CDF rows for unit 0's survival probability
+    __shared__ uint4 s_ent[NW][64];      // drawing bins of a round: grid index (lo, hi), depo, N
     fill_recip(s_recip);
     const RasterArgs& a0 = U.a[0];
     if (a0.fluct) fill_cdf(s_cdf, s_recip, a0);
@@ -568,16 +569,67 @@ raster_small_kernel(const __grid_constant__ RasterUnits U, ws_patches pt, long l
             ia = (int)(((float)local + 0.5f) * s_rnt[wib][d]);
             ib = local - ia * s_nt[wib][d];
         };
-        for (int g = lane; g < total; g += 32) {
-            int d, local, ia, ib;
-            locate(g, d, local, ia, ib);
-            const int w = s_w0[wib][d] + ia, k = s_k0[wib][d] + ib;
-            W v = s_q[wib][d] * s_wx[wib][d][ia] * s_wt[wib][d][ib];
-            if (a.fluct)
-                v = (W)binomial_bin<P>(electrons(v), a, (uint32_t)((int64_t)w * a.nticks + k), (uint32_t)(base + d),
-                                       s_recip, cdf);
-            if (MODE == EMIT_GRID) emit<P>(a, grid, (int64_t)w * a.nticks + k, v);
-            else pt.val[pt.off[base + d] + local] = (float)v;
+        if (MODE == EMIT_GRID && a.fluct && !a.keep_all && a.T != 0u) {
+            // Rounds of 64 bins, two per lane: bins that draw are compacted
+            // into a per-warp list, normal-approximation bins first, so that
+            // a warp runs one sampler at a time (only the chunk straddling
+            // the two kinds diverges).
+            const unsigned lt = (1u << lane) - 1u;
+            for (int gb = 0; gb < total; gb += 64) {
+                int64_t idx[2];
+                int N[2];
+                bool nrm[2], exa[2];
+                uint32_t dep[2];
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int g = gb + 32 * h + lane;
+                    N[h] = 0; idx[h] = 0; dep[h] = 0;
+                    if (g < total) {
+                        int d, local, ia, ib;
+                        locate(g, d, local, ia, ib);
+                        idx[h] = (int64_t)(s_w0[wib][d] + ia) * a.nticks + s_k0[wib][d] + ib;
+                        N[h] = electrons(s_q[wib][d] * s_wx[wib][d][ia] * s_wt[wib][d][ib]);
+                        dep[h] = (uint32_t)(base + d);
+                    }
+                    nrm[h] = N[h] > a.exact_max;
+                    exa[h] = N[h] > 0 && !nrm[h];
+                }
+                const unsigned n0 = __ballot_sync(0xffffffffu, nrm[0]), n1 = __ballot_sync(0xffffffffu, nrm[1]);
+                const unsigned e0 = __ballot_sync(0xffffffffu, exa[0]), e1 = __ballot_sync(0xffffffffu, exa[1]);
+                const int nn0 = __popc(n0), nn = nn0 + __popc(n1);
+                const int ne0 = __popc(e0), ntot = nn + ne0 + __popc(e1);
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    if (nrm[h] || exa[h]) {
+                        const int pos = nrm[h] ? (h ? nn0 + __popc(n1 & lt) : __popc(n0 & lt))
+                                               : nn + (h ? ne0 + __popc(e1 & lt) : __popc(e0 & lt));
+                        s_ent[wib][pos] = make_uint4((uint32_t)idx[h], (uint32_t)((uint64_t)idx[h] >> 32), dep[h],
+                                                     (uint32_t)N[h]);
+                    }
+                }
+                __syncwarp();
+                for (int it = lane; it < ntot; it += 32) {
+                    const uint4 en = s_ent[wib][it];
+                    const int n = (int)en.w;
+                    const uint4 x = philox4x32_10(make_uint4(0u, en.x, en.z, a.evpl), a.key0, a.key1);
+                    const int c = it < nn ? normal_draw<P>(x, n, a)
+                                          : (cdf ? invert_binomial_table(n, x.x, a, cdf) : invert_binomial(n, x.x, a, s_recip));
+                    emit<P>(a, grid, (int64_t)(((uint64_t)en.y << 32) | en.x), (W)c);
+                }
+                __syncwarp();
+            }
+        } else {
+            for (int g = lane; g < total; g += 32) {
+                int d, local, ia, ib;
+                locate(g, d, local, ia, ib);
+                const int w = s_w0[wib][d] + ia, k = s_k0[wib][d] + ib;
+                W v = s_q[wib][d] * s_wx[wib][d][ia] * s_wt[wib][d][ib];
+                if (a.fluct)
+                    v = (W)binomial_bin<P>(electrons(v), a, (uint32_t)((int64_t)w * a.nticks + k), (uint32_t)(base + d),
+                                           s_recip, cdf);
+                if (MODE == EMIT_GRID) emit<P>(a, grid, (int64_t)w * a.nticks + k, v);
+                else pt.val[pt.off[base + d] + local] = (float)v;
+            }
         }
         __syncwarp();
     }
