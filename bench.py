@@ -66,7 +66,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(gpu_index), f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "100"],
+                 "--format=csv,noheader,nounits", "-lms", "50"],
                 stdout=self.tmp, stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
@@ -384,18 +384,29 @@ def run_gpu(args):
         step_per_plane()
     torch.cuda.synchronize(dev)
 
-    # timed region: the batched path (all planes of the event per launch),
-    # with the library's launch trace on the stream
+    # the batched path launched on the stream, with the library's launch
+    # trace (per-kernel device times for the roofline)
     planes[0].trace(args.steps * 8 + 16)
+    stream_ms = _time_steps(step, args.steps, stream, flush)
+    stats = planes[0].trace_read()
+    planes[0].trace(0)
+
+    # the same event one plane at a time
+    pp_ms = _time_steps(step_per_plane, args.steps, stream, flush)
+
+    # timed region: the batched step replayed from a CUDA graph (the
+    # production path: one graph launch per event)
+    batch.capture()
+    for _ in range(max(args.warmup, 0)):
+        batch.replay()
+    torch.cuda.synchronize(dev)
     sampler = ClockSampler(local) if local == 0 else None
     _barrier(dist)
     torch.cuda.synchronize(dev)
-    step_ms = _time_steps(step, args.steps, stream, flush)
+    graph_ms = _time_steps(batch.replay, args.steps, stream, flush)
     _barrier(dist)
     clocks = sampler.stop() if sampler else None
-    total_ms = _max_over_ranks(dist, float(sum(step_ms)), dev)
-    stats = planes[0].trace_read()
-    planes[0].trace(0)
+    total_ms = _max_over_ranks(dist, float(sum(graph_ms)), dev)
 
     # per-kernel algorithmic work (sum over the event's planes per launch)
     kern = {name: [n, ms] for name, (n, ms) in stats.items()}
@@ -435,50 +446,62 @@ def run_gpu(args):
                          "fp32_tflops": per_launch_flops[name] / a / 1e12,
                          "fp32_frac": per_launch_flops[name] / a / 1e12 / FP32_PEAK_TFLOPS}
 
-    # the same event one plane at a time, and replayed from a CUDA graph
-    pp_ms = _time_steps(step_per_plane, args.steps, stream, flush)
-    batch.capture()
-    batch.replay()
-    torch.cuda.synchronize(dev)
-    graph_ms = _time_steps(batch.replay, args.steps, stream, flush)
-
-    # end to end through the public API with host buffers
+    # end to end through the public API with host buffers: every step copies
+    # its depos in from pinned host memory, replays the event's graph and
+    # copies the three waveforms out; two pipelines (own planes, buffers,
+    # graph and stream) alternate so that one step's copies overlap the
+    # other's kernels
     e2e = None
     if not args.no_e2e:
         host_in = [[torch.from_numpy(a).pin_memory() for a in (d.q, d.x_mm, d.t_us)] for d in ev]
-        host_out = [torch.empty((sp.nwires, sp.nticks), dtype=torch.float32).pin_memory() for sp in w.planes]
-        dev_in = [[torch.empty_like(a, device=dev) for a in trip] for trip in host_in]
-        dd_e2e = [wiresim.DeviceDepos(*trip, device=dev) for trip in dev_in]
-        b2 = wiresim.Batch(planes, [dd_e2e], params, units_per_wave=len(planes), device=dev)
         h2d = sum(a.numel() * 4 for trip in host_in for a in trip)
-        d2h = sum(o.numel() * 4 for o in host_out)
+        pipes = []
+        for _ in range(2):
+            pl2 = [wiresim.Plane(sp.nwires, sp.nticks, sp.response, plane_id=sp.plane_id, device=dev)
+                   for sp in w.planes]
+            dev_in = [[torch.empty_like(a, device=dev) for a in trip] for trip in host_in]
+            dd2 = [wiresim.DeviceDepos(*trip, device=dev) for trip in dev_in]
+            b2 = wiresim.Batch(pl2, [dd2], params, units_per_wave=len(pl2), device=dev)
+            b2.capture()
+            host_out = [torch.empty((sp.nwires, sp.nticks), dtype=torch.float32).pin_memory() for sp in w.planes]
+            pipes.append((pl2, dev_in, b2, host_out, torch.cuda.Stream(dev)))
+        d2h = sum(o.numel() * 4 for o in pipes[0][3])
 
-        def e2e_step():
-            for trip_h, trip_d in zip(host_in, dev_in):
-                for a_h, a_d in zip(trip_h, trip_d):
-                    a_d.copy_(a_h, non_blocking=True)
-            b2.run(stream)
-            for o, oh in zip(b2.outs, host_out):
-                oh.copy_(o, non_blocking=True)
+        def e2e_step(j):
+            _, dev_in, b2, host_out, st = pipes[j % 2]
+            with torch.cuda.stream(st):
+                for trip_h, trip_d in zip(host_in, dev_in):
+                    for a_h, a_d in zip(trip_h, trip_d):
+                        a_d.copy_(a_h, non_blocking=True)
+                b2.replay()
+                for o, oh in zip(b2.outs, host_out):
+                    oh.copy_(o, non_blocking=True)
 
-        for _ in range(max(args.warmup, 1)):
-            e2e_step()
+        for j in range(max(args.warmup, 2)):
+            e2e_step(j)
         torch.cuda.synchronize(dev)
         s0 = torch.cuda.Event(enable_timing=True)
         s1 = torch.cuda.Event(enable_timing=True)
-        e_steps = max(1, args.steps)
+        e_steps = max(2, args.steps)
         _barrier(dist)
         torch.cuda.synchronize(dev)
-        s0.record(stream)
-        for _ in range(e_steps):
-            e2e_step()
-        s1.record(stream)
+        s0.record(pipes[0][4])
+        pipes[1][4].wait_event(s0)
+        for j in range(e_steps):
+            e2e_step(j)
+        pipes[0][4].wait_stream(pipes[1][4])
+        s1.record(pipes[0][4])
         torch.cuda.synchronize(dev)
         _barrier(dist)
         e_ms = _max_over_ranks(dist, s0.elapsed_time(s1), dev)
         e_total = _sum_over_ranks(dist, float(ndepo_planes * e_steps), dev)
         e2e = {"value": e_total / (e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d,
-               "d2h_bytes_per_step": d2h}
+               "d2h_bytes_per_step": d2h, "ms_per_step": e_ms / e_steps,
+               "path": "Batch.replay (CUDA graph) per step; pinned host copies in and out on the step's stream; "
+                       "two alternating pipelines overlap one step's copies with the other's kernels"}
+        for p2 in pipes:
+            for pl in p2[0]:
+                pl.close()
 
     all_depos = _sum_over_ranks(dist, float(ndepo_planes * args.steps), dev)
     all_planes = _sum_over_ranks(dist, float(len(planes) * args.steps), dev)
@@ -497,7 +520,7 @@ def run_gpu(args):
         cpu = {"value": done / secs, "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": f"{nplanes} planes of this event ({done} depo-planes), FP64, single thread"}
     pp = sum(pp_ms) / len(pp_ms)
-    gr = sum(graph_ms) / len(graph_ms)
+    sl = sum(stream_ms) / len(stream_ms)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
@@ -507,12 +530,14 @@ def run_gpu(args):
                    "fluctuate": w.fluctuate, "p_survive": w.p_survive,
                    "fft_len_tick": planes[0].info.fft_len_tick,
                    "wire_conv_variant": [pl.info.wire_conv_variant for pl in planes],
-                   "path": "ws_simulate_batch over the event's planes (one launch per stage)",
+                   "path": "ws_simulate_batch over the event's planes (one launch per stage), "
+                           "replayed from a CUDA graph",
                    "l2": "flushed between timed steps (512 MiB write)"},
         "planes_per_s": all_planes / (total_ms * 1e-3),
         "raster_scatter_depos_per_s": all_depos / (raster_ms * 1e-3) if raster_ms > 0 else None,
         "per_plane_path": {"ms_per_step": pp, "value": ndepo_planes / (pp * 1e-3)},
-        "graph_replay": {"ms_per_step": gr, "value": ndepo_planes / (gr * 1e-3)},
+        "stream_launch": {"ms_per_step": sl, "value": ndepo_planes / (sl * 1e-3),
+                          "note": "the same batched step launched kernel by kernel (traced: kernels, roofline)"},
         "kernels": kernels,
         "roofline": roof,
         "gpu_launches": launches,
@@ -529,7 +554,7 @@ def run_gpu(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="wiresim", choices=["wiresim", "reference"])
     ap.add_argument("--workload", default="three_planes", choices=["three_planes", "single_plane"])
