@@ -234,6 +234,19 @@ def run_reference(args):
 
 # -------------------------------------------------------------------- main
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # 152 SMs x 128 FP32 lanes x FMA x max SM clock
+INT_MUL_PEAK_T = 152 * 64 * 2.070e9 / 1e12          # 152 SMs x 64 INT32 multiply lanes x max SM clock
+PHILOX_MULS = 40    # 32-bit multiplies per Philox4x32-10 block: 10 rounds x 2 products x (low, high)
+
+
+def drawing_bins(wiresim, planes, depos) -> int:
+    """Bins that draw one Philox block in binomial mode: in-grid bins holding
+    N = floor(q w + 1/2) >= 1 electrons, counted on the expected-value
+    patches of the same depos."""
+    n = 0
+    for pl, dd in zip(planes, depos):
+        pt = pl.rasterize(dd, wiresim.Params(p_survive=1.0))
+        n += int((pt["val"][:pt["capacity"]] >= 0.5).sum().item())
+    return n
 
 
 def algorithmic_flops(kernel: str, nw: int, nt: int, L: int, nfreq: int, kw: int) -> float:
@@ -420,15 +433,30 @@ def run_gpu(args):
         per_launch_flops[name] = sum(algorithmic_flops(name, sp.nwires, sp.nticks, pl.info.fft_len_tick,
                                                        pl.info.nfreq, sp.response.shape[0])
                                      for pl, sp in zip(planes, w.planes))
+    # raster: the Philox multiplies of the binomial draws are its irreducible
+    # arithmetic (INT32 multiply pipe)
+    per_launch_muls = {name: 0.0 for name in kern}
+    if w.fluctuate and 0.0 < w.p_survive < 1.0 and "raster_scatter" in kern:
+        per_launch_muls["raster_scatter"] = PHILOX_MULS * float(drawing_bins(wiresim, planes, depos))
     dominant = max(kern, key=lambda k: kern[k][1])
     dn, dms = kern[dominant]
     avg_s = dms / dn * 1e-3
     peak_gbs, sm_max, peak_src = _peaks()
     bw = per_launch_bytes[dominant] / avg_s / 1e9
     fl = per_launch_flops[dominant] / avg_s / 1e12
+    im = per_launch_muls[dominant] / avg_s / 1e12
     t_hbm = per_launch_bytes[dominant] / (peak_gbs * 1e9)
     t_alu = per_launch_flops[dominant] / (FP32_PEAK_TFLOPS * 1e12)
-    if t_alu > t_hbm:
+    t_int = per_launch_muls[dominant] / (INT_MUL_PEAK_T * 1e12)
+    if t_int > max(t_alu, t_hbm):
+        roof = {"kernel": dominant, "bound": "alu", "achieved": im, "peak": INT_MUL_PEAK_T,
+                "unit": "T int32-mul/s", "frac": im / INT_MUL_PEAK_T, "traffic": None,
+                "peak_source": "derived: 152 SMs x 64 INT32 multiply lanes x 2.07 GHz "
+                               "(a Philox-only loop reaches 19.0, 94%)",
+                "work": f"{PHILOX_MULS} multiplies per Philox block x one block per drawing bin "
+                        f"({per_launch_muls[dominant] / PHILOX_MULS:.0f} bins)",
+                "hbm_frac_of_measured": bw / peak_gbs}
+    elif t_alu > t_hbm:
         roof = {"kernel": dominant, "bound": "alu", "achieved": fl, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": fl / FP32_PEAK_TFLOPS, "traffic": None,
                 "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz",
@@ -444,7 +472,8 @@ def run_gpu(args):
                          "hbm_gbs": per_launch_bytes[name] / a / 1e9,
                          "hbm_frac": per_launch_bytes[name] / a / 1e9 / peak_gbs,
                          "fp32_tflops": per_launch_flops[name] / a / 1e12,
-                         "fp32_frac": per_launch_flops[name] / a / 1e12 / FP32_PEAK_TFLOPS}
+                         "fp32_frac": per_launch_flops[name] / a / 1e12 / FP32_PEAK_TFLOPS,
+                         "int_mul_frac": per_launch_muls[name] / a / 1e12 / INT_MUL_PEAK_T}
 
     # end to end through the public API with host buffers: every step copies
     # its depos in from pinned host memory, replays the event's graph and
@@ -452,6 +481,7 @@ def run_gpu(args):
     # graph and stream) alternate so that one step's copies overlap the
     # other's kernels
     e2e = None
+    two_event = None
     if not args.no_e2e:
         host_in = [[torch.from_numpy(a).pin_memory() for a in (d.q, d.x_mm, d.t_us)] for d in ev]
         h2d = sum(a.numel() * 4 for trip in host_in for a in trip)
@@ -477,6 +507,28 @@ def run_gpu(args):
                 for o, oh in zip(b2.outs, host_out):
                     oh.copy_(o, non_blocking=True)
 
+        # the same two pipelines without the copies: events overlap on the
+        # device (one event's raster next to the other's transforms)
+        def overlap_step(j):
+            _, _, b2, _, st = pipes[j % 2]
+            with torch.cuda.stream(st):
+                b2.replay()
+
+        for j in range(max(args.warmup, 2)):
+            overlap_step(j)
+        torch.cuda.synchronize(dev)
+        o0 = torch.cuda.Event(enable_timing=True)
+        o1 = torch.cuda.Event(enable_timing=True)
+        o_steps = max(2, args.steps)
+        o0.record(pipes[0][4])
+        pipes[1][4].wait_event(o0)
+        for j in range(o_steps):
+            overlap_step(j)
+        pipes[0][4].wait_stream(pipes[1][4])
+        o1.record(pipes[0][4])
+        torch.cuda.synchronize(dev)
+        overlap_ms = o0.elapsed_time(o1) / o_steps
+
         for j in range(max(args.warmup, 2)):
             e2e_step(j)
         torch.cuda.synchronize(dev)
@@ -499,6 +551,10 @@ def run_gpu(args):
                "d2h_bytes_per_step": d2h, "ms_per_step": e_ms / e_steps,
                "path": "Batch.replay (CUDA graph) per step; pinned host copies in and out on the step's stream; "
                        "two alternating pipelines overlap one step's copies with the other's kernels"}
+        two_event = {"ms_per_step": overlap_ms, "value": ndepo_planes / (overlap_ms * 1e-3),
+                     "note": "events alternating between two graph pipelines on two streams (two events in "
+                             "flight), no host copies, no L2 flush between events (an event's buffers, ~190 MB, "
+                             "exceed L2)"}
         for p2 in pipes:
             for pl in p2[0]:
                 pl.close()
@@ -538,6 +594,7 @@ def run_gpu(args):
         "per_plane_path": {"ms_per_step": pp, "value": ndepo_planes / (pp * 1e-3)},
         "stream_launch": {"ms_per_step": sl, "value": ndepo_planes / (sl * 1e-3),
                           "note": "the same batched step launched kernel by kernel (traced: kernels, roofline)"},
+        "two_event_overlap": two_event,
         "kernels": kernels,
         "roofline": roof,
         "gpu_launches": launches,

@@ -242,9 +242,9 @@ ws_status ws_simulate(ws_plane* plane, const ws_depos* depos, const ws_params* p
 ws_status ws_convolve_noalloc(const ws_plane_desc* desc, const float* response_dev,
                               const float* grid_dev, float* out_dev, void* stream);
 
-/* Device workspace of ws_simulate_batch: a large-patch hand-over list and
- * two spectra (max nwires x (L_t/2+1) complex64) per unit of a wave.
- * units_per_wave: 1 .. 32. */
+/* Device workspace of ws_simulate_batch: two wave slots, each a large-patch
+ * hand-over list and two spectra (max nwires x (L_t/2+1) complex64) per unit
+ * of a wave.  units_per_wave: 1 .. 32. */
 ws_status ws_batch_workspace_bytes(ws_plane* const* planes, int nplanes, int units_per_wave,
                                    size_t* bytes);
 
@@ -258,8 +258,12 @@ ws_status ws_batch_workspace_bytes(ws_plane* const* planes, int nplanes, int uni
  * nwires(p) x nticks output (cleared, then simulated); event e uses
  * event_id = params->event_id + e.  All planes must share the transform
  * length, tick count and response shape (else WS_ERR_UNSUPPORTED_SIZE).
- * Results equal ws_simulate unit by unit (up to summation order).  Makes no
- * host synchronisation, so it can be captured into a CUDA graph. */
+ * Results equal ws_simulate unit by unit (up to summation order).  With more
+ * than one wave, odd waves run on a second stream owned by the library (one
+ * per host thread and device) that forks from `stream` at the start of the
+ * call and joins it at the end through events, so one wave's raster overlaps
+ * the previous wave's transforms; the call stays ordered on `stream`.  Makes
+ * no host synchronisation, so it can be captured into a CUDA graph. */
 ws_status ws_simulate_batch(ws_plane* const* planes, int nplanes, const ws_depos* depos, int nevents,
                             const ws_params* params, float* const* out_dev, void* workspace_dev,
                             size_t workspace_bytes, int units_per_wave, void* stream);

@@ -621,8 +621,10 @@ ws_status ws_simulate_backward(ws_plane* pl, const ws_depos* depos, const ws_par
 
 namespace {
 
+// Two wave slots, each with its own counters, large-patch list and spectra,
+// so that consecutive waves run on two streams.
 struct BatchLayout {
-    size_t off_counters, off_list, off_spec, spec_bytes, total;
+    size_t off_counters, off_list, off_spec, spec_bytes, slot_bytes, total;
 };
 
 ws_status batch_layout(ws_plane* const* planes, int nplanes, int units_per_wave, BatchLayout* lay) {
@@ -647,9 +649,30 @@ ws_status batch_layout(ws_plane* const* planes, int nplanes, int units_per_wave,
     lay->off_list = o; o = align256(o + sizeof(long long) * (size_t)ws::kLargeListCap);
     lay->spec_bytes = align256(sizeof(float2) * (size_t)maxw * p0->fstride);
     lay->off_spec = o; o += 2 * (size_t)units_per_wave * lay->spec_bytes;
-    lay->total = o;
+    lay->slot_bytes = o;
+    lay->total = 2 * o;
     return WS_OK;
 }
+
+// The library's second stream for this thread and device (created once, kept
+// for the life of the process).
+cudaError_t aux_stream(cudaStream_t* out) {
+    thread_local cudaStream_t streams[64] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    if (!streams[dev]) {
+        e = cudaStreamCreateWithFlags(&streams[dev], cudaStreamNonBlocking);
+        if (e != cudaSuccess) return e;
+    }
+    *out = streams[dev];
+    return cudaSuccess;
+}
+
+ws_status batch_waves(ws_plane* const* planes, int nplanes, const ws_depos* depos, const ws_params* params,
+                      float* const* out_dev, char* ws_base, const BatchLayout& lay, int units_per_wave, int nunits,
+                      cudaStream_t s0, cudaStream_t s1);
 
 }  // namespace
 
@@ -682,19 +705,61 @@ ws_status ws_simulate_batch(ws_plane* const* planes, int nplanes, const ws_depos
         if (st != WS_OK) return st;
         if (!out_dev[u] || !aligned(out_dev[u], 4)) return WS_ERR_INVALID_ARG;
     }
-    cudaStream_t s = (cudaStream_t)stream;
-    char* base = (char*)workspace_dev;
-    ws::LargeList L;
-    L.list = (long long*)(base + lay.off_list);
-    L.count = (unsigned*)(base + lay.off_counters);
-    L.done = (unsigned*)(base + lay.off_counters + 4);
-    L.cap = ws::kLargeListCap;
-    WS_CUDA(cudaMemsetAsync(base + lay.off_counters, 0, 256, s));
+    cudaStream_t s0 = (cudaStream_t)stream;
+    // Waves alternate between the caller's stream and the library's second
+    // stream (slot k % 2): one wave's raster runs beside the other's
+    // transforms.  Fork and join go through events, so the call stays
+    // stream-ordered for the caller and can be captured into a graph.
+    const int nwaves = (nunits + units_per_wave - 1) / units_per_wave;
+    const bool two = nwaves > 1;
+    cudaStream_t s1 = s0;
+    cudaEvent_t fork = nullptr, join = nullptr;
+    if (two) {
+        WS_CUDA(aux_stream(&s1));
+        WS_CUDA(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
+        cudaError_t e = cudaEventCreateWithFlags(&join, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventRecord(fork, s0);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(s1, fork, 0);
+        if (e != cudaSuccess) {
+            cudaEventDestroy(fork);
+            if (join) cudaEventDestroy(join);
+            return cuda_fail(e, "batch fork");
+        }
+    }
+    ws_status wst = batch_waves(planes, nplanes, depos, params, out_dev, (char*)workspace_dev, lay, units_per_wave,
+                                nunits, s0, s1);
+    if (two) {
+        cudaError_t e = cudaEventRecord(join, s1);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(s0, join, 0);
+        cudaEventDestroy(fork);
+        cudaEventDestroy(join);
+        if (e != cudaSuccess && wst == WS_OK) return cuda_fail(e, "batch join");
+    }
+    return wst;
+}
+
+}  // extern "C"
+
+namespace {
+
+ws_status batch_waves(ws_plane* const* planes, int nplanes, const ws_depos* depos, const ws_params* params,
+                      float* const* out_dev, char* ws_base, const BatchLayout& lay, int units_per_wave, int nunits,
+                      cudaStream_t s0, cudaStream_t s1) {
     ws_plane* p0 = planes[0];
     const ws_plane_desc& d0 = p0->desc;
     const int circ = d0.conv_mode == WS_CONV_CIRCULAR;
-    for (int u0 = 0; u0 < nunits; u0 += units_per_wave) {
+    for (int slot = 0; slot < 2; ++slot)
+        WS_CUDA(cudaMemsetAsync(ws_base + slot * lay.slot_bytes + lay.off_counters, 0, 256, slot ? s1 : s0));
+    for (int u0 = 0, wave = 0; u0 < nunits; u0 += units_per_wave, ++wave) {
         const int nu = nunits - u0 < units_per_wave ? nunits - u0 : units_per_wave;
+        const int slot = wave & 1;
+        cudaStream_t s = slot ? s1 : s0;
+        char* base = ws_base + slot * lay.slot_bytes;
+        ws::LargeList L;
+        L.list = (long long*)(base + lay.off_list);
+        L.count = (unsigned*)(base + lay.off_counters);
+        L.done = (unsigned*)(base + lay.off_counters + 4);
+        L.cap = ws::kLargeListCap;
         ws::RasterBatch rb;
         ws::RowBatch fb, ib;
         ws::ConvBatch cb;
@@ -737,7 +802,7 @@ ws_status ws_simulate_batch(ws_plane* const* planes, int nplanes, const ws_depos
     return WS_OK;
 }
 
-}  // extern "C"
+}  // namespace
 
 extern "C" {
 
