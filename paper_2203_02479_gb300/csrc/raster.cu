@@ -118,10 +118,8 @@ __device__ __forceinline__ int normal_draw(uint4 x, int N, const RasterArgs& a) 
 // N (N - 1) / 2) holds F_0 .. F_{N-1} built by invert_binomial's operations
 // for one (r, 1 - s), so the first k with u < F_k is a binary search with the
 // same result.
-constexpr int kCdfTable = kExactCap * (kExactCap + 1) / 2;
-
-__device__ void fill_cdf(float* cdf, const float* recip, const RasterArgs& a) {
-    for (int N = threadIdx.x + 1; N <= kExactCap; N += blockDim.x) {
+__device__ void fill_cdf(float* cdf, const float* recip, const RasterArgs& a, int rows) {
+    for (int N = threadIdx.x + 1; N <= rows; N += blockDim.x) {
         float f = 1.0f, base = a.inv_base;
         for (int n = N; n > 0; n >>= 1) {
             if (n & 1) f = __fmul_rn(f, base);
@@ -483,9 +481,9 @@ __device__ __forceinline__ void lane_weights(const RasterArgs& a, W mu, W sigma,
 constexpr int kBinMap = 1024;    // bins of a depo group addressed through a byte map (else a search)
 
 template <int MODE, int P>
-__global__ void __launch_bounds__(32 * kSmallWarpsPerBlock, 6)
+__global__ void __launch_bounds__(32 * kSmallWarpsPerBlock, 7)
 raster_small_kernel(const __grid_constant__ RasterUnits U, ws_patches pt, long long* __restrict__ list,
-                    unsigned* list_count, unsigned list_cap) {
+                    unsigned* list_count, unsigned list_cap, int cdf_rows) {
     using W = typename PrecT<P>::W;
     constexpr int NW = kSmallWarpsPerBlock;
     constexpr int G = kSmallGroup;
@@ -499,11 +497,11 @@ raster_small_kernel(const __grid_constant__ RasterUnits U, ws_patches pt, long l
     __shared__ W s_q[NW][G];
     __shared__ unsigned char s_bdep[NW][kBinMap];   // bin -> depo slot
     __shared__ float s_recip[kExactCap + 1];
-    __shared__ float s_cdf[kCdfTable];   // exact-branch CDF rows for unit 0's survival probability
     __shared__ uint4 s_ent[NW][64];      // drawing bins of a round: grid index (lo, hi), depo, N
+    extern __shared__ float s_cdf[];     // exact-branch CDF rows 1 .. cdf_rows for unit 0's survival probability
     fill_recip(s_recip);
     const RasterArgs& a0 = U.a[0];
-    if (a0.fluct) fill_cdf(s_cdf, s_recip, a0);
+    if (cdf_rows > 0) fill_cdf(s_cdf, s_recip, a0, cdf_rows);
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
     const int64_t nwarps = (int64_t)gridDim.x * NW;
@@ -514,7 +512,8 @@ raster_small_kernel(const __grid_constant__ RasterUnits U, ws_patches pt, long l
         const RasterArgs& a = U.a[uu];
         float* __restrict__ grid = U.grid[uu];
         const W inv_norm = window_norm<W>(a);
-        const float* cdf = (a0.fluct && a.inv_r == a0.inv_r && a.inv_base == a0.inv_base) ? s_cdf : nullptr;
+        const float* cdf = (cdf_rows > 0 && a.exact_max <= cdf_rows && a.inv_r == a0.inv_r &&
+                            a.inv_base == a0.inv_base) ? s_cdf : nullptr;
         const int64_t base = (grp - U.gprefix[uu]) * G;
         const int64_t i = base + dl;
         ExtentT<W> e;
@@ -608,13 +607,25 @@ raster_small_kernel(const __grid_constant__ RasterUnits U, ws_patches pt, long l
                     }
                 }
                 __syncwarp();
-                for (int it = lane; it < ntot; it += 32) {
-                    const uint4 en = s_ent[wib][it];
+                // entries lane and lane + 32: two independent Philox chains
+                // in flight per lane when the round has more than 32
+                auto draw = [&](int it, const uint4& en, const uint4& x) {
                     const int n = (int)en.w;
-                    const uint4 x = philox4x32_10(make_uint4(0u, en.x, en.z, a.evpl), a.key0, a.key1);
                     const int c = it < nn ? normal_draw<P>(x, n, a)
                                           : (cdf ? invert_binomial_table(n, x.x, a, cdf) : invert_binomial(n, x.x, a, s_recip));
                     emit<P>(a, grid, (int64_t)(((uint64_t)en.y << 32) | en.x), (W)c);
+                };
+                if (ntot > 32) {
+                    const bool ok1 = lane + 32 < ntot;
+                    const uint4 en0 = s_ent[wib][lane];
+                    const uint4 en1 = ok1 ? s_ent[wib][lane + 32] : en0;
+                    const uint4 x0 = philox4x32_10(make_uint4(0u, en0.x, en0.z, a.evpl), a.key0, a.key1);
+                    const uint4 x1 = philox4x32_10(make_uint4(0u, en1.x, en1.z, a.evpl), a.key0, a.key1);
+                    draw(lane, en0, x0);
+                    if (ok1) draw(lane + 32, en1, x1);
+                } else if (lane < ntot) {
+                    const uint4 en0 = s_ent[wib][lane];
+                    draw(lane, en0, philox4x32_10(make_uint4(0u, en0.x, en0.z, a.evpl), a.key0, a.key1));
                 }
                 __syncwarp();
             }
@@ -924,7 +935,12 @@ static cudaError_t launch_raster_units(const RasterUnits& U, const ws_patches& p
     if (U.dprefix[U.n] <= 0) return cudaSuccess;
     const int64_t groups = U.gprefix[U.n];
     int blocks = grid_for(groups * 32, 32 * kSmallWarpsPerBlock, 16);
-    raster_small_kernel<MODE, P><<<blocks, 32 * kSmallWarpsPerBlock, 0, s>>>(U, p, L.list, L.count, L.cap);
+    // CDF rows for the exact branch of unit 0's survival probability (rows up
+    // to its exact_max), in dynamic shared memory
+    const RasterArgs& a0 = U.a[0];
+    const int rows = (a0.fluct && !a0.keep_all && a0.T != 0u) ? (a0.exact_max < kExactCap ? a0.exact_max : kExactCap) : 0;
+    const size_t dyn = sizeof(float) * (size_t)rows * (rows + 1) / 2;
+    raster_small_kernel<MODE, P><<<blocks, 32 * kSmallWarpsPerBlock, dyn, s>>>(U, p, L.list, L.count, L.cap, rows);
     raster_kernel<MODE, P><<<num_sms() * 2, 32 * kWarpsPerBlock, 0, s>>>(U, p, L.list, L.count, L.cap, L.done);
     return cudaGetLastError();
 }
