@@ -266,7 +266,8 @@ def _time_steps(step, steps, stream, flush):
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
     for i in range(steps):
-        flush.zero_()
+        if flush is not None:
+            flush.zero_()
         starts[i].record(stream)
         step()
         ends[i].record(stream)
@@ -379,14 +380,33 @@ def run_gpu(args):
               for sp in w.planes]
     depos = [wiresim.DeviceDepos.from_plane_depos(d, device=dev) for d in ev]
     params = wiresim.Params(fluctuate=w.fluctuate, p_survive=w.p_survive, seed=w.seed, event_id=rank)
-    batch = wiresim.Batch(planes, [depos], params, units_per_wave=len(planes), device=dev)
+    flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device=dev)
+    # wave size of the event's batch, picked by timing graph replays: with
+    # fewer units per wave than planes, the second wave runs on the library's
+    # second stream beside the first
+    best = None
+    for upw in range(len(planes), 0, -1):
+        cand = wiresim.Batch(planes, [depos], params, units_per_wave=upw, device=dev)
+        cand.capture()
+        for _ in range(3):
+            cand.replay()
+        torch.cuda.synchronize(dev)
+        t = sorted(_time_steps(cand.replay, 20, torch.cuda.current_stream(dev), flush))[10]
+        if best is None or t < best[0]:
+            best = (t, upw, cand)
+        else:
+            del cand
+    _, upw_event, batch = best
     outs = [torch.empty((sp.nwires, sp.nticks), dtype=torch.float32, device=dev) for sp in w.planes]
     ndepo_planes = sum(d.n for d in ev)
     stream = torch.cuda.current_stream(dev)
-    flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device=dev)
+
+    # one launch per stage over all planes (no concurrent kernels): its
+    # traced launches give the per-kernel device times and the roofline
+    serial = wiresim.Batch(planes, [depos], params, units_per_wave=len(planes), device=dev)
 
     def step():
-        batch.run(stream)
+        serial.run(stream)
 
     def step_per_plane():
         for pl, dd, o in zip(planes, depos, outs):
@@ -397,11 +417,19 @@ def run_gpu(args):
         step_per_plane()
     torch.cuda.synchronize(dev)
 
-    # the batched path launched on the stream, with the library's launch
+    # the batched path launched kernel by kernel, with the library's launch
     # trace (per-kernel device times for the roofline)
-    planes[0].trace(args.steps * 8 + 16)
+    planes[0].trace(args.steps * 16 + 16)
     stream_ms = _time_steps(step, args.steps, stream, flush)
     stats = planes[0].trace_read()
+    planes[0].trace(0)
+    # kernels per step of the timed batch (its waves), from the same trace
+    planes[0].trace(20 * 32 + 16)
+    for _ in range(20):
+        batch.run(stream)
+    torch.cuda.synchronize(dev)
+    per_step_launches = sum(n * (2 if name == "raster_scatter" else 1)
+                            for name, (n, _) in planes[0].trace_read().items()) / 20.0
     planes[0].trace(0)
 
     # the same event one plane at a time
@@ -424,7 +452,7 @@ def run_gpu(args):
     # per-kernel algorithmic work (sum over the event's planes per launch)
     kern = {name: [n, ms] for name, (n, ms) in stats.items()}
     # each traced raster_scatter entry is two kernels (lane-pair + large-patch)
-    launches = sum(n * (2 if name == "raster_scatter" else 1) for name, (n, _) in kern.items())
+    launches = int(round(per_step_launches * args.steps))
     per_launch_bytes, per_launch_flops = {}, {}
     for name in kern:
         per_launch_bytes[name] = sum(algorithmic_bytes(name, sp.nwires, sp.nticks, pl.info.nfreq,
@@ -491,7 +519,7 @@ def run_gpu(args):
                    for sp in w.planes]
             dev_in = [[torch.empty_like(a, device=dev) for a in trip] for trip in host_in]
             dd2 = [wiresim.DeviceDepos(*trip, device=dev) for trip in dev_in]
-            b2 = wiresim.Batch(pl2, [dd2], params, units_per_wave=len(pl2), device=dev)
+            b2 = wiresim.Batch(pl2, [dd2], params, units_per_wave=upw_event, device=dev)
             b2.capture()
             host_out = [torch.empty((sp.nwires, sp.nticks), dtype=torch.float32).pin_memory() for sp in w.planes]
             pipes.append((pl2, dev_in, b2, host_out, torch.cuda.Stream(dev)))
@@ -585,6 +613,7 @@ def run_gpu(args):
                    "wires": [sp.nwires for sp in w.planes], "nticks": w.planes[0].nticks,
                    "fluctuate": w.fluctuate, "p_survive": w.p_survive,
                    "fft_len_tick": planes[0].info.fft_len_tick,
+                   "units_per_wave": upw_event,
                    "wire_conv_variant": [pl.info.wire_conv_variant for pl in planes],
                    "path": "ws_simulate_batch over the event's planes (one launch per stage), "
                            "replayed from a CUDA graph",
@@ -593,7 +622,8 @@ def run_gpu(args):
         "raster_scatter_depos_per_s": all_depos / (raster_ms * 1e-3) if raster_ms > 0 else None,
         "per_plane_path": {"ms_per_step": pp, "value": ndepo_planes / (pp * 1e-3)},
         "stream_launch": {"ms_per_step": sl, "value": ndepo_planes / (sl * 1e-3),
-                          "note": "the same batched step launched kernel by kernel (traced: kernels, roofline)"},
+                          "note": "one launch per stage over the three planes, launched kernel by kernel "
+                                  "(traced: kernels, roofline)"},
         "two_event_overlap": two_event,
         "kernels": kernels,
         "roofline": roof,
