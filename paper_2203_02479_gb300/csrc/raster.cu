@@ -83,8 +83,8 @@ __device__ __forceinline__ int invert_binomial(int N, uint32_t x0, const RasterA
 // Normal approximation of Binomial(N, p) from words 0, 1 of Philox block 0
 // (Box-Muller), with the integer part of N p taken exactly from the 64-bit
 // product N T.  In single precision the approximation itself is far coarser
-// than the rounding, so the fast logarithm and cosine are used; the FP64
-// path uses the double-precision functions.
+// than the rounding, so the fast logarithm, cosine and reciprocal square root
+// are used; the FP64 path uses the double-precision functions.
 template <int P>
 __device__ __forceinline__ int normal_draw(uint4 x, int N, const RasterArgs& a) {
     const uint64_t nt = (uint64_t)(uint32_t)N * (uint64_t)a.T;
@@ -103,13 +103,15 @@ __device__ __forceinline__ int normal_draw(uint4 x, int N, const RasterArgs& a) 
         const float two_m32 = 2.3283064365386963e-10f;  // 2^-32
         const float u1 = fmaf((float)x.x, two_m32, 0.5f * two_m32);
         const float u2 = fmaf((float)x.y, two_m32, 0.5f * two_m32);
-        // cos(2 pi u2) = -cos(2 pi (u2 - 1/2)), argument within [-pi, pi]
-        const float r = sqrtf(fmaxf(-2.f * __logf(u1), 0.f));
-        const float z = -r * __cosf(6.28318530717958648f * (u2 - 0.5f));
+        // z sd = sqrt(-2 ln u1 * N p (1 - p)) cos(2 pi u2), one square root
+        // (reciprocal-square-root form); cos(2 pi u2) = -cos(2 pi (u2 - 1/2)),
+        // argument within [-pi, pi]
         const float frac = (float)(uint32_t)nt * two_m32;
         const float pe = (float)a.T * two_m32;
-        const float sd = sqrtf(((float)ipart + frac) * (1.f - pe));
-        const int k = ipart + (int)floorf(frac + z * sd + 0.5f);
+        const float t = fmaxf(-2.f * __logf(u1), 0.f) * (((float)ipart + frac) * (1.f - pe));
+        const float rs = t > 0.f ? t * rsqrtf(t) : 0.f;
+        const float dz = -rs * __cosf(6.28318530717958648f * (u2 - 0.5f));
+        const int k = ipart + (int)floorf(frac + dz + 0.5f);
         return k < 0 ? 0 : (k > N ? N : k);
     }
 }
