@@ -237,6 +237,13 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # 152 SMs x 128 FP32 lanes x
 INT_MUL_PEAK_T = 152 * 64 * 2.070e9 / 1e12          # 152 SMs x 64 INT32 multiply lanes x max SM clock
 PHILOX_MULS = 40    # 32-bit multiplies per Philox4x32-10 block: 10 rounds x 2 products x (low, high)
 
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from
+# one ncu capture of the three-plane step with one launch per stage over the
+# three planes (the configuration of the per-kernel table), as of the current
+# kernels.
+NCU_TRAFFIC = {"three_planes_800_800_960x6000": {
+    "raster_scatter": 8.38e6, "fwd_rows": 77.6e6, "wire_conv": 86.4e6, "inv_rows": 78.4e6, "memset_grid": 3.75e6}}
+
 
 def drawing_bins(wiresim, planes, depos) -> int:
     """Bins that draw one Philox block in binomial mode: in-grid bins holding
@@ -380,12 +387,16 @@ def run_gpu(args):
               for sp in w.planes]
     depos = [wiresim.DeviceDepos.from_plane_depos(d, device=dev) for d in ev]
     params = wiresim.Params(fluctuate=w.fluctuate, p_survive=w.p_survive, seed=w.seed, event_id=rank)
+    if args.wire_conv_variant >= 0:
+        for pl in planes:
+            pl.set_wire_conv_variant(args.wire_conv_variant)
     flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device=dev)
     # wave size of the event's batch, picked by timing graph replays: with
     # fewer units per wave than planes, the second wave runs on the library's
     # second stream beside the first
     best = None
-    for upw in range(len(planes), 0, -1):
+    choices = [args.units_per_wave] if args.units_per_wave > 0 else list(range(len(planes), 0, -1))
+    for upw in choices:
         cand = wiresim.Batch(planes, [depos], params, units_per_wave=upw, device=dev)
         cand.capture()
         for _ in range(3):
@@ -444,7 +455,11 @@ def run_gpu(args):
     sampler = ClockSampler(local) if local == 0 else None
     _barrier(dist)
     torch.cuda.synchronize(dev)
+    if args.profile_timed:
+        torch.cuda.profiler.start()
     graph_ms = _time_steps(batch.replay, args.steps, stream, flush)
+    if args.profile_timed:
+        torch.cuda.profiler.stop()
     _barrier(dist)
     clocks = sampler.stop() if sampler else None
     total_ms = _max_over_ranks(dist, float(sum(graph_ms)), dev)
@@ -476,9 +491,10 @@ def run_gpu(args):
     t_hbm = per_launch_bytes[dominant] / (peak_gbs * 1e9)
     t_alu = per_launch_flops[dominant] / (FP32_PEAK_TFLOPS * 1e12)
     t_int = per_launch_muls[dominant] / (INT_MUL_PEAK_T * 1e12)
+    traffic = NCU_TRAFFIC.get(w.name, {}).get(dominant)
     if t_int > max(t_alu, t_hbm):
         roof = {"kernel": dominant, "bound": "alu", "achieved": im, "peak": INT_MUL_PEAK_T,
-                "unit": "T int32-mul/s", "frac": im / INT_MUL_PEAK_T, "traffic": None,
+                "unit": "T int32-mul/s", "frac": im / INT_MUL_PEAK_T, "traffic": traffic,
                 "peak_source": "derived: 152 SMs x 64 INT32 multiply lanes x 2.07 GHz "
                                "(a Philox-only loop reaches 19.0, 94%)",
                 "work": f"{PHILOX_MULS} multiplies per Philox block x one block per drawing bin "
@@ -486,12 +502,12 @@ def run_gpu(args):
                 "hbm_frac_of_measured": bw / peak_gbs}
     elif t_alu > t_hbm:
         roof = {"kernel": dominant, "bound": "alu", "achieved": fl, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": fl / FP32_PEAK_TFLOPS, "traffic": None,
+                "frac": fl / FP32_PEAK_TFLOPS, "traffic": traffic,
                 "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz",
                 "hbm_frac_of_measured": bw / peak_gbs}
     else:
         roof = {"kernel": dominant, "bound": "hbm", "achieved": bw, "peak": peak_gbs, "unit": "GB/s",
-                "frac": bw / peak_gbs, "traffic": None, "peak_source": f"{peak_src} hbm_gbs",
+                "frac": bw / peak_gbs, "traffic": traffic, "peak_source": f"{peak_src} hbm_gbs",
                 "alu_frac_of_derived": fl / FP32_PEAK_TFLOPS}
     kernels = {}
     for name, (n, ms) in sorted(kern.items()):
@@ -501,7 +517,8 @@ def run_gpu(args):
                          "hbm_frac": per_launch_bytes[name] / a / 1e9 / peak_gbs,
                          "fp32_tflops": per_launch_flops[name] / a / 1e12,
                          "fp32_frac": per_launch_flops[name] / a / 1e12 / FP32_PEAK_TFLOPS,
-                         "int_mul_frac": per_launch_muls[name] / a / 1e12 / INT_MUL_PEAK_T}
+                         "int_mul_frac": per_launch_muls[name] / a / 1e12 / INT_MUL_PEAK_T,
+                         "ncu_dram_bytes": NCU_TRAFFIC.get(w.name, {}).get(name)}
 
     # end to end through the public API with host buffers: every step copies
     # its depos in from pinned host memory, replays the event's graph and
@@ -652,6 +669,12 @@ def main():
                     help="print the per-plane precision comparison of the large three-plane workload instead")
     ap.add_argument("--precision-depos", type=int, default=2_000_000)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--wire-conv-variant", type=int, default=-1,
+                    help="force the planes' wire-convolution kernel (default: each plane's autotuned choice)")
+    ap.add_argument("--units-per-wave", type=int, default=0,
+                    help="force the event's wave size (default: picked by timing)")
+    ap.add_argument("--profile-timed", action="store_true",
+                    help="bracket the timed graph replays with cudaProfilerStart/Stop (for ncu --profile-from-start off)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "wiresim":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)

@@ -377,6 +377,7 @@ class Plane:
     def set_wire_conv_variant(self, variant: int):
         _check(load_library().ws_plane_set_wire_conv_variant(self.handle, variant),
                "ws_plane_set_wire_conv_variant")
+        self.info = ws_plane_get_info(self.handle)
 
     def set_response(self, response, stream=None):
         torch = _torch()
