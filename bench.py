@@ -12,11 +12,17 @@ reported beside it.
 Prints ONE JSON line (rank 0).  ``--impl reference`` times the FP64 oracle
 on the host cores instead (the CPU baseline arm).
 
-Timing: W untimed warm-up steps; then K steps, each bracketed by CUDA events
-on the launching stream, with L2 flushed (a 512 MiB write) between steps,
-outside the events; barrier + synchronize on both sides; the max over ranks.
-Per-kernel device times come from the library's own launch trace (CUDA
-events around every launch, on the same stream) over the same timed steps.
+Timing: the event's batch (wave size picked by timing) is captured into a
+CUDA graph; W untimed warm-up replays; then K replays, each bracketed by
+CUDA events on the launching stream, with L2 flushed (a 512 MiB write)
+between steps, outside the events; barrier + synchronize on both sides; the
+max over ranks.  Per-kernel device times come from the library's own launch
+trace (CUDA events around every launch, on the launching stream) over K
+steps of the same event launched one stage at a time.
+
+Under torchrun each rank simulates its own event (its own seed and event id):
+the units are independent, so there is no collective on the data path, only
+the barrier and the max/sum reductions of the timing (weak scaling).
 """
 from __future__ import annotations
 
