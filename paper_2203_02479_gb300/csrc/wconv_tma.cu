@@ -81,6 +81,8 @@ wire_conv_tma_kernel(const __grid_constant__ TmaConvUnits U, int nfreq, int64_t 
     __shared__ __align__(8) uint64_t bar[2];
     auto buf = [&](int st) { return reinterpret_cast<float2*>(smem + (st ? TILE_BYTES : 0u)); };
     const int total = U.prefix[U.n];
+    // tiles run wire block fastest, so a CTA's consecutive tiles share their
+    // column block (the taps stay in registers) and overlap in halo rows
     auto tile_of = [&](int t, int& u, int& k0, int& w0) {
         int lo = 0, hi = U.n - 1;
         while (lo < hi) {
@@ -89,8 +91,9 @@ wire_conv_tma_kernel(const __grid_constant__ TmaConvUnits U, int nfreq, int64_t 
         }
         u = lo;
         const int tt = t - U.prefix[u];
-        k0 = (tt % nkblocks) * kCols;
-        w0 = (tt / nkblocks) * B;
+        const int nwb = (U.nwires[u] + B - 1) / B;
+        k0 = (tt / nwb) * kCols;
+        w0 = (tt % nwb) * B;
     };
     auto issue = [&](int t, int st) {
         int u, k0, w0;
@@ -103,14 +106,19 @@ wire_conv_tma_kernel(const __grid_constant__ TmaConvUnits U, int nfreq, int64_t 
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
-    int t = blockIdx.x;
-    if (t < total && threadIdx.x == 0) issue(t, 0);
+    // each CTA takes a contiguous run of tiles
+    const int t_end = (int)((int64_t)total * (blockIdx.x + 1) / gridDim.x);
+    int t = (int)((int64_t)total * blockIdx.x / gridDim.x);
+    if (t < t_end && threadIdx.x == 0) issue(t, 0);
     uint32_t parity[2] = {0u, 0u};
     bool inflight_next = false;
-    for (int i = 0; t < total; ++i, t += gridDim.x) {
+    int cur_u = -1, cur_k = -1;
+    float cc[K], cm[K], cp[K];   // taps of the current column block (Karatsuba form)
+    float2 c[K];                 // the same, plain form
+    for (int i = 0; t < t_end; ++i, ++t) {
         const int st = i & 1;
-        const int tn = t + gridDim.x;
-        inflight_next = tn < total;
+        const int tn = t + 1;
+        inflight_next = tn < t_end;
         if (inflight_next && threadIdx.x == 0) issue(tn, st ^ 1);
         const bool ok = mbar_wait(&bar[st], parity[st]);
         parity[st] ^= 1u;
@@ -128,16 +136,24 @@ wire_conv_tma_kernel(const __grid_constant__ TmaConvUnits U, int nfreq, int64_t 
         float2* __restrict__ Y = static_cast<float2*>(U.Y[u]);
         const float2* __restrict__ Rt = static_cast<const float2*>(U.Rt[u]);
         const float2* col = buf(st) + threadIdx.x;
-        if (k < nfreq) {
-            if constexpr (KARATSUBA) {
-                float cc[K], cm[K], cp[K];
+        if (u != cur_u || k0 != cur_k) {
+            cur_u = u;
+            cur_k = k0;
 #pragma unroll
-                for (int r = 0; r < K; ++r) {
-                    const float2 v = r < kw ? __ldg(&Rt[(int64_t)r * stride + k]) : make_float2(0.f, 0.f);
+            for (int r = 0; r < K; ++r) {
+                const float2 v =
+                    (r < kw && k < nfreq) ? __ldg(&Rt[(int64_t)r * stride + k]) : make_float2(0.f, 0.f);
+                if constexpr (KARATSUBA) {
                     cc[r] = v.x;
                     cm[r] = v.y - v.x;
                     cp[r] = v.x + v.y;
+                } else {
+                    c[r] = v;
                 }
+            }
+        }
+        if (k < nfreq) {
+            if constexpr (KARATSUBA) {
                 float k1[B], k2[B], k3[B];
 #pragma unroll
                 for (int b = 0; b < B; ++b) k1[b] = k2[b] = k3[b] = 0.f;
@@ -159,9 +175,6 @@ wire_conv_tma_kernel(const __grid_constant__ TmaConvUnits U, int nfreq, int64_t 
                 for (int b = 0; b < B; ++b)
                     if (w0 + b < nwires) Y[(int64_t)(w0 + b) * stride + k] = make_float2(k1[b] - k3[b], k1[b] + k2[b]);
             } else {
-                float2 c[K];
-#pragma unroll
-                for (int r = 0; r < K; ++r) c[r] = r < kw ? __ldg(&Rt[(int64_t)r * stride + k]) : make_float2(0.f, 0.f);
                 float2 acc[B];
 #pragma unroll
                 for (int b = 0; b < B; ++b) acc[b] = make_float2(0.f, 0.f);
