@@ -233,17 +233,32 @@ __device__ __forceinline__ bool axis_range(W mu, W sigma, W delta, W nsig, int n
     return l <= h;
 }
 
+// A depo's inputs as loaded from the arrays (widths only if given).
+struct DepoIn {
+    float q, x, t, sig_t, sig_x;
+};
+
+__device__ __forceinline__ DepoIn load_depo(const RasterArgs& a, int64_t i) {
+    DepoIn d;
+    d.q = __ldg(a.q + i);
+    d.x = __ldg(a.x + i);
+    d.t = __ldg(a.t + i);
+    d.sig_t = a.sig_t ? __ldg(a.sig_t + i) : 0.f;
+    d.sig_x = a.sig_t ? __ldg(a.sig_x + i) : 0.f;
+    return d;
+}
+
 // Returns false if the depo has no in-grid bins or is invalid (then *bad).
 template <typename W>
-__device__ __forceinline__ bool depo_extent(const RasterArgs& a, int64_t i, ExtentT<W>* e, W* q, bool* bad) {
+__device__ __forceinline__ bool depo_extent(const RasterArgs& a, const DepoIn& in, ExtentT<W>* e, W* q, bool* bad) {
     *bad = false;
-    const float qf = __ldg(a.q + i), xf = __ldg(a.x + i), tf = __ldg(a.t + i);
+    const float qf = in.q, xf = in.x, tf = in.t;
     bool ok = isfinite(qf) && isfinite(xf) && isfinite(tf);
     const W ti = (W)tf;
     W st, sx;
     if (a.sig_t) {
-        st = (W)__ldg(a.sig_t + i);
-        sx = (W)__ldg(a.sig_x + i);
+        st = (W)in.sig_t;
+        sx = (W)in.sig_x;
     } else {
         ok = ok && tf >= 0.f;
         const W tt = ti > (W)0 ? ti : (W)0;
@@ -268,6 +283,11 @@ __device__ __forceinline__ bool depo_extent(const RasterArgs& a, int64_t i, Exte
     if (!axis_range<W>(ti, st, tick, nsig, a.nticks, &e->k0, &e->k1, &e->point_t)) return false;
     if (!axis_range<W>((W)xf, sx, pitch, nsig, a.nwires, &e->w0, &e->w1, &e->point_x)) return false;
     return true;
+}
+
+template <typename W>
+__device__ __forceinline__ bool depo_extent(const RasterArgs& a, int64_t i, ExtentT<W>* e, W* q, bool* bad) {
+    return depo_extent<W>(a, load_depo(a, i), e, q, bad);
 }
 
 // Weight of a bin from its two clamped standardized edges u and erfc(|u|).
@@ -363,12 +383,15 @@ raster_kernel(const __grid_constant__ RasterUnits U, ws_patches pt, const long l
     __shared__ W s_wt[kWarpsPerBlock][kChunk];
     __shared__ W s_wx[kWarpsPerBlock][kChunk];
     __shared__ float s_recip[kExactCap + 1];
+    const unsigned nlist = *(volatile unsigned*)list_count;
+    const bool use_list = nlist <= list_cap;
+    // an empty list needs no work and no reset (the counters are zero)
+    if (use_list && nlist == 0u) return;
     fill_recip(s_recip);
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
     const int64_t nwarps = (int64_t)gridDim.x * kWarpsPerBlock;
-    const unsigned nlist = *(volatile unsigned*)list_count;
-    const bool use_list = nlist <= list_cap;
+
     const int64_t nitems = use_list ? (int64_t)nlist : U.dprefix[U.n];
     for (int64_t it = (int64_t)blockIdx.x * kWarpsPerBlock + wib; it < nitems; it += nwarps) {
         int u;
@@ -480,6 +503,7 @@ __device__ __forceinline__ void lane_weights(const RasterArgs& a, W mu, W sigma,
     lane_axis_weights<W, W>(mu, sigma, delta, nsig, point, first, nb, inv_norm, w);
 }
 
+constexpr int kRoundPerLane = 2;   // bins per lane per binomial round
 constexpr int kBinMap = 1024;    // bins of a depo group addressed through a byte map (else a search)
 
 template <int MODE, int P>
@@ -499,7 +523,7 @@ raster_small_kernel(const __grid_constant__ RasterUnits U, ws_patches pt, long l
     __shared__ W s_q[NW][G];
     __shared__ unsigned char s_bdep[NW][kBinMap];   // bin -> depo slot
     __shared__ float s_recip[kExactCap + 1];
-    __shared__ uint4 s_ent[NW][64];      // drawing bins of a round: grid index (lo, hi), depo, N
+    __shared__ uint4 s_ent[NW][32 * kRoundPerLane];   // drawing bins of a round: grid index (lo, hi), depo, N
     extern __shared__ float s_cdf[];     // exact-branch CDF rows 1 .. cdf_rows for unit 0's survival probability
     fill_recip(s_recip);
     const RasterArgs& a0 = U.a[0];
@@ -571,18 +595,21 @@ raster_small_kernel(const __grid_constant__ RasterUnits U, ws_patches pt, long l
             ib = local - ia * s_nt[wib][d];
         };
         if (MODE == EMIT_GRID && a.fluct && !a.keep_all && a.T != 0u) {
-            // Rounds of 64 bins, two per lane: bins that draw are compacted
-            // into a per-warp list, normal-approximation bins first, so that
-            // a warp runs one sampler at a time (only the chunk straddling
-            // the two kinds diverges).
+            // Rounds of 32 kRoundPerLane bins, kRoundPerLane per lane: bins
+            // that draw are compacted into a per-warp list, normal-
+            // approximation bins first, so that a warp runs one sampler at a
+            // time (only the chunk straddling the two kinds diverges); a
+            // full round keeps kRoundPerLane independent Philox chains in
+            // flight per lane.
+            constexpr int H = kRoundPerLane;
             const unsigned lt = (1u << lane) - 1u;
-            for (int gb = 0; gb < total; gb += 64) {
-                int64_t idx[2];
-                int N[2];
-                bool nrm[2], exa[2];
-                uint32_t dep[2];
+            for (int gb = 0; gb < total; gb += 32 * H) {
+                int64_t idx[H];
+                int N[H];
+                bool nrm[H], exa[H];
+                uint32_t dep[H];
 #pragma unroll
-                for (int h = 0; h < 2; ++h) {
+                for (int h = 0; h < H; ++h) {
                     const int g = gb + 32 * h + lane;
                     N[h] = 0; idx[h] = 0; dep[h] = 0;
                     if (g < total) {
@@ -595,39 +622,48 @@ raster_small_kernel(const __grid_constant__ RasterUnits U, ws_patches pt, long l
                     nrm[h] = N[h] > a.exact_max;
                     exa[h] = N[h] > 0 && !nrm[h];
                 }
-                const unsigned n0 = __ballot_sync(0xffffffffu, nrm[0]), n1 = __ballot_sync(0xffffffffu, nrm[1]);
-                const unsigned e0 = __ballot_sync(0xffffffffu, exa[0]), e1 = __ballot_sync(0xffffffffu, exa[1]);
-                const int nn0 = __popc(n0), nn = nn0 + __popc(n1);
-                const int ne0 = __popc(e0), ntot = nn + ne0 + __popc(e1);
+                unsigned nb[H], eb[H];
+                int nbefore[H], ebefore[H], nn = 0, ne = 0;
 #pragma unroll
-                for (int h = 0; h < 2; ++h) {
+                for (int h = 0; h < H; ++h) {
+                    nb[h] = __ballot_sync(0xffffffffu, nrm[h]);
+                    eb[h] = __ballot_sync(0xffffffffu, exa[h]);
+                    nbefore[h] = nn;
+                    ebefore[h] = ne;
+                    nn += __popc(nb[h]);
+                    ne += __popc(eb[h]);
+                }
+                const int ntot = nn + ne;
+#pragma unroll
+                for (int h = 0; h < H; ++h) {
                     if (nrm[h] || exa[h]) {
-                        const int pos = nrm[h] ? (h ? nn0 + __popc(n1 & lt) : __popc(n0 & lt))
-                                               : nn + (h ? ne0 + __popc(e1 & lt) : __popc(e0 & lt));
+                        const int pos = nrm[h] ? nbefore[h] + __popc(nb[h] & lt) : nn + ebefore[h] + __popc(eb[h] & lt);
                         s_ent[wib][pos] = make_uint4((uint32_t)idx[h], (uint32_t)((uint64_t)idx[h] >> 32), dep[h],
                                                      (uint32_t)N[h]);
                     }
                 }
                 __syncwarp();
-                // entries lane and lane + 32: two independent Philox chains
-                // in flight per lane when the round has more than 32
                 auto draw = [&](int it, const uint4& en, const uint4& x) {
                     const int n = (int)en.w;
                     const int c = it < nn ? normal_draw<P>(x, n, a)
                                           : (cdf ? invert_binomial_table(n, x.x, a, cdf) : invert_binomial(n, x.x, a, s_recip));
                     emit<P>(a, grid, (int64_t)(((uint64_t)en.y << 32) | en.x), (W)c);
                 };
-                if (ntot > 32) {
-                    const bool ok1 = lane + 32 < ntot;
-                    const uint4 en0 = s_ent[wib][lane];
-                    const uint4 en1 = ok1 ? s_ent[wib][lane + 32] : en0;
-                    const uint4 x0 = philox4x32_10(make_uint4(0u, en0.x, en0.z, a.evpl), a.key0, a.key1);
-                    const uint4 x1 = philox4x32_10(make_uint4(0u, en1.x, en1.z, a.evpl), a.key0, a.key1);
-                    draw(lane, en0, x0);
-                    if (ok1) draw(lane + 32, en1, x1);
-                } else if (lane < ntot) {
-                    const uint4 en0 = s_ent[wib][lane];
-                    draw(lane, en0, philox4x32_10(make_uint4(0u, en0.x, en0.z, a.evpl), a.key0, a.key1));
+                if (ntot > 32 * (H - 1)) {
+                    // entries lane + 32 h: H independent Philox chains per lane
+                    uint4 en[H], x[H];
+#pragma unroll
+                    for (int h = 0; h < H; ++h) en[h] = (lane + 32 * h < ntot) ? s_ent[wib][lane + 32 * h] : s_ent[wib][lane];
+#pragma unroll
+                    for (int h = 0; h < H; ++h) x[h] = philox4x32_10(make_uint4(0u, en[h].x, en[h].z, a.evpl), a.key0, a.key1);
+#pragma unroll
+                    for (int h = 0; h < H; ++h)
+                        if (lane + 32 * h < ntot) draw(lane + 32 * h, en[h], x[h]);
+                } else {
+                    for (int it = lane; it < ntot; it += 32) {
+                        const uint4 en = s_ent[wib][it];
+                        draw(it, en, philox4x32_10(make_uint4(0u, en.x, en.z, a.evpl), a.key0, a.key1));
+                    }
                 }
                 __syncwarp();
             }
