@@ -332,6 +332,32 @@ def batched_workload_comparison(wiresim, dev, stream, flush, steps: int):
             "batched_ms": g, "per_plane_ms": pp}
 
 
+def adjoint_leg(wiresim, dev, stream, flush, steps: int):
+    """Forward and adjoint (ws_simulate_backward: gradients for q, x, t of
+    every depo, D_L, D_T and the response) of one 960 x 6000 plane with
+    20,000 depos (t >= 1 us), expected-value mode."""
+    import torch
+    w = inputs.single_plane(n=20000, seed=1003, t_min_us=1.0)
+    sp, d = w.planes[0], w.events[0][0]
+    plane = wiresim.Plane(sp.nwires, sp.nticks, sp.response, device=dev)
+    dd = wiresim.DeviceDepos.from_plane_depos(d, device=dev)
+    params = wiresim.Params()
+    out = torch.empty((sp.nwires, sp.nticks), dtype=torch.float32, device=dev)
+    g = torch.randn((sp.nwires, sp.nticks), generator=torch.Generator().manual_seed(1003)).to(dev)
+    fwd = lambda: plane.simulate(dd, params, out=out, stream=stream)
+    bwd = lambda: plane.backward(dd, params, g, want_response=True, stream=stream)
+    for _ in range(3):
+        fwd()
+        bwd()
+    torch.cuda.synchronize(dev)
+    f_ms = sorted(_time_steps(fwd, steps, stream, flush))[steps // 2]
+    b_ms = sorted(_time_steps(bwd, steps, stream, flush))[steps // 2]
+    plane.close()
+    return {"workload": "single_plane_960x6000, 20000 depos (t >= 1 us), expected value",
+            "forward_ms": f_ms, "backward_ms": b_ms, "backward_over_forward": b_ms / f_ms,
+            "backward_outputs": "dL/dq, dL/dx, dL/dt per depo; dL/dD_L, dL/dD_T; dL/dR (21 x 200)"}
+
+
 def precision_study(args):
     """Large three-plane detector (2560/2560/3840 x 6000, 2M track depos):
     every GPU precision path against the FP64 oracle, per plane, with the
@@ -613,8 +639,10 @@ def run_gpu(args):
     all_depos = _sum_over_ranks(dist, float(ndepo_planes * args.steps), dev)
     all_planes = _sum_over_ranks(dist, float(len(planes) * args.steps), dev)
     batched = None
+    adjoint = None
     if rank == 0 and world == 1 and not args.no_batched_workload:
         batched = batched_workload_comparison(wiresim, dev, stream, flush, max(3, min(args.steps, 10)))
+        adjoint = adjoint_leg(wiresim, dev, stream, flush, max(5, min(args.steps, 50)))
     if rank != 0:
         if dist is not None:
             dist.destroy_process_group()
@@ -655,6 +683,7 @@ def run_gpu(args):
         "e2e": e2e,
         "cpu_baseline": cpu,
         "batched_workload": batched,
+        "adjoint": adjoint,
     }
     print(json.dumps(line), flush=True)
     if dist is not None:

@@ -745,40 +745,58 @@ __global__ void adj_coeffs_kernel(const float2* __restrict__ Rt, float2* __restr
 }
 
 // Response-gradient spectra: A[r][k] += scale * sum_w conj(XS[w - (r - c)][k])
-// XG[w][k] over this thread's chunk of wires (XS zero outside the grid, or
-// wrapped), accumulated into A with atomics.
-constexpr int kRespGradRows = 64;
+// XG[w][k] over this block's chunk of wires (XS zero outside the grid, or
+// wrapped), accumulated into A with atomics.  Each thread walks its column
+// down the chunk keeping the K rows of XS that the current wire needs in a
+// register window (row w + c - K + 1 + j in slot (step + j) mod K), so every
+// element of XS and XG is read once per chunk.
+constexpr int kRespGradRows = 32;
+constexpr int kRespGradThreads = 64;
 
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(kRespGradThreads)
 resp_grad_kernel(const float2* __restrict__ XG, const float2* __restrict__ XS, float2* __restrict__ A, int nwires,
                  int nfreq, int64_t stride, int kw, int center, int circular, float scale) {
+    constexpr int K = kMaxRespWires;
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= nfreq) return;
     const int w0 = blockIdx.y * kRespGradRows;
     const int w1 = min(nwires, w0 + kRespGradRows);
-    float2 acc[kMaxRespWires];
+    auto xs_row = [&](int row) -> float2 {
+        if (circular) {
+            row %= nwires;
+            if (row < 0) row += nwires;
+        } else if (row < 0 || row >= nwires) {
+            return make_float2(0.f, 0.f);
+        }
+        return __ldg(&XS[(int64_t)row * stride + k]);
+    };
+    float2 win[K];
+    float2 acc[K];
 #pragma unroll
-    for (int r = 0; r < kMaxRespWires; ++r) acc[r] = make_float2(0.f, 0.f);
-    for (int w = w0; w < w1; ++w) {
-        const float2 xg = __ldg(&XG[(int64_t)w * stride + k]);
+    for (int r = 0; r < K; ++r) acc[r] = make_float2(0.f, 0.f);
+    // window of the first wire: rows w0 + c - K + 1 + j, j = 0 .. K - 2 (row
+    // j = K - 1 is loaded by the first step)
 #pragma unroll
-        for (int r = 0; r < kMaxRespWires; ++r) {
-            if (r >= kw) break;
-            int ws = w - (r - center);
-            if (circular) {
-                ws %= nwires;
-                if (ws < 0) ws += nwires;
-            } else if (ws < 0 || ws >= nwires) {
-                continue;
+    for (int j = 0; j < K - 1; ++j) win[j] = xs_row(w0 + center - K + 1 + j);
+    for (int wb = w0; wb < w1; wb += K) {
+#pragma unroll
+        for (int jj = 0; jj < K; ++jj) {
+            const int w = wb + jj;
+            if (w < w1) {
+                win[(jj + K - 1) % K] = xs_row(w + center);
+                const float2 xg = __ldg(&XG[(int64_t)w * stride + k]);
+#pragma unroll
+                for (int r = 0; r < K; ++r) {
+                    // XS row w - (r - c) = w + c - K + 1 + j with j = K - 1 - r
+                    const float2 xs = win[(jj + K - 1 - r) % K];
+                    acc[r].x = fmaf(xs.x, xg.x, fmaf(xs.y, xg.y, acc[r].x));
+                    acc[r].y = fmaf(xs.x, xg.y, fmaf(-xs.y, xg.x, acc[r].y));
+                }
             }
-            const float2 xs = __ldg(&XS[(int64_t)ws * stride + k]);
-            // conj(xs) * xg
-            acc[r].x = fmaf(xs.x, xg.x, fmaf(xs.y, xg.y, acc[r].x));
-            acc[r].y = fmaf(xs.x, xg.y, fmaf(-xs.y, xg.x, acc[r].y));
         }
     }
 #pragma unroll
-    for (int r = 0; r < kMaxRespWires; ++r) {
+    for (int r = 0; r < K; ++r) {
         if (r >= kw) break;
         atomicAdd(&A[(int64_t)r * stride + k].x, scale * acc[r].x);
         atomicAdd(&A[(int64_t)r * stride + k].y, scale * acc[r].y);
@@ -795,8 +813,8 @@ cudaError_t launch_adj_coeffs(const float2* Rt, float2* A, int kw, int64_t strid
 cudaError_t launch_resp_grad(const float2* XG, const float2* XS, float2* A, int nwires, int nfreq, int64_t stride,
                              int kw, int center, int circular, float scale, cudaStream_t s) {
     if (nwires <= 0 || nfreq <= 0) return cudaSuccess;
-    dim3 grid((nfreq + 127) / 128, (nwires + kRespGradRows - 1) / kRespGradRows);
-    resp_grad_kernel<<<grid, 128, 0, s>>>(XG, XS, A, nwires, nfreq, stride, kw, center, circular, scale);
+    dim3 grid((nfreq + kRespGradThreads - 1) / kRespGradThreads, (nwires + kRespGradRows - 1) / kRespGradRows);
+    resp_grad_kernel<<<grid, kRespGradThreads, 0, s>>>(XG, XS, A, nwires, nfreq, stride, kw, center, circular, scale);
     return cudaGetLastError();
 }
 

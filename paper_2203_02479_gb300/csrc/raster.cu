@@ -700,10 +700,11 @@ struct GradArgs {
     double DL, DT;
 };
 
-// Per-axis weights and their mu / sigma derivatives for bins [first, first + nb).
+// Per-axis weights and their mu / sigma derivatives for bins [first, first + nb)
+// (edge values: clamped u, phi(u)/sigma and erfc(|u|/sqrt 2), one per edge).
 __device__ __forceinline__ void axis_weights_grad(float mu, float sigma, float delta, float nsig, bool point,
                                                   int first, int nb, float inv_norm, float* u_s, float* c_s,
-                                                  float* w, float* dmu, float* dsig, int lane) {
+                                                  float* v_s, float* w, float* dmu, float* dsig, int lane) {
     if (point) {
         for (int b = lane; b < nb; b += 32) { w[b] = 1.f; dmu[b] = 0.f; dsig[b] = 0.f; }
         __syncwarp();
@@ -718,13 +719,13 @@ __device__ __forceinline__ void axis_weights_grad(float mu, float sigma, float d
         u_s[j] = uc;
         // phi(u) / sigma, or 0 on a window bound
         c_s[j] = clamped ? 0.f : 0.398942280401432678f * __expf(-0.5f * uc * uc) * inv_s;
+        v_s[j] = erfcf(fabsf(uc) * 0.707106781186547524f);
     }
     __syncwarp();
-    const float r2 = 0.707106781186547524f;
     for (int b = lane; b < nb; b += 32) {
         const float u0 = u_s[b], u1 = u_s[b + 1];
         const float p0 = c_s[b], p1 = c_s[b + 1];
-        const float v0 = erfcf(fabsf(u0) * r2), v1 = erfcf(fabsf(u1) * r2);
+        const float v0 = v_s[b], v1 = v_s[b + 1];
         float m;
         if (u0 >= 0.f) m = 0.5f * (v0 - v1);
         else if (u1 <= 0.f) m = 0.5f * (v1 - v0);
@@ -740,6 +741,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock)
 depo_grad_kernel(RasterArgs a, GradArgs g) {
     __shared__ float s_u[kWarpsPerBlock][kChunk + 1];
     __shared__ float s_c[kWarpsPerBlock][kChunk + 1];
+    __shared__ float s_v[kWarpsPerBlock][kChunk + 1];
     __shared__ float s_wt[kWarpsPerBlock][3][kChunk];
     __shared__ float s_wx[kWarpsPerBlock][3][kChunk];
     __shared__ double s_red[kWarpsPerBlock][2];
@@ -766,11 +768,11 @@ depo_grad_kernel(RasterArgs a, GradArgs g) {
         for (int kc = any ? e.k0 : 1; any && kc <= e.k1; kc += kChunk) {
             const int ntc = min(kChunk, e.k1 - kc + 1);
             axis_weights_grad(e.mu_t, e.st, a.tick, a.nsig, e.point_t, kc, ntc, inv_norm, s_u[wib], s_c[wib],
-                              s_wt[wib][0], s_wt[wib][1], s_wt[wib][2], lane);
+                              s_v[wib], s_wt[wib][0], s_wt[wib][1], s_wt[wib][2], lane);
             for (int wc = e.w0; wc <= e.w1; wc += kChunk) {
                 const int nxc = min(kChunk, e.w1 - wc + 1);
                 axis_weights_grad(e.mu_x, e.sx, a.pitch, a.nsig, e.point_x, wc, nxc, inv_norm, s_u[wib],
-                                  s_c[wib], s_wx[wib][0], s_wx[wib][1], s_wx[wib][2], lane);
+                                  s_c[wib], s_v[wib], s_wx[wib][0], s_wx[wib][1], s_wx[wib][2], lane);
                 for (int idx = lane; idx < nxc * ntc; idx += 32) {
                     const int ia = idx / ntc, ib = idx - ia * ntc;
                     const float gv = __ldg(g.dS + (int64_t)(wc + ia) * a.nticks + kc + ib);
