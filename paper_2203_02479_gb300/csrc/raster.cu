@@ -737,33 +737,184 @@ __device__ __forceinline__ void axis_weights_grad(float mu, float sigma, float d
     __syncwarp();
 }
 
+// One more bin on each side of a non-point axis: the FP32 bin range can drop
+// a sliver bin whose edge lies within rounding of the window bound; bins
+// wholly outside get both edges clamped (zero weight, zero derivative), so
+// the clamp test on u alone decides which side of the kink the depo is on.
+__device__ __forceinline__ void widen_for_grad(const RasterArgs& a, Extent& e) {
+    if (!e.point_t) { e.k0 = max(e.k0 - 1, 0); e.k1 = min(e.k1 + 1, a.nticks - 1); }
+    if (!e.point_x) { e.w0 = max(e.w0 - 1, 0); e.w1 = min(e.w1 + 1, a.nwires - 1); }
+}
+
+constexpr int kGradT = kSmallT + 2;   // widened patch a lane-per-depo gradient takes
+constexpr int kGradX = kSmallW + 2;
+
+__device__ __forceinline__ bool grad_is_small(const Extent& e) {
+    return e.k1 - e.k0 + 1 <= kGradT && e.w1 - e.w0 + 1 <= kGradX;
+}
+
+// Lane-serial axis_weights_grad for one depo: bin b's weight, mu and sigma
+// derivatives into w[b * ld], dmu[b * ld], dsig[b * ld].
+__device__ __forceinline__ void lane_axis_grad(float mu, float sigma, float delta, float nsig, bool point, int first,
+                                               int nb, float inv_norm, float* w, float* dmu, float* dsig, int ld) {
+    if (point) {
+        for (int b = 0; b < nb; ++b) { w[b * ld] = 1.f; dmu[b * ld] = 0.f; dsig[b * ld] = 0.f; }
+        return;
+    }
+    const float inv_s = 1.f / sigma;
+    float u_prev = 0.f, c_prev = 0.f, v_prev = 0.f;
+    for (int j = 0; j <= nb; ++j) {
+        const float e = (float)(first + j) * delta;
+        const float u = (e - mu) * inv_s;
+        const bool clamped = u <= -nsig || u >= nsig;
+        const float uc = fminf(fmaxf(u, -nsig), nsig);
+        const float c = clamped ? 0.f : 0.398942280401432678f * __expf(-0.5f * uc * uc) * inv_s;
+        const float v = erfcf(fabsf(uc) * 0.707106781186547524f);
+        if (j > 0) {
+            const int b = j - 1;
+            float m;
+            if (u_prev >= 0.f) m = 0.5f * (v_prev - v);
+            else if (uc <= 0.f) m = 0.5f * (v - v_prev);
+            else m = 1.f - 0.5f * (v_prev + v);
+            w[b * ld] = m * inv_norm;
+            dmu[b * ld] = -(c - c_prev) * inv_norm;
+            dsig[b * ld] = -(uc * c - u_prev * c_prev) * inv_norm;
+        }
+        u_prev = uc;
+        c_prev = c;
+        v_prev = v;
+    }
+}
+
+// dq, dx, dt of one depo from the five patch sums (as in depo_grad_kernel's
+// last step) and its D_L, D_T terms.
+__device__ __forceinline__ void finish_grad(const RasterArgs& a, const GradArgs& g, int64_t i, bool any, const Extent& e,
+                                            float q, float Sq, float Smt, float Sst, float Smx, float Ssx,
+                                            double& accL, double& accT) {
+    const float pq = a.p * q;
+    float dq = 0.f, dx = 0.f, dt = 0.f;
+    if (any) {
+        dq = a.p * Sq;
+        dx = pq * Smx;
+        dt = pq * Smt;
+        const float dst = pq * Sst, dsx = pq * Ssx;
+        if (!a.sig_t && e.mu_t > 0.f) {
+            dt += (dst * e.st + dsx * e.sx) / (2.f * e.mu_t);
+            if (g.DL > 0.0) accL += (double)dst * e.st / (2.0 * g.DL);
+            if (g.DT > 0.0) accT += (double)dsx * e.sx / (2.0 * g.DT);
+        }
+    }
+    if (g.gq) g.gq[i] = dq;
+    if (g.gx) g.gx[i] = dx;
+    if (g.gt) g.gt[i] = dt;
+}
+
+// Lane per depo: each lane builds its depo's widened weight and derivative
+// tables (shared memory, bin-major so the lanes' entries interleave) and walks
+// its own bins, gathering dL/dS.  Depos whose widened patch exceeds
+// kGradT x kGradX are left to depo_grad_kernel.
+constexpr int kGradWarps = 4;
+
+__global__ void __launch_bounds__(32 * kGradWarps)
+depo_grad_small_kernel(RasterArgs a, GradArgs g, long long* __restrict__ list, unsigned* list_count,
+                       unsigned list_cap) {
+    __shared__ float s_t[kGradWarps][3][kGradT][32];
+    __shared__ float s_x[kGradWarps][3][kGradX][32];
+    __shared__ double s_red[kGradWarps][2];
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    const float inv_norm = 1.f / erff(a.nsig * 0.707106781186547524f);
+    double accL = 0.0, accT = 0.0;
+    const int64_t nwarps = (int64_t)gridDim.x * kGradWarps;
+    for (int64_t base = ((int64_t)blockIdx.x * kGradWarps + wib) * 32; base < a.n; base += nwarps * 32) {
+        const int64_t i = base + lane;
+        Extent e;
+        float q = 0.f;
+        bool bad = false, any = false;
+        if (i < a.n) any = depo_extent<float>(a, i, &e, &q, &bad);
+        if (any) widen_for_grad(a, e);
+        const bool mine = i < a.n && (!any || grad_is_small(e));
+        if (i < a.n && !mine) {   // hand the depo to the warp-per-depo kernel
+            const unsigned slot = atomicAdd(list_count, 1u);
+            if (slot < list_cap) list[slot] = (long long)i;
+        }
+        float Sq = 0.f, Smt = 0.f, Sst = 0.f, Smx = 0.f, Ssx = 0.f;
+        if (any && mine) {
+            const int nt = e.k1 - e.k0 + 1, nx = e.w1 - e.w0 + 1;
+            float* tw = &s_t[wib][0][0][lane];
+            float* xw = &s_x[wib][0][0][lane];
+            lane_axis_grad(e.mu_t, e.st, a.tick, a.nsig, e.point_t, e.k0, nt, inv_norm, tw, tw + kGradT * 32,
+                           tw + 2 * kGradT * 32, 32);
+            lane_axis_grad(e.mu_x, e.sx, a.pitch, a.nsig, e.point_x, e.w0, nx, inv_norm, xw, xw + kGradX * 32,
+                           xw + 2 * kGradX * 32, 32);
+            for (int ia = 0; ia < nx; ++ia) {
+                const float wx = xw[ia * 32], mx = xw[(kGradX + ia) * 32], sx = xw[(2 * kGradX + ia) * 32];
+                const float* row = g.dS + (int64_t)(e.w0 + ia) * a.nticks + e.k0;
+                float r0 = 0.f, r1 = 0.f, r2 = 0.f;   // sums over the row of gv w_t, gv dmu_t, gv dsig_t
+                for (int ib = 0; ib < nt; ++ib) {
+                    const float gv = __ldg(row + ib);
+                    r0 = fmaf(gv, tw[ib * 32], r0);
+                    r1 = fmaf(gv, tw[(kGradT + ib) * 32], r1);
+                    r2 = fmaf(gv, tw[(2 * kGradT + ib) * 32], r2);
+                }
+                Sq = fmaf(wx, r0, Sq);
+                Smt = fmaf(wx, r1, Smt);
+                Sst = fmaf(wx, r2, Sst);
+                Smx = fmaf(mx, r0, Smx);
+                Ssx = fmaf(sx, r0, Ssx);
+            }
+        }
+        if (mine) finish_grad(a, g, i, any, e, q, Sq, Smt, Sst, Smx, Ssx, accL, accT);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        accL += __shfl_down_sync(0xffffffffu, accL, o);
+        accT += __shfl_down_sync(0xffffffffu, accT, o);
+    }
+    if (lane == 0) {
+        s_red[wib][0] = accL;
+        s_red[wib][1] = accT;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double L = 0.0, T = 0.0;
+        for (int w = 0; w < kGradWarps; ++w) { L += s_red[w][0]; T += s_red[w][1]; }
+        if (g.gDL && L != 0.0) atomicAdd(g.gDL, L);
+        if (g.gDT && T != 0.0) atomicAdd(g.gDT, T);
+    }
+}
+
+// Warp per depo for the depos whose widened patch the lane-per-depo kernel
+// leaves (chunks of kChunk bins per axis): the hand-over list's entries if
+// they fit in it, else every depo whose widened patch is large.  The last
+// block to finish resets the list counter for the next launch.
 __global__ void __launch_bounds__(32 * kWarpsPerBlock)
-depo_grad_kernel(RasterArgs a, GradArgs g) {
+depo_grad_kernel(RasterArgs a, GradArgs g, const long long* __restrict__ list, unsigned* list_count,
+                 unsigned list_cap, unsigned* done) {
     __shared__ float s_u[kWarpsPerBlock][kChunk + 1];
     __shared__ float s_c[kWarpsPerBlock][kChunk + 1];
     __shared__ float s_v[kWarpsPerBlock][kChunk + 1];
     __shared__ float s_wt[kWarpsPerBlock][3][kChunk];
     __shared__ float s_wx[kWarpsPerBlock][3][kChunk];
     __shared__ double s_red[kWarpsPerBlock][2];
+    const unsigned nlist = *(volatile unsigned*)list_count;
+    const bool use_list = nlist <= list_cap;
+    if (use_list && nlist == 0u) return;   // nothing handed over, counters already zero
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
     const int64_t nwarps = (int64_t)gridDim.x * kWarpsPerBlock;
     const float inv_norm = 1.f / erff(a.nsig * 0.707106781186547524f);
     double accL = 0.0, accT = 0.0;
-    for (int64_t i = (int64_t)blockIdx.x * kWarpsPerBlock + wib; i < a.n; i += nwarps) {
+    const int64_t nitems = use_list ? (int64_t)nlist : a.n;
+    for (int64_t it = (int64_t)blockIdx.x * kWarpsPerBlock + wib; it < nitems; it += nwarps) {
+        const int64_t i = use_list ? (int64_t)list[it] : it;
         Extent e;
         float q;
         bool bad;
         const bool any = depo_extent<float>(a, i, &e, &q, &bad);
-        if (any) {
-            // One more bin on each side of a non-point axis: the FP32 bin
-            // range can drop a sliver bin whose edge lies within rounding of
-            // the window bound; bins wholly outside get both edges clamped
-            // (zero weight, zero derivative), so the clamp test on u alone
-            // decides which side of the kink the depo is on.
-            if (!e.point_t) { e.k0 = max(e.k0 - 1, 0); e.k1 = min(e.k1 + 1, a.nticks - 1); }
-            if (!e.point_x) { e.w0 = max(e.w0 - 1, 0); e.w1 = min(e.w1 + 1, a.nwires - 1); }
-        }
+        if (!any) continue;   // written by the lane-per-depo kernel
+        widen_for_grad(a, e);
+        if (grad_is_small(e)) continue;
         float Sq = 0.f, Smt = 0.f, Sst = 0.f, Smx = 0.f, Ssx = 0.f;
         for (int kc = any ? e.k0 : 1; any && kc <= e.k1; kc += kChunk) {
             const int ntc = min(kChunk, e.k1 - kc + 1);
@@ -794,24 +945,7 @@ depo_grad_kernel(RasterArgs a, GradArgs g) {
             Smx += __shfl_down_sync(0xffffffffu, Smx, o);
             Ssx += __shfl_down_sync(0xffffffffu, Ssx, o);
         }
-        if (lane == 0) {
-            const float pq = a.p * q;
-            float dq = 0.f, dx = 0.f, dt = 0.f;
-            if (any) {
-                dq = a.p * Sq;
-                dx = pq * Smx;
-                dt = pq * Smt;
-                const float dst = pq * Sst, dsx = pq * Ssx;
-                if (!a.sig_t && e.mu_t > 0.f) {
-                    dt += (dst * e.st + dsx * e.sx) / (2.f * e.mu_t);
-                    if (g.DL > 0.0) accL += (double)dst * e.st / (2.0 * g.DL);
-                    if (g.DT > 0.0) accT += (double)dsx * e.sx / (2.0 * g.DT);
-                }
-            }
-            if (g.gq) g.gq[i] = dq;
-            if (g.gx) g.gx[i] = dx;
-            if (g.gt) g.gt[i] = dt;
-        }
+        if (lane == 0) finish_grad(a, g, i, any, e, q, Sq, Smt, Sst, Smx, Ssx, accL, accT);
     }
     if (lane == 0) {
         s_red[wib][0] = accL;
@@ -823,6 +957,12 @@ depo_grad_kernel(RasterArgs a, GradArgs g) {
         for (int w = 0; w < kWarpsPerBlock; ++w) { L += s_red[w][0]; T += s_red[w][1]; }
         if (g.gDL && L != 0.0) atomicAdd(g.gDL, L);
         if (g.gDT && T != 0.0) atomicAdd(g.gDT, T);
+        __threadfence();
+        if (atomicAdd(done, 1u) == gridDim.x - 1) {
+            *list_count = 0u;
+            *done = 0u;
+            __threadfence();
+        }
     }
 }
 
@@ -1058,10 +1198,12 @@ cudaError_t launch_zero_grids(const RasterBatch& rb, const int64_t* counts, cuda
 }
 
 cudaError_t launch_depo_grads(const RasterArgs& a, const float* dS, float* gq, float* gx, float* gt, double* gDL,
-                              double* gDT, double DL, double DT, cudaStream_t s) {
+                              double* gDT, double DL, double DT, const LargeList& L, cudaStream_t s) {
     if (a.n <= 0) return cudaSuccess;
     GradArgs g{dS, gq, gx, gt, gDL, gDT, DL, DT};
-    depo_grad_kernel<<<grid_for(a.n, kWarpsPerBlock, 8), 32 * kWarpsPerBlock, 0, s>>>(a, g);
+    depo_grad_small_kernel<<<grid_for((a.n + 31) / 32, kGradWarps, 8), 32 * kGradWarps, 0, s>>>(a, g, L.list,
+                                                                                                  L.count, L.cap);
+    depo_grad_kernel<<<num_sms() * 2, 32 * kWarpsPerBlock, 0, s>>>(a, g, L.list, L.count, L.cap, L.done);
     return cudaGetLastError();
 }
 

@@ -598,7 +598,7 @@ ws_status ws_simulate_backward(ws_plane* pl, const ws_depos* depos, const ws_par
     if (gDL) WS_CUDA(cudaMemsetAsync(gDL, 0, sizeof(double), s));
     if (gDT) WS_CUDA(cudaMemsetAsync(gDT, 0, sizeof(double), s));
     WS_LAUNCH(pl, K_DGRAD, s, ws::launch_depo_grads(a, pl->grid2, gq, gx, gt, gDL, gDT, params->DL_mm2_us,
-                                                    params->DT_mm2_us, s));
+                                                    params->DT_mm2_us, pl->large, s));
     if (gR) {
         // dL/dR: recompute S, transform it, correlate with the transform of G
         // (still in X) over wires, inverse transform, keep the response window.

@@ -184,7 +184,7 @@ cudaError_t launch_patch_sizes(const RasterArgs& a, int64_t* sizes, unsigned lon
 // Adjoint of the expected-value raster: per-depo dL/dq, dL/dx, dL/dt from
 // dS = dL/dS; dL/dD_L and dL/dD_T accumulated into gDL / gDT (FP64).
 cudaError_t launch_depo_grads(const RasterArgs& a, const float* dS, float* gq, float* gx, float* gt, double* gDL,
-                              double* gDT, double DL, double DT, cudaStream_t s);
+                              double* gDT, double DL, double DT, const LargeList& L, cudaStream_t s);
 cudaError_t launch_scan_inplace(int64_t* v, int64_t n, int64_t* scratch, cudaStream_t s);
 cudaError_t launch_raster_patches(const RasterArgs& a, const ws_patches& p, const LargeList& L, cudaStream_t s);
 cudaError_t launch_scatter_patches(const ws_patches& p, float* grid, int nwires, int nticks,

@@ -140,3 +140,37 @@ def test_backward_rejects_fluctuation(ws):
     d = ws.DeviceDepos([10.0], [12.0], [30.0])
     with pytest.raises(ws.WiresimError):
         plane.backward(d, ws.Params(fluctuate=True, p_survive=0.7), torch.zeros(8, 300, device="cuda"))
+
+
+def test_backward_wide_patches_take_the_warp_path(ws):
+    """Given widths: half the depos have patches wider than the
+    lane-per-depo gradient kernel takes (handed over to the warp-per-depo
+    kernel through the list), half narrow; every gradient against the
+    oracle's."""
+    import torch
+    nw, nt, n = 64, 2000, 400
+    d = inputs.uniform_depos(n, nw, 71, nticks=nt, t_min_us=1.0)
+    rng = np.random.Generator(np.random.PCG64(72))
+    wide = rng.uniform(size=n) < 0.5
+    st = np.where(wide, rng.uniform(6.0, 12.0, n), rng.uniform(0.3, 1.0, n)).astype(np.float32)
+    sx = np.where(wide, rng.uniform(15.0, 40.0, n), rng.uniform(0.5, 2.0, n)).astype(np.float32)
+    R = inputs.response("bipolar")
+    G = np.random.Generator(np.random.PCG64(73)).standard_normal((nw, nt))
+    ref = oracle.simulate_backward(d.q, d.x_mm, d.t_us, nw, nt, R, 10, G, sig_t_us=st, sig_x_mm=sx)
+    plane = ws.Plane(nw, nt, R)
+    got = plane.backward(ws.DeviceDepos(d.q, d.x_mm, d.t_us, st, sx), ws.Params(),
+                         torch.from_numpy(G.astype(np.float32)).cuda())
+    torch.cuda.synchronize()
+    got = [g.cpu().numpy() if hasattr(g, "cpu") else g for g in got]
+    m = np.zeros(n, bool)
+    for mu, sg, delta in ((d.t_us.astype(np.float64), st.astype(np.float64), oracle.TICK_US),
+                          (d.x_mm.astype(np.float64), sx.astype(np.float64), oracle.PITCH_MM)):
+        for sign in (-1.0, 1.0):
+            b = (mu + sign * 3.0 * sg) / delta
+            m |= np.abs(b - np.round(b)) * delta < 1e-5 * sg
+    for name, g, r in zip(("gq", "gx", "gt"), got[:3], ref[:3]):
+        assert np.isfinite(g).all(), name
+        for sel in (wide & ~m, ~wide & ~m):
+            assert rel(g[sel], r[sel]) <= TOL, (name, rel(g[sel], r[sel]))
+    assert rel(got[5], ref[5]) <= TOL
+    assert plane.status() == 0
