@@ -753,37 +753,44 @@ __device__ __forceinline__ bool grad_is_small(const Extent& e) {
     return e.k1 - e.k0 + 1 <= kGradT && e.w1 - e.w0 + 1 <= kGradX;
 }
 
-// Lane-serial axis_weights_grad for one depo: bin b's weight, mu and sigma
-// derivatives into w[b * ld], dmu[b * ld], dsig[b * ld].
-__device__ __forceinline__ void lane_axis_grad(float mu, float sigma, float delta, float nsig, bool point, int first,
-                                               int nb, float inv_norm, float* w, float* dmu, float* dsig, int ld) {
+// One axis of a depo's gradient tables, spread over the kGradLanes lanes of
+// its group: edge values (clamped u, phi(u)/sigma, erfc(|u|/sqrt 2)) into
+// ed[0..2][j], then bin b's weight and mu / sigma derivatives (as in
+// axis_weights_grad) into bn[0..2][b].
+constexpr int kGradLanes = 4;
+
+template <int NE>
+__device__ __forceinline__ void group_axis_grad(float mu, float sigma, float delta, float nsig, bool point, int first,
+                                                int nb, float inv_norm, float (*ed)[NE], float (*bn)[NE - 1], int sub) {
     if (point) {
-        for (int b = 0; b < nb; ++b) { w[b * ld] = 1.f; dmu[b * ld] = 0.f; dsig[b * ld] = 0.f; }
+        if (sub == 0) { bn[0][0] = 1.f; bn[1][0] = 0.f; bn[2][0] = 0.f; }
+        __syncwarp();
         return;
     }
     const float inv_s = 1.f / sigma;
-    float u_prev = 0.f, c_prev = 0.f, v_prev = 0.f;
-    for (int j = 0; j <= nb; ++j) {
+    for (int j = sub; j <= nb; j += kGradLanes) {
         const float e = (float)(first + j) * delta;
         const float u = (e - mu) * inv_s;
         const bool clamped = u <= -nsig || u >= nsig;
         const float uc = fminf(fmaxf(u, -nsig), nsig);
-        const float c = clamped ? 0.f : 0.398942280401432678f * __expf(-0.5f * uc * uc) * inv_s;
-        const float v = erfcf(fabsf(uc) * 0.707106781186547524f);
-        if (j > 0) {
-            const int b = j - 1;
-            float m;
-            if (u_prev >= 0.f) m = 0.5f * (v_prev - v);
-            else if (uc <= 0.f) m = 0.5f * (v - v_prev);
-            else m = 1.f - 0.5f * (v_prev + v);
-            w[b * ld] = m * inv_norm;
-            dmu[b * ld] = -(c - c_prev) * inv_norm;
-            dsig[b * ld] = -(uc * c - u_prev * c_prev) * inv_norm;
-        }
-        u_prev = uc;
-        c_prev = c;
-        v_prev = v;
+        ed[0][j] = uc;
+        ed[1][j] = clamped ? 0.f : 0.398942280401432678f * __expf(-0.5f * uc * uc) * inv_s;
+        ed[2][j] = erfcf(fabsf(uc) * 0.707106781186547524f);
     }
+    __syncwarp();
+    for (int b = sub; b < nb; b += kGradLanes) {
+        const float u0 = ed[0][b], u1 = ed[0][b + 1];
+        const float c0 = ed[1][b], c1 = ed[1][b + 1];
+        const float v0 = ed[2][b], v1 = ed[2][b + 1];
+        float m;
+        if (u0 >= 0.f) m = 0.5f * (v0 - v1);
+        else if (u1 <= 0.f) m = 0.5f * (v1 - v0);
+        else m = 1.f - 0.5f * (v0 + v1);
+        bn[0][b] = m * inv_norm;
+        bn[1][b] = -(c1 - c0) * inv_norm;
+        bn[2][b] = -(u1 * c1 - u0 * c0) * inv_norm;
+    }
+    __syncwarp();
 }
 
 // dq, dx, dt of one depo from the five patch sums (as in depo_grad_kernel's
@@ -809,62 +816,75 @@ __device__ __forceinline__ void finish_grad(const RasterArgs& a, const GradArgs&
     if (g.gt) g.gt[i] = dt;
 }
 
-// Lane per depo: each lane builds its depo's widened weight and derivative
-// tables (shared memory, bin-major so the lanes' entries interleave) and walks
-// its own bins, gathering dL/dS.  Depos whose widened patch exceeds
-// kGradT x kGradX are left to depo_grad_kernel.
+// kGradLanes lanes per depo (eight depos per warp): the group builds its
+// depo's widened edge, weight and derivative tables in shared memory and
+// splits the patch rows, gathering dL/dS; the partial sums meet by shuffles.
+// Depos whose widened patch exceeds kGradT x kGradX go to depo_grad_kernel
+// through the hand-over list.
 constexpr int kGradWarps = 4;
+constexpr int kGradSlots = 32 / kGradLanes;
 
 __global__ void __launch_bounds__(32 * kGradWarps)
 depo_grad_small_kernel(RasterArgs a, GradArgs g, long long* __restrict__ list, unsigned* list_count,
                        unsigned list_cap) {
-    __shared__ float s_t[kGradWarps][3][kGradT][32];
-    __shared__ float s_x[kGradWarps][3][kGradX][32];
+    __shared__ float s_te[kGradWarps][kGradSlots][3][kGradT + 1];
+    __shared__ float s_tb[kGradWarps][kGradSlots][3][kGradT];
+    __shared__ float s_xe[kGradWarps][kGradSlots][3][kGradX + 1];
+    __shared__ float s_xb[kGradWarps][kGradSlots][3][kGradX];
     __shared__ double s_red[kGradWarps][2];
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
+    const int slot = lane / kGradLanes, sub = lane % kGradLanes;
     const float inv_norm = 1.f / erff(a.nsig * 0.707106781186547524f);
     double accL = 0.0, accT = 0.0;
     const int64_t nwarps = (int64_t)gridDim.x * kGradWarps;
-    for (int64_t base = ((int64_t)blockIdx.x * kGradWarps + wib) * 32; base < a.n; base += nwarps * 32) {
-        const int64_t i = base + lane;
+    for (int64_t base = ((int64_t)blockIdx.x * kGradWarps + wib) * kGradSlots; base < a.n;
+         base += nwarps * kGradSlots) {
+        const int64_t i = base + slot;
         Extent e;
         float q = 0.f;
         bool bad = false, any = false;
         if (i < a.n) any = depo_extent<float>(a, i, &e, &q, &bad);
         if (any) widen_for_grad(a, e);
         const bool mine = i < a.n && (!any || grad_is_small(e));
-        if (i < a.n && !mine) {   // hand the depo to the warp-per-depo kernel
-            const unsigned slot = atomicAdd(list_count, 1u);
-            if (slot < list_cap) list[slot] = (long long)i;
+        if (sub == 0 && i < a.n && !mine) {   // hand the depo to the warp-per-depo kernel
+            const unsigned s = atomicAdd(list_count, 1u);
+            if (s < list_cap) list[s] = (long long)i;
         }
+        const bool work = any && mine;
+        const int nt = work ? e.k1 - e.k0 + 1 : 0, nx = work ? e.w1 - e.w0 + 1 : 0;
+        group_axis_grad<kGradT + 1>(work ? e.mu_t : 0.f, work ? e.st : 1.f, a.tick, a.nsig, work && e.point_t,
+                                    work ? e.k0 : 0, nt, inv_norm, s_te[wib][slot], s_tb[wib][slot], sub);
+        group_axis_grad<kGradX + 1>(work ? e.mu_x : 0.f, work ? e.sx : 1.f, a.pitch, a.nsig, work && e.point_x,
+                                    work ? e.w0 : 0, nx, inv_norm, s_xe[wib][slot], s_xb[wib][slot], sub);
         float Sq = 0.f, Smt = 0.f, Sst = 0.f, Smx = 0.f, Ssx = 0.f;
-        if (any && mine) {
-            const int nt = e.k1 - e.k0 + 1, nx = e.w1 - e.w0 + 1;
-            float* tw = &s_t[wib][0][0][lane];
-            float* xw = &s_x[wib][0][0][lane];
-            lane_axis_grad(e.mu_t, e.st, a.tick, a.nsig, e.point_t, e.k0, nt, inv_norm, tw, tw + kGradT * 32,
-                           tw + 2 * kGradT * 32, 32);
-            lane_axis_grad(e.mu_x, e.sx, a.pitch, a.nsig, e.point_x, e.w0, nx, inv_norm, xw, xw + kGradX * 32,
-                           xw + 2 * kGradX * 32, 32);
-            for (int ia = 0; ia < nx; ++ia) {
-                const float wx = xw[ia * 32], mx = xw[(kGradX + ia) * 32], sx = xw[(2 * kGradX + ia) * 32];
-                const float* row = g.dS + (int64_t)(e.w0 + ia) * a.nticks + e.k0;
-                float r0 = 0.f, r1 = 0.f, r2 = 0.f;   // sums over the row of gv w_t, gv dmu_t, gv dsig_t
-                for (int ib = 0; ib < nt; ++ib) {
-                    const float gv = __ldg(row + ib);
-                    r0 = fmaf(gv, tw[ib * 32], r0);
-                    r1 = fmaf(gv, tw[(kGradT + ib) * 32], r1);
-                    r2 = fmaf(gv, tw[(2 * kGradT + ib) * 32], r2);
-                }
-                Sq = fmaf(wx, r0, Sq);
-                Smt = fmaf(wx, r1, Smt);
-                Sst = fmaf(wx, r2, Sst);
-                Smx = fmaf(mx, r0, Smx);
-                Ssx = fmaf(sx, r0, Ssx);
+        const float (*tb)[kGradT] = s_tb[wib][slot];
+        const float (*xb)[kGradX] = s_xb[wib][slot];
+        for (int ia = sub; ia < nx; ia += kGradLanes) {
+            const float* row = g.dS + (int64_t)(e.w0 + ia) * a.nticks + e.k0;
+            float r0 = 0.f, r1 = 0.f, r2 = 0.f;   // sums over the row of gv w_t, gv dmu_t, gv dsig_t
+            for (int ib = 0; ib < nt; ++ib) {
+                const float gv = __ldg(row + ib);
+                r0 = fmaf(gv, tb[0][ib], r0);
+                r1 = fmaf(gv, tb[1][ib], r1);
+                r2 = fmaf(gv, tb[2][ib], r2);
             }
+            Sq = fmaf(xb[0][ia], r0, Sq);
+            Smt = fmaf(xb[0][ia], r1, Smt);
+            Sst = fmaf(xb[0][ia], r2, Sst);
+            Smx = fmaf(xb[1][ia], r0, Smx);
+            Ssx = fmaf(xb[2][ia], r0, Ssx);
         }
-        if (mine) finish_grad(a, g, i, any, e, q, Sq, Smt, Sst, Smx, Ssx, accL, accT);
+#pragma unroll
+        for (int o = 1; o < kGradLanes; o <<= 1) {
+            Sq += __shfl_xor_sync(0xffffffffu, Sq, o);
+            Smt += __shfl_xor_sync(0xffffffffu, Smt, o);
+            Sst += __shfl_xor_sync(0xffffffffu, Sst, o);
+            Smx += __shfl_xor_sync(0xffffffffu, Smx, o);
+            Ssx += __shfl_xor_sync(0xffffffffu, Ssx, o);
+        }
+        if (sub == 0 && mine) finish_grad(a, g, i, any, e, q, Sq, Smt, Sst, Smx, Ssx, accL, accT);
+        __syncwarp();
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -1201,8 +1221,8 @@ cudaError_t launch_depo_grads(const RasterArgs& a, const float* dS, float* gq, f
                               double* gDT, double DL, double DT, const LargeList& L, cudaStream_t s) {
     if (a.n <= 0) return cudaSuccess;
     GradArgs g{dS, gq, gx, gt, gDL, gDT, DL, DT};
-    depo_grad_small_kernel<<<grid_for((a.n + 31) / 32, kGradWarps, 8), 32 * kGradWarps, 0, s>>>(a, g, L.list,
-                                                                                                  L.count, L.cap);
+    depo_grad_small_kernel<<<grid_for((a.n + kGradSlots - 1) / kGradSlots, kGradWarps, 8), 32 * kGradWarps, 0, s>>>(
+        a, g, L.list, L.count, L.cap);
     depo_grad_kernel<<<num_sms() * 2, 32 * kWarpsPerBlock, 0, s>>>(a, g, L.list, L.count, L.cap, L.done);
     return cudaGetLastError();
 }
