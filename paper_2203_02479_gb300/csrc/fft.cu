@@ -441,6 +441,11 @@ struct Shape {
         for (int i = 0; i < p; ++i) n *= radix[i];
         return n;
     }
+    // one middle pass whose butterflies fit one per thread runs in place
+    // (inputs held in registers across a barrier): one shared buffer
+    static constexpr bool inplace = npass == 3 && L / radix[npass == 3 ? 1 : 0] <= NT;
+    static constexpr int buffers = inplace ? 1 : 2;
+    static constexpr int ctas = inplace ? 3 : 2;   // per SM
 };
 
 template <int R, bool INV, typename C>
@@ -514,6 +519,26 @@ __device__ __forceinline__ void fwd_last_pass(const C* __restrict__ tw, Ld ld, i
 // and writing buf[p&1].
 template <typename SH, bool INV, typename C>
 __device__ __forceinline__ void shape_middle(const FftPlan& plan, C* buf0, C* buf1, const C* __restrict__ tw) {
+    if constexpr (SH::inplace) {
+        constexpr int R = SH::radix[1], Ns = SH::ns(1), nb = SH::L / R;
+        const int j = threadIdx.x;
+        const int k = j % Ns;
+        C v[R];
+        if (j < nb) {
+#pragma unroll
+            for (int r = 0; r < R; ++r) v[r] = buf0[j + r * nb];
+            if (Ns > 1) twiddle_inputs<R, INV>(v, tw[plan.twoff[1] + k]);
+            Dft<R, INV, C>::run(v);
+        }
+        __syncthreads();   // every input read before any output lands
+        if (j < nb) {
+            const int d = (j - k) * R + k;
+#pragma unroll
+            for (int r = 0; r < R; ++r) buf0[d + r * Ns] = v[r];
+        }
+        __syncthreads();
+        return;
+    }
     sfor<SH::npass>([&](auto pc) {
         constexpr int p = decltype(pc)::value;
         if constexpr (p > 0 && p + 1 < SH::npass) {
@@ -528,7 +553,7 @@ __device__ __forceinline__ void shape_middle(const FftPlan& plan, C* buf0, C* bu
 }
 
 template <typename SH>
-__global__ void __launch_bounds__(SH::threads, 2)
+__global__ void __launch_bounds__(SH::threads, SH::ctas)
 fwd_rows_shape_kernel(FftPlan plan, const float2* __restrict__ tw, const __grid_constant__ RowUnits U, int ncols,
                       int64_t in_stride, int64_t out_stride, int nfreq, float scale) {
     using C = float2;
@@ -561,7 +586,7 @@ fwd_rows_shape_kernel(FftPlan plan, const float2* __restrict__ tw, const __grid_
     }, [&](int i, C v) { buf0[i] = v; });
     __syncthreads();
     shape_middle<SH, false>(plan, buf0, buf1, tw);
-    const C* z = (last - 1) & 1 ? buf1 : buf0;
+    const C* z = (!SH::inplace && ((last - 1) & 1)) ? buf1 : buf0;
     C* oa = static_cast<C*>(U.out[u]) + (int64_t)r0 * out_stride;
     C* ob = oa + out_stride;
     const float h = 0.5f * scale;
@@ -573,7 +598,7 @@ fwd_rows_shape_kernel(FftPlan plan, const float2* __restrict__ tw, const __grid_
 }
 
 template <typename SH>
-__global__ void __launch_bounds__(SH::threads, 2)
+__global__ void __launch_bounds__(SH::threads, SH::ctas)
 inv_rows_shape_kernel(FftPlan plan, const float2* __restrict__ tw, const __grid_constant__ RowUnits U,
                       int64_t in_stride, int nfreq, int ncols, int64_t out_stride) {
     using C = float2;
@@ -598,7 +623,7 @@ inv_rows_shape_kernel(FftPlan plan, const float2* __restrict__ tw, const __grid_
     }, [&](int i, C v) { buf0[i] = v; });
     __syncthreads();
     shape_middle<SH, true>(plan, buf0, buf1, tw);
-    const C* z = (last - 1) & 1 ? buf1 : buf0;
+    const C* z = (!SH::inplace && ((last - 1) & 1)) ? buf1 : buf0;
     float* oa = static_cast<float*>(U.out[u]) + (int64_t)r0 * out_stride;
     float* ob = oa + out_stride;
     const int nst = ncols < L ? ncols : L;
@@ -856,15 +881,16 @@ struct ShapeKernels {
     int npass;
     int radix[4];
     FwdShapeFn fwd;
-    int fwd_threads;
+    int fwd_threads, fwd_buffers;
     InvShapeFn inv;
-    int inv_threads;
+    int inv_threads, inv_buffers;
 };
 constexpr int kFwdShapeThreads = 320;
 constexpr int kInvShapeThreads = 320;
 #define WS_SHAPE3(A, B, C)                                                                                  \
     {3, {A, B, C}, fwd_rows_shape_kernel<Shape<kFwdShapeThreads, A, B, C>>, kFwdShapeThreads,                \
-     inv_rows_shape_kernel<Shape<kInvShapeThreads, A, B, C>>, kInvShapeThreads}
+     Shape<kFwdShapeThreads, A, B, C>::buffers, inv_rows_shape_kernel<Shape<kInvShapeThreads, A, B, C>>,     \
+     kInvShapeThreads, Shape<kInvShapeThreads, A, B, C>::buffers}
 static const ShapeKernels kShapes[] = {
     WS_SHAPE3(25, 25, 10),  // 6250: linear convolution of 6000 ticks with a 200-tick response
     WS_SHAPE3(25, 16, 15),  // 6000: circular convolution of 6000 ticks
@@ -891,7 +917,7 @@ static cudaError_t fwd_rows_t(const FftPlan& plan, const cplx<S>* tw, const RowB
     if (rb.n <= 0) return cudaSuccess;
     if constexpr (std::is_same<S, float>::value && std::is_same<TIN, float>::value) {
         if (const ShapeKernels* k = shape_kernels(plan)) {
-            const int smem = 2 * ((plan.L + 1) & ~1) * (int)sizeof(float2);
+            const int smem = k->fwd_buffers * ((plan.L + 1) & ~1) * (int)sizeof(float2);
             cudaError_t e = set_smem((const void*)k->fwd, smem);
             if (e != cudaSuccess) return e;
             bool al = false;
@@ -920,7 +946,7 @@ static cudaError_t inv_rows_t(const FftPlan& plan, const cplx<S>* tw, const RowB
     if (rb.n <= 0) return cudaSuccess;
     if constexpr (std::is_same<S, float>::value) {
         if (const ShapeKernels* k = shape_kernels(plan)) {
-            const int smem = 2 * ((plan.L + 1) & ~1) * (int)sizeof(float2);
+            const int smem = k->inv_buffers * ((plan.L + 1) & ~1) * (int)sizeof(float2);
             cudaError_t e = set_smem((const void*)k->inv, smem);
             if (e != cudaSuccess) return e;
             bool al = false;
