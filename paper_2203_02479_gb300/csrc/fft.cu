@@ -886,7 +886,7 @@ struct ShapeKernels {
     int inv_threads, inv_buffers;
 };
 constexpr int kFwdShapeThreads = 320;
-constexpr int kInvShapeThreads = 320;
+constexpr int kInvShapeThreads = 256;
 #define WS_SHAPE3(A, B, C)                                                                                  \
     {3, {A, B, C}, fwd_rows_shape_kernel<Shape<kFwdShapeThreads, A, B, C>>, kFwdShapeThreads,                \
      Shape<kFwdShapeThreads, A, B, C>::buffers, inv_rows_shape_kernel<Shape<kInvShapeThreads, A, B, C>>,     \
