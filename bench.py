@@ -666,8 +666,8 @@ def run_gpu(args):
                    "fft_len_tick": planes[0].info.fft_len_tick,
                    "units_per_wave": upw_event,
                    "wire_conv_variant": [pl.info.wire_conv_variant for pl in planes],
-                   "path": "ws_simulate_batch over the event's planes (one launch per stage), "
-                           "replayed from a CUDA graph",
+                   "path": "ws_simulate_batch over the event's planes in waves of units_per_wave (consecutive "
+                           "waves on two streams), replayed from a CUDA graph",
                    "l2": "flushed between timed steps (512 MiB write)"},
         "planes_per_s": all_planes / (total_ms * 1e-3),
         "raster_scatter_depos_per_s": all_depos / (raster_ms * 1e-3) if raster_ms > 0 else None,
