@@ -358,51 +358,6 @@ def adjoint_leg(wiresim, dev, stream, flush, steps: int):
             "backward_outputs": "dL/dq, dL/dx, dL/dt per depo; dL/dD_L, dL/dD_T; dL/dR (21 x 200)"}
 
 
-def precision_study(args):
-    """Large three-plane detector (2560/2560/3840 x 6000, 2M track depos):
-    every GPU precision path against the FP64 oracle, per plane, with the
-    binomial fluctuation of the workload and in expected-value mode (which
-    isolates arithmetic error from the rare one-electron differences of the
-    FP32 normal-approximation branch)."""
-    import torch
-    import oracle
-    from paper_2203_02479_gb300 import wiresim
-    wiresim.load_library()
-    dev = torch.device("cuda", 0)
-    w = inputs.large_planes(n=args.precision_depos)
-    modes = (("fp32", wiresim.WS_PREC_FP32), ("fp32_comp", wiresim.WS_PREC_FP32_COMP),
-             ("fp64", wiresim.WS_PREC_FP64))
-    result = {"study": "precision", "workload": w.name, "depos": w.events[0][0].n, "planes": []}
-    for sp, d in zip(w.planes, w.events[0]):
-        plane = wiresim.Plane(sp.nwires, sp.nticks, sp.response, plane_id=sp.plane_id, fp64=True, device=dev)
-        dd = wiresim.DeviceDepos.from_plane_depos(d, device=dev)
-        entry = {"nwires": sp.nwires}
-        for fluct in (True, False):
-            S = oracle.raster_scatter(d.q, d.x_mm, d.t_us, sp.nwires, sp.nticks, fluctuate=fluct, p=w.p_survive,
-                                      seed=w.seed, plane_id=sp.plane_id)
-            ref = oracle.convolve_fft(S, sp.response, 10)
-            nref = float(np.linalg.norm(ref))
-            for name, prec in modes:
-                params = wiresim.Params(fluctuate=fluct, p_survive=w.p_survive, seed=w.seed, precision=prec)
-                out = plane.simulate(dd, params)
-                torch.cuda.synchronize()
-                t0 = torch.cuda.Event(enable_timing=True)
-                t1 = torch.cuda.Event(enable_timing=True)
-                t0.record()
-                for _ in range(3):
-                    plane.simulate(dd, params, out=out)
-                t1.record()
-                torch.cuda.synchronize()
-                got = out.cpu().numpy().astype(np.float64)
-                key = f"{name}_{'binomial' if fluct else 'expected'}"
-                entry[key] = {"rel_l2": float(np.linalg.norm(got - ref) / nref),
-                              "max_abs": float(np.abs(got - ref).max()), "max_ref": float(np.abs(ref).max()),
-                              "ms": t0.elapsed_time(t1) / 3}
-        result["planes"].append(entry)
-        plane.close()
-    print(json.dumps(result), flush=True)
-
-
 def run_gpu(args):
     import torch
     from paper_2203_02479_gb300 import wiresim
@@ -700,9 +655,6 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched-workload", action="store_true")
-    ap.add_argument("--precision-study", action="store_true",
-                    help="print the per-plane precision comparison of the large three-plane workload instead")
-    ap.add_argument("--precision-depos", type=int, default=2_000_000)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--wire-conv-variant", type=int, default=-1,
                     help="force the planes' wire-convolution kernel (default: each plane's autotuned choice)")
@@ -715,8 +667,6 @@ def main():
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
     if args.impl == "reference":
         run_reference(args)
-    elif args.precision_study:
-        precision_study(args)
     else:
         run_gpu(args)
 

@@ -80,3 +80,47 @@ def test_fp64_needs_fp64_workspace(ws):
     with pytest.raises(ws.WiresimError) as ei:
         plane.simulate(d, ws.Params(precision=ws.WS_PREC_FP64))
     assert ei.value.status == 6
+
+
+def test_precision_study_large_planes(ws):
+    """Large three-plane detector (2560 / 2560 / 3840 wires x 6000 ticks, 2M
+    track depos): every precision path against the FP64 oracle, per plane,
+    in binomial mode (the workload) and expected-value mode (which isolates
+    arithmetic error from the rare one-electron differences of the FP32
+    normal branch).  Prints the table; bounds: FP32 and FP32_COMP 1e-5,
+    FP64 1e-7.  Also counts the depos whose width falls under the narrow
+    threshold (sigma < bin / 8 on an axis) that FP32_COMP takes in FP64."""
+    import torch
+    w = inputs.large_planes(n=2_000_000)
+    modes = (("fp32", ws.WS_PREC_FP32, 1e-5), ("fp32_comp", ws.WS_PREC_FP32_COMP, 1e-5),
+             ("fp64", ws.WS_PREC_FP64, 1e-7))
+    t = w.events[0][0].t_us.astype(np.float64)
+    st = np.sqrt(2 * oracle.DL * t) / oracle.V
+    sx = np.sqrt(2 * oracle.DT * t)
+    narrow = (st < oracle.TICK_US / 8) | (sx < oracle.PITCH_MM / 8)
+    print(f"\nnarrow depos (FP64 edges under FP32_COMP): {narrow.mean():.4%}")
+    for sp, d in zip(w.planes, w.events[0]):
+        plane = ws.Plane(sp.nwires, sp.nticks, sp.response, plane_id=sp.plane_id, fp64=True)
+        dd = ws.DeviceDepos.from_plane_depos(d)
+        for fluct in (True, False):
+            S = oracle.raster_scatter(d.q, d.x_mm, d.t_us, sp.nwires, sp.nticks, fluctuate=fluct, p=w.p_survive,
+                                      seed=w.seed, plane_id=sp.plane_id)
+            ref = oracle.convolve_fft(S, sp.response, 10)
+            for name, prec, bound in modes:
+                params = ws.Params(fluctuate=fluct, p_survive=w.p_survive, seed=w.seed, precision=prec)
+                out = plane.simulate(dd, params)
+                torch.cuda.synchronize()
+                t0 = torch.cuda.Event(enable_timing=True)
+                t1 = torch.cuda.Event(enable_timing=True)
+                t0.record()
+                for _ in range(3):
+                    plane.simulate(dd, params, out=out)
+                t1.record()
+                torch.cuda.synchronize()
+                got = out.cpu().numpy().astype(np.float64)
+                r = rel(got, ref)
+                print(f"plane {sp.plane_id} ({sp.nwires} wires) {name:9s} {'binomial' if fluct else 'expected'}: "
+                      f"rel L2 {r:.2e}, max abs {np.abs(got - ref).max():.2f} of {np.abs(ref).max():.3g}, "
+                      f"{t0.elapsed_time(t1) / 3:.2f} ms")
+                assert r <= bound, (sp.plane_id, name, fluct, r)
+        plane.close()
