@@ -295,8 +295,9 @@ ws_status ws_plane_sync(ws_plane* plane, void* stream, uint32_t* bits);
 /* Clear the plane's device status word (stream-ordered). */
 ws_status ws_plane_clear_status(ws_plane* plane, void* stream);
 
-/* Override the autotuned wire-convolution kernel (0..3, see
- * ws_plane_info.wire_conv_variant); all variants compute the same sum. */
+/* Override the autotuned wire-convolution kernel (0..7, see
+ * ws_plane_info.wire_conv_variant; 4..7 need linear mode); all variants
+ * compute the same sum. */
 ws_status ws_plane_set_wire_conv_variant(ws_plane* plane, int variant);
 
 /* Launch tracing (timing of each kernel with CUDA events).  With
@@ -315,6 +316,16 @@ typedef struct {
  * clears the records.  SYNCHRONISES on the last recorded event.  Writes at
  * most max_stats entries and their count to *nstats. */
 ws_status ws_plane_trace_read(ws_plane* plane, ws_trace_stat* stats, int max_stats, int* nstats);
+
+/* Failure-detection check of the bounded waits (no counterpart in the
+ * paper).  Launches one CTA on `stream` that waits on an mbarrier expecting
+ * an arrival nobody makes, the wait the TMA kernels use for their copies
+ * (they give up after 2^18 attempts, about a second): after `iters`
+ * attempts (1 .. 2^20) it gives up, ORs WS_DEV_TIMEOUT into
+ * *status_dev (device uint32_t, caller-owned) and returns; if cycles_dev is
+ * not NULL the SM cycles spent waiting go to *cycles_dev (device uint64_t).
+ * The context stays usable.  Stream-ordered, no host synchronisation. */
+ws_status ws_selftest_bounded_wait(uint32_t* status_dev, int iters, unsigned long long* cycles_dev, void* stream);
 
 const char* ws_status_string(ws_status status);
 

@@ -24,7 +24,7 @@ namespace ws {
 namespace {
 
 constexpr int kCols = 128;                 // complex columns per tile (one thread each)
-constexpr int kWaitIters = 1 << 20;        // try_wait attempts before giving up
+constexpr int kWaitIters = 1 << 18;        // try_wait attempts before giving up (~1 s: an attempt suspends ~4 us)
 
 struct TmaConvUnits {
     CUtensorMap map[kMaxUnits];            // X of each unit: {2 * stride floats, nwires rows}
@@ -43,19 +43,21 @@ __device__ __forceinline__ void mbar_init(uint64_t* bar) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(bar)) : "memory");
 }
 
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
-    const uint32_t b = smem_addr(bar);
-    for (int it = 0; it < kWaitIters; ++it) {
-        uint32_t done;
-        asm volatile(
-            "{\n\t.reg .pred p;\n\t"
-            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-            "selp.u32 %0, 1, 0, p;\n\t}"
-            : "=r"(done)
-            : "r"(b), "r"(parity)
-            : "memory");
-        if (done) return true;
-    }
+__device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return done != 0u;
+}
+
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int iters = kWaitIters) {
+    for (int it = 0; it < iters; ++it)
+        if (mbar_try(bar, parity)) return true;
     return false;
 }
 
@@ -254,9 +256,33 @@ cudaError_t launch_tma(const ConvBatch& cb, int nfreq, int64_t stride, int kw, i
     return cudaGetLastError();
 }
 
+// The bounded-wait path on its own: one CTA waits on an mbarrier that
+// expects an arrival nobody makes; after `iters` attempts it gives up,
+// records WS_DEV_TIMEOUT and returns (cycles spent into *cycles).
+__global__ void bounded_wait_selftest_kernel(uint32_t* status, int iters, unsigned long long* cycles) {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    const long long t0 = clock64();
+    const bool ok = mbar_wait(&bar, 0u, iters);
+    const long long t1 = clock64();
+    if (threadIdx.x == 0) {
+        if (!ok) atomicOr(status, WS_DEV_TIMEOUT);
+        if (cycles) *cycles = (unsigned long long)(t1 - t0);
+    }
+}
+
 }  // namespace
 
 bool tma_available() { return encode_fn() != nullptr; }
+
+cudaError_t launch_bounded_wait_selftest(uint32_t* status, int iters, unsigned long long* cycles, cudaStream_t s) {
+    bounded_wait_selftest_kernel<<<1, 32, 0, s>>>(status, iters, cycles);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_wire_conv_tma(const ConvBatch& cb, int nfreq, int64_t stride, int kw, int center, int variant,
                                  uint32_t* status, cudaStream_t s) {

@@ -806,6 +806,12 @@ ws_status batch_waves(ws_plane* const* planes, int nplanes, const ws_depos* depo
 
 extern "C" {
 
+ws_status ws_selftest_bounded_wait(uint32_t* status_dev, int iters, unsigned long long* cycles_dev, void* stream) {
+    if (!status_dev || iters < 1 || iters > (1 << 20) || !aligned(status_dev, 4)) return WS_ERR_INVALID_ARG;
+    WS_CUDA(ws::launch_bounded_wait_selftest(status_dev, iters, cycles_dev, (cudaStream_t)stream));
+    return WS_OK;
+}
+
 ws_status ws_plane_sync(ws_plane* pl, void* stream, uint32_t* bits) {
     if (!pl || !bits) return WS_ERR_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)stream;

@@ -138,6 +138,7 @@ cudaError_t launch_wire_conv(const float2* X, float2* Y, const float2* Rt, int n
                              cudaStream_t s, int variant = 0, uint32_t* status = nullptr);
 // TMA-fed wire convolution (wconv_tma.cu), variant 0..3 as above.
 bool tma_available();
+cudaError_t launch_bounded_wait_selftest(uint32_t* status, int iters, unsigned long long* cycles, cudaStream_t s);
 cudaError_t launch_wire_conv_tma(const ConvBatch& cb, int nfreq, int64_t stride, int kw, int center, int variant,
                                  uint32_t* status, cudaStream_t s);
 

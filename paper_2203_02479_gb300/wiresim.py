@@ -32,8 +32,8 @@ EXPORTED = ("ws_plane_workspace_bytes", "ws_plane_create", "ws_plane_destroy", "
             "ws_patch_capacity", "ws_rasterize", "ws_scatter", "ws_convolve", "ws_simulate",
             "ws_plane_sync", "ws_plane_clear_status", "ws_plane_trace", "ws_plane_trace_read",
             "ws_convolve_noalloc", "ws_plane_set_wire_conv_variant", "ws_plane_set_response",
-            "ws_simulate_backward", "ws_batch_workspace_bytes", "ws_simulate_batch", "ws_status_string",
-            "ws_last_error")
+            "ws_simulate_backward", "ws_batch_workspace_bytes", "ws_simulate_batch", "ws_selftest_bounded_wait",
+            "ws_status_string", "ws_last_error")
 
 
 class WiresimError(RuntimeError):
@@ -113,6 +113,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
             "ws_convolve": [P, P, P, P],
             "ws_simulate": [P, ctypes.POINTER(WsDepos), ctypes.POINTER(WsParams), P, P],
             "ws_plane_sync": [P, P, ctypes.POINTER(ctypes.c_uint32)],
+            "ws_selftest_bounded_wait": [P, ctypes.c_int, P, P],
             "ws_plane_clear_status": [P, P],
             "ws_plane_trace": [P, ctypes.c_int],
             "ws_plane_trace_read": [P, ctypes.POINTER(WsTraceStat), ctypes.c_int,
@@ -196,6 +197,13 @@ def ws_convolve(plane: int, grid_dev: int, out_dev: int, stream: int):
 def ws_simulate(plane: int, depos: WsDepos, params: WsParams, out_dev: int, stream: int):
     _check(load_library().ws_simulate(plane, ctypes.byref(depos), ctypes.byref(params), out_dev, stream),
            "ws_simulate")
+
+
+def ws_selftest_bounded_wait(status_dev: int, iters: int, cycles_dev: int, stream: int):
+    """Bounded-wait check (see include/wiresim.h): a wait nobody satisfies
+    gives up after `iters` attempts and sets WS_DEV_TIMEOUT in *status_dev."""
+    _check(load_library().ws_selftest_bounded_wait(status_dev, iters, cycles_dev, stream),
+           "ws_selftest_bounded_wait")
 
 
 def ws_plane_sync(plane: int, stream: int) -> int:
