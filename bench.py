@@ -212,26 +212,38 @@ def run_reference(args):
     if rank != 0:
         return
     w = make_workload(args.workload, 0)
+    # a step is one plane of the event through the oracle (~0.5 s on one
+    # thread); warm-up and timed steps stop early once the time budget is
+    # spent so that any --steps ends within a few minutes
+    t_start = time.perf_counter()
     for _ in range(args.warmup):
         oracle_sample(w, 0.0)
+        if time.perf_counter() - t_start > 0.2 * args.reference_seconds:
+            break
     t0 = time.perf_counter()
     done = 0
     planes = 0
+    steps = 0
     for _ in range(args.steps):
         d, _, p = oracle_sample(w, 0.0)   # one plane per step
         done += d
         planes += p
+        steps += 1
+        if time.perf_counter() - t0 > args.reference_seconds:
+            break
     dt = time.perf_counter() - t0
     value = done / dt
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+        "steps": steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
         "config": {"workload": w.name, "sample": "one plane of the event per step (cycling U, V, W)",
-                   "depos_per_plane": w.events[0][0].n},
+                   "depos_per_plane": w.events[0][0].n, "steps_requested": args.steps,
+                   "time_budget_s": args.reference_seconds},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": f"{args.steps} steps x one plane of {w.events[0][0].n} depos"},
+                         "sample": f"{steps} steps (of {args.steps} requested, {args.reference_seconds:.0f} s "
+                                   f"budget) x one plane of {w.events[0][0].n} depos"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
         "planes_per_s": planes / dt,
     }
@@ -656,6 +668,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched-workload", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--reference-seconds", type=float, default=150.0,
+                    help="time budget of the --impl reference timed steps")
     ap.add_argument("--wire-conv-variant", type=int, default=-1,
                     help="force the planes' wire-convolution kernel (default: each plane's autotuned choice)")
     ap.add_argument("--units-per-wave", type=int, default=0,
