@@ -408,3 +408,23 @@ def test_simulate_of_one_point_charge_is_the_response():
     ref = np.zeros((16, 30))
     ref[7 - 2:7 + 3, 0:9] = 2.0 * R
     np.testing.assert_allclose(M, ref, atol=1e-12)
+
+
+def test_oracle_matches_its_golden_fixtures():
+    """Regression guard (not a pin): the oracle's Philox blocks and
+    exact-branch counts equal the fixtures tests/golden/make_golden.py
+    wrote from it."""
+    import os
+    gdir = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+    for line in open(os.path.join(gdir, "philox_blocks.txt")):
+        if line.startswith("#"):
+            continue
+        v = [int(x, 16) for x in line.split()]
+        assert list(oracle.philox(v[:4], v[4:6])) == v[6:10]
+    lines = [l for l in open(os.path.join(gdir, "binomial_inversion.txt")) if not l.startswith("#")]
+    words = np.array([int(x, 16) for x in lines[0].split()[1:]], dtype=np.uint32)
+    for line in lines[1:]:
+        head, counts = line.split(":")
+        N, p = head.split()
+        got = oracle.binomial_invert(int(N), float(p), words)
+        assert list(got) == [int(c) for c in counts.split()], (N, p)
