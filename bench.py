@@ -465,7 +465,7 @@ def run_gpu(args):
 
     # per-kernel algorithmic work (sum over the event's planes per launch)
     kern = {name: [n, ms] for name, (n, ms) in stats.items()}
-    # each traced raster_scatter entry is two kernels (lane-pair + large-patch)
+    # each traced raster_scatter entry is two kernels (lane per depo + large-patch)
     launches = int(round(per_step_launches * args.steps))
     per_launch_bytes, per_launch_flops = {}, {}
     for name in kern:

@@ -192,7 +192,9 @@ ws_status ws_patch_capacity(ws_plane* plane, const ws_depos* depos, const ws_par
                             void* stream, int64_t* bins_out);
 
 /* Diffusion + raster (+ fluctuation) of every depo into its own patch
- * (Sec. 2.2 "Raster", Sec. 3.1).  One warp per depo.  Each bin holds
+ * (Sec. 2.2 "Raster", Sec. 3.1).  A lane per depo for its geometry and
+ * edge tables, its patch's bins spread over the warp (a warp per depo for
+ * patches above 16 ticks x 8 wires).  Each bin holds
  * q * p * w_t * w_x (expected value) or a binomial survivor count, with
  * w the Gaussian mass of the bin clipped to mu +- nsigma*sigma over the
  * window's total mass.  Writes out->off (exclusive scan of patch sizes),

@@ -369,7 +369,7 @@ __device__ __forceinline__ W window_norm(const RasterArgs& a) {
     else return 1.f / erff(a.nsig * 0.707106781186547524f);
 }
 
-// Warp per depo for the large patches the lane-pair kernel handed over:
+// Warp per depo for the large patches the lane-per-depo kernel handed over:
 // the list's (unit, depo) entries if they fit in it, else every depo of
 // every unit whose patch is large.  The last block to finish resets the
 // list counter for the next launch.
