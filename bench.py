@@ -311,7 +311,7 @@ def batched_workload_comparison(wiresim, dev, stream, flush, steps: int):
     params = wiresim.Params(fluctuate=w.fluctuate, p_survive=w.p_survive, seed=w.seed)
     ndp = sum(d.n for ev in w.events for d in ev)
     best = None
-    for upw in (3, 6, 12, 24):
+    for upw in (3, 6, 12, 16, 24, 32):
         b = wiresim.Batch(planes, events, params, units_per_wave=upw, device=dev)
         b.run(stream)
         torch.cuda.synchronize()
