@@ -260,7 +260,7 @@ PHILOX_MULS = 40    # 32-bit multiplies per Philox4x32-10 block: 10 rounds x 2 p
 # three planes (the configuration of the per-kernel table), as of the current
 # kernels.
 NCU_TRAFFIC = {"three_planes_800_800_960x6000": {
-    "raster_scatter": 8.38e6, "fwd_rows": 76.0e6, "wire_conv": 92.8e6, "inv_rows": 77.1e6, "memset_grid": 3.35e6}}
+    "raster_scatter": 8.39e6, "fwd_rows": 75.9e6, "wire_conv": 92.7e6, "inv_rows": 76.9e6, "memset_grid": 3.84e6}}
 
 
 def drawing_bins(wiresim, planes, depos) -> int:
