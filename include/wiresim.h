@@ -152,9 +152,11 @@ typedef struct {
     int32_t radices[16];
     size_t workspace_bytes;
     int32_t wire_conv_variant;  /* autotuned wire-convolution kernel: wire
-                                   block 16 (0, 1, 4, 5) or 8 (2, 3, 6, 7),
-                                   Karatsuba three-product taps (odd), tiles
-                                   by TMA (4..7, linear mode only)          */
+                                   block 16 (0, 1, 4, 5, 8, 9) or 8 (2, 3,
+                                   6, 7), Karatsuba three-product taps
+                                   (odd), tiles by TMA (4..7) or TMA chunks
+                                   into a ring kept along a run of wire
+                                   blocks (8, 9); 4..9 linear mode only     */
     int32_t row_fft_fixed_shape; /* 1: this L_t's FP32 tick-axis transforms
                                    run kernels compiled for its radix plan
                                    (first and last passes on global memory);
@@ -297,8 +299,8 @@ ws_status ws_plane_sync(ws_plane* plane, void* stream, uint32_t* bits);
 /* Clear the plane's device status word (stream-ordered). */
 ws_status ws_plane_clear_status(ws_plane* plane, void* stream);
 
-/* Override the autotuned wire-convolution kernel (0..7, see
- * ws_plane_info.wire_conv_variant; 4..7 need linear mode); all variants
+/* Override the autotuned wire-convolution kernel (0..9, see
+ * ws_plane_info.wire_conv_variant; 4..9 need linear mode); all variants
  * compute the same sum. */
 ws_status ws_plane_set_wire_conv_variant(ws_plane* plane, int variant);
 

@@ -201,6 +201,162 @@ wire_conv_tma_kernel(const __grid_constant__ TmaConvUnits U, int nfreq, int64_t 
     }
 }
 
+// Ring-fed variant: a CTA walks a run of consecutive wire blocks of one
+// column block, and the input rows arrive once per run in chunks of
+// kRingRows rows (one TMA copy each) into a ring of kRingSlots chunk
+// buffers, instead of one (B + K - 1)-row tile per output block: the
+// window of tile i of a run (rows ybase + 16 i .. + 35) is chunks i, i + 1
+// and the head of i + 2, so each further tile fetches only its 16 new rows.
+// Chunk i + 3 (for tile i + 1) is issued into chunk i's slot as soon as the
+// window's first 16 rows have been read, half-way through tile i.  48 KB of
+// shared memory per CTA lets four CTAs (16 warps) share an SM.
+constexpr int kRingRows = 16;
+constexpr int kRingSlots = 3;
+
+template <int K, bool KARATSUBA>
+__global__ void __launch_bounds__(kCols, 4)
+wire_conv_ring_kernel(const __grid_constant__ TmaConvUnits U, int nfreq, int64_t stride, int kw, int center,
+                      uint32_t* status) {
+    constexpr int B = kRingRows;
+    constexpr int ROWS = B + K - 1;
+    static_assert(ROWS > 2 * kRingRows && ROWS <= kRingSlots * kRingRows, "window spans three chunks");
+    constexpr uint32_t CHUNK_BYTES = kRingRows * kCols * sizeof(float2);
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ __align__(8) uint64_t bar[kRingSlots];
+    auto slot_buf = [&](int sl) { return reinterpret_cast<const float2*>(smem + sl * CHUNK_BYTES); };
+    const int total = U.prefix[U.n];
+    auto tile_of = [&](int t, int& u, int& k0, int& wb, int& nwb) {
+        int lo = 0, hi = U.n - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (U.prefix[mid] <= t) lo = mid; else hi = mid - 1;
+        }
+        u = lo;
+        const int tt = t - U.prefix[u];
+        nwb = (U.nwires[u] + B - 1) / B;
+        k0 = (tt / nwb) * kCols;
+        wb = tt % nwb;
+    };
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < kRingSlots; ++i) mbar_init(&bar[i]);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    uint32_t phase = 0u, pending = 0u;   // per slot: parity of its next completion; copy in flight
+    // Give up on a copy: flag it, drain the others (bounded) and report.
+    auto fail = [&]() {
+        if (threadIdx.x == 0) atomicOr(status, WS_DEV_TIMEOUT);
+        for (int sl = 0; sl < kRingSlots; ++sl)
+            if (pending & (1u << sl)) mbar_wait(&bar[sl], (phase >> sl) & 1u);
+    };
+    auto wait_slot = [&](int sl) -> bool {
+        if (!(pending & (1u << sl))) return true;
+        const bool ok = mbar_wait(&bar[sl], (phase >> sl) & 1u);
+        if (__syncthreads_or(!ok)) return false;
+        phase ^= 1u << sl;
+        pending &= ~(1u << sl);
+        return true;
+    };
+    const int t_end = (int)((int64_t)total * (blockIdx.x + 1) / gridDim.x);
+    int t = (int)((int64_t)total * blockIdx.x / gridDim.x);
+    float cc[K], cm[K], cp[K];   // taps of the run's column block (Karatsuba form)
+    float2 c[K];                 // the same, plain form
+    while (t < t_end) {
+        int u, k0, wb, nwb;
+        tile_of(t, u, k0, wb, nwb);
+        const int n = min(t_end - t, nwb - wb);   // tiles in this run
+        const int ybase = wb * B + center - (K - 1);
+        const CUtensorMap* map = &U.map[u];
+        auto issue = [&](int j) {   // chunk j of the run into slot j % 3 (thread 0 copies, all track)
+            const int sl = j % kRingSlots;
+            if (threadIdx.x == 0) tma_load_tile(smem + sl * CHUNK_BYTES, map, 2 * k0, ybase + kRingRows * j, &bar[sl],
+                                                CHUNK_BYTES);
+            pending |= 1u << sl;
+        };
+        for (int j = 0; j < kRingSlots; ++j) issue(j);
+        const int k = k0 + threadIdx.x;
+        const int nwires = U.nwires[u];
+        float2* __restrict__ Y = static_cast<float2*>(U.Y[u]);
+        const float2* __restrict__ Rt = static_cast<const float2*>(U.Rt[u]);
+#pragma unroll
+        for (int r = 0; r < K; ++r) {
+            const float2 v = (r < kw && k < nfreq) ? __ldg(&Rt[(int64_t)r * stride + k]) : make_float2(0.f, 0.f);
+            if constexpr (KARATSUBA) {
+                cc[r] = v.x;
+                cm[r] = v.y - v.x;
+                cp[r] = v.x + v.y;
+            } else {
+                c[r] = v;
+            }
+        }
+        for (int i = 0; i < n; ++i) {
+            const int s0 = i % kRingSlots, s1 = (i + 1) % kRingSlots, s2 = (i + 2) % kRingSlots;
+            if (!wait_slot(s0) || !wait_slot(s1) || !wait_slot(s2)) {
+                fail();
+                return;
+            }
+            const float2* col0 = slot_buf(s0) + threadIdx.x;
+            const float2* col1 = slot_buf(s1) + threadIdx.x;
+            const float2* col2 = slot_buf(s2) + threadIdx.x;
+            const int w0 = (wb + i) * B;
+            float k1[B], k2[B], k3[B];
+            float2 acc[B];
+#pragma unroll
+            for (int b = 0; b < B; ++b) {
+                k1[b] = k2[b] = k3[b] = 0.f;
+                acc[b] = make_float2(0.f, 0.f);
+            }
+            // window row uu: input row ybase + 16 i + uu, read by outputs b = uu - (K - 1) + r
+            auto row = [&](const float2 x, const int uu) {
+                if constexpr (KARATSUBA) {
+                    const float sab = x.x + x.y;
+#pragma unroll
+                    for (int b = 0; b < B; ++b) {
+                        const int r = b + K - 1 - uu;
+                        if (r >= 0 && r < K) {
+                            k1[b] = fmaf(cc[r], sab, k1[b]);
+                            k2[b] = fmaf(cm[r], x.x, k2[b]);
+                            k3[b] = fmaf(cp[r], x.y, k3[b]);
+                        }
+                    }
+                } else {
+#pragma unroll
+                    for (int b = 0; b < B; ++b) {
+                        const int r = b + K - 1 - uu;
+                        if (r >= 0 && r < K) {
+                            acc[b].x = fmaf(c[r].x, x.x, fmaf(-c[r].y, x.y, acc[b].x));
+                            acc[b].y = fmaf(c[r].x, x.y, fmaf(c[r].y, x.x, acc[b].y));
+                        }
+                    }
+                }
+            };
+            const bool live = k < nfreq;
+            if (live) {
+#pragma unroll
+                for (int uu = 0; uu < kRingRows; ++uu) row(col0[uu * kCols], uu);
+            }
+            __syncthreads();   // chunk i read by every thread: its slot takes chunk i + 3
+            if (i + 1 < n) issue(i + 3);
+            if (live) {
+#pragma unroll
+                for (int uu = kRingRows; uu < ROWS; ++uu)
+                    row(uu < 2 * kRingRows ? col1[(uu - kRingRows) * kCols] : col2[(uu - 2 * kRingRows) * kCols], uu);
+#pragma unroll
+                for (int b = 0; b < B; ++b) {
+                    if (w0 + b < nwires) {
+                        if constexpr (KARATSUBA)
+                            Y[(int64_t)(w0 + b) * stride + k] = make_float2(k1[b] - k3[b], k1[b] + k2[b]);
+                        else
+                            Y[(int64_t)(w0 + b) * stride + k] = acc[b];
+                    }
+                }
+            }
+        }
+        __syncthreads();   // the run's last chunks read before the next run reuses the slots
+        t += n;
+    }
+}
+
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
     static std::once_flag once;
     static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
@@ -256,6 +412,46 @@ cudaError_t launch_tma(const ConvBatch& cb, int nfreq, int64_t stride, int kw, i
     return cudaGetLastError();
 }
 
+template <bool KS>
+cudaError_t launch_ring(const ConvBatch& cb, int nfreq, int64_t stride, int kw, int center, uint32_t* status,
+                        cudaStream_t s) {
+    constexpr int K = kMaxRespWires;
+    const PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
+    if (!enc) return cudaErrorNotSupported;
+    TmaConvUnits U;
+    const int nkblocks = (nfreq + kCols - 1) / kCols;
+    U.n = cb.n;
+    U.prefix[0] = 0;
+    for (int i = 0; i < cb.n; ++i) {
+        const cuuint64_t dims[2] = {(cuuint64_t)(2 * stride), (cuuint64_t)cb.nwires[i]};
+        const cuuint64_t strides[1] = {(cuuint64_t)(2 * stride * sizeof(float))};
+        const cuuint32_t box[2] = {2 * kCols, kRingRows};
+        const cuuint32_t estr[2] = {1, 1};
+        const CUresult r = enc(&U.map[i], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void*>(cb.X[i]), dims,
+                               strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+        U.nwires[i] = cb.nwires[i];
+        U.Y[i] = cb.Y[i];
+        U.Rt[i] = cb.Rt[i];
+        U.prefix[i + 1] = U.prefix[i] + nkblocks * ((cb.nwires[i] + kRingRows - 1) / kRingRows);
+    }
+    const int total = U.prefix[cb.n];
+    if (total <= 0) return cudaSuccess;
+    const int smem = kRingSlots * kRingRows * kCols * (int)sizeof(float2);
+    cudaError_t e = cudaFuncSetAttribute((const void*)wire_conv_ring_kernel<K, KS>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, wire_conv_ring_kernel<K, KS>, kCols, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) per_sm = 1;
+    int grid = num_sms() * per_sm;
+    if (grid > total) grid = total;
+    wire_conv_ring_kernel<K, KS><<<grid, kCols, smem, s>>>(U, nfreq, stride, kw, center, status);
+    return cudaGetLastError();
+}
+
 // The bounded-wait path on its own: one CTA waits on an mbarrier that
 // expects an arrival nobody makes; after `iters` attempts it gives up,
 // records WS_DEV_TIMEOUT and returns (cycles spent into *cycles).
@@ -291,6 +487,8 @@ cudaError_t launch_wire_conv_tma(const ConvBatch& cb, int nfreq, int64_t stride,
         case 1: return launch_tma<16, true>(cb, nfreq, stride, kw, center, status, s);
         case 2: return launch_tma<8, false>(cb, nfreq, stride, kw, center, status, s);
         case 3: return launch_tma<8, true>(cb, nfreq, stride, kw, center, status, s);
+        case 4: return launch_ring<false>(cb, nfreq, stride, kw, center, status, s);
+        case 5: return launch_ring<true>(cb, nfreq, stride, kw, center, status, s);
         default: return launch_tma<16, false>(cb, nfreq, stride, kw, center, status, s);
     }
 }

@@ -130,13 +130,15 @@ cudaError_t launch_fwd_rows_comp(const FftPlan& plan, const float2* tw, const fl
                                  int ncols, int64_t in_stride, float2* out, int64_t out_stride, int nfreq,
                                  cudaStream_t s);
 // variant: 0 = 16 wires per thread, 1 = 16 Karatsuba, 2 = 8, 3 = 8 Karatsuba,
-// with plain loads; 4..7 the same four fed by TMA tile copies (linear mode
-// only; they report a copy that never lands in *status).
-constexpr int kWireConvVariants = 8;
+// with plain loads; 4..7 the same four fed by TMA tile copies; 8, 9 = 16
+// wires (plain, Karatsuba) fed by TMA chunk copies into a ring that a CTA
+// keeps along a run of wire blocks (4..9: linear mode only; they report a
+// copy that never lands in *status).
+constexpr int kWireConvVariants = 10;
 cudaError_t launch_wire_conv(const float2* X, float2* Y, const float2* Rt, int nwires,
                              int nfreq, int64_t stride, int kw, int center, int circular,
                              cudaStream_t s, int variant = 0, uint32_t* status = nullptr);
-// TMA-fed wire convolution (wconv_tma.cu), variant 0..3 as above.
+// TMA-fed wire convolution (wconv_tma.cu), variant 0..5 = 4..9 above.
 bool tma_available();
 cudaError_t launch_bounded_wait_selftest(uint32_t* status, int iters, unsigned long long* cycles, cudaStream_t s);
 cudaError_t launch_wire_conv_tma(const ConvBatch& cb, int nfreq, int64_t stride, int kw, int center, int variant,

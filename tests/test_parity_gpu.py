@@ -69,12 +69,13 @@ def test_convolve_matches_oracle(ws, circular, nw, nt, kw, kt, c):
     assert rel_l2(to_np(out), ref) <= REL_L2
 
 
-@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4, 5, 6, 7])
+@pytest.mark.parametrize("variant", list(range(10)))
 @pytest.mark.parametrize("circular", [False, True])
 def test_every_wire_conv_variant(ws, variant, circular):
     """Each wire-convolution kernel (wire blocks of 16 or 8, plain or
-    Karatsuba taps, plain loads or TMA tiles) gives the oracle's
-    convolution, with a ragged wire tail; TMA tiles are linear mode only."""
+    Karatsuba taps, plain loads, TMA tiles or a TMA-fed chunk ring) gives
+    the oracle's convolution, with a ragged wire tail; the TMA kernels are
+    linear mode only."""
     import torch
     if circular and variant >= 4:
         pytest.skip("TMA tiles zero-fill outside the grid: linear mode only")
