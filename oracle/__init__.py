@@ -93,6 +93,9 @@ def _lib():
                 ctypes.c_double, ctypes.c_double, _f64p, _f64p, _f64p, _f64p,
                 ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
             h.wso_depo_grads.restype = ctypes.c_int64
+            h.wso_noise_spectrum.argtypes = [ctypes.c_int, ctypes.c_int, _f64p, ctypes.c_void_p, ctypes.c_int,
+                                             _u32p, ctypes.c_uint32, _f64p, _f64p]
+            h.wso_noise_spectrum.restype = None
             _handle = h
     return _handle
 
@@ -281,10 +284,67 @@ def convolve_points(S, R, wire_center: int, pw, pt, circular: bool = False) -> n
 
 
 def simulate(q, x_mm, t_us, nwires: int, nticks: int, R, wire_center: int = 10, *,
-             circular: bool = False, **kw) -> np.ndarray:
-    """The whole hot path: raster, (fluctuate), scatter-add, convolve (Eq. 2)."""
+             circular: bool = False, noise_amp=None, noise_coh=None, noise_group: int = 1,
+             fft_len_tick: int = 0, **kw) -> np.ndarray:
+    """The whole hot path: raster, (fluctuate), scatter-add, convolve (Eq. 2),
+    plus the noise term of Eq. 1 when noise_amp is given (on the transform
+    length fft_len_tick, by default ``fft_len`` of the plane)."""
     S = raster_scatter(q, x_mm, t_us, nwires, nticks, **kw)
-    return convolve_fft(S, R, wire_center, circular)
+    M = convolve_fft(S, R, wire_center, circular)
+    if noise_amp is not None:
+        kt = np.asarray(R).shape[1]
+        L = fft_len_tick or fft_len(nticks if circular else nticks + kt - 1)
+        nk = {k: kw[k] for k in ("seed", "event_id", "plane_id") if k in kw}
+        M = M + noise(nwires, nticks, L, noise_amp, noise_coh, noise_group, **nk)
+    return M
+
+
+def fft_len(n: int) -> int:
+    """Smallest 2^a 3^b 5^c >= n: the tick axis's default transform length
+    (n = nticks + K_t - 1 in linear mode, nticks in circular mode)."""
+    m = max(int(n), 1)
+    while True:
+        r = m
+        for f in (2, 3, 5):
+            while r % f == 0:
+                r //= f
+        if r == 1:
+            return m
+        m += 1
+
+
+# -------------------------------------------------------------------- noise
+def noise_spectrum(nwires: int, L: int, amp, coh=None, group: int = 1, *, seed: int = 0,
+                   event_id: int = 0, plane_id: int = 0) -> np.ndarray:
+    """Nhat_w[k], k = 0 .. L/2, of the noise term N(t, x) of Eq. 1 (reading
+    in ``wsoracle.c``): incoherent amplitudes amp[k] per wire plus coherent
+    amplitudes coh[k] shared by groups of ``group`` consecutive wires, with
+    complex normals from Philox words by Box-Muller.
+
+    Pinned by the normality and independence of its draws and, through
+    ``noise``, by the closed-form variance and covariances."""
+    nfreq = L // 2 + 1
+    a = _c64(amp)
+    if a.shape != (nfreq,):
+        raise ValueError("amp needs L/2 + 1 entries")
+    c = None if coh is None else _c64(coh)
+    if c is not None and (c.shape != (nfreq,) or group < 1):
+        raise ValueError("coh needs L/2 + 1 entries and group >= 1")
+    re = np.zeros((nwires, nfreq)); im = np.zeros((nwires, nfreq))
+    evpl = ((event_id << 4) | (plane_id & 15)) & 0xFFFFFFFF
+    _lib().wso_noise_spectrum(int(nwires), int(L), a, _opt_ptr(c), int(group), seed_key(seed), evpl, re, im)
+    return re + 1j * im
+
+
+def noise(nwires: int, nticks: int, L: int, amp, coh=None, group: int = 1, **kw) -> np.ndarray:
+    """n_w[t] for t < nticks: the inverse real DFT (1/L normalisation, numpy)
+    of ``noise_spectrum`` over the Hermitian extension.
+
+    Pinned by the closed forms of its per-sample variance (1/L^2) sum_k A^2,
+    its autocovariance and the within- and across-group covariances, and by
+    a direct DFT sum on small lengths."""
+    spec = noise_spectrum(nwires, L, amp, coh, group, **kw)
+    return np.ascontiguousarray(np.fft.irfft(spec, n=L, axis=1)[:, :nticks])
 
 
 # ------------------------------------------------------------------ adjoint

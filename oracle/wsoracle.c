@@ -453,3 +453,70 @@ int64_t wso_depo_grads(int64_t n, const double* q, const double* x_mm, const dou
     free(wt); free(mt); free(st_); free(wx); free(mx); free(sx_);
     return skipped;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Noise term N(t, x) of Eq. 1 (Sec. 2.1).  The paper names the term and
+ * leaves it out of the ported signal path; its model is not given.  Reading
+ * taken here: per wire, a stationary Gaussian process given by amplitude
+ * spectra on the tick axis's transform length L, an incoherent part
+ * independent per wire and a coherent part shared by the wires of a group of
+ * G consecutive wires:
+ *   Nhat_w[k] = A[k] xi_w[k] + Ac[k] xi'_{floor(w / G)}[k],  k = 0 .. L/2,
+ * with xi = (z1 + i z2) / sqrt 2 for 0 < k < L/2 and xi = z1 at k = 0 and
+ * k = L/2 (L even), and the noise waveform n_w[t] = (1/L) sum over the
+ * Hermitian extension of Nhat_w[k] e^{2 pi i k t / L} (the Python layer does
+ * that sum with numpy's inverse real FFT).
+ * The normals: z1 = sqrt(-2 ln u1) cos(2 pi u2), z2 = sqrt(-2 ln u1)
+ * sin(2 pi u2) (Box and Muller, 1958), u = (m + 1/2) / 2^23 with m the top 23
+ * bits of a Philox word.  Incoherent wire w, bin k: Philox block with counter
+ * (1, k, floor(w / 2), event << 4 | plane), words 2 (w mod 2) and
+ * 2 (w mod 2) + 1; coherent group g: counter (2, k, floor(g / 2), same),
+ * words 2 (g mod 2), 2 (g mod 2) + 1.  (The fluctuation's counters start
+ * with 0, so the streams are disjoint.)
+ * re, im: nwires x nfreq outputs (nfreq = L/2 + 1).  coh may be NULL. */
+static void wso_normal_pair(uint32_t a, uint32_t b, double* z1, double* z2)
+{
+    const double u1 = ((double)(a >> 9) + 0.5) / 8388608.0;
+    const double u2 = ((double)(b >> 9) + 0.5) / 8388608.0;
+    const double rad = sqrt(-2.0 * log(u1));
+    *z1 = rad * cos(2.0 * M_PI * u2);
+    *z2 = rad * sin(2.0 * M_PI * u2);
+}
+
+static void wso_xi(int k, int L, uint32_t domain, int64_t idx, const uint32_t key[2], uint32_t evpl,
+                   double* re, double* im)
+{
+    const uint32_t ctr[4] = {domain, (uint32_t)k, (uint32_t)(idx / 2), evpl};
+    uint32_t x[4];
+    wso_philox4x32_10(ctr, key, x);
+    const int h = (int)(idx % 2);
+    double z1, z2;
+    wso_normal_pair(x[2 * h], x[2 * h + 1], &z1, &z2);
+    if (k == 0 || 2 * k == L) {
+        *re = z1;
+        *im = 0.0;
+    } else {
+        *re = z1 / sqrt(2.0);
+        *im = z2 / sqrt(2.0);
+    }
+}
+
+void wso_noise_spectrum(int nwires, int L, const double* amp, const double* coh, int group,
+                        const uint32_t key[2], uint32_t evpl, double* re, double* im)
+{
+    const int nfreq = L / 2 + 1;
+    for (int w = 0; w < nwires; ++w) {
+        for (int k = 0; k < nfreq; ++k) {
+            double xr, xi;
+            wso_xi(k, L, 1u, w, key, evpl, &xr, &xi);
+            double sr = amp[k] * xr, si = amp[k] * xi;
+            if (coh) {
+                wso_xi(k, L, 2u, w / group, key, evpl, &xr, &xi);
+                sr += coh[k] * xr;
+                si += coh[k] * xi;
+            }
+            re[(int64_t)w * nfreq + k] = sr;
+            im[(int64_t)w * nfreq + k] = si;
+        }
+    }
+}
