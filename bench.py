@@ -344,6 +344,33 @@ def batched_workload_comparison(wiresim, dev, stream, flush, steps: int):
             "batched_ms": g, "per_plane_ms": pp}
 
 
+def noise_leg(wiresim, dev, stream, flush, steps: int, units_per_wave: int, plain_ms: float):
+    """The benchmark event with the noise term of Eq. 1 switched on (an
+    incoherent spectrum per wire plus a coherent one per group of 32 wires,
+    synthetic shapes), replayed from a CUDA graph like the timed step."""
+    import torch
+    w = make_workload("three_planes", 0)
+    planes = [wiresim.Plane(sp.nwires, sp.nticks, sp.response, plane_id=sp.plane_id, device=dev) for sp in w.planes]
+    L = planes[0].info.fft_len_tick
+    for pl in planes:
+        pl.set_noise(inputs.noise_amplitudes(L), inputs.noise_amplitudes(L, "coherent"), 32)
+    depos = [wiresim.DeviceDepos.from_plane_depos(d, device=dev) for d in w.events[0]]
+    params = wiresim.Params(fluctuate=w.fluctuate, p_survive=w.p_survive, seed=w.seed)
+    b = wiresim.Batch(planes, [depos], params, units_per_wave=units_per_wave, device=dev)
+    b.capture()
+    for _ in range(3):
+        b.replay()
+    torch.cuda.synchronize(dev)
+    ms = sorted(_time_steps(b.replay, steps, stream, flush))[steps // 2]
+    ndp = sum(d.n for d in w.events[0])
+    for pl in planes:
+        pl.close()
+    return {"workload": w.name + " + noise (incoherent, coherent groups of 32)", "ms_per_step": ms,
+            "value": ndp / (ms * 1e-3), "unit": UNIT, "over_plain": ms / plain_ms,
+            "where": "noise drawn per (wire, bin) and added to the half spectra between the wire convolution "
+                     "and the inverse transform (one more launch per wave)"}
+
+
 def adjoint_leg(wiresim, dev, stream, flush, steps: int):
     """Forward and adjoint (ws_simulate_backward: gradients for q, x, t of
     every depo, D_L, D_T and the response) of one 960 x 6000 plane with
@@ -607,9 +634,12 @@ def run_gpu(args):
     all_planes = _sum_over_ranks(dist, float(len(planes) * args.steps), dev)
     batched = None
     adjoint = None
+    noise = None
     if rank == 0 and world == 1 and not args.no_batched_workload:
         batched = batched_workload_comparison(wiresim, dev, stream, flush, max(3, min(args.steps, 10)))
         adjoint = adjoint_leg(wiresim, dev, stream, flush, max(5, min(args.steps, 50)))
+        noise = noise_leg(wiresim, dev, stream, flush, max(5, min(args.steps, 200)), upw_event,
+                          sorted(graph_ms)[len(graph_ms) // 2])
     if rank != 0:
         if dist is not None:
             dist.destroy_process_group()
@@ -651,6 +681,7 @@ def run_gpu(args):
         "cpu_baseline": cpu,
         "batched_workload": batched,
         "adjoint": adjoint,
+        "noise": noise,
     }
     print(json.dumps(line), flush=True)
     if dist is not None:

@@ -220,7 +220,8 @@ ws_status ws_convolve(ws_plane* plane, const float* grid_dev, float* out_dev, vo
 
 /* The whole hot path for one plane and one event: clear out_dev, raster +
  * fluctuate + scatter-add every depo straight into it (no patch buffer),
- * then convolve in place.  out_dev: nwires x nticks float32. */
+ * then convolve in place, adding the plane's noise term if one is set
+ * (ws_plane_set_noise).  out_dev: nwires x nticks float32. */
 ws_status ws_simulate(ws_plane* plane, const ws_depos* depos, const ws_params* params,
                       float* out_dev, void* stream);
 
@@ -262,6 +263,7 @@ ws_status ws_batch_workspace_bytes(ws_plane* const* planes, int nplanes, int uni
  * nwires(p) x nticks output (cleared, then simulated); event e uses
  * event_id = params->event_id + e.  All planes must share the transform
  * length, tick count and response shape (else WS_ERR_UNSUPPORTED_SIZE).
+ * Each plane's noise term (ws_plane_set_noise) is added as in ws_simulate.
  * Results equal ws_simulate unit by unit (up to summation order).  With more
  * than one wave, odd waves run on a second stream owned by the library (one
  * per host thread and device) that forks from `stream` at the start of the
@@ -271,6 +273,30 @@ ws_status ws_batch_workspace_bytes(ws_plane* const* planes, int nplanes, int uni
 ws_status ws_simulate_batch(ws_plane* const* planes, int nplanes, const ws_depos* depos, int nevents,
                             const ws_params* params, float* const* out_dev, void* workspace_dev,
                             size_t workspace_bytes, int units_per_wave, void* stream);
+
+/* Noise term N(t, x) of Eq. 1 (Sec. 2.1 names it; the paper's port leaves
+ * it out, and its model is this library's reading): from now on
+ * ws_simulate and ws_simulate_batch add to each wire w of this plane the
+ * stationary Gaussian noise with half spectrum, on the plane's tick
+ * transform length L (ws_plane_info.fft_len_tick),
+ *   Nhat_w[k] = amp[k] xi_w[k] + coh_amp[k] xi'_{floor(w / coh_group)}[k],
+ *   k = 0 .. L/2,   n_w[t] = (1/L) sum_{k<L} Nhat_w[k] e^{2 pi i k t / L}
+ * over the Hermitian extension, for t < nticks.  xi and xi' are complex
+ * normals (z1 + i z2)/sqrt 2 (z1 alone at k = 0 and k = L/2) from
+ * Box-Muller, u = (top 23 bits of a Philox word + 1/2) / 2^23, keyed by
+ * the call's seed with counter (1, k, floor(w/2), event << 4 | plane) for
+ * the incoherent part (words 2(w%2), 2(w%2)+1) and (2, k, floor(g/2), ...)
+ * for group g's coherent part; the fluctuation's counters start with 0, so
+ * the streams never overlap.  amp_dev, coh_amp_dev: L/2 + 1 float32 device
+ * amplitudes, copied (stream-ordered) into the plane's workspace;
+ * coh_amp_dev may be NULL (no coherent part; coh_group is then ignored,
+ * else it must be >= 1).  Both NULL switch the noise off.  The noise is
+ * added to the half spectra (in place, one more launch) between the wire
+ * convolution and the inverse transform, where the 1/L is already folded
+ * in.  ws_convolve (the pure convolution) and the adjoint are unaffected
+ * (the noise does not depend on the inputs). */
+ws_status ws_plane_set_noise(ws_plane* plane, const float* amp_dev, const float* coh_amp_dev,
+                             int32_t coh_group, void* stream);
 
 /* Replace the plane's response (K_w x K_t float32 device array, same shape
  * as at creation) and recompute its spectrum on `stream`. */

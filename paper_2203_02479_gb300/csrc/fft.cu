@@ -228,6 +228,126 @@ __device__ __forceinline__ int find_unit(const int* prefix, int n, int b) {
     return lo;
 }
 
+// ------------------------------------------------------------------ noise
+// Standard normals z1, z2 from two Philox words by Box-Muller: u = (m + 1/2)
+// 2^-23 with m the word's top 23 bits (exact in float and double), z1 =
+// sqrt(-2 ln u1) cos(2 pi u2), z2 = sqrt(-2 ln u1) sin(2 pi u2).  In single
+// precision the hardware logarithm, sine, cosine and reciprocal square root
+// (absolute errors ~2^-21 on these ranges: ~1e-6 of a typical normal) keep
+// the noise well inside the FP32 path's 1e-5; cos(2 pi u) = -cos(2 pi (u -
+// 1/2)) puts the argument in [-pi, pi].
+__device__ __forceinline__ void normal_pair(uint32_t a, uint32_t b, float& z1, float& z2) {
+    const float u1 = ((float)(a >> 9) + 0.5f) * 1.1920928955078125e-7f;
+    const float u2 = ((float)(b >> 9) + 0.5f) * 1.1920928955078125e-7f;
+    const float t = -2.0f * __logf(u1);   // > 0: u1 < 1
+    const float rad = t * rsqrtf(t);
+    const float ang = 6.28318530717958648f * (u2 - 0.5f);
+    z1 = -rad * __cosf(ang);
+    z2 = -rad * __sinf(ang);
+}
+__device__ __forceinline__ void normal_pair(uint32_t a, uint32_t b, double& z1, double& z2) {
+    const double u1 = ((double)(a >> 9) + 0.5) * 1.1920928955078125e-7;
+    const double u2 = ((double)(b >> 9) + 0.5) * 1.1920928955078125e-7;
+    const double rad = sqrt(-2.0 * log(u1));
+    double sn, cs;
+    sincospi(2.0 * u2, &sn, &cs);
+    z1 = rad * cs;
+    z2 = rad * sn;
+}
+
+// xi from words 2h, 2h + 1 of block x: (z1 + i z2) / sqrt 2, or z1 on the
+// real bins (k = 0, k = L/2).
+template <typename C>
+__device__ __forceinline__ C noise_xi(const uint4& x, int h, bool edge) {
+    using S = decltype(C{}.x);
+    S z1, z2;
+    normal_pair(h ? x.z : x.x, h ? x.w : x.y, z1, z2);
+    if (edge) return mkc(z1, (S)0);
+    const S r = (S)0.70710678118654752440;
+    return mkc(z1 * r, z2 * r);
+}
+
+// Noise term of Eq. 1 added to the spectra Y (between the wire convolution
+// and the inverse transform; Y carries the 1/L of the unnormalised
+// inverse): thread = one bin k of one unit and a block of kNoiseRows wires,
+// taken in pairs (one Philox block serves a pair's incoherent draws); the
+// coherent draw of a group is made once per run of the group's wires in the
+// block and reused.
+constexpr int kNoiseRows = 8;
+constexpr int kNoiseCols = 128;
+
+template <typename C>
+__global__ void __launch_bounds__(kNoiseCols)
+add_noise_kernel(const __grid_constant__ NoiseUnits U, int nfreq, int L, int64_t stride) {
+    using S = decltype(C{}.x);
+    const int u = find_unit(U.prefix, U.n, (int)blockIdx.y);
+    const int k = blockIdx.x * kNoiseCols + threadIdx.x;
+    if (k >= nfreq) return;
+    const NoiseUnit& nz = U.noise[u];
+    C* __restrict__ Y = static_cast<C*>(U.Y[u]);
+    const int w0 = ((int)blockIdx.y - U.prefix[u]) * kNoiseRows;   // even
+    const int nr = min(kNoiseRows, U.nwires[u] - w0);
+    // the block's spectra first (independent loads in flight), then the draws
+    C yv[kNoiseRows];
+#pragma unroll
+    for (int i = 0; i < kNoiseRows; ++i)
+        if (i < nr) yv[i] = Y[(int64_t)(w0 + i) * stride + k];
+    const bool edge = k == 0 || 2 * k == L;
+    const S a = (S)__ldg(nz.amp + k) * (S)nz.scale;
+    const S c = nz.coh ? (S)__ldg(nz.coh + k) * (S)nz.scale : (S)0;
+    int cur_g = -1;
+    C xg = mkc((S)0, (S)0);
+#pragma unroll
+    for (int i = 0; i < kNoiseRows; i += 2) {   // wires w0 + i, w0 + i + 1 share a block
+        if (i >= nr) break;
+        const uint4 x =
+            philox4x32_10(make_uint4(1u, (uint32_t)k, (uint32_t)((w0 + i) >> 1), nz.evpl), U.key0, U.key1);
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            if (i + h >= nr) break;
+            const C v = noise_xi<C>(x, h, edge);
+            S ax = a * v.x, ay = a * v.y;
+            if (nz.coh) {
+                const int g = (w0 + i + h) / nz.group;
+                if (g != cur_g) {
+                    const uint4 y = philox4x32_10(make_uint4(2u, (uint32_t)k, (uint32_t)(g >> 1), nz.evpl), U.key0,
+                                                  U.key1);
+                    xg = noise_xi<C>(y, g & 1, edge);
+                    cur_g = g;
+                }
+                ax += c * xg.x;
+                ay += c * xg.y;
+            }
+            yv[i + h].x += ax;
+            yv[i + h].y += ay;
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < kNoiseRows; ++i)
+        if (i < nr) Y[(int64_t)(w0 + i) * stride + k] = yv[i];
+}
+
+template <typename C>
+static cudaError_t add_noise_t(const NoiseBatch& nb, int nfreq, int L, int64_t stride, cudaStream_t s) {
+    NoiseUnits U;
+    U.n = 0;
+    U.prefix[0] = 0;
+    U.key0 = nb.key0;
+    U.key1 = nb.key1;
+    for (int i = 0; i < nb.n; ++i) {
+        if (!nb.noise[i].amp) continue;
+        const int j = U.n++;
+        U.Y[j] = nb.Y[i];
+        U.nwires[j] = nb.nwires[i];
+        U.noise[j] = nb.noise[i];
+        U.prefix[j + 1] = U.prefix[j] + (nb.nwires[i] + kNoiseRows - 1) / kNoiseRows;
+    }
+    if (U.n == 0 || U.prefix[U.n] == 0 || nfreq <= 0) return cudaSuccess;
+    dim3 grid((nfreq + kNoiseCols - 1) / kNoiseCols, U.prefix[U.n]);
+    add_noise_kernel<C><<<grid, kNoiseCols, 0, s>>>(U, nfreq, L, stride);
+    return cudaGetLastError();
+}
+
 // One Stockham pass of radix R over a length-L sequence: butterfly j reads
 // src[j + r L/R], multiplies input r by w^r with w = e^{-+2 pi i (j mod Ns) /
 // (Ns R)} (w from the pass's table of Ns base twiddles, its powers by a
@@ -946,13 +1066,14 @@ static cudaError_t inv_rows_t(const FftPlan& plan, const cplx<S>* tw, const RowB
     if (rb.n <= 0) return cudaSuccess;
     if constexpr (std::is_same<S, float>::value) {
         if (const ShapeKernels* k = shape_kernels(plan)) {
+            const InvShapeFn fn = k->inv;
             const int smem = k->inv_buffers * ((plan.L + 1) & ~1) * (int)sizeof(float2);
-            cudaError_t e = set_smem((const void*)k->inv, smem);
+            cudaError_t e = set_smem((const void*)fn, smem);
             if (e != cudaSuccess) return e;
             bool al = false;
             const RowUnits U = row_units(rb, &al);
             if (U.prefix[rb.n] <= 0) return cudaSuccess;
-            k->inv<<<U.prefix[rb.n], k->inv_threads, smem, s>>>(plan, tw, U, in_stride, nfreq, ncols, out_stride);
+            fn<<<U.prefix[rb.n], k->inv_threads, smem, s>>>(plan, tw, U, in_stride, nfreq, ncols, out_stride);
             return cudaGetLastError();
         }
     }
@@ -1059,6 +1180,14 @@ cudaError_t launch_wire_conv(const float2* X, float2* Y, const float2* Rt, int n
     if (nwires <= 0 || nfreq <= 0) return cudaSuccess;
     return launch_wire_conv_batch(one_conv(X, Y, Rt, nwires), nfreq, stride, kw, center, circular, s, variant,
                                   status);
+}
+
+cudaError_t launch_add_noise(const NoiseBatch& nb, int nfreq, int L, int64_t stride, cudaStream_t s) {
+    return add_noise_t<float2>(nb, nfreq, L, stride, s);
+}
+
+cudaError_t launch_add_noise64(const NoiseBatch& nb, int nfreq, int L, int64_t stride, cudaStream_t s) {
+    return add_noise_t<double2>(nb, nfreq, L, stride, s);
 }
 
 cudaError_t launch_wire_conv64(const double2* X, double2* Y, const double2* Rt, int nwires, int nfreq, int64_t stride,

@@ -38,21 +38,6 @@ template <> struct PrecT<2> { using W = double; };
 __device__ __forceinline__ float erfc_t(float x) { return erfcf(x); }
 __device__ __forceinline__ double erfc_t(double x) { return erfc(x); }
 
-// Philox4x32-10 (Salmon et al., SC'11): ten rounds of two 32x32 multiplies
-// whose high halves are mixed with the other counter words and the key; the
-// key advances by two Weyl constants per round.
-__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1) {
-#pragma unroll
-    for (int r = 0; r < 10; ++r) {
-        const uint32_t hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
-        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
-        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
-        k0 += 0x9E3779B9u;
-        k1 += 0xBB67AE85u;
-    }
-    return c;
-}
-
 // Exact branch: sequential-search inversion of the Binomial(N, s) CDF,
 // s = min(p, 1 - p), in single precision with every operation rounded in a
 // fixed order (f_0 = (1 - s)^N by binary powering over the bits of N, low

@@ -29,9 +29,9 @@ thread_local char g_last_error[256] = "";
 
 const char* const kKernelNames[] = {"memset_grid", "raster_scatter", "fwd_rows", "wire_conv", "inv_rows",
                                     "patch_sizes", "scan", "raster_patches", "scatter_patches", "depo_grads",
-                                    "resp_grad"};
+                                    "resp_grad", "add_noise"};
 enum { K_MEMSET, K_RASTER_SCATTER, K_FWD, K_WCONV, K_INV, K_SIZES, K_SCAN, K_RPATCH, K_SCATTER, K_DGRAD,
-       K_RGRAD, K_COUNT };
+       K_RGRAD, K_NOISE, K_COUNT };
 
 // Record a start event for a traced launch; returns the record slot or -1.
 int trace_begin(ws_plane* pl, int kind, cudaStream_t s) {
@@ -111,7 +111,7 @@ size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 struct Layout {
     ws::FftPlan plan;
     int nfreq, fstride;
-    size_t off_status, off_tw, off_rt, off_x, off_y, off_scan, off_large, off_radj, off_racc, off_grid2;
+    size_t off_status, off_tw, off_rt, off_x, off_y, off_scan, off_large, off_radj, off_racc, off_grid2, off_noise;
     size_t off_tw64, off_rt64, off_x64, off_y64, off_g64, total;
 };
 
@@ -151,6 +151,7 @@ ws_status plan_layout(const ws_plane_desc* d, Layout* lay) {
     lay->off_radj = o; o = align256(o + sizeof(float2) * (size_t)d->resp_nwires * lay->fstride);
     lay->off_racc = o; o = align256(o + sizeof(float2) * (size_t)d->resp_nwires * lay->fstride);
     lay->off_grid2 = o; o = align256(o + sizeof(float) * (size_t)d->nwires * d->nticks);
+    lay->off_noise = o; o = align256(o + 2 * sizeof(float) * (size_t)lay->fstride);
     lay->off_tw64 = lay->off_rt64 = lay->off_x64 = lay->off_y64 = lay->off_g64 = 0;
     if (d->fp64) {
         lay->off_tw64 = o; o = align256(o + sizeof(double2) * (size_t)L);
@@ -228,13 +229,48 @@ ws::RasterArgs raster_args(const ws_plane* pl, const ws_depos* d, const ws_param
     return a;
 }
 
-ws_status convolve_impl(ws_plane* pl, const float* grid, float* out, cudaStream_t s) {
+// The plane's noise term for one simulation call (false: no noise set).
+bool noise_unit(const ws_plane* pl, const ws_params* p, uint32_t event_id, ws::NoiseUnit* nz) {
+    if (pl->noise_mode == 0) return false;
+    nz->amp = pl->noise_amp;
+    nz->coh = pl->noise_mode == 2 ? pl->noise_amp + pl->fstride : nullptr;
+    nz->group = pl->noise_group;
+    nz->evpl = (event_id << 4) | ((uint32_t)pl->desc.plane_id & 15u);
+    nz->scale = 1.0 / (double)pl->plan.L;
+    (void)p;
+    return true;
+}
+
+// One plane's noise over its spectra Y (float2, or double2 for the FP64
+// path) if the plane has noise set.
+ws_status add_plane_noise(ws_plane* pl, const ws_params* p, void* Y, bool fp64, cudaStream_t s) {
+    ws::NoiseBatch nb;
+    if (!noise_unit(pl, p, p->event_id, &nb.noise[0])) return WS_OK;
+    nb.n = 1;
+    nb.Y[0] = Y;
+    nb.nwires[0] = pl->desc.nwires;
+    nb.key0 = (uint32_t)(p->seed & 0xFFFFFFFFu);
+    nb.key1 = (uint32_t)(p->seed >> 32);
+    if (fp64) {
+        WS_LAUNCH(pl, K_NOISE, s, ws::launch_add_noise64(nb, pl->nfreq, pl->plan.L, pl->fstride, s));
+    } else {
+        WS_LAUNCH(pl, K_NOISE, s, ws::launch_add_noise(nb, pl->nfreq, pl->plan.L, pl->fstride, s));
+    }
+    return WS_OK;
+}
+
+ws_status convolve_impl(ws_plane* pl, const float* grid, float* out, cudaStream_t s,
+                        const ws_params* noise_params = nullptr) {
     const ws_plane_desc& d = pl->desc;
     WS_LAUNCH(pl, K_FWD, s, ws::launch_fwd_rows(pl->plan, pl->tw, grid, d.nwires, d.nticks, d.nticks, pl->X,
                                                 pl->fstride, pl->nfreq, 1.0f, s));
     WS_LAUNCH(pl, K_WCONV, s, ws::launch_wire_conv(pl->X, pl->Y, pl->Rt, d.nwires, pl->nfreq, pl->fstride,
                                                    d.resp_nwires, d.resp_wire_center,
                                                    d.conv_mode == WS_CONV_CIRCULAR, s, pl->wconv_variant, pl->status));
+    if (noise_params) {
+        const ws_status st = add_plane_noise(pl, noise_params, pl->Y, false, s);
+        if (st != WS_OK) return st;
+    }
     WS_LAUNCH(pl, K_INV, s, ws::launch_inv_rows(pl->plan, pl->tw, pl->Y, d.nwires, pl->fstride, pl->nfreq, out,
                                                 d.nticks, d.nticks, s));
     return WS_OK;
@@ -316,6 +352,9 @@ ws_status ws_plane_create(const ws_plane_desc* desc, const float* response_dev, 
     pl->Radj = (float2*)(base + lay.off_radj);
     pl->Racc = (float2*)(base + lay.off_racc);
     pl->grid2 = (float*)(base + lay.off_grid2);
+    pl->noise_amp = (float*)(base + lay.off_noise);
+    pl->noise_mode = 0;
+    pl->noise_group = 1;
     pl->fp64 = desc->fp64 != 0;
     pl->tw64 = pl->fp64 ? (double2*)(base + lay.off_tw64) : nullptr;
     pl->Rt64 = pl->fp64 ? (double2*)(base + lay.off_rt64) : nullptr;
@@ -336,33 +375,39 @@ ws_status ws_plane_create(const ws_plane_desc* desc, const float* response_dev, 
     if (e == cudaSuccess && pl->fp64)
         e = ws::launch_fwd_rows64(lay.plan, pl->tw64, response_dev, false, desc->resp_nwires, desc->resp_nticks,
                                   desc->resp_nticks, pl->Rt64, lay.fstride, lay.nfreq, 1.0f / (float)lay.plan.L, s);
-    // Autotune the wire convolution on this plane's own buffers: each variant
-    // once to warm up, then three timed launches; the fastest is kept.
+    // Autotune the wire convolution on this plane's own buffers: every
+    // variant once to warm up, then three rounds over all variants of three
+    // timed launches each (rounds interleave the variants, so a drifting
+    // clock biases none); a variant's time is its best round, and the
+    // fastest variant is kept.
     pl->wconv_variant = 0;
     if (e == cudaSuccess) e = cudaMemsetAsync(pl->X, 0, sizeof(float2) * (size_t)desc->nwires * lay.fstride, s);
     if (e == cudaSuccess) {
         cudaEvent_t t0 = nullptr, t1 = nullptr;
         e = cudaEventCreate(&t0);
         if (e == cudaSuccess) e = cudaEventCreate(&t1);
-        float best = 1e30f;
         const int circ = desc->conv_mode == WS_CONV_CIRCULAR;
         const int nvar = (circ || !ws::tma_available()) ? 4 : ws::kWireConvVariants;
-        for (int v = 0; v < nvar && e == cudaSuccess; ++v) {
-            e = ws::launch_wire_conv(pl->X, pl->Y, pl->Rt, desc->nwires, lay.nfreq, lay.fstride, desc->resp_nwires,
-                                     desc->resp_wire_center, circ, s, v, pl->status);
-            if (e == cudaSuccess) e = cudaEventRecord(t0, s);
-            for (int r = 0; r < 3 && e == cudaSuccess; ++r)
-                e = ws::launch_wire_conv(pl->X, pl->Y, pl->Rt, desc->nwires, lay.nfreq, lay.fstride,
-                                         desc->resp_nwires, desc->resp_wire_center, circ, s, v, pl->status);
-            if (e == cudaSuccess) e = cudaEventRecord(t1, s);
-            if (e == cudaSuccess) e = cudaEventSynchronize(t1);
-            float ms = 0.f;
-            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, t0, t1);
-            if (e == cudaSuccess && ms < best) {
-                best = ms;
-                pl->wconv_variant = v;
+        float best_of[ws::kWireConvVariants];
+        for (int v = 0; v < nvar; ++v) best_of[v] = 1e30f;
+        auto conv = [&](int v) {
+            return ws::launch_wire_conv(pl->X, pl->Y, pl->Rt, desc->nwires, lay.nfreq, lay.fstride,
+                                        desc->resp_nwires, desc->resp_wire_center, circ, s, v, pl->status);
+        };
+        for (int v = 0; v < nvar && e == cudaSuccess; ++v) e = conv(v);
+        for (int round = 0; round < 3 && e == cudaSuccess; ++round) {
+            for (int v = 0; v < nvar && e == cudaSuccess; ++v) {
+                e = cudaEventRecord(t0, s);
+                for (int r = 0; r < 3 && e == cudaSuccess; ++r) e = conv(v);
+                if (e == cudaSuccess) e = cudaEventRecord(t1, s);
+                if (e == cudaSuccess) e = cudaEventSynchronize(t1);
+                float ms = 0.f;
+                if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, t0, t1);
+                if (e == cudaSuccess && ms < best_of[v]) best_of[v] = ms;
             }
         }
+        for (int v = 1; v < nvar; ++v)
+            if (best_of[v] < best_of[pl->wconv_variant]) pl->wconv_variant = v;
         if (t0) cudaEventDestroy(t0);
         if (t1) cudaEventDestroy(t1);
     }
@@ -537,6 +582,8 @@ ws_status ws_simulate(ws_plane* pl, const ws_depos* depos, const ws_params* para
         WS_LAUNCH(pl, K_WCONV, s, ws::launch_wire_conv64(pl->X64, pl->Y64, pl->Rt64, d.nwires, pl->nfreq, pl->fstride,
                                                          d.resp_nwires, d.resp_wire_center,
                                                          d.conv_mode == WS_CONV_CIRCULAR, s));
+        st = add_plane_noise(pl, params, pl->Y64, true, s);
+        if (st != WS_OK) return st;
         WS_LAUNCH(pl, K_INV, s, ws::launch_inv_rows64(pl->plan, pl->tw64, pl->Y64, d.nwires, pl->fstride, pl->nfreq,
                                                       out_dev, d.nticks, d.nticks, s));
         return WS_OK;
@@ -553,12 +600,33 @@ ws_status ws_simulate(ws_plane* pl, const ws_depos* depos, const ws_params* para
         WS_LAUNCH(pl, K_WCONV, s, ws::launch_wire_conv(pl->X, pl->Y, pl->Rt, d.nwires, pl->nfreq, pl->fstride,
                                                        d.resp_nwires, d.resp_wire_center,
                                                        d.conv_mode == WS_CONV_CIRCULAR, s, pl->wconv_variant, pl->status));
+        st = add_plane_noise(pl, params, pl->Y, false, s);
+        if (st != WS_OK) return st;
         WS_LAUNCH(pl, K_INV, s, ws::launch_inv_rows(pl->plan, pl->tw, pl->Y, d.nwires, pl->fstride, pl->nfreq, out_dev,
                                                     d.nticks, d.nticks, s));
         return WS_OK;
     }
     WS_LAUNCH(pl, K_RASTER_SCATTER, s, ws::launch_raster_scatter(a, out_dev, pl->large, s));
-    return convolve_impl(pl, out_dev, out_dev, s);
+    return convolve_impl(pl, out_dev, out_dev, s, params);
+}
+
+ws_status ws_plane_set_noise(ws_plane* pl, const float* amp_dev, const float* coh_amp_dev, int32_t coh_group,
+                             void* stream) {
+    if (!pl) return WS_ERR_INVALID_ARG;
+    if (!amp_dev && !coh_amp_dev) {
+        pl->noise_mode = 0;
+        return WS_OK;
+    }
+    if (!amp_dev || !aligned(amp_dev, 4) || (coh_amp_dev && (!aligned(coh_amp_dev, 4) || coh_group < 1)))
+        return WS_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t bytes = sizeof(float) * (size_t)pl->nfreq;
+    WS_CUDA(cudaMemcpyAsync(pl->noise_amp, amp_dev, bytes, cudaMemcpyDeviceToDevice, s));
+    if (coh_amp_dev)
+        WS_CUDA(cudaMemcpyAsync(pl->noise_amp + pl->fstride, coh_amp_dev, bytes, cudaMemcpyDeviceToDevice, s));
+    pl->noise_mode = coh_amp_dev ? 2 : 1;
+    pl->noise_group = coh_amp_dev ? coh_group : 1;
+    return WS_OK;
 }
 
 ws_status ws_plane_set_response(ws_plane* pl, const float* response_dev, void* stream) {
@@ -764,8 +832,12 @@ ws_status batch_waves(ws_plane* const* planes, int nplanes, const ws_depos* depo
         ws::RowBatch fb, ib;
         ws::ConvBatch cb;
         int64_t counts[ws::kMaxUnits];
-        rb.n = fb.n = ib.n = cb.n = nu;
+        ws::NoiseBatch nb;
+        bool noisy = false;
+        rb.n = fb.n = ib.n = cb.n = nb.n = nu;
         rb.prec = WS_PREC_FP32;
+        nb.key0 = (uint32_t)(params->seed & 0xFFFFFFFFu);
+        nb.key1 = (uint32_t)(params->seed >> 32);
         for (int j = 0; j < nu; ++j) {
             const int u = u0 + j, e = u / nplanes, pi = u % nplanes;
             ws_plane* pl = planes[pi];
@@ -788,6 +860,10 @@ ws_status batch_waves(ws_plane* const* planes, int nplanes, const ws_depos* depo
             ib.in2[j] = nullptr;
             ib.out[j] = out_dev[u];
             ib.nrows[j] = pl->desc.nwires;
+            nb.Y[j] = Y;
+            nb.nwires[j] = pl->desc.nwires;
+            if (noise_unit(pl, params, pe.event_id, &nb.noise[j])) noisy = true;
+            else nb.noise[j] = ws::NoiseUnit{};
         }
         WS_LAUNCH(p0, K_MEMSET, s, ws::launch_zero_grids(rb, counts, s));
         WS_LAUNCH(p0, K_RASTER_SCATTER, s, ws::launch_raster_scatter_batch(rb, L, s));
@@ -796,6 +872,7 @@ ws_status batch_waves(ws_plane* const* planes, int nplanes, const ws_depos* depo
         WS_LAUNCH(p0, K_WCONV, s, ws::launch_wire_conv_batch(cb, p0->nfreq, p0->fstride, d0.resp_nwires,
                                                              d0.resp_wire_center, circ, s, p0->wconv_variant,
                                                              p0->status));
+        if (noisy) WS_LAUNCH(p0, K_NOISE, s, ws::launch_add_noise(nb, p0->nfreq, p0->plan.L, p0->fstride, s));
         WS_LAUNCH(p0, K_INV, s, ws::launch_inv_rows_batch(p0->plan, p0->tw, ib, p0->fstride, p0->nfreq, d0.nticks,
                                                           d0.nticks, s));
     }

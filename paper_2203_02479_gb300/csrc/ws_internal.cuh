@@ -58,6 +58,35 @@ struct RasterArgs {
 // ---- unit tables for launches that cover several (event, plane) units
 constexpr int kMaxUnits = 32;
 
+// Philox4x32-10 (Salmon et al., SC'11): ten rounds of two 32x32 multiplies
+// whose high halves are mixed with the other counter words and the key; the
+// key advances by two Weyl constants per round.
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
+        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    return c;
+}
+
+// Noise term N(t, x) of Eq. 1 for one unit, added to the half spectra Y
+// between the wire convolution and the inverse transform (amp null: none).  Wire w, bin k:
+// Nhat = A[k] xi_w[k] + Ac[k] xi'_{w / group}[k], xi = (z1 + i z2)/sqrt 2
+// (z1 alone at k = 0 and k = L/2), z1, z2 by Box-Muller from words
+// 2 (w % 2), 2 (w % 2) + 1 of the Philox block with counter
+// (1, k, w / 2, evpl) (coherent: (2, k, g / 2, evpl), words by g % 2).
+struct NoiseUnit {
+    const float* amp;     // incoherent amplitude spectrum A[k], L/2 + 1 entries
+    const float* coh;     // coherent amplitude spectrum, or null
+    int group;            // wires per coherent group (>= 1 with coh)
+    uint32_t evpl;        // event << 4 | plane
+    double scale;         // 1 / L: the inverse transform is unnormalised
+};
+
 // Host-side batch descriptions.
 struct RowBatch {          // row transforms: unit i has nrows[i] rows in[i] -> out[i]
     int n;
@@ -65,6 +94,13 @@ struct RowBatch {          // row transforms: unit i has nrows[i] rows in[i] -> 
     const void* in2[kMaxUnits];   // optional float low parts added to in (compensated grids)
     void* out[kMaxUnits];
     int nrows[kMaxUnits];
+};
+struct NoiseBatch {        // noise added to the spectra Y[i] (nwires[i] rows) of each unit
+    int n = 0;
+    void* Y[kMaxUnits];
+    int nwires[kMaxUnits];
+    NoiseUnit noise[kMaxUnits] = {};
+    uint32_t key0 = 0, key1 = 0;       // Philox key (the call's seed)
 };
 struct ConvBatch {         // wire convolutions: unit i maps X[i] -> Y[i] with taps Rt[i]
     int n;
@@ -81,6 +117,14 @@ struct RowUnits {
     const void* in2[kMaxUnits];
     void* out[kMaxUnits];
     int nrows[kMaxUnits];
+};
+struct NoiseUnits {
+    int n;
+    int prefix[kMaxUnits + 1];   // cumulative blocks of kNoiseRows wires
+    void* Y[kMaxUnits];
+    int nwires[kMaxUnits];
+    NoiseUnit noise[kMaxUnits];
+    uint32_t key0, key1;
 };
 struct ConvUnits {
     int n;
@@ -104,6 +148,11 @@ cudaError_t launch_fwd_rows(const FftPlan& plan, const float2* tw, const float* 
 cudaError_t launch_inv_rows(const FftPlan& plan, const float2* tw, const float2* in, int nrows,
                             int64_t in_stride, int nfreq, float* out, int ncols,
                             int64_t out_stride, cudaStream_t s);
+// Noise term of Eq. 1 added in place to each unit's spectra (float2 or
+// double2 rows of `stride`, nfreq bins of a length-L transform); units with
+// a null amplitude are skipped.
+cudaError_t launch_add_noise(const NoiseBatch& nb, int nfreq, int L, int64_t stride, cudaStream_t s);
+cudaError_t launch_add_noise64(const NoiseBatch& nb, int nfreq, int L, int64_t stride, cudaStream_t s);
 // Y[w][k] = sum_r Rt[r][k] * X[w + center - r][k]  (zero or wrapped outside).
 // Batched forms: one launch over every unit (all units share plan, strides,
 // response shape and wire-convolution variant).
@@ -222,6 +271,9 @@ struct ws_plane {
     ws::LargeList large;  // hand-over list of large patches
     float2* Radj;       // K_w x fstride flipped conjugate taps (adjoint)
     float2* Racc;       // K_w x fstride response-gradient spectra
+    float* noise_amp;   // fstride noise amplitudes (incoherent), then fstride coherent
+    int noise_mode;     // 0 none, 1 incoherent, 2 incoherent + coherent
+    int noise_group;    // wires per coherent group
     float* grid2;       // nwires x nticks float scratch grid (adjoint, compensated low parts)
     bool fp64;          // FP64 buffers present
     double2* tw64;      // FP64 pass twiddles

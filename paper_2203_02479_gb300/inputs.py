@@ -19,6 +19,9 @@ workloads the measurements use:
 * ``response``: a 2D response that is a Gaussian in wire times a
   Gaussian-derivative (bipolar, induction planes) or Gaussian (unipolar,
   collection plane) in time.
+* ``noise_amplitudes``: amplitude spectra of the noise term of Eq. 1 (an
+  electronics-shaped bump plus a white floor; a coherent bump shared by a
+  group of channels).
 
 All draws use ``numpy.random.Generator(PCG64(seed))``; every array is
 contiguous float32.
@@ -189,6 +192,24 @@ def response(kind: str = "bipolar", nwires: int = RESP_NWIRES, nticks: int = RES
     else:
         raise ValueError(f"unknown response kind {kind!r}")
     return _f32(np.outer(g, h))
+
+
+def noise_amplitudes(L: int, kind: str = "incoherent", peak: float = 2.0e5, peak_frac: float = 0.1,
+                     floor: float = 0.1) -> np.ndarray:
+    """Synthetic noise amplitude spectrum on the L/2 + 1 half-spectrum bins of
+    a length-L tick transform, float32: a shaped-electronics bump
+    peak * (x / x0) * exp(1 - x / x0) over x = k / (L/2) (x0 = peak_frac of
+    the Nyquist frequency) plus a white floor of floor * peak; the coherent
+    kind is the same bump at 0.3x the height with no floor (it stands in
+    for the noise a group of channels shares)."""
+    k = np.arange(L // 2 + 1, dtype=np.float64)
+    x = k / max(L / 2.0, 1.0)
+    bump = (x / peak_frac) * np.exp(1.0 - x / peak_frac)
+    if kind == "incoherent":
+        return _f32(peak * (bump + floor))
+    if kind == "coherent":
+        return _f32(0.3 * peak * bump)
+    raise ValueError(f"unknown noise kind {kind!r}")
 
 
 # ---------------------------------------------------------------- workloads

@@ -31,7 +31,7 @@ WS_PREC_FP32, WS_PREC_FP32_COMP, WS_PREC_FP64 = 0, 1, 2
 EXPORTED = ("ws_plane_workspace_bytes", "ws_plane_create", "ws_plane_destroy", "ws_plane_get_info",
             "ws_patch_capacity", "ws_rasterize", "ws_scatter", "ws_convolve", "ws_simulate",
             "ws_plane_sync", "ws_plane_clear_status", "ws_plane_trace", "ws_plane_trace_read",
-            "ws_convolve_noalloc", "ws_plane_set_wire_conv_variant", "ws_plane_set_response",
+            "ws_convolve_noalloc", "ws_plane_set_wire_conv_variant", "ws_plane_set_response", "ws_plane_set_noise",
             "ws_simulate_backward", "ws_batch_workspace_bytes", "ws_simulate_batch", "ws_selftest_bounded_wait",
             "ws_status_string", "ws_last_error")
 
@@ -121,6 +121,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
             "ws_convolve_noalloc": [ctypes.POINTER(WsPlaneDesc), P, P, P, P],
             "ws_plane_set_wire_conv_variant": [P, ctypes.c_int],
             "ws_plane_set_response": [P, P, P],
+            "ws_plane_set_noise": [P, P, P, ctypes.c_int32, P],
             "ws_batch_workspace_bytes": [ctypes.POINTER(P), ctypes.c_int, ctypes.c_int,
                                          ctypes.POINTER(ctypes.c_size_t)],
             "ws_simulate_batch": [ctypes.POINTER(P), ctypes.c_int, ctypes.POINTER(WsDepos), ctypes.c_int,
@@ -394,6 +395,28 @@ class Plane:
         self.response = response.to(device=self.device, dtype=torch.float32).contiguous()
         _check(load_library().ws_plane_set_response(self.handle, _ptr(self.response), _stream_handle(stream)),
                "ws_plane_set_response")
+
+    def set_noise(self, amp, coh=None, group: int = 1, stream=None):
+        """Noise term of Eq. 1 for later simulate calls: amplitude spectra of
+        L/2 + 1 entries (L = info.fft_len_tick), incoherent ``amp`` per wire and
+        optional coherent ``coh`` shared by groups of ``group`` wires; both
+        None switch it off."""
+        torch = _torch()
+
+        def dev(a):
+            if a is None:
+                return None
+            if not hasattr(a, "data_ptr"):
+                a = torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32))
+            a = a.to(device=self.device, dtype=torch.float32).contiguous()
+            if a.numel() != self.info.nfreq:
+                raise ValueError(f"noise spectra need {self.info.nfreq} entries (L/2 + 1)")
+            return a
+
+        self.noise = (dev(amp), dev(coh))   # kept alive until the copies ran
+        _check(load_library().ws_plane_set_noise(self.handle, _ptr(self.noise[0]), _ptr(self.noise[1]),
+                                                 int(group), _stream_handle(stream)),
+               "ws_plane_set_noise")
 
     def backward(self, depos: DeviceDepos, params: Params, grad_out, want_response: bool = True, stream=None):
         """(gq, gx, gt, gDL, gDT, gR) as device tensors (gR None if not wanted)."""
