@@ -205,8 +205,11 @@ def raster_scatter(q, x_mm, t_us, nwires: int, nticks: int, *, sig_t_us=None, si
                    exact_max: int = EXACT_MAX, return_skipped: bool = False):
     """Raster every depo into its patch and scatter-add into S[wire][tick] (FP64).
 
-    Sec. 2.2 (raster, scatter-add), Sec. 3.1 (binomial fluctuation).  Pinned
-    by patch sums (closed form), linearity and the pins of its parts."""
+    Sec. 2.2 (raster, scatter-add), Sec. 3.1 (binomial fluctuation).
+    fluctuate: False/0 expected value, True/1 a binomial per bin, 2 the
+    charge-conserving multinomial split of each depo's survivors.  Pinned
+    by patch sums (closed form), linearity and the pins of its parts; the
+    multinomial by exact conservation and the multinomial's moments."""
     q = _c64(q); x = _c64(x_mm); t = _c64(t_us)
     st = None if sig_t_us is None else _c64(sig_t_us)
     sx = None if sig_x_mm is None else _c64(sig_x_mm)
@@ -215,7 +218,7 @@ def raster_scatter(q, x_mm, t_us, nwires: int, nticks: int, *, sig_t_us=None, si
     S = np.zeros((nwires, nticks))
     skipped = _lib().wso_raster_scatter(
         q.shape[0], q, x, t, _opt_ptr(st), _opt_ptr(sx), nwires, nticks, pitch_mm, tick_us,
-        nsig, DL_, DT_, v, int(bool(fluctuate)), float(p), int(seed) & (2 ** 64 - 1),
+        nsig, DL_, DT_, v, int(fluctuate), float(p), int(seed) & (2 ** 64 - 1),
         event_id & 0xFFFFFFFF, plane_id & 0xFFFFFFFF, int(exact_max), S)
     return (S, int(skipped)) if return_skipped else S
 

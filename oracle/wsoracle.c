@@ -206,6 +206,95 @@ int64_t wso_binomial(int64_t N, double p, int exact_max, const uint32_t key[2],
 }
 
 /* ------------------------------------------------------------------------ */
+/* Charge-conserving fluctuation (alternative sampler; the paper's CPU
+ * reference draws binomials, Sec. 3.1, without saying how the bins share a
+ * depo's electrons).  Reading: the depo carries N = floor(q + 1/2)
+ * electrons; K ~ Binomial(N, p) survive (block (5, 0, depo, evpl), the
+ * sampler of wso_binomial); the K are spread over the patch multinomially
+ * with the bin weights w_x[j] w_t[i]: over the in-grid wires in order by
+ * conditional binomials n_j ~ Binomial(rem, w_x[j] / W) (W the wire mass
+ * not yet visited, W = 1 at the start, both in float; block
+ * (4, wire, depo, evpl)), then within wire j over its in-grid ticks the
+ * same way (block (3, wire * nticks + tick, depo, evpl)).  Electrons still
+ * unassigned after the last in-grid bin belong to bins off the grid and are
+ * lost; when every bin of an axis's window is on the grid, that axis's
+ * last bin takes all that remain, so an interior depo keeps exactly K.
+ * A conditional draw Binomial(n, pr), pr a float: pr <= 0 gives 0, pr >= 1
+ * gives n; n <= exact_max: the float inversion of wso_binomial_invert; else
+ * the normal approximation from words 0, 1 of the block (Box-Muller as in
+ * wso_binomial), k = clamp(floor(n pr + z sqrt(n pr (1 - pr)) + 1/2), 0, n). */
+static int64_t wso_binom_var(int64_t n, float pr, int exact_max, const uint32_t key[2],
+                             uint32_t c0, uint32_t c1, uint32_t depo, uint32_t evpl)
+{
+    if (n <= 0 || !(pr > 0.0f)) return 0;
+    if (pr >= 1.0f) return n;
+    uint32_t ctr[4] = {c0, c1, depo, evpl}, x[4];
+    wso_philox4x32_10(ctr, key, x);
+    if (n <= exact_max) return wso_binomial_invert(n, (double)pr, x[0]);
+    double u1 = ((double)x[0] + 0.5) / 4294967296.0;
+    double u2 = ((double)x[1] + 0.5) / 4294967296.0;
+    double z = sqrt(-2.0 * log(u1)) * cos(2.0 * M_PI * u2);
+    double mean = (double)n * (double)pr;
+    double k = floor(mean + z * sqrt(mean * (1.0 - (double)pr)) + 0.5);
+    if (k < 0.0) k = 0.0;
+    if (k > (double)n) k = (double)n;
+    return (int64_t)k;
+}
+
+/* Survivors of the depo, then its multinomial split, added into S. */
+static void wso_multinomial_depo(double q, int64_t wlo, int nw, const double* wx, int64_t klo, int nt,
+                                 const double* wt, int nwires, int nticks, double p, int exact_max,
+                                 const uint32_t key[2], uint32_t depo, uint32_t evpl, double* S)
+{
+    int64_t N = (int64_t)floor(q + 0.5);
+    if (N <= 0 || !(p > 0.0)) return;
+    int64_t K = N;
+    if (p < 1.0) {
+        uint32_t ctr[4] = {5u, 0u, depo, evpl}, x[4];
+        wso_philox4x32_10(ctr, key, x);
+        if (N <= exact_max) {
+            K = wso_binomial_invert(N, p, x[0]);
+        } else {
+            const uint32_t T = wso_survive_threshold(p);
+            double u1 = ((double)x[0] + 0.5) / 4294967296.0;
+            double u2 = ((double)x[1] + 0.5) / 4294967296.0;
+            double z = sqrt(-2.0 * log(u1)) * cos(2.0 * M_PI * u2);
+            double pe = (double)T / 4294967296.0;
+            double mean = (double)N * pe;
+            double k = floor(mean + z * sqrt(mean * (1.0 - pe)) + 0.5);
+            K = (int64_t)(k < 0.0 ? 0.0 : (k > (double)N ? (double)N : k));
+        }
+    }
+    int64_t rem = K;
+    float Wx = 1.0f;
+    const int64_t wlast = wlo + nw - 1, klast = klo + nt - 1;
+    /* the last bin takes all that remain only if no bin of the axis is off the grid */
+    const int wfull = wlo >= 0 && wlast < nwires, kfull = klo >= 0 && klast < nticks;
+    for (int a = 0; a < nw && rem > 0; ++a) {
+        const int64_t w = wlo + a;
+        if (w < 0 || w >= nwires) continue;
+        const float wf = (float)wx[a];
+        const float pr = (wfull && w == wlast) ? 1.0f : wf / Wx;
+        const int64_t nj = wso_binom_var(rem, pr, exact_max, key, 4u, (uint32_t)w, depo, evpl);
+        rem -= nj;
+        Wx = Wx - wf;
+        int64_t rem2 = nj;
+        float Wt = 1.0f;
+        for (int b = 0; b < nt && rem2 > 0; ++b) {
+            const int64_t k = klo + b;
+            if (k < 0 || k >= nticks) continue;
+            const float tf = (float)wt[b];
+            const float pt = (kfull && k == klast) ? 1.0f : tf / Wt;
+            const int64_t m = wso_binom_var(rem2, pt, exact_max, key, 3u, (uint32_t)(w * (int64_t)nticks + k),
+                                            depo, evpl);
+            rem2 -= m;
+            Wt = Wt - tf;
+            S[w * (int64_t)nticks + k] += (double)m;
+        }
+    }
+}
+
+/* ------------------------------------------------------------------------ */
 /* One plane's raster + fluctuation + scatter-add (Sec. 2.2).  Depos are
  * processed one by one; each patch bin inside the nwires x nticks grid is
  * added into S (row-major [wire][tick], double).  Bins outside the grid are
@@ -214,8 +303,9 @@ int64_t wso_binomial(int64_t N, double p, int exact_max, const uint32_t key[2],
  * return value.
  *
  * sig_t_us / sig_x_mm may be NULL, in which case they come from diffusion.
- * If fluctuate == 0 a bin receives the expected value p*q*w_t*w_x; else it
- * receives a binomial count (see wso_binomial). */
+ * If fluctuate == 0 a bin receives the expected value p*q*w_t*w_x; if 1 a
+ * binomial count (see wso_binomial); if 2 the depo's surviving electrons are
+ * spread multinomially (see wso_multinomial_depo). */
 #define WSO_MAXBINS 65536
 
 int64_t wso_raster_scatter(int64_t n, const double* q, const double* x_mm, const double* t_us,
@@ -242,6 +332,11 @@ int64_t wso_raster_scatter(int64_t n, const double* q, const double* x_mm, const
         int nt = wso_axis_weights(ti, st, tick_us, nsig, WSO_MAXBINS, &klo, wt);
         int nw = wso_axis_weights(xi, sx, pitch_mm, nsig, WSO_MAXBINS, &wlo, wx);
         if (nt < 0 || nw < 0) { ++skipped; continue; }
+        if (fluctuate == 2) {
+            wso_multinomial_depo(qi, wlo, nw, wx, klo, nt, wt, nwires, nticks, p, exact_max, key, (uint32_t)i,
+                                 evpl, S);
+            continue;
+        }
         for (int a = 0; a < nw; ++a) {
             int64_t w = wlo + a;
             if (w < 0 || w >= nwires) continue;
