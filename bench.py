@@ -371,6 +371,38 @@ def noise_leg(wiresim, dev, stream, flush, steps: int, units_per_wave: int, plai
                      "and the inverse transform (one more launch per wave)"}
 
 
+def multinomial_leg(wiresim, dev, stream, flush, steps: int, units_per_wave: int, plain_ms: float):
+    """The benchmark event with the charge-conserving fluctuation
+    (fluctuate = 2: binomial survivors per depo, multinomial split over the
+    patch), replayed from a CUDA graph like the timed step."""
+    import torch
+    w = make_workload("three_planes", 0)
+    planes = [wiresim.Plane(sp.nwires, sp.nticks, sp.response, plane_id=sp.plane_id, device=dev) for sp in w.planes]
+    depos = [wiresim.DeviceDepos.from_plane_depos(d, device=dev) for d in w.events[0]]
+    params = wiresim.Params(fluctuate=2, p_survive=w.p_survive, seed=w.seed)
+    b = wiresim.Batch(planes, [depos], params, units_per_wave=units_per_wave, device=dev)
+    b.capture()
+    for _ in range(3):
+        b.replay()
+    torch.cuda.synchronize(dev)
+    ms = sorted(_time_steps(b.replay, steps, stream, flush))[steps // 2]
+    # the raster stage alone, traced
+    planes[0].trace(steps * 16 + 16)
+    for _ in range(steps):
+        flush.zero_()
+        b.run(stream)
+    torch.cuda.synchronize(dev)
+    st = planes[0].trace_read()
+    planes[0].trace(0)
+    ndp = sum(d.n for d in w.events[0])
+    for pl in planes:
+        pl.close()
+    rn, rms = st.get("raster_scatter", (1, 0.0))
+    return {"workload": w.name + ", fluctuate = 2 (charge-conserving multinomial)", "ms_per_step": ms,
+            "value": ndp / (ms * 1e-3), "unit": UNIT, "over_plain": ms / plain_ms,
+            "raster_ms_per_launch": rms / max(rn, 1)}
+
+
 def adjoint_leg(wiresim, dev, stream, flush, steps: int):
     """Forward and adjoint (ws_simulate_backward: gradients for q, x, t of
     every depo, D_L, D_T and the response) of one 960 x 6000 plane with
@@ -635,11 +667,14 @@ def run_gpu(args):
     batched = None
     adjoint = None
     noise = None
+    multinomial = None
     if rank == 0 and world == 1 and not args.no_batched_workload:
         batched = batched_workload_comparison(wiresim, dev, stream, flush, max(3, min(args.steps, 10)))
         adjoint = adjoint_leg(wiresim, dev, stream, flush, max(5, min(args.steps, 50)))
         noise = noise_leg(wiresim, dev, stream, flush, max(5, min(args.steps, 200)), upw_event,
                           sorted(graph_ms)[len(graph_ms) // 2])
+        multinomial = multinomial_leg(wiresim, dev, stream, flush, max(5, min(args.steps, 200)), upw_event,
+                                      sorted(graph_ms)[len(graph_ms) // 2])
     if rank != 0:
         if dist is not None:
             dist.destroy_process_group()
@@ -682,6 +717,7 @@ def run_gpu(args):
         "batched_workload": batched,
         "adjoint": adjoint,
         "noise": noise,
+        "multinomial": multinomial,
     }
     print(json.dumps(line), flush=True)
     if dist is not None:

@@ -109,7 +109,16 @@ typedef struct {
     double DT_mm2_us;         /* transverse diffusion constant              */
     double v_mm_us;           /* drift speed                                */
     int32_t fluctuate;        /* 0: expected value p*q*w per bin;
-                                 1: Binomial(floor(q*w + 1/2), p) per bin   */
+                                 1: Binomial(floor(q*w + 1/2), p) per bin;
+                                 2: charge-conserving: K ~ Binomial(
+                                    floor(q + 1/2), p) survivors per depo,
+                                    spread over its bins multinomially by
+                                    conditional binomials over the in-grid
+                                    wires, then ticks (Philox counters
+                                    (5,0,depo,.), (4,wire,depo,.),
+                                    (3,bin,depo,.)); electrons of off-grid
+                                    bins are lost, an interior depo keeps
+                                    exactly K.  Other values are invalid.   */
     double p_survive;         /* electron survival probability p            */
     uint64_t seed;            /* Philox key                                 */
     uint32_t event_id;        /* < 2^28, part of the Philox counter         */

@@ -46,8 +46,9 @@ __device__ __forceinline__ double erfc_t(double x) { return erfc(x); }
 // 24 bits of the word over 2^24; k = the first k with u < F_k (N if none),
 // mirrored to N - k for p > 1/2.  Any IEEE-754 machine doing these steps
 // takes the same decisions.  recip[i] holds 1/i.
-__device__ __forceinline__ int invert_binomial(int N, uint32_t x0, const RasterArgs& a, const float* recip) {
-    float f = 1.0f, base = a.inv_base;
+__device__ __forceinline__ int invert_binomial_s(int N, uint32_t x0, float inv_base, float inv_r, int flip,
+                                                 const float* recip) {
+    float f = 1.0f, base = inv_base;
     for (int n = N; n > 0; n >>= 1) {
         if (n & 1) f = __fmul_rn(f, base);
         base = __fmul_rn(base, base);
@@ -56,13 +57,17 @@ __device__ __forceinline__ int invert_binomial(int N, uint32_t x0, const RasterA
     float F = f;
     int k = 0;
     while (!(u < F) && k < N) {
-        f = __fmul_rn(f, a.inv_r);
+        f = __fmul_rn(f, inv_r);
         f = __fmul_rn(f, __int2float_rn(N - k));
         f = __fmul_rn(f, recip[k + 1]);
         F = __fadd_rn(F, f);
         ++k;
     }
-    return a.inv_flip ? N - k : k;
+    return flip ? N - k : k;
+}
+
+__device__ __forceinline__ int invert_binomial(int N, uint32_t x0, const RasterArgs& a, const float* recip) {
+    return invert_binomial_s(N, x0, a.inv_base, a.inv_r, a.inv_flip, recip);
 }
 
 // Normal approximation of Binomial(N, p) from words 0, 1 of Philox block 0
@@ -669,6 +674,165 @@ raster_small_kernel(const __grid_constant__ RasterUnits U, ws_patches pt, long l
     }
 }
 
+// ---- charge-conserving (multinomial) fluctuation, ws_params.fluctuate = 2
+//
+// A depo's N = floor(q + 1/2) electrons survive as K ~ Binomial(N, p)
+// (Philox block (5, 0, depo, evpl), the sampler of the binomial mode), and
+// the K are spread over the patch multinomially with its bin weights: over
+// the in-grid wires in order by conditional binomials n_j ~ Binomial(rem,
+// w_x[j] / W) (W the wire mass not yet visited, from 1, in float; block
+// (4, wire, depo, evpl)), then within wire j over its in-grid ticks alike
+// (block (3, wire * nticks + tick, depo, evpl)).  What is still unassigned
+// after the last in-grid bin fell off the grid and is lost; when a whole
+// axis window lies on the grid its last bin takes all that remain, so an
+// interior depo keeps exactly K.  Lane per depo; the weights are formed
+// edge by edge as the walk goes (one erfc per bin edge).
+
+// Binomial(n, pr) for a float pr: float inversion (same operations as the
+// binomial mode's exact branch) for n <= exact_max; else the normal
+// approximation with the mean n pr exact in double and z from words 0, 1.
+__device__ __forceinline__ int binomial_var(int n, float pr, const RasterArgs& a, uint32_t c0, uint32_t c1,
+                                            uint32_t depo, const float* recip) {
+    if (n <= 0 || !(pr > 0.f)) return 0;
+    if (pr >= 1.f) return n;
+    const uint4 x = philox4x32_10(make_uint4(c0, c1, depo, a.evpl), a.key0, a.key1);
+    if (n <= a.exact_max) {
+        const int flip = pr > 0.5f;
+        const float sv = flip ? __fsub_rn(1.f, pr) : pr;
+        const float base = __fsub_rn(1.f, sv);
+        return invert_binomial_s(n, x.x, base, __fdiv_rn(sv, base), flip, recip);
+    }
+    const float two_m32 = 2.3283064365386963e-10f;
+    const float u1 = fmaf((float)x.x, two_m32, 0.5f * two_m32);
+    const float u2 = fmaf((float)x.y, two_m32, 0.5f * two_m32);
+    const float z = sqrtf(fmaxf(-2.f * __logf(u1), 0.f)) * -__cosf(6.28318530717958648f * (u2 - 0.5f));
+    const double mean = (double)n * (double)pr;
+    const double sd = sqrt(mean * (1.0 - (double)pr));
+    const double kf = floor(mean + (double)z * sd + 0.5);
+    return kf < 0.0 ? 0 : (kf > (double)n ? n : (int)kf);
+}
+
+// Standardised clamped edge u and erfc(|u|) of bin edge e along an axis.
+struct AxisWalk {
+    float mu, inv_s2, umax, delta, inv_norm;
+    bool point;
+    __device__ __forceinline__ void edge(int e, float& u, float& c) const {
+        u = fminf(fmaxf(((float)e * delta - mu) * inv_s2, -umax), umax);
+        c = erfcf(fabsf(u));
+    }
+};
+
+__device__ __forceinline__ AxisWalk axis_walk(float mu, float sigma, float delta, float nsig, bool point,
+                                              float inv_norm) {
+    AxisWalk w;
+    w.mu = mu;
+    w.point = point;
+    w.delta = delta;
+    w.inv_s2 = point ? 0.f : 1.f / (1.41421356237309504880f * sigma);
+    w.umax = nsig * 0.70710678118654752440f;
+    w.inv_norm = inv_norm;
+    return w;
+}
+
+// Whether the unclipped window of the axis lies on the grid.
+__device__ __forceinline__ bool window_on_grid(float mu, float sigma, float delta, float nsig, bool point,
+                                               int nbins) {
+    const float lo_e = point ? mu : mu - nsig * sigma;
+    const float hi_e = point ? mu : mu + nsig * sigma;
+    return floorf(lo_e / delta) >= 0.f && floorf(hi_e / delta) <= (float)(nbins - 1);
+}
+
+template <int MODE, int P>
+__global__ void __launch_bounds__(128)
+raster_multinomial_kernel(const __grid_constant__ RasterUnits U, ws_patches pt) {
+    using W = typename PrecT<P>::W;
+    __shared__ float s_recip[kExactCap + 1];
+    fill_recip(s_recip);
+    const int64_t total = U.dprefix[U.n];
+    for (int64_t it = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; it < total;
+         it += (int64_t)gridDim.x * blockDim.x) {
+        const int u = find_unit64(U.dprefix, U.n, it);
+        const int64_t i = it - U.dprefix[u];
+        const RasterArgs& a = U.a[u];
+        float* __restrict__ grid = U.grid[u];
+        Extent e;
+        float q = 0.f;
+        bool bad = false;
+        const bool any = depo_extent<float>(a, i, &e, &q, &bad);
+        if (bad) atomicOr(a.status, WS_DEV_BAD_DEPO);
+        const int ntc = any ? e.k1 - e.k0 + 1 : 0;
+        const int nxc = any ? e.w1 - e.w0 + 1 : 0;
+        int64_t off = 0;
+        if (MODE == EMIT_PATCH) {
+            off = pt.off[i];
+            const bool fits = off + (int64_t)ntc * nxc <= pt.capacity_bins;
+            pt.w0[i] = any ? e.w0 : 0;
+            pt.t0[i] = any ? e.k0 : 0;
+            pt.nw[i] = fits ? nxc : 0;
+            pt.nt[i] = fits ? ntc : 0;
+            if (!fits) atomicOr(a.status, WS_DEV_PATCH_OVERFLOW);
+            if (!fits) continue;
+        }
+        if (!any) continue;
+        const int N = electrons(q);
+        int K = 0;
+        if (N > 0 && a.T != 0u) {
+            if (a.keep_all) {
+                K = N;
+            } else {
+                const uint4 x = philox4x32_10(make_uint4(5u, 0u, (uint32_t)i, a.evpl), a.key0, a.key1);
+                K = N <= a.exact_max ? invert_binomial(N, x.x, a, s_recip) : normal_draw<0>(x, N, a);
+            }
+        }
+        const float inv_norm = window_norm<float>(a);
+        const AxisWalk wx = axis_walk(e.mu_x, e.sx, a.pitch, a.nsig, e.point_x, inv_norm);
+        const AxisWalk wt = axis_walk(e.mu_t, e.st, a.tick, a.nsig, e.point_t, inv_norm);
+        const bool xfull = window_on_grid(e.mu_x, e.sx, a.pitch, a.nsig, e.point_x, a.nwires);
+        const bool tfull = window_on_grid(e.mu_t, e.st, a.tick, a.nsig, e.point_t, a.nticks);
+        int rem = K;
+        float Wx = 1.f;
+        float ux0 = 0.f, cx0 = 0.f;
+        if (!e.point_x) wx.edge(e.w0, ux0, cx0);
+        for (int j = e.w0; j <= e.w1; ++j) {
+            if (MODE == EMIT_GRID && rem <= 0) break;
+            float wj = 1.f;
+            if (!e.point_x) {
+                float ux1, cx1;
+                wx.edge(j + 1, ux1, cx1);
+                wj = bin_mass(ux0, ux1, cx0, cx1) * inv_norm;
+                ux0 = ux1;
+                cx0 = cx1;
+            }
+            const float prj = (xfull && j == e.w1) ? 1.f : __fdiv_rn(wj, Wx);
+            const int nj = binomial_var(rem, prj, a, 4u, (uint32_t)j, (uint32_t)i, s_recip);
+            rem -= nj;
+            Wx = __fsub_rn(Wx, wj);
+            int rem2 = nj;
+            float Wt = 1.f;
+            float ut0 = 0.f, ct0 = 0.f;
+            if (!e.point_t) wt.edge(e.k0, ut0, ct0);
+            for (int k = e.k0; k <= e.k1; ++k) {
+                if (MODE == EMIT_GRID && rem2 <= 0) break;
+                float wk = 1.f;
+                if (!e.point_t) {
+                    float ut1, ct1;
+                    wt.edge(k + 1, ut1, ct1);
+                    wk = bin_mass(ut0, ut1, ct0, ct1) * inv_norm;
+                    ut0 = ut1;
+                    ct0 = ct1;
+                }
+                const float prk = (tfull && k == e.k1) ? 1.f : __fdiv_rn(wk, Wt);
+                const int64_t bin = (int64_t)j * a.nticks + k;
+                const int m = binomial_var(rem2, prk, a, 3u, (uint32_t)bin, (uint32_t)i, s_recip);
+                rem2 -= m;
+                Wt = __fsub_rn(Wt, wk);
+                if (MODE == EMIT_GRID) emit<P>(a, grid, bin, (W)m);
+                else pt.val[off + (int64_t)(j - e.w0) * ntc + (k - e.k0)] = (float)m;
+            }
+        }
+    }
+}
+
 // ---- adjoint of the expected-value raster (warp per depo)
 //
 // Patch = p q w_t w_x; with u = (e - mu)/sigma clamped to +-n at the window
@@ -1118,6 +1282,10 @@ template <int MODE, int P>
 static cudaError_t launch_raster_units(const RasterUnits& U, const ws_patches& p, const LargeList& L,
                                        cudaStream_t s) {
     if (U.dprefix[U.n] <= 0) return cudaSuccess;
+    if (U.a[0].fluct == 2) {   // every unit of a call shares its fluctuation mode
+        raster_multinomial_kernel<MODE, P><<<grid_for(U.dprefix[U.n], 128, 16), 128, 0, s>>>(U, p);
+        return cudaGetLastError();
+    }
     const int64_t groups = U.gprefix[U.n];
     int blocks = grid_for(groups * 32, 32 * kSmallWarpsPerBlock, 16);
     // CDF rows for the exact branch of unit 0's survival probability (rows up

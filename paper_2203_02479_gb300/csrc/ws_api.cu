@@ -182,6 +182,7 @@ ws_status check_params(const ws_params* p) {
     if (!(p->p_survive >= 0) || !(p->p_survive <= 1)) return WS_ERR_INVALID_ARG;
     if (p->event_id >= (1u << 28)) return WS_ERR_INVALID_ARG;
     if (p->fluct_exact_max < 0 || p->fluct_exact_max > ws::kExactCap) return WS_ERR_INVALID_ARG;
+    if (p->fluctuate < 0 || p->fluctuate > 2) return WS_ERR_INVALID_ARG;
     if (p->precision != WS_PREC_FP32 && p->precision != WS_PREC_FP32_COMP && p->precision != WS_PREC_FP64)
         return WS_ERR_INVALID_ARG;
     return WS_OK;
@@ -198,7 +199,7 @@ ws::RasterArgs raster_args(const ws_plane* pl, const ws_depos* d, const ws_param
     a.two_DL = (float)(2.0 * p->DL_mm2_us);
     a.two_DT = (float)(2.0 * p->DT_mm2_us);
     a.inv_v = (float)(1.0 / p->v_mm_us);
-    a.fluct = p->fluctuate ? 1 : 0;
+    a.fluct = p->fluctuate;
     a.p = (float)p->p_survive;
     if (!(p->p_survive > 0)) a.T = 0u;
     else if (p->p_survive >= 1.0) a.T = 0xFFFFFFFFu;

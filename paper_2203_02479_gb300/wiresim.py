@@ -260,7 +260,7 @@ class Params:
     DL_mm2_us: float = 4.0e-4
     DT_mm2_us: float = 8.8e-4
     v_mm_us: float = 1.6
-    fluctuate: bool = False
+    fluctuate: int = 0        # 0 expected value, 1 (True) binomial per bin, 2 multinomial (charge-conserving)
     p_survive: float = 1.0
     seed: int = 0
     event_id: int = 0
@@ -268,7 +268,7 @@ class Params:
     precision: int = WS_PREC_FP32
 
     def c(self) -> WsParams:
-        return WsParams(self.DL_mm2_us, self.DT_mm2_us, self.v_mm_us, int(bool(self.fluctuate)),
+        return WsParams(self.DL_mm2_us, self.DT_mm2_us, self.v_mm_us, int(self.fluctuate),
                         self.p_survive, self.seed & (2 ** 64 - 1), self.event_id, self.fluct_exact_max,
                         self.precision)
 

@@ -1,0 +1,168 @@
+"""Charge-conserving (multinomial) fluctuation on the GPU (fluctuate = 2).
+
+Both sides take every sampling decision in float from the same Philox words
+(the conditional probabilities w / W in float, the exact branch's float CDF
+inversion, the normal branch's mean n*pr exact in double), so a depo's patch
+is bit-identical to the oracle's unless a float weight (erfcf on the GPU,
+erfc in double rounded to float in the oracle) or the FP32 normal deviate
+lands a decision on the other side of a boundary; then that depo's later
+draws differ.  The tests ask for >= 97% identical patches, equal totals for
+>= 99% of depos, exact conservation for interior depos (a closed form, on
+the GPU alone), the multinomial's moments over seeds, and batch ==
+per-unit bit for bit.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2203_02479_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ws():
+    import torch
+    from paper_2203_02479_gb300 import build, wiresim
+    build.build()
+    wiresim.load_library()
+    torch.cuda.set_device(0)
+    return wiresim
+
+
+def to_np(t):
+    import torch
+    torch.cuda.synchronize()
+    return t.detach().cpu().numpy().astype(np.float64)
+
+
+def _gpu_patches(ws, plane, d, params):
+    p = plane.rasterize(ws.DeviceDepos.from_plane_depos(d), params)
+    h = {k: to_np(v) if hasattr(v, "data_ptr") else v for k, v in p.items()}
+    out = []
+    for i in range(d.n):
+        nw, nt = int(h["nw"][i]), int(h["nt"][i])
+        off = int(h["off"][i])
+        out.append((int(h["w0"][i]), int(h["t0"][i]), h["val"][off:off + nw * nt].reshape(nw, nt)))
+    return out
+
+
+def _oracle_patch(d, i, nw, nt, **kw):
+    """Depo i alone (the others masked as non-finite, so it keeps index i)."""
+    q = np.full(d.n, np.nan)
+    q[i] = d.q[i]
+    return oracle.raster_scatter(q, d.x_mm, d.t_us, nw, nt, fluctuate=2, **kw)
+
+
+@pytest.mark.parametrize("p,exact_max", [(0.7, 32), (1.0, 64), (0.3, 0)])
+def test_patches_match_oracle(ws, p, exact_max):
+    nw, nt = 48, 600
+    pl = ws.Plane(nw, nt, inputs.response("bipolar"), plane_id=3)
+    d = inputs.uniform_depos(300, nw, seed=17, nticks=nt)
+    params = ws.Params(fluctuate=2, p_survive=p, seed=4242, event_id=5, fluct_exact_max=exact_max)
+    got = _gpu_patches(ws, pl, d, params)
+    same = tot_same = 0
+    for i in range(d.n):
+        ref = _oracle_patch(d, i, nw, nt, p=p, seed=4242, event_id=5, plane_id=3, exact_max=exact_max)
+        w0, t0, P = got[i]
+        G = np.zeros((nw, nt))
+        G[w0:w0 + P.shape[0], t0:t0 + P.shape[1]] = P
+        same += np.array_equal(G, ref)
+        tot_same += G.sum() == ref.sum()
+        assert np.all(P >= 0) and np.all(P == np.round(P))
+    assert same >= 0.97 * d.n, same
+    assert tot_same >= 0.99 * d.n, tot_same
+    assert pl.status() == 0
+
+
+def test_interior_depos_conserve_exactly(ws):
+    """p = 1: every depo whose window lies on the grid keeps floor(q + 1/2)."""
+    nw, nt = 64, 2000
+    pl = ws.Plane(nw, nt, inputs.response("bipolar"))
+    rng = np.random.Generator(np.random.PCG64(9))
+    n = 5000
+    q = rng.uniform(1, 60000, n).astype(np.float32)
+    x = rng.uniform(30, nw * 5.0 - 30, n).astype(np.float32)
+    t = rng.uniform(10, nt * 0.5 - 20, n).astype(np.float32)
+    d = inputs.PlaneDepos(q, x, t)
+    got = _gpu_patches(ws, pl, d, ws.Params(fluctuate=2, p_survive=1.0, seed=1))
+    sums = np.array([P.sum() for _, _, P in got])
+    assert np.array_equal(sums, np.floor(q.astype(np.float64) + 0.5))
+
+
+def test_moments_over_seeds(ws):
+    """One depo, p = 1, N = 3000: per-bin mean N w and variance N w (1 - w),
+    and the negative covariance -N w_a w_b of the two heaviest bins."""
+    import torch
+    nw, nt = 16, 200
+    pl = ws.Plane(nw, nt, inputs.response("unipolar"))
+    x, t, N = 41.0, 60.0, 3000.0
+    d = ws.DeviceDepos(np.array([N], np.float32), np.array([x], np.float32), np.array([t], np.float32))
+    st, sx = oracle.sigmas([np.float32(t)])
+    k0, wt = oracle.axis_weights(float(np.float32(t)), st[0], oracle.TICK_US)
+    w0, wx = oracle.axis_weights(float(np.float32(x)), sx[0], oracle.PITCH_MM)
+    W = np.zeros((nw, nt))
+    W[w0:w0 + len(wx), k0:k0 + len(wt)] = np.outer(wx, wt)
+    idx = np.argwhere(W > 0.01)
+    w = W[idx[:, 0], idx[:, 1]]
+    reps = 1500
+    C = np.zeros((reps, len(w)))
+    for s in range(reps):
+        p = pl.rasterize(d, ws.Params(fluctuate=2, p_survive=1.0, seed=77 + s))
+        G = np.zeros((nw, nt))
+        nwp, ntp = int(p["nw"][0]), int(p["nt"][0])
+        G[int(p["w0"][0]):int(p["w0"][0]) + nwp, int(p["t0"][0]):int(p["t0"][0]) + ntp] = \
+            to_np(p["val"][: nwp * ntp]).reshape(nwp, ntp)
+        C[s] = G[idx[:, 0], idx[:, 1]]
+        assert G.sum() == N
+    var = N * w * (1 - w)
+    assert np.all(np.abs(C.mean(axis=0) - N * w) < 5 * np.sqrt(var / reps))
+    a, b = np.argsort(w)[-2:]
+    cov = np.mean((C[:, a] - C[:, a].mean()) * (C[:, b] - C[:, b].mean()))
+    expect = -N * w[a] * w[b]
+    assert abs(cov - expect) < 5 * np.sqrt((var[a] * var[b] + expect ** 2) / reps)
+
+
+def test_three_planes_full_size(ws):
+    """The benchmark event with fluctuate = 2 against the oracle: whole
+    waveforms within 1e-3 (rare depos take a different draw) and the
+    grids' total charge within 1e-4."""
+    import torch
+    w = inputs.three_planes()
+    for sp, dp in zip(w.planes, w.events[0]):
+        pl = ws.Plane(sp.nwires, sp.nticks, sp.response, plane_id=sp.plane_id)
+        params = ws.Params(fluctuate=2, p_survive=0.7, seed=w.seed)
+        got = to_np(pl.simulate(ws.DeviceDepos.from_plane_depos(dp), params))
+        S = oracle.raster_scatter(dp.q, dp.x_mm, dp.t_us, sp.nwires, sp.nticks, fluctuate=2, p=0.7, seed=w.seed,
+                                  plane_id=sp.plane_id)
+        ref = oracle.convolve_fft(S, sp.response, 10)
+        assert np.linalg.norm(got - ref) / np.linalg.norm(ref) <= 1e-3
+        delta = np.zeros((21, 200), np.float32); delta[10, 0] = 1.0
+        pl.set_response(delta)
+        Sg = to_np(pl.simulate(ws.DeviceDepos.from_plane_depos(dp), params))
+        assert abs(Sg.sum() - S.sum()) <= 1e-4 * S.sum()
+        assert pl.status() == 0
+
+
+def test_batch_equals_per_unit_and_fp64(ws):
+    import torch
+    wires, nt = (40, 40, 48), 1500
+    planes = [ws.Plane(nw, nt, inputs.response("bipolar" if i < 2 else "unipolar"), plane_id=i, fp64=True)
+              for i, nw in enumerate(wires)]
+    counts = [200, 0, 900]
+    host = [[inputs.uniform_depos(n, nw, 500 + 10 * e + p, nticks=nt) for p, nw in enumerate(wires)]
+            for e, n in enumerate(counts)]
+    events = [[ws.DeviceDepos.from_plane_depos(d) for d in row] for row in host]
+    params = ws.Params(fluctuate=2, p_survive=0.7, seed=31337, event_id=2)
+    outs = ws.Batch(planes, events, params, units_per_wave=2).run()
+    torch.cuda.synchronize()
+    for e in range(len(counts)):
+        for p, pl in enumerate(planes):
+            pe = ws.Params(**{**params.__dict__, "event_id": params.event_id + e})
+            ref = to_np(pl.simulate(events[e][p], pe))
+            got = to_np(outs[e * 3 + p])
+            assert np.linalg.norm(got - ref) <= 1e-6 * max(np.linalg.norm(ref), 1.0), (e, p)
+            # FP64 path: same integers, double transforms
+            pe64 = ws.Params(**{**pe.__dict__, "precision": ws.WS_PREC_FP64})
+            r64 = to_np(pl.simulate(events[e][p], pe64))
+            assert np.linalg.norm(r64 - ref) <= 1e-5 * max(np.linalg.norm(ref), 1.0)
