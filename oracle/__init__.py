@@ -350,6 +350,43 @@ def noise(nwires: int, nticks: int, L: int, amp, coh=None, group: int = 1, **kw)
     return np.ascontiguousarray(np.fft.irfft(spec, n=L, axis=1)[:, :nticks])
 
 
+# ------------------------------------------------------------ impact sampling
+def raster_scatter_impacts(q, x_mm, t_us, nwires: int, nticks: int, impacts: int, *,
+                           pitch_mm: float = PITCH_MM, **kw) -> np.ndarray:
+    """The raster with the pitch axis binned at pitch/impacts: fine row
+    f = w * impacts + i holds the charge of wire w at sub-pitch position i
+    (the position's bin covers [(w + i/I) pitch, (w + (i+1)/I) pitch)).
+    Same truncation, weights and fluctuation as ``raster_scatter`` on that
+    finer grid.  Pinned by the fine rows of a wire summing to the wire's
+    coarse bin (expected-value mode) and by the point charge landing in its
+    sub-position's rows."""
+    return raster_scatter(q, x_mm, t_us, nwires * impacts, nticks, pitch_mm=pitch_mm / impacts, **kw)
+
+
+def convolve_impacts(S_fine, R, wire_center: int, circular: bool = False) -> np.ndarray:
+    """Eq. 1 with a response that depends on the charge's position inside
+    the pitch: M = sum_i R[i] (*) S_i with S_i[w] = S_fine[w * I + i]
+    (R: impacts x K_w x K_t), each term by ``convolve_fft``.  Pinned by the
+    direct sum of Eq. 1 per impact and by equal responses reducing it to
+    the plain convolution of the summed grid."""
+    R = np.asarray(R, dtype=np.float64)
+    I = R.shape[0]
+    S_fine = np.asarray(S_fine, dtype=np.float64)
+    nw = S_fine.shape[0] // I
+    M = np.zeros((nw, S_fine.shape[1]))
+    for i in range(I):
+        M += convolve_fft(S_fine[i::I], R[i], wire_center, circular)
+    return M
+
+
+def simulate_impacts(q, x_mm, t_us, nwires: int, nticks: int, R, wire_center: int = 10, *,
+                     circular: bool = False, **kw) -> np.ndarray:
+    """The hot path with sub-pitch impact positions (R: impacts x K_w x K_t)."""
+    I = np.asarray(R).shape[0]
+    S = raster_scatter_impacts(q, x_mm, t_us, nwires, nticks, I, **kw)
+    return convolve_impacts(S, R, wire_center, circular)
+
+
 # ------------------------------------------------------------------ adjoint
 def convolve_adjoint(G, R, wire_center: int, circular: bool = False) -> np.ndarray:
     """Adjoint of ``convolve_fft`` applied to G = dL/dM: dL/dS[w][t] =

@@ -194,6 +194,30 @@ def response(kind: str = "bipolar", nwires: int = RESP_NWIRES, nticks: int = RES
     return _f32(np.outer(g, h))
 
 
+def impact_response(kind: str = "bipolar", impacts: int = 10, nwires: int = RESP_NWIRES,
+                    nticks: int = RESP_NTICKS, wire_center: int = RESP_WIRE_CENTER, wire_sigma: float = 1.5,
+                    tick_peak: float = 100.0, tick_sigma: float = 10.0) -> np.ndarray:
+    """Synthetic response at ``impacts`` positions inside the pitch,
+    R[i][wire_offset + center][tick], float32: as ``response`` with the wire
+    factor's centre moved to the charge's sub-pitch position,
+    exp(-(d + 1/2 - (i + 1/2)/I)^2 / (2 sw^2)) (a charge near the pitch's low
+    edge induces more on the lower neighbour)."""
+    d = np.arange(nwires, dtype=np.float64) - wire_center
+    u = (np.arange(nticks, dtype=np.float64) - tick_peak) / tick_sigma
+    if kind == "bipolar":
+        h = -u * np.exp(-0.5 * u * u)
+    elif kind == "unipolar":
+        h = np.exp(-0.5 * u * u)
+    else:
+        raise ValueError(f"unknown response kind {kind!r}")
+    out = np.zeros((impacts, nwires, nticks))
+    for i in range(impacts):
+        shift = 0.5 - (i + 0.5) / impacts
+        g = np.exp(-(d + shift) ** 2 / (2.0 * wire_sigma ** 2))
+        out[i] = np.outer(g, h)
+    return _f32(out)
+
+
 def noise_amplitudes(L: int, kind: str = "incoherent", peak: float = 2.0e5, peak_frac: float = 0.1,
                      floor: float = 0.1) -> np.ndarray:
     """Synthetic noise amplitude spectrum on the L/2 + 1 half-spectrum bins of
