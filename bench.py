@@ -403,6 +403,46 @@ def multinomial_leg(wiresim, dev, stream, flush, steps: int, units_per_wave: int
             "raster_ms_per_launch": rms / max(rn, 1)}
 
 
+def impacts_leg(wiresim, dev, stream, flush, steps: int, impacts: int = 10):
+    """The benchmark event on planes whose response depends on the charge's
+    position inside the pitch (10 sub-pitch positions, synthetic slices):
+    the raster bins the pitch axis at pitch/10 and the forward transform
+    runs over 10x the rows; one ws_simulate per plane."""
+    import torch
+    w = make_workload("three_planes", 0)
+    kinds = ["bipolar", "bipolar", "unipolar"]
+    planes = [wiresim.Plane(sp.nwires, sp.nticks, inputs.impact_response(kinds[i], impacts=impacts),
+                            plane_id=sp.plane_id, device=dev) for i, sp in enumerate(w.planes)]
+    depos = [wiresim.DeviceDepos.from_plane_depos(d, device=dev) for d in w.events[0]]
+    params = wiresim.Params(fluctuate=w.fluctuate, p_survive=w.p_survive, seed=w.seed)
+    outs = [torch.empty((sp.nwires, sp.nticks), dtype=torch.float32, device=dev) for sp in w.planes]
+
+    def step():
+        for pl, d, o in zip(planes, depos, outs):
+            pl.simulate(d, params, out=o, stream=stream)
+
+    for _ in range(3):
+        step()
+    torch.cuda.synchronize(dev)
+    ms = sorted(_time_steps(step, steps, stream, flush))[steps // 2]
+    for pl in planes:
+        pl.trace(16 * steps + 16)
+    for _ in range(steps):
+        flush.zero_()
+        step()
+    torch.cuda.synchronize(dev)
+    kern = {}
+    for pl in planes:
+        for name, (n, t) in pl.trace_read().items():
+            kern[name] = kern.get(name, 0.0) + t / steps
+        pl.trace(0)
+        pl.close()
+    ndp = sum(d.n for d in w.events[0])
+    return {"workload": w.name + f", {impacts} sub-pitch response positions per plane", "ms_per_step": ms,
+            "value": ndp / (ms * 1e-3), "unit": UNIT, "kernels_ms_per_step": kern,
+            "path": "ws_simulate per plane (fine grid of nwires*10 rows, per-impact wire convolution)"}
+
+
 def adjoint_leg(wiresim, dev, stream, flush, steps: int):
     """Forward and adjoint (ws_simulate_backward: gradients for q, x, t of
     every depo, D_L, D_T and the response) of one 960 x 6000 plane with
@@ -668,11 +708,13 @@ def run_gpu(args):
     adjoint = None
     noise = None
     multinomial = None
+    impacts = None
     if rank == 0 and world == 1 and not args.no_batched_workload:
         batched = batched_workload_comparison(wiresim, dev, stream, flush, max(3, min(args.steps, 10)))
         adjoint = adjoint_leg(wiresim, dev, stream, flush, max(5, min(args.steps, 50)))
         noise = noise_leg(wiresim, dev, stream, flush, max(5, min(args.steps, 200)), upw_event,
                           sorted(graph_ms)[len(graph_ms) // 2])
+        impacts = impacts_leg(wiresim, dev, stream, flush, max(5, min(args.steps, 50)))
         multinomial = multinomial_leg(wiresim, dev, stream, flush, max(5, min(args.steps, 200)), upw_event,
                                       sorted(graph_ms)[len(graph_ms) // 2])
     if rank != 0:
@@ -718,6 +760,7 @@ def run_gpu(args):
         "adjoint": adjoint,
         "noise": noise,
         "multinomial": multinomial,
+        "impacts": impacts,
     }
     print(json.dumps(line), flush=True)
     if dist is not None:

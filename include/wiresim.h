@@ -88,6 +88,18 @@ typedef struct {
     int32_t fp64;             /* nonzero: also hold the FP64 tables and
                                  buffers that WS_PREC_FP64 needs (about
                                  2x the workspace)                          */
+    int32_t impacts;          /* 0 or 1: one response for the whole pitch.
+                                 I = 2 .. 32: the response depends on where
+                                 in the pitch the charge is (I sub-pitch
+                                 positions; the paper's WCT field responses
+                                 are of this kind, Sec. 2.1): the response
+                                 array is I x K_w x K_t (slice i for charge
+                                 at [(w + i/I), (w + (i+1)/I)) pitches), the
+                                 raster bins the pitch axis at pitch/I into
+                                 a fine grid of nwires*I rows (fine row
+                                 w*I + i), and M = sum_i R_i (*) S_i.  FP32
+                                 only; ws_simulate_batch and the adjoint
+                                 reject such planes                         */
 } ws_plane_desc;
 
 /* Depos of one event as seen by one plane: structure of arrays of float32
@@ -224,7 +236,9 @@ ws_status ws_scatter(ws_plane* plane, const ws_patches* patches, float* grid_dev
 /* Eq. 2: out = IFFT(R_hat * FFT(grid)), i.e. Eq. 1's sum of
  * R[d + c][j] * S[w - d][t - j] with S = 0 outside the grid (linear) or
  * indices wrapping (circular).  grid_dev and out_dev are nwires x nticks;
- * they may be the same buffer.  Uses the plane's workspace. */
+ * they may be the same buffer.  Uses the plane's workspace.  On a plane
+ * with impacts I > 1, grid_dev is the fine grid (nwires*I x nticks, row
+ * w*I + i), out_dev is nwires x nticks and they must not overlap. */
 ws_status ws_convolve(ws_plane* plane, const float* grid_dev, float* out_dev, void* stream);
 
 /* The whole hot path for one plane and one event: clear out_dev, raster +
@@ -252,7 +266,8 @@ ws_status ws_simulate(ws_plane* plane, const ws_depos* depos, const ws_params* p
  *     it: order them on one stream.
  *   - Allocates nothing (no cudaMalloc/cudaFree, no allocating library
  *     call).  desc, grid_dev and out_dev as for ws_plane_create and
- *     ws_convolve (grid and out may be the same buffer). */
+ *     ws_convolve (grid and out may be the same buffer); planes with
+ *     impacts > 1 are rejected with WS_ERR_UNSUPPORTED_SIZE. */
 ws_status ws_convolve_noalloc(const ws_plane_desc* desc, const float* response_dev,
                               const float* grid_dev, float* out_dev, void* stream);
 

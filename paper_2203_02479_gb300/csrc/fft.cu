@@ -859,6 +859,73 @@ wire_conv_kernel(const __grid_constant__ ConvUnits U, int nfreq, int64_t stride,
     }
 }
 
+// Wire convolution over sub-pitch impact positions: a CTA owns 128 columns
+// x B output wires; for each impact i it stages the B + K - 1 input wires'
+// rows of that impact (fine rows wire * impacts + i) in shared memory and
+// adds that impact's K-tap sum (Karatsuba taps in registers) into the same
+// accumulators.
+template <int K, int B>
+__global__ void __launch_bounds__(kConvCols)
+wire_conv_impacts_kernel(const float2* __restrict__ X, float2* __restrict__ Y, const float2* __restrict__ Rt,
+                         int nwires, int impacts, int nfreq, int64_t stride, int kw, int center, int circular) {
+    constexpr int ROWS = B + K - 1;
+    __shared__ __align__(16) float2 tile[ROWS][kConvCols];
+    const int k0 = blockIdx.x * kConvCols;
+    const int w0 = blockIdx.y * B;
+    const int ibase = w0 + center - (K - 1);
+    const int k = k0 + threadIdx.x;
+    float k1[B], k2[B], k3[B];
+#pragma unroll
+    for (int b = 0; b < B; ++b) k1[b] = k2[b] = k3[b] = 0.f;
+    for (int im = 0; im < impacts; ++im) {
+        __syncthreads();   // the previous impact's tile is read
+        for (int e = threadIdx.x; e < ROWS * (kConvCols / 2); e += kConvCols) {
+            const int uu = e / (kConvCols / 2), c2 = e - uu * (kConvCols / 2);
+            int wi = ibase + uu;
+            const int kk = k0 + 2 * c2;
+            bool ok = kk < stride;
+            if (circular) {
+                wi %= nwires;
+                if (wi < 0) wi += nwires;
+            } else {
+                ok = ok && wi >= 0 && wi < nwires;
+            }
+            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (ok) v = __ldg(reinterpret_cast<const float4*>(X + ((int64_t)wi * impacts + im) * stride + kk));
+            reinterpret_cast<float4*>(&tile[uu][0])[c2] = v;
+        }
+        __syncthreads();
+        if (k < nfreq) {
+            float cc[K], cm[K], cp[K];
+#pragma unroll
+            for (int r = 0; r < K; ++r) {
+                const float2 t = r < kw ? __ldg(&Rt[((int64_t)im * kw + r) * stride + k]) : make_float2(0.f, 0.f);
+                cc[r] = t.x;
+                cm[r] = t.y - t.x;
+                cp[r] = t.x + t.y;
+            }
+#pragma unroll
+            for (int uu = 0; uu < ROWS; ++uu) {
+                const float2 x = tile[uu][threadIdx.x];
+                const float sab = x.x + x.y;
+#pragma unroll
+                for (int b = 0; b < B; ++b) {
+                    const int r = b + K - 1 - uu;
+                    if (r >= 0 && r < K) {
+                        k1[b] = fmaf(cc[r], sab, k1[b]);
+                        k2[b] = fmaf(cm[r], x.x, k2[b]);
+                        k3[b] = fmaf(cp[r], x.y, k3[b]);
+                    }
+                }
+            }
+        }
+    }
+    if (k >= nfreq) return;
+#pragma unroll
+    for (int b = 0; b < B; ++b)
+        if (w0 + b < nwires) Y[(int64_t)(w0 + b) * stride + k] = make_float2(k1[b] - k3[b], k1[b] + k2[b]);
+}
+
 template <int B, bool KS, typename S>
 void launch_wc(const ConvBatch& cb, int nfreq, int64_t stride, int kw, int center, int circular, cudaStream_t s) {
     constexpr int K = kMaxRespWires;
@@ -1180,6 +1247,16 @@ cudaError_t launch_wire_conv(const float2* X, float2* Y, const float2* Rt, int n
     if (nwires <= 0 || nfreq <= 0) return cudaSuccess;
     return launch_wire_conv_batch(one_conv(X, Y, Rt, nwires), nfreq, stride, kw, center, circular, s, variant,
                                   status);
+}
+
+cudaError_t launch_wire_conv_impacts(const float2* X, float2* Y, const float2* Rt, int nwires, int impacts,
+                                     int nfreq, int64_t stride, int kw, int center, int circular, cudaStream_t s) {
+    if (nwires <= 0 || nfreq <= 0) return cudaSuccess;
+    constexpr int B = 16;
+    dim3 grid((nfreq + kConvCols - 1) / kConvCols, (nwires + B - 1) / B);
+    wire_conv_impacts_kernel<kMaxRespWires, B><<<grid, kConvCols, 0, s>>>(X, Y, Rt, nwires, impacts, nfreq, stride, kw,
+                                                                          center, circular);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_add_noise(const NoiseBatch& nb, int nfreq, int L, int64_t stride, cudaStream_t s) {

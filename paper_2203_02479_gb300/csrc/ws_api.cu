@@ -112,6 +112,8 @@ struct Layout {
     ws::FftPlan plan;
     int nfreq, fstride;
     size_t off_status, off_tw, off_rt, off_x, off_y, off_scan, off_large, off_radj, off_racc, off_grid2, off_noise;
+    size_t off_fine;
+    int impacts;
     size_t off_tw64, off_rt64, off_x64, off_y64, off_g64, total;
 };
 
@@ -123,6 +125,10 @@ ws_status plan_layout(const ws_plane_desc* d, Layout* lay) {
         (d->conv_mode != WS_CONV_LINEAR && d->conv_mode != WS_CONV_CIRCULAR) || d->fft_len_tick < 0)
         return WS_ERR_INVALID_ARG;
     if (d->resp_nwires > ws::kMaxRespWires) return WS_ERR_UNSUPPORTED_SIZE;
+    if (d->impacts < 0 || d->impacts > ws::kMaxImpacts) return WS_ERR_INVALID_ARG;
+    const int I = d->impacts > 1 ? d->impacts : 1;
+    if (I > 1 && d->fp64) return WS_ERR_UNSUPPORTED_SIZE;   // impact planes run FP32
+    lay->impacts = I;
     int L;
     if (d->fft_len_tick > 0) {
         L = d->fft_len_tick;
@@ -143,8 +149,8 @@ ws_status plan_layout(const ws_plane_desc* d, Layout* lay) {
     size_t o = 0;
     lay->off_status = o; o = align256(o + 256);
     lay->off_tw = o; o = align256(o + sizeof(float2) * (size_t)L);
-    lay->off_rt = o; o = align256(o + sizeof(float2) * (size_t)d->resp_nwires * lay->fstride);
-    lay->off_x = o; o = align256(o + sizeof(float2) * (size_t)d->nwires * lay->fstride);
+    lay->off_rt = o; o = align256(o + sizeof(float2) * (size_t)I * d->resp_nwires * lay->fstride);
+    lay->off_x = o; o = align256(o + sizeof(float2) * (size_t)I * d->nwires * lay->fstride);
     lay->off_y = o; o = align256(o + sizeof(float2) * (size_t)d->nwires * lay->fstride);
     lay->off_scan = o; o = align256(o + sizeof(int64_t) * (size_t)ws::kScanScratch);
     lay->off_large = o; o = align256(o + sizeof(long long) * (size_t)ws::kLargeListCap);
@@ -152,6 +158,8 @@ ws_status plan_layout(const ws_plane_desc* d, Layout* lay) {
     lay->off_racc = o; o = align256(o + sizeof(float2) * (size_t)d->resp_nwires * lay->fstride);
     lay->off_grid2 = o; o = align256(o + sizeof(float) * (size_t)d->nwires * d->nticks);
     lay->off_noise = o; o = align256(o + 2 * sizeof(float) * (size_t)lay->fstride);
+    lay->off_fine = 0;
+    if (I > 1) { lay->off_fine = o; o = align256(o + sizeof(float) * (size_t)I * d->nwires * d->nticks); }
     lay->off_tw64 = lay->off_rt64 = lay->off_x64 = lay->off_y64 = lay->off_g64 = 0;
     if (d->fp64) {
         lay->off_tw64 = o; o = align256(o + sizeof(double2) * (size_t)L);
@@ -193,8 +201,9 @@ ws::RasterArgs raster_args(const ws_plane* pl, const ws_depos* d, const ws_param
     a.q = d->q; a.x = d->x_mm; a.t = d->t_us;
     a.sig_t = d->sigma_t_us; a.sig_x = d->sigma_x_mm;
     a.n = d->n;
-    a.nwires = pl->desc.nwires; a.nticks = pl->desc.nticks;
-    a.pitch = (float)pl->desc.pitch_mm; a.tick = (float)pl->desc.tick_us;
+    // impact planes bin the pitch axis at pitch / I (fine row w * I + i)
+    a.nwires = pl->desc.nwires * pl->impacts; a.nticks = pl->desc.nticks;
+    a.pitch = (float)(pl->desc.pitch_mm / pl->impacts); a.tick = (float)pl->desc.tick_us;
     a.nsig = (float)pl->desc.nsigma;
     a.two_DL = (float)(2.0 * p->DL_mm2_us);
     a.two_DT = (float)(2.0 * p->DT_mm2_us);
@@ -223,7 +232,7 @@ ws::RasterArgs raster_args(const ws_plane* pl, const ws_depos* d, const ws_param
     a.two_DL64 = 2.0 * p->DL_mm2_us;
     a.two_DT64 = 2.0 * p->DT_mm2_us;
     a.v64 = p->v_mm_us;
-    a.pitch64 = pl->desc.pitch_mm;
+    a.pitch64 = pl->desc.pitch_mm / pl->impacts;
     a.tick64 = pl->desc.tick_us;
     a.nsig64 = pl->desc.nsigma;
     a.p64 = p->p_survive;
@@ -263,11 +272,18 @@ ws_status add_plane_noise(ws_plane* pl, const ws_params* p, void* Y, bool fp64, 
 ws_status convolve_impl(ws_plane* pl, const float* grid, float* out, cudaStream_t s,
                         const ws_params* noise_params = nullptr) {
     const ws_plane_desc& d = pl->desc;
-    WS_LAUNCH(pl, K_FWD, s, ws::launch_fwd_rows(pl->plan, pl->tw, grid, d.nwires, d.nticks, d.nticks, pl->X,
-                                                pl->fstride, pl->nfreq, 1.0f, s));
-    WS_LAUNCH(pl, K_WCONV, s, ws::launch_wire_conv(pl->X, pl->Y, pl->Rt, d.nwires, pl->nfreq, pl->fstride,
-                                                   d.resp_nwires, d.resp_wire_center,
-                                                   d.conv_mode == WS_CONV_CIRCULAR, s, pl->wconv_variant, pl->status));
+    WS_LAUNCH(pl, K_FWD, s, ws::launch_fwd_rows(pl->plan, pl->tw, grid, d.nwires * pl->impacts, d.nticks, d.nticks,
+                                                pl->X, pl->fstride, pl->nfreq, 1.0f, s));
+    if (pl->impacts > 1) {
+        WS_LAUNCH(pl, K_WCONV, s, ws::launch_wire_conv_impacts(pl->X, pl->Y, pl->Rt, d.nwires, pl->impacts, pl->nfreq,
+                                                               pl->fstride, d.resp_nwires, d.resp_wire_center,
+                                                               d.conv_mode == WS_CONV_CIRCULAR, s));
+    } else {
+        WS_LAUNCH(pl, K_WCONV, s, ws::launch_wire_conv(pl->X, pl->Y, pl->Rt, d.nwires, pl->nfreq, pl->fstride,
+                                                       d.resp_nwires, d.resp_wire_center,
+                                                       d.conv_mode == WS_CONV_CIRCULAR, s, pl->wconv_variant,
+                                                       pl->status));
+    }
     if (noise_params) {
         const ws_status st = add_plane_noise(pl, noise_params, pl->Y, false, s);
         if (st != WS_OK) return st;
@@ -354,6 +370,8 @@ ws_status ws_plane_create(const ws_plane_desc* desc, const float* response_dev, 
     pl->Racc = (float2*)(base + lay.off_racc);
     pl->grid2 = (float*)(base + lay.off_grid2);
     pl->noise_amp = (float*)(base + lay.off_noise);
+    pl->impacts = lay.impacts;
+    pl->fine = lay.impacts > 1 ? (float*)(base + lay.off_fine) : nullptr;
     pl->noise_mode = 0;
     pl->noise_group = 1;
     pl->fp64 = desc->fp64 != 0;
@@ -368,10 +386,10 @@ ws_status ws_plane_create(const ws_plane_desc* desc, const float* response_dev, 
     // Response spectrum: per response row, the tick transform scaled by 1/L so
     // that the inverse transform needs no scaling.
     if (e == cudaSuccess)
-        e = ws::launch_fwd_rows(lay.plan, pl->tw, response_dev, desc->resp_nwires, desc->resp_nticks,
+        e = ws::launch_fwd_rows(lay.plan, pl->tw, response_dev, lay.impacts * desc->resp_nwires, desc->resp_nticks,
                                 desc->resp_nticks, pl->Rt, lay.fstride, lay.nfreq, 1.0f / (float)lay.plan.L, s);
     if (e == cudaSuccess)
-        e = ws::launch_adj_coeffs(pl->Rt, pl->Radj, desc->resp_nwires, lay.fstride, lay.nfreq, s);
+        e = ws::launch_adj_coeffs(pl->Rt, pl->Radj, desc->resp_nwires, lay.fstride, lay.nfreq, s);   // slice 0
     if (e == cudaSuccess && pl->fp64) e = ws::launch_twiddles64(pl->tw64, lay.plan, s);
     if (e == cudaSuccess && pl->fp64)
         e = ws::launch_fwd_rows64(lay.plan, pl->tw64, response_dev, false, desc->resp_nwires, desc->resp_nticks,
@@ -383,7 +401,7 @@ ws_status ws_plane_create(const ws_plane_desc* desc, const float* response_dev, 
     // fastest variant is kept.
     pl->wconv_variant = 0;
     if (e == cudaSuccess) e = cudaMemsetAsync(pl->X, 0, sizeof(float2) * (size_t)desc->nwires * lay.fstride, s);
-    if (e == cudaSuccess) {
+    if (e == cudaSuccess && lay.impacts == 1) {   // impact planes have one wire-convolution kernel
         cudaEvent_t t0 = nullptr, t1 = nullptr;
         e = cudaEventCreate(&t0);
         if (e == cudaSuccess) e = cudaEventCreate(&t1);
@@ -552,13 +570,21 @@ ws_status ws_scatter(ws_plane* pl, const ws_patches* patches, float* grid_dev, v
         return WS_ERR_INVALID_ARG;
     if (!aligned(grid_dev, 4)) return WS_ERR_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)stream;
-    WS_LAUNCH(pl, K_SCATTER, s, ws::launch_scatter_patches(*patches, grid_dev, pl->desc.nwires, pl->desc.nticks, s));
+    WS_LAUNCH(pl, K_SCATTER, s, ws::launch_scatter_patches(*patches, grid_dev, pl->desc.nwires * pl->impacts,
+                                                          pl->desc.nticks, s));
     return WS_OK;
 }
 
 ws_status ws_convolve(ws_plane* pl, const float* grid_dev, float* out_dev, void* stream) {
     if (!pl || !grid_dev || !out_dev) return WS_ERR_INVALID_ARG;
     if (!aligned(grid_dev, 4) || !aligned(out_dev, 4)) return WS_ERR_INVALID_ARG;
+    if (pl->impacts > 1) {   // fine input and coarse output must not overlap
+        const char* g0 = (const char*)grid_dev;
+        const char* g1 = g0 + sizeof(float) * (size_t)pl->impacts * pl->desc.nwires * pl->desc.nticks;
+        const char* o0 = (const char*)out_dev;
+        const char* o1 = o0 + sizeof(float) * (size_t)pl->desc.nwires * pl->desc.nticks;
+        if (o0 < g1 && g0 < o1) return WS_ERR_INVALID_ARG;
+    }
     return convolve_impl(pl, grid_dev, out_dev, (cudaStream_t)stream);
 }
 
@@ -572,6 +598,12 @@ ws_status ws_simulate(ws_plane* pl, const ws_depos* depos, const ws_params* para
     const ws_plane_desc& d = pl->desc;
     const size_t grid_bytes = sizeof(float) * (size_t)d.nwires * d.nticks;
     ws::RasterArgs a = raster_args(pl, depos, params);
+    if (pl->impacts > 1) {
+        if (params->precision != WS_PREC_FP32) return WS_ERR_UNSUPPORTED_SIZE;
+        WS_LAUNCH(pl, K_MEMSET, s, cudaMemsetAsync(pl->fine, 0, grid_bytes * pl->impacts, s));
+        WS_LAUNCH(pl, K_RASTER_SCATTER, s, ws::launch_raster_scatter(a, pl->fine, pl->large, s));
+        return convolve_impl(pl, pl->fine, out_dev, s, params);
+    }
     if (params->precision == WS_PREC_FP64) {
         if (!pl->fp64) return WS_ERR_WORKSPACE;
         // FP64 throughout: double grid, double transforms, float output.
@@ -634,8 +666,8 @@ ws_status ws_plane_set_response(ws_plane* pl, const float* response_dev, void* s
     if (!pl || !response_dev || !aligned(response_dev, 4)) return WS_ERR_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     const ws_plane_desc& d = pl->desc;
-    WS_CUDA(ws::launch_fwd_rows(pl->plan, pl->tw, response_dev, d.resp_nwires, d.resp_nticks, d.resp_nticks, pl->Rt,
-                                pl->fstride, pl->nfreq, 1.0f / (float)pl->plan.L, s));
+    WS_CUDA(ws::launch_fwd_rows(pl->plan, pl->tw, response_dev, pl->impacts * d.resp_nwires, d.resp_nticks,
+                                d.resp_nticks, pl->Rt, pl->fstride, pl->nfreq, 1.0f / (float)pl->plan.L, s));
     WS_CUDA(ws::launch_adj_coeffs(pl->Rt, pl->Radj, d.resp_nwires, pl->fstride, pl->nfreq, s));
     if (pl->fp64)
         WS_CUDA(ws::launch_fwd_rows64(pl->plan, pl->tw64, response_dev, false, d.resp_nwires, d.resp_nticks,
@@ -651,6 +683,7 @@ ws_status ws_simulate_backward(ws_plane* pl, const ws_depos* depos, const ws_par
     if (st == WS_OK) st = check_params(params);
     if (st != WS_OK) return st;
     if (params->fluctuate) return WS_ERR_INVALID_ARG;  // the adjoint is of the expected-value path
+    if (pl->impacts > 1) return WS_ERR_UNSUPPORTED_SIZE;
     cudaStream_t s = (cudaStream_t)stream;
     const ws_plane_desc& d = pl->desc;
     const int circ = d.conv_mode == WS_CONV_CIRCULAR;
@@ -704,6 +737,7 @@ ws_status batch_layout(ws_plane* const* planes, int nplanes, int units_per_wave,
     for (int i = 0; i < nplanes; ++i) {
         const ws_plane* p = planes[i];
         if (!p) return WS_ERR_INVALID_ARG;
+        if (p->impacts > 1) return WS_ERR_UNSUPPORTED_SIZE;
         // one launch per stage needs one transform plan and one response shape
         if (p->plan.L != p0->plan.L || p->plan.npass != p0->plan.npass || p->fstride != p0->fstride ||
             p->desc.nticks != p0->desc.nticks || p->desc.resp_nwires != p0->desc.resp_nwires ||

@@ -12,6 +12,7 @@ namespace ws {
 constexpr int kMaxPasses = 16;
 constexpr int kMaxFftLen = 14336;   // two complex64 buffers of this length fit in shared memory
 constexpr int kMaxRespWires = 21;   // wire taps of the register-blocked wire convolution
+constexpr int kMaxImpacts = 32;     // sub-pitch response positions of a plane
 constexpr int64_t kScanScratch = 65536;
 
 // Mixed-radix Stockham plan for one complex transform length.
@@ -187,6 +188,11 @@ constexpr int kWireConvVariants = 10;
 cudaError_t launch_wire_conv(const float2* X, float2* Y, const float2* Rt, int nwires,
                              int nfreq, int64_t stride, int kw, int center, int circular,
                              cudaStream_t s, int variant = 0, uint32_t* status = nullptr);
+// Wire convolution with sub-pitch impact positions: Y[w][k] = sum_i sum_r
+// Rt[i*kw + r][k] * X[(w + center - r)*impacts + i][k] (X has nwires*impacts
+// rows, zero or wrapped outside the wires).
+cudaError_t launch_wire_conv_impacts(const float2* X, float2* Y, const float2* Rt, int nwires, int impacts,
+                                     int nfreq, int64_t stride, int kw, int center, int circular, cudaStream_t s);
 // TMA-fed wire convolution (wconv_tma.cu), variant 0..5 = 4..9 above.
 bool tma_available();
 cudaError_t launch_bounded_wait_selftest(uint32_t* status, int iters, unsigned long long* cycles, cudaStream_t s);
@@ -271,6 +277,8 @@ struct ws_plane {
     ws::LargeList large;  // hand-over list of large patches
     float2* Radj;       // K_w x fstride flipped conjugate taps (adjoint)
     float2* Racc;       // K_w x fstride response-gradient spectra
+    int impacts;        // sub-pitch response positions (1: none)
+    float* fine;        // nwires*impacts x nticks fine grid (impacts > 1)
     float* noise_amp;   // fstride noise amplitudes (incoherent), then fstride coherent
     int noise_mode;     // 0 none, 1 incoherent, 2 incoherent + coherent
     int noise_group;    // wires per coherent group

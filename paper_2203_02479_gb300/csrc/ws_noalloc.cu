@@ -58,6 +58,7 @@ extern "C" ws_status ws_convolve_noalloc(const ws_plane_desc* desc, const float*
                                          const float* grid_dev, float* out_dev, void* stream) {
     if (!desc || !response_dev || !grid_dev || !out_dev) return WS_ERR_INVALID_ARG;
     if (((uintptr_t)response_dev | (uintptr_t)grid_dev | (uintptr_t)out_dev) & 3) return WS_ERR_INVALID_ARG;
+    if (desc->impacts > 1) return WS_ERR_UNSUPPORTED_SIZE;   // one response for the whole pitch only
     ws::FftPlan plan;
     int nfreq = 0, fstride = 0;
     ws_status st = ws::conv_plan(desc, &plan, &nfreq, &fstride);

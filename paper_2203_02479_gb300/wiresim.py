@@ -51,7 +51,7 @@ class WsPlaneDesc(ctypes.Structure):
                 ("resp_nwires", ctypes.c_int32), ("resp_nticks", ctypes.c_int32),
                 ("resp_wire_center", ctypes.c_int32), ("conv_mode", ctypes.c_int32),
                 ("fft_len_tick", ctypes.c_int32), ("nsigma", ctypes.c_double),
-                ("plane_id", ctypes.c_int32), ("fp64", ctypes.c_int32)]
+                ("plane_id", ctypes.c_int32), ("fp64", ctypes.c_int32), ("impacts", ctypes.c_int32)]
 
 
 class WsDepos(ctypes.Structure):
@@ -309,15 +309,18 @@ class Plane:
                  tick_us: float = 0.5, wire_center: int = 10, circular: bool = False,
                  fft_len_tick: int = 0, nsigma: float = 3.0, plane_id: int = 0, fp64: bool = False,
                  device="cuda", stream=None):
+        """response: K_w x K_t, or impacts x K_w x K_t for a response that
+        depends on the charge's sub-pitch position (impact planes)."""
         torch = _torch()
         resp = response
         if isinstance(resp, np.ndarray):
             resp = torch.from_numpy(np.ascontiguousarray(resp, dtype=np.float32))
         self.response = resp.to(device=device, dtype=torch.float32).contiguous()
-        kw, kt = int(self.response.shape[0]), int(self.response.shape[1])
+        self.impacts = int(self.response.shape[0]) if self.response.dim() == 3 else 1
+        kw, kt = int(self.response.shape[-2]), int(self.response.shape[-1])
         self.desc = WsPlaneDesc(nwires, nticks, pitch_mm, tick_us, kw, kt, wire_center,
                                 WS_CONV_CIRCULAR if circular else WS_CONV_LINEAR, fft_len_tick,
-                                nsigma, plane_id, int(bool(fp64)))
+                                nsigma, plane_id, int(bool(fp64)), self.impacts if self.impacts > 1 else 0)
         self.nwires, self.nticks = nwires, nticks
         nbytes = ws_plane_workspace_bytes(self.desc)
         self.workspace = torch.empty(nbytes + 256, dtype=torch.uint8, device=device)
@@ -340,8 +343,10 @@ class Plane:
             pass
 
     def new_grid(self):
+        """A zeroed grid for scatter / convolve: nwires x nticks, or the fine
+        grid nwires*impacts x nticks of an impact plane."""
         torch = _torch()
-        return torch.zeros((self.nwires, self.nticks), dtype=torch.float32, device=self.device)
+        return torch.zeros((self.nwires * self.impacts, self.nticks), dtype=torch.float32, device=self.device)
 
     def simulate(self, depos: DeviceDepos, params: Params, out=None, stream=None):
         if out is None:
@@ -351,7 +356,7 @@ class Plane:
 
     def convolve(self, grid, out=None, stream=None):
         if out is None:
-            out = _torch().empty_like(grid)
+            out = _torch().empty((self.nwires, self.nticks), dtype=_torch().float32, device=self.device)
         ws_convolve(self.handle, _ptr(grid), _ptr(out), _stream_handle(stream))
         return out
 
