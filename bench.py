@@ -690,8 +690,30 @@ def run_gpu(args):
         _barrier(dist)
         e_ms = _max_over_ranks(dist, s0.elapsed_time(s1), dev)
         e_total = _sum_over_ranks(dist, float(ndepo_planes * e_steps), dev)
+        # the host link's own rate: the step's device-to-host copies alone,
+        # back to back (the direction that bounds the pipelined step, whose
+        # kernels and host-to-device copies hide behind it)
+        def d2h_only():
+            _, _, b2, host_out, st = pipes[0]
+            with torch.cuda.stream(st):
+                for o, oh in zip(b2.outs, host_out):
+                    oh.copy_(o, non_blocking=True)
+
+        d2h_only()
+        torch.cuda.synchronize(dev)
+        c0 = torch.cuda.Event(enable_timing=True)
+        c1 = torch.cuda.Event(enable_timing=True)
+        c0.record(pipes[0][4])
+        for _ in range(10):
+            d2h_only()
+        c1.record(pipes[0][4])
+        torch.cuda.synchronize(dev)
+        copy_ms = c0.elapsed_time(c1) / 10
         e2e = {"value": e_total / (e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h, "ms_per_step": e_ms / e_steps,
+               "d2h_alone_ms_per_step": copy_ms,
+               "d2h_gbs_measured": d2h / (copy_ms * 1e-3) / 1e9,
+               "frac_of_d2h_bound": copy_ms / (e_ms / e_steps),
                "path": "Batch.replay (CUDA graph) per step; pinned host copies in and out on the step's stream; "
                        "two alternating pipelines overlap one step's copies with the other's kernels"}
         two_event = {"ms_per_step": overlap_ms, "value": ndepo_planes / (overlap_ms * 1e-3),
