@@ -259,8 +259,11 @@ PHILOX_MULS = 40    # 32-bit multiplies per Philox4x32-10 block: 10 rounds x 2 p
 # one ncu capture of the three-plane step with one launch per stage over the
 # three planes (the configuration of the per-kernel table), as of the current
 # kernels.
+# DRAM bytes per launch (read + write) from one ncu --set full capture of the
+# step's kernels (one launch per stage over the three planes; wire
+# convolution variant 9 on every plane); see profiles/.
 NCU_TRAFFIC = {"three_planes_800_800_960x6000": {
-    "raster_scatter": 8.39e6, "fwd_rows": 75.9e6, "wire_conv": 92.7e6, "inv_rows": 76.9e6, "memset_grid": 3.84e6}}
+    "raster_scatter": 8.39e6, "fwd_rows": 76.2e6, "wire_conv": 93.9e6, "inv_rows": 77.3e6, "memset_grid": 3.19e6}}
 
 
 def drawing_bins(wiresim, planes, depos) -> int:
