@@ -690,7 +690,11 @@ raster_small_kernel(const __grid_constant__ RasterUnits U, ws_patches pt, long l
 
 // Binomial(n, pr) for a float pr: float inversion (same operations as the
 // binomial mode's exact branch) for n <= exact_max; else the normal
-// approximation with the mean n pr exact in double and z from words 0, 1.
+// approximation with z from words 0, 1 and the mean n pr carried exactly as
+// a float pair (hi + lo, the product's rounding error by an FMA), so the
+// floor sees hi's integer part exactly and adds the small remainder
+// (hi - floor hi) + lo + z sd + 1/2 in float.  (No double arithmetic: this
+// GPU's FP64 rate is a small fraction of its FP32 rate.)
 __device__ __forceinline__ int binomial_var(int n, float pr, const RasterArgs& a, uint32_t c0, uint32_t c1,
                                             uint32_t depo, const float* recip) {
     if (n <= 0 || !(pr > 0.f)) return 0;
@@ -706,10 +710,13 @@ __device__ __forceinline__ int binomial_var(int n, float pr, const RasterArgs& a
     const float u1 = fmaf((float)x.x, two_m32, 0.5f * two_m32);
     const float u2 = fmaf((float)x.y, two_m32, 0.5f * two_m32);
     const float z = sqrtf(fmaxf(-2.f * __logf(u1), 0.f)) * -__cosf(6.28318530717958648f * (u2 - 0.5f));
-    const double mean = (double)n * (double)pr;
-    const double sd = sqrt(mean * (1.0 - (double)pr));
-    const double kf = floor(mean + (double)z * sd + 0.5);
-    return kf < 0.0 ? 0 : (kf > (double)n ? n : (int)kf);
+    const float nf = (float)n;                 // n < 2^24: exact
+    const float hi = nf * pr;
+    const float lo = fmaf(nf, pr, -hi);        // n pr = hi + lo exactly
+    const float sd = sqrtf(hi * (1.f - pr));
+    const float ip = floorf(hi);
+    const float kf = ip + floorf(((hi - ip) + lo) + fmaf(z, sd, 0.5f));
+    return kf < 0.f ? 0 : (kf > nf ? n : (int)kf);
 }
 
 // Standardised clamped edge u and erfc(|u|) of bin edge e along an axis.
