@@ -566,6 +566,14 @@ struct Shape {
     static constexpr bool inplace = npass == 3 && L / radix[npass == 3 ? 1 : 0] <= NT;
     static constexpr int buffers = inplace ? 1 : 2;
     static constexpr int ctas = inplace ? 3 : 2;   // per SM
+    // A half spectrum rounded up to 16 bytes, and a buffer that holds either
+    // L complex values or two such half spectra (the rows fetched by bulk
+    // copies before the first pass).
+    static constexpr int nfe = ((L / 2 + 1) + 1) & ~1;
+    static constexpr int buf = ((L + 1) & ~1) > 2 * nfe ? ((L + 1) & ~1) : 2 * nfe;
+    // the first pass has one butterfly per thread, so it can read its inputs
+    // from the buffer it then overwrites
+    static constexpr bool first_inplace = L / radix[0] <= NT;
 };
 
 template <int R, bool INV, typename C>
@@ -672,7 +680,53 @@ __device__ __forceinline__ void shape_middle(const FftPlan& plan, C* buf0, C* bu
     });
 }
 
-template <typename SH>
+// First pass with Ns = 1 (no twiddles) from inputs in shared memory into the
+// same buffer: one butterfly per thread reads its R inputs into registers,
+// every thread passes a barrier, then the outputs land at j R + r.
+template <typename SH, bool INV, typename Ld>
+__device__ __forceinline__ void first_pass_inplace(float2* buf, Ld ld) {
+    constexpr int R = SH::radix[0], nb = SH::L / R;
+    static_assert(SH::first_inplace, "one butterfly per thread");
+    const int j = threadIdx.x;
+    float2 v[R];
+    if (j < nb) {
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[r] = ld(j + r * nb);
+    }
+    __syncthreads();   // every input read before any output lands
+    if (j < nb) {
+        Dft<R, INV, float2>::run(v);
+#pragma unroll
+        for (int r = 0; r < R; ++r) buf[j * R + r] = v[r];
+    }
+    __syncthreads();
+}
+
+// Fetch `bytes0` from src0 (and bytes1 from src1 if non-null) into shared
+// memory with bulk copies on one mbarrier; false (after flagging
+// WS_DEV_TIMEOUT and letting a late copy drain) if they never land.
+__device__ __forceinline__ bool bulk_fetch_rows(void* dst0, const void* src0, uint32_t bytes0, void* dst1,
+                                                const void* src1, uint32_t bytes1, uint64_t* bar, uint32_t* status) {
+    if (threadIdx.x == 0) {
+        mbar_init(bar);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        bulk_expect(bar, bytes0 + (src1 ? bytes1 : 0u));
+        bulk_load(dst0, src0, bytes0, bar);
+        if (src1) bulk_load(dst1, src1, bytes1, bar);
+    }
+    const bool ok = mbar_wait(bar, 0u);
+    if (__syncthreads_or(!ok)) {
+        if (threadIdx.x == 0) atomicOr(status, WS_DEV_TIMEOUT);
+        mbar_wait(bar, 0u);
+        return false;
+    }
+    return true;
+}
+
+template <typename SH, bool BULK>
 __global__ void __launch_bounds__(SH::threads, SH::ctas)
 fwd_rows_shape_kernel(FftPlan plan, const float2* __restrict__ tw, const __grid_constant__ RowUnits U, int ncols,
                       int64_t in_stride, int64_t out_stride, int nfreq, float scale) {
@@ -681,7 +735,7 @@ fwd_rows_shape_kernel(FftPlan plan, const float2* __restrict__ tw, const __grid_
     static_assert(SH::npass >= 2, "edge passes");
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* buf0 = reinterpret_cast<C*>(smem_raw);
-    C* buf1 = buf0 + ((L + 1) & ~1);
+    C* buf1 = buf0 + SH::buf;
     const int u = find_unit(U.prefix, U.n, (int)blockIdx.x);
     const float* __restrict__ in = static_cast<const float*>(U.in[u]);
     const float* __restrict__ in2 = static_cast<const float*>(U.in2[u]);
@@ -692,19 +746,31 @@ fwd_rows_shape_kernel(FftPlan plan, const float2* __restrict__ tw, const __grid_
     const float* __restrict__ la = in2 ? in2 + (int64_t)r0 * in_stride : nullptr;
     const float* __restrict__ lb = (in2 && has_b) ? la + in_stride : la;
     const int nload = ncols < L ? ncols : L;
-    io_pass<SH::radix[0], 1, L, SH::threads, false>(tw, [&](int n) {
-        float xa = 0.f, xb = 0.f;
-        if (n < nload) {
-            xa = __ldg(pa + n);
-            if (has_b) xb = __ldg(pb + n);
-            if (in2) {
-                xa += __ldg(la + n);
-                if (has_b) xb += __ldg(lb + n);
+    if constexpr (BULK) {
+        // the two rows (nload floats each, a multiple of 4) by bulk copies
+        __shared__ __align__(8) uint64_t bar;
+        float* sa = reinterpret_cast<float*>(buf0);
+        float* sb = sa + nload;
+        const uint32_t bytes = (uint32_t)nload * 4u;
+        if (!bulk_fetch_rows(sa, pa, bytes, sb, has_b ? pb : nullptr, bytes, &bar, U.status)) return;
+        first_pass_inplace<SH, false>(buf0, [&](int n) {
+            return n < nload ? make_float2(sa[n], has_b ? sb[n] : 0.f) : make_float2(0.f, 0.f);
+        });
+    } else {
+        io_pass<SH::radix[0], 1, L, SH::threads, false>(tw, [&](int n) {
+            float xa = 0.f, xb = 0.f;
+            if (n < nload) {
+                xa = __ldg(pa + n);
+                if (has_b) xb = __ldg(pb + n);
+                if (in2) {
+                    xa += __ldg(la + n);
+                    if (has_b) xb += __ldg(lb + n);
+                }
             }
-        }
-        return make_float2(xa, xb);
-    }, [&](int i, C v) { buf0[i] = v; });
-    __syncthreads();
+            return make_float2(xa, xb);
+        }, [&](int i, C v) { buf0[i] = v; });
+        __syncthreads();
+    }
     shape_middle<SH, false>(plan, buf0, buf1, tw);
     const C* z = (!SH::inplace && ((last - 1) & 1)) ? buf1 : buf0;
     C* oa = static_cast<C*>(U.out[u]) + (int64_t)r0 * out_stride;
@@ -717,7 +783,7 @@ fwd_rows_shape_kernel(FftPlan plan, const float2* __restrict__ tw, const __grid_
     });
 }
 
-template <typename SH>
+template <typename SH, bool BULK>
 __global__ void __launch_bounds__(SH::threads, SH::ctas)
 inv_rows_shape_kernel(FftPlan plan, const float2* __restrict__ tw, const __grid_constant__ RowUnits U,
                       int64_t in_stride, int nfreq, int ncols, int64_t out_stride) {
@@ -726,22 +792,36 @@ inv_rows_shape_kernel(FftPlan plan, const float2* __restrict__ tw, const __grid_
     static_assert(SH::npass >= 2, "edge passes");
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* buf0 = reinterpret_cast<C*>(smem_raw);
-    C* buf1 = buf0 + ((L + 1) & ~1);
+    C* buf1 = buf0 + SH::buf;
     const int u = find_unit(U.prefix, U.n, (int)blockIdx.x);
     const int r0 = 2 * ((int)blockIdx.x - U.prefix[u]);
     const bool has_b = r0 + 1 < U.nrows[u];
     const C* __restrict__ ya = static_cast<const C*>(U.in[u]) + (int64_t)r0 * in_stride;
     const C* __restrict__ yb = has_b ? ya + in_stride : ya;
-    io_pass<SH::radix[0], 1, L, SH::threads, true>(tw, [&](int k) {
+    // Z = A + iB over the Hermitian extension of both half spectra (global
+    // spectra through the read-only path, or their copies in shared memory)
+    auto hermitian = [&](const C* a, const C* b, int k) {
         const bool upper = k >= nfreq;
         const int kk = upper ? L - k : k;
-        C A = __ldg(ya + kk);
-        C B = has_b ? __ldg(yb + kk) : make_float2(0.f, 0.f);
+        C A = BULK ? a[kk] : __ldg(a + kk);
+        C B = has_b ? (BULK ? b[kk] : __ldg(b + kk)) : make_float2(0.f, 0.f);
         if (kk == 0 || (L % 2 == 0 && 2 * kk == L)) { A.y = 0.f; B.y = 0.f; }
         if (upper) { A.y = -A.y; B.y = -B.y; }
         return make_float2(A.x - B.y, A.y + B.x);
-    }, [&](int i, C v) { buf0[i] = v; });
-    __syncthreads();
+    };
+    if constexpr (BULK) {
+        // both half spectra (nfreq <= SH::nfe values each) by bulk copies
+        __shared__ __align__(8) uint64_t bar;
+        C* sA = buf0;
+        C* sB = buf0 + SH::nfe;
+        const uint32_t bytes = (uint32_t)SH::nfe * (uint32_t)sizeof(C);
+        if (!bulk_fetch_rows(sA, ya, bytes, sB, has_b ? yb : nullptr, bytes, &bar, U.status)) return;
+        first_pass_inplace<SH, true>(buf0, [&](int k) { return hermitian(sA, sB, k); });
+    } else {
+        io_pass<SH::radix[0], 1, L, SH::threads, true>(tw, [&](int k) { return hermitian(ya, yb, k); },
+                                                     [&](int i, C v) { buf0[i] = v; });
+        __syncthreads();
+    }
     shape_middle<SH, true>(plan, buf0, buf1, tw);
     const C* z = (!SH::inplace && ((last - 1) & 1)) ? buf1 : buf0;
     float* oa = static_cast<float*>(U.out[u]) + (int64_t)r0 * out_stride;
@@ -1048,6 +1128,7 @@ static RowUnits row_units(const RowBatch& rb, bool* aligned16) {
     RowUnits U;
     U.n = rb.n;
     U.prefix[0] = 0;
+    U.status = rb.status;
     *aligned16 = true;
     for (int i = 0; i < rb.n; ++i) {
         U.in[i] = rb.in[i];
@@ -1067,17 +1148,20 @@ using InvShapeFn = void (*)(FftPlan, const float2*, const RowUnits, int64_t, int
 struct ShapeKernels {
     int npass;
     int radix[4];
-    FwdShapeFn fwd;
-    int fwd_threads, fwd_buffers;
-    InvShapeFn inv;
-    int inv_threads, inv_buffers;
+    FwdShapeFn fwd, fwd_bulk;    // first-pass rows by loads / by bulk copies
+    int fwd_threads, fwd_buffers, fwd_buf;
+    InvShapeFn inv, inv_bulk;
+    int inv_threads, inv_buffers, inv_buf;
 };
 constexpr int kFwdShapeThreads = 320;
 constexpr int kInvShapeThreads = 256;
 #define WS_SHAPE3(A, B, C)                                                                                  \
-    {3, {A, B, C}, fwd_rows_shape_kernel<Shape<kFwdShapeThreads, A, B, C>>, kFwdShapeThreads,                \
-     Shape<kFwdShapeThreads, A, B, C>::buffers, inv_rows_shape_kernel<Shape<kInvShapeThreads, A, B, C>>,     \
-     kInvShapeThreads, Shape<kInvShapeThreads, A, B, C>::buffers}
+    {3, {A, B, C}, fwd_rows_shape_kernel<Shape<kFwdShapeThreads, A, B, C>, false>,                          \
+     fwd_rows_shape_kernel<Shape<kFwdShapeThreads, A, B, C>, true>, kFwdShapeThreads,                       \
+     Shape<kFwdShapeThreads, A, B, C>::buffers, Shape<kFwdShapeThreads, A, B, C>::buf,                      \
+     inv_rows_shape_kernel<Shape<kInvShapeThreads, A, B, C>, false>,                                         \
+     inv_rows_shape_kernel<Shape<kInvShapeThreads, A, B, C>, true>, kInvShapeThreads,                        \
+     Shape<kInvShapeThreads, A, B, C>::buffers, Shape<kInvShapeThreads, A, B, C>::buf}
 static const ShapeKernels kShapes[] = {
     WS_SHAPE3(25, 25, 10),  // 6250: linear convolution of 6000 ticks with a 200-tick response
     WS_SHAPE3(25, 16, 15),  // 6000: circular convolution of 6000 ticks
@@ -1104,13 +1188,17 @@ static cudaError_t fwd_rows_t(const FftPlan& plan, const cplx<S>* tw, const RowB
     if (rb.n <= 0) return cudaSuccess;
     if constexpr (std::is_same<S, float>::value && std::is_same<TIN, float>::value) {
         if (const ShapeKernels* k = shape_kernels(plan)) {
-            const int smem = k->fwd_buffers * ((plan.L + 1) & ~1) * (int)sizeof(float2);
-            cudaError_t e = set_smem((const void*)k->fwd, smem);
-            if (e != cudaSuccess) return e;
             bool al = false;
             const RowUnits U = row_units(rb, &al);
             if (U.prefix[rb.n] <= 0) return cudaSuccess;
-            k->fwd<<<U.prefix[rb.n], k->fwd_threads, smem, s>>>(plan, tw, U, ncols, in_stride, out_stride, nfreq, scale);
+            // bulk copies need 16-byte rows and a status word to report a copy that never lands
+            bool bulk = rb.status != nullptr && al && in_stride % 4 == 0 && (ncols < plan.L ? ncols : plan.L) % 4 == 0;
+            for (int i = 0; i < rb.n; ++i) bulk = bulk && rb.in2[i] == nullptr;
+            const FwdShapeFn fn = bulk ? k->fwd_bulk : k->fwd;
+            const int smem = k->fwd_buffers * k->fwd_buf * (int)sizeof(float2);
+            cudaError_t e = set_smem((const void*)fn, smem);
+            if (e != cudaSuccess) return e;
+            fn<<<U.prefix[rb.n], k->fwd_threads, smem, s>>>(plan, tw, U, ncols, in_stride, out_stride, nfreq, scale);
             return cudaGetLastError();
         }
     }
@@ -1133,13 +1221,16 @@ static cudaError_t inv_rows_t(const FftPlan& plan, const cplx<S>* tw, const RowB
     if (rb.n <= 0) return cudaSuccess;
     if constexpr (std::is_same<S, float>::value) {
         if (const ShapeKernels* k = shape_kernels(plan)) {
-            const InvShapeFn fn = k->inv;
-            const int smem = k->inv_buffers * ((plan.L + 1) & ~1) * (int)sizeof(float2);
-            cudaError_t e = set_smem((const void*)fn, smem);
-            if (e != cudaSuccess) return e;
-            bool al = false;
+            bool al = true;
             const RowUnits U = row_units(rb, &al);
             if (U.prefix[rb.n] <= 0) return cudaSuccess;
+            bool in16 = in_stride % 2 == 0 && nfreq == plan.L / 2 + 1;
+            for (int i = 0; i < rb.n; ++i) in16 = in16 && (uintptr_t)rb.in[i] % 16 == 0;
+            const bool bulk = rb.status != nullptr && in16;
+            const InvShapeFn fn = bulk ? k->inv_bulk : k->inv;
+            const int smem = k->inv_buffers * k->inv_buf * (int)sizeof(float2);
+            cudaError_t e = set_smem((const void*)fn, smem);
+            if (e != cudaSuccess) return e;
             fn<<<U.prefix[rb.n], k->inv_threads, smem, s>>>(plan, tw, U, in_stride, nfreq, ncols, out_stride);
             return cudaGetLastError();
         }
@@ -1174,10 +1265,11 @@ cudaError_t launch_fwd_rows_batch(const FftPlan& plan, const float2* tw, const R
 
 cudaError_t launch_fwd_rows(const FftPlan& plan, const float2* tw, const float* in, int nrows,
                             int ncols, int64_t in_stride, float2* out, int64_t out_stride,
-                            int nfreq, float scale, cudaStream_t s) {
+                            int nfreq, float scale, cudaStream_t s, uint32_t* status) {
     if (nrows <= 0) return cudaSuccess;
-    return launch_fwd_rows_batch(plan, tw, one_row(in, nullptr, out, nrows), ncols, in_stride, out_stride, nfreq,
-                                 scale, s);
+    RowBatch rb = one_row(in, nullptr, out, nrows);
+    rb.status = status;
+    return launch_fwd_rows_batch(plan, tw, rb, ncols, in_stride, out_stride, nfreq, scale, s);
 }
 
 cudaError_t launch_fwd_rows_comp(const FftPlan& plan, const float2* tw, const float* hi, const float* lo, int nrows,
@@ -1204,9 +1296,11 @@ cudaError_t launch_inv_rows_batch(const FftPlan& plan, const float2* tw, const R
 
 cudaError_t launch_inv_rows(const FftPlan& plan, const float2* tw, const float2* in, int nrows,
                             int64_t in_stride, int nfreq, float* out, int ncols,
-                            int64_t out_stride, cudaStream_t s) {
+                            int64_t out_stride, cudaStream_t s, uint32_t* status) {
     if (nrows <= 0) return cudaSuccess;
-    return launch_inv_rows_batch(plan, tw, one_row(in, nullptr, out, nrows), in_stride, nfreq, ncols, out_stride, s);
+    RowBatch rb = one_row(in, nullptr, out, nrows);
+    rb.status = status;
+    return launch_inv_rows_batch(plan, tw, rb, in_stride, nfreq, ncols, out_stride, s);
 }
 
 cudaError_t launch_inv_rows64(const FftPlan& plan, const double2* tw, const double2* in, int nrows, int64_t in_stride,

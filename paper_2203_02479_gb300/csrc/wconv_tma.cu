@@ -24,7 +24,6 @@ namespace ws {
 namespace {
 
 constexpr int kCols = 128;                 // complex columns per tile (one thread each)
-constexpr int kWaitIters = 1 << 18;        // try_wait attempts before giving up (~1 s: an attempt suspends ~4 us)
 
 struct TmaConvUnits {
     CUtensorMap map[kMaxUnits];            // X of each unit: {2 * stride floats, nwires rows}
@@ -34,32 +33,6 @@ struct TmaConvUnits {
     void* Y[kMaxUnits];
     const void* Rt[kMaxUnits];
 };
-
-__device__ __forceinline__ uint32_t smem_addr(const void* p) {
-    return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t* bar) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(bar)) : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity) {
-    uint32_t done;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(done)
-        : "r"(smem_addr(bar)), "r"(parity)
-        : "memory");
-    return done != 0u;
-}
-
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int iters = kWaitIters) {
-    for (int it = 0; it < iters; ++it)
-        if (mbar_try(bar, parity)) return true;
-    return false;
-}
 
 // 2D tile copy of the box at (x, y) into dst, completing on bar.
 __device__ __forceinline__ void tma_load_tile(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar,

@@ -273,7 +273,7 @@ ws_status convolve_impl(ws_plane* pl, const float* grid, float* out, cudaStream_
                         const ws_params* noise_params = nullptr) {
     const ws_plane_desc& d = pl->desc;
     WS_LAUNCH(pl, K_FWD, s, ws::launch_fwd_rows(pl->plan, pl->tw, grid, d.nwires * pl->impacts, d.nticks, d.nticks,
-                                                pl->X, pl->fstride, pl->nfreq, 1.0f, s));
+                                                pl->X, pl->fstride, pl->nfreq, 1.0f, s, pl->status));
     if (pl->impacts > 1) {
         WS_LAUNCH(pl, K_WCONV, s, ws::launch_wire_conv_impacts(pl->X, pl->Y, pl->Rt, d.nwires, pl->impacts, pl->nfreq,
                                                                pl->fstride, d.resp_nwires, d.resp_wire_center,
@@ -289,7 +289,7 @@ ws_status convolve_impl(ws_plane* pl, const float* grid, float* out, cudaStream_
         if (st != WS_OK) return st;
     }
     WS_LAUNCH(pl, K_INV, s, ws::launch_inv_rows(pl->plan, pl->tw, pl->Y, d.nwires, pl->fstride, pl->nfreq, out,
-                                                d.nticks, d.nticks, s));
+                                                d.nticks, d.nticks, s, pl->status));
     return WS_OK;
 }
 
@@ -636,7 +636,7 @@ ws_status ws_simulate(ws_plane* pl, const ws_depos* depos, const ws_params* para
         st = add_plane_noise(pl, params, pl->Y, false, s);
         if (st != WS_OK) return st;
         WS_LAUNCH(pl, K_INV, s, ws::launch_inv_rows(pl->plan, pl->tw, pl->Y, d.nwires, pl->fstride, pl->nfreq, out_dev,
-                                                    d.nticks, d.nticks, s));
+                                                    d.nticks, d.nticks, s, pl->status));
         return WS_OK;
     }
     WS_LAUNCH(pl, K_RASTER_SCATTER, s, ws::launch_raster_scatter(a, out_dev, pl->large, s));
@@ -870,6 +870,7 @@ ws_status batch_waves(ws_plane* const* planes, int nplanes, const ws_depos* depo
         ws::NoiseBatch nb;
         bool noisy = false;
         rb.n = fb.n = ib.n = cb.n = nb.n = nu;
+        fb.status = ib.status = p0->status;
         rb.prec = WS_PREC_FP32;
         nb.key0 = (uint32_t)(params->seed & 0xFFFFFFFFu);
         nb.key1 = (uint32_t)(params->seed >> 32);

@@ -74,6 +74,50 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1
     return c;
 }
 
+// ---- shared-memory mbarriers and bulk (TMA) copies
+constexpr int kWaitIters = 1 << 18;   // try_wait attempts before giving up (~1 s: an attempt suspends ~4 us)
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(bar)) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return done != 0u;
+}
+
+// Bounded wait: false if the phase did not complete within `iters` attempts.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int iters = kWaitIters) {
+    for (int it = 0; it < iters; ++it)
+        if (mbar_try(bar, parity)) return true;
+    return false;
+}
+
+// One thread: expect `bytes` on bar, then copy [src, src + each) into dst
+// with the bulk copy engine (addresses and sizes multiples of 16 bytes).
+__device__ __forceinline__ void bulk_expect(uint64_t* bar, uint32_t bytes) {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 ::"r"(smem_addr(dst)), "l"(src), "r"(bytes), "r"(smem_addr(bar))
+                 : "memory");
+}
+
 // Noise term N(t, x) of Eq. 1 for one unit, added to the half spectra Y
 // between the wire convolution and the inverse transform (amp null: none).  Wire w, bin k:
 // Nhat = A[k] xi_w[k] + Ac[k] xi'_{w / group}[k], xi = (z1 + i z2)/sqrt 2
@@ -95,6 +139,8 @@ struct RowBatch {          // row transforms: unit i has nrows[i] rows in[i] -> 
     const void* in2[kMaxUnits];   // optional float low parts added to in (compensated grids)
     void* out[kMaxUnits];
     int nrows[kMaxUnits];
+    uint32_t* status = nullptr;   // device status word: lets the fixed-shape kernels fetch rows by
+                                  // bulk copies (a copy that never lands is reported there)
 };
 struct NoiseBatch {        // noise added to the spectra Y[i] (nwires[i] rows) of each unit
     int n = 0;
@@ -118,6 +164,7 @@ struct RowUnits {
     const void* in2[kMaxUnits];
     void* out[kMaxUnits];
     int nrows[kMaxUnits];
+    uint32_t* status;
 };
 struct NoiseUnits {
     int n;
@@ -143,12 +190,12 @@ cudaError_t launch_twiddles(float2* tw, const FftPlan& plan, cudaStream_t s);
 // for k < nfreq; rows shorter than L are zero padded.
 cudaError_t launch_fwd_rows(const FftPlan& plan, const float2* tw, const float* in, int nrows,
                             int ncols, int64_t in_stride, float2* out, int64_t out_stride,
-                            int nfreq, float scale, cudaStream_t s);
+                            int nfreq, float scale, cudaStream_t s, uint32_t* status = nullptr);
 // Half spectra -> real rows: out[r][n] = sum_k Y[r][k] e^{+2 pi i k n / L} over the
 // Hermitian-extended spectrum, for n < ncols.
 cudaError_t launch_inv_rows(const FftPlan& plan, const float2* tw, const float2* in, int nrows,
                             int64_t in_stride, int nfreq, float* out, int ncols,
-                            int64_t out_stride, cudaStream_t s);
+                            int64_t out_stride, cudaStream_t s, uint32_t* status = nullptr);
 // Noise term of Eq. 1 added in place to each unit's spectra (float2 or
 // double2 rows of `stride`, nfreq bins of a length-L transform); units with
 // a null amplitude are skipped.
