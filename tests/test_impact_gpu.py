@@ -112,3 +112,25 @@ def test_long_response(ws, kt):
     got = to_np(pl.simulate(ws.DeviceDepos.from_plane_depos(d), ws.Params()))
     ref = oracle.simulate(d.q, d.x_mm, d.t_us, nw, nt, R, 10)
     assert rel_l2(got, ref) <= REL_L2
+
+
+@pytest.mark.parametrize("I", [2, 32])
+def test_impact_count_limits(ws, I):
+    """The smallest and largest sub-pitch position counts, depos partly off
+    the grid on both sides."""
+    nw, nt = 12, 900
+    R = inputs.impact_response("unipolar", impacts=I)
+    pl = ws.Plane(nw, nt, R)
+    rng = np.random.Generator(np.random.PCG64(I))
+    q = rng.exponential(5000, 300).astype(np.float32)
+    x = rng.uniform(-10, nw * 5.0 + 10, 300).astype(np.float32)
+    t = rng.uniform(1, nt * 0.5, 300).astype(np.float32)
+    got = to_np(pl.simulate(ws.DeviceDepos(q, x, t), ws.Params()))
+    ref = oracle.simulate_impacts(q, x, t, nw, nt, R, 10)
+    assert rel_l2(got, ref) <= REL_L2
+
+
+def test_impact_count_above_limit_rejected(ws):
+    R = inputs.impact_response("unipolar", impacts=33, nwires=3, nticks=10, wire_center=1)
+    with pytest.raises(ws.WiresimError):
+        ws.Plane(4, 100, R, wire_center=1)

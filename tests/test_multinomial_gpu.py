@@ -166,3 +166,25 @@ def test_batch_equals_per_unit_and_fp64(ws):
             pe64 = ws.Params(**{**pe.__dict__, "precision": ws.WS_PREC_FP64})
             r64 = to_np(pl.simulate(events[e][p], pe64))
             assert np.linalg.norm(r64 - ref) <= 1e-5 * max(np.linalg.norm(ref), 1.0)
+
+
+def test_edge_cases(ws):
+    """No depos, p = 0 (nothing survives), a depo entirely off the grid, a
+    point charge (zero widths: one bin takes every survivor)."""
+    nw, nt = 16, 400
+    pl = ws.Plane(nw, nt, inputs.response("bipolar"))
+    z = np.zeros(0, np.float32)
+    out = to_np(pl.simulate(ws.DeviceDepos(z, z, z), ws.Params(fluctuate=2, p_survive=0.7, seed=1)))
+    assert not np.any(out)
+    d = inputs.uniform_depos(200, nw, seed=2, nticks=nt)
+    S = _gpu_patches(ws, pl, d, ws.Params(fluctuate=2, p_survive=0.0, seed=3))
+    assert all(not np.any(P) for _, _, P in S)
+    off = ws.DeviceDepos(np.array([5000.0], np.float32), np.array([-500.0], np.float32),
+                         np.array([100.0], np.float32))
+    assert not np.any(to_np(pl.simulate(off, ws.Params(fluctuate=2, p_survive=1.0, seed=4))))
+    pt = ws.DeviceDepos(np.array([1234.0], np.float32), np.array([42.0], np.float32), np.array([50.2], np.float32),
+                        np.array([0.0], np.float32), np.array([0.0], np.float32))
+    p = pl.rasterize(pt, ws.Params(fluctuate=2, p_survive=1.0, seed=5))
+    assert int(p["nw"][0]) == 1 and int(p["nt"][0]) == 1
+    assert float(to_np(p["val"][:1])[0]) == 1234.0
+    assert pl.status() == 0

@@ -168,3 +168,16 @@ def test_set_noise_argument_errors(ws):
     assert lib.ws_plane_set_noise(pl.handle, 0, a.data_ptr(), 4, None) == 1      # coherent without incoherent
     with pytest.raises(ValueError):
         pl.set_noise(np.ones(L // 2, np.float32))
+
+
+def test_noise_edge_cases(ws):
+    """One wire (odd row count, a group wider than the plane), and the
+    largest coherent group equal to the plane."""
+    for nw, group in ((1, 48), (7, 7)):
+        pl, R, L = _plane(ws, nw, 700)
+        amp = inputs.noise_amplitudes(L)
+        coh = inputs.noise_amplitudes(L, "coherent")
+        pl.set_noise(amp, coh, group)
+        got = to_np(pl.simulate(_no_depos(ws), ws.Params(seed=11)))
+        ref = oracle.noise(nw, 700, L, amp, coh, group, seed=11)
+        assert rel_l2(got, ref) <= REL_L2
