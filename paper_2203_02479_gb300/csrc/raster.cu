@@ -366,7 +366,7 @@ __device__ __forceinline__ W window_norm(const RasterArgs& a) {
 template <int MODE, int P>
 __global__ void __launch_bounds__(32 * kWarpsPerBlock)
 raster_kernel(const __grid_constant__ RasterUnits U, ws_patches pt, const long long* __restrict__ list,
-              unsigned* list_count, unsigned list_cap, unsigned* done) {
+              unsigned* list_count, unsigned list_cap, unsigned* done, int cdf_rows) {
     using W = typename PrecT<P>::W;
     __shared__ W s_u[kWarpsPerBlock][kChunk + 1];
     __shared__ W s_c[kWarpsPerBlock][kChunk + 1];
@@ -378,6 +378,11 @@ raster_kernel(const __grid_constant__ RasterUnits U, ws_patches pt, const long l
     // an empty list needs no work and no reset (the counters are zero)
     if (use_list && nlist == 0u) return;
     fill_recip(s_recip);
+    // exact-branch CDF rows for unit 0's survival probability, as in the
+    // lane-per-depo kernel (dynamic shared memory)
+    extern __shared__ float s_cdf_large[];
+    const RasterArgs& a0 = U.a[0];
+    if (cdf_rows > 0) fill_cdf(s_cdf_large, s_recip, a0, cdf_rows);
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
     const int64_t nwarps = (int64_t)gridDim.x * kWarpsPerBlock;
@@ -396,6 +401,8 @@ raster_kernel(const __grid_constant__ RasterUnits U, ws_patches pt, const long l
         }
         const RasterArgs& a = U.a[u];
         float* __restrict__ grid = U.grid[u];
+        const float* cdf = (cdf_rows > 0 && a.exact_max <= cdf_rows && a.inv_r == a0.inv_r &&
+                            a.inv_base == a0.inv_base) ? s_cdf_large : nullptr;
         ExtentT<W> e;
         W q;
         bool bad;
@@ -440,7 +447,7 @@ raster_kernel(const __grid_constant__ RasterUnits U, ws_patches pt, const long l
                     } else {
                         const int N = electrons(q * s_wx[wib][ia] * s_wt[wib][ib]);
                         v = (W)binomial_bin<P>(N, a, (uint32_t)((int64_t)w * a.nticks + k), (uint32_t)i, s_recip,
-                                               nullptr);
+                                               cdf);
                     }
                     if (MODE == EMIT_GRID) emit<P>(a, grid, (int64_t)w * a.nticks + k, v);
                     else pt.val[off + (int64_t)(w - e.w0) * ntf + (k - e.k0)] = (float)v;
@@ -1301,7 +1308,8 @@ static cudaError_t launch_raster_units(const RasterUnits& U, const ws_patches& p
     const int rows = (a0.fluct && !a0.keep_all && a0.T != 0u) ? (a0.exact_max < kExactCap ? a0.exact_max : kExactCap) : 0;
     const size_t dyn = sizeof(float) * (size_t)rows * (rows + 1) / 2;
     raster_small_kernel<MODE, P><<<blocks, 32 * kSmallWarpsPerBlock, dyn, s>>>(U, p, L.list, L.count, L.cap, rows);
-    raster_kernel<MODE, P><<<num_sms() * 2, 32 * kWarpsPerBlock, 0, s>>>(U, p, L.list, L.count, L.cap, L.done);
+    raster_kernel<MODE, P><<<num_sms() * 2, 32 * kWarpsPerBlock, dyn, s>>>(U, p, L.list, L.count, L.cap, L.done,
+                                                                         rows);
     return cudaGetLastError();
 }
 
