@@ -425,6 +425,98 @@ cudaError_t launch_ring(const ConvBatch& cb, int nfreq, int64_t stride, int kw, 
     return cudaGetLastError();
 }
 
+// Wire convolution over sub-pitch impact positions (fine rows w * I + i of
+// X), fed by TMA: persistent CTAs walk units (tile, impact) with the impact
+// fastest, double-buffering the (B + K - 1)-row tile of the next unit while
+// computing the current one; impact i's rows come through tensor map i
+// (base row i, row pitch I rows), and one set of accumulators per tile sums
+// the impacts before Y is stored.  Each CTA takes a contiguous run of whole
+// tiles.  Waits are bounded as in the other TMA kernels.
+template <int K, int B>
+__global__ void __launch_bounds__(kCols)
+wire_conv_impacts_tma_kernel(const __grid_constant__ TmaConvUnits U, int impacts, int nwires, int nfreq,
+                             int64_t stride, int kw, int center, int nkblocks, void* Yv, const void* Rtv,
+                             uint32_t* status) {
+    constexpr int ROWS = B + K - 1;
+    constexpr uint32_t TILE_BYTES = ROWS * kCols * sizeof(float2);
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ __align__(8) uint64_t bar[2];
+    auto buf = [&](int st) { return reinterpret_cast<const float2*>(smem + (st ? TILE_BYTES : 0u)); };
+    float2* __restrict__ Y = static_cast<float2*>(Yv);
+    const float2* __restrict__ Rt = static_cast<const float2*>(Rtv);
+    const int nwb = (nwires + B - 1) / B;
+    const int ntiles = nkblocks * nwb;
+    const int tile_beg = (int)((int64_t)ntiles * blockIdx.x / gridDim.x);
+    const int tile_end = (int)((int64_t)ntiles * (blockIdx.x + 1) / gridDim.x);
+    const int t_beg = tile_beg * impacts, t_end = tile_end * impacts;
+    auto issue = [&](int t, int st) {
+        const int tile = t / impacts, im = t - tile * impacts;
+        const int k0 = (tile / nwb) * kCols, w0 = (tile % nwb) * B;
+        tma_load_tile(smem + (st ? TILE_BYTES : 0u), &U.map[im], 2 * k0, w0 + center - (K - 1), &bar[st], TILE_BYTES);
+    };
+    if (threadIdx.x == 0) {
+        mbar_init(&bar[0]);
+        mbar_init(&bar[1]);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    if (t_beg < t_end && threadIdx.x == 0) issue(t_beg, 0);
+    uint32_t parity[2] = {0u, 0u};
+    float k1[B], k2[B], k3[B];
+    for (int i = 0, t = t_beg; t < t_end; ++i, ++t) {
+        const int st = i & 1;
+        const bool inflight_next = t + 1 < t_end;
+        if (inflight_next && threadIdx.x == 0) issue(t + 1, st ^ 1);
+        const int tile = t / impacts, im = t - tile * impacts;
+        const int k0 = (tile / nwb) * kCols, w0 = (tile % nwb) * B;
+        const int k = k0 + threadIdx.x;
+        // this impact's taps (loaded while the tile lands)
+        float cc[K], cm[K], cp[K];
+#pragma unroll
+        for (int r = 0; r < K; ++r) {
+            const float2 v = (r < kw && k < nfreq) ? __ldg(&Rt[((int64_t)im * kw + r) * stride + k])
+                                                   : make_float2(0.f, 0.f);
+            cc[r] = v.x;
+            cm[r] = v.y - v.x;
+            cp[r] = v.x + v.y;
+        }
+        if (im == 0) {
+#pragma unroll
+            for (int b = 0; b < B; ++b) k1[b] = k2[b] = k3[b] = 0.f;
+        }
+        const bool ok = mbar_wait(&bar[st], parity[st]);
+        parity[st] ^= 1u;
+        if (__syncthreads_or(!ok)) {
+            if (threadIdx.x == 0) atomicOr(status, WS_DEV_TIMEOUT);
+            if (inflight_next) mbar_wait(&bar[st ^ 1], parity[st ^ 1]);
+            return;
+        }
+        const float2* col = buf(st) + threadIdx.x;
+        if (k < nfreq) {
+#pragma unroll
+            for (int uu = 0; uu < ROWS; ++uu) {
+                const float2 x = col[uu * kCols];
+                const float sab = x.x + x.y;
+#pragma unroll
+                for (int b = 0; b < B; ++b) {
+                    const int r = b + K - 1 - uu;
+                    if (r >= 0 && r < K) {
+                        k1[b] = fmaf(cc[r], sab, k1[b]);
+                        k2[b] = fmaf(cm[r], x.x, k2[b]);
+                        k3[b] = fmaf(cp[r], x.y, k3[b]);
+                    }
+                }
+            }
+            if (im == impacts - 1) {
+#pragma unroll
+                for (int b = 0; b < B; ++b)
+                    if (w0 + b < nwires) Y[(int64_t)(w0 + b) * stride + k] = make_float2(k1[b] - k3[b], k1[b] + k2[b]);
+            }
+        }
+        __syncthreads();   // buffer st is free for the copy issued next iteration
+    }
+}
+
 // The bounded-wait path on its own: one CTA waits on an mbarrier that
 // expects an arrival nobody makes; after `iters` attempts it gives up,
 // records WS_DEV_TIMEOUT and returns (cycles spent into *cycles).
@@ -447,6 +539,45 @@ __global__ void bounded_wait_selftest_kernel(uint32_t* status, int iters, unsign
 }  // namespace
 
 bool tma_available() { return encode_fn() != nullptr; }
+
+cudaError_t launch_wire_conv_impacts_tma(const float2* X, float2* Y, const float2* Rt, int nwires, int impacts,
+                                         int nfreq, int64_t stride, int kw, int center, uint32_t* status,
+                                         cudaStream_t s) {
+    constexpr int K = kMaxRespWires, B = 16;
+    constexpr int ROWS = B + K - 1;
+    const PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
+    if (!enc) return cudaErrorNotSupported;
+    if (impacts < 1 || impacts > kMaxUnits || nwires <= 0 || nfreq <= 0) return cudaErrorInvalidValue;
+    TmaConvUnits U;
+    U.n = impacts;
+    for (int i = 0; i < impacts; ++i) {
+        // impact i: fine rows i, i + I, i + 2I, ... (one per wire)
+        const cuuint64_t dims[2] = {(cuuint64_t)(2 * stride), (cuuint64_t)nwires};
+        const cuuint64_t strides[1] = {(cuuint64_t)(2 * stride * sizeof(float)) * (cuuint64_t)impacts};
+        const cuuint32_t box[2] = {2 * kCols, ROWS};
+        const cuuint32_t estr[2] = {1, 1};
+        const CUresult r = enc(&U.map[i], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2,
+                               const_cast<float2*>(X) + (int64_t)i * stride, dims, strides, box, estr,
+                               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+    }
+    const int nkblocks = (nfreq + kCols - 1) / kCols;
+    const int ntiles = nkblocks * ((nwires + B - 1) / B);
+    const int smem = 2 * ROWS * kCols * (int)sizeof(float2);
+    cudaError_t e = cudaFuncSetAttribute((const void*)wire_conv_impacts_tma_kernel<K, B>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, wire_conv_impacts_tma_kernel<K, B>, kCols, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) per_sm = 1;
+    int grid = num_sms() * per_sm;
+    if (grid > ntiles) grid = ntiles;
+    wire_conv_impacts_tma_kernel<K, B><<<grid, kCols, smem, s>>>(U, impacts, nwires, nfreq, stride, kw, center,
+                                                                 nkblocks, Y, Rt, status);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_bounded_wait_selftest(uint32_t* status, int iters, unsigned long long* cycles, cudaStream_t s) {
     bounded_wait_selftest_kernel<<<1, 32, 0, s>>>(status, iters, cycles);

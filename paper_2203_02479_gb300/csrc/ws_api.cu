@@ -275,9 +275,16 @@ ws_status convolve_impl(ws_plane* pl, const float* grid, float* out, cudaStream_
     WS_LAUNCH(pl, K_FWD, s, ws::launch_fwd_rows(pl->plan, pl->tw, grid, d.nwires * pl->impacts, d.nticks, d.nticks,
                                                 pl->X, pl->fstride, pl->nfreq, 1.0f, s, pl->status));
     if (pl->impacts > 1) {
-        WS_LAUNCH(pl, K_WCONV, s, ws::launch_wire_conv_impacts(pl->X, pl->Y, pl->Rt, d.nwires, pl->impacts, pl->nfreq,
-                                                               pl->fstride, d.resp_nwires, d.resp_wire_center,
-                                                               d.conv_mode == WS_CONV_CIRCULAR, s));
+        if (d.conv_mode == WS_CONV_LINEAR && ws::tma_available()) {
+            WS_LAUNCH(pl, K_WCONV, s, ws::launch_wire_conv_impacts_tma(pl->X, pl->Y, pl->Rt, d.nwires, pl->impacts,
+                                                                       pl->nfreq, pl->fstride, d.resp_nwires,
+                                                                       d.resp_wire_center, pl->status, s));
+        } else {
+            WS_LAUNCH(pl, K_WCONV, s, ws::launch_wire_conv_impacts(pl->X, pl->Y, pl->Rt, d.nwires, pl->impacts,
+                                                                   pl->nfreq, pl->fstride, d.resp_nwires,
+                                                                   d.resp_wire_center, d.conv_mode == WS_CONV_CIRCULAR,
+                                                                   s));
+        }
     } else {
         WS_LAUNCH(pl, K_WCONV, s, ws::launch_wire_conv(pl->X, pl->Y, pl->Rt, d.nwires, pl->nfreq, pl->fstride,
                                                        d.resp_nwires, d.resp_wire_center,

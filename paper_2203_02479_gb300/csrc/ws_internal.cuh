@@ -245,6 +245,11 @@ bool tma_available();
 cudaError_t launch_bounded_wait_selftest(uint32_t* status, int iters, unsigned long long* cycles, cudaStream_t s);
 cudaError_t launch_wire_conv_tma(const ConvBatch& cb, int nfreq, int64_t stride, int kw, int center, int variant,
                                  uint32_t* status, cudaStream_t s);
+// The impact wire convolution fed by TMA (linear mode; a copy that never
+// lands sets WS_DEV_TIMEOUT in *status).
+cudaError_t launch_wire_conv_impacts_tma(const float2* X, float2* Y, const float2* Rt, int nwires, int impacts,
+                                         int nfreq, int64_t stride, int kw, int center, uint32_t* status,
+                                         cudaStream_t s);
 
 // Hand-over list of depos whose patches are too large for the lane-per-depo
 // raster kernel (workspace-resident; count and done must start at zero and
