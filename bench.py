@@ -262,6 +262,8 @@ PHILOX_MULS = 40    # 32-bit multiplies per Philox4x32-10 block: 10 rounds x 2 p
 # DRAM bytes per launch (read + write) from one ncu --set full capture of the
 # step's kernels (one launch per stage over the three planes; wire
 # convolution variant 9 on every plane); see profiles/.
+# the raster's share of issue slots in the same capture (it is issue-bound)
+NCU_ISSUE_ACTIVE = {"three_planes_800_800_960x6000": 0.692}
 NCU_TRAFFIC = {"three_planes_800_800_960x6000": {
     "raster_scatter": 8.39e6, "fwd_rows": 76.2e6, "wire_conv": 93.9e6, "inv_rows": 77.3e6, "memset_grid": 3.19e6}}
 
@@ -620,6 +622,25 @@ def run_gpu(args):
                          "fp32_frac": per_launch_flops[name] / a / 1e12 / FP32_PEAK_TFLOPS,
                          "int_mul_frac": per_launch_muls[name] / a / 1e12 / INT_MUL_PEAK_T,
                          "ncu_dram_bytes": NCU_TRAFFIC.get(w.name, {}).get(name)}
+    if "raster_scatter" in kernels:
+        kernels["raster_scatter"]["ncu_issue_active"] = NCU_ISSUE_ACTIVE.get(w.name)
+    if roof["kernel"] == "raster_scatter":
+        roof["ncu_issue_active"] = NCU_ISSUE_ACTIVE.get(w.name)
+    # the FFT convolution (a5-a7) as a whole: its three kernels' time against
+    # the bytes each pass reads and writes, and against the least any
+    # convolution must move (the grid in, the waveform out, the response)
+    conv_names = [k for k in ("fwd_rows", "wire_conv", "inv_rows") if k in kern]
+    convolution = None
+    if len(conv_names) == 3:
+        c_s = sum(kern[k][1] / kern[k][0] for k in conv_names) * 1e-3
+        pass_bytes = sum(per_launch_bytes[k] for k in conv_names)
+        min_bytes = sum(8.0 * sp.nwires * sp.nticks + 4.0 * sp.response.size for sp in w.planes)
+        convolution = {"kernels": conv_names, "ms_per_step": c_s * 1e3,
+                       "pass_bytes": pass_bytes, "hbm_frac_pass_bytes": pass_bytes / c_s / 1e9 / peak_gbs,
+                       "min_bytes": min_bytes, "hbm_frac_min_bytes": min_bytes / c_s / 1e9 / peak_gbs,
+                       "note": "pass bytes: each of the three passes reads its input and writes its output once "
+                               "(about 25 B per grid cell in all); min bytes: the grid in and the waveform out "
+                               "(8 B per grid cell) plus the response"}
 
     # end to end through the public API with host buffers: every step copies
     # its depos in from pinned host memory, replays the event's graph and
@@ -776,6 +797,7 @@ def run_gpu(args):
                                   "(traced: kernels, roofline)"},
         "two_event_overlap": two_event,
         "kernels": kernels,
+        "convolution": convolution,
         "roofline": roof,
         "gpu_launches": launches,
         "clocks": clocks,
