@@ -295,31 +295,35 @@ add_noise_kernel(const __grid_constant__ NoiseUnits U, int nfreq, int L, int64_t
     const bool edge = k == 0 || 2 * k == L;
     const S a = (S)__ldg(nz.amp + k) * (S)nz.scale;
     const S c = nz.coh ? (S)__ldg(nz.coh + k) * (S)nz.scale : (S)0;
-    int cur_g = -1;
-    C xg = mkc((S)0, (S)0);
+    // the pairs' incoherent blocks first (independent Philox chains in flight)
+    uint4 xs[kNoiseRows / 2];
 #pragma unroll
-    for (int i = 0; i < kNoiseRows; i += 2) {   // wires w0 + i, w0 + i + 1 share a block
-        if (i >= nr) break;
-        const uint4 x =
-            philox4x32_10(make_uint4(1u, (uint32_t)k, (uint32_t)((w0 + i) >> 1), nz.evpl), U.key0, U.key1);
+    for (int i = 0; i < kNoiseRows; i += 2)
+        if (i < nr) xs[i / 2] = philox4x32_10(make_uint4(1u, (uint32_t)k, (uint32_t)((w0 + i) >> 1), nz.evpl), U.key0,
+                                              U.key1);
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            if (i + h >= nr) break;
-            const C v = noise_xi<C>(x, h, edge);
-            S ax = a * v.x, ay = a * v.y;
-            if (nz.coh) {
-                const int g = (w0 + i + h) / nz.group;
-                if (g != cur_g) {
-                    const uint4 y = philox4x32_10(make_uint4(2u, (uint32_t)k, (uint32_t)(g >> 1), nz.evpl), U.key0,
-                                                  U.key1);
-                    xg = noise_xi<C>(y, g & 1, edge);
-                    cur_g = g;
+    for (int i = 0; i < kNoiseRows; ++i) {
+        if (i < nr) {
+            const C v = noise_xi<C>(xs[i / 2], i & 1, edge);
+            yv[i].x += a * v.x;
+            yv[i].y += a * v.y;
+        }
+    }
+    if (nz.coh) {
+        // the block's wires span groups g_first .. g_last (usually one)
+        int gr[kNoiseRows];
+#pragma unroll
+        for (int i = 0; i < kNoiseRows; ++i) gr[i] = (w0 + i) / nz.group;
+        for (int g = gr[0]; g <= gr[nr - 1]; ++g) {
+            const uint4 y = philox4x32_10(make_uint4(2u, (uint32_t)k, (uint32_t)(g >> 1), nz.evpl), U.key0, U.key1);
+            const C xg = noise_xi<C>(y, g & 1, edge);
+#pragma unroll
+            for (int i = 0; i < kNoiseRows; ++i) {
+                if (i < nr && gr[i] == g) {
+                    yv[i].x += c * xg.x;
+                    yv[i].y += c * xg.y;
                 }
-                ax += c * xg.x;
-                ay += c * xg.y;
             }
-            yv[i + h].x += ax;
-            yv[i + h].y += ay;
         }
     }
 #pragma unroll

@@ -692,8 +692,9 @@ raster_small_kernel(const __grid_constant__ RasterUnits U, ws_patches pt, long l
 // (block (3, wire * nticks + tick, depo, evpl)).  What is still unassigned
 // after the last in-grid bin fell off the grid and is lost; when a whole
 // axis window lies on the grid its last bin takes all that remain, so an
-// interior depo keeps exactly K.  Lane per depo; the weights are formed
-// edge by edge as the walk goes (one erfc per bin edge).
+// interior depo keeps exactly K.  Lane per depo; the wire weights are
+// formed edge by edge as the walk goes (one erfc per bin edge), the tick
+// weights once per depo into a per-lane shared-memory row.
 
 // Binomial(n, pr) for a float pr: float inversion (same operations as the
 // binomial mode's exact branch) for n <= exact_max; else the normal
@@ -756,11 +757,16 @@ __device__ __forceinline__ bool window_on_grid(float mu, float sigma, float delt
     return floorf(lo_e / delta) >= 0.f && floorf(hi_e / delta) <= (float)(nbins - 1);
 }
 
+constexpr int kMultiThreads = 128;
+constexpr int kMultiTicks = 32;   // tick weights a lane tabulates once per depo (wider patches: edge by edge)
+
 template <int MODE, int P>
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(kMultiThreads)
 raster_multinomial_kernel(const __grid_constant__ RasterUnits U, ws_patches pt) {
     using W = typename PrecT<P>::W;
     __shared__ float s_recip[kExactCap + 1];
+    __shared__ float s_wt[kMultiThreads][kMultiTicks + 1];
+    float* wtab = s_wt[threadIdx.x];
     fill_recip(s_recip);
     const int64_t total = U.dprefix[U.n];
     for (int64_t it = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; it < total;
@@ -803,6 +809,23 @@ raster_multinomial_kernel(const __grid_constant__ RasterUnits U, ws_patches pt) 
         const AxisWalk wt = axis_walk(e.mu_t, e.st, a.tick, a.nsig, e.point_t, inv_norm);
         const bool xfull = window_on_grid(e.mu_x, e.sx, a.pitch, a.nsig, e.point_x, a.nwires);
         const bool tfull = window_on_grid(e.mu_t, e.st, a.tick, a.nsig, e.point_t, a.nticks);
+        // the tick weights, once per depo when they fit the table
+        const bool tab = ntc <= kMultiTicks;
+        if (tab) {
+            if (e.point_t) {
+                wtab[0] = 1.f;
+            } else {
+                float u0, c0;
+                wt.edge(e.k0, u0, c0);
+                for (int k = e.k0; k <= e.k1; ++k) {
+                    float u1, c1;
+                    wt.edge(k + 1, u1, c1);
+                    wtab[k - e.k0] = bin_mass(u0, u1, c0, c1) * inv_norm;
+                    u0 = u1;
+                    c0 = c1;
+                }
+            }
+        }
         int rem = K;
         float Wx = 1.f;
         float ux0 = 0.f, cx0 = 0.f;
@@ -824,11 +847,13 @@ raster_multinomial_kernel(const __grid_constant__ RasterUnits U, ws_patches pt) 
             int rem2 = nj;
             float Wt = 1.f;
             float ut0 = 0.f, ct0 = 0.f;
-            if (!e.point_t) wt.edge(e.k0, ut0, ct0);
+            if (!tab && !e.point_t) wt.edge(e.k0, ut0, ct0);
             for (int k = e.k0; k <= e.k1; ++k) {
                 if (MODE == EMIT_GRID && rem2 <= 0) break;
                 float wk = 1.f;
-                if (!e.point_t) {
+                if (tab) {
+                    wk = wtab[k - e.k0];
+                } else if (!e.point_t) {
                     float ut1, ct1;
                     wt.edge(k + 1, ut1, ct1);
                     wk = bin_mass(ut0, ut1, ct0, ct1) * inv_norm;
@@ -1297,7 +1322,7 @@ static cudaError_t launch_raster_units(const RasterUnits& U, const ws_patches& p
                                        cudaStream_t s) {
     if (U.dprefix[U.n] <= 0) return cudaSuccess;
     if (U.a[0].fluct == 2) {   // every unit of a call shares its fluctuation mode
-        raster_multinomial_kernel<MODE, P><<<grid_for(U.dprefix[U.n], 128, 16), 128, 0, s>>>(U, p);
+        raster_multinomial_kernel<MODE, P><<<grid_for(U.dprefix[U.n], kMultiThreads, 16), kMultiThreads, 0, s>>>(U, p);
         return cudaGetLastError();
     }
     const int64_t groups = U.gprefix[U.n];
