@@ -77,3 +77,26 @@ def test_null_arguments_rejected_without_device_work(lib):
     # workspace missing -> WS_ERR_WORKSPACE before any CUDA call
     assert lib.ws_plane_create(ctypes.byref(d), ctypes.c_void_p(256), None, 0, None, ctypes.byref(h)) == 6
     assert lib.ws_status_string(2) == b"unsupported size"
+
+
+def test_impact_planes_in_the_planner(lib):
+    """Impact planes: the fine grid (nwires*I x nticks floats) and I times the
+    spectra and response spectra; more than 32 positions and FP64 buffers
+    with impacts are refused before any device work."""
+    from paper_2203_02479_gb300 import wiresim
+    plain = wiresim.ws_plane_workspace_bytes(_desc())
+    imp = wiresim.ws_plane_workspace_bytes(_desc(impacts=10))
+    extra = 960 * 10 * 6000 * 4 + 9 * 960 * 3136 * 8 + 9 * 21 * 3136 * 8
+    assert extra <= imp - plain < extra + 1024 * 1024
+    assert wiresim.ws_plane_workspace_bytes(_desc(impacts=1)) == plain
+    for kw, code in ((dict(impacts=33), 1), (dict(impacts=-1), 1), (dict(impacts=4, fp64=1), 2)):
+        with pytest.raises(wiresim.WiresimError) as ei:
+            wiresim.ws_plane_workspace_bytes(_desc(**kw))
+        assert ei.value.status == code
+
+
+def test_new_entry_points_reject_null_planes(lib):
+    """ws_plane_set_noise, like every entry point, answers a null plane with
+    WS_ERR_INVALID_ARG and touches no device."""
+    assert lib.ws_plane_set_noise(None, None, None, 0, None) == 1
+    assert lib.ws_convolve_noalloc(None, None, None, None, None) == 1
