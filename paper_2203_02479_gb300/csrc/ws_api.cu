@@ -240,14 +240,13 @@ ws::RasterArgs raster_args(const ws_plane* pl, const ws_depos* d, const ws_param
 }
 
 // The plane's noise term for one simulation call (false: no noise set).
-bool noise_unit(const ws_plane* pl, const ws_params* p, uint32_t event_id, ws::NoiseUnit* nz) {
+bool noise_unit(const ws_plane* pl, uint32_t event_id, ws::NoiseUnit* nz) {
     if (pl->noise_mode == 0) return false;
     nz->amp = pl->noise_amp;
     nz->coh = pl->noise_mode == 2 ? pl->noise_amp + pl->fstride : nullptr;
     nz->group = pl->noise_group;
     nz->evpl = (event_id << 4) | ((uint32_t)pl->desc.plane_id & 15u);
     nz->scale = 1.0 / (double)pl->plan.L;
-    (void)p;
     return true;
 }
 
@@ -255,7 +254,7 @@ bool noise_unit(const ws_plane* pl, const ws_params* p, uint32_t event_id, ws::N
 // path) if the plane has noise set.
 ws_status add_plane_noise(ws_plane* pl, const ws_params* p, void* Y, bool fp64, cudaStream_t s) {
     ws::NoiseBatch nb;
-    if (!noise_unit(pl, p, p->event_id, &nb.noise[0])) return WS_OK;
+    if (!noise_unit(pl, p->event_id, &nb.noise[0])) return WS_OK;
     nb.n = 1;
     nb.Y[0] = Y;
     nb.nwires[0] = pl->desc.nwires;
@@ -905,7 +904,7 @@ ws_status batch_waves(ws_plane* const* planes, int nplanes, const ws_depos* depo
             ib.nrows[j] = pl->desc.nwires;
             nb.Y[j] = Y;
             nb.nwires[j] = pl->desc.nwires;
-            if (noise_unit(pl, params, pe.event_id, &nb.noise[j])) noisy = true;
+            if (noise_unit(pl, pe.event_id, &nb.noise[j])) noisy = true;
             else nb.noise[j] = ws::NoiseUnit{};
         }
         WS_LAUNCH(p0, K_MEMSET, s, ws::launch_zero_grids(rb, counts, s));
