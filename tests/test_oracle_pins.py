@@ -428,3 +428,46 @@ def test_oracle_matches_its_golden_fixtures():
         N, p = head.split()
         got = oracle.binomial_invert(int(N), float(p), words)
         assert list(got) == [int(c) for c in counts.split()], (N, p)
+
+
+def test_convolution_parseval_against_a_direct_dft():
+    """Circular mode (Eq. 2 on the grid): sum M^2 equals (1/N) sum over the
+    2D spectrum of |S_hat R_hat|^2, with both spectra from an explicit DFT
+    matrix (not the FFT the oracle uses)."""
+    rng = np.random.Generator(np.random.PCG64(51))
+    nw, nt = 6, 10
+    S = rng.standard_normal((nw, nt))
+    R = rng.standard_normal((3, 4))
+    M = oracle.convolve_fft(S, R, 1, circular=True)
+    Rc = np.zeros((nw, nt))
+    for r in range(3):
+        for j in range(4):
+            Rc[(r - 1) % nw, j % nt] += R[r, j]
+    Fw = np.exp(-2j * np.pi * np.outer(np.arange(nw), np.arange(nw)) / nw)
+    Ft = np.exp(-2j * np.pi * np.outer(np.arange(nt), np.arange(nt)) / nt)
+    Sh = Fw @ S @ Ft.T
+    Rh = Fw @ Rc @ Ft.T
+    assert abs(np.sum(M ** 2) - np.sum(np.abs(Sh * Rh) ** 2) / (nw * nt)) < 1e-9 * np.sum(M ** 2)
+
+
+def test_gaussian_convolved_with_gaussian_stays_gaussian():
+    """Sampled Gaussians of variances a and b (wire and tick axes) convolve
+    into the sampled Gaussian of variance a + b, scaled by the product of
+    the normalisations; the discrete sum differs from the continuous one by
+    terms of order exp(-2 pi^2 ab/(a+b)), far below double precision here."""
+    nw, nt = 64, 160
+    a_w, a_t, b_w, b_t = 2.0 ** 2, 3.0 ** 2, 1.5 ** 2, 4.0 ** 2
+    w = np.arange(nw)[:, None]
+    t = np.arange(nt)[None, :]
+    S = np.exp(-(w - 30) ** 2 / (2 * a_w) - (t - 60) ** 2 / (2 * a_t))
+    kw, kt, c = 21, 81, 10               # response kept to 6.7 sigma in wires, 10 sigma in ticks
+    r = np.arange(kw)[:, None] - c
+    j = np.arange(kt)[None, :] - 40      # tick offset j - 40, handled by shifting the answer
+    R = np.exp(-r ** 2 / (2 * b_w) - j ** 2 / (2 * b_t))
+    M = oracle.convolve_fft(S, R, c)
+    cw = 2 * np.pi * a_w * b_w / (a_w + b_w)
+    ct = 2 * np.pi * a_t * b_t / (a_t + b_t)
+    expect = np.sqrt(cw * ct) * np.exp(-(w - 30) ** 2 / (2 * (a_w + b_w)) - (t - 100) ** 2 / (2 * (a_t + b_t)))
+    # away from the edges, where the response's truncation and the grid clip nothing
+    sl = (slice(15, 45), slice(60, 140))
+    assert np.max(np.abs(M[sl] - expect[sl])) < 1e-9 * np.max(expect)
