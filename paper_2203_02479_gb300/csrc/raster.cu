@@ -347,10 +347,11 @@ __device__ __forceinline__ int find_unit64(const long long* prefix, int n, long 
 
 constexpr int kSmallT = 16;  // largest patch (ticks x wires) the lane-per-depo kernel takes
 constexpr int kSmallW = 8;
+constexpr int kWideW = 32;   // the same for planes binned at pitch / I (impact positions)
 
-template <typename W>
+template <int SW, typename W>
 __device__ __forceinline__ bool is_large(const ExtentT<W>& e) {
-    return (e.k1 - e.k0 + 1) > kSmallT || (e.w1 - e.w0 + 1) > kSmallW;
+    return (e.k1 - e.k0 + 1) > kSmallT || (e.w1 - e.w0 + 1) > SW;
 }
 
 template <typename W>
@@ -363,7 +364,7 @@ __device__ __forceinline__ W window_norm(const RasterArgs& a) {
 // the list's (unit, depo) entries if they fit in it, else every depo of
 // every unit whose patch is large.  The last block to finish resets the
 // list counter for the next launch.
-template <int MODE, int P>
+template <int MODE, int P, int SW>
 __global__ void __launch_bounds__(32 * kWarpsPerBlock)
 raster_kernel(const __grid_constant__ RasterUnits U, ws_patches pt, const long long* __restrict__ list,
               unsigned* list_count, unsigned list_cap, unsigned* done, int cdf_rows) {
@@ -407,7 +408,7 @@ raster_kernel(const __grid_constant__ RasterUnits U, ws_patches pt, const long l
         W q;
         bool bad;
         const bool any = depo_extent<W>(a, i, &e, &q, &bad);
-        if (!(any && is_large(e))) continue;  // not handed over
+        if (!(any && is_large<SW>(e))) continue;  // not handed over
         int64_t off = 0;
         int ntf = 0;
         if (MODE == EMIT_PATCH) {
@@ -503,7 +504,7 @@ __device__ __forceinline__ void lane_weights(const RasterArgs& a, W mu, W sigma,
 constexpr int kRoundPerLane = 2;   // bins per lane per binomial round
 constexpr int kBinMap = 1024;    // bins of a depo group addressed through a byte map (else a search)
 
-template <int MODE, int P>
+template <int MODE, int P, int SW>
 __global__ void __launch_bounds__(32 * kSmallWarpsPerBlock, 7)
 raster_small_kernel(const __grid_constant__ RasterUnits U, ws_patches pt, long long* __restrict__ list,
                     unsigned* list_count, unsigned list_cap, int cdf_rows) {
@@ -511,7 +512,7 @@ raster_small_kernel(const __grid_constant__ RasterUnits U, ws_patches pt, long l
     constexpr int NW = kSmallWarpsPerBlock;
     constexpr int G = kSmallGroup;
     __shared__ W s_wt[NW][G][kSmallT + 1];
-    __shared__ W s_wx[NW][G][kSmallW + 1];
+    __shared__ W s_wx[NW][G][SW + 1];
     __shared__ int s_off[NW][G];     // inclusive scan of the depos' bin counts
     __shared__ int s_k0[NW][G];
     __shared__ int s_w0[NW][G];
@@ -544,7 +545,7 @@ raster_small_kernel(const __grid_constant__ RasterUnits U, ws_patches pt, long l
         bool bad = false, any = false;
         if (i < a.n) any = depo_extent<W>(a, i, &e, &q, &bad);
         if (bad) atomicOr(a.status, WS_DEV_BAD_DEPO);
-        const bool large = any && is_large(e);
+        const bool large = any && is_large<SW>(e);
         if (large) {
             const unsigned slot = atomicAdd(list_count, 1u);
             if (slot < list_cap) list[slot] = ((long long)uu << 40) | (long long)i;
@@ -1317,6 +1318,15 @@ static RasterUnits raster_units(const RasterBatch& rb) {
     return U;
 }
 
+template <int MODE, int P, int SW>
+static cudaError_t launch_raster_pair(const RasterUnits& U, const ws_patches& p, const LargeList& L, int rows,
+                                      size_t dyn, int blocks, cudaStream_t s) {
+    raster_small_kernel<MODE, P, SW><<<blocks, 32 * kSmallWarpsPerBlock, dyn, s>>>(U, p, L.list, L.count, L.cap, rows);
+    raster_kernel<MODE, P, SW><<<num_sms() * 2, 32 * kWarpsPerBlock, dyn, s>>>(U, p, L.list, L.count, L.cap, L.done,
+                                                                           rows);
+    return cudaGetLastError();
+}
+
 template <int MODE, int P>
 static cudaError_t launch_raster_units(const RasterUnits& U, const ws_patches& p, const LargeList& L,
                                        cudaStream_t s) {
@@ -1332,10 +1342,11 @@ static cudaError_t launch_raster_units(const RasterUnits& U, const ws_patches& p
     const RasterArgs& a0 = U.a[0];
     const int rows = (a0.fluct && !a0.keep_all && a0.T != 0u) ? (a0.exact_max < kExactCap ? a0.exact_max : kExactCap) : 0;
     const size_t dyn = sizeof(float) * (size_t)rows * (rows + 1) / 2;
-    raster_small_kernel<MODE, P><<<blocks, 32 * kSmallWarpsPerBlock, dyn, s>>>(U, p, L.list, L.count, L.cap, rows);
-    raster_kernel<MODE, P><<<num_sms() * 2, 32 * kWarpsPerBlock, dyn, s>>>(U, p, L.list, L.count, L.cap, L.done,
-                                                                         rows);
-    return cudaGetLastError();
+    // a launch's units are all fine-pitch (impact) planes or none is
+    if constexpr (P == 0) {
+        if (a0.wide) return launch_raster_pair<MODE, P, kWideW>(U, p, L, rows, dyn, blocks, s);
+    }
+    return launch_raster_pair<MODE, P, kSmallW>(U, p, L, rows, dyn, blocks, s);
 }
 
 cudaError_t launch_raster_scatter_batch(const RasterBatch& rb, const LargeList& L, cudaStream_t s) {

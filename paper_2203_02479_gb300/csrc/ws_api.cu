@@ -218,6 +218,7 @@ ws::RasterArgs raster_args(const ws_plane* pl, const ws_depos* d, const ws_param
     a.evpl = (p->event_id << 4) | ((uint32_t)pl->desc.plane_id & 15u);
     a.keep_all = p->p_survive >= 1.0 ? 1 : 0;
     a.exact_max = p->fluct_exact_max;
+    a.wide = pl->impacts > 1 ? 1 : 0;
     {
         const float pf = a.p;
         a.inv_flip = pf > 0.5f ? 1 : 0;

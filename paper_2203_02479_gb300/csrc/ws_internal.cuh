@@ -45,6 +45,7 @@ struct RasterArgs {
     uint32_t key0, key1;  // Philox key from the seed
     uint32_t evpl;        // (event_id << 4) | plane_id
     int exact_max;        // N <= exact_max: CDF inversion; above: normal approximation
+    int wide;             // grid binned at pitch / I (impact planes): wider lane-per-depo patches
     // CDF inversion on s = min(p, 1-p) (float): r = s / (1 - s), base = 1 - s
     float inv_r, inv_base;
     int inv_flip;         // p > 1/2: the search counts losses, k = N - k'
