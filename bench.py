@@ -349,7 +349,21 @@ def batched_workload_comparison(wiresim, dev, stream, flush, steps: int):
             "batched_ms": g, "per_plane_ms": pp}
 
 
-def noise_leg(wiresim, dev, stream, flush, steps: int, units_per_wave: int, plain_ms: float):
+def _profiled_once(step, enabled: bool):
+    """One more step bracketed by cudaProfilerStart/Stop (for an ncu launch
+    list taken with --profile-from-start off)."""
+    if not enabled:
+        return
+    import torch
+    torch.cuda.synchronize()
+    torch.cuda.profiler.start()
+    step()
+    torch.cuda.synchronize()
+    torch.cuda.profiler.stop()
+
+
+def noise_leg(wiresim, dev, stream, flush, steps: int, units_per_wave: int, plain_ms: float,
+              profile: bool = False, wire_conv_variant: int = -1):
     """The benchmark event with the noise term of Eq. 1 switched on (an
     incoherent spectrum per wire plus a coherent one per group of 32 wires,
     synthetic shapes), replayed from a CUDA graph like the timed step."""
@@ -359,6 +373,8 @@ def noise_leg(wiresim, dev, stream, flush, steps: int, units_per_wave: int, plai
     L = planes[0].info.fft_len_tick
     for pl in planes:
         pl.set_noise(inputs.noise_amplitudes(L), inputs.noise_amplitudes(L, "coherent"), 32)
+        if wire_conv_variant >= 0:
+            pl.set_wire_conv_variant(wire_conv_variant)
     depos = [wiresim.DeviceDepos.from_plane_depos(d, device=dev) for d in w.events[0]]
     params = wiresim.Params(fluctuate=w.fluctuate, p_survive=w.p_survive, seed=w.seed)
     b = wiresim.Batch(planes, [depos], params, units_per_wave=units_per_wave, device=dev)
@@ -367,6 +383,7 @@ def noise_leg(wiresim, dev, stream, flush, steps: int, units_per_wave: int, plai
         b.replay()
     torch.cuda.synchronize(dev)
     ms = sorted(_time_steps(b.replay, steps, stream, flush))[steps // 2]
+    _profiled_once(b.replay, profile)
     ndp = sum(d.n for d in w.events[0])
     for pl in planes:
         pl.close()
@@ -376,13 +393,17 @@ def noise_leg(wiresim, dev, stream, flush, steps: int, units_per_wave: int, plai
                      "and the inverse transform (one more launch per wave)"}
 
 
-def multinomial_leg(wiresim, dev, stream, flush, steps: int, units_per_wave: int, plain_ms: float):
+def multinomial_leg(wiresim, dev, stream, flush, steps: int, units_per_wave: int, plain_ms: float,
+                    profile: bool = False, wire_conv_variant: int = -1):
     """The benchmark event with the charge-conserving fluctuation
     (fluctuate = 2: binomial survivors per depo, multinomial split over the
     patch), replayed from a CUDA graph like the timed step."""
     import torch
     w = make_workload("three_planes", 0)
     planes = [wiresim.Plane(sp.nwires, sp.nticks, sp.response, plane_id=sp.plane_id, device=dev) for sp in w.planes]
+    if wire_conv_variant >= 0:
+        for pl in planes:
+            pl.set_wire_conv_variant(wire_conv_variant)
     depos = [wiresim.DeviceDepos.from_plane_depos(d, device=dev) for d in w.events[0]]
     params = wiresim.Params(fluctuate=2, p_survive=w.p_survive, seed=w.seed)
     b = wiresim.Batch(planes, [depos], params, units_per_wave=units_per_wave, device=dev)
@@ -391,6 +412,7 @@ def multinomial_leg(wiresim, dev, stream, flush, steps: int, units_per_wave: int
         b.replay()
     torch.cuda.synchronize(dev)
     ms = sorted(_time_steps(b.replay, steps, stream, flush))[steps // 2]
+    _profiled_once(b.replay, profile)
     # the raster stage alone, traced
     planes[0].trace(steps * 16 + 16)
     for _ in range(steps):
@@ -408,7 +430,7 @@ def multinomial_leg(wiresim, dev, stream, flush, steps: int, units_per_wave: int
             "raster_ms_per_launch": rms / max(rn, 1)}
 
 
-def impacts_leg(wiresim, dev, stream, flush, steps: int, impacts: int = 10):
+def impacts_leg(wiresim, dev, stream, flush, steps: int, impacts: int = 10, profile: bool = False):
     """The benchmark event on planes whose response depends on the charge's
     position inside the pitch (10 sub-pitch positions, synthetic slices):
     the raster bins the pitch axis at pitch/10 and the forward transform
@@ -430,6 +452,7 @@ def impacts_leg(wiresim, dev, stream, flush, steps: int, impacts: int = 10):
         step()
     torch.cuda.synchronize(dev)
     ms = sorted(_time_steps(step, steps, stream, flush))[steps // 2]
+    _profiled_once(step, profile)
     for pl in planes:
         pl.trace(16 * steps + 16)
     for _ in range(steps):
@@ -759,10 +782,11 @@ def run_gpu(args):
         batched = batched_workload_comparison(wiresim, dev, stream, flush, max(3, min(args.steps, 10)))
         adjoint = adjoint_leg(wiresim, dev, stream, flush, max(5, min(args.steps, 50)))
         noise = noise_leg(wiresim, dev, stream, flush, max(5, min(args.steps, 200)), upw_event,
-                          sorted(graph_ms)[len(graph_ms) // 2])
-        impacts = impacts_leg(wiresim, dev, stream, flush, max(5, min(args.steps, 50)))
+                          sorted(graph_ms)[len(graph_ms) // 2], args.profile_legs, args.wire_conv_variant)
+        impacts = impacts_leg(wiresim, dev, stream, flush, max(5, min(args.steps, 50)), profile=args.profile_legs)
         multinomial = multinomial_leg(wiresim, dev, stream, flush, max(5, min(args.steps, 200)), upw_event,
-                                      sorted(graph_ms)[len(graph_ms) // 2])
+                                      sorted(graph_ms)[len(graph_ms) // 2], args.profile_legs,
+                                      args.wire_conv_variant)
     if rank != 0:
         if dist is not None:
             dist.destroy_process_group()
@@ -833,6 +857,9 @@ def main():
                     help="force the event's wave size (default: picked by timing)")
     ap.add_argument("--profile-timed", action="store_true",
                     help="bracket the timed graph replays with cudaProfilerStart/Stop (for ncu --profile-from-start off)")
+    ap.add_argument("--profile-legs", action="store_true",
+                    help="bracket one more step of the noise, impact and multinomial legs with "
+                         "cudaProfilerStart/Stop (for ncu --profile-from-start off)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "wiresim":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
