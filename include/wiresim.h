@@ -180,25 +180,32 @@ typedef struct {
                                    blocks (8, 9); 4..9 linear mode only     */
     int32_t row_fft_fixed_shape; /* 1: this L_t's FP32 tick-axis transforms
                                    run kernels compiled for its radix plan
-                                   (first and last passes on global memory);
-                                   0: the generic kernels                   */
+                                   (each row pair fetched into shared memory
+                                   by bulk copies, first and middle passes
+                                   in place, the last pass writing global
+                                   memory); 0: the generic kernels          */
 } ws_plane_info;
 
 typedef struct ws_plane ws_plane;
 
 /* Bytes of device workspace a plane with this description needs (response
  * spectrum, twiddles, two spectra of nwires x (L_t/2+1) complex64, status
- * word and scan scratch).  Host-only; fails with WS_ERR_UNSUPPORTED_SIZE if
- * the FFT length is not 2/3/5-smooth or exceeds 14336. */
+ * word, scan scratch, noise spectra; with impacts I > 1 also the fine grid
+ * of nwires*I x nticks floats and I times the first spectrum and the
+ * response spectrum).  Host-only; fails with WS_ERR_UNSUPPORTED_SIZE if the
+ * FFT length is not 2/3/5-smooth or exceeds 14336, or for FP64 buffers on an
+ * impact plane, and with WS_ERR_INVALID_ARG for impacts outside 0 .. 32. */
 ws_status ws_plane_workspace_bytes(const ws_plane_desc* desc, size_t* bytes);
 
 /* Create a plane over a caller-owned device workspace (>= the size above,
  * 256-byte aligned) and compute the response spectrum once (the transform
  * of R in Eq. 2) on `stream`.  It also autotunes the wire-convolution
  * kernel by timing its variants on the plane's buffers, which SYNCHRONISES
- * `stream` once.  response_dev: K_w x K_t float32, row-major,
- * row r holding wire offset r - resp_wire_center, column j tick offset j
- * (causal).  The response is read during this call's stream work only.
+ * `stream` once (impact planes have one wire-convolution kernel and skip
+ * it).  response_dev: K_w x K_t float32, row-major, row r holding wire
+ * offset r - resp_wire_center, column j tick offset j (causal); on an
+ * impact plane I such slices, slice i first-index-major.  The response is
+ * read during this call's stream work only.
  * The plane object itself is host memory, freed by ws_plane_destroy. */
 ws_status ws_plane_create(const ws_plane_desc* desc, const float* response_dev,
                           void* workspace_dev, size_t workspace_bytes, void* stream,
@@ -217,8 +224,11 @@ ws_status ws_patch_capacity(ws_plane* plane, const ws_depos* depos, const ws_par
 /* Diffusion + raster (+ fluctuation) of every depo into its own patch
  * (Sec. 2.2 "Raster", Sec. 3.1).  A lane per depo for its geometry and
  * edge tables, its patch's bins spread over the warp (a warp per depo for
- * patches above 16 ticks x 8 wires).  Each bin holds
- * q * p * w_t * w_x (expected value) or a binomial survivor count, with
+ * patches above 16 ticks x 8 wires, 32 fine wires on impact planes, whose
+ * patches lie on the fine grid of nwires*I rows; a lane per depo for the
+ * whole patch with fluctuate = 2).  Each bin holds
+ * q * p * w_t * w_x (expected value), a binomial survivor count or its
+ * share of the depo's multinomially spread survivors (see fluctuate), with
  * w the Gaussian mass of the bin clipped to mu +- nsigma*sigma over the
  * window's total mass.  Writes out->off (exclusive scan of patch sizes),
  * w0/t0/nw/nt and val.  If the total exceeds capacity_bins the device
