@@ -569,7 +569,10 @@ struct Shape {
     // (inputs held in registers across a barrier): one shared buffer
     static constexpr bool inplace = npass == 3 && L / radix[npass == 3 ? 1 : 0] <= NT;
     static constexpr int buffers = inplace ? 1 : 2;
-    static constexpr int ctas = inplace ? 3 : 2;   // per SM
+    // CTAs per SM: one 50 KB buffer lets four 256-thread CTAs share an SM
+    // (64 registers each; the inverse measured faster so, the forward at 320
+    // threads keeps three)
+    static constexpr int ctas = inplace ? (NT <= 256 ? 4 : 3) : 2;
     // A half spectrum rounded up to 16 bytes, and a buffer that holds either
     // L complex values or two such half spectra (the rows fetched by bulk
     // copies before the first pass).
