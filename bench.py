@@ -263,9 +263,9 @@ PHILOX_MULS = 40    # 32-bit multiplies per Philox4x32-10 block: 10 rounds x 2 p
 # step's kernels (one launch per stage over the three planes; wire
 # convolution variant 9 on every plane); see profiles/.
 # the raster's share of issue slots in the same capture (it is issue-bound)
-NCU_ISSUE_ACTIVE = {"three_planes_800_800_960x6000": 0.691}
+NCU_ISSUE_ACTIVE = {"three_planes_800_800_960x6000": 0.688}
 NCU_TRAFFIC = {"three_planes_800_800_960x6000": {
-    "raster_scatter": 8.39e6, "fwd_rows": 74.5e6, "wire_conv": 94.2e6, "inv_rows": 75.6e6, "memset_grid": 3.06e6}}
+    "raster_scatter": 8.39e6, "fwd_rows": 74.5e6, "wire_conv": 94.0e6, "inv_rows": 72.1e6, "memset_grid": 3.12e6}}
 
 
 def drawing_bins(wiresim, planes, depos) -> int:
