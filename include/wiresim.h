@@ -30,6 +30,9 @@
  *     ws_plane_sync.
  *   - A plane's workspace is shared by all calls on that plane: calls on one
  *     plane must be ordered (one stream, or events between streams).
+ *   - With WS_LOG set in the environment, CUDA failures and non-zero device
+ *     status words read by ws_plane_sync are also printed to stderr.  The
+ *     simulation entry points mark their host work with NVTX ranges.
  *
  * Units: pitch in mm, time in microseconds, charge in electrons.
  * Bin conventions (the paper is silent; the oracle follows the same):

@@ -12,6 +12,8 @@
 #include <new>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "ws_internal.cuh"
 
 // Per-plane launch trace: a ring of (kernel, start event, end event) records
@@ -49,10 +51,24 @@ void trace_end(ws_plane* pl, int slot, cudaStream_t s) {
 }
 
 
+// Host logging of failures: set WS_LOG (to anything) in the environment.
+bool log_enabled() {
+    static const bool on = getenv("WS_LOG") != nullptr;
+    return on;
+}
+
 ws_status cuda_fail(cudaError_t e, const char* where) {
     snprintf(g_last_error, sizeof g_last_error, "%s: %s", where, cudaGetErrorString(e));
+    if (log_enabled()) fprintf(stderr, "wiresim: %s\n", g_last_error);
     return WS_ERR_CUDA;
 }
+
+// An NVTX range over an entry point's host work (its launches), for
+// profilers; costs nothing when no tool listens.
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+};
 
 #define WS_CUDA(call)                                   \
     do {                                                \
@@ -583,6 +599,7 @@ ws_status ws_scatter(ws_plane* pl, const ws_patches* patches, float* grid_dev, v
 }
 
 ws_status ws_convolve(ws_plane* pl, const float* grid_dev, float* out_dev, void* stream) {
+    NvtxRange range("ws_convolve");
     if (!pl || !grid_dev || !out_dev) return WS_ERR_INVALID_ARG;
     if (!aligned(grid_dev, 4) || !aligned(out_dev, 4)) return WS_ERR_INVALID_ARG;
     if (pl->impacts > 1) {   // fine input and coarse output must not overlap
@@ -597,6 +614,7 @@ ws_status ws_convolve(ws_plane* pl, const float* grid_dev, float* out_dev, void*
 
 ws_status ws_simulate(ws_plane* pl, const ws_depos* depos, const ws_params* params, float* out_dev,
                       void* stream) {
+    NvtxRange range("ws_simulate");
     if (!pl || !out_dev || !aligned(out_dev, 4)) return WS_ERR_INVALID_ARG;
     ws_status st = check_depos(depos);
     if (st == WS_OK) st = check_params(params);
@@ -685,6 +703,7 @@ ws_status ws_plane_set_response(ws_plane* pl, const float* response_dev, void* s
 ws_status ws_simulate_backward(ws_plane* pl, const ws_depos* depos, const ws_params* params,
                                const float* grad_out_dev, float* gq, float* gx, float* gt, double* gDL,
                                double* gDT, float* gR, void* stream) {
+    NvtxRange range("ws_simulate_backward");
     if (!pl || !grad_out_dev || !aligned(grad_out_dev, 4)) return WS_ERR_INVALID_ARG;
     ws_status st = check_depos(depos);
     if (st == WS_OK) st = check_params(params);
@@ -800,6 +819,7 @@ ws_status ws_batch_workspace_bytes(ws_plane* const* planes, int nplanes, int uni
 ws_status ws_simulate_batch(ws_plane* const* planes, int nplanes, const ws_depos* depos, int nevents,
                             const ws_params* params, float* const* out_dev, void* workspace_dev,
                             size_t workspace_bytes, int units_per_wave, void* stream) {
+    NvtxRange range("ws_simulate_batch");
     BatchLayout lay;
     ws_status st = batch_layout(planes, nplanes, units_per_wave, &lay);
     if (st != WS_OK) return st;
@@ -939,6 +959,9 @@ ws_status ws_plane_sync(ws_plane* pl, void* stream, uint32_t* bits) {
     WS_CUDA(cudaMemcpyAsync(&v, pl->status, sizeof v, cudaMemcpyDeviceToHost, s));
     WS_CUDA(cudaStreamSynchronize(s));
     *bits = v;
+    if (v && log_enabled())
+        fprintf(stderr, "wiresim: device status 0x%x%s%s%s\n", v, (v & WS_DEV_BAD_DEPO) ? " bad-depo" : "",
+                (v & WS_DEV_PATCH_OVERFLOW) ? " patch-overflow" : "", (v & WS_DEV_TIMEOUT) ? " timeout" : "");
     return WS_OK;
 }
 
