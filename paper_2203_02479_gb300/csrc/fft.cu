@@ -547,13 +547,15 @@ inv_rows_kernel(FftPlan plan, const cplx<S>* __restrict__ tw, const __grid_const
 // Ns are template constants: index arithmetic folds, each kernel holds only
 // its own passes (the generic kernels above carry all thirteen radices and
 // their code outgrows the instruction cache when edge passes are fused), and
-// the first and last passes talk to global memory directly:
-//   forward: pass 0 loads the two input rows; the last pass pairs butterflies
-//            j and Ns - j so that each thread holds Z_k and Z_{L-k} and
-//            writes the split spectra A_k, B_k;
-//   inverse: pass 0 reads the Hermitian extension of both half spectra; the
-//            last pass stores the real and imaginary rows.
-// Only the middle passes go through shared memory.
+// the edge passes are fused with the row I/O:
+//   forward: pass 0 reads the two input rows (fetched into shared memory by
+//            bulk copies when the launch has a status word, else loaded by
+//            every thread); the last pass pairs butterflies j and Ns - j so
+//            that each thread holds Z_k and Z_{L-k} and writes the split
+//            spectra A_k, B_k to global memory;
+//   inverse: pass 0 reads the Hermitian extension of both half spectra
+//            (fetched the same way); the last pass stores the real and
+//            imaginary rows.
 template <int NT, int... Rs>
 struct Shape {
     static constexpr int threads = NT;
