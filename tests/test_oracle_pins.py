@@ -471,3 +471,25 @@ def test_gaussian_convolved_with_gaussian_stays_gaussian():
     # away from the edges, where the response's truncation and the grid clip nothing
     sl = (slice(15, 45), slice(60, 140))
     assert np.max(np.abs(M[sl] - expect[sl])) < 1e-9 * np.max(expect)
+
+
+def test_shift_equivariance_by_whole_bins():
+    """Moving every depo by one pitch (or one tick, with given widths: the
+    diffusion widths depend on t) moves S by one wire row (one tick column);
+    the convolution (linear mode, away from the edges) follows."""
+    rng = np.random.Generator(np.random.PCG64(61))
+    nw, nt, n = 30, 400, 300
+    q = rng.exponential(5000, n)
+    x = rng.uniform(30.0, (nw - 8) * oracle.PITCH_MM, n)
+    t = rng.uniform(20.0, (nt - 60) * oracle.TICK_US, n)
+    st = rng.uniform(0.2, 2.0, n)
+    sx = rng.uniform(0.3, 3.0, n)
+    S = oracle.raster_scatter(q, x, t, nw, nt, sig_t_us=st, sig_x_mm=sx)
+    Sx = oracle.raster_scatter(q, x + oracle.PITCH_MM, t, nw, nt, sig_t_us=st, sig_x_mm=sx)
+    St = oracle.raster_scatter(q, x, t + oracle.TICK_US, nw, nt, sig_t_us=st, sig_x_mm=sx)
+    assert np.allclose(Sx[1:], S[:-1], rtol=1e-10, atol=1e-9 * S.max())
+    assert np.allclose(St[:, 1:], S[:, :-1], rtol=1e-10, atol=1e-9 * S.max())
+    R = np.random.Generator(np.random.PCG64(62)).standard_normal((21, 200))
+    M = oracle.convolve_fft(S, R, 10)
+    Mx = oracle.convolve_fft(Sx, R, 10)
+    assert np.allclose(Mx[12:-1], M[11:-2], rtol=1e-9, atol=1e-9 * np.abs(M).max())

@@ -357,3 +357,29 @@ def test_fixed_shape_row_transforms(ws, nw, nt, kt, circular, L, fixed):
     out = plane.convolve(torch.from_numpy(S).cuda())
     assert rel_l2(to_np(out), oracle.convolve_fft(S.astype(np.float64), R, 10, circular)) <= REL_L2
     assert plane.status() == 0
+
+
+def test_shift_equivariance_by_whole_bins(ws):
+    """Depos moved by one pitch (one tick, with given widths) give the grid
+    moved by one wire row (tick column), to FP32 rounding of the moved
+    coordinates."""
+    import torch
+    rng = np.random.Generator(np.random.PCG64(63))
+    nw, nt, n = 40, 1000, 2000
+    q = rng.exponential(5000, n).astype(np.float32)
+    x = rng.uniform(30.0, (nw - 8) * 5.0, n).astype(np.float32)
+    t = rng.uniform(20.0, (nt - 60) * 0.5, n).astype(np.float32)
+    st = rng.uniform(0.2, 2.0, n).astype(np.float32)
+    sx = rng.uniform(0.3, 3.0, n).astype(np.float32)
+    plane = ws.Plane(nw, nt, inputs.response("bipolar"))
+    params = ws.Params()
+
+    def grid(xx, tt):
+        d = ws.DeviceDepos(q, xx, tt, st, sx)
+        return gpu_grid_via_patches(ws, plane, d, params)[1]
+
+    S = grid(x, t)
+    Sx = grid(x + np.float32(5.0), t)
+    St = grid(x, t + np.float32(0.5))
+    assert rel_l2(Sx[1:], S[:-1]) <= 1e-6
+    assert rel_l2(St[:, 1:], S[:, :-1]) <= 1e-6
