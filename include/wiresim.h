@@ -242,7 +242,8 @@ ws_status ws_rasterize(ws_plane* plane, const ws_depos* depos, const ws_params* 
 
 /* Scatter-add of patches into a grid (Sec. 2.2 "Scatter-add"):
  * grid_dev[w][t] += val of every patch bin at (w, t).  The grid is
- * accumulated into, not cleared. */
+ * accumulated into, not cleared.  grid_dev is nwires x nticks, or on a
+ * plane with impacts I > 1 the fine grid of nwires*I x nticks. */
 ws_status ws_scatter(ws_plane* plane, const ws_patches* patches, float* grid_dev,
                      void* stream);
 

@@ -254,6 +254,27 @@ def _ptr(t) -> int:
     return 0 if t is None else int(t.data_ptr())
 
 
+def _require(t, name: str, shape, device, dtype=None):
+    """Check a tensor whose raw pointer goes to the library: the kernels
+    index it by the plane's sizes, so a tensor of another shape or dtype,
+    a strided view or one on another device would be read or written out of
+    bounds.  Raises ValueError before any call into the library."""
+    torch = _torch()
+    dtype = torch.float32 if dtype is None else dtype
+    if not hasattr(t, "data_ptr"):
+        raise ValueError(f"{name}: expected a torch tensor, got {type(t).__name__}")
+    if tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name}: expected shape {tuple(shape)}, got {tuple(t.shape)}")
+    if t.dtype != dtype:
+        raise ValueError(f"{name}: expected dtype {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name}: expected a contiguous tensor")
+    want = torch.device(device)
+    if t.device.type != want.type or (want.index is not None and t.device.index != want.index):
+        raise ValueError(f"{name}: expected a tensor on {want}, got one on {t.device}")
+    return t
+
+
 @dataclasses.dataclass
 class Params:
     """Physics and numerics of a simulation call (mirrors ``ws_params``)."""
@@ -288,9 +309,12 @@ class DeviceDepos:
 
         self.q, self.x_mm, self.t_us = dev(q), dev(x_mm), dev(t_us)
         self.sigma_t_us, self.sigma_x_mm = dev(sigma_t_us), dev(sigma_x_mm)
+        if self.q.dim() != 1:
+            raise ValueError("depo arrays must be one-dimensional")
         self.n = int(self.q.shape[0])
-        for a in (self.x_mm, self.t_us):
-            if int(a.shape[0]) != self.n:
+        # the kernels read n entries of every array given (the widths too)
+        for a in (self.x_mm, self.t_us, self.sigma_t_us, self.sigma_x_mm):
+            if a is not None and tuple(a.shape) != (self.n,):
                 raise ValueError("depo arrays differ in length")
 
     @classmethod
@@ -351,12 +375,15 @@ class Plane:
     def simulate(self, depos: DeviceDepos, params: Params, out=None, stream=None):
         if out is None:
             out = _torch().empty((self.nwires, self.nticks), dtype=_torch().float32, device=self.device)
+        _require(out, "out", (self.nwires, self.nticks), self.device)
         ws_simulate(self.handle, depos.c(), params.c(), _ptr(out), _stream_handle(stream))
         return out
 
     def convolve(self, grid, out=None, stream=None):
         if out is None:
             out = _torch().empty((self.nwires, self.nticks), dtype=_torch().float32, device=self.device)
+        _require(grid, "grid", (self.nwires * self.impacts, self.nticks), self.device)
+        _require(out, "out", (self.nwires, self.nticks), self.device)
         ws_convolve(self.handle, _ptr(grid), _ptr(out), _stream_handle(stream))
         return out
 
@@ -385,6 +412,7 @@ class Plane:
                          _ptr(p["off"]), int(p["capacity"]), int(p["n"]))
 
     def scatter(self, patches, grid, stream=None):
+        _require(grid, "grid", (self.nwires * self.impacts, self.nticks), self.device)
         ws_scatter(self.handle, self.patches_c(patches), _ptr(grid), _stream_handle(stream))
         return grid
 
@@ -397,7 +425,9 @@ class Plane:
         torch = _torch()
         if not hasattr(response, "data_ptr"):
             response = torch.from_numpy(np.ascontiguousarray(response, dtype=np.float32))
-        self.response = response.to(device=self.device, dtype=torch.float32).contiguous()
+        response = response.to(device=self.device, dtype=torch.float32).contiguous()
+        # the plane's response shape is fixed at creation (impacts x K_w x K_t or K_w x K_t)
+        self.response = _require(response, "response", tuple(self.response.shape), self.device)
         _check(load_library().ws_plane_set_response(self.handle, _ptr(self.response), _stream_handle(stream)),
                "ws_plane_set_response")
 
@@ -433,7 +463,7 @@ class Plane:
         gt = torch.empty(n, dtype=torch.float32, device=dev)
         gD = torch.zeros(2, dtype=torch.float64, device=dev)
         gR = torch.empty(tuple(self.response.shape), dtype=torch.float32, device=dev) if want_response else None
-        g = grad_out.contiguous()
+        g = _require(grad_out.contiguous(), "grad_out", (self.nwires, self.nticks), self.device)
         _check(load_library().ws_simulate_backward(
             self.handle, ctypes.byref(depos.c()), ctypes.byref(params.c()), _ptr(g), _ptr(gq), _ptr(gx), _ptr(gt),
             _ptr(gD), _ptr(gD) + 8, _ptr(gR), _stream_handle(stream)), "ws_simulate_backward")

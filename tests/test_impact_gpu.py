@@ -83,8 +83,12 @@ def test_impact_convolve_and_patches_on_the_fine_grid(ws):
     assert rel_l2(to_np(fine), S) <= 1e-6
     M = pl.convolve(fine)
     assert rel_l2(to_np(M), oracle.convolve_impacts(S, R, 10)) <= REL_L2
-    with pytest.raises(ws.WiresimError):
-        pl.convolve(fine, out=fine)           # fine input and output may not overlap
+    import torch
+    stream = torch.cuda.current_stream().cuda_stream
+    with pytest.raises(ws.WiresimError):      # the library refuses an output on the fine input
+        ws.ws_convolve(pl.handle, fine.data_ptr(), fine.data_ptr(), stream)
+    with pytest.raises(ValueError):           # the binding checks the output's shape before the call
+        pl.convolve(fine, out=fine)
 
 
 def test_impact_planes_rejected_where_unsupported(ws):

@@ -385,3 +385,26 @@ def test_shift_equivariance_by_whole_bins(ws):
     St = grid(x, t + np.float32(0.5))
     assert rel_l2(Sx[1:], S[:-1]) <= 1e-6
     assert rel_l2(St[:, 1:], S[:, :-1]) <= 1e-6
+
+
+def test_binding_checks_tensor_arguments_before_the_call(ws):
+    """Tensors of the wrong shape, dtype or layout never reach the library:
+    the binding raises ValueError first and the plane stays usable."""
+    import torch
+    R = inputs.response("bipolar")
+    plane = ws.Plane(8, 300, R)
+    with pytest.raises(ValueError, match="shape"):
+        plane.convolve(torch.zeros((8, 299), device="cuda"))
+    with pytest.raises(ValueError, match="dtype"):
+        plane.convolve(torch.zeros((8, 300), dtype=torch.float64, device="cuda"))
+    with pytest.raises(ValueError, match="contiguous"):
+        plane.convolve(torch.zeros((300, 8), device="cuda").t())
+    with pytest.raises(ValueError, match="shape"):
+        plane.set_response(R[:, :199])
+    d = ws.DeviceDepos([3000.0], [20.0], [40.0])
+    with pytest.raises(ValueError, match="shape"):
+        plane.simulate(d, ws.Params(), out=torch.empty((16, 150), device="cuda"))
+    with pytest.raises(ValueError, match="shape"):
+        plane.backward(d, ws.Params(), torch.zeros((8, 301), device="cuda"))
+    out = plane.simulate(d, ws.Params())
+    assert plane.status() == 0 and float(out.abs().sum()) > 0
