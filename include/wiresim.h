@@ -108,7 +108,8 @@ typedef struct {
 /* Depos of one event as seen by one plane: structure of arrays of float32
  * device pointers, all of length n (Sec. 2.3: the depo arrays are laid out
  * as structures of arrays).  sigma_t_us / sigma_x_mm are either both NULL
- * (widths come from diffusion, see ws_params) or both set (given widths). */
+ * (widths come from diffusion, see ws_params) or both set (given widths).
+ * Every array given is 4-byte aligned (else WS_ERR_INVALID_ARG). */
 typedef struct {
     const float* q;           /* charge [electrons]                         */
     const float* x_mm;        /* pitch position                             */
@@ -155,7 +156,8 @@ typedef struct {
  * Patch i covers wires [w0[i], w0[i]+nw[i]) and ticks [t0[i], t0[i]+nt[i])
  * of the grid (already clipped to it); its values are val[off[i] ...
  * off[i] + nw[i]*nt[i]) row-major [wire][tick].  off has n + 1 entries,
- * off[n] being the total number of bins. */
+ * off[n] being the total number of bins.  Every array is aligned to its
+ * element size (else WS_ERR_INVALID_ARG). */
 typedef struct {
     float* val;
     int32_t* w0;
@@ -351,8 +353,9 @@ ws_status ws_plane_set_response(ws_plane* plane, const float* response_dev, void
  * patch is recomputed, not stored.  Derivatives of the clamped-edge bin
  * weights hold everywhere except where a window bound crosses a bin edge.
  * Any output pointer may be NULL to skip it (gR == NULL skips the
- * response-gradient work).  All outputs are device pointers; uses the
- * plane's workspace. */
+ * response-gradient work).  All outputs are device pointers aligned to
+ * their element size (else WS_ERR_INVALID_ARG); uses the plane's
+ * workspace. */
 ws_status ws_simulate_backward(ws_plane* plane, const ws_depos* depos, const ws_params* params,
                                const float* grad_out_dev, float* gq, float* gx, float* gt,
                                double* gDL, double* gDT, float* gR, void* stream);

@@ -190,12 +190,20 @@ ws_status plan_layout(const ws_plane_desc* d, Layout* lay) {
 
 bool aligned(const void* p, size_t a) { return ((uintptr_t)p & (a - 1)) == 0; }
 
+// Patch arrays are read and written as their element types (a null pointer
+// counts as aligned; the callers check which may be null).
+bool patches_aligned(const ws_patches* p) {
+    return aligned(p->val, 4) && aligned(p->w0, 4) && aligned(p->t0, 4) && aligned(p->nw, 4) && aligned(p->nt, 4) &&
+           aligned(p->off, 8);
+}
+
 ws_status check_depos(const ws_depos* d) {
     if (!d || d->n < 0) return WS_ERR_INVALID_ARG;
     if (d->n == 0) return WS_OK;
     if (!d->q || !d->x_mm || !d->t_us) return WS_ERR_INVALID_ARG;
     if ((d->sigma_t_us == nullptr) != (d->sigma_x_mm == nullptr)) return WS_ERR_INVALID_ARG;
     if (!aligned(d->q, 4) || !aligned(d->x_mm, 4) || !aligned(d->t_us, 4)) return WS_ERR_INVALID_ARG;
+    if (d->sigma_t_us && (!aligned(d->sigma_t_us, 4) || !aligned(d->sigma_x_mm, 4))) return WS_ERR_INVALID_ARG;
     if (d->n > ((int64_t)1 << 32)) return WS_ERR_UNSUPPORTED_SIZE;  // depo index is a 32-bit counter word
     return WS_OK;
 }
@@ -578,6 +586,7 @@ ws_status ws_rasterize(ws_plane* pl, const ws_depos* depos, const ws_params* par
     if (out->n != depos->n || out->capacity_bins < 0 || !out->off) return WS_ERR_INVALID_ARG;
     if (depos->n > 0 && (!out->w0 || !out->t0 || !out->nw || !out->nt)) return WS_ERR_INVALID_ARG;
     if (out->capacity_bins > 0 && !out->val) return WS_ERR_INVALID_ARG;
+    if (!patches_aligned(out)) return WS_ERR_INVALID_ARG;
     if ((depos->n + 1 + 4095) / 4096 > ws::kScanScratch) return WS_ERR_UNSUPPORTED_SIZE;
     cudaStream_t s = (cudaStream_t)stream;
     ws::RasterArgs a = raster_args(pl, depos, params);
@@ -591,7 +600,7 @@ ws_status ws_scatter(ws_plane* pl, const ws_patches* patches, float* grid_dev, v
     if (!pl || !patches || !grid_dev || patches->n < 0) return WS_ERR_INVALID_ARG;
     if (patches->n > 0 && (!patches->off || !patches->w0 || !patches->t0 || !patches->nw || !patches->nt))
         return WS_ERR_INVALID_ARG;
-    if (!aligned(grid_dev, 4)) return WS_ERR_INVALID_ARG;
+    if (!aligned(grid_dev, 4) || !patches_aligned(patches)) return WS_ERR_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     WS_LAUNCH(pl, K_SCATTER, s, ws::launch_scatter_patches(*patches, grid_dev, pl->desc.nwires * pl->impacts,
                                                           pl->desc.nticks, s));
@@ -709,6 +718,9 @@ ws_status ws_simulate_backward(ws_plane* pl, const ws_depos* depos, const ws_par
     if (st == WS_OK) st = check_params(params);
     if (st != WS_OK) return st;
     if (params->fluctuate) return WS_ERR_INVALID_ARG;  // the adjoint is of the expected-value path
+    if (!aligned(gq, 4) || !aligned(gx, 4) || !aligned(gt, 4) || !aligned(gR, 4) || !aligned(gDL, 8) ||
+        !aligned(gDT, 8))
+        return WS_ERR_INVALID_ARG;
     if (pl->impacts > 1) return WS_ERR_UNSUPPORTED_SIZE;
     cudaStream_t s = (cudaStream_t)stream;
     const ws_plane_desc& d = pl->desc;
