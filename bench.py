@@ -518,8 +518,8 @@ def run_gpu(args):
             pl.set_wire_conv_variant(args.wire_conv_variant)
     flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device=dev)
     # wave size of the event's batch, picked by timing graph replays: with
-    # fewer units per wave than planes, the second wave runs on the library's
-    # second stream beside the first
+    # fewer units per wave than planes, the later waves run on the library's
+    # extra streams beside the first (wave k on stream k % 3)
     best = None
     choices = [args.units_per_wave] if args.units_per_wave > 0 else list(range(len(planes), 0, -1))
     for upw in choices:
@@ -810,8 +810,8 @@ def run_gpu(args):
                    "fft_len_tick": planes[0].info.fft_len_tick,
                    "units_per_wave": upw_event,
                    "wire_conv_variant": [pl.info.wire_conv_variant for pl in planes],
-                   "path": "ws_simulate_batch over the event's planes in waves of units_per_wave (consecutive "
-                           "waves on two streams), replayed from a CUDA graph",
+                   "path": "ws_simulate_batch over the event's planes in waves of units_per_wave (wave k on "
+                           "stream k % 3), replayed from a CUDA graph",
                    "l2": "flushed between timed steps (512 MiB write)"},
         "planes_per_s": all_planes / (total_ms * 1e-3),
         "raster_scatter_depos_per_s": all_depos / (raster_ms * 1e-3) if raster_ms > 0 else None,

@@ -287,9 +287,9 @@ ws_status ws_simulate(ws_plane* plane, const ws_depos* depos, const ws_params* p
 ws_status ws_convolve_noalloc(const ws_plane_desc* desc, const float* response_dev,
                               const float* grid_dev, float* out_dev, void* stream);
 
-/* Device workspace of ws_simulate_batch: two wave slots, each a large-patch
- * hand-over list and two spectra (max nwires x (L_t/2+1) complex64) per unit
- * of a wave.  units_per_wave: 1 .. 32. */
+/* Device workspace of ws_simulate_batch: three wave slots, each a
+ * large-patch hand-over list and two spectra (max nwires x (L_t/2+1)
+ * complex64) per unit of a wave.  units_per_wave: 1 .. 32. */
 ws_status ws_batch_workspace_bytes(ws_plane* const* planes, int nplanes, int units_per_wave,
                                    size_t* bytes);
 
@@ -305,11 +305,13 @@ ws_status ws_batch_workspace_bytes(ws_plane* const* planes, int nplanes, int uni
  * length, tick count and response shape (else WS_ERR_UNSUPPORTED_SIZE).
  * Each plane's noise term (ws_plane_set_noise) is added as in ws_simulate.
  * Results equal ws_simulate unit by unit (up to summation order).  With more
- * than one wave, odd waves run on a second stream owned by the library (one
- * per host thread and device) that forks from `stream` at the start of the
- * call and joins it at the end through events, so one wave's raster overlaps
- * the previous wave's transforms; the call stays ordered on `stream`.  Makes
- * no host synchronisation, so it can be captured into a CUDA graph. */
+ * than one wave, the waves go round `stream` and up to two more streams
+ * owned by the library (per host thread and device): wave k runs on stream
+ * k % S, S = min(waves, 3), each with its own workspace slot.  The extra
+ * streams fork from `stream` at the start of the call and join it at the
+ * end through events, so one wave's raster overlaps the other waves'
+ * transforms and the call stays ordered on `stream`.  Makes no host
+ * synchronisation, so it can be captured into a CUDA graph. */
 ws_status ws_simulate_batch(ws_plane* const* planes, int nplanes, const ws_depos* depos, int nevents,
                             const ws_params* params, float* const* out_dev, void* workspace_dev,
                             size_t workspace_bytes, int units_per_wave, void* stream);

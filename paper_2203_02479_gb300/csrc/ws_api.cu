@@ -761,8 +761,10 @@ ws_status ws_simulate_backward(ws_plane* pl, const ws_depos* depos, const ws_par
 
 namespace {
 
-// Two wave slots, each with its own counters, large-patch list and spectra,
-// so that consecutive waves run on two streams.
+// Wave slots, each with its own counters, large-patch list and spectra, so
+// that consecutive waves run on kBatchSlots streams (wave k in slot k % S).
+constexpr int kBatchSlots = 3;
+
 struct BatchLayout {
     size_t off_counters, off_list, off_spec, spec_bytes, slot_bytes, total;
 };
@@ -791,29 +793,29 @@ ws_status batch_layout(ws_plane* const* planes, int nplanes, int units_per_wave,
     lay->spec_bytes = align256(sizeof(float2) * (size_t)maxw * p0->fstride);
     lay->off_spec = o; o += 2 * (size_t)units_per_wave * lay->spec_bytes;
     lay->slot_bytes = o;
-    lay->total = 2 * o;
+    lay->total = kBatchSlots * o;
     return WS_OK;
 }
 
-// The library's second stream for this thread and device (created once, kept
-// for the life of the process).
-cudaError_t aux_stream(cudaStream_t* out) {
-    thread_local cudaStream_t streams[64] = {};
+// The library's k-th extra stream (k < kBatchSlots - 1) for this thread and
+// device (created once, kept for the life of the process).
+cudaError_t aux_stream(int k, cudaStream_t* out) {
+    thread_local cudaStream_t streams[64][kBatchSlots - 1] = {};
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
-    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
-    if (!streams[dev]) {
-        e = cudaStreamCreateWithFlags(&streams[dev], cudaStreamNonBlocking);
+    if (dev < 0 || dev >= 64 || k < 0 || k >= kBatchSlots - 1) return cudaErrorInvalidDevice;
+    if (!streams[dev][k]) {
+        e = cudaStreamCreateWithFlags(&streams[dev][k], cudaStreamNonBlocking);
         if (e != cudaSuccess) return e;
     }
-    *out = streams[dev];
+    *out = streams[dev][k];
     return cudaSuccess;
 }
 
 ws_status batch_waves(ws_plane* const* planes, int nplanes, const ws_depos* depos, const ws_params* params,
                       float* const* out_dev, char* ws_base, const BatchLayout& lay, int units_per_wave, int nunits,
-                      cudaStream_t s0, cudaStream_t s1);
+                      const cudaStream_t* ss, int nstreams);
 
 }  // namespace
 
@@ -847,36 +849,44 @@ ws_status ws_simulate_batch(ws_plane* const* planes, int nplanes, const ws_depos
         if (st != WS_OK) return st;
         if (!out_dev[u] || !aligned(out_dev[u], 4)) return WS_ERR_INVALID_ARG;
     }
-    cudaStream_t s0 = (cudaStream_t)stream;
-    // Waves alternate between the caller's stream and the library's second
-    // stream (slot k % 2): one wave's raster runs beside the other's
-    // transforms.  Fork and join go through events, so the call stays
-    // stream-ordered for the caller and can be captured into a graph.
+    if (nunits == 0) return WS_OK;
+    // Waves go round the caller's stream and the library's extra streams
+    // (wave k in slot k % S, S = min(waves, kBatchSlots)): one wave's raster
+    // runs beside the others' transforms.  Fork and join go through events,
+    // so the call stays stream-ordered for the caller and can be captured
+    // into a graph.
     const int nwaves = (nunits + units_per_wave - 1) / units_per_wave;
-    const bool two = nwaves > 1;
-    cudaStream_t s1 = s0;
-    cudaEvent_t fork = nullptr, join = nullptr;
-    if (two) {
-        WS_CUDA(aux_stream(&s1));
-        WS_CUDA(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
-        cudaError_t e = cudaEventCreateWithFlags(&join, cudaEventDisableTiming);
-        if (e == cudaSuccess) e = cudaEventRecord(fork, s0);
-        if (e == cudaSuccess) e = cudaStreamWaitEvent(s1, fork, 0);
+    const int nstreams = nwaves < kBatchSlots ? nwaves : kBatchSlots;
+    cudaStream_t ss[kBatchSlots];
+    for (int k = 0; k < kBatchSlots; ++k) ss[k] = (cudaStream_t)stream;
+    cudaEvent_t fork = nullptr, join[kBatchSlots] = {};
+    auto release = [&]() {
+        if (fork) cudaEventDestroy(fork);
+        for (int k = 0; k < kBatchSlots; ++k)
+            if (join[k]) cudaEventDestroy(join[k]);
+    };
+    if (nstreams > 1) {
+        cudaError_t e = cudaEventCreateWithFlags(&fork, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventRecord(fork, ss[0]);
+        for (int k = 1; k < nstreams && e == cudaSuccess; ++k) {
+            e = aux_stream(k - 1, &ss[k]);
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&join[k], cudaEventDisableTiming);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(ss[k], fork, 0);
+        }
         if (e != cudaSuccess) {
-            cudaEventDestroy(fork);
-            if (join) cudaEventDestroy(join);
+            release();
             return cuda_fail(e, "batch fork");
         }
     }
     ws_status wst = batch_waves(planes, nplanes, depos, params, out_dev, (char*)workspace_dev, lay, units_per_wave,
-                                nunits, s0, s1);
-    if (two) {
-        cudaError_t e = cudaEventRecord(join, s1);
-        if (e == cudaSuccess) e = cudaStreamWaitEvent(s0, join, 0);
-        cudaEventDestroy(fork);
-        cudaEventDestroy(join);
-        if (e != cudaSuccess && wst == WS_OK) return cuda_fail(e, "batch join");
+                                nunits, ss, nstreams);
+    cudaError_t e = cudaSuccess;
+    for (int k = 1; k < nstreams; ++k) {
+        if (e == cudaSuccess) e = cudaEventRecord(join[k], ss[k]);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(ss[0], join[k], 0);
     }
+    release();
+    if (e != cudaSuccess && wst == WS_OK) return cuda_fail(e, "batch join");
     return wst;
 }
 
@@ -886,16 +896,16 @@ namespace {
 
 ws_status batch_waves(ws_plane* const* planes, int nplanes, const ws_depos* depos, const ws_params* params,
                       float* const* out_dev, char* ws_base, const BatchLayout& lay, int units_per_wave, int nunits,
-                      cudaStream_t s0, cudaStream_t s1) {
+                      const cudaStream_t* ss, int nstreams) {
     ws_plane* p0 = planes[0];
     const ws_plane_desc& d0 = p0->desc;
     const int circ = d0.conv_mode == WS_CONV_CIRCULAR;
-    for (int slot = 0; slot < 2; ++slot)
-        WS_CUDA(cudaMemsetAsync(ws_base + slot * lay.slot_bytes + lay.off_counters, 0, 256, slot ? s1 : s0));
+    for (int slot = 0; slot < nstreams; ++slot)
+        WS_CUDA(cudaMemsetAsync(ws_base + slot * lay.slot_bytes + lay.off_counters, 0, 256, ss[slot]));
     for (int u0 = 0, wave = 0; u0 < nunits; u0 += units_per_wave, ++wave) {
         const int nu = nunits - u0 < units_per_wave ? nunits - u0 : units_per_wave;
-        const int slot = wave & 1;
-        cudaStream_t s = slot ? s1 : s0;
+        const int slot = wave % nstreams;
+        cudaStream_t s = ss[slot];
         char* base = ws_base + slot * lay.slot_bytes;
         ws::LargeList L;
         L.list = (long long*)(base + lay.off_list);
