@@ -21,6 +21,7 @@
 //      narrower than an eighth of a bin take their edge differences in FP64;
 //   2  FP64: widths, bin ranges, weights, values, binomial tail and the grid
 //      in double.
+#include <atomic>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -1294,13 +1295,18 @@ int grid_for(int64_t items, int per_block, int blocks_per_sm) {
 
 }  // namespace
 
+// SM count of the current device, cached per device (any thread may ask).
+// Only grid sizes depend on it and every kernel sized by it strides over its
+// work, so if the query fails (the next launch then reports the error) one
+// is returned and nothing is cached.
 int num_sms() {
-    static int n = 0;
-    if (n == 0) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 132;
-    }
+    static std::atomic<int> cache[64];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 1;
+    int n = cache[dev].load(std::memory_order_relaxed);
+    if (n > 0) return n;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) return 1;
+    cache[dev].store(n, std::memory_order_relaxed);
     return n;
 }
 
