@@ -184,10 +184,11 @@ def algorithmic_bytes(kernel: str, nw: int, nt: int, nfreq: int, kw: int, ndepo:
 _ORACLE_NEXT = [0]
 
 
-def oracle_sample(w, budget_s: float):
+def oracle_sample(w, budget_s: float, keep=None):
     """Run the FP64 oracle over the workload's planes (cycling through them
     across calls) for about budget_s seconds, at least one plane; returns
-    (depo-planes processed, seconds, planes)."""
+    (depo-planes processed, seconds, planes).  keep: a dict that receives
+    the first waveform computed for each plane index (event 0)."""
     import oracle
     done = 0
     planes = 0
@@ -198,13 +199,32 @@ def oracle_sample(w, budget_s: float):
         sp = w.planes[i % len(w.planes)]
         d = w.events[0][i % len(w.planes)]
         S = oracle.raster_scatter(d.q, d.x_mm, d.t_us, sp.nwires, sp.nticks, fluctuate=w.fluctuate,
-                                  p=w.p_survive, seed=w.seed, plane_id=sp.plane_id)
-        oracle.convolve_fft(S, sp.response, 10)
+                                  p=w.p_survive, seed=w.seed, event_id=0, plane_id=sp.plane_id)
+        M = oracle.convolve_fft(S, sp.response, 10)
+        if keep is not None and i % len(w.planes) not in keep:
+            keep[i % len(w.planes)] = M
         done += d.n
         planes += 1
         if time.perf_counter() - t0 >= budget_s:
             break
     return done, time.perf_counter() - t0, planes
+
+
+def oracle_error_of(gpu_out, kept, w):
+    """Error of the timed event's waveforms against the FP64 oracle for the
+    planes the CPU baseline computed: relative L2 over the plane and the
+    largest absolute difference over the largest |M|.  Fluctuated events
+    use the same counters on both sides; bins where FP32 and FP64 round
+    q w to different electron counts differ by one electron."""
+    out = []
+    for i in sorted(kept):
+        M = kept[i]
+        diff = gpu_out[i].astype(np.float64) - M
+        out.append({"plane_id": w.planes[i].plane_id,
+                    "rel_l2": float(np.linalg.norm(diff) / max(np.linalg.norm(M), 1e-300)),
+                    "max_abs_over_max": float(np.abs(diff).max() / max(np.abs(M).max(), 1e-300))})
+    return {"planes": out, "mode": "binomial" if w.fluctuate else "expected value",
+            "note": "same seed and counters as the GPU; FP32 on the GPU against FP64"}
 
 
 def run_reference(args):
@@ -589,6 +609,10 @@ def run_gpu(args):
     _barrier(dist)
     clocks = sampler.stop() if sampler else None
     total_ms = _max_over_ranks(dist, float(sum(graph_ms)), dev)
+    # the event's waveforms as the timed graph left them, for the error
+    # against the oracle (rank 0 at N = 1, beside the CPU baseline)
+    check_oracle = world == 1 and not args.no_cpu_baseline
+    gpu_out = [o.cpu().numpy() for o in batch.outs] if check_oracle else None
 
     # per-kernel algorithmic work (sum over the event's planes per launch)
     kern = {name: [n, ms] for name, (n, ms) in stats.items()}
@@ -794,10 +818,13 @@ def run_gpu(args):
     value = all_depos / (total_ms * 1e-3)
     raster_ms = kern.get("raster_scatter", [0, 0.0])[1] + kern.get("memset_grid", [0, 0.0])[1]
     cpu = None
-    if world == 1 and not args.no_cpu_baseline:
-        done, secs, nplanes = oracle_sample(w, args.cpu_seconds)
+    oracle_error = None
+    if check_oracle:
+        kept = {}
+        done, secs, nplanes = oracle_sample(w, args.cpu_seconds, keep=kept)
         cpu = {"value": done / secs, "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": f"{nplanes} planes of this event ({done} depo-planes), FP64, single thread"}
+        oracle_error = oracle_error_of(gpu_out, kept, w)
     pp = sum(pp_ms) / len(pp_ms)
     sl = sum(stream_ms) / len(stream_ms)
     line = {
@@ -807,6 +834,7 @@ def run_gpu(args):
         "config": {"workload": w.name, "depos_per_event": ev[0].n, "planes": len(planes),
                    "wires": [sp.nwires for sp in w.planes], "nticks": w.planes[0].nticks,
                    "fluctuate": w.fluctuate, "p_survive": w.p_survive,
+                   "seed": w.seed, "event_id": rank,
                    "fft_len_tick": planes[0].info.fft_len_tick,
                    "units_per_wave": upw_event,
                    "wire_conv_variant": [pl.info.wire_conv_variant for pl in planes],
@@ -827,6 +855,9 @@ def run_gpu(args):
         "clocks": clocks,
         "e2e": e2e,
         "cpu_baseline": cpu,
+        "oracle_error": oracle_error,
+        "gpu": torch.cuda.get_device_name(dev),
+        "host_cores": os.cpu_count(),
         "batched_workload": batched,
         "adjoint": adjoint,
         "noise": noise,
