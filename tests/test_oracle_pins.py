@@ -33,13 +33,15 @@ def _curand():
     return None
 
 
-def _curand_host_words(lib, seed, nwords):
+def _curand_host_words(lib, seed, nwords, offset=0):
     gen = ctypes.c_void_p()
     philox4_32_10 = 161  # CURAND_RNG_PSEUDO_PHILOX4_32_10
     if lib.curandCreateGeneratorHost(ctypes.byref(gen), philox4_32_10) != 0:
         pytest.skip("cuRAND host generator unavailable")
     try:
         assert lib.curandSetPseudoRandomGeneratorSeed(gen, ctypes.c_ulonglong(seed)) == 0
+        if offset:
+            assert lib.curandSetGeneratorOffset(gen, ctypes.c_ulonglong(offset)) == 0
         out = np.zeros(nwords, dtype=np.uint32)
         assert lib.curandGenerate(gen, out.ctypes.data_as(ctypes.c_void_p),
                                   ctypes.c_size_t(nwords)) == 0
@@ -62,6 +64,27 @@ def test_philox_matches_curand_host_generator(seed):
     for b in blocks:
         got = oracle.philox([b // 65536, 0, b % 65536, 0], key)
         assert (got == words[b]).all(), (seed, b, got, words[b])
+
+
+@pytest.mark.parametrize("seed", [3, 0xFEDCBA9876543210])
+def test_philox_second_counter_word_matches_curand(seed):
+    """The same generator started 2^50 words in (block 2^48 of its stream)
+    runs counters whose word 1 is not zero: block b of the stream is
+    Philox(((b // 65536) mod 2^32, (b // 65536) >> 32, b % 65536, 0)).  With
+    word 1 set and word 3 zero, a mix-up of the two words in the round
+    function fails here (the pin above has both zero)."""
+    lib = _curand()
+    if lib is None:
+        pytest.skip("libcurand not found")
+    key = oracle.seed_key(seed)
+    for first in (2 ** 48, 2 ** 48 + 65536 * 5 + 3, 3 * 2 ** 48 + 77):
+        words = _curand_host_words(lib, seed, 4 * 8, offset=4 * first).reshape(-1, 4)
+        for j in range(8):
+            b = first + j
+            c = [(b // 65536) & 0xFFFFFFFF, (b // 65536) >> 32, b % 65536, 0]
+            assert c[1] != 0
+            got = oracle.philox(c, key)
+            assert (got == words[j]).all(), (seed, b, got, words[j])
 
 
 def test_philox_counter_words_all_matter():
