@@ -210,6 +210,30 @@ def test_edge_cases(ws):
     torch.cuda.synchronize()
 
 
+def test_bad_given_widths_are_skipped_and_flagged(ws):
+    """Given widths that are NaN, negative or infinite make the depo invalid:
+    it is skipped and the status word says so; the valid depos are
+    simulated as the oracle does."""
+    nw, nt = 20, 400
+    plane = ws.Plane(nw, nt, inputs.response())
+    q = [100.0, 200.0, 300.0, 400.0, 500.0]
+    x = [10.0, 30.0, 50.0, 70.0, 80.0]
+    t = [20.0, 40.0, 60.0, 80.0, 100.0]
+    st = [1.0, np.nan, -0.5, 1.5, 0.8]
+    sx = [2.0, 1.0, 1.0, -np.inf, 3.0]
+    out = to_np(plane.simulate(ws.DeviceDepos(q, x, t, st, sx), ws.Params()))
+    assert plane.status() & ws.WS_DEV_BAD_DEPO
+    keep = [0, 4]
+    ref = oracle.simulate([q[i] for i in keep], [x[i] for i in keep], [t[i] for i in keep], nw, nt,
+                          inputs.response(), 10, sig_t_us=[st[i] for i in keep], sig_x_mm=[sx[i] for i in keep])
+    assert rel_l2(out, ref) <= REL_L2
+    plane.clear_status()
+    good = ws.DeviceDepos([q[i] for i in keep], [x[i] for i in keep], [t[i] for i in keep],
+                          [st[i] for i in keep], [sx[i] for i in keep])
+    assert rel_l2(to_np(plane.simulate(good, ws.Params())), out) <= 1e-6
+    assert plane.status() == 0
+
+
 def test_patch_capacity_overflow_is_flagged(ws):
     nw, nt = 30, 600
     d = inputs.uniform_depos(50, nw, seed=24, nticks=nt)
