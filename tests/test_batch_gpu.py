@@ -129,3 +129,20 @@ def test_batch_rejects_mismatched_planes(ws):
     with pytest.raises(ws.WiresimError) as ei:
         ws.Batch([p1, p2], [[d, d]], ws.Params())
     assert ei.value.status == 2
+
+
+def test_batch_of_no_events_and_one_wave_per_plane(ws):
+    """No events: nothing is enqueued.  One plane per wave over more waves
+    than streams (wave k on stream k % 3) equals one wave of everything."""
+    import torch
+    planes, events, _ = _setup(ws, [200, 0, 900, 50], seed=110)
+    assert ws.Batch(planes, [], ws.Params()).run() == []
+    params = ws.Params(fluctuate=True, p_survive=0.7, seed=9)
+    one = [o.clone() for o in ws.Batch(planes, events, params, units_per_wave=12).run()]
+    many = ws.Batch(planes, events, params, units_per_wave=1).run()
+    torch.cuda.synchronize()
+    assert len(one) == len(many) == 12
+    for a, b in zip(one, many):
+        assert rel(b.cpu().numpy(), a.cpu().numpy()) <= 1e-6
+    for pl in planes:
+        assert pl.status() == 0
