@@ -432,3 +432,36 @@ def test_binding_checks_tensor_arguments_before_the_call(ws):
         plane.backward(d, ws.Params(), torch.zeros((8, 301), device="cuda"))
     out = plane.simulate(d, ws.Params())
     assert plane.status() == 0 and float(out.abs().sum()) > 0
+
+
+def test_three_planes_in_the_benchmark_launch_configuration(ws):
+    """The benchmark's step at full size: the three-plane event (100k track
+    depos, binomial fluctuation) through ws_simulate_batch captured into a
+    CUDA graph and replayed, one plane per wave on three streams (the
+    schedule the benchmark picks), and two or three planes per wave;
+    waveforms against the oracle's."""
+    import torch
+    w = inputs.three_planes()
+    planes = [ws.Plane(sp.nwires, sp.nticks, sp.response, plane_id=sp.plane_id) for sp in w.planes]
+    depos = [ws.DeviceDepos.from_plane_depos(d) for d in w.events[0]]
+    params = ws.Params(fluctuate=True, p_survive=w.p_survive, seed=w.seed)
+    outs = {}
+    for upw in (1, 2, 3):
+        b = ws.Batch(planes, [depos], params, units_per_wave=upw)
+        b.capture()
+        for o in b.outs:
+            o.fill_(float("nan"))
+        b.replay()
+        b.replay()
+        torch.cuda.synchronize()
+        outs[upw] = [o.cpu().numpy() for o in b.outs]
+    for p, (sp, d) in enumerate(zip(w.planes, w.events[0])):
+        S = oracle.raster_scatter(d.q, d.x_mm, d.t_us, sp.nwires, sp.nticks, fluctuate=True,
+                                  p=w.p_survive, seed=w.seed, plane_id=sp.plane_id)
+        M = oracle.convolve_fft(S, sp.response, 10)
+        for upw in (1, 2, 3):
+            assert np.isfinite(outs[upw][p]).all()
+            assert rel_l2(outs[upw][p], M) <= 1e-3, (upw, p)
+            assert rel_l2(outs[upw][p], outs[1][p]) <= 1e-6
+    for pl in planes:
+        assert pl.status() == 0
