@@ -219,6 +219,9 @@ ws_status ws_plane_create(const ws_plane_desc* desc, const float* response_dev,
 /* Free the host plane object; the workspace stays the caller's. */
 ws_status ws_plane_destroy(ws_plane* plane);
 
+/* The plane's plan (ws_plane_info: transform length and radices, spectrum
+ * stride, workspace size, chosen wire-convolution kernel) into *info.
+ * Host-only; WS_ERR_INVALID_ARG for a NULL plane or info. */
 ws_status ws_plane_get_info(const ws_plane* plane, ws_plane_info* info);
 
 /* Exact number of in-grid patch bins ws_rasterize will write for these
@@ -400,6 +403,7 @@ ws_status ws_plane_trace_read(ws_plane* plane, ws_trace_stat* stats, int max_sta
  * The context stays usable.  Stream-ordered, no host synchronisation. */
 ws_status ws_selftest_bounded_wait(uint32_t* status_dev, int iters, unsigned long long* cycles_dev, void* stream);
 
+/* Static text naming a status code ("unknown status" for other values). */
 const char* ws_status_string(ws_status status);
 
 /* Text of the last CUDA error seen by a ws_* call on this thread ("" if

@@ -77,6 +77,10 @@ def test_null_arguments_rejected_without_device_work(lib):
     # workspace missing -> WS_ERR_WORKSPACE before any CUDA call
     assert lib.ws_plane_create(ctypes.byref(d), ctypes.c_void_p(256), None, 0, None, ctypes.byref(h)) == 6
     assert lib.ws_status_string(2) == b"unsupported size"
+    assert lib.ws_status_string(99) == b"unknown status"
+    from paper_2203_02479_gb300 import wiresim
+    info = wiresim.WsPlaneInfo()
+    assert lib.ws_plane_get_info(None, ctypes.byref(info)) == 1
 
 
 def test_impact_planes_in_the_planner(lib):
