@@ -516,3 +516,40 @@ def test_shift_equivariance_by_whole_bins():
     M = oracle.convolve_fft(S, R, 10)
     Mx = oracle.convolve_fft(Sx, R, 10)
     assert np.allclose(Mx[12:-1], M[11:-2], rtol=1e-9, atol=1e-9 * np.abs(M).max())
+
+
+def test_patch_extents_by_scanning_every_bin():
+    """Brute force on a small grid: a bin belongs to a depo's patch when its
+    interval overlaps the window mu +- 3 sigma with positive length (the
+    Gaussian density is positive there, so the bin's mass is), or, for a
+    point charge, when it holds mu.  Scanning every bin must give exactly the
+    oracle's extents (floor-and-clamp arithmetic), for depos inside, across
+    and outside the grid edges; the total is the sum of the patch sizes."""
+    nw, nt, pitch, tick = 16, 60, 5.0, 0.5
+    rng = np.random.Generator(np.random.PCG64(404))
+    n = 400
+    x = rng.uniform(-25.0, nw * pitch + 25.0, n)
+    t = rng.uniform(-5.0, nt * tick + 5.0, n)
+    sx = rng.uniform(0.05, 4.0, n)
+    st = rng.uniform(0.02, 1.5, n)
+    sx[:20] = 1e-9                     # point charges along the wire axis
+    st[20:40] = 1e-9                   # and along ticks
+    w0, nwp, t0, ntp, total = oracle.patch_extents(x, t, nw, nt, sig_t_us=st, sig_x_mm=sx)
+
+    def scan(mu, sigma, delta, nbins):
+        if sigma <= 1e-6 * delta:
+            hit = [b for b in range(nbins) if b * delta <= mu < (b + 1) * delta]
+        else:
+            lo, hi = mu - 3.0 * sigma, mu + 3.0 * sigma
+            hit = [b for b in range(nbins) if min((b + 1) * delta, hi) - max(b * delta, lo) > 0.0]
+        return (hit[0], len(hit)) if hit else (None, 0)
+
+    for i in range(n):
+        bw, cw = scan(x[i], sx[i], pitch, nw)
+        bt, ct = scan(t[i], st[i], tick, nt)
+        if cw == 0 or ct == 0:
+            assert nwp[i] * ntp[i] == 0, i
+            continue
+        assert (w0[i], nwp[i], t0[i], ntp[i]) == (bw, cw, bt, ct), i
+    assert total == int(np.sum(nwp.astype(np.int64) * ntp))
+    assert 0 < np.count_nonzero(nwp * ntp) < n      # some depos fall off the grid
