@@ -62,3 +62,17 @@ def test_impact_response_shape_and_symmetry():
     assert R.shape == (10, 21, 200)
     # mirrored sub-positions are mirrored in the wire offset
     assert np.allclose(R[0], R[9][::-1], atol=1e-7)
+
+
+def test_simulate_impacts_with_equal_slices_is_the_plain_simulation():
+    """The whole impact path with every slice equal to R: the fine rows of a
+    wire sum to its coarse bin, so sum_i R (*) S_i = R (*) S, the plain
+    simulation, in both convolution modes (expected value, p = 0.8)."""
+    nw, nt, I = 12, 300, 4
+    R = inputs.response("bipolar")
+    RI = np.ascontiguousarray(np.broadcast_to(R, (I,) + R.shape))
+    d = inputs.uniform_depos(80, nw, seed=31, nticks=nt)
+    for circular in (False, True):
+        got = oracle.simulate_impacts(d.q, d.x_mm, d.t_us, nw, nt, RI, 10, circular=circular, p=0.8)
+        ref = oracle.simulate(d.q, d.x_mm, d.t_us, nw, nt, R, 10, circular=circular, p=0.8)
+        assert np.linalg.norm(got - ref) <= 1e-12 * np.linalg.norm(ref)
