@@ -45,3 +45,23 @@ def test_oracle_sample_keeps_one_waveform_per_plane_and_reports_error():
     assert rep["planes"][0]["rel_l2"] <= 1e-7
     assert abs(rep["planes"][1]["max_abs_over_max"] - 0.5) <= 1e-6
     assert rep["planes"][1]["rel_l2"] > 1e-3
+
+
+def test_algorithmic_bytes_of_the_three_plane_step():
+    """Per-launch minimum bytes of each stage over the event's three planes
+    (800 + 800 + 960 rows of 6000 ticks, 3126 frequencies, 21 response
+    wires), against the hand count: the forward reads a 4 B cell and writes
+    an 8 B frequency per row, the wire convolution reads and writes the
+    spectra and reads each plane's 21-row response spectrum, the inverse
+    the reverse of the forward."""
+    import bench
+    rows, nt, nf, kw = 2560, 6000, 3126, 21
+    tot = {k: sum(bench.algorithmic_bytes(k, nw, nt, nf, kw, 100_000) for nw in (800, 800, 960))
+           for k in ("fwd_rows", "wire_conv", "inv_rows", "memset_grid", "raster_scatter")}
+    assert tot["fwd_rows"] == rows * (4 * nt + 8 * nf)
+    assert tot["inv_rows"] == rows * (8 * nf + 4 * nt)
+    assert tot["wire_conv"] == rows * 16 * nf + 3 * 8 * nf * kw
+    assert tot["memset_grid"] == rows * nt * 4
+    assert tot["raster_scatter"] == 3 * 12 * 100_000 + rows * nt * 4
+    # the convolution's pass bytes as the benchmark line reports them
+    assert tot["fwd_rows"] + tot["wire_conv"] + tot["inv_rows"] == 380_537_424
