@@ -1,38 +1,46 @@
 #!/usr/bin/env python
 """Throughput of the signal-simulation hot path on one GB300 (or N, weak scaling).
 
-A step simulates one event on the three-plane detector (800/800/960 wires x
-6000 ticks, 100,000 track depos, binomial fluctuation with survival 0.7):
-for every plane, diffusion + raster + fluctuation + scatter-add into the
-grid, then the FFT convolution with that plane's response.  The metric is
-depos per second through the whole path (a depo counts once per plane it is
-simulated on), with planes per second and the raster+scatter-only rate
-reported beside it.
+A step simulates the batched workload: 64 events on the three-plane detector
+(800/800/960 wires x 6000 ticks), each with a log-uniform number of track
+depos between 1,000 and 500,000 (10.9 M depo-planes in all), with binomial
+fluctuation at survival 0.7.  For every (event, plane) unit: diffusion +
+raster + fluctuation + scatter-add into the grid, then the FFT convolution
+with that plane's response (Eq. 1, Eq. 2).  The whole step is one
+``ws_simulate_batch`` call (waves of units, the wave size picked by the
+library's autotuner) replayed from a CUDA graph.  The metric is depos per
+second through the whole path (a depo counts once per plane it is simulated
+on), with planes per second beside it.
 
 Prints ONE JSON line (rank 0).  ``--impl reference`` times the FP64 oracle
 on the host cores instead (the CPU baseline arm).
 
-Timing: the event's batch (wave size picked by timing) is captured into a
-CUDA graph; W untimed warm-up replays; then K replays, each bracketed by
-CUDA events on the launching stream, with L2 flushed (a 512 MiB write)
-between steps, outside the events; barrier + synchronize on both sides; the
-max over ranks.  Per-kernel device times come from the library's own launch
-trace (CUDA events around every launch, on the launching stream) over K
-steps of the same event launched one stage at a time.
+Timing: W untimed warm-up replays; then K replays, each bracketed by CUDA
+events on the launching stream, with L2 flushed (a 512 MiB write) between
+steps, outside the events (a step's buffers, ~5 GB, exceed L2 anyway);
+barrier + synchronize on both sides; the max over ranks.  Per-kernel device
+times come from the library's own launch trace (CUDA events around every
+launch, on the launching stream) over the same step launched one wave at a
+time on one stream.  SM clocks and throttle reasons are sampled with
+nvidia-smi during the timed region.
 
-Under torchrun each rank simulates its own event (its own seed and event id):
-the units are independent, so there is no collective on the data path, only
-the barrier and the max/sum reductions of the timing (weak scaling).
+Under torchrun each rank simulates its own 64 events (its own seeds and
+event ids): the units are independent, so there is no collective on the data
+path, only the barrier and the max/sum reductions of the timing (weak
+scaling).
 """
 from __future__ import annotations
 
 import argparse
+import concurrent.futures as cf
+import glob
+import hashlib
 import json
 import os
 import statistics
 import subprocess
 import sys
-import tempfile
+import threading
 import time
 
 import numpy as np
@@ -44,8 +52,11 @@ from paper_2203_02479_gb300 import inputs  # noqa: E402
 
 METRIC = "depos/sec and planes/sec (raster+scatter+FFT conv) at 1 GB300; % of HBM roofline"
 UNIT = "depos/s"
-FP32_LANES_PER_SM = 128
 NUM_SMS_GB300 = 152
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # 152 SMs x 128 FP32 lanes x FMA x max SM clock
+INT_MUL_PEAK_T = 152 * 64 * 2.070e9 / 1e12          # 152 SMs x 64 INT32 multiply lanes x max SM clock
+PHILOX_MULS = 40    # 32-bit multiplies per Philox4x32-10 block: 10 rounds x 2 products x (low, high)
+WORKLOADS = ("batched", "three_planes", "single_plane", "large")
 
 
 def _peaks():
@@ -58,43 +69,88 @@ def _peaks():
         return 6800.0, 2070.0, "fallback"
 
 
+def kernel_source_hash() -> str:
+    """Hash of the CUDA sources (the same on every machine that builds them):
+    ncu figures taken from one build are published only while it matches."""
+    h = hashlib.sha256()
+    for p in sorted(glob.glob(os.path.join(ROOT, "paper_2203_02479_gb300", "csrc", "*"))):
+        with open(p, "rb") as f:
+            h.update(os.path.basename(p).encode() + b"\0" + f.read())
+    return h.hexdigest()[:16]
+
+
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) and
+# issue-slot shares from ncu captures of the named workload's kernels, valid
+# for the kernel sources whose hash is given (see profiles/); published as
+# null once the sources change.
+NCU = {
+    "source_hash": None,
+    "workloads": {},
+}
+
+
+def ncu_figures(workload: str):
+    """(traffic by kernel, issue-active by kernel, note) for the running build."""
+    if NCU["source_hash"] is None or NCU["source_hash"] != kernel_source_hash():
+        return {}, {}, "no ncu capture of the current kernel sources"
+    w = NCU["workloads"].get(workload, {})
+    return w.get("traffic", {}), w.get("issue_active", {}), w.get("note", "")
+
+
 # ------------------------------------------------------------------ clocks
 class ClockSampler:
-    """nvidia-smi samples of SM clock and throttle reasons while running."""
+    """nvidia-smi samples of SM clock and throttle reasons, each stamped on
+    arrival; ``window()`` keeps the samples taken inside a time window (or
+    the two nearest to it when the window is shorter than the period)."""
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, gpu_index: int):
+    def __init__(self, gpu_index: int, period_ms: int = 50):
+        self.rows = []
         self.proc = None
-        self.tmp = tempfile.NamedTemporaryFile(prefix="clocks_", suffix=".csv", delete=False)
+        self.thread = None
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(gpu_index), f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "50"],
-                stdout=self.tmp, stderr=subprocess.DEVNULL)
+                 "--format=csv,noheader,nounits", "-lms", str(period_ms)],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except Exception:
             self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                self.rows.append((time.perf_counter(), parts))
+
+    def wait_first(self, timeout_s: float = 5.0):
+        t0 = time.perf_counter()
+        while self.proc is not None and not self.rows and time.perf_counter() - t0 < timeout_s:
+            time.sleep(0.01)
 
     def stop(self):
-        if self.proc is None:
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            if self.thread is not None:
+                self.thread.join(timeout=5)
+
+    def window(self, t0: float, t1: float):
+        if not self.rows:
             return None
-        self.proc.terminate()
-        try:
-            self.proc.wait(timeout=5)
-        except Exception:
-            self.proc.kill()
-        self.tmp.close()
-        rows = []
-        with open(self.tmp.name) as f:
-            for line in f:
-                parts = [p.strip() for p in line.split(",")]
-                if len(parts) >= 9:
-                    rows.append(parts)
-        os.unlink(self.tmp.name)
-        if not rows:
-            return None
+        inside = [r for t, r in self.rows if t0 <= t <= t1 + 0.06]
+        if not inside:
+            before = [r for t, r in self.rows if t < t0]
+            after = [r for t, r in self.rows if t > t1]
+            inside = before[-1:] + after[:1]
 
         def num(x):
             try:
@@ -102,17 +158,20 @@ class ClockSampler:
             except ValueError:
                 return None
 
-        sm = [num(r[1]) for r in rows if num(r[1]) is not None]
-        mx = [num(r[2]) for r in rows if num(r[2]) is not None]
+        sm = [num(r[1]) for r in inside if num(r[1]) is not None]
+        mx = [num(r[2]) for r in inside if num(r[2]) is not None]
+        pw = [num(r[3]) for r in inside if num(r[3]) is not None]
         reasons = set()
         names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
-        for r in rows:
+        for r in inside:
             for name, v in zip(names, r[5:9]):
                 if v.strip().lower() == "active":
                     reasons.add(name)
         return {"sm_mhz": statistics.median(sm) if sm else None,
                 "sm_max_mhz": max(mx) if mx else None,
-                "reasons": sorted(reasons), "samples": len(rows)}
+                "power_w_max": max(pw) if pw else None,
+                "reasons": sorted(reasons), "samples": len(inside),
+                "window_s": t1 - t0}
 
 
 # ------------------------------------------------------------ distributed
@@ -156,11 +215,22 @@ def _sum_over_ranks(dist, value: float, device) -> float:
 
 # -------------------------------------------------------------- workloads
 def make_workload(name: str, rank: int):
+    """The named synthetic workload; rank r > 0 draws its own inputs (weak
+    scaling: same sizes, other seeds)."""
+    if name == "batched":
+        return inputs.batched_events(seed=1002 + 7919 * rank)
     if name == "three_planes":
         return inputs.three_planes(seed=1001 + 7919 * rank)
     if name == "single_plane":
         return inputs.single_plane(seed=1000 + 7919 * rank)
+    if name == "large":
+        return inputs.large_planes(seed=1004 + 7919 * rank)
     raise SystemExit(f"unknown workload {name}")
+
+
+def workload_units(w):
+    """(event, plane) units of a workload in event-major order."""
+    return [(e, p) for e in range(len(w.events)) for p in range(len(w.planes))]
 
 
 def algorithmic_bytes(kernel: str, nw: int, nt: int, nfreq: int, kw: int, ndepo: int) -> float:
@@ -180,125 +250,6 @@ def algorithmic_bytes(kernel: str, nw: int, nt: int, nfreq: int, kw: int, ndepo:
     return 0.0
 
 
-# ------------------------------------------------------------------ oracle
-_ORACLE_NEXT = [0]
-
-
-def oracle_sample(w, budget_s: float, keep=None):
-    """Run the FP64 oracle over the workload's planes (cycling through them
-    across calls) for about budget_s seconds, at least one plane; returns
-    (depo-planes processed, seconds, planes).  keep: a dict that receives
-    the first waveform computed for each plane index (event 0)."""
-    import oracle
-    done = 0
-    planes = 0
-    t0 = time.perf_counter()
-    while True:
-        i = _ORACLE_NEXT[0]
-        _ORACLE_NEXT[0] += 1
-        sp = w.planes[i % len(w.planes)]
-        d = w.events[0][i % len(w.planes)]
-        S = oracle.raster_scatter(d.q, d.x_mm, d.t_us, sp.nwires, sp.nticks, fluctuate=w.fluctuate,
-                                  p=w.p_survive, seed=w.seed, event_id=0, plane_id=sp.plane_id)
-        M = oracle.convolve_fft(S, sp.response, 10)
-        if keep is not None and i % len(w.planes) not in keep:
-            keep[i % len(w.planes)] = M
-        done += d.n
-        planes += 1
-        if time.perf_counter() - t0 >= budget_s:
-            break
-    return done, time.perf_counter() - t0, planes
-
-
-def oracle_error_of(gpu_out, kept, w):
-    """Error of the timed event's waveforms against the FP64 oracle for the
-    planes the CPU baseline computed: relative L2 over the plane and the
-    largest absolute difference over the largest |M|.  Fluctuated events
-    use the same counters on both sides; bins where FP32 and FP64 round
-    q w to different electron counts differ by one electron."""
-    out = []
-    for i in sorted(kept):
-        M = kept[i]
-        diff = gpu_out[i].astype(np.float64) - M
-        out.append({"plane_id": w.planes[i].plane_id,
-                    "rel_l2": float(np.linalg.norm(diff) / max(np.linalg.norm(M), 1e-300)),
-                    "max_abs_over_max": float(np.abs(diff).max() / max(np.abs(M).max(), 1e-300))})
-    return {"planes": out, "mode": "binomial" if w.fluctuate else "expected value",
-            "note": "same seed and counters as the GPU; FP32 on the GPU against FP64"}
-
-
-def run_reference(args):
-    world, rank, _ = _dist()
-    if rank != 0:
-        return
-    w = make_workload(args.workload, 0)
-    # a step is one plane of the event through the oracle (~0.5 s on one
-    # thread); warm-up and timed steps stop early once the time budget is
-    # spent so that any --steps ends within a few minutes
-    t_start = time.perf_counter()
-    for _ in range(args.warmup):
-        oracle_sample(w, 0.0)
-        if time.perf_counter() - t_start > 0.2 * args.reference_seconds:
-            break
-    t0 = time.perf_counter()
-    done = 0
-    planes = 0
-    steps = 0
-    for _ in range(args.steps):
-        d, _, p = oracle_sample(w, 0.0)   # one plane per step
-        done += d
-        planes += p
-        steps += 1
-        if time.perf_counter() - t0 > args.reference_seconds:
-            break
-    dt = time.perf_counter() - t0
-    value = done / dt
-    line = {
-        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
-        "steps": steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / steps,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic",
-        "config": {"workload": w.name, "sample": "one plane of the event per step (cycling U, V, W)",
-                   "depos_per_plane": w.events[0][0].n, "steps_requested": args.steps,
-                   "time_budget_s": args.reference_seconds},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": f"{steps} steps (of {args.steps} requested, {args.reference_seconds:.0f} s "
-                                   f"budget) x one plane of {w.events[0][0].n} depos"},
-        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
-        "planes_per_s": planes / dt,
-    }
-    print(json.dumps(line), flush=True)
-
-
-# -------------------------------------------------------------------- main
-FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # 152 SMs x 128 FP32 lanes x FMA x max SM clock
-INT_MUL_PEAK_T = 152 * 64 * 2.070e9 / 1e12          # 152 SMs x 64 INT32 multiply lanes x max SM clock
-PHILOX_MULS = 40    # 32-bit multiplies per Philox4x32-10 block: 10 rounds x 2 products x (low, high)
-
-# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from
-# one ncu capture of the three-plane step with one launch per stage over the
-# three planes (the configuration of the per-kernel table), as of the current
-# kernels.
-# DRAM bytes per launch (read + write) from one ncu --set full capture of the
-# step's kernels (one launch per stage over the three planes; wire
-# convolution variant 9 on every plane); see profiles/.
-# the raster's share of issue slots in the same capture (it is issue-bound)
-NCU_ISSUE_ACTIVE = {"three_planes_800_800_960x6000": 0.688}
-NCU_TRAFFIC = {"three_planes_800_800_960x6000": {
-    "raster_scatter": 8.39e6, "fwd_rows": 74.5e6, "wire_conv": 94.0e6, "inv_rows": 72.1e6, "memset_grid": 3.12e6}}
-
-
-def drawing_bins(wiresim, planes, depos) -> int:
-    """Bins that draw one Philox block in binomial mode: in-grid bins holding
-    N = floor(q w + 1/2) >= 1 electrons, counted on the expected-value
-    patches of the same depos."""
-    n = 0
-    for pl, dd in zip(planes, depos):
-        pt = pl.rasterize(dd, wiresim.Params(p_survive=1.0))
-        n += int((pt["val"][:pt["capacity"]] >= 0.5).sum().item())
-    return n
-
-
 def algorithmic_flops(kernel: str, nw: int, nt: int, L: int, nfreq: int, kw: int) -> float:
     """FP32 flops a kernel's step needs by the usual count, per launch on one
     plane: 5 L log2 L per complex L-point FFT (two real rows per transform),
@@ -311,6 +262,152 @@ def algorithmic_flops(kernel: str, nw: int, nt: int, L: int, nfreq: int, kw: int
     return 0.0
 
 
+# ------------------------------------------------------------------ oracle
+def oracle_unit(w, e: int, p: int):
+    """The FP64 oracle's waveform of unit (event e, plane p): raster,
+    scatter-add (with the binomial fluctuation on the GPU's Philox counters:
+    event id e, the plane's id) and Eq. 2's convolution."""
+    import oracle
+    sp, d = w.planes[p], w.events[e][p]
+    S = oracle.raster_scatter(d.q, d.x_mm, d.t_us, sp.nwires, sp.nticks, fluctuate=w.fluctuate,
+                              p=w.p_survive, seed=w.seed, event_id=e, plane_id=sp.plane_id)
+    return oracle.convolve_fft(S, sp.response, 10)
+
+
+def sample_order(w, seed: int = 1002):
+    """The workload's units in a seeded random order (a bounded sample taken
+    from its front mixes small and large events as the workload does)."""
+    units = workload_units(w)
+    order = np.random.Generator(np.random.PCG64(seed)).permutation(len(units))
+    return [units[i] for i in order]
+
+
+def oracle_units(w, units, threads: int, budget_s: float, on_done=None):
+    """Run the oracle over ``units`` on ``threads`` host threads (the C loops
+    and numpy's FFT release the GIL) until ``budget_s`` is spent: units not
+    started by then are skipped, but each thread runs at least one.
+    Returns (depo-planes done, wall seconds to the last finish, units done);
+    ``on_done(unit, waveform)`` sees every finished waveform."""
+    t0 = time.perf_counter()
+    lock = threading.Lock()
+    st = {"dp": 0, "n": 0, "started": 0, "t_last": t0}
+
+    def work(u):
+        with lock:
+            if st["started"] >= threads and time.perf_counter() - t0 > budget_s:
+                return
+            st["started"] += 1
+        M = oracle_unit(w, *u)
+        if on_done is not None:
+            on_done(u, M)
+        with lock:
+            st["dp"] += w.events[u[0]][u[1]].n
+            st["n"] += 1
+            st["t_last"] = time.perf_counter()
+
+    if threads <= 1:
+        for u in units:
+            work(u)
+    else:
+        with cf.ThreadPoolExecutor(max_workers=threads) as ex:
+            list(ex.map(work, units))
+    return st["dp"], st["t_last"] - t0, st["n"]
+
+
+def unit_error(gpu, M) -> dict:
+    """Relative L2 of a GPU waveform against the oracle's, and the largest
+    absolute difference over the largest |M|."""
+    diff = np.asarray(gpu, np.float64) - M
+    return {"rel_l2": float(np.linalg.norm(diff) / max(np.linalg.norm(M), 1e-300)),
+            "max_abs_over_max": float(np.abs(diff).max() / max(np.abs(M).max(), 1e-300))}
+
+
+def error_summary(errs: dict, w) -> dict:
+    """Summary of per-unit errors {(e, p): unit_error}: the worst and median
+    relative L2 and the worst peak-relative difference, per plane and over
+    all units."""
+    if not errs:
+        return None
+    rel = {u: v["rel_l2"] for u, v in errs.items()}
+    worst = max(rel, key=rel.get)
+    planes = {}
+    for pi, sp in enumerate(w.planes):
+        r = [v for (e, p), v in rel.items() if p == pi]
+        if r:
+            planes[str(sp.plane_id)] = {"units": len(r), "rel_l2_max": max(r), "rel_l2_median": statistics.median(r)}
+    return {"units": len(errs), "rel_l2_max": rel[worst], "rel_l2_median": statistics.median(rel.values()),
+            "max_abs_over_max": max(v["max_abs_over_max"] for v in errs.values()),
+            "worst_unit": {"event": worst[0], "plane_id": w.planes[worst[1]].plane_id}, "by_plane": planes,
+            "mode": "binomial" if w.fluctuate else "expected value",
+            "note": "same seed and Philox counters as the GPU; FP32 on the GPU against FP64"}
+
+
+def cpu_baselines(w, budget_1t: float, budget_all: float, gpu_outs=None):
+    """The oracle timed on one host thread and on every host core, each on a
+    bounded sample of the workload's units taken in a seeded random order;
+    with ``gpu_outs`` ({unit: host waveform}) the all-core run also measures
+    the GPU's error on every unit it computes."""
+    units = sample_order(w)
+    dp1, s1, n1 = oracle_units(w, units, 1, budget_1t)
+    cores = os.cpu_count() or 1
+    errs = {}
+    lock = threading.Lock()
+
+    def keep(u, M):
+        if gpu_outs is not None and u in gpu_outs:
+            e = unit_error(gpu_outs[u], M)
+            with lock:
+                errs[u] = e
+
+    dpa, sa, na = oracle_units(w, units, cores, budget_all, keep)
+    total = len(units)
+    one = {"value": dp1 / s1, "unit": UNIT, "cores": 1, "kind": "oracle",
+           "sample": f"{n1} of the workload's {total} (event, plane) units in a seeded random order "
+                     f"({dp1} depo-planes), FP64, one thread"}
+    allc = {"value": dpa / sa, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{na} of the workload's {total} (event, plane) units in a seeded random order "
+                      f"({dpa} depo-planes), FP64, a thread per host core", "one_thread": one}
+    return allc, errs
+
+
+def run_reference(args):
+    """The reference arm: the FP64 oracle on the host cores (a thread per
+    core), on the same workload, metric and unit as the GPU arm.  A step is
+    one unit per core, the units taken in a seeded random order and run as
+    one continuous pool; the run stops at the time budget whatever --steps
+    asks, and reports the steps it completed."""
+    world, rank, _ = _dist()
+    if rank != 0:
+        return
+    w = make_workload(args.workload, 0)
+    cores = os.cpu_count() or 1
+    order = sample_order(w)
+    small = min(workload_units(w), key=lambda u: w.events[u[0]][u[1]].n)
+    for _ in range(min(args.warmup, 1)):
+        oracle_unit(w, *small)
+    want = max(args.steps, 1) * cores
+    units = [order[i % len(order)] for i in range(want)]
+    dp, secs, n = oracle_units(w, units, cores, args.reference_seconds)
+    steps = max(1, n // cores)
+    value = dp / secs
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / (n / cores),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": w.name, "units": len(order),
+                   "sample": "one (event, plane) unit per host core per step, seeded random order",
+                   "steps_requested": args.steps, "time_budget_s": args.reference_seconds},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"{n} units ({dp} depo-planes) of {w.name} in {secs:.1f} s "
+                                   f"({args.reference_seconds:.0f} s budget), a thread per core"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "planes_per_s": n / secs,
+    }
+    print(json.dumps(line), flush=True)
+
+
+# --------------------------------------------------------------- GPU helpers
 def _time_steps(step, steps, stream, flush):
     import torch
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
@@ -325,85 +422,227 @@ def _time_steps(step, steps, stream, flush):
     return [a.elapsed_time(b) for a, b in zip(starts, ends)]
 
 
-def batched_workload_comparison(wiresim, dev, stream, flush, steps: int):
-    """64 events x 3 planes with log-uniform depo counts: the batched path
-    (one launch per stage per wave, replayed from a CUDA graph; wave size
-    picked by timing) against one ws_simulate call per (event, plane)."""
+def traced(plane0, run, nsteps: int, records_per_step: int):
+    """{kernel: (launches, total ms)} of the library's launch trace (CUDA
+    events around every launch on its stream) over ``nsteps`` calls of
+    ``run``; the traced launches are those of plane0 (a batch traces on its
+    first plane)."""
     import torch
-    w = inputs.batched_events()
-    planes = [wiresim.Plane(sp.nwires, sp.nticks, sp.response, plane_id=sp.plane_id, device=dev) for sp in w.planes]
-    events = [[wiresim.DeviceDepos.from_plane_depos(d, device=dev) for d in ev] for ev in w.events]
-    params = wiresim.Params(fluctuate=w.fluctuate, p_survive=w.p_survive, seed=w.seed)
-    ndp = sum(d.n for ev in w.events for d in ev)
-    best = None
-    for upw in (3, 6, 12, 16, 24, 32):
-        b = wiresim.Batch(planes, events, params, units_per_wave=upw, device=dev)
-        b.run(stream)
-        torch.cuda.synchronize()
-        ms = sum(_time_steps(lambda: b.run(stream), 2, stream, flush)) / 2
-        if best is None or ms < best[0]:
-            best = (ms, upw, b)
-        else:
-            del b
-    _, upw, b = best
-    b.capture()
-    b.replay()
+    plane0.trace(nsteps * records_per_step + 16)
+    for _ in range(nsteps):
+        run()
     torch.cuda.synchronize()
-    graph_ms = _time_steps(b.replay, steps, stream, flush)
-    outs = [torch.empty((pl.nwires, pl.nticks), dtype=torch.float32, device=dev) for pl in planes]
+    st = plane0.trace_read()
+    plane0.trace(0)
+    return st
+
+
+def kernel_launches(stats: dict, nsteps: int) -> float:
+    """Kernels per step from a trace (a traced raster is two kernels: lane
+    per depo, then warp per depo for the large patches)."""
+    return sum(n * (2 if name == "raster_scatter" else 1) for name, (n, _) in stats.items()) / nsteps
+
+
+def drawing_bins(wiresim, pairs) -> int:
+    """Bins that draw one Philox block in binomial mode, over (plane,
+    DeviceDepos) pairs: in-grid bins holding N = floor(q w + 1/2) >= 1
+    electrons, counted on the expected-value patches of the same depos."""
+    n = 0
+    for pl, dd in pairs:
+        if dd.n == 0:
+            continue
+        pt = pl.rasterize(dd, wiresim.Params(p_survive=1.0))
+        n += int((pt["val"][:pt["capacity"]] >= 0.5).sum().item())
+        del pt
+    return n
+
+
+def kernel_table(stats, nsteps, specs, muls_per_step, peak_gbs, traffic):
+    """Per-kernel device time per step and its fractions of the HBM, FP32 and
+    INT32-multiply peaks by algorithmic work.  specs: (nwires, nticks,
+    nfreq, L, kw, ndepo) of every unit a step runs."""
+    out = {}
+    for name, (n, ms) in sorted(stats.items()):
+        t = ms / nsteps * 1e-3
+        b = sum(algorithmic_bytes(name, nw, nt, nf, kw, nd) for nw, nt, nf, L, kw, nd in specs)
+        f = sum(algorithmic_flops(name, nw, nt, L, nf, kw) for nw, nt, nf, L, kw, nd in specs)
+        m = muls_per_step if name == "raster_scatter" else 0.0
+        out[name] = {"ms_per_step": t * 1e3, "launches_per_step": n / nsteps,
+                     "algorithmic_bytes_per_step": b, "hbm_gbs": b / t / 1e9, "hbm_frac": b / t / 1e9 / peak_gbs,
+                     "fp32_frac": f / t / 1e12 / FP32_PEAK_TFLOPS, "int_mul_frac": m / t / 1e12 / INT_MUL_PEAK_T,
+                     "ncu_dram_bytes_per_step": traffic.get(name)}
+    return out
+
+
+def roofline_of(table, muls_per_step, peak_gbs, peak_src, traffic, issue):
+    """The roofline of the dominant kernel of a step (largest device time):
+    the raster against the INT32 multiply peak by its Philox multiplies when
+    those bound it, else HBM or FP32 by its algorithmic bytes or flops."""
+    dom = max(table, key=lambda k: table[k]["ms_per_step"])
+    k = table[dom]
+    t = k["ms_per_step"] * 1e-3
+    fr = {"hbm": k["hbm_frac"], "alu": k["fp32_frac"], "int": k["int_mul_frac"]}
+    base = {"kernel": dom, "traffic": traffic.get(dom), "ncu_issue_active": issue.get(dom),
+            "ms_per_step": k["ms_per_step"], "launches_per_step": k["launches_per_step"]}
+    if dom == "raster_scatter" and muls_per_step > 0 and fr["int"] >= max(fr["hbm"], fr["alu"]):
+        a = muls_per_step / t / 1e12
+        base.update({"bound": "alu", "achieved": a, "peak": INT_MUL_PEAK_T, "unit": "T int32-mul/s",
+                     "frac": a / INT_MUL_PEAK_T,
+                     "peak_source": "derived: 152 SMs x 64 INT32 multiply lanes x 2.07 GHz "
+                                    "(a Philox-only loop reaches 19.0, 94%)",
+                     "work": f"{PHILOX_MULS} multiplies per Philox block x one block per drawing bin "
+                             f"({muls_per_step / PHILOX_MULS:.0f} bins per step)",
+                     "hbm_frac_of_measured": k["hbm_frac"]})
+    elif fr["alu"] > fr["hbm"]:
+        base.update({"bound": "alu", "achieved": fr["alu"] * FP32_PEAK_TFLOPS, "peak": FP32_PEAK_TFLOPS,
+                     "unit": "TFLOP/s", "frac": fr["alu"],
+                     "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz",
+                     "hbm_frac_of_measured": k["hbm_frac"]})
+    else:
+        base.update({"bound": "hbm", "achieved": k["hbm_gbs"], "peak": peak_gbs, "unit": "GB/s",
+                     "frac": k["hbm_frac"], "peak_source": f"{peak_src} hbm_gbs",
+                     "fp32_frac_of_derived": k["fp32_frac"]})
+    return base
+
+
+def convolution_report(table, specs, peak_gbs):
+    """The FFT convolution (forward tick transform, wire-axis sum, inverse)
+    as a whole: its time per step against the bytes each pass reads and
+    writes, against the 12 B per grid cell of a grid in, a waveform out and
+    a half spectrum of the response, and against the least any convolution
+    must move (grid in, waveform out, the response)."""
+    names = [k for k in ("fwd_rows", "wire_conv", "inv_rows") if k in table]
+    if len(names) != 3:
+        return None
+    t = sum(table[k]["ms_per_step"] for k in names) * 1e-3
+    pass_bytes = sum(table[k]["algorithmic_bytes_per_step"] for k in names)
+    cells = sum(nw * nt for nw, nt, nf, L, kw, nd in specs)
+    resp = sum(4.0 * kw * 200 for nw, nt, nf, L, kw, nd in specs)
+    b12, bmin = 12.0 * cells, 8.0 * cells + resp
+    return {"kernels": names, "ms_per_step": t * 1e3, "cells_per_step": cells,
+            "pass_bytes": pass_bytes, "hbm_frac_pass_bytes": pass_bytes / t / 1e9 / peak_gbs,
+            "bytes_12_per_cell": b12, "hbm_frac_12_per_cell": b12 / t / 1e9 / peak_gbs,
+            "min_bytes": bmin, "hbm_frac_min_bytes": bmin / t / 1e9 / peak_gbs,
+            "note": "pass bytes: each pass reads its input and writes its output once; 12 B per cell: grid in, "
+                    "waveform out and a half spectrum per cell; min bytes: grid in and waveform out (8 B per cell) "
+                    "plus the response"}
+
+
+def unit_specs(planes_by_unit, depos_by_unit):
+    return [(pl.nwires, pl.nticks, pl.info.nfreq, pl.info.fft_len_tick, int(pl.response.shape[-2]), d.n)
+            for pl, d in zip(planes_by_unit, depos_by_unit)]
+
+
+# ---------------------------------------------------------------------- legs
+def event_leg(wiresim, dev, stream, flush, steps: int, peak, oracle_check: bool):
+    """The single three-plane event (800/800/960 x 6000, 100,000 track depos,
+    binomial): its batch replayed from a CUDA graph (wave size by the
+    library's autotuner), one ws_simulate per plane, per-kernel times with
+    one launch per stage over the three planes, the raster's roofline, and
+    the FP64 oracle's error on its three planes."""
+    import torch
+    peak_gbs, peak_src = peak
+    w = make_workload("three_planes", 0)
+    planes = [wiresim.Plane(sp.nwires, sp.nticks, sp.response, plane_id=sp.plane_id, device=dev) for sp in w.planes]
+    depos = [wiresim.DeviceDepos.from_plane_depos(d, device=dev) for d in w.events[0]]
+    params = wiresim.Params(fluctuate=w.fluctuate, p_survive=w.p_survive, seed=w.seed)
+    b = wiresim.Batch(planes, [depos], params, device=dev)
+    b.capture()
+    for _ in range(3):
+        b.replay()
+    torch.cuda.synchronize(dev)
+    ms = statistics.median(_time_steps(b.replay, steps, stream, flush))
+    outs = [torch.empty((sp.nwires, sp.nticks), dtype=torch.float32, device=dev) for sp in w.planes]
 
     def per_plane():
-        for e, ev in enumerate(events):
-            pe = wiresim.Params(**{**params.__dict__, "event_id": e})
-            for pl, d, o in zip(planes, ev, outs):
-                pl.simulate(d, pe, out=o, stream=stream)
+        for pl, dd, o in zip(planes, depos, outs):
+            pl.simulate(dd, params, out=o, stream=stream)
 
     per_plane()
-    torch.cuda.synchronize()
-    pp_ms = _time_steps(per_plane, steps, stream, flush)
-    g = sum(graph_ms) / len(graph_ms)
-    pp = sum(pp_ms) / len(pp_ms)
-    return {"workload": w.name, "events": len(w.events), "depo_planes": ndp,
-            "units_per_wave": upw, "batched_graph_depos_per_s": ndp / (g * 1e-3),
-            "per_plane_depos_per_s": ndp / (pp * 1e-3), "speedup": pp / g,
-            "batched_ms": g, "per_plane_ms": pp}
+    pp = statistics.median(_time_steps(per_plane, steps, stream, flush))
+    serial = wiresim.Batch(planes, [depos], params, units_per_wave=len(planes), device=dev)
+    nsteps = max(5, min(steps, 200))
+    stats = traced(planes[0], lambda: (flush.zero_(), serial.run(stream)), nsteps, 8)
+    muls = PHILOX_MULS * float(drawing_bins(wiresim, list(zip(planes, depos))))
+    traffic, issue, _ = ncu_figures(w.name)
+    specs = unit_specs(planes, depos)
+    table = kernel_table(stats, nsteps, specs, muls, peak_gbs, traffic)
+    ndp = sum(d.n for d in w.events[0])
+    res = {"workload": w.name, "depos_per_plane": w.events[0][0].n, "ms_per_step": ms, "value": ndp / (ms * 1e-3),
+           "unit": UNIT, "units_per_wave": b.chosen_units_per_wave,
+           "per_plane_path": {"ms_per_step": pp, "value": ndp / (pp * 1e-3)},
+           "kernels": table, "roofline": roofline_of(table, muls, peak_gbs, peak_src, traffic, issue),
+           "convolution": convolution_report(table, specs, peak_gbs)}
+    if oracle_check:
+        gpu = {(0, p): o.cpu().numpy() for p, o in enumerate(b.outs)}
+        errs = {}
+        oracle_units(w, list(gpu), 3, 0.0, lambda u, M: errs.__setitem__(u, unit_error(gpu[u], M)))
+        res["oracle_error"] = error_summary(errs, w)
+    for pl in planes:
+        pl.close()
+    return res
 
 
-def _profiled_once(step, enabled: bool):
-    """One more step bracketed by cudaProfilerStart/Stop (for an ncu launch
-    list taken with --profile-from-start off)."""
-    if not enabled:
-        return
+def large_leg(wiresim, dev, stream, flush, steps: int, oracle_check: bool):
+    """The large three-plane detector (2560/2560/3840 x 6000, 2M track depos,
+    binomial): one ws_simulate per plane on the FP32, compensated
+    (FP32 + TwoSum scatter + FP64 narrow edges) and FP64 paths, timed by CUDA
+    events, each against the FP64 oracle per plane."""
     import torch
-    torch.cuda.synchronize()
-    torch.cuda.profiler.start()
-    step()
-    torch.cuda.synchronize()
-    torch.cuda.profiler.stop()
+    w = make_workload("large", 0)
+    paths = (("fp32", wiresim.WS_PREC_FP32), ("fp32_comp", wiresim.WS_PREC_FP32_COMP),
+             ("fp64", wiresim.WS_PREC_FP64))
+    refs = {}
+    if oracle_check:
+        oracle_units(w, workload_units(w), 3, 0.0, lambda u, M: refs.__setitem__(u, M))
+    res = {"workload": w.name, "depos": w.events[0][0].n, "wires": [sp.nwires for sp in w.planes], "paths": {}}
+    for name, prec in paths:
+        res["paths"][name] = {"ms_per_plane": [], "rel_l2": [], "max_abs_over_max": []}
+    for p, (sp, d) in enumerate(zip(w.planes, w.events[0])):
+        pl = wiresim.Plane(sp.nwires, sp.nticks, sp.response, plane_id=sp.plane_id, fp64=True, device=dev)
+        dd = wiresim.DeviceDepos.from_plane_depos(d, device=dev)
+        out = torch.empty((sp.nwires, sp.nticks), dtype=torch.float32, device=dev)
+        for name, prec in paths:
+            params = wiresim.Params(fluctuate=w.fluctuate, p_survive=w.p_survive, seed=w.seed, precision=prec)
+            pl.simulate(dd, params, out=out, stream=stream)
+            ms = statistics.median(_time_steps(lambda: pl.simulate(dd, params, out=out, stream=stream),
+                                               steps, stream, flush))
+            r = res["paths"][name]
+            r["ms_per_plane"].append(ms)
+            if (0, p) in refs:
+                e = unit_error(out.cpu().numpy(), refs[(0, p)])
+                r["rel_l2"].append(e["rel_l2"])
+                r["max_abs_over_max"].append(e["max_abs_over_max"])
+        pl.close()
+    ndp = sum(d.n for d in w.events[0])
+    for name, _ in paths:
+        r = res["paths"][name]
+        r["ms_per_event"] = sum(r["ms_per_plane"])
+        r["value"] = ndp / (r["ms_per_event"] * 1e-3)
+    res["unit"] = UNIT
+    res["note"] = "one ws_simulate per plane (the precision paths run there); relative L2 against the FP64 oracle " \
+                  "per plane (binomial, same Philox counters)"
+    return res
 
 
-def noise_leg(wiresim, dev, stream, flush, steps: int, units_per_wave: int, plain_ms: float,
-              profile: bool = False, wire_conv_variant: int = -1):
-    """The benchmark event with the noise term of Eq. 1 switched on (an
+def noise_leg(wiresim, dev, stream, flush, steps: int, plain_ms: float):
+    """The three-plane event with the noise term of Eq. 1 switched on (an
     incoherent spectrum per wire plus a coherent one per group of 32 wires,
-    synthetic shapes), replayed from a CUDA graph like the timed step."""
+    synthetic shapes), replayed from a CUDA graph like the plain event."""
     import torch
     w = make_workload("three_planes", 0)
     planes = [wiresim.Plane(sp.nwires, sp.nticks, sp.response, plane_id=sp.plane_id, device=dev) for sp in w.planes]
     L = planes[0].info.fft_len_tick
     for pl in planes:
         pl.set_noise(inputs.noise_amplitudes(L), inputs.noise_amplitudes(L, "coherent"), 32)
-        if wire_conv_variant >= 0:
-            pl.set_wire_conv_variant(wire_conv_variant)
     depos = [wiresim.DeviceDepos.from_plane_depos(d, device=dev) for d in w.events[0]]
     params = wiresim.Params(fluctuate=w.fluctuate, p_survive=w.p_survive, seed=w.seed)
-    b = wiresim.Batch(planes, [depos], params, units_per_wave=units_per_wave, device=dev)
+    b = wiresim.Batch(planes, [depos], params, device=dev)
     b.capture()
     for _ in range(3):
         b.replay()
     torch.cuda.synchronize(dev)
-    ms = sorted(_time_steps(b.replay, steps, stream, flush))[steps // 2]
-    _profiled_once(b.replay, profile)
+    ms = statistics.median(_time_steps(b.replay, steps, stream, flush))
     ndp = sum(d.n for d in w.events[0])
     for pl in planes:
         pl.close()
@@ -413,34 +652,23 @@ def noise_leg(wiresim, dev, stream, flush, steps: int, units_per_wave: int, plai
                      "and the inverse transform (one more launch per wave)"}
 
 
-def multinomial_leg(wiresim, dev, stream, flush, steps: int, units_per_wave: int, plain_ms: float,
-                    profile: bool = False, wire_conv_variant: int = -1):
-    """The benchmark event with the charge-conserving fluctuation
+def multinomial_leg(wiresim, dev, stream, flush, steps: int, plain_ms: float):
+    """The three-plane event with the charge-conserving fluctuation
     (fluctuate = 2: binomial survivors per depo, multinomial split over the
-    patch), replayed from a CUDA graph like the timed step."""
+    patch), replayed from a CUDA graph, and its raster launch alone (traced)."""
     import torch
     w = make_workload("three_planes", 0)
     planes = [wiresim.Plane(sp.nwires, sp.nticks, sp.response, plane_id=sp.plane_id, device=dev) for sp in w.planes]
-    if wire_conv_variant >= 0:
-        for pl in planes:
-            pl.set_wire_conv_variant(wire_conv_variant)
     depos = [wiresim.DeviceDepos.from_plane_depos(d, device=dev) for d in w.events[0]]
     params = wiresim.Params(fluctuate=2, p_survive=w.p_survive, seed=w.seed)
-    b = wiresim.Batch(planes, [depos], params, units_per_wave=units_per_wave, device=dev)
+    b = wiresim.Batch(planes, [depos], params, device=dev)
     b.capture()
     for _ in range(3):
         b.replay()
     torch.cuda.synchronize(dev)
-    ms = sorted(_time_steps(b.replay, steps, stream, flush))[steps // 2]
-    _profiled_once(b.replay, profile)
-    # the raster stage alone, traced
-    planes[0].trace(steps * 16 + 16)
-    for _ in range(steps):
-        flush.zero_()
-        b.run(stream)
-    torch.cuda.synchronize(dev)
-    st = planes[0].trace_read()
-    planes[0].trace(0)
+    ms = statistics.median(_time_steps(b.replay, steps, stream, flush))
+    serial = wiresim.Batch(planes, [depos], params, units_per_wave=len(planes), device=dev)
+    st = traced(planes[0], lambda: (flush.zero_(), serial.run(stream)), steps, 8)
     ndp = sum(d.n for d in w.events[0])
     for pl in planes:
         pl.close()
@@ -450,8 +678,8 @@ def multinomial_leg(wiresim, dev, stream, flush, steps: int, units_per_wave: int
             "raster_ms_per_launch": rms / max(rn, 1)}
 
 
-def impacts_leg(wiresim, dev, stream, flush, steps: int, impacts: int = 10, profile: bool = False):
-    """The benchmark event on planes whose response depends on the charge's
+def impacts_leg(wiresim, dev, stream, flush, steps: int, impacts: int = 10):
+    """The three-plane event on planes whose response depends on the charge's
     position inside the pitch (10 sub-pitch positions, synthetic slices):
     the raster bins the pitch axis at pitch/10 and the forward transform
     runs over 10x the rows; one ws_simulate per plane."""
@@ -471,15 +699,14 @@ def impacts_leg(wiresim, dev, stream, flush, steps: int, impacts: int = 10, prof
     for _ in range(3):
         step()
     torch.cuda.synchronize(dev)
-    ms = sorted(_time_steps(step, steps, stream, flush))[steps // 2]
-    _profiled_once(step, profile)
+    ms = statistics.median(_time_steps(step, steps, stream, flush))
+    kern = {}
     for pl in planes:
         pl.trace(16 * steps + 16)
     for _ in range(steps):
         flush.zero_()
         step()
     torch.cuda.synchronize(dev)
-    kern = {}
     for pl in planes:
         for name, (n, t) in pl.trace_read().items():
             kern[name] = kern.get(name, 0.0) + t / steps
@@ -509,14 +736,15 @@ def adjoint_leg(wiresim, dev, stream, flush, steps: int):
         fwd()
         bwd()
     torch.cuda.synchronize(dev)
-    f_ms = sorted(_time_steps(fwd, steps, stream, flush))[steps // 2]
-    b_ms = sorted(_time_steps(bwd, steps, stream, flush))[steps // 2]
+    f_ms = statistics.median(_time_steps(fwd, steps, stream, flush))
+    b_ms = statistics.median(_time_steps(bwd, steps, stream, flush))
     plane.close()
     return {"workload": "single_plane_960x6000, 20000 depos (t >= 1 us), expected value",
             "forward_ms": f_ms, "backward_ms": b_ms, "backward_over_forward": b_ms / f_ms,
             "backward_outputs": "dL/dq, dL/dx, dL/dt per depo; dL/dD_L, dL/dD_T; dL/dR (21 x 200)"}
 
 
+# -------------------------------------------------------------------- main
 def run_gpu(args):
     import torch
     from paper_2203_02479_gb300 import wiresim
@@ -526,371 +754,268 @@ def run_gpu(args):
     dev = torch.device("cuda", local)
     dist = _init_pg(world, "nccl")
     wiresim.load_library()
+    peak_gbs, _, peak_src = _peaks()
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device=dev)
 
     w = make_workload(args.workload, rank)
-    ev = w.events[0]
-    planes = [wiresim.Plane(sp.nwires, sp.nticks, sp.response, plane_id=sp.plane_id, device=dev)
-              for sp in w.planes]
-    depos = [wiresim.DeviceDepos.from_plane_depos(d, device=dev) for d in ev]
-    params = wiresim.Params(fluctuate=w.fluctuate, p_survive=w.p_survive, seed=w.seed, event_id=rank)
+    nplanes, nevents = len(w.planes), len(w.events)
+    planes = [wiresim.Plane(sp.nwires, sp.nticks, sp.response, plane_id=sp.plane_id, device=dev) for sp in w.planes]
     if args.wire_conv_variant >= 0:
         for pl in planes:
             pl.set_wire_conv_variant(args.wire_conv_variant)
-    flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device=dev)
-    # wave size of the event's batch, picked by timing graph replays: with
-    # fewer units per wave than planes, the later waves run on the library's
-    # extra streams beside the first (wave k on stream k % 3)
-    best = None
-    choices = [args.units_per_wave] if args.units_per_wave > 0 else list(range(len(planes), 0, -1))
-    for upw in choices:
-        cand = wiresim.Batch(planes, [depos], params, units_per_wave=upw, device=dev)
-        cand.capture()
-        for _ in range(3):
-            cand.replay()
-        torch.cuda.synchronize(dev)
-        t = sorted(_time_steps(cand.replay, 20, torch.cuda.current_stream(dev), flush))[10]
-        if best is None or t < best[0]:
-            best = (t, upw, cand)
-        else:
-            del cand
-    _, upw_event, batch = best
-    outs = [torch.empty((sp.nwires, sp.nticks), dtype=torch.float32, device=dev) for sp in w.planes]
-    ndepo_planes = sum(d.n for d in ev)
-    stream = torch.cuda.current_stream(dev)
+    events = [[wiresim.DeviceDepos.from_plane_depos(d, device=dev) for d in ev] for ev in w.events]
+    params = wiresim.Params(fluctuate=w.fluctuate, p_survive=w.p_survive, seed=w.seed)
+    units = workload_units(w)
+    unit_planes = [planes[p] for _, p in units]
+    unit_depos = [events[e][p] for e, p in units]
+    specs = unit_specs(unit_planes, unit_depos)
+    ndepo_planes = sum(d.n for d in unit_depos)
 
-    # one launch per stage over all planes (no concurrent kernels): its
-    # traced launches give the per-kernel device times and the roofline
-    serial = wiresim.Batch(planes, [depos], params, units_per_wave=len(planes), device=dev)
+    # the step: one ws_simulate_batch over every unit, wave size from the
+    # library's autotuner unless forced
+    batch = wiresim.Batch(planes, events, params, units_per_wave=args.units_per_wave, device=dev)
+    upw = batch.autotune(stream) if args.units_per_wave <= 0 else args.units_per_wave
+    nwaves = (len(units) + upw - 1) // upw
+    launch_stats = traced(planes[0], lambda: batch.run(stream), 2, 8 * nwaves)
+    launches_per_step = kernel_launches(launch_stats, 2)
 
-    def step():
-        serial.run(stream)
+    # per-kernel device times: the same step one wave at a time on one
+    # stream (whole events, at most 32 units per wave, one shared workspace,
+    # the batch's own outputs), traced
+    ev_chunk = max(1, 32 // nplanes)
+    chunk_upw = ev_chunk * nplanes
+    shared_ws = wiresim.batch_workspace(planes, chunk_upw, device=dev)
+    chunks = []
+    for e0 in range(0, nevents, ev_chunk):
+        pe = wiresim.Params(**{**params.__dict__, "event_id": e0})
+        chunks.append(wiresim.Batch(planes, events[e0:e0 + ev_chunk], pe, units_per_wave=chunk_upw, device=dev,
+                                    workspace=shared_ws, outs=batch.outs[e0 * nplanes:(e0 + ev_chunk) * nplanes]))
 
-    def step_per_plane():
-        for pl, dd, o in zip(planes, depos, outs):
-            pl.simulate(dd, params, out=o, stream=stream)
+    def serial_step():
+        for c in chunks:
+            c.run(stream)
 
-    for _ in range(max(args.warmup, 0)):
-        step()
-        step_per_plane()
+    for _ in range(max(args.warmup, 1)):
+        serial_step()
     torch.cuda.synchronize(dev)
+    nk = max(3, min(args.steps, 10))
+    serial_ms = statistics.median(_time_steps(serial_step, nk, stream, flush))
+    stats = traced(planes[0], lambda: (flush.zero_(), serial_step()), nk, 8 * len(chunks))
+    fluct = w.fluctuate and 0.0 < w.p_survive < 1.0
+    muls = PHILOX_MULS * float(drawing_bins(wiresim, list(zip(unit_planes, unit_depos)))) if fluct else 0.0
+    traffic, issue, ncu_note = ncu_figures(w.name)
+    table = kernel_table(stats, nk, specs, muls, peak_gbs, traffic)
+    roof = roofline_of(table, muls, peak_gbs, peak_src, traffic, issue)
+    convolution = convolution_report(table, specs, peak_gbs)
 
-    # the batched path launched kernel by kernel, with the library's launch
-    # trace (per-kernel device times for the roofline)
-    planes[0].trace(args.steps * 16 + 16)
-    stream_ms = _time_steps(step, args.steps, stream, flush)
-    stats = planes[0].trace_read()
-    planes[0].trace(0)
-    # kernels per step of the timed batch (its waves), from the same trace
-    planes[0].trace(20 * 32 + 16)
-    for _ in range(20):
-        batch.run(stream)
+    # the plain path: one ws_simulate per (event, plane) unit
+    unit_params = [wiresim.Params(**{**params.__dict__, "event_id": e}) for e, _ in units]
+
+    def per_plane():
+        for pl, d, pe, o in zip(unit_planes, unit_depos, unit_params, batch.outs):
+            pl.simulate(d, pe, out=o, stream=stream)
+
+    per_plane()
     torch.cuda.synchronize(dev)
-    per_step_launches = sum(n * (2 if name == "raster_scatter" else 1)
-                            for name, (n, _) in planes[0].trace_read().items()) / 20.0
-    planes[0].trace(0)
+    pp_ms = statistics.median(_time_steps(per_plane, nk, stream, flush))
 
-    # the same event one plane at a time
-    pp_ms = _time_steps(step_per_plane, args.steps, stream, flush)
-
-    # timed region: the batched step replayed from a CUDA graph (the
-    # production path: one graph launch per event)
+    # timed region: the batch replayed from a CUDA graph
     batch.capture()
     for _ in range(max(args.warmup, 0)):
         batch.replay()
     torch.cuda.synchronize(dev)
     sampler = ClockSampler(local) if local == 0 else None
+    if sampler is not None:
+        sampler.wait_first()
     _barrier(dist)
     torch.cuda.synchronize(dev)
     if args.profile_timed:
         torch.cuda.profiler.start()
+    tw0 = time.perf_counter()
     graph_ms = _time_steps(batch.replay, args.steps, stream, flush)
+    tw1 = time.perf_counter()
     if args.profile_timed:
         torch.cuda.profiler.stop()
     _barrier(dist)
-    clocks = sampler.stop() if sampler else None
+    clocks = None
+    if sampler is not None:
+        sampler.stop()
+        clocks = sampler.window(tw0, tw1)
     total_ms = _max_over_ranks(dist, float(sum(graph_ms)), dev)
-    # the event's waveforms as the timed graph left them, for the error
-    # against the oracle (rank 0 at N = 1, beside the CPU baseline)
     check_oracle = world == 1 and not args.no_cpu_baseline
-    gpu_out = [o.cpu().numpy() for o in batch.outs] if check_oracle else None
+    gpu_outs = {u: o.cpu().numpy() for u, o in zip(units, batch.outs)} if check_oracle else None
 
-    # per-kernel algorithmic work (sum over the event's planes per launch)
-    kern = {name: [n, ms] for name, (n, ms) in stats.items()}
-    # each traced raster_scatter entry is two kernels (lane per depo + large-patch)
-    launches = int(round(per_step_launches * args.steps))
-    per_launch_bytes, per_launch_flops = {}, {}
-    for name in kern:
-        per_launch_bytes[name] = sum(algorithmic_bytes(name, sp.nwires, sp.nticks, pl.info.nfreq,
-                                                       sp.response.shape[0], d.n)
-                                     for pl, sp, d in zip(planes, w.planes, ev))
-        per_launch_flops[name] = sum(algorithmic_flops(name, sp.nwires, sp.nticks, pl.info.fft_len_tick,
-                                                       pl.info.nfreq, sp.response.shape[0])
-                                     for pl, sp in zip(planes, w.planes))
-    # raster: the Philox multiplies of the binomial draws are its irreducible
-    # arithmetic (INT32 multiply pipe)
-    per_launch_muls = {name: 0.0 for name in kern}
-    if w.fluctuate and 0.0 < w.p_survive < 1.0 and "raster_scatter" in kern:
-        per_launch_muls["raster_scatter"] = PHILOX_MULS * float(drawing_bins(wiresim, planes, depos))
-    dominant = max(kern, key=lambda k: kern[k][1])
-    dn, dms = kern[dominant]
-    avg_s = dms / dn * 1e-3
-    peak_gbs, sm_max, peak_src = _peaks()
-    bw = per_launch_bytes[dominant] / avg_s / 1e9
-    fl = per_launch_flops[dominant] / avg_s / 1e12
-    im = per_launch_muls[dominant] / avg_s / 1e12
-    t_hbm = per_launch_bytes[dominant] / (peak_gbs * 1e9)
-    t_alu = per_launch_flops[dominant] / (FP32_PEAK_TFLOPS * 1e12)
-    t_int = per_launch_muls[dominant] / (INT_MUL_PEAK_T * 1e12)
-    traffic = NCU_TRAFFIC.get(w.name, {}).get(dominant)
-    if t_int > max(t_alu, t_hbm):
-        roof = {"kernel": dominant, "bound": "alu", "achieved": im, "peak": INT_MUL_PEAK_T,
-                "unit": "T int32-mul/s", "frac": im / INT_MUL_PEAK_T, "traffic": traffic,
-                "peak_source": "derived: 152 SMs x 64 INT32 multiply lanes x 2.07 GHz "
-                               "(a Philox-only loop reaches 19.0, 94%)",
-                "work": f"{PHILOX_MULS} multiplies per Philox block x one block per drawing bin "
-                        f"({per_launch_muls[dominant] / PHILOX_MULS:.0f} bins)",
-                "hbm_frac_of_measured": bw / peak_gbs}
-    elif t_alu > t_hbm:
-        roof = {"kernel": dominant, "bound": "alu", "achieved": fl, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": fl / FP32_PEAK_TFLOPS, "traffic": traffic,
-                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz",
-                "hbm_frac_of_measured": bw / peak_gbs}
-    else:
-        roof = {"kernel": dominant, "bound": "hbm", "achieved": bw, "peak": peak_gbs, "unit": "GB/s",
-                "frac": bw / peak_gbs, "traffic": traffic, "peak_source": f"{peak_src} hbm_gbs",
-                "alu_frac_of_derived": fl / FP32_PEAK_TFLOPS}
-    kernels = {}
-    for name, (n, ms) in sorted(kern.items()):
-        a = ms / n * 1e-3
-        kernels[name] = {"ms_per_step": ms / args.steps, "launches_per_step": n / args.steps,
-                         "hbm_gbs": per_launch_bytes[name] / a / 1e9,
-                         "hbm_frac": per_launch_bytes[name] / a / 1e9 / peak_gbs,
-                         "fp32_tflops": per_launch_flops[name] / a / 1e12,
-                         "fp32_frac": per_launch_flops[name] / a / 1e12 / FP32_PEAK_TFLOPS,
-                         "int_mul_frac": per_launch_muls[name] / a / 1e12 / INT_MUL_PEAK_T,
-                         "ncu_dram_bytes": NCU_TRAFFIC.get(w.name, {}).get(name)}
-    if "raster_scatter" in kernels:
-        kernels["raster_scatter"]["ncu_issue_active"] = NCU_ISSUE_ACTIVE.get(w.name)
-    if roof["kernel"] == "raster_scatter":
-        roof["ncu_issue_active"] = NCU_ISSUE_ACTIVE.get(w.name)
-    # the FFT convolution (a5-a7) as a whole: its three kernels' time against
-    # the bytes each pass reads and writes, and against the least any
-    # convolution must move (the grid in, the waveform out, the response)
-    conv_names = [k for k in ("fwd_rows", "wire_conv", "inv_rows") if k in kern]
-    convolution = None
-    if len(conv_names) == 3:
-        c_s = sum(kern[k][1] / kern[k][0] for k in conv_names) * 1e-3
-        pass_bytes = sum(per_launch_bytes[k] for k in conv_names)
-        min_bytes = sum(8.0 * sp.nwires * sp.nticks + 4.0 * sp.response.size for sp in w.planes)
-        convolution = {"kernels": conv_names, "ms_per_step": c_s * 1e3,
-                       "pass_bytes": pass_bytes, "hbm_frac_pass_bytes": pass_bytes / c_s / 1e9 / peak_gbs,
-                       "min_bytes": min_bytes, "hbm_frac_min_bytes": min_bytes / c_s / 1e9 / peak_gbs,
-                       "note": "pass bytes: each of the three passes reads its input and writes its output once "
-                               "(about 25 B per grid cell in all); min bytes: the grid in and the waveform out "
-                               "(8 B per grid cell) plus the response"}
-
-    # end to end through the public API with host buffers: every step copies
-    # its depos in from pinned host memory, replays the event's graph and
-    # copies the three waveforms out; two pipelines (own planes, buffers,
-    # graph and stream) alternate so that one step's copies overlap the
-    # other's kernels
     e2e = None
-    two_event = None
     if not args.no_e2e:
-        host_in = [[torch.from_numpy(a).pin_memory() for a in (d.q, d.x_mm, d.t_us)] for d in ev]
-        h2d = sum(a.numel() * 4 for trip in host_in for a in trip)
-        pipes = []
-        for _ in range(2):
-            pl2 = [wiresim.Plane(sp.nwires, sp.nticks, sp.response, plane_id=sp.plane_id, device=dev)
-                   for sp in w.planes]
-            dev_in = [[torch.empty_like(a, device=dev) for a in trip] for trip in host_in]
-            dd2 = [wiresim.DeviceDepos(*trip, device=dev) for trip in dev_in]
-            b2 = wiresim.Batch(pl2, [dd2], params, units_per_wave=upw_event, device=dev)
-            b2.capture()
-            host_out = [torch.empty((sp.nwires, sp.nticks), dtype=torch.float32).pin_memory() for sp in w.planes]
-            pipes.append((pl2, dev_in, b2, host_out, torch.cuda.Stream(dev)))
-        d2h = sum(o.numel() * 4 for o in pipes[0][3])
-
-        def e2e_step(j):
-            _, dev_in, b2, host_out, st = pipes[j % 2]
-            with torch.cuda.stream(st):
-                for trip_h, trip_d in zip(host_in, dev_in):
-                    for a_h, a_d in zip(trip_h, trip_d):
-                        a_d.copy_(a_h, non_blocking=True)
-                b2.replay()
-                for o, oh in zip(b2.outs, host_out):
-                    oh.copy_(o, non_blocking=True)
-
-        # the same two pipelines without the copies: events overlap on the
-        # device (one event's raster next to the other's transforms)
-        def overlap_step(j):
-            _, _, b2, _, st = pipes[j % 2]
-            with torch.cuda.stream(st):
-                b2.replay()
-
-        for j in range(max(args.warmup, 2)):
-            overlap_step(j)
-        torch.cuda.synchronize(dev)
-        o0 = torch.cuda.Event(enable_timing=True)
-        o1 = torch.cuda.Event(enable_timing=True)
-        o_steps = max(2, args.steps)
-        o0.record(pipes[0][4])
-        pipes[1][4].wait_event(o0)
-        for j in range(o_steps):
-            overlap_step(j)
-        pipes[0][4].wait_stream(pipes[1][4])
-        o1.record(pipes[0][4])
-        torch.cuda.synchronize(dev)
-        overlap_ms = o0.elapsed_time(o1) / o_steps
-
-        for j in range(max(args.warmup, 2)):
-            e2e_step(j)
-        torch.cuda.synchronize(dev)
-        s0 = torch.cuda.Event(enable_timing=True)
-        s1 = torch.cuda.Event(enable_timing=True)
-        e_steps = max(2, args.steps)
-        _barrier(dist)
-        torch.cuda.synchronize(dev)
-        s0.record(pipes[0][4])
-        pipes[1][4].wait_event(s0)
-        for j in range(e_steps):
-            e2e_step(j)
-        pipes[0][4].wait_stream(pipes[1][4])
-        s1.record(pipes[0][4])
-        torch.cuda.synchronize(dev)
-        _barrier(dist)
-        e_ms = _max_over_ranks(dist, s0.elapsed_time(s1), dev)
-        e_total = _sum_over_ranks(dist, float(ndepo_planes * e_steps), dev)
-        # the host link's own rate: the step's device-to-host copies alone,
-        # back to back (the direction that bounds the pipelined step, whose
-        # kernels and host-to-device copies hide behind it)
-        def d2h_only():
-            _, _, b2, host_out, st = pipes[0]
-            with torch.cuda.stream(st):
-                for o, oh in zip(b2.outs, host_out):
-                    oh.copy_(o, non_blocking=True)
-
-        d2h_only()
-        torch.cuda.synchronize(dev)
-        c0 = torch.cuda.Event(enable_timing=True)
-        c1 = torch.cuda.Event(enable_timing=True)
-        c0.record(pipes[0][4])
-        for _ in range(10):
-            d2h_only()
-        c1.record(pipes[0][4])
-        torch.cuda.synchronize(dev)
-        copy_ms = c0.elapsed_time(c1) / 10
-        e2e = {"value": e_total / (e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d,
-               "d2h_bytes_per_step": d2h, "ms_per_step": e_ms / e_steps,
-               "d2h_alone_ms_per_step": copy_ms,
-               "d2h_gbs_measured": d2h / (copy_ms * 1e-3) / 1e9,
-               "frac_of_d2h_bound": copy_ms / (e_ms / e_steps),
-               "path": "Batch.replay (CUDA graph) per step; pinned host copies in and out on the step's stream; "
-                       "two alternating pipelines overlap one step's copies with the other's kernels"}
-        two_event = {"ms_per_step": overlap_ms, "value": ndepo_planes / (overlap_ms * 1e-3),
-                     "note": "events alternating between two graph pipelines on two streams (two events in "
-                             "flight), no host copies, no L2 flush between events (an event's buffers, ~190 MB, "
-                             "exceed L2)"}
-        for p2 in pipes:
-            for pl in p2[0]:
-                pl.close()
+        e2e = e2e_leg(wiresim, w, params, upw, dev, dist, max(2, min(args.steps, 6)), max(args.warmup, 1))
 
     all_depos = _sum_over_ranks(dist, float(ndepo_planes * args.steps), dev)
-    all_planes = _sum_over_ranks(dist, float(len(planes) * args.steps), dev)
-    batched = None
-    adjoint = None
-    noise = None
-    multinomial = None
-    impacts = None
-    if rank == 0 and world == 1 and not args.no_batched_workload:
-        batched = batched_workload_comparison(wiresim, dev, stream, flush, max(3, min(args.steps, 10)))
-        adjoint = adjoint_leg(wiresim, dev, stream, flush, max(5, min(args.steps, 50)))
-        noise = noise_leg(wiresim, dev, stream, flush, max(5, min(args.steps, 200)), upw_event,
-                          sorted(graph_ms)[len(graph_ms) // 2], args.profile_legs, args.wire_conv_variant)
-        impacts = impacts_leg(wiresim, dev, stream, flush, max(5, min(args.steps, 50)), profile=args.profile_legs)
-        multinomial = multinomial_leg(wiresim, dev, stream, flush, max(5, min(args.steps, 200)), upw_event,
-                                      sorted(graph_ms)[len(graph_ms) // 2], args.profile_legs,
-                                      args.wire_conv_variant)
+    all_planes = _sum_over_ranks(dist, float(len(units) * args.steps), dev)
+    legs = {}
+    if rank == 0 and world == 1 and not args.no_legs:
+        ls = max(5, min(args.steps, 50))
+        legs["three_planes_event"] = event_leg(wiresim, dev, stream, flush, ls, (peak_gbs, peak_src),
+                                               not args.no_cpu_baseline)
+        plain = legs["three_planes_event"]["ms_per_step"]
+        if not args.no_large:
+            legs["large"] = large_leg(wiresim, dev, stream, flush, 3, not args.no_cpu_baseline)
+        legs["adjoint"] = adjoint_leg(wiresim, dev, stream, flush, ls)
+        legs["noise"] = noise_leg(wiresim, dev, stream, flush, ls, plain)
+        legs["multinomial"] = multinomial_leg(wiresim, dev, stream, flush, ls, plain)
+        legs["impacts"] = impacts_leg(wiresim, dev, stream, flush, max(5, min(args.steps, 20)))
     if rank != 0:
         if dist is not None:
             dist.destroy_process_group()
         return
-    value = all_depos / (total_ms * 1e-3)
-    raster_ms = kern.get("raster_scatter", [0, 0.0])[1] + kern.get("memset_grid", [0, 0.0])[1]
     cpu = None
     oracle_error = None
     if check_oracle:
-        kept = {}
-        done, secs, nplanes = oracle_sample(w, args.cpu_seconds, keep=kept)
-        cpu = {"value": done / secs, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"{nplanes} planes of this event ({done} depo-planes), FP64, single thread"}
-        oracle_error = oracle_error_of(gpu_out, kept, w)
-    pp = sum(pp_ms) / len(pp_ms)
-    sl = sum(stream_ms) / len(stream_ms)
+        cpu, errs = cpu_baselines(w, args.cpu_seconds, args.cpu_all_seconds, gpu_outs)
+        oracle_error = error_summary(errs, w)
+    del gpu_outs
+    value = all_depos / (total_ms * 1e-3)
+    counts = [ev[0].n for ev in w.events]
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": w.name, "depos_per_event": ev[0].n, "planes": len(planes),
+        "config": {"workload": w.name, "events": nevents, "planes": nplanes, "units": len(units),
                    "wires": [sp.nwires for sp in w.planes], "nticks": w.planes[0].nticks,
-                   "fluctuate": w.fluctuate, "p_survive": w.p_survive,
-                   "seed": w.seed, "event_id": rank,
-                   "fft_len_tick": planes[0].info.fft_len_tick,
-                   "units_per_wave": upw_event,
+                   "depo_planes_per_step": ndepo_planes,
+                   "depos_per_event": {"min": min(counts), "max": max(counts), "mean": sum(counts) / len(counts)},
+                   "fluctuate": w.fluctuate, "p_survive": w.p_survive, "seed": w.seed,
+                   "fft_len_tick": planes[0].info.fft_len_tick, "units_per_wave": upw,
                    "wire_conv_variant": [pl.info.wire_conv_variant for pl in planes],
-                   "path": "ws_simulate_batch over the event's planes in waves of units_per_wave (wave k on "
-                           "stream k % 3), replayed from a CUDA graph",
-                   "l2": "flushed between timed steps (512 MiB write)"},
+                   "path": "ws_simulate_batch over every (event, plane) unit in waves of units_per_wave (chosen by "
+                           "ws_batch_autotune; wave k on stream k % 3), replayed from a CUDA graph",
+                   "l2": "flushed between timed steps (512 MiB write); a step's buffers (~5 GB) exceed L2"},
         "planes_per_s": all_planes / (total_ms * 1e-3),
-        "raster_scatter_depos_per_s": all_depos / (raster_ms * 1e-3) if raster_ms > 0 else None,
-        "per_plane_path": {"ms_per_step": pp, "value": ndepo_planes / (pp * 1e-3)},
-        "stream_launch": {"ms_per_step": sl, "value": ndepo_planes / (sl * 1e-3),
-                          "note": "one launch per stage over the three planes, launched kernel by kernel "
-                                  "(traced: kernels, roofline)"},
-        "two_event_overlap": two_event,
-        "kernels": kernels,
+        "per_plane_path": {"ms_per_step": pp_ms, "value": ndepo_planes / (pp_ms * 1e-3),
+                           "batched_speedup": pp_ms / (total_ms / args.steps),
+                           "note": "one ws_simulate per (event, plane) unit, same outputs"},
+        "stream_launch": {"ms_per_step": serial_ms, "value": ndepo_planes / (serial_ms * 1e-3),
+                          "note": "the step one wave (at most 32 units) at a time on one stream, launched kernel "
+                                  "by kernel; its trace gives kernels and roofline"},
+        "kernels": table,
         "convolution": convolution,
         "roofline": roof,
-        "gpu_launches": launches,
+        "gpu_launches": int(round(launches_per_step * args.steps)),
         "clocks": clocks,
         "e2e": e2e,
         "cpu_baseline": cpu,
         "oracle_error": oracle_error,
         "gpu": torch.cuda.get_device_name(dev),
         "host_cores": os.cpu_count(),
-        "batched_workload": batched,
-        "adjoint": adjoint,
-        "noise": noise,
-        "multinomial": multinomial,
-        "impacts": impacts,
+        "kernel_source_hash": kernel_source_hash(),
+        "ncu_note": ncu_note,
+        "legs": legs,
     }
     print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
 
 
+def e2e_leg(wiresim, w, params, upw: int, dev, dist, steps: int, warmup: int):
+    """End to end through the public API with host buffers: every step copies
+    every unit's depos in from pinned host memory, replays the batch's CUDA
+    graph and copies every waveform out to pinned host memory.  Two
+    pipelines (own planes, device buffers, graph, stream and host outputs)
+    alternate, so one step's copies overlap the other's kernels."""
+    import torch
+    host_in = [[[torch.from_numpy(a).pin_memory() for a in (d.q, d.x_mm, d.t_us)] for d in ev] for ev in w.events]
+    h2d = sum(a.numel() * 4 for ev in host_in for trip in ev for a in trip)
+    ndp = sum(d.n for ev in w.events for d in ev)
+    pipes = []
+    for _ in range(2):
+        pl2 = [wiresim.Plane(sp.nwires, sp.nticks, sp.response, plane_id=sp.plane_id, device=dev) for sp in w.planes]
+        dev_in = [[[torch.empty_like(a, device=dev) for a in trip] for trip in ev] for ev in host_in]
+        ev2 = [[wiresim.DeviceDepos(*trip, device=dev) for trip in ev] for ev in dev_in]
+        b2 = wiresim.Batch(pl2, ev2, params, units_per_wave=upw, device=dev)
+        b2.capture()
+        host_out = [torch.empty(tuple(o.shape), dtype=torch.float32).pin_memory() for o in b2.outs]
+        pipes.append((pl2, dev_in, b2, host_out, torch.cuda.Stream(dev)))
+    d2h = sum(o.numel() * 4 for o in pipes[0][3])
+
+    def step(j):
+        _, dev_in, b2, host_out, st = pipes[j % 2]
+        with torch.cuda.stream(st):
+            for ev_h, ev_d in zip(host_in, dev_in):
+                for trip_h, trip_d in zip(ev_h, ev_d):
+                    for a_h, a_d in zip(trip_h, trip_d):
+                        a_d.copy_(a_h, non_blocking=True)
+            b2.replay()
+            for o, oh in zip(b2.outs, host_out):
+                oh.copy_(o, non_blocking=True)
+
+    for j in range(warmup):
+        step(j)
+    torch.cuda.synchronize(dev)
+    s0 = torch.cuda.Event(enable_timing=True)
+    s1 = torch.cuda.Event(enable_timing=True)
+    _barrier(dist)
+    torch.cuda.synchronize(dev)
+    s0.record(pipes[0][4])
+    pipes[1][4].wait_event(s0)
+    for j in range(steps):
+        step(j)
+    pipes[0][4].wait_stream(pipes[1][4])
+    s1.record(pipes[0][4])
+    torch.cuda.synchronize(dev)
+    _barrier(dist)
+    e_ms = _max_over_ranks(dist, s0.elapsed_time(s1), dev)
+    e_total = _sum_over_ranks(dist, float(ndp * steps), dev)
+
+    # the host link's own rate: one step's device-to-host copies alone
+    def d2h_only():
+        _, _, b2, host_out, st = pipes[0]
+        with torch.cuda.stream(st):
+            for o, oh in zip(b2.outs, host_out):
+                oh.copy_(o, non_blocking=True)
+
+    d2h_only()
+    torch.cuda.synchronize(dev)
+    c0 = torch.cuda.Event(enable_timing=True)
+    c1 = torch.cuda.Event(enable_timing=True)
+    c0.record(pipes[0][4])
+    for _ in range(3):
+        d2h_only()
+    c1.record(pipes[0][4])
+    torch.cuda.synchronize(dev)
+    copy_ms = c0.elapsed_time(c1) / 3
+    for p2 in pipes:
+        for pl in p2[0]:
+            pl.close()
+    return {"value": e_total / (e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+            "ms_per_step": e_ms / steps, "steps": steps, "d2h_alone_ms_per_step": copy_ms,
+            "d2h_gbs_measured": d2h / (copy_ms * 1e-3) / 1e9, "frac_of_d2h_bound": copy_ms / (e_ms / steps),
+            "path": "Batch.replay (CUDA graph) per step; pinned host copies of every unit's depos in and every "
+                    "waveform out on the step's stream; two alternating pipelines overlap one step's copies with "
+                    "the other's kernels"}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="wiresim", choices=["wiresim", "reference"])
-    ap.add_argument("--workload", default="three_planes", choices=["three_planes", "single_plane"])
+    ap.add_argument("--workload", default="batched", choices=list(WORKLOADS))
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-batched-workload", action="store_true")
-    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the oracle (CPU baseline, oracle_error)")
+    ap.add_argument("--no-legs", action="store_true", help="skip the single-event, large, adjoint, noise, "
+                    "multinomial and impact legs")
+    ap.add_argument("--no-large", action="store_true", help="skip the large three-plane leg")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0, help="budget of the one-thread oracle sample")
+    ap.add_argument("--cpu-all-seconds", type=float, default=30.0, help="budget of the all-core oracle sample")
     ap.add_argument("--reference-seconds", type=float, default=150.0,
                     help="time budget of the --impl reference timed steps")
     ap.add_argument("--wire-conv-variant", type=int, default=-1,
                     help="force the planes' wire-convolution kernel (default: each plane's autotuned choice)")
     ap.add_argument("--units-per-wave", type=int, default=0,
-                    help="force the event's wave size (default: picked by timing)")
+                    help="force the batch's wave size (default: the library's autotuner)")
     ap.add_argument("--profile-timed", action="store_true",
                     help="bracket the timed graph replays with cudaProfilerStart/Stop (for ncu --profile-from-start off)")
-    ap.add_argument("--profile-legs", action="store_true",
-                    help="bracket one more step of the noise, impact and multinomial legs with "
-                         "cudaProfilerStart/Stop (for ncu --profile-from-start off)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "wiresim":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)

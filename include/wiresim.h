@@ -292,7 +292,8 @@ ws_status ws_convolve_noalloc(const ws_plane_desc* desc, const float* response_d
 
 /* Device workspace of ws_simulate_batch: three wave slots, each a
  * large-patch hand-over list and two spectra (max nwires x (L_t/2+1)
- * complex64) per unit of a wave.  units_per_wave: 1 .. 32. */
+ * complex64) per unit of a wave.  units_per_wave: 1 .. 32, or 0 for the
+ * largest wave (32 units), which holds every wave size. */
 ws_status ws_batch_workspace_bytes(ws_plane* const* planes, int nplanes, int units_per_wave,
                                    size_t* bytes);
 
@@ -318,6 +319,24 @@ ws_status ws_batch_workspace_bytes(ws_plane* const* planes, int nplanes, int uni
 ws_status ws_simulate_batch(ws_plane* const* planes, int nplanes, const ws_depos* depos, int nevents,
                             const ws_params* params, float* const* out_dev, void* workspace_dev,
                             size_t workspace_bytes, int units_per_wave, void* stream);
+/* units_per_wave == 0 in ws_simulate_batch: the wave size ws_batch_autotune
+ * recorded on planes[0] if the workspace holds it, else the largest wave
+ * (at most 32 units, at most nevents * nplanes) the workspace holds. */
+
+/* Autotuner of ws_simulate_batch's wave size (the throughput motivation is
+ * the paper's Sec. 3.3): runs the batch on the caller's own inputs for each
+ * candidate wave size (1 .. 4 units, whole events of nplanes x 1, 2, 4, ...
+ * units, and the largest wave; only sizes whose workspace fits
+ * workspace_bytes), once to warm up and then three interleaved timed rounds
+ * (CUDA events on `stream`), keeps the fastest by its best round, writes it
+ * to *units_per_wave_out and records it on every plane of the call for
+ * later calls with units_per_wave == 0.  Arguments as for
+ * ws_simulate_batch; out_dev ends up holding the batch's result.
+ * SYNCHRONISES `stream` (so it cannot be captured into a graph: call it
+ * before capturing).  WS_ERR_WORKSPACE if no candidate fits. */
+ws_status ws_batch_autotune(ws_plane* const* planes, int nplanes, const ws_depos* depos, int nevents,
+                            const ws_params* params, float* const* out_dev, void* workspace_dev,
+                            size_t workspace_bytes, void* stream, int* units_per_wave_out);
 
 /* Noise term N(t, x) of Eq. 1 (Sec. 2.1 names it; the paper's port leaves
  * it out, and its model is this library's reading): from now on

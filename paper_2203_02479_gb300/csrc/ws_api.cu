@@ -431,6 +431,7 @@ ws_status ws_plane_create(const ws_plane_desc* desc, const float* response_dev, 
     // clock biases none); a variant's time is its best round, and the
     // fastest variant is kept.
     pl->wconv_variant = 0;
+    pl->batch_upw = 0;
     if (e == cudaSuccess) e = cudaMemsetAsync(pl->X, 0, sizeof(float2) * (size_t)desc->nwires * lay.fstride, s);
     if (e == cudaSuccess && lay.impacts == 1) {   // impact planes have one wire-convolution kernel
         cudaEvent_t t0 = nullptr, t1 = nullptr;
@@ -770,7 +771,8 @@ struct BatchLayout {
 };
 
 ws_status batch_layout(ws_plane* const* planes, int nplanes, int units_per_wave, BatchLayout* lay) {
-    if (!planes || nplanes <= 0 || units_per_wave <= 0 || units_per_wave > ws::kMaxUnits) return WS_ERR_INVALID_ARG;
+    if (units_per_wave == 0) units_per_wave = ws::kMaxUnits;
+    if (!planes || nplanes <= 0 || units_per_wave < 0 || units_per_wave > ws::kMaxUnits) return WS_ERR_INVALID_ARG;
     int maxw = 0;
     const ws_plane* p0 = planes[0];
     if (!p0) return WS_ERR_INVALID_ARG;
@@ -817,6 +819,24 @@ ws_status batch_waves(ws_plane* const* planes, int nplanes, const ws_depos* depo
                       float* const* out_dev, char* ws_base, const BatchLayout& lay, int units_per_wave, int nunits,
                       const cudaStream_t* ss, int nstreams);
 
+// Whether a wave of `upw` units fits `bytes` of batch workspace.
+bool wave_fits(ws_plane* const* planes, int nplanes, int upw, size_t bytes) {
+    BatchLayout lay;
+    return batch_layout(planes, nplanes, upw, &lay) == WS_OK && lay.total <= bytes;
+}
+
+// Wave size of a call with units_per_wave == 0: the autotuner's choice
+// recorded on the first plane if it fits the workspace, else the largest
+// wave (at most kMaxUnits, at most the call's units) that fits; 1 if none
+// does (the call then fails its workspace check).
+int auto_wave_size(ws_plane* const* planes, int nplanes, int nunits, size_t bytes) {
+    const int tuned = planes[0]->batch_upw;
+    if (tuned > 0 && wave_fits(planes, nplanes, tuned, bytes)) return tuned;
+    int upw = nunits < ws::kMaxUnits ? nunits : ws::kMaxUnits;
+    while (upw > 1 && !wave_fits(planes, nplanes, upw, bytes)) --upw;
+    return upw;
+}
+
 }  // namespace
 
 extern "C" {
@@ -834,6 +854,8 @@ ws_status ws_simulate_batch(ws_plane* const* planes, int nplanes, const ws_depos
                             const ws_params* params, float* const* out_dev, void* workspace_dev,
                             size_t workspace_bytes, int units_per_wave, void* stream) {
     NvtxRange range("ws_simulate_batch");
+    if (units_per_wave == 0 && planes && nplanes > 0 && planes[0] && nevents > 0)
+        units_per_wave = auto_wave_size(planes, nplanes, nevents * nplanes, workspace_bytes);
     BatchLayout lay;
     ws_status st = batch_layout(planes, nplanes, units_per_wave, &lay);
     if (st != WS_OK) return st;
@@ -888,6 +910,73 @@ ws_status ws_simulate_batch(ws_plane* const* planes, int nplanes, const ws_depos
     release();
     if (e != cudaSuccess && wst == WS_OK) return cuda_fail(e, "batch join");
     return wst;
+}
+
+ws_status ws_batch_autotune(ws_plane* const* planes, int nplanes, const ws_depos* depos, int nevents,
+                            const ws_params* params, float* const* out_dev, void* workspace_dev,
+                            size_t workspace_bytes, void* stream, int* units_per_wave_out) {
+    NvtxRange range("ws_batch_autotune");
+    if (!units_per_wave_out || !planes || nplanes <= 0 || nevents <= 0) return WS_ERR_INVALID_ARG;
+    for (int i = 0; i < nplanes; ++i)
+        if (!planes[i]) return WS_ERR_INVALID_ARG;
+    const int nunits = nevents * nplanes;
+    const int most = nunits < ws::kMaxUnits ? nunits : ws::kMaxUnits;
+    // Candidates: every size up to 4 units; whole events (nplanes x 1, 2, 4,
+    // ...); the largest wave; all of them limited to what the workspace holds.
+    int cand[2 * ws::kMaxUnits];
+    int nc = 0;
+    auto add = [&](int u) {
+        if (u < 1 || u > most || !wave_fits(planes, nplanes, u, workspace_bytes)) return;
+        for (int i = 0; i < nc; ++i)
+            if (cand[i] == u) return;
+        cand[nc++] = u;
+    };
+    for (int u = 1; u <= 4; ++u) add(u);
+    for (int k = 1; k * nplanes <= most; k *= 2) add(k * nplanes);
+    add(most - most % nplanes);
+    add(most);
+    if (nc == 0) return WS_ERR_WORKSPACE;
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaEvent_t t0 = nullptr, t1 = nullptr;
+    cudaError_t e = cudaEventCreate(&t0);
+    if (e == cudaSuccess) e = cudaEventCreate(&t1);
+    if (e != cudaSuccess) {
+        if (t0) cudaEventDestroy(t0);
+        return cuda_fail(e, "ws_batch_autotune");
+    }
+    // Every candidate once to warm up, then three rounds over all candidates
+    // (interleaved, so a drifting clock biases none); a candidate's time is
+    // its best round, the fastest candidate is kept.
+    float best_of[2 * ws::kMaxUnits];
+    ws_status st = WS_OK;
+    for (int i = 0; i < nc && st == WS_OK; ++i) {
+        best_of[i] = 1e30f;
+        st = ws_simulate_batch(planes, nplanes, depos, nevents, params, out_dev, workspace_dev, workspace_bytes,
+                               cand[i], stream);
+    }
+    for (int round = 0; round < 3 && st == WS_OK; ++round) {
+        for (int i = 0; i < nc && st == WS_OK; ++i) {
+            e = cudaEventRecord(t0, s);
+            if (e == cudaSuccess)
+                st = ws_simulate_batch(planes, nplanes, depos, nevents, params, out_dev, workspace_dev,
+                                       workspace_bytes, cand[i], stream);
+            if (e == cudaSuccess && st == WS_OK) e = cudaEventRecord(t1, s);
+            if (e == cudaSuccess && st == WS_OK) e = cudaEventSynchronize(t1);
+            float ms = 0.f;
+            if (e == cudaSuccess && st == WS_OK) e = cudaEventElapsedTime(&ms, t0, t1);
+            if (e != cudaSuccess && st == WS_OK) st = cuda_fail(e, "ws_batch_autotune");
+            if (st == WS_OK && ms < best_of[i]) best_of[i] = ms;
+        }
+    }
+    cudaEventDestroy(t0);
+    cudaEventDestroy(t1);
+    if (st != WS_OK) return st;
+    int best = 0;
+    for (int i = 1; i < nc; ++i)
+        if (best_of[i] < best_of[best]) best = i;
+    for (int i = 0; i < nplanes; ++i) planes[i]->batch_upw = cand[best];
+    *units_per_wave_out = cand[best];
+    return WS_OK;
 }
 
 }  // extern "C"

@@ -32,7 +32,8 @@ EXPORTED = ("ws_plane_workspace_bytes", "ws_plane_create", "ws_plane_destroy", "
             "ws_patch_capacity", "ws_rasterize", "ws_scatter", "ws_convolve", "ws_simulate",
             "ws_plane_sync", "ws_plane_clear_status", "ws_plane_trace", "ws_plane_trace_read",
             "ws_convolve_noalloc", "ws_plane_set_wire_conv_variant", "ws_plane_set_response", "ws_plane_set_noise",
-            "ws_simulate_backward", "ws_batch_workspace_bytes", "ws_simulate_batch", "ws_selftest_bounded_wait",
+            "ws_simulate_backward", "ws_batch_workspace_bytes", "ws_simulate_batch", "ws_batch_autotune",
+            "ws_selftest_bounded_wait",
             "ws_status_string", "ws_last_error")
 
 
@@ -128,6 +129,9 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
                                   ctypes.POINTER(WsParams), ctypes.POINTER(P), P, ctypes.c_size_t, ctypes.c_int, P],
             "ws_simulate_backward": [P, ctypes.POINTER(WsDepos), ctypes.POINTER(WsParams), P, P, P, P, P, P,
                                      P, P],
+            "ws_batch_autotune": [ctypes.POINTER(P), ctypes.c_int, ctypes.POINTER(WsDepos), ctypes.c_int,
+                                  ctypes.POINTER(WsParams), ctypes.POINTER(P), P, ctypes.c_size_t, P,
+                                  ctypes.POINTER(ctypes.c_int)],
         }
         for name, args in sig.items():
             fn = getattr(h, name)
@@ -354,6 +358,8 @@ class Plane:
                                       _stream_handle(stream))
         self.info = ws_plane_get_info(self.handle)
         self.device = device
+        self._resp_src = response            # what the plane's spectrum was computed from
+        self._resp_held = self._resp_key(response)
 
     def close(self):
         if getattr(self, "handle", 0):
@@ -423,6 +429,7 @@ class Plane:
 
     def set_response(self, response, stream=None):
         torch = _torch()
+        src = response
         if not hasattr(response, "data_ptr"):
             response = torch.from_numpy(np.ascontiguousarray(response, dtype=np.float32))
         response = response.to(device=self.device, dtype=torch.float32).contiguous()
@@ -430,6 +437,28 @@ class Plane:
         self.response = _require(response, "response", tuple(self.response.shape), self.device)
         _check(load_library().ws_plane_set_response(self.handle, _ptr(self.response), _stream_handle(stream)),
                "ws_plane_set_response")
+        self._resp_src = src
+        self._resp_held = self._resp_key(src)
+
+    @staticmethod
+    def _resp_key(r):
+        """Identity of a response tensor's contents: its storage, offset,
+        shape, strides and version counter (None for non-tensors).  The plane
+        keeps a reference to the tensor it recorded, so that storage cannot be
+        handed to another tensor while the record stands; an in-place change
+        bumps the version."""
+        if not hasattr(r, "untyped_storage"):
+            return None
+        return (r.device, r.untyped_storage().data_ptr(), r.storage_offset(), tuple(r.shape), tuple(r.stride()),
+                r.dtype, r._version)
+
+    def use_response(self, response, stream=None):
+        """Make the plane hold ``response``: recompute the spectrum only if the
+        plane holds another response (or this one changed in place since)."""
+        key = self._resp_key(response)
+        if key is not None and key == self._resp_held:
+            return
+        self.set_response(response, stream)
 
     def set_noise(self, amp, coh=None, group: int = 1, stream=None):
         """Noise term of Eq. 1 for later simulate calls: amplitude spectra of
@@ -482,15 +511,42 @@ class Plane:
         ws_plane_clear_status(self.handle, _stream_handle(stream))
 
 
+def batch_workspace_bytes(planes, units_per_wave: int) -> int:
+    """Bytes of batch workspace for waves of ``units_per_wave`` units (0: 32)."""
+    P = ctypes.c_void_p
+    arr = (P * len(planes))(*[pl.handle for pl in planes])
+    n = ctypes.c_size_t(0)
+    _check(load_library().ws_batch_workspace_bytes(arr, len(planes), int(units_per_wave), ctypes.byref(n)),
+           "ws_batch_workspace_bytes")
+    return int(n.value)
+
+
+def batch_workspace(planes, units_per_wave: int, device="cuda"):
+    """A device workspace (uint8 tensor, 256 bytes of alignment slack) for
+    batches on these planes with waves of up to ``units_per_wave`` units."""
+    return _torch().empty(batch_workspace_bytes(planes, units_per_wave) + 256, dtype=_torch().uint8, device=device)
+
+
 class Batch:
     """Many events x planes through ``ws_simulate_batch``.
 
     ``events[e][p]`` are DeviceDepos of event e seen by plane p; outputs are
     allocated per unit.  ``run()`` enqueues the batch; ``capture()`` records
     it once into a CUDA graph that ``replay()`` relaunches (the buffers stay
-    fixed, so refill the depo tensors in place between replays)."""
+    fixed, so refill the depo tensors in place between replays).
 
-    def __init__(self, planes, events, params: Params, units_per_wave: int = 6, device="cuda"):
+    ``units_per_wave=0`` (the default) leaves the wave size to the library:
+    ``autotune()`` times the candidate sizes on these inputs
+    (``ws_batch_autotune``) and records the fastest on the planes;
+    ``capture()`` runs it first if it has not run.  The workspace is sized
+    for the largest wave these units can form (at most 32)."""
+
+    def __init__(self, planes, events, params: Params, units_per_wave: int = 0, device="cuda",
+                 workspace=None, outs=None):
+        """workspace: a uint8 device tensor from ``batch_workspace`` to share
+        between batches that never run at the same time (default: one of
+        this batch's own); outs: the units' output tensors (default:
+        allocated here)."""
         torch = _torch()
         self.planes = list(planes)
         self.events = events
@@ -502,17 +558,40 @@ class Batch:
         self._planes_c = (P * self.nplanes)(*[pl.handle for pl in self.planes])
         units = [events[e][p] for e in range(self.nevents) for p in range(self.nplanes)]
         self._depos_c = (WsDepos * len(units))(*[d.c() for d in units])
-        self.outs = [torch.empty((self.planes[u % self.nplanes].nwires, self.planes[u % self.nplanes].nticks),
-                                 dtype=torch.float32, device=device) for u in range(len(units))]
+        if outs is None:
+            outs = [torch.empty((self.planes[u % self.nplanes].nwires, self.planes[u % self.nplanes].nticks),
+                                dtype=torch.float32, device=device) for u in range(len(units))]
+        if len(outs) != len(units):
+            raise ValueError(f"outs: expected {len(units)} tensors, got {len(outs)}")
+        self.outs = [_require(o, "outs", (self.planes[u % self.nplanes].nwires, self.planes[u % self.nplanes].nticks),
+                              device) for u, o in enumerate(outs)]
         self._outs_c = (P * len(units))(*[o.data_ptr() for o in self.outs])
-        n = ctypes.c_size_t(0)
-        _check(load_library().ws_batch_workspace_bytes(self._planes_c, self.nplanes, units_per_wave,
-                                                        ctypes.byref(n)), "ws_batch_workspace_bytes")
-        self.workspace = torch.empty(int(n.value) + 256, dtype=torch.uint8, device=device)
+        ws_upw = units_per_wave if units_per_wave > 0 else max(1, min(32, len(units)))
+        need = batch_workspace_bytes(self.planes, ws_upw)
+        if workspace is None:
+            workspace = batch_workspace(self.planes, ws_upw, device)
+        _require(workspace, "workspace", tuple(workspace.shape), device, dtype=torch.uint8)
+        self.workspace = workspace
         self._ws_ptr = (self.workspace.data_ptr() + 255) & ~255
-        self._ws_bytes = int(n.value)
+        self._ws_bytes = int(self.workspace.numel()) - (self._ws_ptr - self.workspace.data_ptr())
+        if self._ws_bytes < need:
+            raise ValueError(f"workspace: {need} bytes needed, {self._ws_bytes} given")
         self._params_c = params.c()
         self.graph = None
+        self.tuned = units_per_wave > 0
+
+    def autotune(self, stream=None) -> int:
+        """Pick the wave size by timing the candidates on these inputs (the
+        library's ws_batch_autotune; synchronises); returns it.  Later runs
+        with units_per_wave=0 use it."""
+        upw = ctypes.c_int(0)
+        _check(load_library().ws_batch_autotune(self._planes_c, self.nplanes, self._depos_c, self.nevents,
+                                                ctypes.byref(self._params_c), self._outs_c, self._ws_ptr,
+                                                self._ws_bytes, _stream_handle(stream), ctypes.byref(upw)),
+               "ws_batch_autotune")
+        self.chosen_units_per_wave = int(upw.value)
+        self.tuned = True
+        return self.chosen_units_per_wave
 
     def run(self, stream=None):
         _check(load_library().ws_simulate_batch(self._planes_c, self.nplanes, self._depos_c, self.nevents,
@@ -523,6 +602,8 @@ class Batch:
 
     def capture(self):
         torch = _torch()
+        if not self.tuned and self.nevents > 0:
+            self.autotune()
         s = torch.cuda.Stream()
         s.wait_stream(torch.cuda.current_stream())
         with torch.cuda.stream(s):

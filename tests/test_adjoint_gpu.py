@@ -134,6 +134,46 @@ def test_autograd_wrapper(ws):
     assert rel(M.detach().cpu().numpy(), ref_m) <= 1e-5
 
 
+def test_autograd_two_forwards_with_different_responses(ws):
+    """Two forwards on one plane under different responses (a prediction and
+    a target) before one backward through both: each forward's gradients
+    are taken under its own response, against the FP64 oracle's."""
+    import torch
+    from paper_2203_02479_gb300 import autograd
+    nw, nt = 32, 900
+    d = inputs.uniform_depos(150, nw, 62, nticks=nt, t_min_us=1.0)
+    R1n = inputs.response("bipolar")
+    R2n = (0.7 * inputs.response("unipolar")).astype(np.float32)
+    R1 = torch.from_numpy(R1n).cuda().requires_grad_(True)
+    R2 = torch.from_numpy(R2n).cuda().requires_grad_(True)
+    plane = ws.Plane(nw, nt, R2n)
+    q = torch.from_numpy(d.q).cuda().requires_grad_(True)
+    x = torch.from_numpy(d.x_mm).cuda().requires_grad_(True)
+    t = torch.from_numpy(d.t_us).cuda().requires_grad_(True)
+    DL = torch.tensor(4e-4, dtype=torch.float64, device="cuda", requires_grad=True)
+    DT = torch.tensor(8.8e-4, dtype=torch.float64, device="cuda", requires_grad=True)
+    M1 = autograd.simulate(q, x, t, DL, DT, R1, plane)
+    M2 = autograd.simulate(q, x, t, DL, DT, R2, plane)
+    loss = (M1 * M2).sum()
+    loss.backward()
+    torch.cuda.synchronize()
+    A1 = oracle.simulate(d.q, d.x_mm, d.t_us, nw, nt, R1n, 10)
+    A2 = oracle.simulate(d.q, d.x_mm, d.t_us, nw, nt, R2n, 10)
+    assert rel(M1.detach().cpu().numpy(), A1) <= 1e-5
+    assert rel(M2.detach().cpu().numpy(), A2) <= 1e-5
+    # dL/dM1 = M2, dL/dM2 = M1: the two backward passes add up
+    r1 = oracle.simulate_backward(d.q, d.x_mm, d.t_us, nw, nt, R1n, 10, A2)
+    r2 = oracle.simulate_backward(d.q, d.x_mm, d.t_us, nw, nt, R2n, 10, A1)
+    mask = kink_mask(d)
+    for got, a, b in ((q.grad, r1[0], r2[0]), (x.grad, r1[1], r2[1]), (t.grad, r1[2], r2[2])):
+        g = got.cpu().numpy()
+        assert rel(g[~mask], (a + b)[~mask]) <= TOL
+    assert rel(R1.grad.cpu().numpy(), r1[5]) <= TOL
+    assert rel(R2.grad.cpu().numpy(), r2[5]) <= TOL
+    assert rel(DL.grad.cpu().numpy(), r1[3] + r2[3]) <= TOL
+    assert rel(DT.grad.cpu().numpy(), r1[4] + r2[4]) <= TOL
+
+
 def test_backward_rejects_fluctuation(ws):
     import torch
     plane = ws.Plane(8, 300, inputs.response())

@@ -1,7 +1,8 @@
-"""The benchmark's error-against-the-oracle report, on the CPU: the oracle
-sample keeps one waveform per plane, and oracle_error_of measures a GPU
-waveform against it (a float32 copy of the oracle's own waveform is within
-float rounding; a planted error shows in both figures)."""
+"""The benchmark's oracle legs on the CPU: the bounded oracle runs (one
+thread and a thread pool) cover the units they report, and the error report
+measures a GPU waveform against the oracle's (a float32 copy of the oracle's
+own waveform is within float rounding; a planted error shows in both
+figures)."""
 import os
 import sys
 
@@ -17,34 +18,51 @@ if ROOT not in sys.path:
 def _tiny_workload():
     planes = [inputs.PlaneSpec(24, 400, inputs.response("bipolar"), 0),
               inputs.PlaneSpec(20, 400, inputs.response("unipolar"), 1)]
-    events = [[inputs.uniform_depos(150, 24, seed=3, nticks=400), inputs.uniform_depos(120, 20, seed=4, nticks=400)]]
+    events = [[inputs.uniform_depos(150, 24, seed=3, nticks=400), inputs.uniform_depos(120, 20, seed=4, nticks=400)],
+              [inputs.uniform_depos(90, 24, seed=5, nticks=400), inputs.uniform_depos(60, 20, seed=6, nticks=400)]]
     return inputs.Workload("tiny", planes, events, True, 0.7, 11)
 
 
-def test_oracle_sample_keeps_one_waveform_per_plane_and_reports_error():
+def test_oracle_runs_and_error_report():
     import bench
     w = _tiny_workload()
-    bench._ORACLE_NEXT[0] = 0
-    kept = {}
-    done, secs, nplanes = bench.oracle_sample(w, 0.0, keep=kept)
-    assert nplanes == 1 and done == 150 and sorted(kept) == [0]
-    bench.oracle_sample(w, 0.0, keep=kept)
-    bench.oracle_sample(w, 0.0, keep=kept)     # plane 0 again: the first waveform stays
-    assert sorted(kept) == [0, 1]
-    assert kept[0].shape == (24, 400) and kept[1].shape == (20, 400)
-    gpu = [kept[0].astype(np.float32), kept[1].astype(np.float32)]
-    rep = bench.oracle_error_of(gpu, kept, w)
-    assert rep["mode"] == "binomial"
-    assert [p["plane_id"] for p in rep["planes"]] == [0, 1]
-    for p in rep["planes"]:
-        assert p["rel_l2"] <= 1e-7 and p["max_abs_over_max"] <= 1e-7
-    bad = [g.copy() for g in gpu]
-    peak = float(np.abs(kept[1]).max())
-    bad[1][5, 100] += 0.5 * peak
-    rep = bench.oracle_error_of(bad, kept, w)
-    assert rep["planes"][0]["rel_l2"] <= 1e-7
-    assert abs(rep["planes"][1]["max_abs_over_max"] - 0.5) <= 1e-6
-    assert rep["planes"][1]["rel_l2"] > 1e-3
+    units = bench.sample_order(w)
+    assert sorted(units) == [(0, 0), (0, 1), (1, 0), (1, 1)]
+    seen = {}
+    dp, secs, n = bench.oracle_units(w, units, 1, 0.0, lambda u, M: seen.__setitem__(u, M))
+    assert n == 1 and dp == w.events[units[0][0]][units[0][1]].n and list(seen) == units[:1]
+    seen.clear()
+    dp, secs, n = bench.oracle_units(w, units, 3, 60.0, lambda u, M: seen.__setitem__(u, M))
+    assert n == 4 and dp == 150 + 120 + 90 + 60 and sorted(seen) == sorted(units)
+    # the unit's waveform is the oracle's simulation with its event id as Philox counter
+    import oracle
+    d = w.events[1][0]
+    ref = oracle.simulate(d.q, d.x_mm, d.t_us, 24, 400, w.planes[0].response, 10, fluctuate=True, p=0.7,
+                          seed=11, event_id=1, plane_id=0)
+    assert np.array_equal(seen[(1, 0)], ref)
+    errs = {u: bench.unit_error(M.astype(np.float32), M) for u, M in seen.items()}
+    rep = bench.error_summary(errs, w)
+    assert rep["units"] == 4 and rep["mode"] == "binomial"
+    assert rep["rel_l2_max"] <= 1e-7 and rep["max_abs_over_max"] <= 1e-7
+    assert sorted(rep["by_plane"]) == ["0", "1"]
+    bad = seen[(0, 1)].astype(np.float32).copy()
+    peak = float(np.abs(seen[(0, 1)]).max())
+    bad[5, 100] += 0.5 * peak
+    errs[(0, 1)] = bench.unit_error(bad, seen[(0, 1)])
+    rep = bench.error_summary(errs, w)
+    assert rep["worst_unit"] == {"event": 0, "plane_id": 1}
+    assert abs(rep["max_abs_over_max"] - 0.5) <= 1e-6 and rep["rel_l2_max"] > 1e-3
+
+
+def test_cpu_baselines_report_cores_and_sample():
+    import bench
+    w = _tiny_workload()
+    gpu = {(0, 0): np.zeros((24, 400), np.float32)}
+    allc, errs = bench.cpu_baselines(w, 0.0, 60.0, gpu)
+    assert allc["kind"] == "oracle" and allc["cores"] == (os.cpu_count() or 1) and allc["value"] > 0
+    assert allc["one_thread"]["cores"] == 1 and allc["one_thread"]["value"] > 0
+    assert "4 of the workload's 4" in allc["sample"]
+    assert list(errs) == [(0, 0)] and errs[(0, 0)]["rel_l2"] == 1.0
 
 
 def test_algorithmic_bytes_of_the_three_plane_step():

@@ -55,3 +55,18 @@ def test_device_depos_lengths():
             wiresim.DeviceDepos(device="cpu", **kw)
     with pytest.raises(ValueError, match="one-dimensional"):
         wiresim.DeviceDepos(np.ones((2, 2)), np.ones((2, 2)), np.ones((2, 2)), device="cpu")
+
+
+def test_response_key_tracks_identity_and_in_place_changes():
+    """Plane.use_response recomputes the spectrum only when the response's
+    key changes: another tensor, another view, or an in-place change (the
+    version counter); a detached alias of the same tensor keeps the key."""
+    R = torch.ones((21, 200), dtype=torch.float32)
+    k = wiresim.Plane._resp_key(R)
+    assert k == wiresim.Plane._resp_key(R)
+    assert k == wiresim.Plane._resp_key(R.detach())        # same storage, shared version counter
+    assert k != wiresim.Plane._resp_key(R.clone())
+    assert k != wiresim.Plane._resp_key(R[:, 1:])
+    R.mul_(2.0)
+    assert k != wiresim.Plane._resp_key(R)
+    assert wiresim.Plane._resp_key(np.ones((21, 200), np.float32)) is None

@@ -7,7 +7,8 @@ Tolerances:
     where FP32 and FP64 round q*w to different electron counts (those differ
     by at most one electron); normal-branch bins differ by at most one
     electron, in under 1% of bins; per-bin means and variances over seeds
-    match the binomial's.
+    match the binomial's; simulated waveforms within relative L2 1e-5 of
+    the oracle's (the one-electron differences move a waveform by ~1e-6).
 """
 import math
 
@@ -20,6 +21,11 @@ from paper_2203_02479_gb300 import inputs
 pytestmark = pytest.mark.gpu
 
 REL_L2 = 1e-5
+# Binomial waveforms: the FP32 transforms contribute ~5e-7 and the rare
+# one-electron differences (bins where FP32 and FP64 round q*w to different
+# counts, FP32 normal deviates) about as much; measured 1.0-1.4e-6 on the
+# three-plane event, so 1e-5 leaves a factor of ~7 and fails a 1e-4 drift.
+REL_L2_BINOMIAL = 1e-5
 
 
 @pytest.fixture(scope="module")
@@ -360,7 +366,7 @@ def test_three_planes_fluctuated_full_size(ws):
         assert abs(S.sum() - ref.sum()) <= 1e-4 * ref.sum()
         out = to_np(plane.simulate(dd, params))
         ref_m = oracle.convolve_fft(ref, sp.response, 10)
-        assert rel_l2(out, ref_m) <= 1e-3
+        assert rel_l2(out, ref_m) <= REL_L2_BINOMIAL
         assert plane.status() == 0
 
 
@@ -461,7 +467,7 @@ def test_three_planes_in_the_benchmark_launch_configuration(ws):
         M = oracle.convolve_fft(S, sp.response, 10)
         for upw in (1, 2, 3):
             assert np.isfinite(outs[upw][p]).all()
-            assert rel_l2(outs[upw][p], M) <= 1e-3, (upw, p)
+            assert rel_l2(outs[upw][p], M) <= REL_L2_BINOMIAL, (upw, p)
             assert rel_l2(outs[upw][p], outs[1][p]) <= 1e-6
     for pl in planes:
         assert pl.status() == 0

@@ -6,13 +6,17 @@ hand over a workspace.  ws_convolve_noalloc takes only the response, the
 input grid and the output grid and keeps its scratch in a fixed 16 MiB array
 inside the library.  These checks call it through the C ABI twice in a row
 (the array keeps the previous call's contents) and compare each result with
-the workspace-based ws_convolve on the same inputs, within the relative-L2
-tolerance the other GPU tests use.  This file is collected last on purpose.
+the workspace-based ws_convolve on the same inputs and with the FP64
+oracle's convolution (Eq. 2), within the relative-L2 tolerance the other GPU
+tests use; a third call writes its output over its input (the header allows
+grid_dev == out_dev).  This file is collected last on purpose.
 """
 import ctypes
 
 import numpy as np
 import pytest
+
+import oracle
 
 pytestmark = pytest.mark.gpu
 
@@ -60,6 +64,15 @@ def test_noalloc_matches_workspace_convolution_twice(lib):
         got = out.cpu().numpy().astype(np.float64)
         assert np.isfinite(got).all()
         assert _rel_l2(got, ref.cpu().numpy().astype(np.float64)) <= REL_L2
+        exact = oracle.convolve_fft(S.cpu().numpy().astype(np.float64), R, c, circ)
+        assert _rel_l2(got, exact) <= REL_L2
+        # in place: the output buffer is the input grid
+        st = lib.ws_convolve_noalloc(ctypes.byref(d), ctypes.c_void_p(Rd.data_ptr()),
+                                     ctypes.c_void_p(S.data_ptr()), ctypes.c_void_p(S.data_ptr()),
+                                     ctypes.c_void_p(stream))
+        assert st == 0, lib.ws_last_error()
+        torch.cuda.synchronize()
+        assert _rel_l2(S.cpu().numpy().astype(np.float64), exact) <= REL_L2
 
 
 def test_noalloc_rejects_planes_beyond_its_scratch(lib):
