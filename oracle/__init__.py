@@ -60,7 +60,7 @@ def _lib():
             h.wso_survive_threshold.argtypes = [ctypes.c_double]
             h.wso_survive_threshold.restype = ctypes.c_uint32
             h.wso_binomial.argtypes = [ctypes.c_int64, ctypes.c_double, ctypes.c_int, _u32p,
-                                       ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32]
+                                       ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32]
             h.wso_binomial.restype = ctypes.c_int64
             h.wso_binomial_invert_many.argtypes = [ctypes.c_int64, ctypes.c_double, ctypes.c_int64, _u32p,
                                                    np.ctypeslib.ndpointer(np.int64, flags="C_CONTIGUOUS")]
@@ -145,19 +145,25 @@ def survive_threshold(p: float) -> int:
     return int(_lib().wso_survive_threshold(float(p)))
 
 
-def binomial(N: int, p: float, seed: int, bin_index: int, depo: int, event_id: int = 0,
-             plane_id: int = 0, exact_max: int = EXACT_MAX) -> int:
-    """Binomial(N, p) survivor count of one bin (Sec. 3.1 reading).
+def binomial(N: int, p: float, seed: int, wire: int, tick: int, depo: int, event_id: int = 0,
+             plane_id: int = 0, exact_max: int = EXACT_MAX, nticks: int = 6000) -> int:
+    """Binomial(N, p) survivor count of bin (wire, tick) of a depo's patch on a
+    grid of nticks ticks (Sec. 3.1 reading): word tick % 4 of the Philox
+    block of the bin's quad (counter (0, wire*ceil(nticks/4) + tick // 4,
+    depo, event << 4 | plane)); inversion of its top 24 bits for
+    N <= exact_max, else Box-Muller on its two 16-bit halves.
 
     Pinned by the exact pmf over every value of the inversion's random word
-    (exact branch), chi-square against scipy.stats.binom over many bins, and
-    the first two moments (normal branch)."""
+    (exact branch), chi-square against scipy.stats.binom over many bins, the
+    independence of the four bins of a quad, and the normal branch's moments
+    and distribution."""
     if exact_max > EXACT_CAP:
         raise ValueError(f"exact_max above {EXACT_CAP}")
     key = seed_key(seed)
     evpl = ((event_id << 4) | (plane_id & 15)) & 0xFFFFFFFF
-    return int(_lib().wso_binomial(int(N), float(p), int(exact_max), key,
-                                   bin_index & 0xFFFFFFFF, depo & 0xFFFFFFFF, evpl))
+    quad = (wire * ((nticks + 3) // 4) + tick // 4) & 0xFFFFFFFF
+    return int(_lib().wso_binomial(int(N), float(p), int(exact_max), key, quad, tick % 4,
+                                   depo & 0xFFFFFFFF, evpl))
 
 
 def binomial_invert(N: int, p: float, x0) -> np.ndarray:

@@ -120,16 +120,21 @@ int wso_axis_weights(double mu, double sigma, double delta, double nsig,
 /* Binomial charge fluctuation (Sec. 3.1: the CPU reference draws binomial
  * numbers; the sampler itself is not given).  Reading: each bin holds
  * N = floor(q*w + 1/2) electrons, each surviving independently with
- * probability p; the bins draw independently from Philox block 0 keyed by
- * the seed, with the counter (0, global bin, depo index, event << 4 | plane).
+ * probability p; the bins draw independently.  Random stream: Philox4x32-10
+ * keyed by the seed; one block serves a quad, the four consecutive ticks
+ * 4g .. 4g+3 of one wire w of one depo, with the counter
+ * (0, w*ceil(nticks/4) + g, depo index, event << 4 | plane), and bin (w, k)
+ * takes word k % 4 of its quad's block.  That one word decides the bin:
  *   - N <= exact_max (at most WSO_EXACT_CAP): inversion of the Binomial CDF
- *     in single precision from word 0 (see wso_binomial_invert).
- *   - N > exact_max: normal approximation from words 0 and 1,
- *     u1 = (x0 + 1/2)/2^32, u2 = (x1 + 1/2)/2^32,
- *     z = sqrt(-2 ln u1) cos(2 pi u2),
+ *     in single precision from the word's top 24 bits (see
+ *     wso_binomial_invert).
+ *   - N > exact_max: normal approximation, Box-Muller on the word's two
+ *     16-bit halves, u1 = (x >> 16 + 1/2)/2^16, u2 = (x & 0xFFFF + 1/2)/2^16,
+ *     z = sqrt(-2 ln u1) cos(2 pi u2) (so |z| <= sqrt(2 ln 2^17) = 4.86),
  *     k = clamp(floor(N p + z sqrt(N p (1 - p)) + 1/2), 0, N), p = T/2^32
  *     with T = floor(p * 2^32).
- *   - p >= 1 keeps every electron, p <= 0 none. */
+ *   - p >= 1 keeps every electron, p <= 0 none.
+ * The four words of a block are independent, so are the bins of a quad. */
 #define WSO_EXACT_CAP 64
 
 uint32_t wso_survive_threshold(double p)
@@ -182,20 +187,24 @@ void wso_binomial_invert_many(int64_t N, double p, int64_t n, const uint32_t* x0
     for (int64_t i = 0; i < n; ++i) k[i] = wso_binomial_invert(N, p, x0[i]);
 }
 
+/* Quad index and word of bin (w, k) on a grid of nticks ticks. */
+static uint32_t wso_quad(int64_t w, int64_t k, int nticks) { return (uint32_t)(w * ((nticks + 3) / 4) + k / 4); }
+
 int64_t wso_binomial(int64_t N, double p, int exact_max, const uint32_t key[2],
-                     uint32_t bin, uint32_t depo, uint32_t evpl)
+                     uint32_t quad, uint32_t word, uint32_t depo, uint32_t evpl)
 {
     if (N <= 0) return 0;
     if (!(p > 0.0)) return 0;
     if (p >= 1.0) return N;
-    if (exact_max > WSO_EXACT_CAP) return -1;
+    if (exact_max > WSO_EXACT_CAP || word > 3u) return -1;
     uint32_t T = wso_survive_threshold(p);
     uint32_t ctr[4], x[4];
-    ctr[0] = 0; ctr[1] = bin; ctr[2] = depo; ctr[3] = evpl;
+    ctr[0] = 0; ctr[1] = quad; ctr[2] = depo; ctr[3] = evpl;
     wso_philox4x32_10(ctr, key, x);
-    if (N <= exact_max) return wso_binomial_invert(N, p, x[0]);
-    double u1 = ((double)x[0] + 0.5) / 4294967296.0;
-    double u2 = ((double)x[1] + 0.5) / 4294967296.0;
+    const uint32_t xw = x[word];
+    if (N <= exact_max) return wso_binomial_invert(N, p, xw);
+    double u1 = ((double)(xw >> 16) + 0.5) / 65536.0;
+    double u2 = ((double)(xw & 0xFFFFu) + 0.5) / 65536.0;
     double z = sqrt(-2.0 * log(u1)) * cos(2.0 * M_PI * u2);
     double pe = (double)T / 4294967296.0;
     double mean = (double)N * pe;
@@ -346,8 +355,8 @@ int64_t wso_raster_scatter(int64_t n, const double* q, const double* x_mm, const
                 double val;
                 if (fluctuate) {
                     int64_t N = (int64_t)floor(qi * wt[b] * wx[a] + 0.5);
-                    uint32_t bin = (uint32_t)(w * (int64_t)nticks + k);
-                    val = (double)wso_binomial(N, p, exact_max, key, bin, (uint32_t)i, evpl);
+                    val = (double)wso_binomial(N, p, exact_max, key, wso_quad(w, k, nticks), (uint32_t)(k % 4),
+                                               (uint32_t)i, evpl);
                 } else {
                     val = p * qi * wt[b] * wx[a];
                 }

@@ -5,7 +5,9 @@ freeze the oracle's exact integer outputs so that an accidental change to
 its sampler or random stream shows up as a diff:
   * philox_blocks.txt: Philox4x32-10 blocks for a few counters and keys;
   * binomial_inversion.txt: exact-branch survivor counts (CDF inversion of
-    the Sec. 3.1 reading) for fixed (N, p) and 32-bit words.
+    the Sec. 3.1 reading) for fixed (N, p) and 32-bit words;
+  * binomial_bins.txt: per-bin survivor counts of both branches for fixed
+    (seed, event, plane, depo, wire, tick) on the quad random stream.
 Run from the repository root: python tests/golden/make_golden.py
 """
 import os
@@ -21,6 +23,11 @@ import oracle  # noqa: E402
 PHILOX_CASES = [((0, 0, 0, 0), (0, 0)), ((1, 2, 3, 4), (5, 6)), ((0xFFFFFFFF, 7, 0x1234, 9), (0xDEADBEEF, 0x12345)),
                 ((0, 3000 * 6000 + 17, 99999, (5 << 4) | 2), (0x89ABCDEF, 0x01234567))]
 INV_CASES = [(1, 0.7), (5, 0.7), (20, 0.7), (32, 0.3), (64, 0.5), (13, 0.999), (9, 0.01)]
+# (N, p, seed, wire, tick, depo, event, plane, nticks): exact and normal branches, all four words of a quad
+BIN_CASES = [(20, 0.7, 0xDEADBEEF12345, 17, 4000 + t, 99, 5, 2, 6000) for t in range(4)] + \
+            [(5000, 0.7, 0xDEADBEEF12345, 17, 4000 + t, 99, 5, 2, 6000) for t in range(4)] + \
+            [(33, 0.3, 1001, 0, 0, 0, 0, 0, 6000), (3, 0.5, 7, 959, 5999, 123456, 63, 1, 6000),
+             (40000, 0.5, 1, 2, 3, 4, 0, 0, 6250), (60, 0.62, 9, 3, 6249, 1, 0, 0, 6250)]
 
 
 def words() -> np.ndarray:
@@ -42,6 +49,11 @@ def main():
         for N, p in INV_CASES:
             k = oracle.binomial_invert(N, p, w)
             f.write(f"{N} {p!r} : " + " ".join(str(int(v)) for v in k) + "\n")
+    with open(os.path.join(HERE, "binomial_bins.txt"), "w") as f:
+        f.write("# N p seed wire tick depo event plane nticks -> count (oracle.binomial, exact_max 32)\n")
+        for N, p, seed, w, t, d, ev, pl, nt in BIN_CASES:
+            k = oracle.binomial(N, p, seed, w, t, d, event_id=ev, plane_id=pl, nticks=nt)
+            f.write(f"{N} {p!r} {seed} {w} {t} {d} {ev} {pl} {nt} {k}\n")
 
 
 if __name__ == "__main__":

@@ -152,18 +152,23 @@ def test_autograd_two_forwards_with_different_responses(ws):
     t = torch.from_numpy(d.t_us).cuda().requires_grad_(True)
     DL = torch.tensor(4e-4, dtype=torch.float64, device="cuda", requires_grad=True)
     DT = torch.tensor(8.8e-4, dtype=torch.float64, device="cuda", requires_grad=True)
+    rng = np.random.Generator(np.random.PCG64(63))
+    T1 = rng.standard_normal((nw, nt)) * 20
+    T2 = rng.standard_normal((nw, nt)) * 20
     M1 = autograd.simulate(q, x, t, DL, DT, R1, plane)
     M2 = autograd.simulate(q, x, t, DL, DT, R2, plane)
-    loss = (M1 * M2).sum()
+    # L = <M1, T1> + <M2, T2>: dL/dM1 = T1 and dL/dM2 = T2 exactly
+    loss = (M1 * torch.from_numpy(T1.astype(np.float32)).cuda()).sum() + \
+        (M2 * torch.from_numpy(T2.astype(np.float32)).cuda()).sum()
     loss.backward()
     torch.cuda.synchronize()
     A1 = oracle.simulate(d.q, d.x_mm, d.t_us, nw, nt, R1n, 10)
     A2 = oracle.simulate(d.q, d.x_mm, d.t_us, nw, nt, R2n, 10)
     assert rel(M1.detach().cpu().numpy(), A1) <= 1e-5
     assert rel(M2.detach().cpu().numpy(), A2) <= 1e-5
-    # dL/dM1 = M2, dL/dM2 = M1: the two backward passes add up
-    r1 = oracle.simulate_backward(d.q, d.x_mm, d.t_us, nw, nt, R1n, 10, A2)
-    r2 = oracle.simulate_backward(d.q, d.x_mm, d.t_us, nw, nt, R2n, 10, A1)
+    # the two backward passes add up, each under its own response
+    r1 = oracle.simulate_backward(d.q, d.x_mm, d.t_us, nw, nt, R1n, 10, T1.astype(np.float32).astype(np.float64))
+    r2 = oracle.simulate_backward(d.q, d.x_mm, d.t_us, nw, nt, R2n, 10, T2.astype(np.float32).astype(np.float64))
     mask = kink_mask(d)
     for got, a, b in ((q.grad, r1[0], r2[0]), (x.grad, r1[1], r2[1]), (t.grad, r1[2], r2[2])):
         g = got.cpu().numpy()

@@ -5,7 +5,7 @@ An impact plane bins the pitch axis at pitch / I (fine row w*I + i) and
 convolves each sub-position's rows with its own response slice,
 M = sum_i R_i (*) S_i; the oracle does the same with its own raster on the
 finer grid and numpy's FFT per slice.  Expected-value mode: relative L2
-<= 1e-5; binomial mode: the whole waveform within 1e-3 (rare one-electron
+<= 1e-5; binomial mode: the whole waveform within 1e-4 (rare one-electron
 differences, as in the plain path).
 """
 import numpy as np
@@ -54,7 +54,7 @@ def test_impact_simulate_matches_oracle(ws, nw, nt, I, circular, fluct):
     got = to_np(pl.simulate(ws.DeviceDepos.from_plane_depos(d), params))
     ref = oracle.simulate_impacts(d.q, d.x_mm, d.t_us, nw, nt, R, 10, circular=circular, fluctuate=fluct, p=0.7,
                                   seed=55, event_id=3, plane_id=1)
-    assert rel_l2(got, ref) <= (1e-3 if fluct else REL_L2)
+    assert rel_l2(got, ref) <= (1e-4 if fluct else REL_L2)
     assert pl.status() == 0
 
 

@@ -125,7 +125,8 @@ def test_moments_over_seeds(ws):
 
 def test_three_planes_full_size(ws):
     """The benchmark event with fluctuate = 2 against the oracle: whole
-    waveforms within 1e-3 (rare depos take a different draw) and the
+    waveforms within 1e-5 (rare depos take a different draw; measured
+    5.6-7.4e-7) and the
     grids' total charge within 1e-4."""
     import torch
     w = inputs.three_planes()
@@ -136,7 +137,7 @@ def test_three_planes_full_size(ws):
         S = oracle.raster_scatter(dp.q, dp.x_mm, dp.t_us, sp.nwires, sp.nticks, fluctuate=2, p=0.7, seed=w.seed,
                                   plane_id=sp.plane_id)
         ref = oracle.convolve_fft(S, sp.response, 10)
-        assert np.linalg.norm(got - ref) / np.linalg.norm(ref) <= 1e-3
+        assert np.linalg.norm(got - ref) / np.linalg.norm(ref) <= 1e-5
         delta = np.zeros((21, 200), np.float32); delta[10, 0] = 1.0
         pl.set_response(delta)
         Sg = to_np(pl.simulate(ws.DeviceDepos.from_plane_depos(dp), params))

@@ -243,7 +243,7 @@ def test_binomial_exact_branch_matches_binomial_pmf():
     Binomial(N, p) (chi-square against scipy.stats.binom)."""
     stats = pytest.importorskip("scipy.stats")
     N, p, m = 20, 0.7, 20000
-    k = np.array([oracle.binomial(N, p, seed=77, bin_index=i, depo=3) for i in range(m)])
+    k = np.array([oracle.binomial(N, p, seed=77, wire=i // 6000, tick=i % 6000, depo=3) for i in range(m)])
     assert k.min() >= 0 and k.max() <= N
     obs = np.bincount(k, minlength=N + 1).astype(float)
     exp = stats.binom.pmf(np.arange(N + 1), N, p) * m
@@ -294,7 +294,7 @@ def test_binomial_inversion_edges():
 
 def test_binomial_exact_max_is_capped():
     with pytest.raises(ValueError):
-        oracle.binomial(10, 0.7, 1, 2, 3, exact_max=oracle.EXACT_CAP + 1)
+        oracle.binomial(10, 0.7, 1, 0, 2, 3, exact_max=oracle.EXACT_CAP + 1)
     with pytest.raises(ValueError):
         oracle.raster_scatter([1.0], [2.0], [3.0], 4, 10, fluctuate=True, p=0.7, exact_max=100)
 
@@ -302,19 +302,64 @@ def test_binomial_exact_max_is_capped():
 def test_binomial_normal_branch_moments():
     """Normal branch (N > exact_max): mean N p and variance N p (1 - p)."""
     N, p, m = 5000, 0.7, 20000
-    k = np.array([oracle.binomial(N, p, seed=78, bin_index=i, depo=9, event_id=2) for i in range(m)],
+    k = np.array([oracle.binomial(N, p, seed=78, wire=i // 6000, tick=i % 6000, depo=9, event_id=2)
+                  for i in range(m)],
                  dtype=float)
     var = N * p * (1 - p)
     assert k.mean() == pytest.approx(N * p, abs=4 * math.sqrt(var / m))
     assert k.var() == pytest.approx(var, rel=0.05)
 
 
+def test_binomial_normal_branch_distribution():
+    """Normal branch: the standardised counts follow the normal distribution
+    that Box-Muller on the word's 16-bit halves draws (the CDF at seven
+    points within its sampling error plus the half-count rounding), and no
+    draw passes the sampler's bound |z| <= sqrt(2 ln 2^17)."""
+    N, p, m = 20000, 0.3, 40000
+    k = np.array([oracle.binomial(N, p, seed=79, wire=i // 4000, tick=i % 4000, depo=4, nticks=4000)
+                  for i in range(m)], dtype=float)
+    mean = N * oracle.survive_threshold(p) / 2 ** 32
+    sd = math.sqrt(mean * (1 - oracle.survive_threshold(p) / 2 ** 32))
+    z = (k - mean) / sd
+    for c in (-2.5, -1.5, -0.7, 0.0, 0.7, 1.5, 2.5):
+        phi = 0.5 * math.erfc(-c / math.sqrt(2))
+        assert abs((z <= c).mean() - phi) <= 4 * math.sqrt(phi * (1 - phi) / m) + 0.5 / sd * 0.4
+    assert np.abs(z).max() <= math.sqrt(2 * math.log(2 ** 17)) + 1.0 / sd
+    assert np.abs(z).max() > 3.5
+
+
+def test_binomial_bins_of_a_quad_are_independent():
+    """The four bins of a quad share one Philox block, one word each: over
+    many quads, the counts of two bins of the same quad are uncorrelated
+    and their joint frequencies factor (chi-square test of independence),
+    for two exact-branch bins and for an exact- and a normal-branch bin; a
+    mix-up of the words (two bins reading one word) fails both."""
+    stats = pytest.importorskip("scipy.stats")
+    m = 12000
+    for (na, ta), (nb, tb) in (((20, 0), (20, 1)), ((20, 2), (20, 3)), ((20, 1), (3000, 2)), ((12, 3), (12, 0))):
+        a = np.array([oracle.binomial(na, 0.6, seed=80, wire=q // 1500, tick=4 * (q % 1500) + ta, depo=7)
+                      for q in range(m)], dtype=float)
+        b = np.array([oracle.binomial(nb, 0.6, seed=80, wire=q // 1500, tick=4 * (q % 1500) + tb, depo=7)
+                      for q in range(m)], dtype=float)
+        r = np.corrcoef(a, b)[0, 1]
+        assert abs(r) < 4 / math.sqrt(m), (ta, tb, r)
+        ca = np.digitize(a, np.quantile(a, [0.25, 0.5, 0.75]))
+        cb = np.digitize(b, np.quantile(b, [0.25, 0.5, 0.75]))
+        table = np.zeros((4, 4))
+        np.add.at(table, (ca, cb), 1)
+        table = table[table.sum(1) > 0][:, table.sum(0) > 0]
+        assert stats.chi2_contingency(table)[1] > 1e-3, (ta, tb)
+    # the same bin is the same draw; the quad's other words are other draws
+    one = [oracle.binomial(20, 0.6, seed=81, wire=3, tick=t, depo=2) for t in range(8, 12)]
+    assert one == [oracle.binomial(20, 0.6, seed=81, wire=3, tick=t, depo=2) for t in range(8, 12)]
+
+
 def test_binomial_special_cases():
-    assert oracle.binomial(0, 0.7, 1, 2, 3) == 0
-    assert oracle.binomial(40, 1.0, 1, 2, 3) == 40
-    assert oracle.binomial(40, 0.0, 1, 2, 3) == 0
+    assert oracle.binomial(0, 0.7, 1, 0, 2, 3) == 0
+    assert oracle.binomial(40, 1.0, 1, 0, 2, 3) == 40
+    assert oracle.binomial(40, 0.0, 1, 0, 2, 3) == 0
     # every draw depends on (seed, bin, depo, event/plane): different keys differ
-    vals = {oracle.binomial(30, 0.5, s, 2, 3) for s in range(40)}
+    vals = {oracle.binomial(30, 0.5, s, 0, 2, 3) for s in range(40)}
     assert len(vals) > 5
 
 
@@ -451,6 +496,12 @@ def test_oracle_matches_its_golden_fixtures():
         N, p = head.split()
         got = oracle.binomial_invert(int(N), float(p), words)
         assert list(got) == [int(c) for c in counts.split()], (N, p)
+    for line in open(os.path.join(gdir, "binomial_bins.txt")):
+        if line.startswith("#"):
+            continue
+        N, p, seed, w, t, d, ev, pl, nt, k = line.split()
+        assert oracle.binomial(int(N), float(p), int(seed), int(w), int(t), int(d), event_id=int(ev),
+                               plane_id=int(pl), nticks=int(nt)) == int(k), line
 
 
 def test_convolution_parseval_against_a_direct_dft():
