@@ -73,10 +73,11 @@ def _functions_importing_oracle(path):
 
 
 def test_oracle_users_outside_tests():
-    """bench.py runs the oracle only in its CPU-baseline sample (also the
-    reference arm); __graft_entry__ only builds it and uses it in smoke()."""
+    """bench.py runs the oracle only through oracle_unit (its CPU baselines,
+    the error against the oracle and the reference arm); __graft_entry__
+    only builds it and uses it in smoke()."""
     fns, top = _functions_importing_oracle(os.path.join(ROOT, "bench.py"))
-    assert not top and fns == {"oracle_sample"}
+    assert not top and fns == {"oracle_unit"}
     fns, top = _functions_importing_oracle(os.path.join(ROOT, "__graft_entry__.py"))
     assert not top and fns <= {"build", "smoke"}
 
