@@ -887,6 +887,7 @@ def run_gpu(args):
                    "fluctuate": w.fluctuate, "p_survive": w.p_survive, "seed": w.seed,
                    "fft_len_tick": planes[0].info.fft_len_tick, "units_per_wave": upw,
                    "wire_conv_variant": [pl.info.wire_conv_variant for pl in planes],
+                   "batch_wire_conv_variant": planes[0].info.batch_wire_conv_variant,
                    "path": "ws_simulate_batch over every (event, plane) unit in waves of units_per_wave (chosen by "
                            "ws_batch_autotune; wave k on stream k % 3), replayed from a CUDA graph",
                    "l2": "flushed between timed steps (512 MiB write); a step's buffers (~5 GB) exceed L2"},

@@ -125,7 +125,12 @@ typedef struct {
     double DT_mm2_us;         /* transverse diffusion constant              */
     double v_mm_us;           /* drift speed                                */
     int32_t fluctuate;        /* 0: expected value p*q*w per bin;
-                                 1: Binomial(floor(q*w + 1/2), p) per bin;
+                                 1: Binomial(floor(q*w + 1/2), p) per bin,
+                                    independent bins; bin (w, k) takes word
+                                    k % 4 of the Philox block with counter
+                                    (0, w*ceil(nticks/4) + k/4, depo,
+                                    event << 4 | plane), one block per
+                                    four ticks of a wire;
                                  2: charge-conserving: K ~ Binomial(
                                     floor(q + 1/2), p) survivors per depo,
                                     spread over its bins multinomially by
@@ -140,8 +145,9 @@ typedef struct {
     uint32_t event_id;        /* < 2^28, part of the Philox counter         */
     int32_t fluct_exact_max;  /* bins with N <= this sample Binomial(N, p)
                                  by inversion of its CDF (single precision,
-                                 one Philox word); larger N use the normal
-                                 approximation; 0 .. 64                     */
+                                 the word's top 24 bits); larger N use the
+                                 normal approximation (Box-Muller on the
+                                 word's two 16-bit halves); 0 .. 64         */
     int32_t precision;        /* WS_PREC_FP32: float throughout;
                                  WS_PREC_FP32_COMP: float with compensated
                                  (TwoSum) scatter-add and FP64 edge weights
@@ -189,6 +195,11 @@ typedef struct {
                                    by bulk copies, first and middle passes
                                    in place, the last pass writing global
                                    memory); 0: the generic kernels          */
+    int32_t batch_units_per_wave;  /* wave size ws_batch_autotune recorded
+                                      on this plane (0: none)               */
+    int32_t batch_wire_conv_variant; /* wire-convolution kernel of batches
+                                      whose first plane this is (-1: the
+                                      plane's own)                          */
 } ws_plane_info;
 
 typedef struct ws_plane ws_plane;
@@ -198,8 +209,9 @@ typedef struct ws_plane ws_plane;
  * word, scan scratch, noise spectra; with impacts I > 1 also the fine grid
  * of nwires*I x nticks floats and I times the first spectrum and the
  * response spectrum).  Host-only; fails with WS_ERR_UNSUPPORTED_SIZE if the
- * FFT length is not 2/3/5-smooth or exceeds 14336, or for FP64 buffers on an
- * impact plane, and with WS_ERR_INVALID_ARG for impacts outside 0 .. 32. */
+ * FFT length is not 2/3/5-smooth or exceeds 14336, for FP64 buffers on an
+ * impact plane, or for a grid (fine grid on an impact plane) of 2^31 cells
+ * or more, and with WS_ERR_INVALID_ARG for impacts outside 0 .. 32. */
 ws_status ws_plane_workspace_bytes(const ws_plane_desc* desc, size_t* bytes);
 
 /* Create a plane over a caller-owned device workspace (>= the size above,
@@ -332,6 +344,11 @@ ws_status ws_simulate_batch(ws_plane* const* planes, int nplanes, const ws_depos
  * to *units_per_wave_out and records it on every plane of the call for
  * later calls with units_per_wave == 0.  Arguments as for
  * ws_simulate_batch; out_dev ends up holding the batch's result.
+ * Then, at that wave size, it times the wire-convolution kernels the
+ * planes allow (one kernel serves every unit of a launch) and records the
+ * fastest on planes[0] for batches, unless a kernel was already chosen for
+ * batches on planes[0] (by an earlier run or ws_plane_set_wire_conv_variant);
+ * the planes keep their own kernels for single-plane calls.
  * SYNCHRONISES `stream` (so it cannot be captured into a graph: call it
  * before capturing).  WS_ERR_WORKSPACE if no candidate fits. */
 ws_status ws_batch_autotune(ws_plane* const* planes, int nplanes, const ws_depos* depos, int nevents,
@@ -391,8 +408,9 @@ ws_status ws_plane_sync(ws_plane* plane, void* stream, uint32_t* bits);
 ws_status ws_plane_clear_status(ws_plane* plane, void* stream);
 
 /* Override the autotuned wire-convolution kernel (0..9, see
- * ws_plane_info.wire_conv_variant; 4..9 need linear mode); all variants
- * compute the same sum. */
+ * ws_plane_info.wire_conv_variant; 4..9 need linear mode) for this plane's
+ * calls and for batches whose first plane it is; all variants compute the
+ * same sum. */
 ws_status ws_plane_set_wire_conv_variant(ws_plane* plane, int variant);
 
 /* Launch tracing (timing of each kernel with CUDA events).  With

@@ -71,20 +71,19 @@ __device__ __forceinline__ int invert_binomial(int N, uint32_t x0, const RasterA
     return invert_binomial_s(N, x0, a.inv_base, a.inv_r, a.inv_flip, recip);
 }
 
-// Normal approximation of Binomial(N, p) from words 0, 1 of Philox block 0
-// (Box-Muller), with the integer part of N p taken exactly from the 64-bit
-// product N T.  In single precision the approximation itself is far coarser
-// than the rounding, so the fast logarithm, cosine and reciprocal square root
-// are used; the FP64 path uses the double-precision functions.
+// Normal approximation of Binomial(N, p) from Box-Muller uniforms u1, u2,
+// with the integer part of N p taken exactly from the 64-bit product N T.
+// In single precision the approximation itself is far coarser than the
+// rounding, so the fast logarithm, cosine and reciprocal square root are
+// used; the FP64 path uses the double-precision functions.
 template <int P>
-__device__ __forceinline__ int normal_draw(uint4 x, int N, const RasterArgs& a) {
+__device__ __forceinline__ int normal_from_uniforms(double du1, double du2, float fu1, float fu2, int N,
+                                                    const RasterArgs& a) {
     const uint64_t nt = (uint64_t)(uint32_t)N * (uint64_t)a.T;
     const int ipart = (int)(uint32_t)(nt >> 32);
     if constexpr (P == 2) {
         const double two_m32 = 2.3283064365386962890625e-10;
-        const double u1 = ((double)x.x + 0.5) * two_m32;
-        const double u2 = ((double)x.y + 0.5) * two_m32;
-        const double z = sqrt(-2.0 * log(u1)) * cospi(2.0 * u2);
+        const double z = sqrt(-2.0 * log(du1)) * cospi(2.0 * du2);
         const double frac = (double)(uint32_t)nt * two_m32;
         const double pe = (double)a.T * two_m32;
         const double sd = sqrt(((double)ipart + frac) * (1.0 - pe));
@@ -92,19 +91,39 @@ __device__ __forceinline__ int normal_draw(uint4 x, int N, const RasterArgs& a) 
         return k < 0 ? 0 : (k > N ? N : k);
     } else {
         const float two_m32 = 2.3283064365386963e-10f;  // 2^-32
-        const float u1 = fmaf((float)x.x, two_m32, 0.5f * two_m32);
-        const float u2 = fmaf((float)x.y, two_m32, 0.5f * two_m32);
         // z sd = sqrt(-2 ln u1 * N p (1 - p)) cos(2 pi u2), one square root
         // (reciprocal-square-root form); cos(2 pi u2) = -cos(2 pi (u2 - 1/2)),
         // argument within [-pi, pi]
         const float frac = (float)(uint32_t)nt * two_m32;
         const float pe = (float)a.T * two_m32;
-        const float t = fmaxf(-2.f * __logf(u1), 0.f) * (((float)ipart + frac) * (1.f - pe));
+        const float t = fmaxf(-2.f * __logf(fu1), 0.f) * (((float)ipart + frac) * (1.f - pe));
         const float rs = t > 0.f ? t * rsqrtf(t) : 0.f;
-        const float dz = -rs * __cosf(6.28318530717958648f * (u2 - 0.5f));
+        const float dz = -rs * __cosf(6.28318530717958648f * (fu2 - 0.5f));
         const int k = ipart + (int)floorf(frac + dz + 0.5f);
         return k < 0 ? 0 : (k > N ? N : k);
     }
+}
+
+// The per-bin normal branch: Box-Muller on the two 16-bit halves of the
+// bin's word, u1 = (x >> 16 + 1/2) / 2^16, u2 = (x & 0xFFFF + 1/2) / 2^16
+// (both exact in float).
+template <int P>
+__device__ __forceinline__ int normal_word(uint32_t x, int N, const RasterArgs& a) {
+    const float f1 = ((float)(x >> 16) + 0.5f) * (1.0f / 65536.0f);
+    const float f2 = ((float)(x & 0xFFFFu) + 0.5f) * (1.0f / 65536.0f);
+    return normal_from_uniforms<P>((double)f1, (double)f2, f1, f2, N, a);
+}
+
+// The depo-level normal branch of the charge-conserving fluctuation's
+// survivor count: Box-Muller on words 0 and 1 of its block,
+// u = (x + 1/2) / 2^32.
+template <int P>
+__device__ __forceinline__ int normal_pair(uint4 x, int N, const RasterArgs& a) {
+    const float two_m32 = 2.3283064365386963e-10f;
+    const double d32 = 2.3283064365386962890625e-10;
+    return normal_from_uniforms<P>(((double)x.x + 0.5) * d32, ((double)x.y + 0.5) * d32,
+                                   fmaf((float)x.x, two_m32, 0.5f * two_m32),
+                                   fmaf((float)x.y, two_m32, 0.5f * two_m32), N, a);
 }
 
 // The same search on a table: row N (N = 1 .. kExactCap, at offset
@@ -148,18 +167,37 @@ __device__ __forceinline__ int invert_binomial_table(int N, uint32_t x0, const R
     return a.inv_flip ? N - k : k;
 }
 
-// Survivor count of a bin holding N electrons: one Philox block with counter
-// (0, global bin, depo, event << 4 | plane); CDF inversion of its word 0 for
-// N <= exact_max, else the normal approximation from words 0 and 1.
-// cdf: the table for this unit's (r, 1 - s), or null for the direct search.
+// Random stream of the per-bin fluctuation: one Philox block per quad (the
+// four consecutive ticks 4g .. 4g+3 of one wire w of one depo), counter
+// (0, w * ceil(nticks / 4) + g, depo, event << 4 | plane); bin (w, k) takes
+// word k % 4.
+__device__ __forceinline__ uint32_t quad_index(int w, int k, int nticks) {
+    return (uint32_t)w * (uint32_t)((nticks + 3) >> 2) + (uint32_t)(k >> 2);
+}
+
+__device__ __forceinline__ uint32_t word_of(const uint4& x, int j) {
+    return j == 0 ? x.x : (j == 1 ? x.y : (j == 2 ? x.z : x.w));
+}
+
+// Survivor count of a bin holding N electrons from its word x: CDF
+// inversion for N <= exact_max, else the normal approximation.  cdf: the
+// table for this unit's (r, 1 - s), or null for the direct search.
 template <int P>
-__device__ __forceinline__ int binomial_bin(int N, const RasterArgs& a, uint32_t bin, uint32_t depo,
+__device__ __forceinline__ int draw_word(int N, uint32_t x, const RasterArgs& a, const float* recip,
+                                         const float* cdf) {
+    if (N <= a.exact_max) return cdf ? invert_binomial_table(N, x, a, cdf) : invert_binomial(N, x, a, recip);
+    return normal_word<P>(x, N, a);
+}
+
+// Survivor count of bin (w, k) holding N electrons (its quad's block
+// computed for this bin alone).
+template <int P>
+__device__ __forceinline__ int binomial_bin(int N, const RasterArgs& a, int w, int k, uint32_t depo,
                                             const float* recip, const float* cdf) {
     if (N <= 0 || a.T == 0u) return 0;
     if (a.keep_all) return N;
-    const uint4 x = philox4x32_10(make_uint4(0u, bin, depo, a.evpl), a.key0, a.key1);
-    if (N <= a.exact_max) return cdf ? invert_binomial_table(N, x.x, a, cdf) : invert_binomial(N, x.x, a, recip);
-    return normal_draw<P>(x, N, a);
+    const uint4 x = philox4x32_10(make_uint4(0u, quad_index(w, k, a.nticks), depo, a.evpl), a.key0, a.key1);
+    return draw_word<P>(N, word_of(x, k & 3), a, recip, cdf);
 }
 
 // Reciprocals 1/i, i = 0 .. kExactCap, correctly rounded, into shared memory
@@ -448,8 +486,7 @@ raster_kernel(const __grid_constant__ RasterUnits U, ws_patches pt, const long l
                         v = scale * s_wx[wib][ia] * s_wt[wib][ib];
                     } else {
                         const int N = electrons(q * s_wx[wib][ia] * s_wt[wib][ib]);
-                        v = (W)binomial_bin<P>(N, a, (uint32_t)((int64_t)w * a.nticks + k), (uint32_t)i, s_recip,
-                                               cdf);
+                        v = (W)binomial_bin<P>(N, a, w, k, (uint32_t)i, s_recip, cdf);
                     }
                     if (MODE == EMIT_GRID) emit<P>(a, grid, (int64_t)w * a.nticks + k, v);
                     else pt.val[off + (int64_t)(w - e.w0) * ntf + (k - e.k0)] = (float)v;
@@ -502,8 +539,7 @@ __device__ __forceinline__ void lane_weights(const RasterArgs& a, W mu, W sigma,
     lane_axis_weights<W, W>(mu, sigma, delta, nsig, point, first, nb, inv_norm, w);
 }
 
-constexpr int kRoundPerLane = 2;   // bins per lane per binomial round
-constexpr int kBinMap = 1024;    // bins of a depo group addressed through a byte map (else a search)
+constexpr int kBinMap = 1024;    // items of a depo group addressed through a byte map (else a search)
 
 template <int MODE, int P, int SW>
 __global__ void __launch_bounds__(32 * kSmallWarpsPerBlock, 7)
@@ -517,12 +553,16 @@ raster_small_kernel(const __grid_constant__ RasterUnits U, ws_patches pt, long l
     __shared__ int s_off[NW][G];     // inclusive scan of the depos' bin counts
     __shared__ int s_k0[NW][G];
     __shared__ int s_w0[NW][G];
-    __shared__ int s_nt[NW][G];
-    __shared__ float s_rnt[NW][G];   // 1 / nt
+    __shared__ int s_nt[NW][G];      // items per patch row: ticks, or quads when fluctuating
+    __shared__ int s_kn[NW][G];      // ticks per patch row
+    __shared__ float s_rnt[NW][G];   // 1 / s_nt
     __shared__ W s_q[NW][G];
-    __shared__ unsigned char s_bdep[NW][kBinMap];   // bin -> depo slot
+    __shared__ unsigned char s_bdep[NW][kBinMap];   // item -> depo slot
     __shared__ float s_recip[kExactCap + 1];
-    __shared__ uint4 s_ent[NW][32 * kRoundPerLane];   // drawing bins of a round: grid index (lo, hi), depo, N
+    // drawing bins of a round (at most four per lane): grid index, N, Philox word
+    __shared__ uint32_t s_eidx[NW][128];
+    __shared__ uint32_t s_en[NW][128];
+    __shared__ uint32_t s_ew[NW][128];
     extern __shared__ float s_cdf[];     // exact-branch CDF rows 1 .. cdf_rows for unit 0's survival probability
     fill_recip(s_recip);
     const RasterArgs& a0 = U.a[0];
@@ -553,7 +593,13 @@ raster_small_kernel(const __grid_constant__ RasterUnits U, ws_patches pt, long l
         }
         const int ntc = any ? e.k1 - e.k0 + 1 : 0;
         const int nxc = any ? e.w1 - e.w0 + 1 : 0;
-        int nb = (any && !large) ? ntc * nxc : 0;
+        // The per-bin fluctuation into the grid walks quads (four ticks of a
+        // wire sharing one Philox block) instead of bins; the same for every
+        // depo of the group (one unit).
+        const bool quads = MODE == EMIT_GRID && a.fluct && !a.keep_all && a.T != 0u;
+        const int nqt = ntc > 0 ? (e.k1 >> 2) - (e.k0 >> 2) + 1 : 0;
+        const int ncol = quads ? nqt : ntc;   // items per patch row: quads or bins
+        int nb = (any && !large) ? ncol * nxc : 0;
         if (MODE == EMIT_PATCH && i < a.n && !large) {
             const int64_t off = pt.off[i];
             const bool fits = off + nb <= pt.capacity_bins;
@@ -579,90 +625,84 @@ raster_small_kernel(const __grid_constant__ RasterUnits U, ws_patches pt, long l
         s_off[wib][dl] = incl;
         s_k0[wib][dl] = any ? e.k0 : 0;
         s_w0[wib][dl] = any ? e.w0 : 0;
-        s_nt[wib][dl] = ntc;
-        s_rnt[wib][dl] = ntc > 0 ? 1.f / (float)ntc : 0.f;
+        s_nt[wib][dl] = ncol;
+        s_kn[wib][dl] = ntc;
+        s_rnt[wib][dl] = ncol > 0 ? 1.f / (float)ncol : 0.f;
         s_q[wib][dl] = a.fluct ? q : (sizeof(W) == 8 ? (W)a.p64 : (W)a.p) * q;
         if (use_bmap)
             for (int j = incl - nb; j < incl; ++j) s_bdep[wib][j] = (unsigned char)dl;
         __syncwarp();
         const int* off = s_off[wib];
-        // bin g of the group -> depo slot d, index inside its patch, (wire, tick)
+        // item g of the group -> depo slot d, index inside its patch, (row, column)
         auto locate = [&](int g, int& d, int& local, int& ia, int& ib) {
             d = use_bmap ? (int)s_bdep[wib][g] : find_slot<G>(off, g);
             local = g - (d > 0 ? off[d - 1] : 0);
             ia = (int)(((float)local + 0.5f) * s_rnt[wib][d]);
             ib = local - ia * s_nt[wib][d];
         };
-        if (MODE == EMIT_GRID && a.fluct && !a.keep_all && a.T != 0u) {
-            // Rounds of 32 kRoundPerLane bins, kRoundPerLane per lane: bins
-            // that draw are compacted into a per-warp list, normal-
-            // approximation bins first, so that a warp runs one sampler at a
-            // time (only the chunk straddling the two kinds diverges); a
-            // full round keeps kRoundPerLane independent Philox chains in
-            // flight per lane.
-            constexpr int H = kRoundPerLane;
+        if (quads) {
+            // Rounds of 32 quads, one per lane: the lane forms the quad's (up
+            // to four) electron counts and, if any bin holds electrons, its
+            // Philox block; the bins that draw are compacted with their words
+            // into a per-warp list, normal-approximation bins first, so that a
+            // warp runs one sampler at a time (only the entry straddling the
+            // two kinds diverges).
             const unsigned lt = (1u << lane) - 1u;
-            for (int gb = 0; gb < total; gb += 32 * H) {
-                int64_t idx[H];
-                int N[H];
-                bool nrm[H], exa[H];
-                uint32_t dep[H];
+            const uint32_t qstride = (uint32_t)((a.nticks + 3) >> 2);
+            for (int gb = 0; gb < total; gb += 32) {
+                const int g = gb + lane;
+                int N[4] = {0, 0, 0, 0};
+                uint32_t first = 0;
+                uint4 x = make_uint4(0u, 0u, 0u, 0u);
+                if (g < total) {
+                    int d, local, ia, iq;
+                    locate(g, d, local, ia, iq);
+                    const int k0 = s_k0[wib][d];
+                    const int nt = s_kn[wib][d];
+                    const int w = s_w0[wib][d] + ia;
+                    const int kq = (k0 >> 2) + iq;          // the quad's tick group
+                    const W qw = s_q[wib][d] * s_wx[wib][d][ia];
 #pragma unroll
-                for (int h = 0; h < H; ++h) {
-                    const int g = gb + 32 * h + lane;
-                    N[h] = 0; idx[h] = 0; dep[h] = 0;
-                    if (g < total) {
-                        int d, local, ia, ib;
-                        locate(g, d, local, ia, ib);
-                        idx[h] = (int64_t)(s_w0[wib][d] + ia) * a.nticks + s_k0[wib][d] + ib;
-                        N[h] = electrons(s_q[wib][d] * s_wx[wib][d][ia] * s_wt[wib][d][ib]);
-                        dep[h] = (uint32_t)(base + d);
+                    for (int j = 0; j < 4; ++j) {
+                        const int b = 4 * kq + j - k0;
+                        N[j] = (b >= 0 && b < nt) ? electrons(qw * s_wt[wib][d][b]) : 0;
                     }
-                    nrm[h] = N[h] > a.exact_max;
-                    exa[h] = N[h] > 0 && !nrm[h];
+                    first = (uint32_t)w * (uint32_t)a.nticks + (uint32_t)(4 * kq);   // grids hold < 2^31 cells
+                    if ((N[0] | N[1] | N[2] | N[3]) > 0)
+                        x = philox4x32_10(make_uint4(0u, (uint32_t)w * qstride + (uint32_t)kq, (uint32_t)(base + d),
+                                                     a.evpl), a.key0, a.key1);
                 }
-                unsigned nb[H], eb[H];
-                int nbefore[H], ebefore[H], nn = 0, ne = 0;
+                unsigned nbal[4], ebal[4];
+                int nbef[4], ebef[4], nn = 0, ne = 0;
 #pragma unroll
-                for (int h = 0; h < H; ++h) {
-                    nb[h] = __ballot_sync(0xffffffffu, nrm[h]);
-                    eb[h] = __ballot_sync(0xffffffffu, exa[h]);
-                    nbefore[h] = nn;
-                    ebefore[h] = ne;
-                    nn += __popc(nb[h]);
-                    ne += __popc(eb[h]);
+                for (int j = 0; j < 4; ++j) {
+                    const bool nr = N[j] > a.exact_max;
+                    nbal[j] = __ballot_sync(0xffffffffu, nr);
+                    ebal[j] = __ballot_sync(0xffffffffu, N[j] > 0 && !nr);
+                    nbef[j] = nn;
+                    ebef[j] = ne;
+                    nn += __popc(nbal[j]);
+                    ne += __popc(ebal[j]);
                 }
-                const int ntot = nn + ne;
 #pragma unroll
-                for (int h = 0; h < H; ++h) {
-                    if (nrm[h] || exa[h]) {
-                        const int pos = nrm[h] ? nbefore[h] + __popc(nb[h] & lt) : nn + ebefore[h] + __popc(eb[h] & lt);
-                        s_ent[wib][pos] = make_uint4((uint32_t)idx[h], (uint32_t)((uint64_t)idx[h] >> 32), dep[h],
-                                                     (uint32_t)N[h]);
+                for (int j = 0; j < 4; ++j) {
+                    if (N[j] > 0) {
+                        const int pos = N[j] > a.exact_max ? nbef[j] + __popc(nbal[j] & lt)
+                                                           : nn + ebef[j] + __popc(ebal[j] & lt);
+                        s_eidx[wib][pos] = first + (uint32_t)j;
+                        s_en[wib][pos] = (uint32_t)N[j];
+                        s_ew[wib][pos] = word_of(x, j);
                     }
                 }
                 __syncwarp();
-                auto draw = [&](int it, const uint4& en, const uint4& x) {
-                    const int n = (int)en.w;
-                    const int c = it < nn ? normal_draw<P>(x, n, a)
-                                          : (cdf ? invert_binomial_table(n, x.x, a, cdf) : invert_binomial(n, x.x, a, s_recip));
-                    emit<P>(a, grid, (int64_t)(((uint64_t)en.y << 32) | en.x), (W)c);
-                };
-                if (ntot > 32 * (H - 1)) {
-                    // entries lane + 32 h: H independent Philox chains per lane
-                    uint4 en[H], x[H];
-#pragma unroll
-                    for (int h = 0; h < H; ++h) en[h] = (lane + 32 * h < ntot) ? s_ent[wib][lane + 32 * h] : s_ent[wib][lane];
-#pragma unroll
-                    for (int h = 0; h < H; ++h) x[h] = philox4x32_10(make_uint4(0u, en[h].x, en[h].z, a.evpl), a.key0, a.key1);
-#pragma unroll
-                    for (int h = 0; h < H; ++h)
-                        if (lane + 32 * h < ntot) draw(lane + 32 * h, en[h], x[h]);
-                } else {
-                    for (int it = lane; it < ntot; it += 32) {
-                        const uint4 en = s_ent[wib][it];
-                        draw(it, en, philox4x32_10(make_uint4(0u, en.x, en.z, a.evpl), a.key0, a.key1));
-                    }
+                const int ntot = nn + ne;
+                for (int it = lane; it < ntot; it += 32) {
+                    const int n = (int)s_en[wib][it];
+                    const uint32_t xw = s_ew[wib][it];
+                    const int c = it < nn ? normal_word<P>(xw, n, a)
+                                          : (cdf ? invert_binomial_table(n, xw, a, cdf)
+                                                 : invert_binomial(n, xw, a, s_recip));
+                    emit<P>(a, grid, (int64_t)s_eidx[wib][it], (W)c);
                 }
                 __syncwarp();
             }
@@ -673,8 +713,7 @@ raster_small_kernel(const __grid_constant__ RasterUnits U, ws_patches pt, long l
                 const int w = s_w0[wib][d] + ia, k = s_k0[wib][d] + ib;
                 W v = s_q[wib][d] * s_wx[wib][d][ia] * s_wt[wib][d][ib];
                 if (a.fluct)
-                    v = (W)binomial_bin<P>(electrons(v), a, (uint32_t)((int64_t)w * a.nticks + k), (uint32_t)(base + d),
-                                           s_recip, cdf);
+                    v = (W)binomial_bin<P>(electrons(v), a, w, k, (uint32_t)(base + d), s_recip, cdf);
                 if (MODE == EMIT_GRID) emit<P>(a, grid, (int64_t)w * a.nticks + k, v);
                 else pt.val[pt.off[base + d] + local] = (float)v;
             }
@@ -803,7 +842,7 @@ raster_multinomial_kernel(const __grid_constant__ RasterUnits U, ws_patches pt) 
                 K = N;
             } else {
                 const uint4 x = philox4x32_10(make_uint4(5u, 0u, (uint32_t)i, a.evpl), a.key0, a.key1);
-                K = N <= a.exact_max ? invert_binomial(N, x.x, a, s_recip) : normal_draw<0>(x, N, a);
+                K = N <= a.exact_max ? invert_binomial(N, x.x, a, s_recip) : normal_pair<0>(x, N, a);
             }
         }
         const float inv_norm = window_norm<float>(a);

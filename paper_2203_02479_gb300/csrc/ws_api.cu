@@ -144,6 +144,7 @@ ws_status plan_layout(const ws_plane_desc* d, Layout* lay) {
     if (d->impacts < 0 || d->impacts > ws::kMaxImpacts) return WS_ERR_INVALID_ARG;
     const int I = d->impacts > 1 ? d->impacts : 1;
     if (I > 1 && d->fp64) return WS_ERR_UNSUPPORTED_SIZE;   // impact planes run FP32
+    if ((int64_t)I * d->nwires * d->nticks > (int64_t)INT32_MAX) return WS_ERR_UNSUPPORTED_SIZE;   // 32-bit bin index
     lay->impacts = I;
     int L;
     if (d->fft_len_tick > 0) {
@@ -432,6 +433,7 @@ ws_status ws_plane_create(const ws_plane_desc* desc, const float* response_dev, 
     // fastest variant is kept.
     pl->wconv_variant = 0;
     pl->batch_upw = 0;
+    pl->batch_wconv = -1;
     if (e == cudaSuccess) e = cudaMemsetAsync(pl->X, 0, sizeof(float2) * (size_t)desc->nwires * lay.fstride, s);
     if (e == cudaSuccess && lay.impacts == 1) {   // impact planes have one wire-convolution kernel
         cudaEvent_t t0 = nullptr, t1 = nullptr;
@@ -490,6 +492,7 @@ ws_status ws_plane_set_wire_conv_variant(ws_plane* pl, int variant) {
     if (!pl || variant < 0 || variant >= ws::kWireConvVariants) return WS_ERR_INVALID_ARG;
     if (variant >= 4 && (pl->desc.conv_mode == WS_CONV_CIRCULAR || !ws::tma_available())) return WS_ERR_UNSUPPORTED_SIZE;
     pl->wconv_variant = variant;
+    pl->batch_wconv = variant;   // an explicit choice holds for batches too
     return WS_OK;
 }
 
@@ -558,6 +561,8 @@ ws_status ws_plane_get_info(const ws_plane* pl, ws_plane_info* info) {
     info->workspace_bytes = pl->ws_bytes;
     info->wire_conv_variant = pl->wconv_variant;
     info->row_fft_fixed_shape = ws::row_fft_fixed_shape(pl->plan) ? 1 : 0;
+    info->batch_units_per_wave = pl->batch_upw;
+    info->batch_wire_conv_variant = pl->batch_wconv;
     return WS_OK;
 }
 
@@ -854,8 +859,8 @@ ws_status ws_simulate_batch(ws_plane* const* planes, int nplanes, const ws_depos
                             const ws_params* params, float* const* out_dev, void* workspace_dev,
                             size_t workspace_bytes, int units_per_wave, void* stream) {
     NvtxRange range("ws_simulate_batch");
-    if (units_per_wave == 0 && planes && nplanes > 0 && planes[0] && nevents > 0)
-        units_per_wave = auto_wave_size(planes, nplanes, nevents * nplanes, workspace_bytes);
+    if (units_per_wave == 0 && planes && nplanes > 0 && planes[0])
+        units_per_wave = nevents > 0 ? auto_wave_size(planes, nplanes, nevents * nplanes, workspace_bytes) : 1;
     BatchLayout lay;
     ws_status st = batch_layout(planes, nplanes, units_per_wave, &lay);
     if (st != WS_OK) return st;
@@ -968,13 +973,52 @@ ws_status ws_batch_autotune(ws_plane* const* planes, int nplanes, const ws_depos
             if (st == WS_OK && ms < best_of[i]) best_of[i] = ms;
         }
     }
+    int best = 0;
+    if (st == WS_OK) {
+        for (int i = 1; i < nc; ++i)
+            if (best_of[i] < best_of[best]) best = i;
+        for (int i = 0; i < nplanes; ++i) planes[i]->batch_upw = cand[best];
+    }
+    // Then the wire-convolution kernel at that wave size (one kernel serves
+    // every unit of a launch): each variant the planes allow, timed the same
+    // way; the planes keep their own choice for single-plane calls.
+    const int circ = planes[0]->desc.conv_mode == WS_CONV_CIRCULAR;
+    // a kernel already chosen for batches on these planes (by an earlier
+    // run of the autotuner or ws_plane_set_wire_conv_variant) is kept
+    const int nvar = planes[0]->batch_wconv >= 0 ? 0 : ((circ || !ws::tma_available()) ? 4 : ws::kWireConvVariants);
+    float var_ms[ws::kWireConvVariants];
+    for (int v = 0; v < nvar; ++v) var_ms[v] = 1e30f;
+    const int keep = planes[0]->batch_wconv;
+    for (int round = 0; round < 3 && st == WS_OK; ++round) {
+        for (int v = 0; v < nvar && st == WS_OK; ++v) {
+            planes[0]->batch_wconv = v;
+            if (round == 0)
+                st = ws_simulate_batch(planes, nplanes, depos, nevents, params, out_dev, workspace_dev,
+                                       workspace_bytes, cand[best], stream);
+            if (st == WS_OK) e = cudaEventRecord(t0, s);
+            if (st == WS_OK && e == cudaSuccess)
+                st = ws_simulate_batch(planes, nplanes, depos, nevents, params, out_dev, workspace_dev,
+                                       workspace_bytes, cand[best], stream);
+            if (e == cudaSuccess && st == WS_OK) e = cudaEventRecord(t1, s);
+            if (e == cudaSuccess && st == WS_OK) e = cudaEventSynchronize(t1);
+            float ms = 0.f;
+            if (e == cudaSuccess && st == WS_OK) e = cudaEventElapsedTime(&ms, t0, t1);
+            if (e != cudaSuccess && st == WS_OK) st = cuda_fail(e, "ws_batch_autotune");
+            if (st == WS_OK && ms < var_ms[v]) var_ms[v] = ms;
+        }
+    }
     cudaEventDestroy(t0);
     cudaEventDestroy(t1);
-    if (st != WS_OK) return st;
-    int best = 0;
-    for (int i = 1; i < nc; ++i)
-        if (best_of[i] < best_of[best]) best = i;
-    for (int i = 0; i < nplanes; ++i) planes[i]->batch_upw = cand[best];
+    if (st != WS_OK) {
+        planes[0]->batch_wconv = keep;
+        return st;
+    }
+    if (nvar > 0) {
+        int bv = 0;
+        for (int v = 1; v < nvar; ++v)
+            if (var_ms[v] < var_ms[bv]) bv = v;
+        planes[0]->batch_wconv = bv;
+    }
     *units_per_wave_out = cand[best];
     return WS_OK;
 }
@@ -989,6 +1033,9 @@ ws_status batch_waves(ws_plane* const* planes, int nplanes, const ws_depos* depo
     ws_plane* p0 = planes[0];
     const ws_plane_desc& d0 = p0->desc;
     const int circ = d0.conv_mode == WS_CONV_CIRCULAR;
+    // the wire-convolution kernel the batch autotuner picked for these
+    // planes, else the first plane's own
+    const int wconv = p0->batch_wconv >= 0 ? p0->batch_wconv : p0->wconv_variant;
     for (int slot = 0; slot < nstreams; ++slot)
         WS_CUDA(cudaMemsetAsync(ws_base + slot * lay.slot_bytes + lay.off_counters, 0, 256, ss[slot]));
     for (int u0 = 0, wave = 0; u0 < nunits; u0 += units_per_wave, ++wave) {
@@ -1044,8 +1091,7 @@ ws_status batch_waves(ws_plane* const* planes, int nplanes, const ws_depos* depo
         WS_LAUNCH(p0, K_FWD, s, ws::launch_fwd_rows_batch(p0->plan, p0->tw, fb, d0.nticks, d0.nticks, p0->fstride,
                                                           p0->nfreq, 1.0f, s));
         WS_LAUNCH(p0, K_WCONV, s, ws::launch_wire_conv_batch(cb, p0->nfreq, p0->fstride, d0.resp_nwires,
-                                                             d0.resp_wire_center, circ, s, p0->wconv_variant,
-                                                             p0->status));
+                                                             d0.resp_wire_center, circ, s, wconv, p0->status));
         if (noisy) WS_LAUNCH(p0, K_NOISE, s, ws::launch_add_noise(nb, p0->nfreq, p0->plan.L, p0->fstride, s));
         WS_LAUNCH(p0, K_INV, s, ws::launch_inv_rows_batch(p0->plan, p0->tw, ib, p0->fstride, p0->nfreq, d0.nticks,
                                                           d0.nticks, s));

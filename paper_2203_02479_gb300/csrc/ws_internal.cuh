@@ -316,6 +316,7 @@ struct ws_plane {
     ws_trace* trace;    // launch trace, or null
     int wconv_variant;  // wire-convolution kernel chosen by the autotuner
     int batch_upw;      // batch wave size chosen by ws_batch_autotune (0: not tuned)
+    int batch_wconv;    // batch wire-convolution kernel chosen by it (-1: not tuned)
     ws_plane_desc desc;
     ws::FftPlan plan;
     int nfreq;          // L/2 + 1

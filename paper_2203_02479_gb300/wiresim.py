@@ -83,7 +83,8 @@ class WsPlaneInfo(ctypes.Structure):
     _fields_ = [("fft_len_tick", ctypes.c_int32), ("nfreq", ctypes.c_int32),
                 ("nfreq_stride", ctypes.c_int32), ("npasses", ctypes.c_int32),
                 ("radices", ctypes.c_int32 * 16), ("workspace_bytes", ctypes.c_size_t),
-                ("wire_conv_variant", ctypes.c_int32), ("row_fft_fixed_shape", ctypes.c_int32)]
+                ("wire_conv_variant", ctypes.c_int32), ("row_fft_fixed_shape", ctypes.c_int32),
+                ("batch_units_per_wave", ctypes.c_int32), ("batch_wire_conv_variant", ctypes.c_int32)]
 
 
 _lock = threading.Lock()
@@ -591,6 +592,8 @@ class Batch:
                "ws_batch_autotune")
         self.chosen_units_per_wave = int(upw.value)
         self.tuned = True
+        for pl in self.planes:
+            pl.info = ws_plane_get_info(pl.handle)
         return self.chosen_units_per_wave
 
     def run(self, stream=None):

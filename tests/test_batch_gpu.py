@@ -263,3 +263,47 @@ def test_large_patch_list_overflow_falls_back(ws):
     assert abs(got.sum() - ref.sum()) <= 1e-4 * ref.sum()
     for pl in planes:
         assert pl.status() == 0
+
+
+def test_autotuned_wave_size_is_the_fastest_and_changes_nothing(ws):
+    """ws_batch_autotune on the three-plane event (100k track depos,
+    binomial): the wave size it records is, within timing noise, the fastest
+    of the fixed sizes (graph replays, median of 30), and a batch run with
+    the recorded size (units_per_wave = 0) gives the same waveforms as every
+    fixed size."""
+    import torch
+    w = inputs.three_planes()
+    planes = [ws.Plane(sp.nwires, sp.nticks, sp.response, plane_id=sp.plane_id) for sp in w.planes]
+    depos = [ws.DeviceDepos.from_plane_depos(d) for d in w.events[0]]
+    params = ws.Params(fluctuate=True, p_survive=w.p_survive, seed=w.seed)
+    auto = ws.Batch(planes, [depos], params)
+    upw = auto.autotune()
+    assert 1 <= upw <= 3 and planes[0].info.batch_units_per_wave == upw
+    assert 0 <= planes[0].info.batch_wire_conv_variant <= 9
+    ref = [o.cpu().numpy() for o in auto.run()]
+
+    def median_ms(b):
+        b.capture()
+        for _ in range(3):
+            b.replay()
+        t = []
+        for _ in range(30):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            b.replay()
+            e1.record()
+            torch.cuda.synchronize()
+            t.append(e0.elapsed_time(e1))
+        return float(np.median(t))
+
+    times = {}
+    for fixed in (1, 2, 3):
+        b = ws.Batch(planes, [depos], params, units_per_wave=fixed)
+        outs = b.run()
+        torch.cuda.synchronize()
+        for o, r in zip(outs, ref):
+            assert rel(o.cpu().numpy(), r) <= 1e-6, fixed
+        times[fixed] = median_ms(b)
+    assert times[upw] <= 1.15 * min(times.values()) + 0.01, (upw, times)
+    for pl in planes:
+        assert pl.status() == 0
