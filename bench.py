@@ -443,17 +443,39 @@ def kernel_launches(stats: dict, nsteps: int) -> float:
     return sum(n * (2 if name == "raster_scatter" else 1) for name, (n, _) in stats.items()) / nsteps
 
 
-def drawing_bins(wiresim, pairs) -> int:
-    """Bins that draw one Philox block in binomial mode, over (plane,
-    DeviceDepos) pairs: in-grid bins holding N = floor(q w + 1/2) >= 1
-    electrons, counted on the expected-value patches of the same depos."""
+def philox_blocks(wiresim, pairs) -> int:
+    """Philox blocks the binomial raster draws, over (plane, DeviceDepos)
+    pairs, counted on the expected-value patches of the same depos: a bin
+    draws when it holds N = floor(q w + 1/2) >= 1 electrons; the lane-per-depo
+    kernel draws one block per quad (four ticks of a wire) of a depo with any
+    drawing bin, the warp-per-depo kernel (patches above 16 ticks or 8
+    wires) one block per drawing bin."""
+    import torch
     n = 0
     for pl, dd in pairs:
         if dd.n == 0:
             continue
         pt = pl.rasterize(dd, wiresim.Params(p_survive=1.0))
-        n += int((pt["val"][:pt["capacity"]] >= 0.5).sum().item())
-        del pt
+        nd = dd.n
+        nw = pt["nw"][:nd].long()
+        nt = pt["nt"][:nd].long()
+        sizes = nw * nt
+        total = int(sizes.sum().item())
+        if total == 0:
+            continue
+        off = pt["off"][:nd]
+        depo = torch.repeat_interleave(torch.arange(nd, device=sizes.device), sizes)
+        local = torch.arange(total, device=sizes.device) - off[depo]
+        ntd = nt[depo]
+        wire = pt["w0"][:nd].long()[depo] + local // ntd
+        tick = pt["t0"][:nd].long()[depo] + local % ntd
+        draws = pt["val"][off[depo] + local] >= 0.5
+        large = ((nt > 16) | (nw > 8))[depo]
+        n += int((draws & large).sum().item())
+        small = draws & ~large
+        key = (depo[small] * (pl.nwires + 1) + wire[small]) * ((pl.nticks + 3) // 4 + 1) + tick[small] // 4
+        n += int(torch.unique(key).numel())
+        del pt, depo, local, ntd, wire, tick, draws, large, small, key
     return n
 
 
@@ -490,8 +512,9 @@ def roofline_of(table, muls_per_step, peak_gbs, peak_src, traffic, issue):
                      "frac": a / INT_MUL_PEAK_T,
                      "peak_source": "derived: 152 SMs x 64 INT32 multiply lanes x 2.07 GHz "
                                     "(a Philox-only loop reaches 19.0, 94%)",
-                     "work": f"{PHILOX_MULS} multiplies per Philox block x one block per drawing bin "
-                             f"({muls_per_step / PHILOX_MULS:.0f} bins per step)",
+                     "work": f"{PHILOX_MULS} multiplies per Philox block x one block per quad (four ticks of a "
+                             f"wire) of a depo holding >= 1 electron ({muls_per_step / PHILOX_MULS:.0f} blocks "
+                             f"per step)",
                      "hbm_frac_of_measured": k["hbm_frac"]})
     elif fr["alu"] > fr["hbm"]:
         base.update({"bound": "alu", "achieved": fr["alu"] * FP32_PEAK_TFLOPS, "peak": FP32_PEAK_TFLOPS,
@@ -563,7 +586,7 @@ def event_leg(wiresim, dev, stream, flush, steps: int, peak, oracle_check: bool)
     serial = wiresim.Batch(planes, [depos], params, units_per_wave=len(planes), device=dev)
     nsteps = max(5, min(steps, 200))
     stats = traced(planes[0], lambda: (flush.zero_(), serial.run(stream)), nsteps, 8)
-    muls = PHILOX_MULS * float(drawing_bins(wiresim, list(zip(planes, depos))))
+    muls = PHILOX_MULS * float(philox_blocks(wiresim, list(zip(planes, depos))))
     traffic, issue, _ = ncu_figures(w.name)
     specs = unit_specs(planes, depos)
     table = kernel_table(stats, nsteps, specs, muls, peak_gbs, traffic)
@@ -803,7 +826,7 @@ def run_gpu(args):
     serial_ms = statistics.median(_time_steps(serial_step, nk, stream, flush))
     stats = traced(planes[0], lambda: (flush.zero_(), serial_step()), nk, 8 * len(chunks))
     fluct = w.fluctuate and 0.0 < w.p_survive < 1.0
-    muls = PHILOX_MULS * float(drawing_bins(wiresim, list(zip(unit_planes, unit_depos)))) if fluct else 0.0
+    muls = PHILOX_MULS * float(philox_blocks(wiresim, list(zip(unit_planes, unit_depos)))) if fluct else 0.0
     traffic, issue, ncu_note = ncu_figures(w.name)
     table = kernel_table(stats, nk, specs, muls, peak_gbs, traffic)
     roof = roofline_of(table, muls, peak_gbs, peak_src, traffic, issue)
