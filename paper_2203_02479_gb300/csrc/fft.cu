@@ -750,30 +750,52 @@ fwd_rows_shape_kernel(FftPlan plan, const float2* __restrict__ tw, const __grid_
     const float* __restrict__ in2 = static_cast<const float*>(U.in2[u]);
     const int r0 = 2 * ((int)blockIdx.x - U.prefix[u]);
     const bool has_b = r0 + 1 < U.nrows[u];
+    C* oa = static_cast<C*>(U.out[u]) + (int64_t)r0 * out_stride;
+    C* ob = oa + out_stride;
+    // active rows: an unmarked row of S is zero (and was not cleared, so it
+    // is not read); a pair with no marked row has zero spectra, written only
+    // if a live row's wire convolution may read them
+    bool use_a = true, use_b = has_b;
+    if (const uint32_t* marks = U.rows[u]) {
+        const uint32_t cur = read_epoch(U.epoch);
+        use_a = marks[r0] == cur;
+        use_b = has_b && marks[r0 + 1] == cur;
+        if (!use_a && !use_b) {
+            if (cta_any_marked(marks, cur, r0 + U.win_lo, (has_b ? r0 + 1 : r0) + U.win_hi, U.nrows[u])) {
+                for (int k = threadIdx.x; k < nfreq; k += SH::threads) {
+                    oa[k] = make_float2(0.f, 0.f);
+                    if (has_b) ob[k] = make_float2(0.f, 0.f);
+                }
+            }
+            return;
+        }
+    }
     const float* __restrict__ pa = in + (int64_t)r0 * in_stride;
     const float* __restrict__ pb = has_b ? pa + in_stride : pa;
     const float* __restrict__ la = in2 ? in2 + (int64_t)r0 * in_stride : nullptr;
     const float* __restrict__ lb = (in2 && has_b) ? la + in_stride : la;
     const int nload = ncols < L ? ncols : L;
     if constexpr (BULK) {
-        // the two rows (nload floats each, a multiple of 4) by bulk copies
+        // the pair's rows in use (nload floats each, a multiple of 4) by bulk copies
         __shared__ __align__(8) uint64_t bar;
         float* sa = reinterpret_cast<float*>(buf0);
         float* sb = sa + nload;
         const uint32_t bytes = (uint32_t)nload * 4u;
-        if (!bulk_fetch_rows(sa, pa, bytes, sb, has_b ? pb : nullptr, bytes, &bar, U.status)) return;
+        const bool ok = use_a ? bulk_fetch_rows(sa, pa, bytes, sb, use_b ? pb : nullptr, bytes, &bar, U.status)
+                              : bulk_fetch_rows(sb, pb, bytes, nullptr, nullptr, 0u, &bar, U.status);
+        if (!ok) return;
         first_pass_inplace<SH, false>(buf0, [&](int n) {
-            return n < nload ? make_float2(sa[n], has_b ? sb[n] : 0.f) : make_float2(0.f, 0.f);
+            return n < nload ? make_float2(use_a ? sa[n] : 0.f, use_b ? sb[n] : 0.f) : make_float2(0.f, 0.f);
         });
     } else {
         io_pass<SH::radix[0], 1, L, SH::threads, false>(tw, [&](int n) {
             float xa = 0.f, xb = 0.f;
             if (n < nload) {
-                xa = __ldg(pa + n);
-                if (has_b) xb = __ldg(pb + n);
+                if (use_a) xa = __ldg(pa + n);
+                if (use_b) xb = __ldg(pb + n);
                 if (in2) {
-                    xa += __ldg(la + n);
-                    if (has_b) xb += __ldg(lb + n);
+                    if (use_a) xa += __ldg(la + n);
+                    if (use_b) xb += __ldg(lb + n);
                 }
             }
             return make_float2(xa, xb);
@@ -782,8 +804,6 @@ fwd_rows_shape_kernel(FftPlan plan, const float2* __restrict__ tw, const __grid_
     }
     shape_middle<SH, false>(plan, buf0, buf1, tw);
     const C* z = (!SH::inplace && ((last - 1) & 1)) ? buf1 : buf0;
-    C* oa = static_cast<C*>(U.out[u]) + (int64_t)r0 * out_stride;
-    C* ob = oa + out_stride;
     const float h = 0.5f * scale;
     fwd_last_pass<SH::radix[last], SH::ns(last), L, SH::threads>(tw + plan.twoff[last], [&](int i) { return z[i]; }, nfreq,
                                                     [&](int k, C zk, C zm) {
@@ -805,6 +825,25 @@ inv_rows_shape_kernel(FftPlan plan, const float2* __restrict__ tw, const __grid_
     const int u = find_unit(U.prefix, U.n, (int)blockIdx.x);
     const int r0 = 2 * ((int)blockIdx.x - U.prefix[u]);
     const bool has_b = r0 + 1 < U.nrows[u];
+    float* oa = static_cast<float*>(U.out[u]) + (int64_t)r0 * out_stride;
+    float* ob = oa + out_stride;
+    const int nst = ncols < L ? ncols : L;
+    // active rows: a row whose wire-convolution window holds no marked row
+    // is zero (its spectrum, possibly never written, is not read); a pair of
+    // such rows is stored as zeros without a transform
+    bool live_a = true, live_b = has_b;
+    if (const uint32_t* marks = U.rows[u]) {
+        const uint32_t cur = read_epoch(U.epoch);
+        live_a = cta_any_marked(marks, cur, r0 + U.win_lo, r0 + U.win_hi, U.nrows[u]);
+        live_b = has_b && cta_any_marked(marks, cur, r0 + 1 + U.win_lo, r0 + 1 + U.win_hi, U.nrows[u]);
+        if (!live_a && !live_b) {
+            for (int n = threadIdx.x; n < nst; n += SH::threads) {
+                oa[n] = 0.f;
+                if (has_b) ob[n] = 0.f;
+            }
+            return;
+        }
+    }
     const C* __restrict__ ya = static_cast<const C*>(U.in[u]) + (int64_t)r0 * in_stride;
     const C* __restrict__ yb = has_b ? ya + in_stride : ya;
     // Z = A + iB over the Hermitian extension of both half spectra (global
@@ -812,19 +851,21 @@ inv_rows_shape_kernel(FftPlan plan, const float2* __restrict__ tw, const __grid_
     auto hermitian = [&](const C* a, const C* b, int k) {
         const bool upper = k >= nfreq;
         const int kk = upper ? L - k : k;
-        C A = BULK ? a[kk] : __ldg(a + kk);
-        C B = has_b ? (BULK ? b[kk] : __ldg(b + kk)) : make_float2(0.f, 0.f);
+        C A = live_a ? (BULK ? a[kk] : __ldg(a + kk)) : make_float2(0.f, 0.f);
+        C B = live_b ? (BULK ? b[kk] : __ldg(b + kk)) : make_float2(0.f, 0.f);
         if (kk == 0 || (L % 2 == 0 && 2 * kk == L)) { A.y = 0.f; B.y = 0.f; }
         if (upper) { A.y = -A.y; B.y = -B.y; }
         return make_float2(A.x - B.y, A.y + B.x);
     };
     if constexpr (BULK) {
-        // both half spectra (nfreq <= SH::nfe values each) by bulk copies
+        // the live half spectra (nfreq <= SH::nfe values each) by bulk copies
         __shared__ __align__(8) uint64_t bar;
         C* sA = buf0;
         C* sB = buf0 + SH::nfe;
         const uint32_t bytes = (uint32_t)SH::nfe * (uint32_t)sizeof(C);
-        if (!bulk_fetch_rows(sA, ya, bytes, sB, has_b ? yb : nullptr, bytes, &bar, U.status)) return;
+        const bool ok = live_a ? bulk_fetch_rows(sA, ya, bytes, sB, live_b ? yb : nullptr, bytes, &bar, U.status)
+                               : bulk_fetch_rows(sB, yb, bytes, nullptr, nullptr, 0u, &bar, U.status);
+        if (!ok) return;
         first_pass_inplace<SH, true>(buf0, [&](int k) { return hermitian(sA, sB, k); });
     } else {
         io_pass<SH::radix[0], 1, L, SH::threads, true>(tw, [&](int k) { return hermitian(ya, yb, k); },
@@ -833,9 +874,6 @@ inv_rows_shape_kernel(FftPlan plan, const float2* __restrict__ tw, const __grid_
     }
     shape_middle<SH, true>(plan, buf0, buf1, tw);
     const C* z = (!SH::inplace && ((last - 1) & 1)) ? buf1 : buf0;
-    float* oa = static_cast<float*>(U.out[u]) + (int64_t)r0 * out_stride;
-    float* ob = oa + out_stride;
-    const int nst = ncols < L ? ncols : L;
     io_pass<SH::radix[last], SH::ns(last), L, SH::threads, true>(tw + plan.twoff[last], [&](int i) { return z[i]; },
                                                     [&](int n, C v) {
         if (n < nst) {
@@ -869,6 +907,9 @@ wire_conv_kernel(const __grid_constant__ ConvUnits U, int nfreq, int64_t stride,
     const int k0 = blockIdx.x * kConvCols;
     const int w0 = ((int)blockIdx.y - U.prefix[u]) * B;
     const int ibase = w0 + center - (K - 1);
+    // active rows: a tile none of whose output rows is live is never read
+    if (const uint32_t* marks = U.rows[u])
+        if (!cta_any_marked(marks, read_epoch(U.epoch), w0 + center - kw + 1, w0 + B - 1 + center, nwires)) return;
     constexpr int PER = std::is_same<S, float>::value ? 2 : 1;   // complex values per 16-byte load
     for (int e = threadIdx.x; e < ROWS * (kConvCols / PER); e += kConvCols) {
         const int uu = e / (kConvCols / PER), c2 = e - uu * (kConvCols / PER);
@@ -1026,8 +1067,10 @@ void launch_wc(const ConvBatch& cb, int nfreq, int64_t stride, int kw, int cente
         U.Y[i] = cb.Y[i];
         U.Rt[i] = cb.Rt[i];
         U.nwires[i] = cb.nwires[i];
+        U.rows[i] = std::is_same<S, float>::value ? cb.rows[i] : nullptr;
         U.prefix[i + 1] = U.prefix[i] + (cb.nwires[i] + B - 1) / B;
     }
+    U.epoch = cb.epoch;
     dim3 grid((nfreq + kConvCols - 1) / kConvCols, U.prefix[cb.n]);
     wire_conv_kernel<K, B, KS, S><<<grid, kConvCols, 0, s>>>(U, nfreq, stride, kw, center, circular);
 }
@@ -1138,12 +1181,16 @@ static RowUnits row_units(const RowBatch& rb, bool* aligned16) {
     U.n = rb.n;
     U.prefix[0] = 0;
     U.status = rb.status;
+    U.epoch = rb.epoch;
+    U.win_lo = rb.win_lo;
+    U.win_hi = rb.win_hi;
     *aligned16 = true;
     for (int i = 0; i < rb.n; ++i) {
         U.in[i] = rb.in[i];
         U.in2[i] = rb.in2[i];
         U.out[i] = rb.out[i];
         U.nrows[i] = rb.nrows[i];
+        U.rows[i] = rb.rows[i];
         U.prefix[i + 1] = U.prefix[i] + (rb.nrows[i] + 1) / 2;
         *aligned16 = *aligned16 && ((uintptr_t)rb.in[i] % 16 == 0) && ((uintptr_t)rb.out[i] % 16 == 0);
     }
@@ -1211,6 +1258,9 @@ static cudaError_t fwd_rows_t(const FftPlan& plan, const cplx<S>* tw, const RowB
             return cudaGetLastError();
         }
     }
+    // active-row marks are honoured by the fixed-shape kernels only
+    for (int i = 0; i < rb.n; ++i)
+        if (rb.rows[i]) return cudaErrorInvalidValue;
     const int smem = 2 * ((plan.L + 1) & ~1) * (int)sizeof(cplx<S>);
     cudaError_t e = set_smem((const void*)fwd_rows_kernel<S, TIN>, smem);
     if (e != cudaSuccess) return e;
@@ -1244,6 +1294,8 @@ static cudaError_t inv_rows_t(const FftPlan& plan, const cplx<S>* tw, const RowB
             return cudaGetLastError();
         }
     }
+    for (int i = 0; i < rb.n; ++i)
+        if (rb.rows[i]) return cudaErrorInvalidValue;
     const int smem = 2 * ((plan.L + 1) & ~1) * (int)sizeof(cplx<S>);
     cudaError_t e = set_smem((const void*)inv_rows_kernel<S>, smem);
     if (e != cudaSuccess) return e;

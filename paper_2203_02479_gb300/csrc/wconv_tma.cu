@@ -32,6 +32,8 @@ struct TmaConvUnits {
     int nwires[kMaxUnits];
     void* Y[kMaxUnits];
     const void* Rt[kMaxUnits];
+    const uint32_t* rows[kMaxUnits];       // active-row marks, or null (every tile computed)
+    const uint32_t* epoch;
 };
 
 // 2D tile copy of the box at (x, y) into dst, completing on bar.
@@ -108,6 +110,11 @@ wire_conv_tma_kernel(const __grid_constant__ TmaConvUnits U, int nfreq, int64_t 
         tile_of(t, u, k0, w0);
         const int k = k0 + threadIdx.x;
         const int nwires = U.nwires[u];
+        // active rows: a tile none of whose output rows is live is never
+        // read (the barrier inside also frees buffer st for the next copy)
+        if (U.rows[u] &&
+            !cta_any_marked(U.rows[u], read_epoch(U.epoch), w0 + center - kw + 1, w0 + B - 1 + center, nwires))
+            continue;
         float2* __restrict__ Y = static_cast<float2*>(U.Y[u]);
         const float2* __restrict__ Rt = static_cast<const float2*>(U.Rt[u]);
         const float2* col = buf(st) + threadIdx.x;
@@ -234,10 +241,44 @@ wire_conv_ring_kernel(const __grid_constant__ TmaConvUnits U, int nfreq, int64_t
     int t = (int)((int64_t)total * blockIdx.x / gridDim.x);
     float cc[K], cm[K], cp[K];   // taps of the run's column block (Karatsuba form)
     float2 c[K];                 // the same, plain form
+    __shared__ unsigned long long s_live;   // live tiles of the current run (bit i: tile i), with marks
     while (t < t_end) {
         int u, k0, wb, nwb;
         tile_of(t, u, k0, wb, nwb);
-        const int n = min(t_end - t, nwb - wb);   // tiles in this run
+        const int run = min(t_end - t, nwb - wb);   // tiles in this run
+        int n = run;
+        // active rows: trim the run to its first .. last live tile (a tile is
+        // live if a marked row lies in [w0 + c - K_w + 1, w0 + B - 1 + c]),
+        // so the chunks of dead tiles at either end are never fetched
+        if (const uint32_t* marks = U.rows[u]) {
+            const uint32_t cur = read_epoch(U.epoch);
+            const int nw = U.nwires[u];
+            if (threadIdx.x == 0) s_live = 0ull;
+            __syncthreads();
+            const int lo = wb * B + center - kw + 1, hi = (wb + run) * B - 1 + center;
+            unsigned long long mine = 0ull;
+            for (int r = max(lo, 0) + (int)threadIdx.x; r <= min(hi, nw - 1); r += kCols) {
+                if (marks[r] != cur) continue;
+                // tiles i whose window holds row r: w0_i + c - kw + 1 <= r <= w0_i + B - 1 + c
+                const int ia = max(0, (r - center - (B - 1) - wb * B + B - 1) / B);
+                const int ib = min(run - 1, (r - center + kw - 1 - wb * B) / B);
+                for (int i = ia; i <= ib && i < 64; ++i) mine |= 1ull << i;
+            }
+            if (mine) atomicOr(&s_live, mine);
+            __syncthreads();
+            const unsigned long long live = s_live;
+            __syncthreads();   // s_live read by every thread before the next run resets it
+            if (run <= 64) {
+                if (live == 0ull) {
+                    t += run;
+                    continue;
+                }
+                const int first = __ffsll((long long)live) - 1;
+                const int last = 63 - __clzll((long long)live);
+                wb += first;
+                n = last - first + 1;
+            }
+        }
         const int ybase = wb * B + center - (K - 1);
         const CUtensorMap* map = &U.map[u];
         auto issue = [&](int j) {   // chunk j of the run into slot j % 3 (thread 0 copies, all track)
@@ -272,6 +313,10 @@ wire_conv_ring_kernel(const __grid_constant__ TmaConvUnits U, int nfreq, int64_t
             const float2* col1 = slot_buf(s1) + threadIdx.x;
             const float2* col2 = slot_buf(s2) + threadIdx.x;
             const int w0 = (wb + i) * B;
+            // active rows: skip the sums of a tile none of whose output rows
+            // is live (its chunks still stream through the ring)
+            const bool live_tile = !U.rows[u] || cta_any_marked(U.rows[u], read_epoch(U.epoch),
+                                                                w0 + center - kw + 1, w0 + B - 1 + center, nwires);
             float k1[B], k2[B], k3[B];
             float2 acc[B];
 #pragma unroll
@@ -303,7 +348,7 @@ wire_conv_ring_kernel(const __grid_constant__ TmaConvUnits U, int nfreq, int64_t
                     }
                 }
             };
-            const bool live = k < nfreq;
+            const bool live = k < nfreq && live_tile;
             if (live) {
 #pragma unroll
                 for (int uu = 0; uu < kRingRows; ++uu) row(col0[uu * kCols], uu);
@@ -326,7 +371,7 @@ wire_conv_ring_kernel(const __grid_constant__ TmaConvUnits U, int nfreq, int64_t
             }
         }
         __syncthreads();   // the run's last chunks read before the next run reuses the slots
-        t += n;
+        t += run;
     }
 }
 
@@ -367,8 +412,10 @@ cudaError_t launch_tma(const ConvBatch& cb, int nfreq, int64_t stride, int kw, i
         U.nwires[i] = cb.nwires[i];
         U.Y[i] = cb.Y[i];
         U.Rt[i] = cb.Rt[i];
+        U.rows[i] = cb.rows[i];
         U.prefix[i + 1] = U.prefix[i] + nkblocks * ((cb.nwires[i] + B - 1) / B);
     }
+    U.epoch = cb.epoch;
     const int total = U.prefix[cb.n];
     if (total <= 0) return cudaSuccess;
     const int smem = 2 * ROWS * kCols * (int)sizeof(float2);
@@ -407,8 +454,10 @@ cudaError_t launch_ring(const ConvBatch& cb, int nfreq, int64_t stride, int kw, 
         U.nwires[i] = cb.nwires[i];
         U.Y[i] = cb.Y[i];
         U.Rt[i] = cb.Rt[i];
+        U.rows[i] = cb.rows[i];
         U.prefix[i + 1] = U.prefix[i] + nkblocks * ((cb.nwires[i] + kRingRows - 1) / kRingRows);
     }
+    U.epoch = cb.epoch;
     const int total = U.prefix[cb.n];
     if (total <= 0) return cudaSuccess;
     const int smem = kRingSlots * kRingRows * kCols * (int)sizeof(float2);
@@ -550,7 +599,9 @@ cudaError_t launch_wire_conv_impacts_tma(const float2* X, float2* Y, const float
     if (impacts < 1 || impacts > kMaxUnits || nwires <= 0 || nfreq <= 0) return cudaErrorInvalidValue;
     TmaConvUnits U;
     U.n = impacts;
+    U.epoch = nullptr;
     for (int i = 0; i < impacts; ++i) {
+        U.rows[i] = nullptr;
         // impact i: fine rows i, i + I, i + 2I, ... (one per wire)
         const cuuint64_t dims[2] = {(cuuint64_t)(2 * stride), (cuuint64_t)nwires};
         const cuuint64_t strides[1] = {(cuuint64_t)(2 * stride * sizeof(float)) * (cuuint64_t)impacts};

@@ -31,9 +31,9 @@ thread_local char g_last_error[256] = "";
 
 const char* const kKernelNames[] = {"memset_grid", "raster_scatter", "fwd_rows", "wire_conv", "inv_rows",
                                     "patch_sizes", "scan", "raster_patches", "scatter_patches", "depo_grads",
-                                    "resp_grad", "add_noise"};
+                                    "resp_grad", "add_noise", "mark_rows"};
 enum { K_MEMSET, K_RASTER_SCATTER, K_FWD, K_WCONV, K_INV, K_SIZES, K_SCAN, K_RPATCH, K_SCATTER, K_DGRAD,
-       K_RGRAD, K_NOISE, K_COUNT };
+       K_RGRAD, K_NOISE, K_MARK, K_COUNT };
 
 // Record a start event for a traced launch; returns the record slot or -1.
 int trace_begin(ws_plane* pl, int kind, cudaStream_t s) {
@@ -127,7 +127,8 @@ size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 struct Layout {
     ws::FftPlan plan;
     int nfreq, fstride;
-    size_t off_status, off_tw, off_rt, off_x, off_y, off_scan, off_large, off_radj, off_racc, off_grid2, off_noise;
+    size_t off_status, off_tw, off_rt, off_x, off_y, off_scan, off_large, off_radj, off_racc, off_grid2, off_noise,
+        off_rows;
     size_t off_fine;
     int impacts;
     size_t off_tw64, off_rt64, off_x64, off_y64, off_g64, total;
@@ -175,6 +176,7 @@ ws_status plan_layout(const ws_plane_desc* d, Layout* lay) {
     lay->off_racc = o; o = align256(o + sizeof(float2) * (size_t)d->resp_nwires * lay->fstride);
     lay->off_grid2 = o; o = align256(o + sizeof(float) * (size_t)d->nwires * d->nticks);
     lay->off_noise = o; o = align256(o + 2 * sizeof(float) * (size_t)lay->fstride);
+    lay->off_rows = o; o = align256(o + sizeof(uint32_t) * (size_t)d->nwires);
     lay->off_fine = 0;
     if (I > 1) { lay->off_fine = o; o = align256(o + sizeof(float) * (size_t)I * d->nwires * d->nticks); }
     lay->off_tw64 = lay->off_rt64 = lay->off_x64 = lay->off_y64 = lay->off_g64 = 0;
@@ -291,6 +293,72 @@ ws_status add_plane_noise(ws_plane* pl, const ws_params* p, void* Y, bool fp64, 
     } else {
         WS_LAUNCH(pl, K_NOISE, s, ws::launch_add_noise(nb, pl->nfreq, pl->plan.L, pl->fstride, s));
     }
+    return WS_OK;
+}
+
+// Whether a plane's simulations skip inactive rows: FP32 fixed-shape row
+// transforms, linear convolution (windows do not wrap), one impact position
+// and no noise term (noise makes every row of the output live).
+bool marks_apply(const ws_plane* pl) {
+    return pl->impacts == 1 && pl->desc.conv_mode == WS_CONV_LINEAR && pl->noise_mode == 0 &&
+           ws::row_fft_fixed_shape(pl->plan);
+}
+
+// Mark windows of the row transforms (see ws::RowMarks): the forward writes
+// the spectra of rows within K_w - 1 wires of a marked row; the inverse
+// transforms rows whose window [w + c - K_w + 1, w + c] holds a marked row.
+void mark_windows(const ws_plane_desc& d, ws::RowBatch* fwd, ws::RowBatch* inv) {
+    fwd->win_lo = -(d.resp_nwires - 1);
+    fwd->win_hi = d.resp_nwires - 1;
+    inv->win_lo = d.resp_wire_center - d.resp_nwires + 1;
+    inv->win_hi = d.resp_wire_center;
+}
+
+// ws_simulate's FP32 / compensated path with active rows: mark, clear the
+// marked rows, raster, then the three transform stages over marked / live
+// rows only (the same result as clearing and transforming every row).
+ws_status simulate_marked(ws_plane* pl, ws::RasterArgs a, float* out, cudaStream_t s) {
+    const ws_plane_desc& d = pl->desc;
+    ws::RasterBatch rb;
+    rb.n = 1;
+    rb.prec = a.prec;
+    rb.a[0] = a;
+    rb.grid[0] = out;
+    ws::RowMarks m;
+    m.rows[0] = pl->rows;
+    m.epoch = pl->rows_epoch;
+    m.done = pl->rows_done;
+    WS_LAUNCH(pl, K_MARK, s, ws::launch_mark_rows(rb, m, s));
+    WS_LAUNCH(pl, K_MEMSET, s, ws::launch_zero_marked_rows(rb, m, s));
+    WS_LAUNCH(pl, K_RASTER_SCATTER, s, ws::launch_raster_scatter(a, out, pl->large, s));
+    ws::RowBatch fb, ib;
+    fb.n = ib.n = 1;
+    fb.in[0] = out;
+    fb.in2[0] = a.lo;
+    fb.out[0] = pl->X;
+    fb.nrows[0] = d.nwires;
+    ib.in[0] = pl->Y;
+    ib.in2[0] = nullptr;
+    ib.out[0] = out;
+    ib.nrows[0] = d.nwires;
+    fb.status = ib.status = pl->status;
+    fb.rows[0] = ib.rows[0] = pl->rows;
+    fb.epoch = ib.epoch = pl->rows_epoch;
+    mark_windows(d, &fb, &ib);
+    ws::ConvBatch cb;
+    cb.n = 1;
+    cb.X[0] = pl->X;
+    cb.Y[0] = pl->Y;
+    cb.Rt[0] = pl->Rt;
+    cb.nwires[0] = d.nwires;
+    cb.rows[0] = pl->rows;
+    cb.epoch = pl->rows_epoch;
+    WS_LAUNCH(pl, K_FWD, s, ws::launch_fwd_rows_batch(pl->plan, pl->tw, fb, d.nticks, d.nticks, pl->fstride,
+                                                      pl->nfreq, 1.0f, s));
+    WS_LAUNCH(pl, K_WCONV, s, ws::launch_wire_conv_batch(cb, pl->nfreq, pl->fstride, d.resp_nwires,
+                                                         d.resp_wire_center, 0, s, pl->wconv_variant, pl->status));
+    WS_LAUNCH(pl, K_INV, s, ws::launch_inv_rows_batch(pl->plan, pl->tw, ib, pl->fstride, pl->nfreq, d.nticks,
+                                                      d.nticks, s));
     return WS_OK;
 }
 
@@ -412,6 +480,9 @@ ws_status ws_plane_create(const ws_plane_desc* desc, const float* response_dev, 
     pl->X64 = pl->fp64 ? (double2*)(base + lay.off_x64) : nullptr;
     pl->Y64 = pl->fp64 ? (double2*)(base + lay.off_y64) : nullptr;
     pl->g64 = pl->fp64 ? (double*)(base + lay.off_g64) : nullptr;
+    pl->rows = (uint32_t*)(base + lay.off_rows);
+    pl->rows_epoch = (uint32_t*)(base + lay.off_status + 24);   // zeroed with the status region below
+    pl->rows_done = (unsigned*)(base + lay.off_status + 28);
     cudaStream_t s = (cudaStream_t)stream;
     cudaError_t e = cudaMemsetAsync(base + lay.off_status, 0, 256, s);
     if (e == cudaSuccess) e = ws::launch_twiddles(pl->tw, lay.plan, s);
@@ -661,6 +732,10 @@ ws_status ws_simulate(ws_plane* pl, const ws_depos* depos, const ws_params* para
                                                       out_dev, d.nticks, d.nticks, s));
         return WS_OK;
     }
+    if (marks_apply(pl)) {
+        if (params->precision == WS_PREC_FP32_COMP) a.lo = pl->grid2;
+        return simulate_marked(pl, a, out_dev, s);
+    }
     WS_LAUNCH(pl, K_MEMSET, s, cudaMemsetAsync(out_dev, 0, grid_bytes, s));
     if (params->precision == WS_PREC_FP32_COMP) {
         // Compensated scatter: the grid's low parts go to grid2 and are added
@@ -772,8 +847,15 @@ namespace {
 constexpr int kBatchSlots = 3;
 
 struct BatchLayout {
-    size_t off_counters, off_list, off_spec, spec_bytes, slot_bytes, total;
+    size_t off_counters, off_list, off_spec, spec_bytes, off_rows, rows_bytes, slot_bytes, total;
 };
+// Within a slot's 256-byte counter block: the large-patch list's count and
+// done words and the marking kernel's block counter (bytes 0..63, cleared at
+// the start of every call), and the active-row epoch (byte 128, never
+// cleared: any starting value serves).
+constexpr size_t kBatchClearBytes = 64;
+constexpr size_t kBatchRowsDone = 8;
+constexpr size_t kBatchRowsEpoch = 128;
 
 ws_status batch_layout(ws_plane* const* planes, int nplanes, int units_per_wave, BatchLayout* lay) {
     if (units_per_wave == 0) units_per_wave = ws::kMaxUnits;
@@ -799,6 +881,8 @@ ws_status batch_layout(ws_plane* const* planes, int nplanes, int units_per_wave,
     lay->off_list = o; o = align256(o + sizeof(long long) * (size_t)ws::kLargeListCap);
     lay->spec_bytes = align256(sizeof(float2) * (size_t)maxw * p0->fstride);
     lay->off_spec = o; o += 2 * (size_t)units_per_wave * lay->spec_bytes;
+    lay->rows_bytes = align256(sizeof(uint32_t) * (size_t)maxw);
+    lay->off_rows = o; o += (size_t)units_per_wave * lay->rows_bytes;
     lay->slot_bytes = o;
     lay->total = kBatchSlots * o;
     return WS_OK;
@@ -1037,7 +1121,10 @@ ws_status batch_waves(ws_plane* const* planes, int nplanes, const ws_depos* depo
     // planes, else the first plane's own
     const int wconv = p0->batch_wconv >= 0 ? p0->batch_wconv : p0->wconv_variant;
     for (int slot = 0; slot < nstreams; ++slot)
-        WS_CUDA(cudaMemsetAsync(ws_base + slot * lay.slot_bytes + lay.off_counters, 0, 256, ss[slot]));
+        WS_CUDA(cudaMemsetAsync(ws_base + slot * lay.slot_bytes + lay.off_counters, 0, kBatchClearBytes, ss[slot]));
+    // active rows for every unit whose plane allows them (see marks_apply;
+    // the transform plan and convolution mode are shared by the batch)
+    const bool marked = d0.conv_mode == WS_CONV_LINEAR && ws::row_fft_fixed_shape(p0->plan);
     for (int u0 = 0, wave = 0; u0 < nunits; u0 += units_per_wave, ++wave) {
         const int nu = nunits - u0 < units_per_wave ? nunits - u0 : units_per_wave;
         const int slot = wave % nstreams;
@@ -1059,6 +1146,9 @@ ws_status batch_waves(ws_plane* const* planes, int nplanes, const ws_depos* depo
         rb.prec = WS_PREC_FP32;
         nb.key0 = (uint32_t)(params->seed & 0xFFFFFFFFu);
         nb.key1 = (uint32_t)(params->seed >> 32);
+        ws::RowMarks m;
+        m.epoch = (uint32_t*)(base + lay.off_counters + kBatchRowsEpoch);
+        m.done = (unsigned*)(base + lay.off_counters + kBatchRowsDone);
         for (int j = 0; j < nu; ++j) {
             const int u = u0 + j, e = u / nplanes, pi = u % nplanes;
             ws_plane* pl = planes[pi];
@@ -1066,6 +1156,9 @@ ws_status batch_waves(ws_plane* const* planes, int nplanes, const ws_depos* depo
             pe.event_id = params->event_id + (uint32_t)e;
             float2* X = (float2*)(base + lay.off_spec + (size_t)(2 * j) * lay.spec_bytes);
             float2* Y = (float2*)(base + lay.off_spec + (size_t)(2 * j + 1) * lay.spec_bytes);
+            m.rows[j] = (marked && marks_apply(pl)) ? (uint32_t*)(base + lay.off_rows + (size_t)j * lay.rows_bytes)
+                                                    : nullptr;
+            fb.rows[j] = ib.rows[j] = cb.rows[j] = m.rows[j];
             rb.a[j] = raster_args(pl, &depos[u], &pe);
             rb.grid[j] = out_dev[u];
             counts[j] = (int64_t)pl->desc.nwires * pl->desc.nticks;
@@ -1086,7 +1179,14 @@ ws_status batch_waves(ws_plane* const* planes, int nplanes, const ws_depos* depo
             if (noise_unit(pl, pe.event_id, &nb.noise[j])) noisy = true;
             else nb.noise[j] = ws::NoiseUnit{};
         }
-        WS_LAUNCH(p0, K_MEMSET, s, ws::launch_zero_grids(rb, counts, s));
+        if (marked) {
+            fb.epoch = ib.epoch = cb.epoch = m.epoch;
+            mark_windows(d0, &fb, &ib);
+            WS_LAUNCH(p0, K_MARK, s, ws::launch_mark_rows(rb, m, s));
+            WS_LAUNCH(p0, K_MEMSET, s, ws::launch_zero_marked_rows(rb, m, s));
+        } else {
+            WS_LAUNCH(p0, K_MEMSET, s, ws::launch_zero_grids(rb, counts, s));
+        }
         WS_LAUNCH(p0, K_RASTER_SCATTER, s, ws::launch_raster_scatter_batch(rb, L, s));
         WS_LAUNCH(p0, K_FWD, s, ws::launch_fwd_rows_batch(p0->plan, p0->tw, fb, d0.nticks, d0.nticks, p0->fstride,
                                                           p0->nfreq, 1.0f, s));
