@@ -756,8 +756,8 @@ fwd_rows_shape_kernel(FftPlan plan, const float2* __restrict__ tw, const __grid_
     // is not read); a pair with no marked row has zero spectra, written only
     // if a live row's wire convolution may read them
     bool use_a = true, use_b = has_b;
-    if (const uint32_t* marks = U.rows[u]) {
-        const uint32_t cur = read_epoch(U.epoch);
+    if (const mark_t* marks = U.rows[u]) {
+        const mark_t cur = read_epoch(U.epoch);
         use_a = marks[r0] == cur;
         use_b = has_b && marks[r0 + 1] == cur;
         if (!use_a && !use_b) {
@@ -832,8 +832,8 @@ inv_rows_shape_kernel(FftPlan plan, const float2* __restrict__ tw, const __grid_
     // is zero (its spectrum, possibly never written, is not read); a pair of
     // such rows is stored as zeros without a transform
     bool live_a = true, live_b = has_b;
-    if (const uint32_t* marks = U.rows[u]) {
-        const uint32_t cur = read_epoch(U.epoch);
+    if (const mark_t* marks = U.rows[u]) {
+        const mark_t cur = read_epoch(U.epoch);
         live_a = cta_any_marked(marks, cur, r0 + U.win_lo, r0 + U.win_hi, U.nrows[u]);
         live_b = has_b && cta_any_marked(marks, cur, r0 + 1 + U.win_lo, r0 + 1 + U.win_hi, U.nrows[u]);
         if (!live_a && !live_b) {
@@ -908,7 +908,7 @@ wire_conv_kernel(const __grid_constant__ ConvUnits U, int nfreq, int64_t stride,
     const int w0 = ((int)blockIdx.y - U.prefix[u]) * B;
     const int ibase = w0 + center - (K - 1);
     // active rows: a tile none of whose output rows is live is never read
-    if (const uint32_t* marks = U.rows[u])
+    if (const mark_t* marks = U.rows[u])
         if (!cta_any_marked(marks, read_epoch(U.epoch), w0 + center - kw + 1, w0 + B - 1 + center, nwires)) return;
     constexpr int PER = std::is_same<S, float>::value ? 2 : 1;   // complex values per 16-byte load
     for (int e = threadIdx.x; e < ROWS * (kConvCols / PER); e += kConvCols) {

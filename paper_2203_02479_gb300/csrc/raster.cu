@@ -1472,97 +1472,103 @@ cudaError_t launch_zero_grids(const RasterBatch& rb, const int64_t* counts, cuda
 // Active rows, step 1: every depo marks the wire rows [w0 - 1, w1 + 1] of its
 // clipped pitch-axis range (the raster's own extent, computed the same way,
 // widened by one wire against rounding differences between the two
-// kernels) with the new epoch.  Depos along a track share rows, and many
-// threads storing to the same few words serialise in L2, so a warp first
-// merges its lanes' ranges: when they fall within 32 rows of one unit, one
-// lane stores each of the warp's rows once.  The last block to finish
-// stores the epoch and resets the block counter; every block reads the old
-// epoch before any block counts itself done, so all of them mark with the
-// same value.
+// kernels) with the new epoch, base + 1.  Block (x, u) takes unit u's depos
+// x, x + gridDim.x, ... (256 at a time) with the unit's parameters staged in
+// shared memory.  Depos along a track share rows, and many threads storing
+// to the same few words serialise in L2, so a warp merges its lanes' ranges
+// when they fall within 32 rows and stores each of their rows once.  Block
+// (0, 0) stores the epoch; `base` is not written while this kernel runs.
+struct MarkUnit {
+    const float* x;
+    const float* t;
+    const float* sig_x;   // null: widths from diffusion
+    int64_t n;
+    float two_DT, pitch, nsig;
+    int nwires;
+    mark_t* rows;
+};
+
+__device__ __forceinline__ MarkUnit mark_unit(const RasterUnits& U, int u) {
+    const RasterArgs& a = U.a[u];
+    return MarkUnit{a.x, a.t, a.sig_t ? a.sig_x : nullptr, a.n, a.two_DT, a.pitch, a.nsig, a.nwires, U.rows[u]};
+}
+
 __global__ void __launch_bounds__(256)
-mark_rows_kernel(const __grid_constant__ RasterUnits U, uint32_t* epoch, unsigned* done) {
-    const uint32_t e = read_epoch(epoch) + 1u;
-    const int64_t total = U.dprefix[U.n];
+mark_rows_kernel(const __grid_constant__ RasterUnits U, const mark_t* base_epoch, mark_t* epoch) {
+    __shared__ MarkUnit mu;
+    const mark_t e = read_epoch(base_epoch) + 1ull;
+    if (threadIdx.x == 0) mu = mark_unit(U, blockIdx.y);
+    __syncthreads();
+    if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) *epoch = e;
+    if (!mu.rows) return;
     const int lane = threadIdx.x & 31;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     // whole warps iterate together (the merge below needs every lane)
-    for (int64_t base = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < total; base += stride) {
-        const int64_t it = base + lane;
-        int u = -1, lo = 0, hi = -1;
-        if (it < total) {
-            u = find_unit64(U.dprefix, U.n, it);
-            const RasterArgs& a = U.a[u];
-            if (U.rows[u]) {
-                const int64_t i = it - U.dprefix[u];
-                const float x = __ldg(a.x + i);
-                float sx;
-                if (a.sig_t) {
-                    sx = __ldg(a.sig_x + i);
-                } else {
-                    const float t = __ldg(a.t + i);
-                    sx = sqrtf(a.two_DT * (t > 0.f ? t : 0.f));
-                }
-                bool point = false;
-                axis_range<float>(x, sx, a.pitch, a.nsig, a.nwires, &lo, &hi, &point);
-                lo = lo - 1 > 0 ? lo - 1 : 0;
-                hi = hi + 1 < a.nwires - 1 ? hi + 1 : a.nwires - 1;
+    for (int64_t wbase = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); wbase < mu.n; wbase += stride) {
+        const int64_t i = wbase + lane;
+        int lo = 0, hi = -1;
+        if (i < mu.n) {
+            const float x = __ldg(mu.x + i);
+            float sx;
+            if (mu.sig_x) {
+                sx = __ldg(mu.sig_x + i);
             } else {
-                u = -1;
+                const float t = __ldg(mu.t + i);
+                sx = sqrtf(mu.two_DT * (t > 0.f ? t : 0.f));
             }
+            bool point = false;
+            axis_range<float>(x, sx, mu.pitch, mu.nsig, mu.nwires, &lo, &hi, &point);
+            lo = lo - 1 > 0 ? lo - 1 : 0;
+            hi = hi + 1 < mu.nwires - 1 ? hi + 1 : mu.nwires - 1;
         }
-        const bool has = u >= 0 && lo <= hi;
-        const int u0 = __shfl_sync(0xffffffffu, u, 0);
+        const bool has = lo <= hi;
         const int mlo = __reduce_min_sync(0xffffffffu, has ? lo : INT_MAX);
         const int mhi = __reduce_max_sync(0xffffffffu, has ? hi : -1);
-        const bool one_unit = __all_sync(0xffffffffu, !has || u == u0);
         if (mhi < 0) continue;   // no lane marks anything
-        if (one_unit && mhi - mlo < 32) {
+        if (mhi - mlo < 32) {
             const uint32_t mine =
                 has ? (uint32_t)((2ull << (hi - mlo)) - 1ull) & ~((1u << (lo - mlo)) - 1u) : 0u;
-            const uint32_t all = __reduce_or_sync(0xffffffffu, mine);
-            if (lane == 0) {
-                uint32_t* rows = U.rows[u0];
-                for (uint32_t b = all; b; b &= b - 1u) rows[mlo + __ffs((int)b) - 1] = e;
-            }
+            if ((__reduce_or_sync(0xffffffffu, mine) >> lane) & 1u) mu.rows[mlo + lane] = e;
         } else if (has) {
-            uint32_t* rows = U.rows[u];
-            for (int w = lo; w <= hi; ++w) rows[w] = e;
-        }
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        __threadfence();
-        if (atomicAdd(done, 1u) == gridDim.x - 1) {
-            *(volatile uint32_t*)epoch = e;
-            *(volatile unsigned*)done = 0u;
-            __threadfence();
+            for (int w = lo; w <= hi; ++w) mu.rows[w] = e;
         }
     }
 }
 
-// Active rows, step 2: clear the marked rows of every unit's grid (and of
-// its compensated low-part grid); a unit without marks is cleared whole.
-// Rows are taken block by block; a row of float4 stores when it is 16-byte
-// aligned, else scalar stores.
+// Active rows, step 2: clear the marked rows of unit u's grid (and of its
+// compensated low-part grid), a warp per row, or the whole grid of a unit
+// without marks.  Block (0, 0) hands the epoch on to the next call's
+// marking kernel (`base`; the marking kernel is not running).
+struct ZeroUnit {
+    float* grid;
+    float* lo;
+    const mark_t* rows;   // null: every row
+    int nwires, nticks;
+};
+
 __global__ void __launch_bounds__(256)
-zero_marked_rows_kernel(const __grid_constant__ RasterUnits U, const uint32_t* epoch) {
-    const uint32_t cur = read_epoch(epoch);
-    for (int u = 0; u < U.n; ++u) {
-        const RasterArgs& a = U.a[u];
-        const uint32_t* rows = U.rows[u];
-        const int nt = a.nticks;
-        for (int w = blockIdx.x; w < a.nwires; w += gridDim.x) {
-            if (rows && rows[w] != cur) continue;
-            for (int g = 0; g < 2; ++g) {
-                float* row = (g == 0 ? U.grid[u] : a.lo);
-                if (!row) continue;
-                row += (int64_t)w * nt;
-                if ((uintptr_t)row % 16 == 0 && nt % 4 == 0) {
-                    float4* r4 = reinterpret_cast<float4*>(row);
-                    for (int j = threadIdx.x; j < nt / 4; j += blockDim.x) r4[j] = make_float4(0.f, 0.f, 0.f, 0.f);
-                } else {
-                    for (int j = threadIdx.x; j < nt; j += blockDim.x) row[j] = 0.f;
-                }
+zero_marked_rows_kernel(const __grid_constant__ RasterUnits U, const mark_t* epoch, mark_t* base) {
+    __shared__ ZeroUnit zu;
+    const mark_t cur = read_epoch(epoch);
+    if (threadIdx.x == 0) {
+        const int u = blockIdx.y;
+        zu = ZeroUnit{U.grid[u], U.a[u].lo, U.rows[u], U.a[u].nwires, U.a[u].nticks};
+    }
+    __syncthreads();
+    if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0 && base) *base = cur;
+    const int lane = threadIdx.x & 31;
+    const int nt = zu.nticks;
+    for (int w = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); w < zu.nwires; w += gridDim.x * (blockDim.x >> 5)) {
+        if (zu.rows && zu.rows[w] != cur) continue;
+        for (int g = 0; g < 2; ++g) {
+            float* row = g == 0 ? zu.grid : zu.lo;
+            if (!row) continue;
+            row += (int64_t)w * nt;
+            if ((uintptr_t)row % 16 == 0 && nt % 4 == 0) {
+                float4* r4 = reinterpret_cast<float4*>(row);
+                for (int j = lane; j < nt / 4; j += 32) r4[j] = make_float4(0.f, 0.f, 0.f, 0.f);
+            } else {
+                for (int j = lane; j < nt; j += 32) row[j] = 0.f;
             }
         }
     }
@@ -1571,17 +1577,27 @@ zero_marked_rows_kernel(const __grid_constant__ RasterUnits U, const uint32_t* e
 cudaError_t launch_mark_rows(const RasterBatch& rb, const RowMarks& m, cudaStream_t s) {
     if (rb.n <= 0) return cudaSuccess;
     RasterUnits U = raster_units(rb);
-    for (int i = 0; i < rb.n; ++i) U.rows[i] = m.rows[i];
-    // at least one block, so that the epoch advances even with no depos
-    const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((U.dprefix[U.n] + 255) / 256, num_sms() * 8));
-    mark_rows_kernel<<<blocks, 256, 0, s>>>(U, m.epoch, m.done);
+    int64_t maxn = 0;
+    for (int i = 0; i < rb.n; ++i) {
+        U.rows[i] = m.rows[i];
+        maxn = std::max<int64_t>(maxn, rb.a[i].n);
+    }
+    // at least one block per unit (block (0, 0) stores the epoch)
+    const int bx = (int)std::max<int64_t>(1, std::min<int64_t>((maxn + 255) / 256, 256));
+    mark_rows_kernel<<<dim3(bx, rb.n), 256, 0, s>>>(U, m.base, m.epoch);
     return cudaGetLastError();
 }
 
 cudaError_t launch_zero_marked_rows(const RasterBatch& rb, const RowMarks& m, cudaStream_t s) {
+    if (rb.n <= 0) return cudaSuccess;
     RasterUnits U = raster_units(rb);
-    for (int i = 0; i < rb.n; ++i) U.rows[i] = m.rows[i];
-    zero_marked_rows_kernel<<<num_sms() * 8, 256, 0, s>>>(U, m.epoch);
+    int maxw = 1;
+    for (int i = 0; i < rb.n; ++i) {
+        U.rows[i] = m.rows[i];
+        maxw = std::max(maxw, rb.a[i].nwires);
+    }
+    const int bx = (maxw + 7) / 8;   // a warp per row
+    zero_marked_rows_kernel<<<dim3(bx, rb.n), 256, 0, s>>>(U, m.epoch, m.base);
     return cudaGetLastError();
 }
 

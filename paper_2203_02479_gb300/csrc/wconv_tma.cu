@@ -32,8 +32,8 @@ struct TmaConvUnits {
     int nwires[kMaxUnits];
     void* Y[kMaxUnits];
     const void* Rt[kMaxUnits];
-    const uint32_t* rows[kMaxUnits];       // active-row marks, or null (every tile computed)
-    const uint32_t* epoch;
+    const mark_t* rows[kMaxUnits];         // active-row marks, or null (every tile computed)
+    const mark_t* epoch;
 };
 
 // 2D tile copy of the box at (x, y) into dst, completing on bar.
@@ -250,8 +250,8 @@ wire_conv_ring_kernel(const __grid_constant__ TmaConvUnits U, int nfreq, int64_t
         // active rows: trim the run to its first .. last live tile (a tile is
         // live if a marked row lies in [w0 + c - K_w + 1, w0 + B - 1 + c]),
         // so the chunks of dead tiles at either end are never fetched
-        if (const uint32_t* marks = U.rows[u]) {
-            const uint32_t cur = read_epoch(U.epoch);
+        if (const mark_t* marks = U.rows[u]) {
+            const mark_t cur = read_epoch(U.epoch);
             const int nw = U.nwires[u];
             if (threadIdx.x == 0) s_live = 0ull;
             __syncthreads();

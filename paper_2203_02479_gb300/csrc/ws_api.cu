@@ -176,7 +176,7 @@ ws_status plan_layout(const ws_plane_desc* d, Layout* lay) {
     lay->off_racc = o; o = align256(o + sizeof(float2) * (size_t)d->resp_nwires * lay->fstride);
     lay->off_grid2 = o; o = align256(o + sizeof(float) * (size_t)d->nwires * d->nticks);
     lay->off_noise = o; o = align256(o + 2 * sizeof(float) * (size_t)lay->fstride);
-    lay->off_rows = o; o = align256(o + sizeof(uint32_t) * (size_t)d->nwires);
+    lay->off_rows = o; o = align256(o + sizeof(ws::mark_t) * (size_t)d->nwires);
     lay->off_fine = 0;
     if (I > 1) { lay->off_fine = o; o = align256(o + sizeof(float) * (size_t)I * d->nwires * d->nticks); }
     lay->off_tw64 = lay->off_rt64 = lay->off_x64 = lay->off_y64 = lay->off_g64 = 0;
@@ -327,7 +327,7 @@ ws_status simulate_marked(ws_plane* pl, ws::RasterArgs a, float* out, cudaStream
     ws::RowMarks m;
     m.rows[0] = pl->rows;
     m.epoch = pl->rows_epoch;
-    m.done = pl->rows_done;
+    m.base = pl->rows_base;
     WS_LAUNCH(pl, K_MARK, s, ws::launch_mark_rows(rb, m, s));
     WS_LAUNCH(pl, K_MEMSET, s, ws::launch_zero_marked_rows(rb, m, s));
     WS_LAUNCH(pl, K_RASTER_SCATTER, s, ws::launch_raster_scatter(a, out, pl->large, s));
@@ -480,11 +480,13 @@ ws_status ws_plane_create(const ws_plane_desc* desc, const float* response_dev, 
     pl->X64 = pl->fp64 ? (double2*)(base + lay.off_x64) : nullptr;
     pl->Y64 = pl->fp64 ? (double2*)(base + lay.off_y64) : nullptr;
     pl->g64 = pl->fp64 ? (double*)(base + lay.off_g64) : nullptr;
-    pl->rows = (uint32_t*)(base + lay.off_rows);
-    pl->rows_epoch = (uint32_t*)(base + lay.off_status + 24);   // zeroed with the status region below
-    pl->rows_done = (unsigned*)(base + lay.off_status + 28);
+    pl->rows = (ws::mark_t*)(base + lay.off_rows);
+    pl->rows_epoch = (ws::mark_t*)(base + lay.off_status + 24);   // zeroed with the status region below
+    pl->rows_base = (ws::mark_t*)(base + lay.off_status + 32);
     cudaStream_t s = (cudaStream_t)stream;
     cudaError_t e = cudaMemsetAsync(base + lay.off_status, 0, 256, s);
+    // marks start below every epoch (the first call marks with 1)
+    if (e == cudaSuccess) e = cudaMemsetAsync(pl->rows, 0, sizeof(ws::mark_t) * (size_t)desc->nwires, s);
     if (e == cudaSuccess) e = ws::launch_twiddles(pl->tw, lay.plan, s);
     // Response spectrum: per response row, the tick transform scaled by 1/L so
     // that the inverse transform needs no scaling.
@@ -849,13 +851,14 @@ constexpr int kBatchSlots = 3;
 struct BatchLayout {
     size_t off_counters, off_list, off_spec, spec_bytes, off_rows, rows_bytes, slot_bytes, total;
 };
-// Within a slot's 256-byte counter block: the large-patch list's count and
-// done words and the marking kernel's block counter (bytes 0..63, cleared at
-// the start of every call), and the active-row epoch (byte 128, never
-// cleared: any starting value serves).
+// Within a slot's 256-byte counter block (cleared at the start of every call):
+// the large-patch list's count and done words, and the active-row epochs
+// (base at byte 8, epoch at byte 16).  The slot's marks are cleared at the
+// start of every call too, so the waves of a call that share a slot mark
+// with epochs 1, 2, ... above every mark there.
 constexpr size_t kBatchClearBytes = 64;
-constexpr size_t kBatchRowsDone = 8;
-constexpr size_t kBatchRowsEpoch = 128;
+constexpr size_t kBatchRowsBase = 8;
+constexpr size_t kBatchRowsEpoch = 16;
 
 ws_status batch_layout(ws_plane* const* planes, int nplanes, int units_per_wave, BatchLayout* lay) {
     if (units_per_wave == 0) units_per_wave = ws::kMaxUnits;
@@ -881,7 +884,7 @@ ws_status batch_layout(ws_plane* const* planes, int nplanes, int units_per_wave,
     lay->off_list = o; o = align256(o + sizeof(long long) * (size_t)ws::kLargeListCap);
     lay->spec_bytes = align256(sizeof(float2) * (size_t)maxw * p0->fstride);
     lay->off_spec = o; o += 2 * (size_t)units_per_wave * lay->spec_bytes;
-    lay->rows_bytes = align256(sizeof(uint32_t) * (size_t)maxw);
+    lay->rows_bytes = align256(sizeof(ws::mark_t) * (size_t)maxw);
     lay->off_rows = o; o += (size_t)units_per_wave * lay->rows_bytes;
     lay->slot_bytes = o;
     lay->total = kBatchSlots * o;
@@ -1120,11 +1123,14 @@ ws_status batch_waves(ws_plane* const* planes, int nplanes, const ws_depos* depo
     // the wire-convolution kernel the batch autotuner picked for these
     // planes, else the first plane's own
     const int wconv = p0->batch_wconv >= 0 ? p0->batch_wconv : p0->wconv_variant;
-    for (int slot = 0; slot < nstreams; ++slot)
-        WS_CUDA(cudaMemsetAsync(ws_base + slot * lay.slot_bytes + lay.off_counters, 0, kBatchClearBytes, ss[slot]));
     // active rows for every unit whose plane allows them (see marks_apply;
     // the transform plan and convolution mode are shared by the batch)
     const bool marked = d0.conv_mode == WS_CONV_LINEAR && ws::row_fft_fixed_shape(p0->plan);
+    for (int slot = 0; slot < nstreams; ++slot) {
+        char* sb = ws_base + slot * lay.slot_bytes;
+        WS_CUDA(cudaMemsetAsync(sb + lay.off_counters, 0, kBatchClearBytes, ss[slot]));
+        if (marked) WS_CUDA(cudaMemsetAsync(sb + lay.off_rows, 0, (size_t)units_per_wave * lay.rows_bytes, ss[slot]));
+    }
     for (int u0 = 0, wave = 0; u0 < nunits; u0 += units_per_wave, ++wave) {
         const int nu = nunits - u0 < units_per_wave ? nunits - u0 : units_per_wave;
         const int slot = wave % nstreams;
@@ -1147,8 +1153,8 @@ ws_status batch_waves(ws_plane* const* planes, int nplanes, const ws_depos* depo
         nb.key0 = (uint32_t)(params->seed & 0xFFFFFFFFu);
         nb.key1 = (uint32_t)(params->seed >> 32);
         ws::RowMarks m;
-        m.epoch = (uint32_t*)(base + lay.off_counters + kBatchRowsEpoch);
-        m.done = (unsigned*)(base + lay.off_counters + kBatchRowsDone);
+        m.epoch = (ws::mark_t*)(base + lay.off_counters + kBatchRowsEpoch);
+        m.base = (ws::mark_t*)(base + lay.off_counters + kBatchRowsBase);
         for (int j = 0; j < nu; ++j) {
             const int u = u0 + j, e = u / nplanes, pi = u % nplanes;
             ws_plane* pl = planes[pi];
@@ -1156,7 +1162,7 @@ ws_status batch_waves(ws_plane* const* planes, int nplanes, const ws_depos* depo
             pe.event_id = params->event_id + (uint32_t)e;
             float2* X = (float2*)(base + lay.off_spec + (size_t)(2 * j) * lay.spec_bytes);
             float2* Y = (float2*)(base + lay.off_spec + (size_t)(2 * j + 1) * lay.spec_bytes);
-            m.rows[j] = (marked && marks_apply(pl)) ? (uint32_t*)(base + lay.off_rows + (size_t)j * lay.rows_bytes)
+            m.rows[j] = (marked && marks_apply(pl)) ? (ws::mark_t*)(base + lay.off_rows + (size_t)j * lay.rows_bytes)
                                                     : nullptr;
             fb.rows[j] = ib.rows[j] = cb.rows[j] = m.rows[j];
             rb.a[j] = raster_args(pl, &depos[u], &pe);

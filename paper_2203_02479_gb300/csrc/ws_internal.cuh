@@ -136,11 +136,14 @@ struct NoiseUnit {
 // ---- active rows
 // A simulation marks, before its raster, every wire row of a unit's grid that
 // the raster may touch (a superset: each depo's clipped wire range widened by
-// one wire); rows[w] == *epoch marks row w.  The marking kernel advances
-// *epoch, so the marks of earlier calls go stale without being cleared, and
-// every later stage reads *epoch once at its start.  An unmarked row of S is
-// zero, so the stages after the raster skip it exactly:
-//   grid clear   clears marked rows only (the raster adds into no other);
+// one wire); rows[w] == the call's epoch marks row w.  Two epoch words: the
+// marking kernel reads `base` and marks with base + 1, which it stores to
+// `epoch`; the clearing kernel that follows it clears the marked rows (the
+// raster adds into no other row) and copies `epoch` to `base` for the next
+// call.  Marks of earlier calls so go stale without being cleared, also
+// across CUDA graph replays, and every later stage reads `epoch` once at its
+// start.  An unmarked row of S is zero, so the stages after the raster skip
+// it exactly:
 //   forward      transforms row pairs with a marked row (an unmarked row of
 //                such a pair reads as zero); writes zero spectra for rows
 //                within K_w - 1 wires of a marked row (the wire convolution
@@ -152,17 +155,19 @@ struct NoiseUnit {
 //                no spectrum for them) and transforms the others.
 // The result is the same as transforming every row: unmarked rows are exact
 // zeros through each stage.
+// Marks and epochs are 64-bit: an epoch never comes round again.
+using mark_t = unsigned long long;
 struct RowMarks {
-    uint32_t* rows[kMaxUnits];    // per unit, nwires entries; null: every row active
-    uint32_t* epoch;              // the call's epoch word (advanced by the marking kernel)
-    unsigned* done;               // the marking kernel's block counter (zero between launches)
+    mark_t* rows[kMaxUnits];      // per unit, nwires entries; null: every row active
+    mark_t* epoch;                // the call's epoch (written by the marking kernel)
+    mark_t* base;                 // the previous call's epoch (copied from `epoch` by the clearing kernel)
 };
 
-__device__ __forceinline__ uint32_t read_epoch(const uint32_t* e) { return *(const volatile uint32_t*)e; }
+__device__ __forceinline__ mark_t read_epoch(const mark_t* e) { return *(const volatile mark_t*)e; }
 
 // Whether any row of [lo, hi] (clipped to [0, n)) is marked; every thread of
 // the CTA calls it (one barrier).
-__device__ __forceinline__ bool cta_any_marked(const uint32_t* rows, uint32_t cur, int lo, int hi, int n) {
+__device__ __forceinline__ bool cta_any_marked(const mark_t* rows, mark_t cur, int lo, int hi, int n) {
     if (lo < 0) lo = 0;
     if (hi > n - 1) hi = n - 1;
     bool any = false;
@@ -183,8 +188,8 @@ struct RowBatch {          // row transforms: unit i has nrows[i] rows in[i] -> 
     // rows), the epoch word, and the window of marks that decides a row:
     // forward, [r - (K_w - 1), r + K_w - 1] (its spectrum is needed);
     // inverse, [r + c - K_w + 1, r + c] (it is live)
-    const uint32_t* rows[kMaxUnits] = {};
-    const uint32_t* epoch = nullptr;
+    const mark_t* rows[kMaxUnits] = {};
+    const mark_t* epoch = nullptr;
     int win_lo = 0, win_hi = 0;
 };
 struct NoiseBatch {        // noise added to the spectra Y[i] (nwires[i] rows) of each unit
@@ -202,8 +207,8 @@ struct ConvBatch {         // wire convolutions: unit i maps X[i] -> Y[i] with t
     int nwires[kMaxUnits];
     // active rows (FP32 kernels; null: compute every tile): a tile is skipped
     // when none of its output rows is live
-    const uint32_t* rows[kMaxUnits] = {};
-    const uint32_t* epoch = nullptr;
+    const mark_t* rows[kMaxUnits] = {};
+    const mark_t* epoch = nullptr;
 };
 // Device-side tables (kernel parameters, read in place as __grid_constant__).
 struct RowUnits {
@@ -214,8 +219,8 @@ struct RowUnits {
     void* out[kMaxUnits];
     int nrows[kMaxUnits];
     uint32_t* status;
-    const uint32_t* rows[kMaxUnits];
-    const uint32_t* epoch;
+    const mark_t* rows[kMaxUnits];
+    const mark_t* epoch;
     int win_lo, win_hi;
 };
 struct NoiseUnits {
@@ -233,8 +238,8 @@ struct ConvUnits {
     void* Y[kMaxUnits];
     const void* Rt[kMaxUnits];
     int nwires[kMaxUnits];
-    const uint32_t* rows[kMaxUnits];
-    const uint32_t* epoch;
+    const mark_t* rows[kMaxUnits];
+    const mark_t* epoch;
 };
 
 // ---- FFT / convolution launchers (fft.cu)
@@ -337,7 +342,7 @@ struct RasterUnits {
     long long dprefix[kMaxUnits + 1];   // cumulative depos
     RasterArgs a[kMaxUnits];
     float* grid[kMaxUnits];
-    uint32_t* rows[kMaxUnits];          // active-row marks (mark / clear kernels), or null
+    mark_t* rows[kMaxUnits];            // active-row marks (mark / clear kernels), or null
 };
 struct ZeroSizes {
     long long count[kMaxUnits];
@@ -345,9 +350,9 @@ struct ZeroSizes {
 cudaError_t launch_raster_scatter_batch(const RasterBatch& rb, const LargeList& L, cudaStream_t s);
 cudaError_t launch_zero_grids(const RasterBatch& rb, const int64_t* counts, cudaStream_t s);
 // Active rows: mark every unit's rows its depos may touch (units with null
-// marks are skipped; advances *m.epoch), then clear the marked rows of every
-// unit's grid (and of its compensated low-part grid, if any; a unit with
-// null marks is cleared whole).
+// marks are skipped), then clear the marked rows of every unit's grid (and
+// of its compensated low-part grid, if any; a unit with null marks is
+// cleared whole).
 cudaError_t launch_mark_rows(const RasterBatch& rb, const RowMarks& m, cudaStream_t s);
 cudaError_t launch_zero_marked_rows(const RasterBatch& rb, const RowMarks& m, cudaStream_t s);
 cudaError_t launch_patch_sizes(const RasterArgs& a, int64_t* sizes, unsigned long long* total,
@@ -404,7 +409,7 @@ struct ws_plane {
     double2* X64;       // FP64 spectra
     double2* Y64;
     double* g64;        // FP64 grid
-    uint32_t* rows;     // nwires active-row marks (ws_simulate)
-    uint32_t* rows_epoch;   // their epoch word and marking-kernel block counter (status region)
-    unsigned* rows_done;
+    ws::mark_t* rows;        // nwires active-row marks (ws_simulate)
+    ws::mark_t* rows_epoch;  // their epoch words (ws::RowMarks epoch and base, status region)
+    ws::mark_t* rows_base;
 };
