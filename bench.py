@@ -233,33 +233,88 @@ def workload_units(w):
     return [(e, p) for e in range(len(w.events)) for p in range(len(w.planes))]
 
 
-def algorithmic_bytes(kernel: str, nw: int, nt: int, nfreq: int, kw: int, ndepo: int) -> float:
+class UnitSpec:
+    """Sizes of one (event, plane) unit for the work model: grid, transform,
+    response, depos, and its row counts under active rows: `touched` rows
+    the raster can reach (each depo's wire range, widened by one wire, as the
+    library marks them), `need` rows whose spectra the wire convolution may
+    read (within K_w - 1 wires of a touched row) and `live` output rows (a
+    touched row within the response window).  Without active rows (noise
+    on, circular mode, no fixed-shape transform) every row counts."""
+
+    def __init__(self, nw, nt, nf, L, kw, nd, touched=None, need=None, live=None):
+        self.nw, self.nt, self.nf, self.L, self.kw, self.nd = nw, nt, nf, L, kw, nd
+        self.touched = nw if touched is None else touched
+        self.need = nw if need is None else need
+        self.live = nw if live is None else live
+
+
+def algorithmic_bytes(kernel: str, u: UnitSpec) -> float:
     """Bytes a kernel's step must move at minimum (inputs read once, outputs
-    written once), per launch on one plane."""
-    spec = 8.0 * nfreq * nw
+    written once), per launch on one unit, counting only the rows the
+    kernel has to touch."""
     if kernel == "raster_scatter":
-        return 12.0 * ndepo + 4.0 * nw * nt
-    if kernel == "fwd_rows":
-        return 4.0 * nw * nt + spec
-    if kernel == "wire_conv":
-        return 2.0 * spec + 8.0 * nfreq * kw
-    if kernel == "inv_rows":
-        return spec + 4.0 * nw * nt
+        return 12.0 * u.nd + 4.0 * u.touched * u.nt
+    if kernel == "mark_rows":
+        return 8.0 * u.nd
     if kernel == "memset_grid":
-        return 4.0 * nw * nt
-    return 0.0
-
-
-def algorithmic_flops(kernel: str, nw: int, nt: int, L: int, nfreq: int, kw: int) -> float:
-    """FP32 flops a kernel's step needs by the usual count, per launch on one
-    plane: 5 L log2 L per complex L-point FFT (two real rows per transform),
-    8 per complex multiply-add of the wire-axis sum."""
-    import math
-    if kernel in ("fwd_rows", "inv_rows"):
-        return (nw + 1) // 2 * 5.0 * L * math.log2(L)
+        return 4.0 * u.touched * u.nt
+    if kernel == "fwd_rows":
+        return 4.0 * u.touched * u.nt + 8.0 * u.nf * u.need
     if kernel == "wire_conv":
-        return 8.0 * kw * nfreq * nw
+        return 8.0 * u.nf * (u.need + u.live) + 8.0 * u.nf * u.kw
+    if kernel == "inv_rows":
+        return 8.0 * u.nf * u.live + 4.0 * u.nw * u.nt
     return 0.0
+
+
+def algorithmic_flops(kernel: str, u: UnitSpec) -> float:
+    """FP32 flops a kernel's step needs by the usual count, per launch on one
+    unit: 5 L log2 L per complex L-point FFT (two real rows per transform)
+    over the rows transformed, 8 per complex multiply-add of the wire-axis
+    sum over the live rows."""
+    import math
+    if kernel == "fwd_rows":
+        return (u.touched + 1) // 2 * 5.0 * u.L * math.log2(u.L)
+    if kernel == "inv_rows":
+        return (u.live + 1) // 2 * 5.0 * u.L * math.log2(u.L)
+    if kernel == "wire_conv":
+        return 8.0 * u.kw * u.nf * u.live
+    return 0.0
+
+
+def row_activity(pl, dd, params, marked: bool):
+    """(touched, need, live) row counts of a unit, from its depos on the
+    device, as the library's marking computes them (see UnitSpec)."""
+    import torch
+    nw = pl.nwires
+    if not marked or dd.n == 0:
+        return (nw, nw, nw) if not marked else (0, 0, 0)
+    x = dd.x_mm.double()
+    if dd.sigma_x_mm is not None:
+        sx = dd.sigma_x_mm.double()
+    else:
+        sx = torch.sqrt(2.0 * params.DT_mm2_us * torch.clamp(dd.t_us.double(), min=0.0))
+    pitch = 5.0
+    pt = sx <= 1e-6 * pitch
+    lo_e = torch.where(pt, x, x - 3.0 * sx)
+    hi_e = torch.where(pt, x, x + 3.0 * sx)
+    lo = torch.clamp(torch.floor(lo_e / pitch), -1, nw).long().clamp(min=0) - 1
+    hi = torch.clamp(torch.floor(hi_e / pitch), -1, nw).long().clamp(max=nw - 1) + 1
+    lo = lo.clamp(min=0)
+    hi = hi.clamp(max=nw - 1)
+    ok = lo <= hi
+    diff = torch.zeros(nw + 1, dtype=torch.long, device=x.device)
+    diff.index_add_(0, lo[ok], torch.ones_like(lo[ok]))
+    diff.index_add_(0, hi[ok] + 1, -torch.ones_like(hi[ok]))
+    touched = (torch.cumsum(diff, 0)[:nw] > 0).to(torch.float32)
+    kw, c = int(pl.response.shape[-2]), 10
+    k = torch.ones(1, 1, 2 * kw - 1, device=x.device)
+    need = torch.nn.functional.conv1d(touched.view(1, 1, -1), k, padding=kw - 1).view(-1) > 0
+    # live[w]: a touched row in [w + c - kw + 1, w + c]
+    pad = torch.nn.functional.pad(touched, (kw - 1 - c, c))
+    live = torch.nn.functional.conv1d(pad.view(1, 1, -1), torch.ones(1, 1, kw, device=x.device)).view(-1) > 0
+    return int(touched.sum().item()), int(need.sum().item()), int(live[:nw].sum().item())
 
 
 # ------------------------------------------------------------------ oracle
@@ -481,13 +536,13 @@ def philox_blocks(wiresim, pairs) -> int:
 
 def kernel_table(stats, nsteps, specs, muls_per_step, peak_gbs, traffic):
     """Per-kernel device time per step and its fractions of the HBM, FP32 and
-    INT32-multiply peaks by algorithmic work.  specs: (nwires, nticks,
-    nfreq, L, kw, ndepo) of every unit a step runs."""
+    INT32-multiply peaks by algorithmic work.  specs: the UnitSpec of
+    every unit a step runs."""
     out = {}
     for name, (n, ms) in sorted(stats.items()):
         t = ms / nsteps * 1e-3
-        b = sum(algorithmic_bytes(name, nw, nt, nf, kw, nd) for nw, nt, nf, L, kw, nd in specs)
-        f = sum(algorithmic_flops(name, nw, nt, L, nf, kw) for nw, nt, nf, L, kw, nd in specs)
+        b = sum(algorithmic_bytes(name, u) for u in specs)
+        f = sum(algorithmic_flops(name, u) for u in specs)
         m = muls_per_step if name == "raster_scatter" else 0.0
         out[name] = {"ms_per_step": t * 1e3, "launches_per_step": n / nsteps,
                      "algorithmic_bytes_per_step": b, "hbm_gbs": b / t / 1e9, "hbm_frac": b / t / 1e9 / peak_gbs,
@@ -497,16 +552,20 @@ def kernel_table(stats, nsteps, specs, muls_per_step, peak_gbs, traffic):
 
 
 def roofline_of(table, muls_per_step, peak_gbs, peak_src, traffic, issue):
-    """The roofline of the dominant kernel of a step (largest device time):
-    the raster against the INT32 multiply peak by its Philox multiplies when
-    those bound it, else HBM or FP32 by its algorithmic bytes or flops."""
+    """The roofline of the dominant kernel of a step (largest device time).
+    The binomial raster is bound by instruction issue, not by DRAM (its
+    grid's atomics resolve in L2; ncu puts its DRAM traffic far below its
+    algorithmic bytes), so it is held to the INT32 multiply peak by its
+    Philox multiplies, the one part of its work with a plain hardware
+    ceiling, with its HBM fraction beside it; any other kernel to HBM or
+    FP32 by its algorithmic bytes or flops."""
     dom = max(table, key=lambda k: table[k]["ms_per_step"])
     k = table[dom]
     t = k["ms_per_step"] * 1e-3
     fr = {"hbm": k["hbm_frac"], "alu": k["fp32_frac"], "int": k["int_mul_frac"]}
     base = {"kernel": dom, "traffic": traffic.get(dom), "ncu_issue_active": issue.get(dom),
             "ms_per_step": k["ms_per_step"], "launches_per_step": k["launches_per_step"]}
-    if dom == "raster_scatter" and muls_per_step > 0 and fr["int"] >= max(fr["hbm"], fr["alu"]):
+    if dom == "raster_scatter" and muls_per_step > 0:
         a = muls_per_step / t / 1e12
         base.update({"bound": "alu", "achieved": a, "peak": INT_MUL_PEAK_T, "unit": "T int32-mul/s",
                      "frac": a / INT_MUL_PEAK_T,
@@ -539,21 +598,35 @@ def convolution_report(table, specs, peak_gbs):
         return None
     t = sum(table[k]["ms_per_step"] for k in names) * 1e-3
     pass_bytes = sum(table[k]["algorithmic_bytes_per_step"] for k in names)
-    cells = sum(nw * nt for nw, nt, nf, L, kw, nd in specs)
-    resp = sum(4.0 * kw * 200 for nw, nt, nf, L, kw, nd in specs)
+    cells = sum(u.nw * u.nt for u in specs)
+    touched = sum(u.touched * u.nt for u in specs)
+    resp = sum(4.0 * u.kw * 200 for u in specs)
     b12, bmin = 12.0 * cells, 8.0 * cells + resp
+    bmin_touched = 4.0 * touched + 4.0 * cells + resp
     return {"kernels": names, "ms_per_step": t * 1e3, "cells_per_step": cells,
+            "touched_cell_frac": touched / cells if cells else 0.0,
             "pass_bytes": pass_bytes, "hbm_frac_pass_bytes": pass_bytes / t / 1e9 / peak_gbs,
             "bytes_12_per_cell": b12, "hbm_frac_12_per_cell": b12 / t / 1e9 / peak_gbs,
             "min_bytes": bmin, "hbm_frac_min_bytes": bmin / t / 1e9 / peak_gbs,
-            "note": "pass bytes: each pass reads its input and writes its output once; 12 B per cell: grid in, "
-                    "waveform out and a half spectrum per cell; min bytes: grid in and waveform out (8 B per cell) "
-                    "plus the response"}
+            "min_bytes_touched": bmin_touched, "hbm_frac_min_bytes_touched": bmin_touched / t / 1e9 / peak_gbs,
+            "note": "pass bytes: each pass reads and writes only the rows it has to (touched rows of the grid, "
+                    "spectra a live row reads, live spectra, every waveform row); 12 B per cell: grid in, waveform "
+                    "out and a half spectrum per cell, over every cell; min bytes: grid in and waveform out "
+                    "(8 B per cell) plus the response, over every cell; min bytes touched: the grid's touched "
+                    "rows in (the others are known zero) and every waveform row out"}
 
 
-def unit_specs(planes_by_unit, depos_by_unit):
-    return [(pl.nwires, pl.nticks, pl.info.nfreq, pl.info.fft_len_tick, int(pl.response.shape[-2]), d.n)
-            for pl, d in zip(planes_by_unit, depos_by_unit)]
+def unit_specs(planes_by_unit, depos_by_unit, params=None, marked=True):
+    """UnitSpec of every unit; active rows apply to noise-free linear planes
+    with fixed-shape transforms (the bench's planes), as in the library."""
+    from paper_2203_02479_gb300 import wiresim
+    params = params or wiresim.Params()
+    out = []
+    for pl, d in zip(planes_by_unit, depos_by_unit):
+        t, n, l = row_activity(pl, d, params, marked)
+        out.append(UnitSpec(pl.nwires, pl.nticks, pl.info.nfreq, pl.info.fft_len_tick, int(pl.response.shape[-2]),
+                            d.n, t, n, l))
+    return out
 
 
 # ---------------------------------------------------------------------- legs
@@ -588,7 +661,7 @@ def event_leg(wiresim, dev, stream, flush, steps: int, peak, oracle_check: bool)
     stats = traced(planes[0], lambda: (flush.zero_(), serial.run(stream)), nsteps, 8)
     muls = PHILOX_MULS * float(philox_blocks(wiresim, list(zip(planes, depos))))
     traffic, issue, _ = ncu_figures(w.name)
-    specs = unit_specs(planes, depos)
+    specs = unit_specs(planes, depos, params)
     table = kernel_table(stats, nsteps, specs, muls, peak_gbs, traffic)
     ndp = sum(d.n for d in w.events[0])
     res = {"workload": w.name, "depos_per_plane": w.events[0][0].n, "ms_per_step": ms, "value": ndp / (ms * 1e-3),
@@ -792,7 +865,7 @@ def run_gpu(args):
     units = workload_units(w)
     unit_planes = [planes[p] for _, p in units]
     unit_depos = [events[e][p] for e, p in units]
-    specs = unit_specs(unit_planes, unit_depos)
+    specs = unit_specs(unit_planes, unit_depos, params)
     ndepo_planes = sum(d.n for d in unit_depos)
 
     # the step: one ws_simulate_batch over every unit, wave size from the

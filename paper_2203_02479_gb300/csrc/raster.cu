@@ -130,8 +130,10 @@ __device__ __forceinline__ int normal_pair(uint4 x, int N, const RasterArgs& a) 
 
 // The same search on a table: row N (N = 1 .. kExactCap, at offset
 // N (N - 1) / 2) holds F_0 .. F_{N-1} built by invert_binomial's operations
-// for one (r, 1 - s), so the first k with u < F_k is a binary search with the
-// same result.
+// for one (r, 1 - s).  F is nondecreasing, so the first k with u < F_k is
+// the number of entries F_j <= u: a branch-free binary search of fixed
+// length (steps 64, 32, ..., 1 cover rows of up to kExactCap = 64 entries)
+// keeps the lanes of a warp together whatever their N.
 __device__ void fill_cdf(float* cdf, const float* recip, const RasterArgs& a, int rows) {
     for (int N = threadIdx.x + 1; N <= rows; N += blockDim.x) {
         float f = 1.0f, base = a.inv_base;
@@ -156,15 +158,11 @@ __device__ void fill_cdf(float* cdf, const float* recip, const RasterArgs& a, in
 __device__ __forceinline__ int invert_binomial_table(int N, uint32_t x0, const RasterArgs& a, const float* cdf) {
     const float u = __fmul_rn(__uint2float_rn(x0 >> 8), 5.9604644775390625e-8f);
     const float* row = cdf + N * (N - 1) / 2;
-    int k = 0, len = N;
-    while (len > 0) {
-        const int half = len >> 1;
-        if (u < row[k + half]) {
-            len = half;
-        } else {
-            k += half + 1;
-            len -= half + 1;
-        }
+    int k = 0;
+#pragma unroll
+    for (int step = 64; step >= 1; step >>= 1) {
+        const int j = k + step;
+        if (j <= N && !(u < row[j - 1])) k = j;
     }
     return a.inv_flip ? N - k : k;
 }

@@ -71,15 +71,34 @@ def test_algorithmic_bytes_of_the_three_plane_step():
     wires), against the hand count: the forward reads a 4 B cell and writes
     an 8 B frequency per row, the wire convolution reads and writes the
     spectra and reads each plane's 21-row response spectrum, the inverse
-    the reverse of the forward."""
+    the reverse of the forward.  With every row active (the dense count):"""
     import bench
     rows, nt, nf, kw = 2560, 6000, 3126, 21
-    tot = {k: sum(bench.algorithmic_bytes(k, nw, nt, nf, kw, 100_000) for nw in (800, 800, 960))
-           for k in ("fwd_rows", "wire_conv", "inv_rows", "memset_grid", "raster_scatter")}
+    units = [bench.UnitSpec(nw, nt, nf, 6250, kw, 100_000) for nw in (800, 800, 960)]
+    tot = {k: sum(bench.algorithmic_bytes(k, u) for u in units)
+           for k in ("fwd_rows", "wire_conv", "inv_rows", "memset_grid", "raster_scatter", "mark_rows")}
     assert tot["fwd_rows"] == rows * (4 * nt + 8 * nf)
     assert tot["inv_rows"] == rows * (8 * nf + 4 * nt)
     assert tot["wire_conv"] == rows * 16 * nf + 3 * 8 * nf * kw
     assert tot["memset_grid"] == rows * nt * 4
     assert tot["raster_scatter"] == 3 * 12 * 100_000 + rows * nt * 4
+    assert tot["mark_rows"] == 3 * 8 * 100_000
     # the convolution's pass bytes as the benchmark line reports them
     assert tot["fwd_rows"] + tot["wire_conv"] + tot["inv_rows"] == 380_537_424
+
+
+def test_algorithmic_bytes_with_active_rows():
+    """With active rows each stage counts only the rows it touches: the grid
+    clear and the forward's input the touched rows, the forward's output the
+    rows a live row reads, the wire convolution those and the live rows, the
+    inverse the live spectra in and every waveform row out."""
+    import bench
+    nt, nf, kw = 6000, 3126, 21
+    u = bench.UnitSpec(960, nt, nf, 6250, kw, 50_000, touched=300, need=340, live=320)
+    assert bench.algorithmic_bytes("memset_grid", u) == 4 * 300 * nt
+    assert bench.algorithmic_bytes("fwd_rows", u) == 4 * 300 * nt + 8 * nf * 340
+    assert bench.algorithmic_bytes("wire_conv", u) == 8 * nf * (340 + 320) + 8 * nf * kw
+    assert bench.algorithmic_bytes("inv_rows", u) == 8 * nf * 320 + 4 * 960 * nt
+    assert bench.algorithmic_bytes("raster_scatter", u) == 12 * 50_000 + 4 * 300 * nt
+    dense = bench.UnitSpec(960, nt, nf, 6250, kw, 50_000)
+    assert dense.touched == dense.need == dense.live == 960
