@@ -84,8 +84,22 @@ def kernel_source_hash() -> str:
 # for the kernel sources whose hash is given (see profiles/); published as
 # null once the sources change.
 NCU = {
-    "source_hash": None,
-    "workloads": {},
+    "source_hash": "ba432438c4ec53e0",
+    "workloads": {
+        "three_planes_800_800_960x6000": {
+            "traffic": {"raster_scatter": 8.36e6, "fwd_rows": 47.63e6, "wire_conv": 62.22e6, "inv_rows": 55.70e6,
+                        "mark_rows": 2.41e6, "memset_grid": 0.16e6},
+            "issue_active": {"raster_scatter": 0.698, "fwd_rows": 0.638, "wire_conv": 0.600, "inv_rows": 0.600},
+            "note": "ncu --set full, one launch per kernel over the three planes (wire convolution kernel 9); "
+                    "cold-cache DRAM bytes; profiles/kernels_three_planes.md",
+        },
+        "batched_64ev_x3planes": {
+            "traffic": {}, "issue_active": {},
+            "note": "no DRAM-counter capture of this step (about 5 GB on the device, above the capture size the "
+                    "profiling rules allow); its launch list is profiles/launches_batched_64ev.md and the "
+                    "three-plane event's counters profiles/kernels_three_planes.md",
+        },
+    },
 }
 
 
@@ -330,17 +344,18 @@ def oracle_unit(w, e: int, p: int):
 
 
 def sample_order(w, seed: int = 1002):
-    """The workload's units in a seeded random order (a bounded sample taken
-    from its front mixes small and large events as the workload does)."""
-    units = workload_units(w)
-    order = np.random.Generator(np.random.PCG64(seed)).permutation(len(units))
-    return [units[i] for i in order]
+    """The workload's units event by event, the events in a seeded random
+    order (a bounded sample taken from its front holds whole events and
+    mixes small and large ones as the workload does)."""
+    order = np.random.Generator(np.random.PCG64(seed)).permutation(len(w.events))
+    return [(int(e), p) for e in order for p in range(len(w.planes))]
 
 
 def oracle_units(w, units, threads: int, budget_s: float, on_done=None):
     """Run the oracle over ``units`` on ``threads`` host threads (the C loops
-    and numpy's FFT release the GIL) until ``budget_s`` is spent: units not
-    started by then are skipped, but each thread runs at least one.
+    and numpy's FFT release the GIL) until ``budget_s`` is spent: events not
+    started by then are skipped (units come event by event, so whole events
+    run), but each thread runs at least one unit.
     Returns (depo-planes done, wall seconds to the last finish, units done);
     ``on_done(unit, waveform)`` sees every finished waveform."""
     t0 = time.perf_counter()
@@ -349,7 +364,10 @@ def oracle_units(w, units, threads: int, budget_s: float, on_done=None):
 
     def work(u):
         with lock:
-            if st["started"] >= threads and time.perf_counter() - t0 > budget_s:
+            # past the budget, start no new event (an event's planes all run)
+            if st["started"] >= threads and u[1] == 0 and time.perf_counter() - t0 > budget_s:
+                st["closed"] = True
+            if st.get("closed"):
                 return
             st["started"] += 1
         M = oracle_unit(w, *u)
@@ -417,11 +435,11 @@ def cpu_baselines(w, budget_1t: float, budget_all: float, gpu_outs=None):
     dpa, sa, na = oracle_units(w, units, cores, budget_all, keep)
     total = len(units)
     one = {"value": dp1 / s1, "unit": UNIT, "cores": 1, "kind": "oracle",
-           "sample": f"{n1} of the workload's {total} (event, plane) units in a seeded random order "
-                     f"({dp1} depo-planes), FP64, one thread"}
+           "sample": f"{n1} of the workload's {total} (event, plane) units, whole events in a seeded random "
+                     f"order ({dp1} depo-planes), FP64, one thread"}
     allc = {"value": dpa / sa, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"{na} of the workload's {total} (event, plane) units in a seeded random order "
-                      f"({dpa} depo-planes), FP64, a thread per host core", "one_thread": one}
+            "sample": f"{na} of the workload's {total} (event, plane) units, whole events in a seeded random "
+                      f"order ({dpa} depo-planes), FP64, a thread per host core", "one_thread": one}
     return allc, errs
 
 

@@ -28,9 +28,13 @@ def test_oracle_runs_and_error_report():
     w = _tiny_workload()
     units = bench.sample_order(w)
     assert sorted(units) == [(0, 0), (0, 1), (1, 0), (1, 1)]
+    # event by event: each event's planes in a row
+    assert [p for _, p in units] == [0, 1, 0, 1] and units[0][0] == units[1][0]
     seen = {}
+    # a spent budget still runs the first event whole
     dp, secs, n = bench.oracle_units(w, units, 1, 0.0, lambda u, M: seen.__setitem__(u, M))
-    assert n == 1 and dp == w.events[units[0][0]][units[0][1]].n and list(seen) == units[:1]
+    e0 = units[0][0]
+    assert n == 2 and dp == sum(d.n for d in w.events[e0]) and list(seen) == units[:2]
     seen.clear()
     dp, secs, n = bench.oracle_units(w, units, 3, 60.0, lambda u, M: seen.__setitem__(u, M))
     assert n == 4 and dp == 150 + 120 + 90 + 60 and sorted(seen) == sorted(units)
