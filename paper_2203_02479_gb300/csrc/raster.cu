@@ -695,13 +695,15 @@ raster_small_kernel(const __grid_constant__ RasterUnits U, ws_patches pt, long l
                     }
                 }
                 __syncwarp();
+                // the two samplers in passes of their own: a pass never
+                // runs both (a pass straddling the two kinds would)
+                for (int it = lane; it < nn; it += 32)
+                    emit<P>(a, grid, (int64_t)s_eidx[wib][it], (W)normal_word<P>(s_ew[wib][it], (int)s_en[wib][it], a));
                 const int ntot = nn + ne;
-                for (int it = lane; it < ntot; it += 32) {
+                for (int it = nn + lane; it < ntot; it += 32) {
                     const int n = (int)s_en[wib][it];
                     const uint32_t xw = s_ew[wib][it];
-                    const int c = it < nn ? normal_word<P>(xw, n, a)
-                                          : (cdf ? invert_binomial_table(n, xw, a, cdf)
-                                                 : invert_binomial(n, xw, a, s_recip));
+                    const int c = cdf ? invert_binomial_table(n, xw, a, cdf) : invert_binomial(n, xw, a, s_recip);
                     emit<P>(a, grid, (int64_t)s_eidx[wib][it], (W)c);
                 }
                 __syncwarp();
