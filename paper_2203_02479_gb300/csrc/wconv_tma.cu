@@ -247,6 +247,10 @@ wire_conv_ring_kernel(const __grid_constant__ TmaConvUnits U, int nfreq, int64_t
         tile_of(t, u, k0, wb, nwb);
         const int run = min(t_end - t, nwb - wb);   // tiles in this run
         int n = run;
+        // live tiles of the (trimmed) run with marks, bit i for tile i;
+        // per_tile: runs over 64 tiles test each tile on its own
+        unsigned long long tiles_live = ~0ull;
+        bool per_tile = false;
         // active rows: trim the run to its first .. last live tile (a tile is
         // live if a marked row lies in [w0 + c - K_w + 1, w0 + B - 1 + c]),
         // so the chunks of dead tiles at either end are never fetched
@@ -277,6 +281,9 @@ wire_conv_ring_kernel(const __grid_constant__ TmaConvUnits U, int nfreq, int64_t
                 const int last = 63 - __clzll((long long)live);
                 wb += first;
                 n = last - first + 1;
+                tiles_live = live >> first;
+            } else {
+                per_tile = true;
             }
         }
         const int ybase = wb * B + center - (K - 1);
@@ -314,9 +321,12 @@ wire_conv_ring_kernel(const __grid_constant__ TmaConvUnits U, int nfreq, int64_t
             const float2* col2 = slot_buf(s2) + threadIdx.x;
             const int w0 = (wb + i) * B;
             // active rows: skip the sums of a tile none of whose output rows
-            // is live (its chunks still stream through the ring)
-            const bool live_tile = !U.rows[u] || cta_any_marked(U.rows[u], read_epoch(U.epoch),
-                                                                w0 + center - kw + 1, w0 + B - 1 + center, nwires);
+            // is live (its chunks still stream through the ring), from the
+            // run's bitmask (no loads or barrier per tile)
+            const bool live_tile = !U.rows[u] ? true
+                                   : per_tile ? cta_any_marked(U.rows[u], read_epoch(U.epoch), w0 + center - kw + 1,
+                                                               w0 + B - 1 + center, nwires)
+                                              : ((tiles_live >> i) & 1ull) != 0ull;   // i < 64 here
             float k1[B], k2[B], k3[B];
             float2 acc[B];
 #pragma unroll
