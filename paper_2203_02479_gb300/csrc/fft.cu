@@ -756,12 +756,12 @@ fwd_rows_shape_kernel(FftPlan plan, const float2* __restrict__ tw, const __grid_
     // is not read); a pair with no marked row has zero spectra, written only
     // if a live row's wire convolution may read them
     bool use_a = true, use_b = has_b;
-    if (const mark_t* marks = U.rows[u]) {
-        const mark_t cur = read_epoch(U.epoch);
-        use_a = marks[r0] == cur;
-        use_b = has_b && marks[r0 + 1] == cur;
+    if (const uint32_t* cls = U.rows[u]) {
+        const uint32_t ca = cls[r0], cb = has_b ? cls[r0 + 1] : 0u;
+        use_a = (ca & ROW_MARKED) != 0u;
+        use_b = (cb & ROW_MARKED) != 0u;
         if (!use_a && !use_b) {
-            if (cta_any_marked(marks, cur, r0 + U.win_lo, (has_b ? r0 + 1 : r0) + U.win_hi, U.nrows[u])) {
+            if ((ca | cb) & ROW_NEEDED) {
                 for (int k = threadIdx.x; k < nfreq; k += SH::threads) {
                     oa[k] = make_float2(0.f, 0.f);
                     if (has_b) ob[k] = make_float2(0.f, 0.f);
@@ -832,10 +832,9 @@ inv_rows_shape_kernel(FftPlan plan, const float2* __restrict__ tw, const __grid_
     // is zero (its spectrum, possibly never written, is not read); a pair of
     // such rows is stored as zeros without a transform
     bool live_a = true, live_b = has_b;
-    if (const mark_t* marks = U.rows[u]) {
-        const mark_t cur = read_epoch(U.epoch);
-        live_a = cta_any_marked(marks, cur, r0 + U.win_lo, r0 + U.win_hi, U.nrows[u]);
-        live_b = has_b && cta_any_marked(marks, cur, r0 + 1 + U.win_lo, r0 + 1 + U.win_hi, U.nrows[u]);
+    if (const uint32_t* cls = U.rows[u]) {
+        live_a = (cls[r0] & ROW_LIVE) != 0u;
+        live_b = has_b && (cls[r0 + 1] & ROW_LIVE) != 0u;
         if (!live_a && !live_b) {
             for (int n = threadIdx.x; n < nst; n += SH::threads) {
                 oa[n] = 0.f;
@@ -1181,9 +1180,6 @@ static RowUnits row_units(const RowBatch& rb, bool* aligned16) {
     U.n = rb.n;
     U.prefix[0] = 0;
     U.status = rb.status;
-    U.epoch = rb.epoch;
-    U.win_lo = rb.win_lo;
-    U.win_hi = rb.win_hi;
     *aligned16 = true;
     for (int i = 0; i < rb.n; ++i) {
         U.in[i] = rb.in[i];

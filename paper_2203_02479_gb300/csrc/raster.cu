@@ -1360,6 +1360,7 @@ static RasterUnits raster_units(const RasterBatch& rb) {
         U.a[i] = rb.a[i];
         U.grid[i] = rb.grid[i];
         U.rows[i] = nullptr;
+        U.cls[i] = nullptr;
         U.gprefix[i + 1] = U.gprefix[i] + (rb.a[i].n + kSmallGroup - 1) / kSmallGroup;
         U.dprefix[i + 1] = U.dprefix[i] + rb.a[i].n;
     }
@@ -1537,29 +1538,48 @@ mark_rows_kernel(const __grid_constant__ RasterUnits U, const mark_t* base_epoch
 
 // Active rows, step 2: clear the marked rows of unit u's grid (and of its
 // compensated low-part grid), a warp per row, or the whole grid of a unit
-// without marks.  Block (0, 0) hands the epoch on to the next call's
+// without marks; with marks, also write every row's class (ROW_MARKED,
+// ROW_NEEDED: a marked row within kw - 1 wires, ROW_LIVE: a marked row in
+// [w + c - kw + 1, w + c]) from the marks of rows w - (kw - 1) .. w + 32 +
+// 31 - (kw - 1), two per lane (kw <= 21, so the widest window, 2 kw - 1
+// rows, fits in 64).  Block (0, 0) hands the epoch on to the next call's
 // marking kernel (`base`; the marking kernel is not running).
 struct ZeroUnit {
     float* grid;
     float* lo;
     const mark_t* rows;   // null: every row
+    uint32_t* cls;
     int nwires, nticks;
 };
 
 __global__ void __launch_bounds__(256)
-zero_marked_rows_kernel(const __grid_constant__ RasterUnits U, const mark_t* epoch, mark_t* base) {
+zero_marked_rows_kernel(const __grid_constant__ RasterUnits U, const mark_t* epoch, mark_t* base, int kw,
+                        int center) {
     __shared__ ZeroUnit zu;
     const mark_t cur = read_epoch(epoch);
     if (threadIdx.x == 0) {
         const int u = blockIdx.y;
-        zu = ZeroUnit{U.grid[u], U.a[u].lo, U.rows[u], U.a[u].nwires, U.a[u].nticks};
+        zu = ZeroUnit{U.grid[u], U.a[u].lo, U.rows[u], U.cls[u], U.a[u].nwires, U.a[u].nticks};
     }
     __syncthreads();
     if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0 && base) *base = cur;
     const int lane = threadIdx.x & 31;
-    const int nt = zu.nticks;
-    for (int w = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); w < zu.nwires; w += gridDim.x * (blockDim.x >> 5)) {
-        if (zu.rows && zu.rows[w] != cur) continue;
+    const int nt = zu.nticks, nw = zu.nwires;
+    for (int w = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); w < nw; w += gridDim.x * (blockDim.x >> 5)) {
+        bool marked = true;
+        if (zu.rows) {
+            const int r0 = w - (kw - 1) + lane, r1 = r0 + 32;
+            const bool m0 = r0 >= 0 && r0 < nw && zu.rows[r0] == cur;
+            const bool m1 = r1 >= 0 && r1 < nw && zu.rows[r1] == cur;
+            const unsigned long long mm =
+                (unsigned long long)__ballot_sync(0xffffffffu, m0) | ((unsigned long long)__ballot_sync(0xffffffffu, m1) << 32);
+            marked = (mm >> (kw - 1)) & 1ull;
+            const bool needed = (mm & ((2ull << (2 * (kw - 1))) - 1ull)) != 0ull;
+            const bool live = ((mm >> center) & ((1ull << kw) - 1ull)) != 0ull;
+            if (lane == 0)
+                zu.cls[w] = (marked ? ROW_MARKED : 0u) | (needed ? ROW_NEEDED : 0u) | (live ? ROW_LIVE : 0u);
+        }
+        if (!marked) continue;
         for (int g = 0; g < 2; ++g) {
             float* row = g == 0 ? zu.grid : zu.lo;
             if (!row) continue;
@@ -1590,14 +1610,17 @@ cudaError_t launch_mark_rows(const RasterBatch& rb, const RowMarks& m, cudaStrea
 
 cudaError_t launch_zero_marked_rows(const RasterBatch& rb, const RowMarks& m, cudaStream_t s) {
     if (rb.n <= 0) return cudaSuccess;
+    if (m.kw < 1 || m.kw > 32 || m.center < 0 || m.center >= m.kw) return cudaErrorInvalidValue;
     RasterUnits U = raster_units(rb);
     int maxw = 1;
     for (int i = 0; i < rb.n; ++i) {
         U.rows[i] = m.rows[i];
+        U.cls[i] = m.rows[i] ? m.cls[i] : nullptr;
+        if (m.rows[i] && !m.cls[i]) return cudaErrorInvalidValue;
         maxw = std::max(maxw, rb.a[i].nwires);
     }
     const int bx = (maxw + 7) / 8;   // a warp per row
-    zero_marked_rows_kernel<<<dim3(bx, rb.n), 256, 0, s>>>(U, m.epoch, m.base);
+    zero_marked_rows_kernel<<<dim3(bx, rb.n), 256, 0, s>>>(U, m.epoch, m.base, m.kw, m.center);
     return cudaGetLastError();
 }
 

@@ -128,7 +128,7 @@ struct Layout {
     ws::FftPlan plan;
     int nfreq, fstride;
     size_t off_status, off_tw, off_rt, off_x, off_y, off_scan, off_large, off_radj, off_racc, off_grid2, off_noise,
-        off_rows;
+        off_rows, off_cls;
     size_t off_fine;
     int impacts;
     size_t off_tw64, off_rt64, off_x64, off_y64, off_g64, total;
@@ -177,6 +177,7 @@ ws_status plan_layout(const ws_plane_desc* d, Layout* lay) {
     lay->off_grid2 = o; o = align256(o + sizeof(float) * (size_t)d->nwires * d->nticks);
     lay->off_noise = o; o = align256(o + 2 * sizeof(float) * (size_t)lay->fstride);
     lay->off_rows = o; o = align256(o + sizeof(ws::mark_t) * (size_t)d->nwires);
+    lay->off_cls = o; o = align256(o + sizeof(uint32_t) * (size_t)d->nwires);
     lay->off_fine = 0;
     if (I > 1) { lay->off_fine = o; o = align256(o + sizeof(float) * (size_t)I * d->nwires * d->nticks); }
     lay->off_tw64 = lay->off_rt64 = lay->off_x64 = lay->off_y64 = lay->off_g64 = 0;
@@ -304,16 +305,6 @@ bool marks_apply(const ws_plane* pl) {
            ws::row_fft_fixed_shape(pl->plan);
 }
 
-// Mark windows of the row transforms (see ws::RowMarks): the forward writes
-// the spectra of rows within K_w - 1 wires of a marked row; the inverse
-// transforms rows whose window [w + c - K_w + 1, w + c] holds a marked row.
-void mark_windows(const ws_plane_desc& d, ws::RowBatch* fwd, ws::RowBatch* inv) {
-    fwd->win_lo = -(d.resp_nwires - 1);
-    fwd->win_hi = d.resp_nwires - 1;
-    inv->win_lo = d.resp_wire_center - d.resp_nwires + 1;
-    inv->win_hi = d.resp_wire_center;
-}
-
 // ws_simulate's FP32 / compensated path with active rows: mark, clear the
 // marked rows, raster, then the three transform stages over marked / live
 // rows only (the same result as clearing and transforming every row).
@@ -326,8 +317,11 @@ ws_status simulate_marked(ws_plane* pl, ws::RasterArgs a, float* out, cudaStream
     rb.grid[0] = out;
     ws::RowMarks m;
     m.rows[0] = pl->rows;
+    m.cls[0] = pl->row_cls;
     m.epoch = pl->rows_epoch;
     m.base = pl->rows_base;
+    m.kw = d.resp_nwires;
+    m.center = d.resp_wire_center;
     WS_LAUNCH(pl, K_MARK, s, ws::launch_mark_rows(rb, m, s));
     WS_LAUNCH(pl, K_MEMSET, s, ws::launch_zero_marked_rows(rb, m, s));
     WS_LAUNCH(pl, K_RASTER_SCATTER, s, ws::launch_raster_scatter(a, out, pl->large, s));
@@ -342,9 +336,7 @@ ws_status simulate_marked(ws_plane* pl, ws::RasterArgs a, float* out, cudaStream
     ib.out[0] = out;
     ib.nrows[0] = d.nwires;
     fb.status = ib.status = pl->status;
-    fb.rows[0] = ib.rows[0] = pl->rows;
-    fb.epoch = ib.epoch = pl->rows_epoch;
-    mark_windows(d, &fb, &ib);
+    fb.rows[0] = ib.rows[0] = pl->row_cls;
     ws::ConvBatch cb;
     cb.n = 1;
     cb.X[0] = pl->X;
@@ -483,6 +475,7 @@ ws_status ws_plane_create(const ws_plane_desc* desc, const float* response_dev, 
     pl->rows = (ws::mark_t*)(base + lay.off_rows);
     pl->rows_epoch = (ws::mark_t*)(base + lay.off_status + 24);   // zeroed with the status region below
     pl->rows_base = (ws::mark_t*)(base + lay.off_status + 32);
+    pl->row_cls = (uint32_t*)(base + lay.off_cls);
     cudaStream_t s = (cudaStream_t)stream;
     cudaError_t e = cudaMemsetAsync(base + lay.off_status, 0, 256, s);
     // marks start below every epoch (the first call marks with 1)
@@ -849,7 +842,7 @@ namespace {
 constexpr int kBatchSlots = 3;
 
 struct BatchLayout {
-    size_t off_counters, off_list, off_spec, spec_bytes, off_rows, rows_bytes, slot_bytes, total;
+    size_t off_counters, off_list, off_spec, spec_bytes, off_rows, rows_bytes, off_cls, cls_bytes, slot_bytes, total;
 };
 // Within a slot's 256-byte counter block (cleared at the start of every call):
 // the large-patch list's count and done words, and the active-row epochs
@@ -886,6 +879,8 @@ ws_status batch_layout(ws_plane* const* planes, int nplanes, int units_per_wave,
     lay->off_spec = o; o += 2 * (size_t)units_per_wave * lay->spec_bytes;
     lay->rows_bytes = align256(sizeof(ws::mark_t) * (size_t)maxw);
     lay->off_rows = o; o += (size_t)units_per_wave * lay->rows_bytes;
+    lay->cls_bytes = align256(sizeof(uint32_t) * (size_t)maxw);
+    lay->off_cls = o; o += (size_t)units_per_wave * lay->cls_bytes;
     lay->slot_bytes = o;
     lay->total = kBatchSlots * o;
     return WS_OK;
@@ -1164,7 +1159,9 @@ ws_status batch_waves(ws_plane* const* planes, int nplanes, const ws_depos* depo
             float2* Y = (float2*)(base + lay.off_spec + (size_t)(2 * j + 1) * lay.spec_bytes);
             m.rows[j] = (marked && marks_apply(pl)) ? (ws::mark_t*)(base + lay.off_rows + (size_t)j * lay.rows_bytes)
                                                     : nullptr;
-            fb.rows[j] = ib.rows[j] = cb.rows[j] = m.rows[j];
+            m.cls[j] = m.rows[j] ? (uint32_t*)(base + lay.off_cls + (size_t)j * lay.cls_bytes) : nullptr;
+            fb.rows[j] = ib.rows[j] = m.cls[j];
+            cb.rows[j] = m.rows[j];
             rb.a[j] = raster_args(pl, &depos[u], &pe);
             rb.grid[j] = out_dev[u];
             counts[j] = (int64_t)pl->desc.nwires * pl->desc.nticks;
@@ -1186,8 +1183,9 @@ ws_status batch_waves(ws_plane* const* planes, int nplanes, const ws_depos* depo
             else nb.noise[j] = ws::NoiseUnit{};
         }
         if (marked) {
-            fb.epoch = ib.epoch = cb.epoch = m.epoch;
-            mark_windows(d0, &fb, &ib);
+            cb.epoch = m.epoch;
+            m.kw = d0.resp_nwires;
+            m.center = d0.resp_wire_center;
             WS_LAUNCH(p0, K_MARK, s, ws::launch_mark_rows(rb, m, s));
             WS_LAUNCH(p0, K_MEMSET, s, ws::launch_zero_marked_rows(rb, m, s));
         } else {

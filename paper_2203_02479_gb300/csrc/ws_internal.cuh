@@ -144,6 +144,8 @@ struct NoiseUnit {
 // across CUDA graph replays, and every later stage reads `epoch` once at its
 // start.  An unmarked row of S is zero, so the stages after the raster skip
 // it exactly:
+// The clearing kernel also classifies every row once per call (RowClass
+// bits), so the row transforms decide per row pair from two words:
 //   forward      transforms row pairs with a marked row (an unmarked row of
 //                such a pair reads as zero); writes zero spectra for rows
 //                within K_w - 1 wires of a marked row (the wire convolution
@@ -159,11 +161,19 @@ struct NoiseUnit {
 using mark_t = unsigned long long;
 struct RowMarks {
     mark_t* rows[kMaxUnits];      // per unit, nwires entries; null: every row active
+    uint32_t* cls[kMaxUnits];     // per unit, nwires row classes (written by the clearing kernel)
     mark_t* epoch;                // the call's epoch (written by the marking kernel)
     mark_t* base;                 // the previous call's epoch (copied from `epoch` by the clearing kernel)
+    int kw = 0, center = 0;       // response wires and centre row (the classes' windows)
 };
 
 __device__ __forceinline__ mark_t read_epoch(const mark_t* e) { return *(const volatile mark_t*)e; }
+
+// Row classes (one word per wire row, written for every row by the clearing
+// kernel): the row is marked; a marked row lies within K_w - 1 wires (its
+// spectrum may be read); a marked row lies in its wire-convolution window
+// [w + c - K_w + 1, w + c] (its output is live).
+enum : uint32_t { ROW_MARKED = 1u, ROW_NEEDED = 2u, ROW_LIVE = 4u };
 
 // Whether any row of [lo, hi] (clipped to [0, n)) is marked; every thread of
 // the CTA calls it (one barrier).
@@ -184,13 +194,9 @@ struct RowBatch {          // row transforms: unit i has nrows[i] rows in[i] -> 
     int nrows[kMaxUnits];
     uint32_t* status = nullptr;   // device status word: lets the fixed-shape kernels fetch rows by
                                   // bulk copies (a copy that never lands is reported there)
-    // active rows (fixed-shape FP32 kernels only): per unit marks (null: all
-    // rows), the epoch word, and the window of marks that decides a row:
-    // forward, [r - (K_w - 1), r + K_w - 1] (its spectrum is needed);
-    // inverse, [r + c - K_w + 1, r + c] (it is live)
-    const mark_t* rows[kMaxUnits] = {};
-    const mark_t* epoch = nullptr;
-    int win_lo = 0, win_hi = 0;
+    // active rows (fixed-shape FP32 kernels only): per unit the row classes
+    // of the call (null: every row marked, needed and live)
+    const uint32_t* rows[kMaxUnits] = {};
 };
 struct NoiseBatch {        // noise added to the spectra Y[i] (nwires[i] rows) of each unit
     int n = 0;
@@ -219,9 +225,7 @@ struct RowUnits {
     void* out[kMaxUnits];
     int nrows[kMaxUnits];
     uint32_t* status;
-    const mark_t* rows[kMaxUnits];
-    const mark_t* epoch;
-    int win_lo, win_hi;
+    const uint32_t* rows[kMaxUnits];   // row classes, or null
 };
 struct NoiseUnits {
     int n;
@@ -343,6 +347,7 @@ struct RasterUnits {
     RasterArgs a[kMaxUnits];
     float* grid[kMaxUnits];
     mark_t* rows[kMaxUnits];            // active-row marks (mark / clear kernels), or null
+    uint32_t* cls[kMaxUnits];           // row classes (clear kernel), with marks
 };
 struct ZeroSizes {
     long long count[kMaxUnits];
@@ -412,4 +417,5 @@ struct ws_plane {
     ws::mark_t* rows;        // nwires active-row marks (ws_simulate)
     ws::mark_t* rows_epoch;  // their epoch words (ws::RowMarks epoch and base, status region)
     ws::mark_t* rows_base;
+    uint32_t* row_cls;       // nwires row classes (ws_simulate)
 };
