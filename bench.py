@@ -634,6 +634,16 @@ def convolution_report(table, specs, peak_gbs):
                     "rows in (the others are known zero) and every waveform row out"}
 
 
+def raster_rate(table, ndepo_planes: int):
+    """Depo-planes per second through diffusion, raster, fluctuation and
+    scatter-add alone (the marking, grid-clear and raster kernels), from the
+    one-wave-at-a-time trace."""
+    ms = sum(table[k]["ms_per_step"] for k in ("mark_rows", "memset_grid", "raster_scatter") if k in table)
+    return {"value": ndepo_planes / (ms * 1e-3) if ms > 0 else None, "unit": UNIT, "ms_per_step": ms,
+            "note": "depos over the device time of the marking, grid-clear and raster kernels (serial trace); "
+                    "`value` counts the whole path"}
+
+
 def unit_specs(planes_by_unit, depos_by_unit, params=None, marked=True):
     """UnitSpec of every unit; active rows apply to noise-free linear planes
     with fixed-shape transforms (the bench's planes), as in the library."""
@@ -1006,6 +1016,7 @@ def run_gpu(args):
                            "ws_batch_autotune; wave k on stream k % 3), replayed from a CUDA graph",
                    "l2": "flushed between timed steps (512 MiB write); a step's buffers (~5 GB) exceed L2"},
         "planes_per_s": all_planes / (total_ms * 1e-3),
+        "raster_scatter_depos_per_s": raster_rate(table, ndepo_planes),
         "per_plane_path": {"ms_per_step": pp_ms, "value": ndepo_planes / (pp_ms * 1e-3),
                            "batched_speedup": pp_ms / (total_ms / args.steps),
                            "note": "one ws_simulate per (event, plane) unit, same outputs"},
