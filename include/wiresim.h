@@ -206,7 +206,8 @@ typedef struct ws_plane ws_plane;
 
 /* Bytes of device workspace a plane with this description needs (response
  * spectrum, twiddles, two spectra of nwires x (L_t/2+1) complex64, status
- * word, scan scratch, noise spectra; with impacts I > 1 also the fine grid
+ * word, scan scratch, noise spectra, a 64-bit row mark and a row class per
+ * wire for ws_simulate's active rows; with impacts I > 1 also the fine grid
  * of nwires*I x nticks floats and I times the first spectrum and the
  * response spectrum).  Host-only; fails with WS_ERR_UNSUPPORTED_SIZE if the
  * FFT length is not 2/3/5-smooth or exceeds 14336, for FP64 buffers on an
@@ -275,7 +276,14 @@ ws_status ws_convolve(ws_plane* plane, const float* grid_dev, float* out_dev, vo
 /* The whole hot path for one plane and one event: clear out_dev, raster +
  * fluctuate + scatter-add every depo straight into it (no patch buffer),
  * then convolve in place, adding the plane's noise term if one is set
- * (ws_plane_set_noise).  out_dev: nwires x nticks float32. */
+ * (ws_plane_set_noise).  out_dev: nwires x nticks float32, every row
+ * written.  On noise-free linear planes with fixed-shape transforms (L_t
+ * 6250, 6000, 6400, 3200 or 1200) only the wire rows a depo can reach are
+ * cleared and transformed, and waveform rows out of the response's reach
+ * of all of them are written as zeros: the same result as transforming
+ * every row (an untouched row is zero through Eq. 2's linear stages).  A
+ * per-plane epoch in the workspace, advanced on the device, keeps calls
+ * and CUDA graph replays apart; calls on one plane must not overlap. */
 ws_status ws_simulate(ws_plane* plane, const ws_depos* depos, const ws_params* params,
                       float* out_dev, void* stream);
 
@@ -303,9 +311,10 @@ ws_status ws_convolve_noalloc(const ws_plane_desc* desc, const float* response_d
                               const float* grid_dev, float* out_dev, void* stream);
 
 /* Device workspace of ws_simulate_batch: three wave slots, each a
- * large-patch hand-over list and two spectra (max nwires x (L_t/2+1)
- * complex64) per unit of a wave.  units_per_wave: 1 .. 32, or 0 for the
- * largest wave (32 units), which holds every wave size. */
+ * large-patch hand-over list and, per unit of a wave, two spectra (max
+ * nwires x (L_t/2+1) complex64) and a row mark and row class per wire.
+ * units_per_wave: 1 .. 32, or 0 for the largest wave (32 units), which
+ * holds every wave size. */
 ws_status ws_batch_workspace_bytes(ws_plane* const* planes, int nplanes, int units_per_wave,
                                    size_t* bytes);
 
@@ -320,7 +329,9 @@ ws_status ws_batch_workspace_bytes(ws_plane* const* planes, int nplanes, int uni
  * event_id = params->event_id + e.  All planes must share the transform
  * length, tick count and response shape (else WS_ERR_UNSUPPORTED_SIZE).
  * Each plane's noise term (ws_plane_set_noise) is added as in ws_simulate.
- * Results equal ws_simulate unit by unit (up to summation order).  With more
+ * Results equal ws_simulate unit by unit (up to summation order); units of
+ * noise-free planes skip untouched wire rows as ws_simulate does, with the
+ * marks in the workspace slots cleared at the start of every call.  With more
  * than one wave, the waves go round `stream` and up to two more streams
  * owned by the library (per host thread and device): wave k runs on stream
  * k % S, S = min(waves, 3), each with its own workspace slot.  The extra
