@@ -805,8 +805,11 @@ def multinomial_leg(wiresim, dev, stream, flush, steps: int, plain_ms: float):
 def impacts_leg(wiresim, dev, stream, flush, steps: int, impacts: int = 10):
     """The three-plane event on planes whose response depends on the charge's
     position inside the pitch (10 sub-pitch positions, synthetic slices):
-    the raster bins the pitch axis at pitch/10 and the forward transform
-    runs over 10x the rows; one ws_simulate per plane."""
+    the raster bins the pitch axis at pitch/10, the forward transform runs
+    over the marked wires' 10 fine rows each, and the impact wire
+    convolution sums the positions' taps.  Timed as one ws_simulate_batch
+    over the event's three planes (the leg's value) and as one ws_simulate
+    per plane."""
     import torch
     w = make_workload("three_planes", 0)
     kinds = ["bipolar", "bipolar", "unipolar"]
@@ -816,30 +819,32 @@ def impacts_leg(wiresim, dev, stream, flush, steps: int, impacts: int = 10):
     params = wiresim.Params(fluctuate=w.fluctuate, p_survive=w.p_survive, seed=w.seed)
     outs = [torch.empty((sp.nwires, sp.nticks), dtype=torch.float32, device=dev) for sp in w.planes]
 
-    def step():
+    def per_plane():
         for pl, d, o in zip(planes, depos, outs):
             pl.simulate(d, params, out=o, stream=stream)
 
+    batch = wiresim.Batch(planes, [depos], params, units_per_wave=len(planes), device=dev, outs=outs)
+
+    def batched():
+        batch.run(stream)
+
     for _ in range(3):
-        step()
+        per_plane()
+        batched()
     torch.cuda.synchronize(dev)
-    ms = statistics.median(_time_steps(step, steps, stream, flush))
-    kern = {}
-    for pl in planes:
-        pl.trace(16 * steps + 16)
-    for _ in range(steps):
-        flush.zero_()
-        step()
-    torch.cuda.synchronize(dev)
-    for pl in planes:
-        for name, (n, t) in pl.trace_read().items():
-            kern[name] = kern.get(name, 0.0) + t / steps
-        pl.trace(0)
-        pl.close()
+    plane_ms = statistics.median(_time_steps(per_plane, steps, stream, flush))
+    ms = statistics.median(_time_steps(batched, steps, stream, flush))
+    st = traced(planes[0], lambda: (flush.zero_(), batched()), steps, 16)
+    kern = {name: t / steps for name, (n, t) in st.items()}
+    variants = [pl.info.wire_conv_variant for pl in planes]
     ndp = sum(d.n for d in w.events[0])
+    for pl in planes:
+        pl.close()
     return {"workload": w.name + f", {impacts} sub-pitch response positions per plane", "ms_per_step": ms,
             "value": ndp / (ms * 1e-3), "unit": UNIT, "kernels_ms_per_step": kern,
-            "path": "ws_simulate per plane (fine grid of nwires*10 rows, per-impact wire convolution)"}
+            "per_plane_ms_per_step": plane_ms, "impact_wire_blocks": [32 if v == 1 else 16 for v in variants],
+            "path": "ws_simulate_batch over the event's planes (fine grids of nwires*10 rows, active wires, "
+                    "impact wire convolution per plane)"}
 
 
 def adjoint_leg(wiresim, dev, stream, flush, steps: int):

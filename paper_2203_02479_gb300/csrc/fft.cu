@@ -757,7 +757,8 @@ fwd_rows_shape_kernel(FftPlan plan, const float2* __restrict__ tw, const __grid_
     // if a live row's wire convolution may read them
     bool use_a = true, use_b = has_b;
     if (const uint32_t* cls = U.rows[u]) {
-        const uint32_t ca = cls[r0], cb = has_b ? cls[r0 + 1] : 0u;
+        const int dv = U.rdiv[u];
+        const uint32_t ca = cls[r0 / dv], cb = has_b ? cls[(r0 + 1) / dv] : 0u;
         use_a = (ca & ROW_MARKED) != 0u;
         use_b = (cb & ROW_MARKED) != 0u;
         if (!use_a && !use_b) {
@@ -1187,6 +1188,7 @@ static RowUnits row_units(const RowBatch& rb, bool* aligned16) {
         U.out[i] = rb.out[i];
         U.nrows[i] = rb.nrows[i];
         U.rows[i] = rb.rows[i];
+        U.rdiv[i] = rb.rdiv[i] > 1 ? rb.rdiv[i] : 1;
         U.prefix[i + 1] = U.prefix[i] + (rb.nrows[i] + 1) / 2;
         *aligned16 = *aligned16 && ((uintptr_t)rb.in[i] % 16 == 0) && ((uintptr_t)rb.out[i] % 16 == 0);
     }

@@ -1361,6 +1361,7 @@ static RasterUnits raster_units(const RasterBatch& rb) {
         U.grid[i] = rb.grid[i];
         U.rows[i] = nullptr;
         U.cls[i] = nullptr;
+        U.imp[i] = 1;
         U.gprefix[i + 1] = U.gprefix[i] + (rb.a[i].n + kSmallGroup - 1) / kSmallGroup;
         U.dprefix[i + 1] = U.dprefix[i] + rb.a[i].n;
     }
@@ -1473,7 +1474,9 @@ cudaError_t launch_zero_grids(const RasterBatch& rb, const int64_t* counts, cuda
 // Active rows, step 1: every depo marks the wire rows [w0 - 1, w1 + 1] of its
 // clipped pitch-axis range (the raster's own extent, computed the same way,
 // widened by one wire against rounding differences between the two
-// kernels) with the new epoch, base + 1.  Block (x, u) takes unit u's depos
+// kernels) with the new epoch, base + 1.  On an impact plane (pitch axis
+// binned at pitch / I) the range is in fine bins: widened by one fine bin,
+// it marks the wires w0 / I .. w1 / I that hold those bins.  Block (x, u) takes unit u's depos
 // x, x + gridDim.x, ... (256 at a time) with the unit's parameters staged in
 // shared memory.  Depos along a track share rows, and many threads storing
 // to the same few words serialise in L2, so a warp merges its lanes' ranges
@@ -1485,13 +1488,15 @@ struct MarkUnit {
     const float* sig_x;   // null: widths from diffusion
     int64_t n;
     float two_DT, pitch, nsig;
-    int nwires;
+    int nwires;   // bins of the pitch axis (wires x impact positions)
+    int imp;      // bins per marked row
     mark_t* rows;
 };
 
 __device__ __forceinline__ MarkUnit mark_unit(const RasterUnits& U, int u) {
     const RasterArgs& a = U.a[u];
-    return MarkUnit{a.x, a.t, a.sig_t ? a.sig_x : nullptr, a.n, a.two_DT, a.pitch, a.nsig, a.nwires, U.rows[u]};
+    return MarkUnit{a.x, a.t, a.sig_t ? a.sig_x : nullptr, a.n, a.two_DT, a.pitch, a.nsig, a.nwires, U.imp[u],
+                    U.rows[u]};
 }
 
 __global__ void __launch_bounds__(256)
@@ -1521,6 +1526,10 @@ mark_rows_kernel(const __grid_constant__ RasterUnits U, const mark_t* base_epoch
             axis_range<float>(x, sx, mu.pitch, mu.nsig, mu.nwires, &lo, &hi, &point);
             lo = lo - 1 > 0 ? lo - 1 : 0;
             hi = hi + 1 < mu.nwires - 1 ? hi + 1 : mu.nwires - 1;
+            if (mu.imp > 1 && lo <= hi) {
+                lo /= mu.imp;
+                hi /= mu.imp;
+            }
         }
         const bool has = lo <= hi;
         const int mlo = __reduce_min_sync(0xffffffffu, has ? lo : INT_MAX);
@@ -1539,17 +1548,20 @@ mark_rows_kernel(const __grid_constant__ RasterUnits U, const mark_t* base_epoch
 // Active rows, step 2: clear the marked rows of unit u's grid (and of its
 // compensated low-part grid), a warp per row, or the whole grid of a unit
 // without marks; with marks, also write every row's class (ROW_MARKED,
-// ROW_NEEDED: a marked row within kw - 1 wires, ROW_LIVE: a marked row in
-// [w + c - kw + 1, w + c]) from the marks of rows w - (kw - 1) .. w + 32 +
-// 31 - (kw - 1), two per lane (kw <= 21, so the widest window, 2 kw - 1
-// rows, fits in 64).  Block (0, 0) hands the epoch on to the next call's
-// marking kernel (`base`; the marking kernel is not running).
+// ROW_NEEDED: a marked row in [w - kw + 1, w + K - 1], ROW_LIVE: a marked
+// row in [w + c - kw + 1, w + c]) from the marks of rows w - (kw - 1) ..
+// w + 32 + 31 - (kw - 1), two per lane (kw, K <= 21, so the widest window,
+// kw + K - 1 rows, fits in 64).  On an impact plane a marked wire's I fine
+// rows are cleared (a warp each).  Block (0, 0) hands the
+// epoch on to the next call's marking kernel (`base`; the marking kernel is
+// not running).
 struct ZeroUnit {
     float* grid;
     float* lo;
     const mark_t* rows;   // null: every row
     uint32_t* cls;
-    int nwires, nticks;
+    int nwires, nticks;   // marked rows (wires) and ticks per grid row
+    int imp;              // grid rows per marked row (a warp clears one)
 };
 
 __global__ void __launch_bounds__(256)
@@ -1559,13 +1571,17 @@ zero_marked_rows_kernel(const __grid_constant__ RasterUnits U, const mark_t* epo
     const mark_t cur = read_epoch(epoch);
     if (threadIdx.x == 0) {
         const int u = blockIdx.y;
-        zu = ZeroUnit{U.grid[u], U.a[u].lo, U.rows[u], U.cls[u], U.a[u].nwires, U.a[u].nticks};
+        const int imp = U.rows[u] ? U.imp[u] : 1;   // without marks: every fine row on its own
+        zu = ZeroUnit{U.grid[u], U.a[u].lo, U.rows[u], U.cls[u], U.a[u].nwires / imp, U.a[u].nticks, imp};
     }
     __syncthreads();
     if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0 && base) *base = cur;
     const int lane = threadIdx.x & 31;
-    const int nt = zu.nticks, nw = zu.nwires;
-    for (int w = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); w < nw; w += gridDim.x * (blockDim.x >> 5)) {
+    const int nt = zu.nticks, nw = zu.nwires, imp = zu.imp;
+    // item (w, piece): grid row w * imp + piece, cleared if wire w is marked
+    for (int item = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); item < nw * imp;
+         item += gridDim.x * (blockDim.x >> 5)) {
+        const int w = item / imp, piece = item - w * imp;
         bool marked = true;
         if (zu.rows) {
             const int r0 = w - (kw - 1) + lane, r1 = r0 + 32;
@@ -1574,16 +1590,16 @@ zero_marked_rows_kernel(const __grid_constant__ RasterUnits U, const mark_t* epo
             const unsigned long long mm =
                 (unsigned long long)__ballot_sync(0xffffffffu, m0) | ((unsigned long long)__ballot_sync(0xffffffffu, m1) << 32);
             marked = (mm >> (kw - 1)) & 1ull;
-            const bool needed = (mm & ((2ull << (2 * (kw - 1))) - 1ull)) != 0ull;
+            const bool needed = (mm & ((2ull << (kw - 1 + kMaxRespWires - 1)) - 1ull)) != 0ull;
             const bool live = ((mm >> center) & ((1ull << kw) - 1ull)) != 0ull;
-            if (lane == 0)
+            if (lane == 0 && piece == 0)
                 zu.cls[w] = (marked ? ROW_MARKED : 0u) | (needed ? ROW_NEEDED : 0u) | (live ? ROW_LIVE : 0u);
         }
         if (!marked) continue;
         for (int g = 0; g < 2; ++g) {
             float* row = g == 0 ? zu.grid : zu.lo;
             if (!row) continue;
-            row += (int64_t)w * nt;
+            row += (int64_t)item * nt;
             if ((uintptr_t)row % 16 == 0 && nt % 4 == 0) {
                 float4* r4 = reinterpret_cast<float4*>(row);
                 for (int j = lane; j < nt / 4; j += 32) r4[j] = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -1600,6 +1616,8 @@ cudaError_t launch_mark_rows(const RasterBatch& rb, const RowMarks& m, cudaStrea
     int64_t maxn = 0;
     for (int i = 0; i < rb.n; ++i) {
         U.rows[i] = m.rows[i];
+        U.imp[i] = m.impacts[i] > 1 ? m.impacts[i] : 1;
+        if (rb.a[i].nwires % U.imp[i] != 0) return cudaErrorInvalidValue;
         maxn = std::max<int64_t>(maxn, rb.a[i].n);
     }
     // at least one block per unit (block (0, 0) stores the epoch)
@@ -1616,8 +1634,10 @@ cudaError_t launch_zero_marked_rows(const RasterBatch& rb, const RowMarks& m, cu
     for (int i = 0; i < rb.n; ++i) {
         U.rows[i] = m.rows[i];
         U.cls[i] = m.rows[i] ? m.cls[i] : nullptr;
+        U.imp[i] = m.impacts[i] > 1 ? m.impacts[i] : 1;
         if (m.rows[i] && !m.cls[i]) return cudaErrorInvalidValue;
-        maxw = std::max(maxw, rb.a[i].nwires);
+        if (rb.a[i].nwires % U.imp[i] != 0) return cudaErrorInvalidValue;
+        maxw = std::max(maxw, rb.a[i].nwires);   // grid rows (a warp each)
     }
     const int bx = (maxw + 7) / 8;   // a warp per row
     zero_marked_rows_kernel<<<dim3(bx, rb.n), 256, 0, s>>>(U, m.epoch, m.base, m.kw, m.center);

@@ -485,33 +485,53 @@ cudaError_t launch_ring(const ConvBatch& cb, int nfreq, int64_t stride, int kw, 
 }
 
 // Wire convolution over sub-pitch impact positions (fine rows w * I + i of
-// X), fed by TMA: persistent CTAs walk units (tile, impact) with the impact
-// fastest, double-buffering the (B + K - 1)-row tile of the next unit while
-// computing the current one; impact i's rows come through tensor map i
-// (base row i, row pitch I rows), and one set of accumulators per tile sums
-// the impacts before Y is stored.  Each CTA takes a contiguous run of whole
-// tiles.  Waits are bounded as in the other TMA kernels.
+// X), fed by TMA: persistent CTAs claim tiles (a column block of kCols
+// frequencies x B output wires) from a counter and walk each tile's units
+// (tile, impact), double-buffering the (B + K - 1)-row tile of the next
+// unit while computing the current one; impact i's rows come through tensor
+// map i (base row i, row pitch I rows), and one set of accumulators per
+// tile sums the impacts before Y is stored.  With active-row marks
+// (U.rows[0], one per wire) a claimed tile none of whose outputs is live
+// (no marked wire in [w0 + c - K_w + 1, w0 + B - 1 + c]) is dropped at once
+// and its Y rows are left for the inverse transform to write as zeros;
+// claiming tiles one by one keeps the SMs evenly loaded when the live tiles
+// cluster.  The CTA claims its next tile before computing the current
+// tile's second-to-last unit.  sched[0] is the claim counter and sched[1] counts
+// finished CTAs; the last CTA to finish sets both back to zero (they start
+// at zero).  Waits are bounded as in the other TMA kernels.
 template <int K, int B>
 __global__ void __launch_bounds__(kCols)
 wire_conv_impacts_tma_kernel(const __grid_constant__ TmaConvUnits U, int impacts, int nwires, int nfreq,
                              int64_t stride, int kw, int center, int nkblocks, void* Yv, const void* Rtv,
-                             uint32_t* status) {
+                             unsigned* sched, uint32_t* status) {
     constexpr int ROWS = B + K - 1;
     constexpr uint32_t TILE_BYTES = ROWS * kCols * sizeof(float2);
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ __align__(8) uint64_t bar[2];
+    __shared__ int s_claim;
     auto buf = [&](int st) { return reinterpret_cast<const float2*>(smem + (st ? TILE_BYTES : 0u)); };
     float2* __restrict__ Y = static_cast<float2*>(Yv);
     const float2* __restrict__ Rt = static_cast<const float2*>(Rtv);
+    const mark_t* marks = U.rows[0];
+    const mark_t cur = marks ? read_epoch(U.epoch) : 0ull;
     const int nwb = (nwires + B - 1) / B;
     const int ntiles = nkblocks * nwb;
-    const int tile_beg = (int)((int64_t)ntiles * blockIdx.x / gridDim.x);
-    const int tile_end = (int)((int64_t)ntiles * (blockIdx.x + 1) / gridDim.x);
-    const int t_beg = tile_beg * impacts, t_end = tile_end * impacts;
-    auto issue = [&](int t, int st) {
-        const int tile = t / impacts, im = t - tile * impacts;
+    auto issue = [&](int tile, int im, int st) {
         const int k0 = (tile / nwb) * kCols, w0 = (tile % nwb) * B;
         tma_load_tile(smem + (st ? TILE_BYTES : 0u), &U.map[im], 2 * k0, w0 + center - (K - 1), &bar[st], TILE_BYTES);
+    };
+    // the next live tile (-1: none left); every thread calls it
+    auto claim = [&]() -> int {
+        for (;;) {
+            if (threadIdx.x == 0) s_claim = (int)atomicAdd(&sched[0], 1u);
+            __syncthreads();
+            const int t = s_claim;
+            __syncthreads();   // s_claim read by every thread before the next claim
+            if (t >= ntiles) return -1;
+            if (!marks) return t;
+            const int w0 = (t % nwb) * B;
+            if (cta_any_marked(marks, cur, w0 + center - kw + 1, w0 + B - 1 + center, nwires)) return t;
+        }
     };
     if (threadIdx.x == 0) {
         mbar_init(&bar[0]);
@@ -519,14 +539,18 @@ wire_conv_impacts_tma_kernel(const __grid_constant__ TmaConvUnits U, int impacts
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
-    if (t_beg < t_end && threadIdx.x == 0) issue(t_beg, 0);
     uint32_t parity[2] = {0u, 0u};
+    int st = 0;   // buffer of the current unit
     float k1[B], k2[B], k3[B];
-    for (int i = 0, t = t_beg; t < t_end; ++i, ++t) {
-        const int st = i & 1;
-        const bool inflight_next = t + 1 < t_end;
-        if (inflight_next && threadIdx.x == 0) issue(t + 1, st ^ 1);
-        const int tile = t / impacts, im = t - tile * impacts;
+    int tile = claim(), next = -1;
+    if (tile >= 0 && threadIdx.x == 0) issue(tile, 0, st);
+    bool failed = false;
+    for (int im = 0; tile >= 0 && !failed;) {
+        if (im == (impacts > 1 ? impacts - 2 : 0)) next = claim();
+        const int tn = im + 1 < impacts ? tile : next;
+        const int imn = im + 1 < impacts ? im + 1 : 0;
+        const bool inflight_next = tn >= 0;
+        if (inflight_next && threadIdx.x == 0) issue(tn, imn, st ^ 1);
         const int k0 = (tile / nwb) * kCols, w0 = (tile % nwb) * B;
         const int k = k0 + threadIdx.x;
         // this impact's taps (loaded while the tile lands)
@@ -548,7 +572,8 @@ wire_conv_impacts_tma_kernel(const __grid_constant__ TmaConvUnits U, int impacts
         if (__syncthreads_or(!ok)) {
             if (threadIdx.x == 0) atomicOr(status, WS_DEV_TIMEOUT);
             if (inflight_next) mbar_wait(&bar[st ^ 1], parity[st ^ 1]);
-            return;
+            failed = true;
+            break;
         }
         const float2* col = buf(st) + threadIdx.x;
         if (k < nfreq) {
@@ -573,6 +598,19 @@ wire_conv_impacts_tma_kernel(const __grid_constant__ TmaConvUnits U, int impacts
             }
         }
         __syncthreads();   // buffer st is free for the copy issued next iteration
+        st ^= 1;
+        tile = tn;
+        im = imn;
+    }
+    // the last CTA out resets the claim counter for the next launch (every
+    // CTA has made its final claim before it counts itself out)
+    if (threadIdx.x == 0) {
+        __threadfence();
+        if (atomicAdd(&sched[1], 1u) == gridDim.x - 1) {
+            sched[0] = 0u;
+            sched[1] = 0u;
+            __threadfence();
+        }
     }
 }
 
@@ -599,19 +637,15 @@ __global__ void bounded_wait_selftest_kernel(uint32_t* status, int iters, unsign
 
 bool tma_available() { return encode_fn() != nullptr; }
 
-cudaError_t launch_wire_conv_impacts_tma(const float2* X, float2* Y, const float2* Rt, int nwires, int impacts,
-                                         int nfreq, int64_t stride, int kw, int center, uint32_t* status,
-                                         cudaStream_t s) {
-    constexpr int K = kMaxRespWires, B = 16;
+template <int B>
+static cudaError_t launch_impacts_tma(TmaConvUnits& U, const float2* X, float2* Y, const float2* Rt, int nwires,
+                                      int impacts, int nfreq, int64_t stride, int kw, int center, unsigned* sched,
+                                      uint32_t* status, cudaStream_t s) {
+    constexpr int K = kMaxRespWires;
     constexpr int ROWS = B + K - 1;
     const PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
     if (!enc) return cudaErrorNotSupported;
-    if (impacts < 1 || impacts > kMaxUnits || nwires <= 0 || nfreq <= 0) return cudaErrorInvalidValue;
-    TmaConvUnits U;
-    U.n = impacts;
-    U.epoch = nullptr;
     for (int i = 0; i < impacts; ++i) {
-        U.rows[i] = nullptr;
         // impact i: fine rows i, i + I, i + 2I, ... (one per wire)
         const cuuint64_t dims[2] = {(cuuint64_t)(2 * stride), (cuuint64_t)nwires};
         const cuuint64_t strides[1] = {(cuuint64_t)(2 * stride * sizeof(float)) * (cuuint64_t)impacts};
@@ -636,8 +670,25 @@ cudaError_t launch_wire_conv_impacts_tma(const float2* X, float2* Y, const float
     int grid = num_sms() * per_sm;
     if (grid > ntiles) grid = ntiles;
     wire_conv_impacts_tma_kernel<K, B><<<grid, kCols, smem, s>>>(U, impacts, nwires, nfreq, stride, kw, center,
-                                                                 nkblocks, Y, Rt, status);
+                                                                 nkblocks, Y, Rt, sched, status);
     return cudaGetLastError();
+}
+
+cudaError_t launch_wire_conv_impacts_tma(const float2* X, float2* Y, const float2* Rt, int nwires, int impacts,
+                                         int nfreq, int64_t stride, int kw, int center, unsigned* sched,
+                                         uint32_t* status, cudaStream_t s, int variant, const mark_t* rows,
+                                         const mark_t* epoch) {
+    if (impacts < 1 || impacts > kMaxUnits || nwires <= 0 || nfreq <= 0 || variant < 0 ||
+        variant >= kImpactConvVariants || (rows && !epoch) || !sched || !status)
+        return cudaErrorInvalidValue;
+    TmaConvUnits U;
+    U.n = impacts;
+    for (int i = 0; i < impacts; ++i) U.rows[i] = nullptr;
+    U.rows[0] = rows;
+    U.epoch = epoch;
+    return variant == 1
+               ? launch_impacts_tma<32>(U, X, Y, Rt, nwires, impacts, nfreq, stride, kw, center, sched, status, s)
+               : launch_impacts_tma<16>(U, X, Y, Rt, nwires, impacts, nfreq, stride, kw, center, sched, status, s);
 }
 
 cudaError_t launch_bounded_wait_selftest(uint32_t* status, int iters, unsigned long long* cycles, cudaStream_t s) {

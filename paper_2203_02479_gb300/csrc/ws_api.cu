@@ -298,23 +298,45 @@ ws_status add_plane_noise(ws_plane* pl, const ws_params* p, void* Y, bool fp64, 
 }
 
 // Whether a plane's simulations skip inactive rows: FP32 fixed-shape row
-// transforms, linear convolution (windows do not wrap), one impact position
-// and no noise term (noise makes every row of the output live).
+// transforms, linear convolution (windows do not wrap) and no noise term
+// (noise makes every row of the output live).  An impact plane marks whole
+// wires (its I fine rows together); its wire convolution is the TMA one.
 bool marks_apply(const ws_plane* pl) {
-    return pl->impacts == 1 && pl->desc.conv_mode == WS_CONV_LINEAR && pl->noise_mode == 0 &&
-           ws::row_fft_fixed_shape(pl->plan);
+    return pl->desc.conv_mode == WS_CONV_LINEAR && pl->noise_mode == 0 && ws::row_fft_fixed_shape(pl->plan) &&
+           (pl->impacts == 1 || ws::tma_available());
+}
+
+// The impact wire convolution of one plane (fine spectra X -> Y), with the
+// call's marks or without (rows null); the launch is traced on plane `tr`.
+ws_status impacts_wconv(ws_plane* pl, ws_plane* tr, const float2* X, float2* Y, const ws::mark_t* rows,
+                        const ws::mark_t* epoch, unsigned* sched, cudaStream_t s, int variant) {
+    const ws_plane_desc& d = pl->desc;
+    if (d.conv_mode == WS_CONV_LINEAR && ws::tma_available()) {
+        WS_LAUNCH(tr, K_WCONV, s, ws::launch_wire_conv_impacts_tma(X, Y, pl->Rt, d.nwires, pl->impacts, pl->nfreq,
+                                                                   pl->fstride, d.resp_nwires, d.resp_wire_center,
+                                                                   sched, pl->status, s, variant, rows, epoch));
+    } else {
+        if (rows) return WS_ERR_UNSUPPORTED_SIZE;
+        WS_LAUNCH(tr, K_WCONV, s, ws::launch_wire_conv_impacts(X, Y, pl->Rt, d.nwires, pl->impacts, pl->nfreq,
+                                                               pl->fstride, d.resp_nwires, d.resp_wire_center,
+                                                               d.conv_mode == WS_CONV_CIRCULAR, s));
+    }
+    return WS_OK;
 }
 
 // ws_simulate's FP32 / compensated path with active rows: mark, clear the
 // marked rows, raster, then the three transform stages over marked / live
-// rows only (the same result as clearing and transforming every row).
+// rows only (the same result as clearing and transforming every row).  The
+// grid is `out` itself, or the fine grid of an impact plane.
 ws_status simulate_marked(ws_plane* pl, ws::RasterArgs a, float* out, cudaStream_t s) {
     const ws_plane_desc& d = pl->desc;
+    const int I = pl->impacts;
+    float* grid = I > 1 ? pl->fine : out;
     ws::RasterBatch rb;
     rb.n = 1;
     rb.prec = a.prec;
     rb.a[0] = a;
-    rb.grid[0] = out;
+    rb.grid[0] = grid;
     ws::RowMarks m;
     m.rows[0] = pl->rows;
     m.cls[0] = pl->row_cls;
@@ -322,33 +344,41 @@ ws_status simulate_marked(ws_plane* pl, ws::RasterArgs a, float* out, cudaStream
     m.base = pl->rows_base;
     m.kw = d.resp_nwires;
     m.center = d.resp_wire_center;
+    m.impacts[0] = I;
     WS_LAUNCH(pl, K_MARK, s, ws::launch_mark_rows(rb, m, s));
     WS_LAUNCH(pl, K_MEMSET, s, ws::launch_zero_marked_rows(rb, m, s));
-    WS_LAUNCH(pl, K_RASTER_SCATTER, s, ws::launch_raster_scatter(a, out, pl->large, s));
+    WS_LAUNCH(pl, K_RASTER_SCATTER, s, ws::launch_raster_scatter(a, grid, pl->large, s));
     ws::RowBatch fb, ib;
     fb.n = ib.n = 1;
-    fb.in[0] = out;
+    fb.in[0] = grid;
     fb.in2[0] = a.lo;
     fb.out[0] = pl->X;
-    fb.nrows[0] = d.nwires;
+    fb.nrows[0] = d.nwires * I;
+    fb.rdiv[0] = I;
     ib.in[0] = pl->Y;
     ib.in2[0] = nullptr;
     ib.out[0] = out;
     ib.nrows[0] = d.nwires;
     fb.status = ib.status = pl->status;
     fb.rows[0] = ib.rows[0] = pl->row_cls;
-    ws::ConvBatch cb;
-    cb.n = 1;
-    cb.X[0] = pl->X;
-    cb.Y[0] = pl->Y;
-    cb.Rt[0] = pl->Rt;
-    cb.nwires[0] = d.nwires;
-    cb.rows[0] = pl->rows;
-    cb.epoch = pl->rows_epoch;
     WS_LAUNCH(pl, K_FWD, s, ws::launch_fwd_rows_batch(pl->plan, pl->tw, fb, d.nticks, d.nticks, pl->fstride,
                                                       pl->nfreq, 1.0f, s));
-    WS_LAUNCH(pl, K_WCONV, s, ws::launch_wire_conv_batch(cb, pl->nfreq, pl->fstride, d.resp_nwires,
-                                                         d.resp_wire_center, 0, s, pl->wconv_variant, pl->status));
+    if (I > 1) {
+        const ws_status st =
+            impacts_wconv(pl, pl, pl->X, pl->Y, pl->rows, pl->rows_epoch, pl->sched, s, pl->wconv_variant);
+        if (st != WS_OK) return st;
+    } else {
+        ws::ConvBatch cb;
+        cb.n = 1;
+        cb.X[0] = pl->X;
+        cb.Y[0] = pl->Y;
+        cb.Rt[0] = pl->Rt;
+        cb.nwires[0] = d.nwires;
+        cb.rows[0] = pl->rows;
+        cb.epoch = pl->rows_epoch;
+        WS_LAUNCH(pl, K_WCONV, s, ws::launch_wire_conv_batch(cb, pl->nfreq, pl->fstride, d.resp_nwires,
+                                                             d.resp_wire_center, 0, s, pl->wconv_variant, pl->status));
+    }
     WS_LAUNCH(pl, K_INV, s, ws::launch_inv_rows_batch(pl->plan, pl->tw, ib, pl->fstride, pl->nfreq, d.nticks,
                                                       d.nticks, s));
     return WS_OK;
@@ -360,16 +390,9 @@ ws_status convolve_impl(ws_plane* pl, const float* grid, float* out, cudaStream_
     WS_LAUNCH(pl, K_FWD, s, ws::launch_fwd_rows(pl->plan, pl->tw, grid, d.nwires * pl->impacts, d.nticks, d.nticks,
                                                 pl->X, pl->fstride, pl->nfreq, 1.0f, s, pl->status));
     if (pl->impacts > 1) {
-        if (d.conv_mode == WS_CONV_LINEAR && ws::tma_available()) {
-            WS_LAUNCH(pl, K_WCONV, s, ws::launch_wire_conv_impacts_tma(pl->X, pl->Y, pl->Rt, d.nwires, pl->impacts,
-                                                                       pl->nfreq, pl->fstride, d.resp_nwires,
-                                                                       d.resp_wire_center, pl->status, s));
-        } else {
-            WS_LAUNCH(pl, K_WCONV, s, ws::launch_wire_conv_impacts(pl->X, pl->Y, pl->Rt, d.nwires, pl->impacts,
-                                                                   pl->nfreq, pl->fstride, d.resp_nwires,
-                                                                   d.resp_wire_center, d.conv_mode == WS_CONV_CIRCULAR,
-                                                                   s));
-        }
+        const ws_status st =
+            impacts_wconv(pl, pl, pl->X, pl->Y, nullptr, nullptr, pl->sched, s, pl->wconv_variant);
+        if (st != WS_OK) return st;
     } else {
         WS_LAUNCH(pl, K_WCONV, s, ws::launch_wire_conv(pl->X, pl->Y, pl->Rt, d.nwires, pl->nfreq, pl->fstride,
                                                        d.resp_nwires, d.resp_wire_center,
@@ -475,6 +498,7 @@ ws_status ws_plane_create(const ws_plane_desc* desc, const float* response_dev, 
     pl->rows = (ws::mark_t*)(base + lay.off_rows);
     pl->rows_epoch = (ws::mark_t*)(base + lay.off_status + 24);   // zeroed with the status region below
     pl->rows_base = (ws::mark_t*)(base + lay.off_status + 32);
+    pl->sched = (unsigned*)(base + lay.off_status + 40);
     pl->row_cls = (uint32_t*)(base + lay.off_cls);
     cudaStream_t s = (cudaStream_t)stream;
     cudaError_t e = cudaMemsetAsync(base + lay.off_status, 0, 256, s);
@@ -500,16 +524,24 @@ ws_status ws_plane_create(const ws_plane_desc* desc, const float* response_dev, 
     pl->wconv_variant = 0;
     pl->batch_upw = 0;
     pl->batch_wconv = -1;
-    if (e == cudaSuccess) e = cudaMemsetAsync(pl->X, 0, sizeof(float2) * (size_t)desc->nwires * lay.fstride, s);
-    if (e == cudaSuccess && lay.impacts == 1) {   // impact planes have one wire-convolution kernel
+    if (e == cudaSuccess)
+        e = cudaMemsetAsync(pl->X, 0, sizeof(float2) * (size_t)lay.impacts * desc->nwires * lay.fstride, s);
+    const int circ = desc->conv_mode == WS_CONV_CIRCULAR;
+    // impact planes: the TMA kernel's two wire-block sizes (linear mode), else
+    // their one generic kernel
+    const int nvar = lay.impacts > 1 ? ((circ || !ws::tma_available()) ? 1 : ws::kImpactConvVariants)
+                                     : ((circ || !ws::tma_available()) ? 4 : ws::kWireConvVariants);
+    if (e == cudaSuccess && nvar > 1) {
         cudaEvent_t t0 = nullptr, t1 = nullptr;
         e = cudaEventCreate(&t0);
         if (e == cudaSuccess) e = cudaEventCreate(&t1);
-        const int circ = desc->conv_mode == WS_CONV_CIRCULAR;
-        const int nvar = (circ || !ws::tma_available()) ? 4 : ws::kWireConvVariants;
         float best_of[ws::kWireConvVariants];
         for (int v = 0; v < nvar; ++v) best_of[v] = 1e30f;
         auto conv = [&](int v) {
+            if (lay.impacts > 1)
+                return ws::launch_wire_conv_impacts_tma(pl->X, pl->Y, pl->Rt, desc->nwires, lay.impacts, lay.nfreq,
+                                                        lay.fstride, desc->resp_nwires, desc->resp_wire_center,
+                                                        pl->sched, pl->status, s, v);
             return ws::launch_wire_conv(pl->X, pl->Y, pl->Rt, desc->nwires, lay.nfreq, lay.fstride,
                                         desc->resp_nwires, desc->resp_wire_center, circ, s, v, pl->status);
         };
@@ -556,6 +588,11 @@ ws_status ws_plane_destroy(ws_plane* plane) {
 
 ws_status ws_plane_set_wire_conv_variant(ws_plane* pl, int variant) {
     if (!pl || variant < 0 || variant >= ws::kWireConvVariants) return WS_ERR_INVALID_ARG;
+    if (pl->impacts > 1) {   // the TMA impact kernel's wire blocks of 16 / 32 (linear mode)
+        if (variant >= ws::kImpactConvVariants) return WS_ERR_UNSUPPORTED_SIZE;
+        if (variant > 0 && (pl->desc.conv_mode == WS_CONV_CIRCULAR || !ws::tma_available()))
+            return WS_ERR_UNSUPPORTED_SIZE;
+    }
     if (variant >= 4 && (pl->desc.conv_mode == WS_CONV_CIRCULAR || !ws::tma_available())) return WS_ERR_UNSUPPORTED_SIZE;
     pl->wconv_variant = variant;
     pl->batch_wconv = variant;   // an explicit choice holds for batches too
@@ -706,6 +743,7 @@ ws_status ws_simulate(ws_plane* pl, const ws_depos* depos, const ws_params* para
     ws::RasterArgs a = raster_args(pl, depos, params);
     if (pl->impacts > 1) {
         if (params->precision != WS_PREC_FP32) return WS_ERR_UNSUPPORTED_SIZE;
+        if (marks_apply(pl)) return simulate_marked(pl, a, out_dev, s);
         WS_LAUNCH(pl, K_MEMSET, s, cudaMemsetAsync(pl->fine, 0, grid_bytes * pl->impacts, s));
         WS_LAUNCH(pl, K_RASTER_SCATTER, s, ws::launch_raster_scatter(a, pl->fine, pl->large, s));
         return convolve_impl(pl, pl->fine, out_dev, s, params);
@@ -841,17 +879,23 @@ namespace {
 // that consecutive waves run on kBatchSlots streams (wave k in slot k % S).
 constexpr int kBatchSlots = 3;
 
+// A unit's spectra: X (I x nwires rows for impact planes) then Y (nwires
+// rows); impact planes also keep a unit's fine grid (I x nwires rows of
+// ticks) in the slot.
 struct BatchLayout {
-    size_t off_counters, off_list, off_spec, spec_bytes, off_rows, rows_bytes, off_cls, cls_bytes, slot_bytes, total;
+    size_t off_counters, off_list, off_spec, xspec_bytes, spec_bytes, off_rows, rows_bytes, off_cls, cls_bytes,
+        off_fine, fine_bytes, slot_bytes, total;
 };
 // Within a slot's 256-byte counter block (cleared at the start of every call):
-// the large-patch list's count and done words, and the active-row epochs
-// (base at byte 8, epoch at byte 16).  The slot's marks are cleared at the
+// the large-patch list's count and done words, the active-row epochs (base
+// at byte 8, epoch at byte 16) and the impact wire convolution's claim words
+// (byte 24; its launches on a slot run one after another).  The slot's marks are cleared at the
 // start of every call too, so the waves of a call that share a slot mark
 // with epochs 1, 2, ... above every mark there.
 constexpr size_t kBatchClearBytes = 64;
 constexpr size_t kBatchRowsBase = 8;
 constexpr size_t kBatchRowsEpoch = 16;
+constexpr size_t kBatchSched = 24;   // the impact wire convolution's two claim words
 
 ws_status batch_layout(ws_plane* const* planes, int nplanes, int units_per_wave, BatchLayout* lay) {
     if (units_per_wave == 0) units_per_wave = ws::kMaxUnits;
@@ -862,9 +906,9 @@ ws_status batch_layout(ws_plane* const* planes, int nplanes, int units_per_wave,
     for (int i = 0; i < nplanes; ++i) {
         const ws_plane* p = planes[i];
         if (!p) return WS_ERR_INVALID_ARG;
-        if (p->impacts > 1) return WS_ERR_UNSUPPORTED_SIZE;
-        // one launch per stage needs one transform plan and one response shape
-        if (p->plan.L != p0->plan.L || p->plan.npass != p0->plan.npass || p->fstride != p0->fstride ||
+        // one launch per stage needs one transform plan, one response shape
+        // and one pitch binning (impact positions)
+        if (p->impacts != p0->impacts || p->plan.L != p0->plan.L || p->plan.npass != p0->plan.npass || p->fstride != p0->fstride ||
             p->desc.nticks != p0->desc.nticks || p->desc.resp_nwires != p0->desc.resp_nwires ||
             p->desc.resp_wire_center != p0->desc.resp_wire_center || p->desc.conv_mode != p0->desc.conv_mode)
             return WS_ERR_UNSUPPORTED_SIZE;
@@ -875,12 +919,16 @@ ws_status batch_layout(ws_plane* const* planes, int nplanes, int units_per_wave,
     size_t o = 0;
     lay->off_counters = o; o = align256(o + 256);
     lay->off_list = o; o = align256(o + sizeof(long long) * (size_t)ws::kLargeListCap);
+    const int I = p0->impacts;
+    lay->xspec_bytes = align256(sizeof(float2) * (size_t)I * maxw * p0->fstride);
     lay->spec_bytes = align256(sizeof(float2) * (size_t)maxw * p0->fstride);
-    lay->off_spec = o; o += 2 * (size_t)units_per_wave * lay->spec_bytes;
+    lay->off_spec = o; o += (size_t)units_per_wave * (lay->xspec_bytes + lay->spec_bytes);
     lay->rows_bytes = align256(sizeof(ws::mark_t) * (size_t)maxw);
     lay->off_rows = o; o += (size_t)units_per_wave * lay->rows_bytes;
     lay->cls_bytes = align256(sizeof(uint32_t) * (size_t)maxw);
     lay->off_cls = o; o += (size_t)units_per_wave * lay->cls_bytes;
+    lay->fine_bytes = I > 1 ? align256(sizeof(float) * (size_t)I * maxw * p0->desc.nticks) : 0;
+    lay->off_fine = o; o += (size_t)units_per_wave * lay->fine_bytes;
     lay->slot_bytes = o;
     lay->total = kBatchSlots * o;
     return WS_OK;
@@ -1067,7 +1115,10 @@ ws_status ws_batch_autotune(ws_plane* const* planes, int nplanes, const ws_depos
     const int circ = planes[0]->desc.conv_mode == WS_CONV_CIRCULAR;
     // a kernel already chosen for batches on these planes (by an earlier
     // run of the autotuner or ws_plane_set_wire_conv_variant) is kept
-    const int nvar = planes[0]->batch_wconv >= 0 ? 0 : ((circ || !ws::tma_available()) ? 4 : ws::kWireConvVariants);
+    const int nvar = planes[0]->batch_wconv >= 0             ? 0
+                     : planes[0]->impacts > 1                  ? ((circ || !ws::tma_available()) ? 0 : ws::kImpactConvVariants)
+                     : (circ || !ws::tma_available())          ? 4
+                                                               : ws::kWireConvVariants;
     float var_ms[ws::kWireConvVariants];
     for (int v = 0; v < nvar; ++v) var_ms[v] = 1e30f;
     const int keep = planes[0]->batch_wconv;
@@ -1119,8 +1170,11 @@ ws_status batch_waves(ws_plane* const* planes, int nplanes, const ws_depos* depo
     // planes, else the first plane's own
     const int wconv = p0->batch_wconv >= 0 ? p0->batch_wconv : p0->wconv_variant;
     // active rows for every unit whose plane allows them (see marks_apply;
-    // the transform plan and convolution mode are shared by the batch)
-    const bool marked = d0.conv_mode == WS_CONV_LINEAR && ws::row_fft_fixed_shape(p0->plan);
+    // the transform plan, convolution mode and impact positions are shared
+    // by the batch)
+    const int I = p0->impacts;
+    const bool marked = d0.conv_mode == WS_CONV_LINEAR && ws::row_fft_fixed_shape(p0->plan) &&
+                        (I == 1 || ws::tma_available());
     for (int slot = 0; slot < nstreams; ++slot) {
         char* sb = ws_base + slot * lay.slot_bytes;
         WS_CUDA(cudaMemsetAsync(sb + lay.off_counters, 0, kBatchClearBytes, ss[slot]));
@@ -1155,20 +1209,24 @@ ws_status batch_waves(ws_plane* const* planes, int nplanes, const ws_depos* depo
             ws_plane* pl = planes[pi];
             ws_params pe = *params;
             pe.event_id = params->event_id + (uint32_t)e;
-            float2* X = (float2*)(base + lay.off_spec + (size_t)(2 * j) * lay.spec_bytes);
-            float2* Y = (float2*)(base + lay.off_spec + (size_t)(2 * j + 1) * lay.spec_bytes);
+            float2* X = (float2*)(base + lay.off_spec + (size_t)j * (lay.xspec_bytes + lay.spec_bytes));
+            float2* Y = (float2*)((char*)X + lay.xspec_bytes);
+            // the grid: the output itself, or the unit's fine grid
+            float* G = I > 1 ? (float*)(base + lay.off_fine + (size_t)j * lay.fine_bytes) : out_dev[u];
             m.rows[j] = (marked && marks_apply(pl)) ? (ws::mark_t*)(base + lay.off_rows + (size_t)j * lay.rows_bytes)
                                                     : nullptr;
             m.cls[j] = m.rows[j] ? (uint32_t*)(base + lay.off_cls + (size_t)j * lay.cls_bytes) : nullptr;
+            m.impacts[j] = I;
             fb.rows[j] = ib.rows[j] = m.cls[j];
+            fb.rdiv[j] = I;
             cb.rows[j] = m.rows[j];
             rb.a[j] = raster_args(pl, &depos[u], &pe);
-            rb.grid[j] = out_dev[u];
-            counts[j] = (int64_t)pl->desc.nwires * pl->desc.nticks;
-            fb.in[j] = out_dev[u];
+            rb.grid[j] = G;
+            counts[j] = (int64_t)I * pl->desc.nwires * pl->desc.nticks;
+            fb.in[j] = G;
             fb.in2[j] = nullptr;
             fb.out[j] = X;
-            fb.nrows[j] = pl->desc.nwires;
+            fb.nrows[j] = I * pl->desc.nwires;
             cb.X[j] = X;
             cb.Y[j] = Y;
             cb.Rt[j] = pl->Rt;
@@ -1194,8 +1252,18 @@ ws_status batch_waves(ws_plane* const* planes, int nplanes, const ws_depos* depo
         WS_LAUNCH(p0, K_RASTER_SCATTER, s, ws::launch_raster_scatter_batch(rb, L, s));
         WS_LAUNCH(p0, K_FWD, s, ws::launch_fwd_rows_batch(p0->plan, p0->tw, fb, d0.nticks, d0.nticks, p0->fstride,
                                                           p0->nfreq, 1.0f, s));
-        WS_LAUNCH(p0, K_WCONV, s, ws::launch_wire_conv_batch(cb, p0->nfreq, p0->fstride, d0.resp_nwires,
-                                                             d0.resp_wire_center, circ, s, wconv, p0->status));
+        if (I > 1) {   // one launch per unit (its I tensor maps)
+            for (int j = 0; j < nu; ++j) {
+                const ws_status st = impacts_wconv(planes[(u0 + j) % nplanes], p0, (const float2*)cb.X[j],
+                                                   (float2*)cb.Y[j], m.rows[j], m.rows[j] ? m.epoch : nullptr,
+                                                   (unsigned*)(base + lay.off_counters + kBatchSched), s,
+                                                   wconv < ws::kImpactConvVariants ? wconv : 0);
+                if (st != WS_OK) return st;
+            }
+        } else {
+            WS_LAUNCH(p0, K_WCONV, s, ws::launch_wire_conv_batch(cb, p0->nfreq, p0->fstride, d0.resp_nwires,
+                                                                 d0.resp_wire_center, circ, s, wconv, p0->status));
+        }
         if (noisy) WS_LAUNCH(p0, K_NOISE, s, ws::launch_add_noise(nb, p0->nfreq, p0->plan.L, p0->fstride, s));
         WS_LAUNCH(p0, K_INV, s, ws::launch_inv_rows_batch(p0->plan, p0->tw, ib, p0->fstride, p0->nfreq, d0.nticks,
                                                           d0.nticks, s));

@@ -165,14 +165,20 @@ struct RowMarks {
     mark_t* epoch;                // the call's epoch (written by the marking kernel)
     mark_t* base;                 // the previous call's epoch (copied from `epoch` by the clearing kernel)
     int kw = 0, center = 0;       // response wires and centre row (the classes' windows)
+    // per unit, grid rows per marked row: impact planes mark whole wires, and
+    // wire w's grid rows are w * I .. w * I + I - 1 (0 or 1: one row per wire)
+    int impacts[kMaxUnits] = {};
 };
 
 __device__ __forceinline__ mark_t read_epoch(const mark_t* e) { return *(const volatile mark_t*)e; }
 
 // Row classes (one word per wire row, written for every row by the clearing
-// kernel): the row is marked; a marked row lies within K_w - 1 wires (its
-// spectrum may be read); a marked row lies in its wire-convolution window
-// [w + c - K_w + 1, w + c] (its output is live).
+// kernel): the row is marked; a marked row lies in [w - K_w + 1, w + K - 1]
+// with K = kMaxRespWires (its spectrum may be read: the register-blocked
+// kernels read every live output's K-row window, whose taps past K_w are
+// zero, and zero times a stale non-finite value is not zero); a marked row
+// lies in its wire-convolution window [w + c - K_w + 1, w + c] (its output
+// is live).
 enum : uint32_t { ROW_MARKED = 1u, ROW_NEEDED = 2u, ROW_LIVE = 4u };
 
 // Whether any row of [lo, hi] (clipped to [0, n)) is marked; every thread of
@@ -195,8 +201,11 @@ struct RowBatch {          // row transforms: unit i has nrows[i] rows in[i] -> 
     uint32_t* status = nullptr;   // device status word: lets the fixed-shape kernels fetch rows by
                                   // bulk copies (a copy that never lands is reported there)
     // active rows (fixed-shape FP32 kernels only): per unit the row classes
-    // of the call (null: every row marked, needed and live)
+    // of the call (null: every row marked, needed and live); row r takes the
+    // class of entry r / rdiv (the fine rows of an impact plane share their
+    // wire's class; 0 or 1: one entry per row)
     const uint32_t* rows[kMaxUnits] = {};
+    int rdiv[kMaxUnits] = {};
 };
 struct NoiseBatch {        // noise added to the spectra Y[i] (nwires[i] rows) of each unit
     int n = 0;
@@ -226,6 +235,7 @@ struct RowUnits {
     int nrows[kMaxUnits];
     uint32_t* status;
     const uint32_t* rows[kMaxUnits];   // row classes, or null
+    int rdiv[kMaxUnits];               // rows per class entry (>= 1)
 };
 struct NoiseUnits {
     int n;
@@ -309,10 +319,16 @@ cudaError_t launch_bounded_wait_selftest(uint32_t* status, int iters, unsigned l
 cudaError_t launch_wire_conv_tma(const ConvBatch& cb, int nfreq, int64_t stride, int kw, int center, int variant,
                                  uint32_t* status, cudaStream_t s);
 // The impact wire convolution fed by TMA (linear mode; a copy that never
-// lands sets WS_DEV_TIMEOUT in *status).
+// lands sets WS_DEV_TIMEOUT in *status); variant 0 / 1: blocks of 16 / 32
+// output wires.  CTAs claim blocks from sched[0] (two zeroed words, left
+// zeroed by the launch; launches sharing them must not overlap).  With
+// active-row marks (one per wire, and the call's epoch) blocks whose outputs
+// are all dead are skipped and their Y rows not written.
+constexpr int kImpactConvVariants = 2;
 cudaError_t launch_wire_conv_impacts_tma(const float2* X, float2* Y, const float2* Rt, int nwires, int impacts,
-                                         int nfreq, int64_t stride, int kw, int center, uint32_t* status,
-                                         cudaStream_t s);
+                                         int nfreq, int64_t stride, int kw, int center, unsigned* sched,
+                                         uint32_t* status, cudaStream_t s, int variant = 0,
+                                         const mark_t* rows = nullptr, const mark_t* epoch = nullptr);
 
 // Hand-over list of depos whose patches are too large for the lane-per-depo
 // raster kernel (workspace-resident; count and done must start at zero and
@@ -348,6 +364,7 @@ struct RasterUnits {
     float* grid[kMaxUnits];
     mark_t* rows[kMaxUnits];            // active-row marks (mark / clear kernels), or null
     uint32_t* cls[kMaxUnits];           // row classes (clear kernel), with marks
+    int imp[kMaxUnits];                 // grid rows per marked row (impact positions; 1: plain)
 };
 struct ZeroSizes {
     long long count[kMaxUnits];
@@ -417,5 +434,6 @@ struct ws_plane {
     ws::mark_t* rows;        // nwires active-row marks (ws_simulate)
     ws::mark_t* rows_epoch;  // their epoch words (ws::RowMarks epoch and base, status region)
     ws::mark_t* rows_base;
+    unsigned* sched;         // impact wire convolution's claim counter and finished CTAs (status region)
     uint32_t* row_cls;       // nwires row classes (ws_simulate)
 };

@@ -96,9 +96,9 @@ def test_impact_planes_rejected_where_unsupported(ws):
     pl = ws.Plane(16, 500, R)
     d = ws.DeviceDepos.from_plane_depos(inputs.uniform_depos(10, 16, seed=1, nticks=500))
     with pytest.raises(ws.WiresimError):
-        ws.Batch([pl], [[d]], ws.Params(), units_per_wave=1).run()
-    with pytest.raises(ws.WiresimError):
         pl.simulate(d, ws.Params(precision=ws.WS_PREC_FP64))
+    with pytest.raises(ws.WiresimError):
+        pl.set_wire_conv_variant(2)      # impact planes: wire blocks of 16 or 32 (0, 1)
     import torch
     with pytest.raises(ws.WiresimError):
         pl.backward(d, ws.Params(), torch.zeros((16, 500), device="cuda"))
