@@ -514,16 +514,6 @@ raster_kernel(const __grid_constant__ RasterUnits U, ws_patches pt, const long l
 constexpr int kSmallWarpsPerBlock = 4;
 constexpr int kSmallGroup = 32;   // depos per warp (a lane per depo)
 
-// First slot of s[0..n) (inclusive prefix sums, nondecreasing) exceeding v.
-template <int N>
-__device__ __forceinline__ int find_slot(const int* s, int v) {
-    int lo = 0;
-#pragma unroll
-    for (int step = N / 2; step >= 1; step >>= 1)
-        if (s[lo + step - 1] <= v) lo += step;
-    return lo;
-}
-
 // One axis of a lane's depo: FP32, or FP64 for the whole FP64 path and for
 // axes narrower than an eighth of a bin in the compensated path.
 template <int P, typename W>
@@ -539,10 +529,9 @@ __device__ __forceinline__ void lane_weights(const RasterArgs& a, W mu, W sigma,
     lane_axis_weights<W, W>(mu, sigma, delta, nsig, point, first, nb, inv_norm, w);
 }
 
-constexpr int kBinMap = 1024;    // items of a depo group addressed through a byte map (else a search)
 
 template <int MODE, int P, int SW>
-__global__ void __launch_bounds__(32 * kSmallWarpsPerBlock, 7)
+__global__ void __launch_bounds__(32 * kSmallWarpsPerBlock, 8)
 raster_small_kernel(const __grid_constant__ RasterUnits U, ws_patches pt, long long* __restrict__ list,
                     unsigned* list_count, unsigned list_cap, int cdf_rows) {
     using W = typename PrecT<P>::W;
@@ -550,14 +539,7 @@ raster_small_kernel(const __grid_constant__ RasterUnits U, ws_patches pt, long l
     constexpr int G = kSmallGroup;
     __shared__ W s_wt[NW][G][kSmallT + 1];
     __shared__ W s_wx[NW][G][SW + 1];
-    __shared__ int s_off[NW][G];     // inclusive scan of the depos' bin counts
-    __shared__ int s_k0[NW][G];
-    __shared__ int s_w0[NW][G];
-    __shared__ int s_nt[NW][G];      // items per patch row: ticks, or quads when fluctuating
-    __shared__ int s_kn[NW][G];      // ticks per patch row
-    __shared__ float s_rnt[NW][G];   // 1 / s_nt
-    __shared__ W s_q[NW][G];
-    __shared__ unsigned char s_bdep[NW][kBinMap];   // item -> depo slot
+    __shared__ unsigned char s_start[NW][G];   // a round's item lane -> depo slot starting there
     __shared__ float s_recip[kExactCap + 1];
     // drawing bins of a round (at most four per lane): grid index, N, Philox word
     __shared__ uint32_t s_eidx[NW][128];
@@ -621,24 +603,45 @@ raster_small_kernel(const __grid_constant__ RasterUnits U, ws_patches pt, long l
             if (lane >= o) incl += y;
         }
         const int total = __shfl_sync(0xffffffffu, incl, 31);
-        const bool use_bmap = total <= kBinMap;
-        s_off[wib][dl] = incl;
-        s_k0[wib][dl] = any ? e.k0 : 0;
-        s_w0[wib][dl] = any ? e.w0 : 0;
-        s_nt[wib][dl] = ncol;
-        s_kn[wib][dl] = ntc;
-        s_rnt[wib][dl] = ncol > 0 ? 1.f / (float)ncol : 0.f;
-        s_q[wib][dl] = a.fluct ? q : (sizeof(W) == 8 ? (W)a.p64 : (W)a.p) * q;
-        if (use_bmap)
-            for (int j = incl - nb; j < incl; ++j) s_bdep[wib][j] = (unsigned char)dl;
-        __syncwarp();
-        const int* off = s_off[wib];
-        // item g of the group -> depo slot d, index inside its patch, (row, column)
-        auto locate = [&](int g, int& d, int& local, int& ia, int& ib) {
-            d = use_bmap ? (int)s_bdep[wib][g] : find_slot<G>(off, g);
-            local = g - (d > 0 ? off[d - 1] : 0);
-            ia = (int)(((float)local + 0.5f) * s_rnt[wib][d]);
-            ib = local - ia * s_nt[wib][d];
+        // this lane's depo, handed to the lanes whose items it holds by shuffles
+        const int my_start = incl - nb;   // its first item
+        const int my_k0 = any ? e.k0 : 0, my_w0 = any ? e.w0 : 0;
+        const float my_rnt = ncol > 0 ? 1.f / (float)ncol : 0.f;
+        const W my_q = a.fluct ? q : (sizeof(W) == 8 ? (W)a.p64 : (W)a.p) * q;
+        __syncwarp();   // the weight tables are written
+        // Round gb (every lane): item g = gb + lane lies in depo slot d, the
+        // first slot whose inclusive count exceeds g: the slot holding item
+        // gb (the number of slots ending at or before gb), unless a slot
+        // starts at an item of the round at or before g, the last such one
+        // (starts marked in a bitmask, slot numbers in a 32-entry map).  Then
+        // the item's index inside that depo's patch, its (row, column) and
+        // the depo's values.  Lanes with g >= total get unused values.
+        struct Item {
+            int d, local, ia, ib, k0, kn, w0;
+            W q;
+        };
+        auto locate = [&](int gb) {
+            Item it;
+            const int d0 = __popc(__ballot_sync(0xffffffffu, incl <= gb));
+            const int s = my_start - gb;
+            const bool starts = nb > 0 && s > 0 && s < G;
+            const unsigned smask = __reduce_or_sync(0xffffffffu, starts ? 1u << s : 0u);
+            __syncwarp();   // the previous round's reads of s_start are done
+            if (starts) s_start[wib][s] = (unsigned char)lane;
+            __syncwarp();
+            const unsigned m = smask & (0xffffffffu >> (31 - lane));
+            it.d = m ? (int)s_start[wib][31 - __clz(m)] : (d0 < G ? d0 : G - 1);
+            const int sd = __shfl_sync(0xffffffffu, my_start, it.d);
+            const float rnt = __shfl_sync(0xffffffffu, my_rnt, it.d);
+            const int nc = __shfl_sync(0xffffffffu, ncol, it.d);
+            it.k0 = __shfl_sync(0xffffffffu, my_k0, it.d);
+            it.kn = __shfl_sync(0xffffffffu, ntc, it.d);
+            it.w0 = __shfl_sync(0xffffffffu, my_w0, it.d);
+            it.q = __shfl_sync(0xffffffffu, my_q, it.d);
+            it.local = gb + lane - sd;
+            it.ia = (int)(((float)it.local + 0.5f) * rnt);
+            it.ib = it.local - it.ia * nc;
+            return it;
         };
         if (quads) {
             // Rounds of 32 quads, one per lane: the lane forms the quad's (up
@@ -654,14 +657,14 @@ raster_small_kernel(const __grid_constant__ RasterUnits U, ws_patches pt, long l
                 int N[4] = {0, 0, 0, 0};
                 uint32_t first = 0;
                 uint4 x = make_uint4(0u, 0u, 0u, 0u);
+                const Item it = locate(gb);
                 if (g < total) {
-                    int d, local, ia, iq;
-                    locate(g, d, local, ia, iq);
-                    const int k0 = s_k0[wib][d];
-                    const int nt = s_kn[wib][d];
-                    const int w = s_w0[wib][d] + ia;
-                    const int kq = (k0 >> 2) + iq;          // the quad's tick group
-                    const W qw = s_q[wib][d] * s_wx[wib][d][ia];
+                    const int d = it.d, ia = it.ia;
+                    const int k0 = it.k0;
+                    const int nt = it.kn;
+                    const int w = it.w0 + ia;
+                    const int kq = (k0 >> 2) + it.ib;          // the quad's tick group
+                    const W qw = it.q * s_wx[wib][d][ia];
 #pragma unroll
                     for (int j = 0; j < 4; ++j) {
                         const int b = 4 * kq + j - k0;
@@ -709,15 +712,16 @@ raster_small_kernel(const __grid_constant__ RasterUnits U, ws_patches pt, long l
                 __syncwarp();
             }
         } else {
-            for (int g = lane; g < total; g += 32) {
-                int d, local, ia, ib;
-                locate(g, d, local, ia, ib);
-                const int w = s_w0[wib][d] + ia, k = s_k0[wib][d] + ib;
-                W v = s_q[wib][d] * s_wx[wib][d][ia] * s_wt[wib][d][ib];
+            for (int gb = 0; gb < total; gb += 32) {
+                const Item it = locate(gb);
+                if (gb + lane >= total) continue;
+                const int d = it.d, ia = it.ia, ib = it.ib;
+                const int w = it.w0 + ia, k = it.k0 + ib;
+                W v = it.q * s_wx[wib][d][ia] * s_wt[wib][d][ib];
                 if (a.fluct)
                     v = (W)binomial_bin<P>(electrons(v), a, w, k, (uint32_t)(base + d), s_recip, cdf);
                 if (MODE == EMIT_GRID) emit<P>(a, grid, (int64_t)w * a.nticks + k, v);
-                else pt.val[pt.off[base + d] + local] = (float)v;
+                else pt.val[pt.off[base + d] + it.local] = (float)v;
             }
         }
         __syncwarp();

@@ -485,40 +485,47 @@ cudaError_t launch_ring(const ConvBatch& cb, int nfreq, int64_t stride, int kw, 
 }
 
 // Wire convolution over sub-pitch impact positions (fine rows w * I + i of
-// X), fed by TMA: persistent CTAs claim tiles (a column block of kCols
-// frequencies x B output wires) from a counter and walk each tile's units
-// (tile, impact), double-buffering the (B + K - 1)-row tile of the next
-// unit while computing the current one; impact i's rows come through tensor
-// map i (base row i, row pitch I rows), and one set of accumulators per
-// tile sums the impacts before Y is stored.  With active-row marks
-// (U.rows[0], one per wire) a claimed tile none of whose outputs is live
-// (no marked wire in [w0 + c - K_w + 1, w0 + B - 1 + c]) is dropped at once
-// and its Y rows are left for the inverse transform to write as zeros;
-// claiming tiles one by one keeps the SMs evenly loaded when the live tiles
+// each unit's X), fed by TMA, over the units of a launch: persistent CTAs
+// claim tiles (a column block of kCols frequencies x B output wires of one
+// unit) from a counter and walk each tile's units of work (tile, impact),
+// double-buffering the (B + K - 1)-row tile of the next one while computing
+// the current one; impact i of unit u comes through tensor map u * I + i
+// (base row i, row pitch I rows), and one set of accumulators per tile sums
+// the impacts before Y is stored.  With active-row marks (U.rows[u], one per
+// wire) a claimed tile none of whose outputs is live (no marked wire in
+// [w0 + c - K_w + 1, w0 + B - 1 + c]) is dropped at once and its Y rows are
+// left for the inverse transform to write as zeros; claiming tiles one by
+// one over all units keeps the SMs evenly loaded when the live tiles
 // cluster.  The CTA claims its next tile before computing the current
-// tile's second-to-last unit.  sched[0] is the claim counter and sched[1] counts
-// finished CTAs; the last CTA to finish sets both back to zero (they start
-// at zero).  Waits are bounded as in the other TMA kernels.
+// tile's second-to-last impact.  sched[0] is the claim counter and sched[1]
+// counts finished CTAs; the last CTA to finish sets both back to zero (they
+// start at zero).  Waits are bounded as in the other TMA kernels.
 template <int K, int B>
 __global__ void __launch_bounds__(kCols)
-wire_conv_impacts_tma_kernel(const __grid_constant__ TmaConvUnits U, int impacts, int nwires, int nfreq,
-                             int64_t stride, int kw, int center, int nkblocks, void* Yv, const void* Rtv,
-                             unsigned* sched, uint32_t* status) {
+wire_conv_impacts_tma_kernel(const __grid_constant__ TmaConvUnits U, int impacts, int nfreq, int64_t stride, int kw,
+                             int center, unsigned* sched, uint32_t* status) {
     constexpr int ROWS = B + K - 1;
     constexpr uint32_t TILE_BYTES = ROWS * kCols * sizeof(float2);
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ __align__(8) uint64_t bar[2];
     __shared__ int s_claim;
     auto buf = [&](int st) { return reinterpret_cast<const float2*>(smem + (st ? TILE_BYTES : 0u)); };
-    float2* __restrict__ Y = static_cast<float2*>(Yv);
-    const float2* __restrict__ Rt = static_cast<const float2*>(Rtv);
-    const mark_t* marks = U.rows[0];
-    const mark_t cur = marks ? read_epoch(U.epoch) : 0ull;
-    const int nwb = (nwires + B - 1) / B;
-    const int ntiles = nkblocks * nwb;
-    auto issue = [&](int tile, int im, int st) {
-        const int k0 = (tile / nwb) * kCols, w0 = (tile % nwb) * B;
-        tma_load_tile(smem + (st ? TILE_BYTES : 0u), &U.map[im], 2 * k0, w0 + center - (K - 1), &bar[st], TILE_BYTES);
+    const mark_t cur = U.epoch ? read_epoch(U.epoch) : 0ull;
+    const int ntiles = U.prefix[U.n];
+    struct Tile {
+        int u, k0, w0;
+    };
+    auto decode = [&](int t) {
+        int u = 0;
+        while (u + 1 < U.n && U.prefix[u + 1] <= t) ++u;
+        const int tt = t - U.prefix[u];
+        const int nwb = (U.nwires[u] + B - 1) / B;
+        return Tile{u, (tt / nwb) * kCols, (tt % nwb) * B};
+    };
+    auto issue = [&](int t, int im, int st) {
+        const Tile T = decode(t);
+        tma_load_tile(smem + (st ? TILE_BYTES : 0u), &U.map[T.u * impacts + im], 2 * T.k0, T.w0 + center - (K - 1),
+                      &bar[st], TILE_BYTES);
     };
     // the next live tile (-1: none left); every thread calls it
     auto claim = [&]() -> int {
@@ -528,9 +535,10 @@ wire_conv_impacts_tma_kernel(const __grid_constant__ TmaConvUnits U, int impacts
             const int t = s_claim;
             __syncthreads();   // s_claim read by every thread before the next claim
             if (t >= ntiles) return -1;
+            const Tile T = decode(t);
+            const mark_t* marks = U.rows[T.u];
             if (!marks) return t;
-            const int w0 = (t % nwb) * B;
-            if (cta_any_marked(marks, cur, w0 + center - kw + 1, w0 + B - 1 + center, nwires)) return t;
+            if (cta_any_marked(marks, cur, T.w0 + center - kw + 1, T.w0 + B - 1 + center, U.nwires[T.u])) return t;
         }
     };
     if (threadIdx.x == 0) {
@@ -540,19 +548,19 @@ wire_conv_impacts_tma_kernel(const __grid_constant__ TmaConvUnits U, int impacts
     }
     __syncthreads();
     uint32_t parity[2] = {0u, 0u};
-    int st = 0;   // buffer of the current unit
+    int st = 0;   // buffer of the current unit of work
     float k1[B], k2[B], k3[B];
     int tile = claim(), next = -1;
     if (tile >= 0 && threadIdx.x == 0) issue(tile, 0, st);
-    bool failed = false;
-    for (int im = 0; tile >= 0 && !failed;) {
+    for (int im = 0; tile >= 0;) {
         if (im == (impacts > 1 ? impacts - 2 : 0)) next = claim();
         const int tn = im + 1 < impacts ? tile : next;
         const int imn = im + 1 < impacts ? im + 1 : 0;
         const bool inflight_next = tn >= 0;
         if (inflight_next && threadIdx.x == 0) issue(tn, imn, st ^ 1);
-        const int k0 = (tile / nwb) * kCols, w0 = (tile % nwb) * B;
-        const int k = k0 + threadIdx.x;
+        const Tile T = decode(tile);
+        const int k = T.k0 + threadIdx.x;
+        const float2* __restrict__ Rt = static_cast<const float2*>(U.Rt[T.u]);
         // this impact's taps (loaded while the tile lands)
         float cc[K], cm[K], cp[K];
 #pragma unroll
@@ -572,7 +580,6 @@ wire_conv_impacts_tma_kernel(const __grid_constant__ TmaConvUnits U, int impacts
         if (__syncthreads_or(!ok)) {
             if (threadIdx.x == 0) atomicOr(status, WS_DEV_TIMEOUT);
             if (inflight_next) mbar_wait(&bar[st ^ 1], parity[st ^ 1]);
-            failed = true;
             break;
         }
         const float2* col = buf(st) + threadIdx.x;
@@ -592,9 +599,11 @@ wire_conv_impacts_tma_kernel(const __grid_constant__ TmaConvUnits U, int impacts
                 }
             }
             if (im == impacts - 1) {
+                float2* __restrict__ Y = static_cast<float2*>(U.Y[T.u]);
+                const int nw = U.nwires[T.u];
 #pragma unroll
                 for (int b = 0; b < B; ++b)
-                    if (w0 + b < nwires) Y[(int64_t)(w0 + b) * stride + k] = make_float2(k1[b] - k3[b], k1[b] + k2[b]);
+                    if (T.w0 + b < nw) Y[(int64_t)(T.w0 + b) * stride + k] = make_float2(k1[b] - k3[b], k1[b] + k2[b]);
             }
         }
         __syncthreads();   // buffer st is free for the copy issued next iteration
@@ -637,28 +646,45 @@ __global__ void bounded_wait_selftest_kernel(uint32_t* status, int iters, unsign
 
 bool tma_available() { return encode_fn() != nullptr; }
 
+// One launch over units [u0, u1) of cb (at most kMaxUnits / I of them, one
+// tensor map per unit and impact).
 template <int B>
-static cudaError_t launch_impacts_tma(TmaConvUnits& U, const float2* X, float2* Y, const float2* Rt, int nwires,
-                                      int impacts, int nfreq, int64_t stride, int kw, int center, unsigned* sched,
-                                      uint32_t* status, cudaStream_t s) {
+static cudaError_t launch_impacts_tma(const ConvBatch& cb, int u0, int u1, int impacts, int nfreq, int64_t stride,
+                                      int kw, int center, unsigned* sched, uint32_t* status, cudaStream_t s) {
     constexpr int K = kMaxRespWires;
     constexpr int ROWS = B + K - 1;
     const PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
     if (!enc) return cudaErrorNotSupported;
-    for (int i = 0; i < impacts; ++i) {
-        // impact i: fine rows i, i + I, i + 2I, ... (one per wire)
-        const cuuint64_t dims[2] = {(cuuint64_t)(2 * stride), (cuuint64_t)nwires};
-        const cuuint64_t strides[1] = {(cuuint64_t)(2 * stride * sizeof(float)) * (cuuint64_t)impacts};
-        const cuuint32_t box[2] = {2 * kCols, ROWS};
-        const cuuint32_t estr[2] = {1, 1};
-        const CUresult r = enc(&U.map[i], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2,
-                               const_cast<float2*>(X) + (int64_t)i * stride, dims, strides, box, estr,
-                               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-        if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
-    }
+    TmaConvUnits U;
+    U.n = u1 - u0;
+    U.prefix[0] = 0;
+    U.epoch = cb.epoch;
     const int nkblocks = (nfreq + kCols - 1) / kCols;
-    const int ntiles = nkblocks * ((nwires + B - 1) / B);
+    for (int j = 0; j < U.n; ++j) {
+        const int u = u0 + j;
+        const int nwires = cb.nwires[u];
+        if (nwires <= 0) return cudaErrorInvalidValue;
+        U.nwires[j] = nwires;
+        U.Y[j] = cb.Y[u];
+        U.Rt[j] = cb.Rt[u];
+        U.rows[j] = cb.rows[u];
+        U.prefix[j + 1] = U.prefix[j] + nkblocks * ((nwires + B - 1) / B);
+        for (int i = 0; i < impacts; ++i) {
+            // impact i: fine rows i, i + I, i + 2I, ... (one per wire)
+            const cuuint64_t dims[2] = {(cuuint64_t)(2 * stride), (cuuint64_t)nwires};
+            const cuuint64_t strides[1] = {(cuuint64_t)(2 * stride * sizeof(float)) * (cuuint64_t)impacts};
+            const cuuint32_t box[2] = {2 * kCols, ROWS};
+            const cuuint32_t estr[2] = {1, 1};
+            const CUresult r = enc(&U.map[j * impacts + i], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2,
+                                   const_cast<float2*>(static_cast<const float2*>(cb.X[u])) + (int64_t)i * stride,
+                                   dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                                   CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+            if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+        }
+    }
+    const int ntiles = U.prefix[U.n];
+    if (ntiles <= 0) return cudaSuccess;
     const int smem = 2 * ROWS * kCols * (int)sizeof(float2);
     cudaError_t e = cudaFuncSetAttribute((const void*)wire_conv_impacts_tma_kernel<K, B>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
@@ -669,26 +695,27 @@ static cudaError_t launch_impacts_tma(TmaConvUnits& U, const float2* X, float2* 
     if (per_sm < 1) per_sm = 1;
     int grid = num_sms() * per_sm;
     if (grid > ntiles) grid = ntiles;
-    wire_conv_impacts_tma_kernel<K, B><<<grid, kCols, smem, s>>>(U, impacts, nwires, nfreq, stride, kw, center,
-                                                                 nkblocks, Y, Rt, sched, status);
+    wire_conv_impacts_tma_kernel<K, B><<<grid, kCols, smem, s>>>(U, impacts, nfreq, stride, kw, center, sched,
+                                                                 status);
     return cudaGetLastError();
 }
 
-cudaError_t launch_wire_conv_impacts_tma(const float2* X, float2* Y, const float2* Rt, int nwires, int impacts,
-                                         int nfreq, int64_t stride, int kw, int center, unsigned* sched,
-                                         uint32_t* status, cudaStream_t s, int variant, const mark_t* rows,
-                                         const mark_t* epoch) {
-    if (impacts < 1 || impacts > kMaxUnits || nwires <= 0 || nfreq <= 0 || variant < 0 ||
-        variant >= kImpactConvVariants || (rows && !epoch) || !sched || !status)
+cudaError_t launch_wire_conv_impacts_tma(const ConvBatch& cb, int impacts, int nfreq, int64_t stride, int kw,
+                                         int center, unsigned* sched, uint32_t* status, cudaStream_t s, int variant) {
+    if (impacts < 1 || impacts > kMaxUnits || nfreq <= 0 || variant < 0 || variant >= kImpactConvVariants ||
+        !sched || !status || cb.n < 0 || cb.n > kMaxUnits)
         return cudaErrorInvalidValue;
-    TmaConvUnits U;
-    U.n = impacts;
-    for (int i = 0; i < impacts; ++i) U.rows[i] = nullptr;
-    U.rows[0] = rows;
-    U.epoch = epoch;
-    return variant == 1
-               ? launch_impacts_tma<32>(U, X, Y, Rt, nwires, impacts, nfreq, stride, kw, center, sched, status, s)
-               : launch_impacts_tma<16>(U, X, Y, Rt, nwires, impacts, nfreq, stride, kw, center, sched, status, s);
+    for (int u = 0; u < cb.n; ++u)
+        if (cb.rows[u] && !cb.epoch) return cudaErrorInvalidValue;
+    const int per_launch = kMaxUnits / impacts;   // tensor maps of a launch: units x impacts
+    for (int u0 = 0; u0 < cb.n; u0 += per_launch) {
+        const int u1 = u0 + per_launch < cb.n ? u0 + per_launch : cb.n;
+        const cudaError_t e =
+            variant == 1 ? launch_impacts_tma<32>(cb, u0, u1, impacts, nfreq, stride, kw, center, sched, status, s)
+                         : launch_impacts_tma<16>(cb, u0, u1, impacts, nfreq, stride, kw, center, sched, status, s);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 cudaError_t launch_bounded_wait_selftest(uint32_t* status, int iters, unsigned long long* cycles, cudaStream_t s) {

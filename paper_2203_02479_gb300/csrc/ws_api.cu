@@ -306,22 +306,41 @@ bool marks_apply(const ws_plane* pl) {
            (pl->impacts == 1 || ws::tma_available());
 }
 
-// The impact wire convolution of one plane (fine spectra X -> Y), with the
-// call's marks or without (rows null); the launch is traced on plane `tr`.
-ws_status impacts_wconv(ws_plane* pl, ws_plane* tr, const float2* X, float2* Y, const ws::mark_t* rows,
-                        const ws::mark_t* epoch, unsigned* sched, cudaStream_t s, int variant) {
+// The impact wire convolution of the units of cb (fine spectra X -> Y; the
+// planes share I, the convolution mode and the response width, pl is one
+// of them), with the call's marks or without (rows null); the launches are
+// traced on plane `tr`.
+ws_status impacts_wconv(ws_plane* pl, ws_plane* tr, const ws::ConvBatch& cb, unsigned* sched, cudaStream_t s,
+                        int variant) {
     const ws_plane_desc& d = pl->desc;
     if (d.conv_mode == WS_CONV_LINEAR && ws::tma_available()) {
-        WS_LAUNCH(tr, K_WCONV, s, ws::launch_wire_conv_impacts_tma(X, Y, pl->Rt, d.nwires, pl->impacts, pl->nfreq,
-                                                                   pl->fstride, d.resp_nwires, d.resp_wire_center,
-                                                                   sched, pl->status, s, variant, rows, epoch));
-    } else {
-        if (rows) return WS_ERR_UNSUPPORTED_SIZE;
-        WS_LAUNCH(tr, K_WCONV, s, ws::launch_wire_conv_impacts(X, Y, pl->Rt, d.nwires, pl->impacts, pl->nfreq,
-                                                               pl->fstride, d.resp_nwires, d.resp_wire_center,
-                                                               d.conv_mode == WS_CONV_CIRCULAR, s));
+        WS_LAUNCH(tr, K_WCONV, s, ws::launch_wire_conv_impacts_tma(cb, pl->impacts, pl->nfreq, pl->fstride,
+                                                                   d.resp_nwires, d.resp_wire_center, sched,
+                                                                   pl->status, s, variant));
+        return WS_OK;
+    }
+    for (int j = 0; j < cb.n; ++j) {
+        if (cb.rows[j]) return WS_ERR_UNSUPPORTED_SIZE;
+        WS_LAUNCH(tr, K_WCONV, s, ws::launch_wire_conv_impacts((const float2*)cb.X[j], (float2*)cb.Y[j],
+                                                               (const float2*)cb.Rt[j], cb.nwires[j], pl->impacts,
+                                                               pl->nfreq, pl->fstride, d.resp_nwires,
+                                                               d.resp_wire_center, d.conv_mode == WS_CONV_CIRCULAR,
+                                                               s));
     }
     return WS_OK;
+}
+
+// One plane's spectra as a one-unit convolution batch (marks optional).
+ws::ConvBatch plane_conv(const ws_plane* pl, const ws::mark_t* rows, const ws::mark_t* epoch) {
+    ws::ConvBatch cb;
+    cb.n = 1;
+    cb.X[0] = pl->X;
+    cb.Y[0] = pl->Y;
+    cb.Rt[0] = pl->Rt;
+    cb.nwires[0] = pl->desc.nwires;
+    cb.rows[0] = rows;
+    cb.epoch = epoch;
+    return cb;
 }
 
 // ws_simulate's FP32 / compensated path with active rows: mark, clear the
@@ -363,19 +382,11 @@ ws_status simulate_marked(ws_plane* pl, ws::RasterArgs a, float* out, cudaStream
     fb.rows[0] = ib.rows[0] = pl->row_cls;
     WS_LAUNCH(pl, K_FWD, s, ws::launch_fwd_rows_batch(pl->plan, pl->tw, fb, d.nticks, d.nticks, pl->fstride,
                                                       pl->nfreq, 1.0f, s));
+    const ws::ConvBatch cb = plane_conv(pl, pl->rows, pl->rows_epoch);
     if (I > 1) {
-        const ws_status st =
-            impacts_wconv(pl, pl, pl->X, pl->Y, pl->rows, pl->rows_epoch, pl->sched, s, pl->wconv_variant);
+        const ws_status st = impacts_wconv(pl, pl, cb, pl->sched, s, pl->wconv_variant);
         if (st != WS_OK) return st;
     } else {
-        ws::ConvBatch cb;
-        cb.n = 1;
-        cb.X[0] = pl->X;
-        cb.Y[0] = pl->Y;
-        cb.Rt[0] = pl->Rt;
-        cb.nwires[0] = d.nwires;
-        cb.rows[0] = pl->rows;
-        cb.epoch = pl->rows_epoch;
         WS_LAUNCH(pl, K_WCONV, s, ws::launch_wire_conv_batch(cb, pl->nfreq, pl->fstride, d.resp_nwires,
                                                              d.resp_wire_center, 0, s, pl->wconv_variant, pl->status));
     }
@@ -391,7 +402,7 @@ ws_status convolve_impl(ws_plane* pl, const float* grid, float* out, cudaStream_
                                                 pl->X, pl->fstride, pl->nfreq, 1.0f, s, pl->status));
     if (pl->impacts > 1) {
         const ws_status st =
-            impacts_wconv(pl, pl, pl->X, pl->Y, nullptr, nullptr, pl->sched, s, pl->wconv_variant);
+            impacts_wconv(pl, pl, plane_conv(pl, nullptr, nullptr), pl->sched, s, pl->wconv_variant);
         if (st != WS_OK) return st;
     } else {
         WS_LAUNCH(pl, K_WCONV, s, ws::launch_wire_conv(pl->X, pl->Y, pl->Rt, d.nwires, pl->nfreq, pl->fstride,
@@ -539,7 +550,7 @@ ws_status ws_plane_create(const ws_plane_desc* desc, const float* response_dev, 
         for (int v = 0; v < nvar; ++v) best_of[v] = 1e30f;
         auto conv = [&](int v) {
             if (lay.impacts > 1)
-                return ws::launch_wire_conv_impacts_tma(pl->X, pl->Y, pl->Rt, desc->nwires, lay.impacts, lay.nfreq,
+                return ws::launch_wire_conv_impacts_tma(plane_conv(pl, nullptr, nullptr), lay.impacts, lay.nfreq,
                                                         lay.fstride, desc->resp_nwires, desc->resp_wire_center,
                                                         pl->sched, pl->status, s, v);
             return ws::launch_wire_conv(pl->X, pl->Y, pl->Rt, desc->nwires, lay.nfreq, lay.fstride,
@@ -1252,14 +1263,11 @@ ws_status batch_waves(ws_plane* const* planes, int nplanes, const ws_depos* depo
         WS_LAUNCH(p0, K_RASTER_SCATTER, s, ws::launch_raster_scatter_batch(rb, L, s));
         WS_LAUNCH(p0, K_FWD, s, ws::launch_fwd_rows_batch(p0->plan, p0->tw, fb, d0.nticks, d0.nticks, p0->fstride,
                                                           p0->nfreq, 1.0f, s));
-        if (I > 1) {   // one launch per unit (its I tensor maps)
-            for (int j = 0; j < nu; ++j) {
-                const ws_status st = impacts_wconv(planes[(u0 + j) % nplanes], p0, (const float2*)cb.X[j],
-                                                   (float2*)cb.Y[j], m.rows[j], m.rows[j] ? m.epoch : nullptr,
-                                                   (unsigned*)(base + lay.off_counters + kBatchSched), s,
-                                                   wconv < ws::kImpactConvVariants ? wconv : 0);
-                if (st != WS_OK) return st;
-            }
+        if (I > 1) {   // the wave's units in as few launches as their tensor maps allow
+            cb.epoch = marked ? m.epoch : nullptr;
+            const ws_status st = impacts_wconv(p0, p0, cb, (unsigned*)(base + lay.off_counters + kBatchSched), s,
+                                               wconv < ws::kImpactConvVariants ? wconv : 0);
+            if (st != WS_OK) return st;
         } else {
             WS_LAUNCH(p0, K_WCONV, s, ws::launch_wire_conv_batch(cb, p0->nfreq, p0->fstride, d0.resp_nwires,
                                                                  d0.resp_wire_center, circ, s, wconv, p0->status));

@@ -319,16 +319,18 @@ cudaError_t launch_bounded_wait_selftest(uint32_t* status, int iters, unsigned l
 cudaError_t launch_wire_conv_tma(const ConvBatch& cb, int nfreq, int64_t stride, int kw, int center, int variant,
                                  uint32_t* status, cudaStream_t s);
 // The impact wire convolution fed by TMA (linear mode; a copy that never
-// lands sets WS_DEV_TIMEOUT in *status); variant 0 / 1: blocks of 16 / 32
-// output wires.  CTAs claim blocks from sched[0] (two zeroed words, left
-// zeroed by the launch; launches sharing them must not overlap).  With
-// active-row marks (one per wire, and the call's epoch) blocks whose outputs
-// are all dead are skipped and their Y rows not written.
+// lands sets WS_DEV_TIMEOUT in *status) over the units of cb (X: I x
+// nwires fine rows each; units share I, the frequency layout and the
+// response width), as few launches as its tensor maps allow; variant 0 / 1:
+// blocks of 16 / 32 output wires.  CTAs claim blocks from sched[0] (two
+// zeroed words, left zeroed by each launch; launches sharing them must not
+// overlap).  With active-row marks (cb.rows, one per wire, and cb.epoch)
+// blocks whose outputs are all dead are skipped and their Y rows not
+// written.
 constexpr int kImpactConvVariants = 2;
-cudaError_t launch_wire_conv_impacts_tma(const float2* X, float2* Y, const float2* Rt, int nwires, int impacts,
-                                         int nfreq, int64_t stride, int kw, int center, unsigned* sched,
-                                         uint32_t* status, cudaStream_t s, int variant = 0,
-                                         const mark_t* rows = nullptr, const mark_t* epoch = nullptr);
+cudaError_t launch_wire_conv_impacts_tma(const ConvBatch& cb, int impacts, int nfreq, int64_t stride, int kw,
+                                         int center, unsigned* sched, uint32_t* status, cudaStream_t s,
+                                         int variant = 0);
 
 // Hand-over list of depos whose patches are too large for the lane-per-depo
 // raster kernel (workspace-resident; count and done must start at zero and
