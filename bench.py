@@ -842,7 +842,9 @@ def impacts_leg(wiresim, dev, stream, flush, steps: int, impacts: int = 10):
         pl.close()
     return {"workload": w.name + f", {impacts} sub-pitch response positions per plane", "ms_per_step": ms,
             "value": ndp / (ms * 1e-3), "unit": UNIT, "kernels_ms_per_step": kern,
-            "per_plane_ms_per_step": plane_ms, "impact_wire_blocks": [32 if v == 1 else 16 for v in variants],
+            "per_plane_ms_per_step": plane_ms,
+            "impact_wire_conv_tiles": [("16", "32", "16", "32")[v] + (" wires x 128" if v < 2 else " wires x 64")
+                                       + " frequencies" for v in variants],
             "path": "ws_simulate_batch over the event's planes (fine grids of nwires*10 rows, active wires, "
                     "impact wire convolution per plane)"}
 

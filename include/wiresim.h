@@ -101,8 +101,9 @@ typedef struct {
                                  raster bins the pitch axis at pitch/I into
                                  a fine grid of nwires*I rows (fine row
                                  w*I + i), and M = sum_i R_i (*) S_i.  FP32
-                                 only; ws_simulate_batch and the adjoint
-                                 reject such planes                         */
+                                 only; ws_simulate and ws_simulate_batch
+                                 take them (a batch's planes share I), the
+                                 adjoint rejects them                       */
 } ws_plane_desc;
 
 /* Depos of one event as seen by one plane: structure of arrays of float32
@@ -188,7 +189,10 @@ typedef struct {
                                    6, 7), Karatsuba three-product taps
                                    (odd), tiles by TMA (4..7) or TMA chunks
                                    into a ring kept along a run of wire
-                                   blocks (8, 9); 4..9 linear mode only     */
+                                   blocks (8, 9); 4..9 linear mode only.
+                                   Impact planes (linear mode): blocks of
+                                   16 / 32 wires by 128 (0 / 1) or 64
+                                   (2 / 3) frequencies                      */
     int32_t row_fft_fixed_shape; /* 1: this L_t's FP32 tick-axis transforms
                                    run kernels compiled for its radix plan
                                    (each row pair fetched into shared memory
@@ -219,8 +223,8 @@ ws_status ws_plane_workspace_bytes(const ws_plane_desc* desc, size_t* bytes);
  * 256-byte aligned) and compute the response spectrum once (the transform
  * of R in Eq. 2) on `stream`.  It also autotunes the wire-convolution
  * kernel by timing its variants on the plane's buffers, which SYNCHRONISES
- * `stream` once (impact planes have one wire-convolution kernel and skip
- * it).  response_dev: K_w x K_t float32, row-major, row r holding wire
+ * `stream` once (impact planes time their four TMA kernels in linear mode
+ * and skip the timing otherwise).  response_dev: K_w x K_t float32, row-major, row r holding wire
  * offset r - resp_wire_center, column j tick offset j (causal); on an
  * impact plane I such slices, slice i first-index-major.  The response is
  * read during this call's stream work only.
@@ -281,8 +285,10 @@ ws_status ws_convolve(ws_plane* plane, const float* grid_dev, float* out_dev, vo
  * 6250, 6000, 6400, 3200 or 1200) only the wire rows a depo can reach are
  * cleared and transformed, and waveform rows out of the response's reach
  * of all of them are written as zeros: the same result as transforming
- * every row (an untouched row is zero through Eq. 2's linear stages).  A
- * per-plane epoch in the workspace, advanced on the device, keeps calls
+ * every row (an untouched row is zero through Eq. 2's linear stages).  On
+ * an impact plane (I > 1) the raster fills the plane's fine grid and whole
+ * wires are marked (their I fine rows cleared and transformed together).
+ * A per-plane epoch in the workspace, advanced on the device, keeps calls
  * and CUDA graph replays apart; calls on one plane must not overlap. */
 ws_status ws_simulate(ws_plane* plane, const ws_depos* depos, const ws_params* params,
                       float* out_dev, void* stream);
@@ -312,9 +318,10 @@ ws_status ws_convolve_noalloc(const ws_plane_desc* desc, const float* response_d
 
 /* Device workspace of ws_simulate_batch: three wave slots, each a
  * large-patch hand-over list and, per unit of a wave, two spectra (max
- * nwires x (L_t/2+1) complex64) and a row mark and row class per wire.
- * units_per_wave: 1 .. 32, or 0 for the largest wave (32 units), which
- * holds every wave size. */
+ * nwires x (L_t/2+1) complex64; the first I times that on impact planes),
+ * a row mark and row class per wire, and on impact planes a fine grid of
+ * I x max nwires x nticks floats.  units_per_wave: 1 .. 32, or 0 for the
+ * largest wave (32 units), which holds every wave size. */
 ws_status ws_batch_workspace_bytes(ws_plane* const* planes, int nplanes, int units_per_wave,
                                    size_t* bytes);
 
@@ -327,7 +334,10 @@ ws_status ws_batch_workspace_bytes(ws_plane* const* planes, int nplanes, int uni
  * throughput, Sec. 3.3).  depos[u] are unit u's depos; out_dev[u] its
  * nwires(p) x nticks output (cleared, then simulated); event e uses
  * event_id = params->event_id + e.  All planes must share the transform
- * length, tick count and response shape (else WS_ERR_UNSUPPORTED_SIZE).
+ * length, tick count, response shape and impact positions I (else
+ * WS_ERR_UNSUPPORTED_SIZE).  With I > 1 each unit rasters into a fine grid
+ * in its wave slot, marks whole wires, and the impact wire convolution runs
+ * once over the wave's units (units of up to 32 / I per launch).
  * Each plane's noise term (ws_plane_set_noise) is added as in ws_simulate.
  * Results equal ws_simulate unit by unit (up to summation order); units of
  * noise-free planes skip untouched wire rows as ws_simulate does, with the
@@ -419,9 +429,9 @@ ws_status ws_plane_sync(ws_plane* plane, void* stream, uint32_t* bits);
 ws_status ws_plane_clear_status(ws_plane* plane, void* stream);
 
 /* Override the autotuned wire-convolution kernel (0..9, see
- * ws_plane_info.wire_conv_variant; 4..9 need linear mode) for this plane's
- * calls and for batches whose first plane it is; all variants compute the
- * same sum. */
+ * ws_plane_info.wire_conv_variant; 4..9 need linear mode; impact planes
+ * 0..3, 1..3 in linear mode) for this plane's calls and for batches whose
+ * first plane it is; all variants compute the same sum. */
 ws_status ws_plane_set_wire_conv_variant(ws_plane* plane, int variant);
 
 /* Launch tracing (timing of each kernel with CUDA events).  With

@@ -500,12 +500,12 @@ cudaError_t launch_ring(const ConvBatch& cb, int nfreq, int64_t stride, int kw, 
 // tile's second-to-last impact.  sched[0] is the claim counter and sched[1]
 // counts finished CTAs; the last CTA to finish sets both back to zero (they
 // start at zero).  Waits are bounded as in the other TMA kernels.
-template <int K, int B>
-__global__ void __launch_bounds__(kCols)
+template <int K, int B, int C>
+__global__ void __launch_bounds__(C)
 wire_conv_impacts_tma_kernel(const __grid_constant__ TmaConvUnits U, int impacts, int nfreq, int64_t stride, int kw,
                              int center, unsigned* sched, uint32_t* status) {
     constexpr int ROWS = B + K - 1;
-    constexpr uint32_t TILE_BYTES = ROWS * kCols * sizeof(float2);
+    constexpr uint32_t TILE_BYTES = ROWS * C * sizeof(float2);
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ __align__(8) uint64_t bar[2];
     __shared__ int s_claim;
@@ -520,7 +520,7 @@ wire_conv_impacts_tma_kernel(const __grid_constant__ TmaConvUnits U, int impacts
         while (u + 1 < U.n && U.prefix[u + 1] <= t) ++u;
         const int tt = t - U.prefix[u];
         const int nwb = (U.nwires[u] + B - 1) / B;
-        return Tile{u, (tt / nwb) * kCols, (tt % nwb) * B};
+        return Tile{u, (tt / nwb) * C, (tt % nwb) * B};
     };
     auto issue = [&](int t, int im, int st) {
         const Tile T = decode(t);
@@ -586,7 +586,7 @@ wire_conv_impacts_tma_kernel(const __grid_constant__ TmaConvUnits U, int impacts
         if (k < nfreq) {
 #pragma unroll
             for (int uu = 0; uu < ROWS; ++uu) {
-                const float2 x = col[uu * kCols];
+                const float2 x = col[uu * C];
                 const float sab = x.x + x.y;
 #pragma unroll
                 for (int b = 0; b < B; ++b) {
@@ -648,7 +648,7 @@ bool tma_available() { return encode_fn() != nullptr; }
 
 // One launch over units [u0, u1) of cb (at most kMaxUnits / I of them, one
 // tensor map per unit and impact).
-template <int B>
+template <int B, int C>
 static cudaError_t launch_impacts_tma(const ConvBatch& cb, int u0, int u1, int impacts, int nfreq, int64_t stride,
                                       int kw, int center, unsigned* sched, uint32_t* status, cudaStream_t s) {
     constexpr int K = kMaxRespWires;
@@ -659,7 +659,7 @@ static cudaError_t launch_impacts_tma(const ConvBatch& cb, int u0, int u1, int i
     U.n = u1 - u0;
     U.prefix[0] = 0;
     U.epoch = cb.epoch;
-    const int nkblocks = (nfreq + kCols - 1) / kCols;
+    const int nkblocks = (nfreq + C - 1) / C;
     for (int j = 0; j < U.n; ++j) {
         const int u = u0 + j;
         const int nwires = cb.nwires[u];
@@ -673,7 +673,7 @@ static cudaError_t launch_impacts_tma(const ConvBatch& cb, int u0, int u1, int i
             // impact i: fine rows i, i + I, i + 2I, ... (one per wire)
             const cuuint64_t dims[2] = {(cuuint64_t)(2 * stride), (cuuint64_t)nwires};
             const cuuint64_t strides[1] = {(cuuint64_t)(2 * stride * sizeof(float)) * (cuuint64_t)impacts};
-            const cuuint32_t box[2] = {2 * kCols, ROWS};
+            const cuuint32_t box[2] = {2 * C, ROWS};
             const cuuint32_t estr[2] = {1, 1};
             const CUresult r = enc(&U.map[j * impacts + i], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2,
                                    const_cast<float2*>(static_cast<const float2*>(cb.X[u])) + (int64_t)i * stride,
@@ -685,17 +685,17 @@ static cudaError_t launch_impacts_tma(const ConvBatch& cb, int u0, int u1, int i
     }
     const int ntiles = U.prefix[U.n];
     if (ntiles <= 0) return cudaSuccess;
-    const int smem = 2 * ROWS * kCols * (int)sizeof(float2);
-    cudaError_t e = cudaFuncSetAttribute((const void*)wire_conv_impacts_tma_kernel<K, B>,
+    const int smem = 2 * ROWS * C * (int)sizeof(float2);
+    cudaError_t e = cudaFuncSetAttribute((const void*)wire_conv_impacts_tma_kernel<K, B, C>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, wire_conv_impacts_tma_kernel<K, B>, kCols, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, wire_conv_impacts_tma_kernel<K, B, C>, C, smem);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) per_sm = 1;
     int grid = num_sms() * per_sm;
     if (grid > ntiles) grid = ntiles;
-    wire_conv_impacts_tma_kernel<K, B><<<grid, kCols, smem, s>>>(U, impacts, nfreq, stride, kw, center, sched,
+    wire_conv_impacts_tma_kernel<K, B, C><<<grid, C, smem, s>>>(U, impacts, nfreq, stride, kw, center, sched,
                                                                  status);
     return cudaGetLastError();
 }
@@ -710,9 +710,14 @@ cudaError_t launch_wire_conv_impacts_tma(const ConvBatch& cb, int impacts, int n
     const int per_launch = kMaxUnits / impacts;   // tensor maps of a launch: units x impacts
     for (int u0 = 0; u0 < cb.n; u0 += per_launch) {
         const int u1 = u0 + per_launch < cb.n ? u0 + per_launch : cb.n;
-        const cudaError_t e =
-            variant == 1 ? launch_impacts_tma<32>(cb, u0, u1, impacts, nfreq, stride, kw, center, sched, status, s)
-                         : launch_impacts_tma<16>(cb, u0, u1, impacts, nfreq, stride, kw, center, sched, status, s);
+        auto run = [&](auto launch) { return launch(cb, u0, u1, impacts, nfreq, stride, kw, center, sched, status, s); };
+        cudaError_t e;
+        switch (variant) {
+            case 1: e = run(launch_impacts_tma<32, 128>); break;
+            case 2: e = run(launch_impacts_tma<16, 64>); break;
+            case 3: e = run(launch_impacts_tma<32, 64>); break;
+            default: e = run(launch_impacts_tma<16, 128>);
+        }
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;

@@ -322,12 +322,12 @@ cudaError_t launch_wire_conv_tma(const ConvBatch& cb, int nfreq, int64_t stride,
 // lands sets WS_DEV_TIMEOUT in *status) over the units of cb (X: I x
 // nwires fine rows each; units share I, the frequency layout and the
 // response width), as few launches as its tensor maps allow; variant 0 / 1:
-// blocks of 16 / 32 output wires.  CTAs claim blocks from sched[0] (two
+// blocks of 16 / 32 output wires by 128 frequencies, 2 / 3: the same by 64.  CTAs claim blocks from sched[0] (two
 // zeroed words, left zeroed by each launch; launches sharing them must not
 // overlap).  With active-row marks (cb.rows, one per wire, and cb.epoch)
 // blocks whose outputs are all dead are skipped and their Y rows not
 // written.
-constexpr int kImpactConvVariants = 2;
+constexpr int kImpactConvVariants = 4;
 cudaError_t launch_wire_conv_impacts_tma(const ConvBatch& cb, int impacts, int nfreq, int64_t stride, int kw,
                                          int center, unsigned* sched, uint32_t* status, cudaStream_t s,
                                          int variant = 0);

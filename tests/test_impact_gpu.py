@@ -98,7 +98,7 @@ def test_impact_planes_rejected_where_unsupported(ws):
     with pytest.raises(ws.WiresimError):
         pl.simulate(d, ws.Params(precision=ws.WS_PREC_FP64))
     with pytest.raises(ws.WiresimError):
-        pl.set_wire_conv_variant(2)      # impact planes: wire blocks of 16 or 32 (0, 1)
+        pl.set_wire_conv_variant(4)      # impact planes: four tile shapes (0 .. 3)
     import torch
     with pytest.raises(ws.WiresimError):
         pl.backward(d, ws.Params(), torch.zeros((16, 500), device="cuda"))

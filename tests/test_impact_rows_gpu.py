@@ -9,7 +9,7 @@ results must equal the unmarked route (ws_rasterize + ws_scatter into the
 fine grid + ws_convolve, which transforms every fine row) and the FP64
 oracle:
   * expected-value mode: relative L2 <= 1e-5 against the oracle's impact
-    simulation, with both wire-block sizes of the TMA impact kernel;
+    simulation, with each tile shape of the TMA impact kernel;
   * binomial mode: the same integers in the fine grid, so relative L2 <=
     1e-6 against the unmarked route (the transforms' rounding);
   * rows beyond the response's reach from every band are exactly zero and
@@ -94,7 +94,7 @@ def unmarked(pl, dd, params):
 BANDS = [[(30, 42)], [(0, 5), (110, 120)], [(60, 61)]]
 
 
-@pytest.mark.parametrize("variant", [0, 1])
+@pytest.mark.parametrize("variant", [0, 1, 2, 3])
 @pytest.mark.parametrize("bands", BANDS)
 def test_expected_value_band_matches_oracle(ws, bands, variant):
     R = inputs.impact_response("bipolar", impacts=I)
