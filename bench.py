@@ -808,8 +808,10 @@ def impacts_leg(wiresim, dev, stream, flush, steps: int, impacts: int = 10):
     the raster bins the pitch axis at pitch/10, the forward transform runs
     over the marked wires' 10 fine rows each, and the impact wire
     convolution sums the positions' taps.  Timed as one ws_simulate_batch
-    over the event's three planes (the leg's value) and as one ws_simulate
-    per plane."""
+    over the event's three planes at the wave size the library's autotuner
+    picks (the leg's value; waves of one plane on the library's three
+    streams overlap one plane's raster with another's transforms) and as
+    one ws_simulate per plane."""
     import torch
     w = make_workload("three_planes", 0)
     kinds = ["bipolar", "bipolar", "unipolar"]
@@ -823,7 +825,8 @@ def impacts_leg(wiresim, dev, stream, flush, steps: int, impacts: int = 10):
         for pl, d, o in zip(planes, depos, outs):
             pl.simulate(d, params, out=o, stream=stream)
 
-    batch = wiresim.Batch(planes, [depos], params, units_per_wave=len(planes), device=dev, outs=outs)
+    batch = wiresim.Batch(planes, [depos], params, units_per_wave=0, device=dev, outs=outs)
+    upw = batch.autotune(stream)
 
     def batched():
         batch.run(stream)
@@ -842,11 +845,11 @@ def impacts_leg(wiresim, dev, stream, flush, steps: int, impacts: int = 10):
         pl.close()
     return {"workload": w.name + f", {impacts} sub-pitch response positions per plane", "ms_per_step": ms,
             "value": ndp / (ms * 1e-3), "unit": UNIT, "kernels_ms_per_step": kern,
-            "per_plane_ms_per_step": plane_ms,
+            "per_plane_ms_per_step": plane_ms, "units_per_wave": upw,
             "impact_wire_conv_tiles": [("16", "32", "16", "32")[v] + (" wires x 128" if v < 2 else " wires x 64")
                                        + " frequencies" for v in variants],
-            "path": "ws_simulate_batch over the event's planes (fine grids of nwires*10 rows, active wires, "
-                    "impact wire convolution per plane)"}
+            "path": "ws_simulate_batch over the event's planes, autotuned waves (fine grids of nwires*10 rows, "
+                    "active wires, impact wire convolution over a wave's planes)"}
 
 
 def adjoint_leg(wiresim, dev, stream, flush, steps: int):

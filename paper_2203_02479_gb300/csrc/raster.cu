@@ -541,8 +541,9 @@ raster_small_kernel(const __grid_constant__ RasterUnits U, ws_patches pt, long l
     __shared__ W s_wx[NW][G][SW + 1];
     __shared__ unsigned char s_start[NW][G];   // a round's item lane -> depo slot starting there
     __shared__ float s_recip[kExactCap + 1];
-    // drawing bins of a round (at most four per lane): grid index, N, Philox word
-    __shared__ uint32_t s_eidx[NW][128];
+    // drawing bins of a round (at most four per lane): N and Philox word in,
+    // survivor count out
+    __shared__ int s_res[NW][128];
     __shared__ uint32_t s_en[NW][128];
     __shared__ uint32_t s_ew[NW][128];
     extern __shared__ float s_cdf[];     // exact-branch CDF rows 1 .. cdf_rows for unit 0's survival probability
@@ -649,9 +650,16 @@ raster_small_kernel(const __grid_constant__ RasterUnits U, ws_patches pt, long l
             // Philox block; the bins that draw are compacted with their words
             // into a per-warp list, normal-approximation bins first, so that a
             // warp runs one sampler at a time (only the entry straddling the
-            // two kinds diverges).
+            // two kinds diverges).  The survivor counts go back through the
+            // list to the quad's lane, which adds the quad's four bins to the
+            // grid with one 16-byte atomic (rows of a multiple of four ticks
+            // on a 16-byte aligned grid): the lanes of a round hold
+            // consecutive quads of a few patch rows, so these atomics touch a
+            // few sectors each, where adds from the compacted list would
+            // scatter over as many sectors as lanes.
             const unsigned lt = (1u << lane) - 1u;
             const uint32_t qstride = (uint32_t)((a.nticks + 3) >> 2);
+            const bool vec4 = P == 0 && (a.nticks & 3) == 0 && ((uintptr_t)grid & 15u) == 0;
             for (int gb = 0; gb < total; gb += 32) {
                 const int g = gb + lane;
                 int N[4] = {0, 0, 0, 0};
@@ -687,27 +695,40 @@ raster_small_kernel(const __grid_constant__ RasterUnits U, ws_patches pt, long l
                     nn += __popc(nbal[j]);
                     ne += __popc(ebal[j]);
                 }
+                int pos[4];
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
+                    pos[j] = -1;
                     if (N[j] > 0) {
-                        const int pos = N[j] > a.exact_max ? nbef[j] + __popc(nbal[j] & lt)
-                                                           : nn + ebef[j] + __popc(ebal[j] & lt);
-                        s_eidx[wib][pos] = first + (uint32_t)j;
-                        s_en[wib][pos] = (uint32_t)N[j];
-                        s_ew[wib][pos] = word_of(x, j);
+                        pos[j] = N[j] > a.exact_max ? nbef[j] + __popc(nbal[j] & lt)
+                                                    : nn + ebef[j] + __popc(ebal[j] & lt);
+                        s_en[wib][pos[j]] = (uint32_t)N[j];
+                        s_ew[wib][pos[j]] = word_of(x, j);
                     }
                 }
                 __syncwarp();
                 // the two samplers in passes of their own: a pass never
                 // runs both (a pass straddling the two kinds would)
                 for (int it = lane; it < nn; it += 32)
-                    emit<P>(a, grid, (int64_t)s_eidx[wib][it], (W)normal_word<P>(s_ew[wib][it], (int)s_en[wib][it], a));
+                    s_res[wib][it] = normal_word<P>(s_ew[wib][it], (int)s_en[wib][it], a);
                 const int ntot = nn + ne;
                 for (int it = nn + lane; it < ntot; it += 32) {
                     const int n = (int)s_en[wib][it];
                     const uint32_t xw = s_ew[wib][it];
-                    const int c = cdf ? invert_binomial_table(n, xw, a, cdf) : invert_binomial(n, xw, a, s_recip);
-                    emit<P>(a, grid, (int64_t)s_eidx[wib][it], (W)c);
+                    s_res[wib][it] = cdf ? invert_binomial_table(n, xw, a, cdf) : invert_binomial(n, xw, a, s_recip);
+                }
+                __syncwarp();
+                int c[4];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) c[j] = pos[j] >= 0 ? s_res[wib][pos[j]] : 0;
+                if ((c[0] | c[1] | c[2] | c[3]) != 0) {
+                    if (vec4) {
+                        atomicAdd(reinterpret_cast<float4*>(grid + first),
+                                  make_float4((float)c[0], (float)c[1], (float)c[2], (float)c[3]));
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) emit<P>(a, grid, (int64_t)first + j, (W)c[j]);
+                    }
                 }
                 __syncwarp();
             }
