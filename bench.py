@@ -56,7 +56,7 @@ NUM_SMS_GB300 = 152
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # 152 SMs x 128 FP32 lanes x FMA x max SM clock
 INT_MUL_PEAK_T = 152 * 64 * 2.070e9 / 1e12          # 152 SMs x 64 INT32 multiply lanes x max SM clock
 PHILOX_MULS = 40    # 32-bit multiplies per Philox4x32-10 block: 10 rounds x 2 products x (low, high)
-WORKLOADS = ("batched", "three_planes", "single_plane", "large")
+WORKLOADS = ("batched", "three_planes", "single_plane", "large", "impacts")
 
 
 def _peaks():
@@ -239,6 +239,8 @@ def make_workload(name: str, rank: int):
         return inputs.single_plane(seed=1000 + 7919 * rank)
     if name == "large":
         return inputs.large_planes(seed=1004 + 7919 * rank)
+    if name == "impacts":
+        return inputs.three_planes_impacts(seed=1001 + 7919 * rank)
     raise SystemExit(f"unknown workload {name}")
 
 
@@ -254,29 +256,33 @@ class UnitSpec:
     library marks them), `need` rows whose spectra the wire convolution may
     read (within K_w - 1 wires of a touched row) and `live` output rows (a
     touched row within the response window).  Without active rows (noise
-    on, circular mode, no fixed-shape transform) every row counts."""
+    on, circular mode, no fixed-shape transform) every row counts.  On an
+    impact plane (`imp` sub-pitch positions) the row counts are wires, each
+    with `imp` fine rows in the grid and the first spectra."""
 
-    def __init__(self, nw, nt, nf, L, kw, nd, touched=None, need=None, live=None):
+    def __init__(self, nw, nt, nf, L, kw, nd, touched=None, need=None, live=None, imp=1):
         self.nw, self.nt, self.nf, self.L, self.kw, self.nd = nw, nt, nf, L, kw, nd
         self.touched = nw if touched is None else touched
         self.need = nw if need is None else need
         self.live = nw if live is None else live
+        self.imp = imp
 
 
 def algorithmic_bytes(kernel: str, u: UnitSpec) -> float:
     """Bytes a kernel's step must move at minimum (inputs read once, outputs
     written once), per launch on one unit, counting only the rows the
     kernel has to touch."""
+    I = u.imp
     if kernel == "raster_scatter":
-        return 12.0 * u.nd + 4.0 * u.touched * u.nt
+        return 12.0 * u.nd + 4.0 * I * u.touched * u.nt
     if kernel == "mark_rows":
         return 8.0 * u.nd
     if kernel == "memset_grid":
-        return 4.0 * u.touched * u.nt
+        return 4.0 * I * u.touched * u.nt
     if kernel == "fwd_rows":
-        return 4.0 * u.touched * u.nt + 8.0 * u.nf * u.need
+        return 4.0 * I * u.touched * u.nt + 8.0 * u.nf * I * u.need
     if kernel == "wire_conv":
-        return 8.0 * u.nf * (u.need + u.live) + 8.0 * u.nf * u.kw
+        return 8.0 * u.nf * (I * u.need + u.live) + 8.0 * u.nf * u.kw * I
     if kernel == "inv_rows":
         return 8.0 * u.nf * u.live + 4.0 * u.nw * u.nt
     return 0.0
@@ -289,11 +295,11 @@ def algorithmic_flops(kernel: str, u: UnitSpec) -> float:
     sum over the live rows."""
     import math
     if kernel == "fwd_rows":
-        return (u.touched + 1) // 2 * 5.0 * u.L * math.log2(u.L)
+        return (u.imp * u.touched + 1) // 2 * 5.0 * u.L * math.log2(u.L)
     if kernel == "inv_rows":
         return (u.live + 1) // 2 * 5.0 * u.L * math.log2(u.L)
     if kernel == "wire_conv":
-        return 8.0 * u.kw * u.nf * u.live
+        return 8.0 * u.kw * u.imp * u.nf * u.live
     return 0.0
 
 
@@ -309,14 +315,16 @@ def row_activity(pl, dd, params, marked: bool):
         sx = dd.sigma_x_mm.double()
     else:
         sx = torch.sqrt(2.0 * params.DT_mm2_us * torch.clamp(dd.t_us.double(), min=0.0))
-    pitch = 5.0
+    I = getattr(pl, "impacts", 1)
+    pitch = 5.0 / I    # the raster's pitch-axis bin (fine on an impact plane)
+    nb = nw * I
     pt = sx <= 1e-6 * pitch
     lo_e = torch.where(pt, x, x - 3.0 * sx)
     hi_e = torch.where(pt, x, x + 3.0 * sx)
-    lo = torch.clamp(torch.floor(lo_e / pitch), -1, nw).long().clamp(min=0) - 1
-    hi = torch.clamp(torch.floor(hi_e / pitch), -1, nw).long().clamp(max=nw - 1) + 1
-    lo = lo.clamp(min=0)
-    hi = hi.clamp(max=nw - 1)
+    lo = torch.clamp(torch.floor(lo_e / pitch), -1, nb).long().clamp(min=0) - 1
+    hi = torch.clamp(torch.floor(hi_e / pitch), -1, nb).long().clamp(max=nb - 1) + 1
+    lo = lo.clamp(min=0) // I       # the wires holding those bins
+    hi = hi.clamp(max=nb - 1) // I
     ok = lo <= hi
     diff = torch.zeros(nw + 1, dtype=torch.long, device=x.device)
     diff.index_add_(0, lo[ok], torch.ones_like(lo[ok]))
@@ -338,8 +346,11 @@ def oracle_unit(w, e: int, p: int):
     event id e, the plane's id) and Eq. 2's convolution."""
     import oracle
     sp, d = w.planes[p], w.events[e][p]
-    S = oracle.raster_scatter(d.q, d.x_mm, d.t_us, sp.nwires, sp.nticks, fluctuate=w.fluctuate,
-                              p=w.p_survive, seed=w.seed, event_id=e, plane_id=sp.plane_id)
+    kw = dict(fluctuate=w.fluctuate, p=w.p_survive, seed=w.seed, event_id=e, plane_id=sp.plane_id)
+    if np.asarray(sp.response).ndim == 3:   # sub-pitch impact positions
+        S = oracle.raster_scatter_impacts(d.q, d.x_mm, d.t_us, sp.nwires, sp.nticks, sp.response.shape[0], **kw)
+        return oracle.convolve_impacts(S, sp.response, 10)
+    S = oracle.raster_scatter(d.q, d.x_mm, d.t_us, sp.nwires, sp.nticks, **kw)
     return oracle.convolve_fft(S, sp.response, 10)
 
 
@@ -653,7 +664,7 @@ def unit_specs(planes_by_unit, depos_by_unit, params=None, marked=True):
     for pl, d in zip(planes_by_unit, depos_by_unit):
         t, n, l = row_activity(pl, d, params, marked)
         out.append(UnitSpec(pl.nwires, pl.nticks, pl.info.nfreq, pl.info.fft_len_tick, int(pl.response.shape[-2]),
-                            d.n, t, n, l))
+                            d.n, t, n, l, imp=getattr(pl, "impacts", 1)))
     return out
 
 
@@ -813,10 +824,8 @@ def impacts_leg(wiresim, dev, stream, flush, steps: int, impacts: int = 10):
     streams overlap one plane's raster with another's transforms) and as
     one ws_simulate per plane."""
     import torch
-    w = make_workload("three_planes", 0)
-    kinds = ["bipolar", "bipolar", "unipolar"]
-    planes = [wiresim.Plane(sp.nwires, sp.nticks, inputs.impact_response(kinds[i], impacts=impacts),
-                            plane_id=sp.plane_id, device=dev) for i, sp in enumerate(w.planes)]
+    w = inputs.three_planes_impacts(impacts=impacts)
+    planes = [wiresim.Plane(sp.nwires, sp.nticks, sp.response, plane_id=sp.plane_id, device=dev) for sp in w.planes]
     depos = [wiresim.DeviceDepos.from_plane_depos(d, device=dev) for d in w.events[0]]
     params = wiresim.Params(fluctuate=w.fluctuate, p_survive=w.p_survive, seed=w.seed)
     outs = [torch.empty((sp.nwires, sp.nticks), dtype=torch.float32, device=dev) for sp in w.planes]
@@ -843,7 +852,7 @@ def impacts_leg(wiresim, dev, stream, flush, steps: int, impacts: int = 10):
     ndp = sum(d.n for d in w.events[0])
     for pl in planes:
         pl.close()
-    return {"workload": w.name + f", {impacts} sub-pitch response positions per plane", "ms_per_step": ms,
+    return {"workload": w.name, "ms_per_step": ms,
             "value": ndp / (ms * 1e-3), "unit": UNIT, "kernels_ms_per_step": kern,
             "per_plane_ms_per_step": plane_ms, "units_per_wave": upw,
             "impact_wire_conv_tiles": [("16", "32", "16", "32")[v] + (" wires x 128" if v < 2 else " wires x 64")

@@ -281,6 +281,18 @@ def three_planes(n: int = 100_000, seed: int = 1001, *, fluctuate: bool = True,
                     fluctuate, p_survive, seed)
 
 
+def three_planes_impacts(n: int = 100_000, seed: int = 1001, *, impacts: int = 10, fluctuate: bool = True,
+                         p_survive: float = 0.7) -> Workload:
+    """The three-plane event on planes whose response depends on the
+    charge's position inside the pitch (``impacts`` sub-pitch positions,
+    ``impact_response`` slices)."""
+    w = three_planes(n, seed, fluctuate=fluctuate, p_survive=p_survive)
+    planes = [PlaneSpec(sp.nwires, sp.nticks,
+                        impact_response("bipolar" if g.bipolar else "unipolar", impacts=impacts), sp.plane_id)
+              for sp, g in zip(w.planes, THREE_PLANES)]
+    return Workload(f"three_planes_impacts{impacts}_800_800_960x6000", planes, w.events, fluctuate, p_survive, seed)
+
+
 def batched_events(nevents: int = 64, seed: int = 1002, *, lo: int = 1000, hi: int = 500000,
                    fluctuate: bool = True, p_survive: float = 0.7) -> Workload:
     """Many events on the three-plane detector with log-uniform depo counts."""

@@ -106,3 +106,25 @@ def test_algorithmic_bytes_with_active_rows():
     assert bench.algorithmic_bytes("raster_scatter", u) == 12 * 50_000 + 4 * 300 * nt
     dense = bench.UnitSpec(960, nt, nf, 6250, kw, 50_000)
     assert dense.touched == dense.need == dense.live == 960
+
+
+def test_impact_units_in_the_work_model_and_the_oracle_leg():
+    """An impact plane's unit counts I fine rows per wire in the grid, the
+    first spectra and the taps, and its oracle waveform is the impact
+    simulation (the fine raster and the per-position convolution)."""
+    import bench
+    import oracle
+    I = 4
+    u1 = bench.UnitSpec(100, 6000, 3126, 6250, 21, 1000, touched=60, need=80, live=70)
+    uI = bench.UnitSpec(100, 6000, 3126, 6250, 21, 1000, touched=60, need=80, live=70, imp=I)
+    assert bench.algorithmic_bytes("memset_grid", uI) == I * bench.algorithmic_bytes("memset_grid", u1)
+    assert bench.algorithmic_bytes("raster_scatter", uI) - 12.0 * 1000 == I * 4.0 * 60 * 6000
+    assert bench.algorithmic_bytes("fwd_rows", uI) == I * bench.algorithmic_bytes("fwd_rows", u1)
+    assert bench.algorithmic_bytes("wire_conv", uI) == 8.0 * 3126 * (I * 80 + 70) + 8.0 * 3126 * 21 * I
+    assert bench.algorithmic_bytes("inv_rows", uI) == bench.algorithmic_bytes("inv_rows", u1)
+    assert bench.algorithmic_flops("wire_conv", uI) == I * bench.algorithmic_flops("wire_conv", u1)
+    R = inputs.impact_response("unipolar", impacts=I, nticks=60)
+    d = inputs.uniform_depos(40, 16, seed=9, nticks=300)
+    w = inputs.Workload("tiny_impacts", [inputs.PlaneSpec(16, 300, R, 2)], [[d]], False, 1.0, 5)
+    M = bench.oracle_unit(w, 0, 0)
+    assert np.allclose(M, oracle.simulate_impacts(d.q, d.x_mm, d.t_us, 16, 300, R, 10), rtol=0, atol=1e-9)
