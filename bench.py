@@ -84,12 +84,12 @@ def kernel_source_hash() -> str:
 # for the kernel sources whose hash is given (see profiles/); published as
 # null once the sources change.
 NCU = {
-    "source_hash": "1b7b11bf9f2051da",
+    "source_hash": "da79e753fb0e9a3a",
     "workloads": {
         "three_planes_800_800_960x6000": {
-            "traffic": {"raster_scatter": 8.35e6, "fwd_rows": 47.49e6, "wire_conv": 62.31e6, "inv_rows": 55.38e6,
-                        "mark_rows": 2.41e6, "memset_grid": 0.20e6},
-            "issue_active": {"raster_scatter": 0.692, "fwd_rows": 0.645, "wire_conv": 0.627, "inv_rows": 0.627},
+            "traffic": {"raster_scatter": 8.37e6, "fwd_rows": 47.75e6, "wire_conv": 62.62e6, "inv_rows": 55.61e6,
+                        "mark_rows": 2.41e6, "memset_grid": 0.17e6},
+            "issue_active": {"raster_scatter": 0.720, "fwd_rows": 0.651, "wire_conv": 0.625, "inv_rows": 0.618},
             "note": "ncu --set full, one launch per kernel over the three planes (wire convolution kernel 9); "
                     "cold-cache DRAM bytes; profiles/kernels_three_planes.md",
         },
@@ -98,6 +98,11 @@ NCU = {
             "note": "no DRAM-counter capture of this step (about 5 GB on the device, above the capture size the "
                     "profiling rules allow); its launch list is profiles/launches_batched_64ev.md and the "
                     "three-plane event's counters profiles/kernels_three_planes.md",
+        },
+        "three_planes_impacts10_800_800_960x6000": {
+            "traffic": {}, "issue_active": {},
+            "note": "captured one plane per launch (waves of one unit), not a whole step: per-launch counters "
+                    "in profiles/kernels_impacts.md",
         },
     },
 }
