@@ -469,3 +469,27 @@ def simulate_backward(q, x_mm, t_us, nwires: int, nticks: int, R, wire_center: i
     S = raster_scatter(q, x_mm, t_us, nwires, nticks, **rkw)
     gR = response_grad(G, S, np.asarray(R).shape[0], np.asarray(R).shape[1], wire_center, circular)
     return gq, gx, gt, gDL, gDT, gR
+
+
+def simulate_backward_impacts(q, x_mm, t_us, nwires: int, nticks: int, R, wire_center: int, G, *,
+                              circular: bool = False, **kw):
+    """All gradients of L given G = dL/dM on a plane with sub-pitch impact
+    positions (R: impacts x K_w x K_t; the forward is ``simulate_impacts``,
+    M = sum_i R_i (*) S_i with S_i[w] = S_fine[w * I + i]):
+    dL/dS_fine[w * I + i] = (R_i's convolution adjoint of G)[w]; the depo
+    gradients of the raster on the fine grid (nwires * I bins at pitch / I,
+    the forward's own binning); dL/dR_i = the response gradient of G against
+    S_i.  Returns (gq, gx, gt, gDL, gDT, gR) with gR shaped like R.  Pinned
+    by central finite differences of the impact simulation's loss."""
+    R = np.asarray(R, dtype=np.float64)
+    I, kw_, kt_ = R.shape
+    rkw = {k: v for k, v in kw.items() if k in ("sig_t_us", "sig_x_mm", "pitch_mm", "tick_us", "nsig",
+                                                 "DL_", "DT_", "v", "p")}
+    pitch = rkw.pop("pitch_mm", PITCH_MM)
+    dS = np.zeros((nwires * I, nticks))
+    for i in range(I):
+        dS[i::I] = convolve_adjoint(G, R[i], wire_center, circular)
+    gq, gx, gt, gDL, gDT = depo_grads(q, x_mm, t_us, nwires * I, nticks, dS, pitch_mm=pitch / I, **rkw)
+    S = raster_scatter_impacts(q, x_mm, t_us, nwires, nticks, I, pitch_mm=pitch, **rkw)
+    gR = np.stack([response_grad(G, S[i::I], kw_, kt_, wire_center, circular) for i in range(I)])
+    return gq, gx, gt, gDL, gDT, gR

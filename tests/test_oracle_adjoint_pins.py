@@ -136,3 +136,64 @@ def test_full_backward_matches_finite_differences_of_the_loss():
             return loss(R=R2)
         est, err = _fd(f, 1e-3)
         assert gR[r, j] == pytest.approx(est, rel=1e-6, abs=10 * err)
+
+
+@pytest.mark.parametrize("circular", [False, True])
+def test_impact_backward_matches_finite_differences_of_the_loss(circular):
+    """An impact plane (I = 3 sub-pitch positions, slices that differ):
+    L = sum (M - T)^2 through the fine raster and the per-position
+    convolution; gradients for q, x, t of two depos (one near a sub-pitch
+    boundary), D_L, D_T and response entries of two slices."""
+    nw, nt, I, c = 12, 600, 3, 2
+    R = inputs.impact_response("bipolar", impacts=I, nwires=5, nticks=40, wire_center=c, tick_peak=15.0,
+                               tick_sigma=4.0).astype(np.float64)
+    R[1] *= 1.3                      # slices of different size as well as shape
+    q = np.array([3000.0, 5000.0]); x = np.array([23.0, 31.62]); t = np.array([150.2, 301.7])
+    T = _rng(19).standard_normal((nw, nt)) * 50
+
+    def loss(q=q, x=x, t=t, DL=oracle.DL, DT=oracle.DT, R=R):
+        M = oracle.simulate_impacts(q, x, t, nw, nt, R, c, circular=circular, DL_=DL, DT_=DT)
+        return float(((M - T) ** 2).sum())
+
+    M = oracle.simulate_impacts(q, x, t, nw, nt, R, c, circular=circular)
+    G = 2 * (M - T)
+    gq, gx, gt, gDL, gDT, gR = oracle.simulate_backward_impacts(q, x, t, nw, nt, R, c, G, circular=circular)
+    assert gR.shape == R.shape
+    for i in range(2):
+        for name, g, h in (("q", gq, 1e-2), ("x", gx, 1e-6), ("t", gt, 1e-6)):
+            def f(d, name=name):
+                v = {"q": q.copy(), "x": x.copy(), "t": t.copy()}
+                v[name][i] += d
+                return loss(**v)
+            est, err = _fd(f, h)
+            assert g[i] == pytest.approx(est, rel=2e-5, abs=10 * err + 1e-6), (name, i)
+    est, err = _fd(lambda d: loss(DL=oracle.DL + d), oracle.DL * 1e-6)
+    assert gDL == pytest.approx(est, rel=2e-5, abs=10 * err)
+    est, err = _fd(lambda d: loss(DT=oracle.DT + d), oracle.DT * 1e-6)
+    assert gDT == pytest.approx(est, rel=2e-5, abs=10 * err)
+    for (s_, r, j) in ((0, 2, 15), (2, 1, 20), (1, 4, 8)):
+        def f(d, s_=s_, r=r, j=j):
+            R2 = R.copy()
+            R2[s_, r, j] += d
+            return loss(R=R2)
+        est, err = _fd(f, 1e-3)
+        assert gR[s_, r, j] == pytest.approx(est, rel=1e-6, abs=10 * err), (s_, r, j)
+
+
+def test_impact_backward_with_equal_slices_is_the_plain_backward():
+    """Equal slices make the impact plane the plain one (the fine rows of a
+    wire sum to its coarse bin), so the depo and diffusion gradients agree
+    with the plain adjoint and each slice's response gradient is the plain
+    one's share over that position's rows (they sum to it)."""
+    nw, nt, I, c = 10, 500, 4, 2
+    R = inputs.response("unipolar", nwires=5, nticks=30, wire_center=c, tick_peak=10.0, tick_sigma=3.0)
+    R = R.astype(np.float64)
+    RI = np.broadcast_to(R, (I,) + R.shape).copy()
+    rng = _rng(23)
+    q = rng.uniform(1000, 6000, 5); x = rng.uniform(5, 45, 5); t = rng.uniform(50, 240, 5)
+    G = rng.standard_normal((nw, nt))
+    plain = oracle.simulate_backward(q, x, t, nw, nt, R, c, G)
+    imp = oracle.simulate_backward_impacts(q, x, t, nw, nt, RI, c, G)
+    for a, b in zip(plain[:5], imp[:5]):
+        assert np.allclose(a, b, rtol=1e-9, atol=1e-9 * np.max(np.abs(a)))
+    assert np.allclose(imp[5].sum(axis=0), plain[5], rtol=1e-9, atol=1e-9 * np.max(np.abs(plain[5])))
