@@ -101,9 +101,9 @@ typedef struct {
                                  raster bins the pitch axis at pitch/I into
                                  a fine grid of nwires*I rows (fine row
                                  w*I + i), and M = sum_i R_i (*) S_i.  FP32
-                                 only; ws_simulate and ws_simulate_batch
-                                 take them (a batch's planes share I), the
-                                 adjoint rejects them                       */
+                                 only; ws_simulate, ws_simulate_batch (a
+                                 batch's planes share I) and the adjoint
+                                 take them                                  */
 } ws_plane_desc;
 
 /* Depos of one event as seen by one plane: structure of arrays of float32
@@ -410,9 +410,12 @@ ws_status ws_plane_set_response(ws_plane* plane, const float* response_dev, void
  *       Gaussian mean and, when widths come from diffusion, through
  *       sigma_L = sqrt(2 D_L t)/v and sigma_T = sqrt(2 D_T t));
  *   gDL, gDT [1 double each]: dL/dD_L, dL/dD_T (zero with given widths);
- *   gR [K_w x K_t floats]: dL/dR.
+ *   gR [K_w x K_t floats]: dL/dR (I x K_w x K_t on an impact plane: one
+ *       slice per sub-pitch position).
  * dL/dS is Eq. 2's adjoint (correlation with the response, by FFT); each
- * patch is recomputed, not stored.  Derivatives of the clamped-edge bin
+ * patch is recomputed, not stored.  On an impact plane dL/dS is formed on
+ * the fine grid (position i's rows by the correlation with slice i) and
+ * the depo gradients are those of the raster at pitch / I.  Derivatives of the clamped-edge bin
  * weights hold everywhere except where a window bound crosses a bin edge.
  * Any output pointer may be NULL to skip it (gR == NULL skips the
  * response-gradient work).  All outputs are device pointers aligned to

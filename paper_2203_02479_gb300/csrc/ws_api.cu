@@ -172,7 +172,7 @@ ws_status plan_layout(const ws_plane_desc* d, Layout* lay) {
     lay->off_y = o; o = align256(o + sizeof(float2) * (size_t)d->nwires * lay->fstride);
     lay->off_scan = o; o = align256(o + sizeof(int64_t) * (size_t)ws::kScanScratch);
     lay->off_large = o; o = align256(o + sizeof(long long) * (size_t)ws::kLargeListCap);
-    lay->off_radj = o; o = align256(o + sizeof(float2) * (size_t)d->resp_nwires * lay->fstride);
+    lay->off_radj = o; o = align256(o + sizeof(float2) * (size_t)I * d->resp_nwires * lay->fstride);
     lay->off_racc = o; o = align256(o + sizeof(float2) * (size_t)d->resp_nwires * lay->fstride);
     lay->off_grid2 = o; o = align256(o + sizeof(float) * (size_t)d->nwires * d->nticks);
     lay->off_noise = o; o = align256(o + 2 * sizeof(float) * (size_t)lay->fstride);
@@ -341,6 +341,52 @@ ws::ConvBatch plane_conv(const ws_plane* pl, const ws::mark_t* rows, const ws::m
     cb.rows[0] = rows;
     cb.epoch = epoch;
     return cb;
+}
+
+// ws_simulate_backward on an impact plane (M = sum_i R_i (*) S_i over the
+// fine rows S_i[w] = S_fine[w * I + i]): G's tick transform once; dL/dR_i
+// from the recomputed fine grid's rows i against it; dL/dS_fine row by row
+// of each position (its correlation with R_i, the inverse transform
+// storing every I-th fine row); then the depo gradients of the raster on
+// the fine grid.  The plane's fine grid holds S, then dL/dS.
+ws_status backward_impacts(ws_plane* pl, const ws_depos* depos, const ws_params* params, const float* G,
+                           float* gq, float* gx, float* gt, double* gDL, double* gDT, float* gR, cudaStream_t s) {
+    const ws_plane_desc& d = pl->desc;
+    const int I = pl->impacts, circ = d.conv_mode == WS_CONV_CIRCULAR;
+    const int64_t fine_stride = (int64_t)I * d.nticks;
+    const size_t slice = (size_t)d.resp_nwires * pl->fstride;
+    ws::RasterArgs a = raster_args(pl, depos, params);
+    WS_LAUNCH(pl, K_FWD, s, ws::launch_fwd_rows(pl->plan, pl->tw, G, d.nwires, d.nticks, d.nticks, pl->X,
+                                                pl->fstride, pl->nfreq, 1.0f, s));
+    if (gR) {
+        const size_t fine_bytes = sizeof(float) * (size_t)I * d.nwires * d.nticks;
+        WS_LAUNCH(pl, K_MEMSET, s, cudaMemsetAsync(pl->fine, 0, fine_bytes, s));
+        WS_LAUNCH(pl, K_RASTER_SCATTER, s, ws::launch_raster_scatter(a, pl->fine, pl->large, s));
+        for (int i = 0; i < I; ++i) {
+            WS_LAUNCH(pl, K_FWD, s, ws::launch_fwd_rows(pl->plan, pl->tw, pl->fine + (size_t)i * d.nticks, d.nwires,
+                                                        d.nticks, fine_stride, pl->Y, pl->fstride, pl->nfreq, 1.0f,
+                                                        s));
+            WS_CUDA(cudaMemsetAsync(pl->Racc, 0, sizeof(float2) * slice, s));
+            WS_LAUNCH(pl, K_RGRAD, s, ws::launch_resp_grad(pl->X, pl->Y, pl->Racc, d.nwires, pl->nfreq, pl->fstride,
+                                                           d.resp_nwires, d.resp_wire_center, circ,
+                                                           1.0f / (float)pl->plan.L, s));
+            WS_LAUNCH(pl, K_INV, s, ws::launch_inv_rows(pl->plan, pl->tw, pl->Racc, d.resp_nwires, pl->fstride,
+                                                        pl->nfreq, gR + (size_t)i * d.resp_nwires * d.resp_nticks,
+                                                        d.resp_nticks, d.resp_nticks, s));
+        }
+    }
+    for (int i = 0; i < I; ++i) {
+        WS_LAUNCH(pl, K_WCONV, s, ws::launch_wire_conv(pl->X, pl->Y, pl->Radj + (size_t)i * slice, d.nwires,
+                                                       pl->nfreq, pl->fstride, d.resp_nwires,
+                                                       d.resp_nwires - 1 - d.resp_wire_center, circ, s, 0, pl->status));
+        WS_LAUNCH(pl, K_INV, s, ws::launch_inv_rows(pl->plan, pl->tw, pl->Y, d.nwires, pl->fstride, pl->nfreq,
+                                                    pl->fine + (size_t)i * d.nticks, d.nticks, fine_stride, s));
+    }
+    if (gDL) WS_CUDA(cudaMemsetAsync(gDL, 0, sizeof(double), s));
+    if (gDT) WS_CUDA(cudaMemsetAsync(gDT, 0, sizeof(double), s));
+    WS_LAUNCH(pl, K_DGRAD, s, ws::launch_depo_grads(a, pl->fine, gq, gx, gt, gDL, gDT, params->DL_mm2_us,
+                                                    params->DT_mm2_us, pl->large, s));
+    return WS_OK;
 }
 
 // ws_simulate's FP32 / compensated path with active rows: mark, clear the
@@ -521,8 +567,10 @@ ws_status ws_plane_create(const ws_plane_desc* desc, const float* response_dev, 
     if (e == cudaSuccess)
         e = ws::launch_fwd_rows(lay.plan, pl->tw, response_dev, lay.impacts * desc->resp_nwires, desc->resp_nticks,
                                 desc->resp_nticks, pl->Rt, lay.fstride, lay.nfreq, 1.0f / (float)lay.plan.L, s);
-    if (e == cudaSuccess)
-        e = ws::launch_adj_coeffs(pl->Rt, pl->Radj, desc->resp_nwires, lay.fstride, lay.nfreq, s);   // slice 0
+    for (int i = 0; i < lay.impacts && e == cudaSuccess; ++i)   // one adjoint tap set per response slice
+        e = ws::launch_adj_coeffs(pl->Rt + (size_t)i * desc->resp_nwires * lay.fstride,
+                                  pl->Radj + (size_t)i * desc->resp_nwires * lay.fstride, desc->resp_nwires,
+                                  lay.fstride, lay.nfreq, s);
     if (e == cudaSuccess && pl->fp64) e = ws::launch_twiddles64(pl->tw64, lay.plan, s);
     if (e == cudaSuccess && pl->fp64)
         e = ws::launch_fwd_rows64(lay.plan, pl->tw64, response_dev, false, desc->resp_nwires, desc->resp_nticks,
@@ -827,7 +875,10 @@ ws_status ws_plane_set_response(ws_plane* pl, const float* response_dev, void* s
     const ws_plane_desc& d = pl->desc;
     WS_CUDA(ws::launch_fwd_rows(pl->plan, pl->tw, response_dev, pl->impacts * d.resp_nwires, d.resp_nticks,
                                 d.resp_nticks, pl->Rt, pl->fstride, pl->nfreq, 1.0f / (float)pl->plan.L, s));
-    WS_CUDA(ws::launch_adj_coeffs(pl->Rt, pl->Radj, d.resp_nwires, pl->fstride, pl->nfreq, s));
+    for (int i = 0; i < pl->impacts; ++i)
+        WS_CUDA(ws::launch_adj_coeffs(pl->Rt + (size_t)i * d.resp_nwires * pl->fstride,
+                                      pl->Radj + (size_t)i * d.resp_nwires * pl->fstride, d.resp_nwires,
+                                      pl->fstride, pl->nfreq, s));
     if (pl->fp64)
         WS_CUDA(ws::launch_fwd_rows64(pl->plan, pl->tw64, response_dev, false, d.resp_nwires, d.resp_nticks,
                                       d.resp_nticks, pl->Rt64, pl->fstride, pl->nfreq, 1.0f / (float)pl->plan.L, s));
@@ -846,10 +897,10 @@ ws_status ws_simulate_backward(ws_plane* pl, const ws_depos* depos, const ws_par
     if (!aligned(gq, 4) || !aligned(gx, 4) || !aligned(gt, 4) || !aligned(gR, 4) || !aligned(gDL, 8) ||
         !aligned(gDT, 8))
         return WS_ERR_INVALID_ARG;
-    if (pl->impacts > 1) return WS_ERR_UNSUPPORTED_SIZE;
     cudaStream_t s = (cudaStream_t)stream;
     const ws_plane_desc& d = pl->desc;
     const int circ = d.conv_mode == WS_CONV_CIRCULAR;
+    if (pl->impacts > 1) return backward_impacts(pl, depos, params, grad_out_dev, gq, gx, gt, gDL, gDT, gR, s);
     // dL/dS = adjoint convolution of G: tick transform, wire correlation with
     // conj(R_hat), inverse transform.
     WS_LAUNCH(pl, K_FWD, s, ws::launch_fwd_rows(pl->plan, pl->tw, grad_out_dev, d.nwires, d.nticks, d.nticks, pl->X,

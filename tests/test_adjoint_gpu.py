@@ -219,3 +219,40 @@ def test_backward_wide_patches_take_the_warp_path(ws):
             assert rel(g[sel], r[sel]) <= TOL, (name, rel(g[sel], r[sel]))
     assert rel(got[5], ref[5]) <= TOL
     assert plane.status() == 0
+
+
+def _kinks_fine(d, I, nsig=3.0, reach=1e-5):
+    """kink_mask on an impact plane: the pitch axis is binned at pitch / I."""
+    t = d.t_us.astype(np.float64); x = d.x_mm.astype(np.float64)
+    st, sx = oracle.sigmas(t)
+    m = np.zeros(t.shape[0], bool)
+    for mu, sg, delta in ((t, st, oracle.TICK_US), (x, sx, oracle.PITCH_MM / I)):
+        for sign in (-1.0, 1.0):
+            b = (mu + sign * nsig * sg) / delta
+            m |= np.abs(b - np.round(b)) * delta < reach * np.maximum(sg, 1e-30)
+    return m
+
+
+@pytest.mark.parametrize("nw,nt,I,n,circular", [
+    (48, 1200, 4, 600, False),      # generic transforms
+    (40, 900, 3, 400, True),        # circular
+    (96, 6000, 10, 2000, False),    # fixed-shape transforms, patches up to ~29 fine wires
+])
+def test_backward_on_impact_planes_matches_oracle(ws, nw, nt, I, n, circular):
+    """dL/dS_fine by each position's correlation, the depo gradients on the
+    fine grid and one response gradient per slice, against the oracle's
+    impact adjoint (itself pinned by finite differences)."""
+    import torch
+    d = inputs.uniform_depos(n, nw, nw + I, nticks=nt, t_min_us=1.0)
+    R = inputs.impact_response("bipolar", impacts=I)
+    T = np.random.Generator(np.random.PCG64(nw)).standard_normal((nw, nt)) * 20
+    M = oracle.simulate_impacts(d.q, d.x_mm, d.t_us, nw, nt, R, 10, circular=circular)
+    G = 2 * (M - T)
+    ref = oracle.simulate_backward_impacts(d.q, d.x_mm, d.t_us, nw, nt, R, 10, G, circular=circular)
+    plane = ws.Plane(nw, nt, R, circular=circular)
+    got = plane.backward(ws.DeviceDepos.from_plane_depos(d), ws.Params(), torch.from_numpy(G.astype(np.float32)).cuda())
+    torch.cuda.synchronize()
+    got = [g.cpu().numpy() if hasattr(g, "cpu") else g for g in got]
+    assert got[5].shape == (I,) + R.shape[1:]
+    compare(got, ref, _kinks_fine(d, I))
+    assert plane.status() == 0
