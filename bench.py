@@ -854,12 +854,23 @@ def impacts_leg(wiresim, dev, stream, flush, steps: int, impacts: int = 10):
     st = traced(planes[0], lambda: (flush.zero_(), batched()), steps, 16)
     kern = {name: t / steps for name, (n, t) in st.items()}
     variants = [pl.info.wire_conv_variant for pl in planes]
+    # the adjoint of the expected-value path on the first plane (dL/dM a
+    # seeded normal grid): forward and backward, each timed alone
+    ev = wiresim.Params(seed=w.seed)
+    G = torch.randn((w.planes[0].nwires, w.planes[0].nticks), generator=torch.Generator().manual_seed(7)).to(dev)
+    fwd_ms = statistics.median(_time_steps(lambda: planes[0].simulate(depos[0], ev, out=outs[0], stream=stream),
+                                           steps, stream, flush))
+    bwd_ms = statistics.median(_time_steps(lambda: planes[0].backward(depos[0], ev, G, stream=stream),
+                                           steps, stream, flush))
     ndp = sum(d.n for d in w.events[0])
     for pl in planes:
         pl.close()
     return {"workload": w.name, "ms_per_step": ms,
             "value": ndp / (ms * 1e-3), "unit": UNIT, "kernels_ms_per_step": kern,
             "per_plane_ms_per_step": plane_ms, "units_per_wave": upw,
+            "adjoint_first_plane": {"forward_ms": fwd_ms, "backward_ms": bwd_ms,
+                                    "note": "expected-value forward and ws_simulate_backward (all gradients, "
+                                            "incl. the ten response slices) of the 800-wire plane"},
             "impact_wire_conv_tiles": [("16", "32", "16", "32")[v] + (" wires x 128" if v < 2 else " wires x 64")
                                        + " frequencies" for v in variants],
             "path": "ws_simulate_batch over the event's planes, autotuned waves (fine grids of nwires*10 rows, "

@@ -92,3 +92,27 @@ def test_multibatch_expected_value_against_oracle(ws):
             M = oracle.simulate(d.q, d.x_mm, d.t_us, WIRES[p], NT, specs[p].response, 10)
             assert rel(got[e * len(WIRES) + p], M) <= 1e-5, (e, p)
     mb.close()
+
+
+def test_multibatch_of_impact_planes(ws):
+    """Impact planes (4 sub-pitch positions) sharded over two batches on the
+    one GPU equal one batch over all events."""
+    import torch
+    from paper_2203_02479_gb300 import shard
+    specs = [inputs.PlaneSpec(nw, NT, inputs.impact_response("bipolar" if p < 2 else "unipolar", impacts=4), p)
+             for p, nw in enumerate(WIRES)]
+    events = [[inputs.uniform_depos(n, nw, seed=700 + 5 * e + p, nticks=NT) for p, nw in enumerate(WIRES)]
+              for e, n in enumerate(COUNTS[:5])]
+    params = ws.Params(fluctuate=1, p_survive=0.7, seed=77, event_id=3)
+    planes = [ws.Plane(sp.nwires, sp.nticks, sp.response, plane_id=sp.plane_id) for sp in specs]
+    devs = [[ws.DeviceDepos.from_plane_depos(d) for d in ev] for ev in events]
+    b = ws.Batch(planes, devs, params, units_per_wave=3)
+    b.run()
+    torch.cuda.synchronize()
+    want = [o.cpu().numpy() for o in b.outs]
+    mb = shard.MultiBatch([torch.device("cuda", 0)] * 2, specs, events, params, units_per_wave=3)
+    got = mb.run().gather()
+    assert len(got) == len(want)
+    for u, (g, w) in enumerate(zip(got, want)):
+        assert rel(g, w) <= 1e-6, (u, rel(g, w))
+    mb.close()
