@@ -71,7 +71,7 @@ def _lib():
                 ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
                 ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                 ctypes.c_int, ctypes.c_double, ctypes.c_uint64, ctypes.c_uint32,
-                ctypes.c_uint32, ctypes.c_int, _f64p]
+                ctypes.c_uint32, ctypes.c_uint32, ctypes.c_int, _f64p]
             h.wso_raster_scatter.restype = ctypes.c_int64
             h.wso_patch_extents.argtypes = [
                 ctypes.c_int64, _f64p, _f64p, opt_f32, opt_f32,
@@ -208,14 +208,17 @@ def raster_scatter(q, x_mm, t_us, nwires: int, nticks: int, *, sig_t_us=None, si
                    pitch_mm: float = PITCH_MM, tick_us: float = TICK_US, nsig: float = NSIGMA,
                    DL_: float = DL, DT_: float = DT, v: float = V, fluctuate: bool = False,
                    p: float = 1.0, seed: int = 0, event_id: int = 0, plane_id: int = 0,
-                   exact_max: int = EXACT_MAX, return_skipped: bool = False):
+                   exact_max: int = EXACT_MAX, depo_offset: int = 0, return_skipped: bool = False):
     """Raster every depo into its patch and scatter-add into S[wire][tick] (FP64).
 
     Sec. 2.2 (raster, scatter-add), Sec. 3.1 (binomial fluctuation).
     fluctuate: False/0 expected value, True/1 a binomial per bin, 2 the
-    charge-conserving multinomial split of each depo's survivors.  Pinned
-    by patch sums (closed form), linearity and the pins of its parts; the
-    multinomial by exact conservation and the multinomial's moments."""
+    charge-conserving multinomial split of each depo's survivors.
+    depo_offset: index of the first depo in the event's whole list (the
+    random counters carry each depo's index in that list).  Pinned by patch
+    sums (closed form), linearity and the pins of its parts; the
+    multinomial by exact conservation and the multinomial's moments; slices
+    with their offsets sum to the whole list."""
     q = _c64(q); x = _c64(x_mm); t = _c64(t_us)
     st = None if sig_t_us is None else _c64(sig_t_us)
     sx = None if sig_x_mm is None else _c64(sig_x_mm)
@@ -225,7 +228,7 @@ def raster_scatter(q, x_mm, t_us, nwires: int, nticks: int, *, sig_t_us=None, si
     skipped = _lib().wso_raster_scatter(
         q.shape[0], q, x, t, _opt_ptr(st), _opt_ptr(sx), nwires, nticks, pitch_mm, tick_us,
         nsig, DL_, DT_, v, int(fluctuate), float(p), int(seed) & (2 ** 64 - 1),
-        event_id & 0xFFFFFFFF, plane_id & 0xFFFFFFFF, int(exact_max), S)
+        event_id & 0xFFFFFFFF, plane_id & 0xFFFFFFFF, int(depo_offset) & 0xFFFFFFFF, int(exact_max), S)
     return (S, int(skipped)) if return_skipped else S
 
 

@@ -314,7 +314,10 @@ static void wso_multinomial_depo(double q, int64_t wlo, int nw, const double* wx
  * sig_t_us / sig_x_mm may be NULL, in which case they come from diffusion.
  * If fluctuate == 0 a bin receives the expected value p*q*w_t*w_x; if 1 a
  * binomial count (see wso_binomial); if 2 the depo's surviving electrons are
- * spread multinomially (see wso_multinomial_depo). */
+ * spread multinomially (see wso_multinomial_depo).  depo0 is the index of
+ * depo 0 in the event's whole depo list: the random counters carry the
+ * depo's index in that list (depo0 + i), so a list rastered in slices
+ * draws exactly as in one call. */
 #define WSO_MAXBINS 65536
 
 int64_t wso_raster_scatter(int64_t n, const double* q, const double* x_mm, const double* t_us,
@@ -322,7 +325,7 @@ int64_t wso_raster_scatter(int64_t n, const double* q, const double* x_mm, const
                            int nwires, int nticks, double pitch_mm, double tick_us,
                            double nsig, double DL, double DT, double v,
                            int fluctuate, double p, uint64_t seed, uint32_t event_id,
-                           uint32_t plane_id, int exact_max, double* S)
+                           uint32_t plane_id, uint32_t depo0, int exact_max, double* S)
 {
     if (fluctuate && exact_max > WSO_EXACT_CAP) return -1;
     double* wt = (double*)malloc(sizeof(double) * WSO_MAXBINS);
@@ -342,8 +345,8 @@ int64_t wso_raster_scatter(int64_t n, const double* q, const double* x_mm, const
         int nw = wso_axis_weights(xi, sx, pitch_mm, nsig, WSO_MAXBINS, &wlo, wx);
         if (nt < 0 || nw < 0) { ++skipped; continue; }
         if (fluctuate == 2) {
-            wso_multinomial_depo(qi, wlo, nw, wx, klo, nt, wt, nwires, nticks, p, exact_max, key, (uint32_t)i,
-                                 evpl, S);
+            wso_multinomial_depo(qi, wlo, nw, wx, klo, nt, wt, nwires, nticks, p, exact_max, key,
+                                 depo0 + (uint32_t)i, evpl, S);
             continue;
         }
         for (int a = 0; a < nw; ++a) {
@@ -356,7 +359,7 @@ int64_t wso_raster_scatter(int64_t n, const double* q, const double* x_mm, const
                 if (fluctuate) {
                     int64_t N = (int64_t)floor(qi * wt[b] * wx[a] + 0.5);
                     val = (double)wso_binomial(N, p, exact_max, key, wso_quad(w, k, nticks), (uint32_t)(k % 4),
-                                               (uint32_t)i, evpl);
+                                               depo0 + (uint32_t)i, evpl);
                 } else {
                     val = p * qi * wt[b] * wx[a];
                 }

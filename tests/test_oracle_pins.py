@@ -604,3 +604,27 @@ def test_patch_extents_by_scanning_every_bin():
         assert (w0[i], nwp[i], t0[i], ntp[i]) == (bw, cw, bt, ct), i
     assert total == int(np.sum(nwp.astype(np.int64) * ntp))
     assert 0 < np.count_nonzero(nwp * ntp) < n      # some depos fall off the grid
+
+
+@pytest.mark.parametrize("fluct", [0, 1, 2])
+def test_slices_with_their_offsets_sum_to_the_whole_list(fluct):
+    """The random counters carry each depo's index in the event's list, so
+    a list rastered in slices (each with the index of its first depo)
+    scatters exactly the whole list's grid, bin for bin (integer counts
+    when fluctuating), while the same slices without their offsets draw
+    other numbers."""
+    nw, nt, n = 20, 400, 300
+    rng = np.random.Generator(np.random.PCG64(41))
+    q = rng.exponential(4000, n); x = rng.uniform(0, nw * 5.0, n); t = rng.uniform(1, nt * 0.5, n)
+    kw = dict(fluctuate=fluct, p=0.7, seed=99, event_id=5, plane_id=1)
+    whole = oracle.raster_scatter(q, x, t, nw, nt, **kw)
+    cuts = [0, 70, 71, 200, 300]
+    spans = list(zip(cuts[:-1], cuts[1:]))
+    total = np.sum([oracle.raster_scatter(q[a:b], x[a:b], t[a:b], nw, nt, depo_offset=a, **kw) for a, b in spans],
+                   axis=0)
+    if fluct:
+        assert np.array_equal(total, whole)
+        blind = np.sum([oracle.raster_scatter(q[a:b], x[a:b], t[a:b], nw, nt, **kw) for a, b in spans], axis=0)
+        assert not np.array_equal(blind, whole)
+    else:
+        assert np.allclose(total, whole, rtol=1e-12, atol=1e-9)
