@@ -157,6 +157,12 @@ typedef struct {
                                  plane created with fp64 != 0).  Only
                                  ws_simulate honours it; the batch, patch
                                  and adjoint entry points run FP32.         */
+    uint32_t depo_offset;     /* index of depos[0] in the event's whole depo
+                                 list: the random counters carry each
+                                 depo's index in that list (depo_offset +
+                                 i), so an event's depos split over calls
+                                 or GPUs draw exactly as in one call.
+                                 depo_offset + n <= 2^32                    */
 } ws_params;
 
 /* Patches as produced by ws_rasterize: caller-allocated device arrays.

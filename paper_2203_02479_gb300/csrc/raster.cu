@@ -486,7 +486,7 @@ raster_kernel(const __grid_constant__ RasterUnits U, ws_patches pt, const long l
                         v = scale * s_wx[wib][ia] * s_wt[wib][ib];
                     } else {
                         const int N = electrons(q * s_wx[wib][ia] * s_wt[wib][ib]);
-                        v = (W)binomial_bin<P>(N, a, w, k, (uint32_t)i, s_recip, cdf);
+                        v = (W)binomial_bin<P>(N, a, w, k, a.depo0 + (uint32_t)i, s_recip, cdf);
                     }
                     if (MODE == EMIT_GRID) emit<P>(a, grid, (int64_t)w * a.nticks + k, v);
                     else pt.val[off + (int64_t)(w - e.w0) * ntf + (k - e.k0)] = (float)v;
@@ -680,8 +680,8 @@ raster_small_kernel(const __grid_constant__ RasterUnits U, ws_patches pt, long l
                     }
                     first = (uint32_t)w * (uint32_t)a.nticks + (uint32_t)(4 * kq);   // grids hold < 2^31 cells
                     if ((N[0] | N[1] | N[2] | N[3]) > 0)
-                        x = philox4x32_10(make_uint4(0u, (uint32_t)w * qstride + (uint32_t)kq, (uint32_t)(base + d),
-                                                     a.evpl), a.key0, a.key1);
+                        x = philox4x32_10(make_uint4(0u, (uint32_t)w * qstride + (uint32_t)kq,
+                                                     a.depo0 + (uint32_t)(base + d), a.evpl), a.key0, a.key1);
                 }
                 unsigned nbal[4], ebal[4];
                 int nbef[4], ebef[4], nn = 0, ne = 0;
@@ -740,7 +740,7 @@ raster_small_kernel(const __grid_constant__ RasterUnits U, ws_patches pt, long l
                 const int w = it.w0 + ia, k = it.k0 + ib;
                 W v = it.q * s_wx[wib][d][ia] * s_wt[wib][d][ib];
                 if (a.fluct)
-                    v = (W)binomial_bin<P>(electrons(v), a, w, k, (uint32_t)(base + d), s_recip, cdf);
+                    v = (W)binomial_bin<P>(electrons(v), a, w, k, a.depo0 + (uint32_t)(base + d), s_recip, cdf);
                 if (MODE == EMIT_GRID) emit<P>(a, grid, (int64_t)w * a.nticks + k, v);
                 else pt.val[pt.off[base + d] + it.local] = (float)v;
             }
@@ -868,7 +868,7 @@ raster_multinomial_kernel(const __grid_constant__ RasterUnits U, ws_patches pt) 
             if (a.keep_all) {
                 K = N;
             } else {
-                const uint4 x = philox4x32_10(make_uint4(5u, 0u, (uint32_t)i, a.evpl), a.key0, a.key1);
+                const uint4 x = philox4x32_10(make_uint4(5u, 0u, a.depo0 + (uint32_t)i, a.evpl), a.key0, a.key1);
                 K = N <= a.exact_max ? invert_binomial(N, x.x, a, s_recip) : normal_pair<0>(x, N, a);
             }
         }
@@ -909,7 +909,7 @@ raster_multinomial_kernel(const __grid_constant__ RasterUnits U, ws_patches pt) 
                 cx0 = cx1;
             }
             const float prj = (xfull && j == e.w1) ? 1.f : __fdiv_rn(wj, Wx);
-            const int nj = binomial_var(rem, prj, a, 4u, (uint32_t)j, (uint32_t)i, s_recip);
+            const int nj = binomial_var(rem, prj, a, 4u, (uint32_t)j, a.depo0 + (uint32_t)i, s_recip);
             rem -= nj;
             Wx = __fsub_rn(Wx, wj);
             int rem2 = nj;
@@ -930,7 +930,7 @@ raster_multinomial_kernel(const __grid_constant__ RasterUnits U, ws_patches pt) 
                 }
                 const float prk = (tfull && k == e.k1) ? 1.f : __fdiv_rn(wk, Wt);
                 const int64_t bin = (int64_t)j * a.nticks + k;
-                const int m = binomial_var(rem2, prk, a, 3u, (uint32_t)bin, (uint32_t)i, s_recip);
+                const int m = binomial_var(rem2, prk, a, 3u, (uint32_t)bin, a.depo0 + (uint32_t)i, s_recip);
                 rem2 -= m;
                 Wt = __fsub_rn(Wt, wk);
                 if (MODE == EMIT_GRID) emit<P>(a, grid, bin, (W)m);

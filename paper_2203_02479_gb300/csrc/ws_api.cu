@@ -212,6 +212,12 @@ ws_status check_depos(const ws_depos* d) {
     return WS_OK;
 }
 
+// The depos' indices in the event's list (depo_offset + i) fit the
+// counters' 32-bit depo word.
+ws_status check_depo_span(const ws_depos* d, const ws_params* p) {
+    return (uint64_t)p->depo_offset + (uint64_t)d->n > ((uint64_t)1 << 32) ? WS_ERR_INVALID_ARG : WS_OK;
+}
+
 ws_status check_params(const ws_params* p) {
     if (!p) return WS_ERR_INVALID_ARG;
     if (!(p->v_mm_us > 0) || !(p->DL_mm2_us >= 0) || !(p->DT_mm2_us >= 0)) return WS_ERR_INVALID_ARG;
@@ -244,6 +250,7 @@ ws::RasterArgs raster_args(const ws_plane* pl, const ws_depos* d, const ws_param
     a.key0 = (uint32_t)(p->seed & 0xFFFFFFFFu);
     a.key1 = (uint32_t)(p->seed >> 32);
     a.evpl = (p->event_id << 4) | ((uint32_t)pl->desc.plane_id & 15u);
+    a.depo0 = p->depo_offset;
     a.keep_all = p->p_survive >= 1.0 ? 1 : 0;
     a.exact_max = p->fluct_exact_max;
     a.wide = pl->impacts > 1 ? 1 : 0;
@@ -733,6 +740,7 @@ ws_status ws_patch_capacity(ws_plane* pl, const ws_depos* depos, const ws_params
     if (!pl || !bins_out) return WS_ERR_INVALID_ARG;
     ws_status st = check_depos(depos);
     if (st == WS_OK) st = check_params(params);
+    if (st == WS_OK) st = check_depo_span(depos, params);
     if (st != WS_OK) return st;
     cudaStream_t s = (cudaStream_t)stream;
     ws::RasterArgs a = raster_args(pl, depos, params);
@@ -750,6 +758,7 @@ ws_status ws_rasterize(ws_plane* pl, const ws_depos* depos, const ws_params* par
     if (!pl || !out) return WS_ERR_INVALID_ARG;
     ws_status st = check_depos(depos);
     if (st == WS_OK) st = check_params(params);
+    if (st == WS_OK) st = check_depo_span(depos, params);
     if (st != WS_OK) return st;
     if (out->n != depos->n || out->capacity_bins < 0 || !out->off) return WS_ERR_INVALID_ARG;
     if (depos->n > 0 && (!out->w0 || !out->t0 || !out->nw || !out->nt)) return WS_ERR_INVALID_ARG;
@@ -795,6 +804,7 @@ ws_status ws_simulate(ws_plane* pl, const ws_depos* depos, const ws_params* para
     if (!pl || !out_dev || !aligned(out_dev, 4)) return WS_ERR_INVALID_ARG;
     ws_status st = check_depos(depos);
     if (st == WS_OK) st = check_params(params);
+    if (st == WS_OK) st = check_depo_span(depos, params);
     if (st != WS_OK) return st;
     cudaStream_t s = (cudaStream_t)stream;
     const ws_plane_desc& d = pl->desc;
@@ -892,6 +902,7 @@ ws_status ws_simulate_backward(ws_plane* pl, const ws_depos* depos, const ws_par
     if (!pl || !grad_out_dev || !aligned(grad_out_dev, 4)) return WS_ERR_INVALID_ARG;
     ws_status st = check_depos(depos);
     if (st == WS_OK) st = check_params(params);
+    if (st == WS_OK) st = check_depo_span(depos, params);
     if (st != WS_OK) return st;
     if (params->fluctuate) return WS_ERR_INVALID_ARG;  // the adjoint is of the expected-value path
     if (!aligned(gq, 4) || !aligned(gx, 4) || !aligned(gt, 4) || !aligned(gR, 4) || !aligned(gDL, 8) ||
@@ -1065,6 +1076,7 @@ ws_status ws_simulate_batch(ws_plane* const* planes, int nplanes, const ws_depos
     const int nunits = nevents * nplanes;
     for (int u = 0; u < nunits; ++u) {
         st = check_depos(&depos[u]);
+        if (st == WS_OK) st = check_depo_span(&depos[u], params);
         if (st != WS_OK) return st;
         if (!out_dev[u] || !aligned(out_dev[u], 4)) return WS_ERR_INVALID_ARG;
     }

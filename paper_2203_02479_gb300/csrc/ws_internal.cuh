@@ -44,6 +44,7 @@ struct RasterArgs {
     int keep_all;         // p >= 1: every electron survives
     uint32_t key0, key1;  // Philox key from the seed
     uint32_t evpl;        // (event_id << 4) | plane_id
+    uint32_t depo0;       // index of depo 0 in the event's whole list (the counters' depo word)
     int exact_max;        // N <= exact_max: CDF inversion; above: normal approximation
     int wide;             // grid binned at pitch / I (impact planes): wider lane-per-depo patches
     // CDF inversion on s = min(p, 1-p) (float): r = s / (1 - s), base = 1 - s

@@ -24,6 +24,16 @@ Two forms:
 * ``rank_range`` / ``gather_units``: one process per GPU (torchrun); each rank
   takes its range and, only if the caller wants the waveforms in one place,
   ``gather_units`` sends them point to point to one rank.
+
+A plane too large for one GPU's time budget splits by depos instead
+(``depo_slices`` / ``simulate_depo_split``): each rank simulates a
+contiguous slice of the plane's depos, with the slice's offset in the list
+(``Params.depo_offset``) so that its random draws are the whole list's,
+and the waveforms are summed across ranks (an all-reduce, or a
+reduce-scatter that leaves each rank a band of wire rows).  Eq. 1 is
+linear in S and S is the sum of the slices' grids, so the sum is the whole
+plane's waveform (bin for bin in S when fluctuating; the transforms'
+rounding in M).  This is the one path with a collective on the data.
 """
 from __future__ import annotations
 
@@ -247,3 +257,57 @@ class MultiBatch:
             for pl in s.planes:
                 pl.close()
         self.shards = []
+
+
+def depo_slices(n: int, nparts: int):
+    """Contiguous slices [lo, hi) of n depos over nparts ranks, sizes
+    differing by at most one (the raster's cost is per depo; the
+    convolution is the whole plane's on every rank)."""
+    if nparts < 1:
+        raise ValueError("nparts must be >= 1")
+    q, r = divmod(n, nparts)
+    out, lo = [], 0
+    for k in range(nparts):
+        hi = lo + q + (1 if k < r else 0)
+        out.append((lo, hi))
+        lo = hi
+    return out
+
+
+def wire_bands(nwires: int, nparts: int):
+    """Wire-row bands [w0, w1) of a reduce-scatter of M over nparts ranks."""
+    return depo_slices(nwires, nparts)
+
+
+def simulate_depo_split(dist, plane, depos, params, out=None, scatter: bool = False, simulate=None):
+    """One plane's event split by depos over the ranks of ``dist``: this rank
+    simulates depos [lo, hi) of its slice (``depo_slices``) with
+    ``depo_offset = lo``, then the ranks' waveforms are summed: all-reduced
+    (every rank returns the whole M), or with ``scatter`` reduce-scattered
+    by wire rows (each rank returns its band of ``wire_bands`` and the band;
+    the plane's wires must split evenly).  ``depos``: the plane's whole
+    depo list as host arrays (``inputs.PlaneDepos``); ``simulate(plane,
+    q, x, t, params)`` runs one slice (default: ``plane.simulate`` on
+    device copies).  The plane's noise term, if any, must be set on one
+    rank only (each rank's waveform is added once)."""
+    import torch
+    world, rank = dist.get_world_size(), dist.get_rank()
+    lo, hi = depo_slices(len(depos.q), world)[rank]
+    p = dataclasses.replace(params, depo_offset=params.depo_offset + lo)
+    if simulate is None:
+        from . import wiresim
+
+        def simulate(plane, q, x, t, p):
+            dd = wiresim.DeviceDepos(q, x, t, device=plane.device)
+            return plane.simulate(dd, p, out=out)
+    M = simulate(plane, depos.q[lo:hi], depos.x_mm[lo:hi], depos.t_us[lo:hi], p)
+    if not scatter:
+        dist.all_reduce(M)
+        return M
+    nw = M.shape[0]
+    if nw % world:
+        raise ValueError(f"{nw} wires do not split evenly over {world} ranks")
+    w0, w1 = wire_bands(nw, world)[rank]
+    band = torch.empty((w1 - w0,) + tuple(M.shape[1:]), dtype=M.dtype, device=M.device)
+    dist.reduce_scatter_tensor(band, M.contiguous())
+    return band, (w0, w1)

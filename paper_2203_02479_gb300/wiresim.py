@@ -66,7 +66,7 @@ class WsParams(ctypes.Structure):
                 ("v_mm_us", ctypes.c_double), ("fluctuate", ctypes.c_int32),
                 ("p_survive", ctypes.c_double), ("seed", ctypes.c_uint64),
                 ("event_id", ctypes.c_uint32), ("fluct_exact_max", ctypes.c_int32),
-                ("precision", ctypes.c_int32)]
+                ("precision", ctypes.c_int32), ("depo_offset", ctypes.c_uint32)]
 
 
 class WsPatches(ctypes.Structure):
@@ -292,11 +292,12 @@ class Params:
     event_id: int = 0
     fluct_exact_max: int = 32
     precision: int = WS_PREC_FP32
+    depo_offset: int = 0      # index of the first depo in the event's whole list (random counters)
 
     def c(self) -> WsParams:
         return WsParams(self.DL_mm2_us, self.DT_mm2_us, self.v_mm_us, int(self.fluctuate),
                         self.p_survive, self.seed & (2 ** 64 - 1), self.event_id, self.fluct_exact_max,
-                        self.precision)
+                        self.precision, self.depo_offset)
 
 
 class DeviceDepos:

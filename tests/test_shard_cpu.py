@@ -163,3 +163,73 @@ def test_two_gloo_ranks_split_and_gather():
     assert all(e1 > e0 for e0, e1 in ranges0)
     assert ok0 and n0 == NEV * NPL          # rank 0 holds every unit, in order
     assert ok1 and n1 == (ranges0[1][1] - ranges0[1][0]) * NPL
+
+
+def test_depo_and_wire_slices():
+    from paper_2203_02479_gb300 import shard as sh
+    for n, k in ((0, 1), (1, 3), (10, 3), (1000, 7), (7, 7)):
+        s = sh.depo_slices(n, k)
+        assert len(s) == k and s[0][0] == 0 and s[-1][1] == n
+        assert all(a[1] == b[0] for a, b in zip(s, s[1:]))
+        sizes = [b - a for a, b in s]
+        assert max(sizes) - min(sizes) <= 1
+    assert sh.wire_bands(800, 4) == [(0, 200), (200, 400), (400, 600), (600, 800)]
+    with pytest.raises(ValueError):
+        sh.depo_slices(5, 0)
+
+
+SPLIT_NW, SPLIT_NT = 24, 600
+
+
+def _split_main(rank, world, port, q, mode):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    sys.path.insert(0, ROOT)
+    import torch
+    import torch.distributed as dist
+
+    import oracle
+    from paper_2203_02479_gb300 import inputs as inp, shard as sh, wiresim
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    d = inp.uniform_depos(500, SPLIT_NW, seed=61, nticks=SPLIT_NT)
+    R = inp.response("unipolar")
+    params = wiresim.Params(fluctuate=1, p_survive=0.7, seed=5, event_id=9)
+    kw = dict(fluctuate=1, p=0.7, seed=5, event_id=9, plane_id=2)
+
+    def sim(plane, qq, xx, tt, p):   # one slice by the oracle, keyed by the slice's offset
+        return torch.from_numpy(oracle.simulate(qq, xx, tt, SPLIT_NW, SPLIT_NT, R, 10, depo_offset=p.depo_offset,
+                                                **kw))
+    whole = oracle.simulate(d.q, d.x_mm, d.t_us, SPLIT_NW, SPLIT_NT, R, 10, **kw)
+    if mode == "all":
+        M = sh.simulate_depo_split(dist, None, d, params, simulate=sim).numpy()
+        ok = np.allclose(M, whole, rtol=0, atol=1e-9 * np.abs(whole).max())
+    else:
+        band, (w0, w1) = sh.simulate_depo_split(dist, None, d, params, scatter=True, simulate=sim)
+        ok = (w0, w1) == sh.wire_bands(SPLIT_NW, world)[rank] and \
+            np.allclose(band.numpy(), whole[w0:w1], rtol=0, atol=1e-9 * np.abs(whole).max())
+    q.put((rank, bool(ok)))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("mode", ["all", "scatter"])
+def test_two_gloo_ranks_split_one_plane_by_depos(mode):
+    """A plane's depos over two ranks: each simulates its slice (the oracle,
+    random draws keyed by the depos' indices in the whole list), the
+    waveforms are summed across ranks, and the sum is the whole list's
+    waveform (all-reduce: on every rank; reduce-scatter: a band of wire
+    rows each)."""
+    import torch.distributed as dist
+    if mode == "scatter" and not dist.is_available():
+        pytest.skip("torch.distributed unavailable")
+    import torch.multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_split_main, args=(r, 2, port, q, mode)) for r in range(2)]
+    for p in procs:
+        p.start()
+    res = sorted(q.get(timeout=240) for _ in procs)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    assert res == [(0, True), (1, True)]

@@ -116,3 +116,31 @@ def test_multibatch_of_impact_planes(ws):
     for u, (g, w) in enumerate(zip(got, want)):
         assert rel(g, w) <= 1e-6, (u, rel(g, w))
     mb.close()
+
+
+@pytest.mark.parametrize("fluct", [1, 2])
+def test_depo_slices_with_offsets_sum_to_the_whole_plane(ws, fluct):
+    """The depo split's device side: slices of one plane's depos simulated
+    with their offsets (Params.depo_offset) sum to one call over the whole
+    list (the random draws are keyed by the depos' indices in the list),
+    and differ from it without the offsets."""
+    import dataclasses
+    import torch
+    from paper_2203_02479_gb300 import shard
+    nw, nt = 200, 6000
+    d = inputs.uniform_depos(30000, nw, seed=3, nticks=nt)
+    pl = ws.Plane(nw, nt, inputs.response("bipolar"))
+    params = ws.Params(fluctuate=fluct, p_survive=0.7, seed=11, event_id=4)
+    whole = pl.simulate(ws.DeviceDepos.from_plane_depos(d), params).clone()
+    total = torch.zeros_like(whole)
+    blind = torch.zeros_like(whole)
+    for lo, hi in shard.depo_slices(len(d.q), 3):
+        dd = ws.DeviceDepos(d.q[lo:hi], d.x_mm[lo:hi], d.t_us[lo:hi])
+        total += pl.simulate(dd, dataclasses.replace(params, depo_offset=lo))
+        blind += pl.simulate(dd, params)
+    torch.cuda.synchronize()
+    assert rel(total.cpu().numpy(), whole.cpu().numpy()) <= 1e-6
+    assert rel(blind.cpu().numpy(), whole.cpu().numpy()) > 1e-4
+    ref = oracle.simulate(d.q, d.x_mm, d.t_us, nw, nt, inputs.response("bipolar"), 10, fluctuate=fluct, p=0.7,
+                          seed=11, event_id=4, plane_id=0)
+    assert rel(total.cpu().numpy(), ref) <= 1e-5
