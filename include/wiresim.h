@@ -219,7 +219,8 @@ typedef struct ws_plane ws_plane;
  * word, scan scratch, noise spectra, a 64-bit row mark and a row class per
  * wire for ws_simulate's active rows; with impacts I > 1 also the fine grid
  * of nwires*I x nticks floats and I times the first spectrum, the
- * response spectrum and the adjoint's taps).  Host-only; fails with WS_ERR_UNSUPPORTED_SIZE if the
+ * response spectrum, the adjoint's taps and the response gradient's
+ * spectra).  Host-only; fails with WS_ERR_UNSUPPORTED_SIZE if the
  * FFT length is not 2/3/5-smooth or exceeds 14336, for FP64 buffers on an
  * impact plane, or for a grid (fine grid on an impact plane) of 2^31 cells
  * or more, and with WS_ERR_INVALID_ARG for impacts outside 0 .. 32. */

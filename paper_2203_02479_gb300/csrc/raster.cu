@@ -1004,9 +1004,11 @@ __device__ __forceinline__ void widen_for_grad(const RasterArgs& a, Extent& e) {
 
 constexpr int kGradT = kSmallT + 2;   // widened patch a lane-per-depo gradient takes
 constexpr int kGradX = kSmallW + 2;
+constexpr int kGradXWide = kWideW + 2;   // the same on planes binned at pitch / I
 
+template <int GX>
 __device__ __forceinline__ bool grad_is_small(const Extent& e) {
-    return e.k1 - e.k0 + 1 <= kGradT && e.w1 - e.w0 + 1 <= kGradX;
+    return e.k1 - e.k0 + 1 <= kGradT && e.w1 - e.w0 + 1 <= GX;
 }
 
 // One axis of a depo's gradient tables, spread over the kGradLanes lanes of
@@ -1075,18 +1077,19 @@ __device__ __forceinline__ void finish_grad(const RasterArgs& a, const GradArgs&
 // kGradLanes lanes per depo (eight depos per warp): the group builds its
 // depo's widened edge, weight and derivative tables in shared memory and
 // splits the patch rows, gathering dL/dS; the partial sums meet by shuffles.
-// Depos whose widened patch exceeds kGradT x kGradX go to depo_grad_kernel
+// Depos whose widened patch exceeds kGradT x GX go to depo_grad_kernel
 // through the hand-over list.
 constexpr int kGradWarps = 4;
 constexpr int kGradSlots = 32 / kGradLanes;
 
+template <int GX>
 __global__ void __launch_bounds__(32 * kGradWarps)
 depo_grad_small_kernel(RasterArgs a, GradArgs g, long long* __restrict__ list, unsigned* list_count,
                        unsigned list_cap) {
     __shared__ float s_te[kGradWarps][kGradSlots][3][kGradT + 1];
     __shared__ float s_tb[kGradWarps][kGradSlots][3][kGradT];
-    __shared__ float s_xe[kGradWarps][kGradSlots][3][kGradX + 1];
-    __shared__ float s_xb[kGradWarps][kGradSlots][3][kGradX];
+    __shared__ float s_xe[kGradWarps][kGradSlots][3][GX + 1];
+    __shared__ float s_xb[kGradWarps][kGradSlots][3][GX];
     __shared__ double s_red[kGradWarps][2];
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
@@ -1102,7 +1105,7 @@ depo_grad_small_kernel(RasterArgs a, GradArgs g, long long* __restrict__ list, u
         bool bad = false, any = false;
         if (i < a.n) any = depo_extent<float>(a, i, &e, &q, &bad);
         if (any) widen_for_grad(a, e);
-        const bool mine = i < a.n && (!any || grad_is_small(e));
+        const bool mine = i < a.n && (!any || grad_is_small<GX>(e));
         if (sub == 0 && i < a.n && !mine) {   // hand the depo to the warp-per-depo kernel
             const unsigned s = atomicAdd(list_count, 1u);
             if (s < list_cap) list[s] = (long long)i;
@@ -1111,11 +1114,11 @@ depo_grad_small_kernel(RasterArgs a, GradArgs g, long long* __restrict__ list, u
         const int nt = work ? e.k1 - e.k0 + 1 : 0, nx = work ? e.w1 - e.w0 + 1 : 0;
         group_axis_grad<kGradT + 1>(work ? e.mu_t : 0.f, work ? e.st : 1.f, a.tick, a.nsig, work && e.point_t,
                                     work ? e.k0 : 0, nt, inv_norm, s_te[wib][slot], s_tb[wib][slot], sub);
-        group_axis_grad<kGradX + 1>(work ? e.mu_x : 0.f, work ? e.sx : 1.f, a.pitch, a.nsig, work && e.point_x,
+        group_axis_grad<GX + 1>(work ? e.mu_x : 0.f, work ? e.sx : 1.f, a.pitch, a.nsig, work && e.point_x,
                                     work ? e.w0 : 0, nx, inv_norm, s_xe[wib][slot], s_xb[wib][slot], sub);
         float Sq = 0.f, Smt = 0.f, Sst = 0.f, Smx = 0.f, Ssx = 0.f;
         const float (*tb)[kGradT] = s_tb[wib][slot];
-        const float (*xb)[kGradX] = s_xb[wib][slot];
+        const float (*xb)[GX] = s_xb[wib][slot];
         for (int ia = sub; ia < nx; ia += kGradLanes) {
             const float* row = g.dS + (int64_t)(e.w0 + ia) * a.nticks + e.k0;
             float r0 = 0.f, r1 = 0.f, r2 = 0.f;   // sums over the row of gv w_t, gv dmu_t, gv dsig_t
@@ -1164,6 +1167,7 @@ depo_grad_small_kernel(RasterArgs a, GradArgs g, long long* __restrict__ list, u
 // leaves (chunks of kChunk bins per axis): the hand-over list's entries if
 // they fit in it, else every depo whose widened patch is large.  The last
 // block to finish resets the list counter for the next launch.
+template <int GX>
 __global__ void __launch_bounds__(32 * kWarpsPerBlock)
 depo_grad_kernel(RasterArgs a, GradArgs g, const long long* __restrict__ list, unsigned* list_count,
                  unsigned list_cap, unsigned* done) {
@@ -1190,7 +1194,7 @@ depo_grad_kernel(RasterArgs a, GradArgs g, const long long* __restrict__ list, u
         const bool any = depo_extent<float>(a, i, &e, &q, &bad);
         if (!any) continue;   // written by the lane-per-depo kernel
         widen_for_grad(a, e);
-        if (grad_is_small(e)) continue;
+        if (grad_is_small<GX>(e)) continue;
         float Sq = 0.f, Smt = 0.f, Sst = 0.f, Smx = 0.f, Ssx = 0.f;
         for (int kc = any ? e.k0 : 1; any && kc <= e.k1; kc += kChunk) {
             const int ntc = min(kChunk, e.k1 - kc + 1);
@@ -1673,9 +1677,16 @@ cudaError_t launch_depo_grads(const RasterArgs& a, const float* dS, float* gq, f
                               double* gDT, double DL, double DT, const LargeList& L, cudaStream_t s) {
     if (a.n <= 0) return cudaSuccess;
     GradArgs g{dS, gq, gx, gt, gDL, gDT, DL, DT};
-    depo_grad_small_kernel<<<grid_for((a.n + kGradSlots - 1) / kGradSlots, kGradWarps, 8), 32 * kGradWarps, 0, s>>>(
-        a, g, L.list, L.count, L.cap);
-    depo_grad_kernel<<<num_sms() * 2, 32 * kWarpsPerBlock, 0, s>>>(a, g, L.list, L.count, L.cap, L.done);
+    const int blocks = grid_for((a.n + kGradSlots - 1) / kGradSlots, kGradWarps, 8);
+    if (a.wide) {   // impact planes: up to kWideW fine wire bins per patch
+        depo_grad_small_kernel<kGradXWide><<<blocks, 32 * kGradWarps, 0, s>>>(a, g, L.list, L.count, L.cap);
+        depo_grad_kernel<kGradXWide><<<num_sms() * 2, 32 * kWarpsPerBlock, 0, s>>>(a, g, L.list, L.count, L.cap,
+                                                                                    L.done);
+    } else {
+        depo_grad_small_kernel<kGradX><<<blocks, 32 * kGradWarps, 0, s>>>(a, g, L.list, L.count, L.cap);
+        depo_grad_kernel<kGradX><<<num_sms() * 2, 32 * kWarpsPerBlock, 0, s>>>(a, g, L.list, L.count, L.cap,
+                                                                                L.done);
+    }
     return cudaGetLastError();
 }
 

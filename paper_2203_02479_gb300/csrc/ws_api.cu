@@ -173,7 +173,7 @@ ws_status plan_layout(const ws_plane_desc* d, Layout* lay) {
     lay->off_scan = o; o = align256(o + sizeof(int64_t) * (size_t)ws::kScanScratch);
     lay->off_large = o; o = align256(o + sizeof(long long) * (size_t)ws::kLargeListCap);
     lay->off_radj = o; o = align256(o + sizeof(float2) * (size_t)I * d->resp_nwires * lay->fstride);
-    lay->off_racc = o; o = align256(o + sizeof(float2) * (size_t)d->resp_nwires * lay->fstride);
+    lay->off_racc = o; o = align256(o + sizeof(float2) * (size_t)I * d->resp_nwires * lay->fstride);
     lay->off_grid2 = o; o = align256(o + sizeof(float) * (size_t)d->nwires * d->nticks);
     lay->off_noise = o; o = align256(o + 2 * sizeof(float) * (size_t)lay->fstride);
     lay->off_rows = o; o = align256(o + sizeof(ws::mark_t) * (size_t)d->nwires);
@@ -351,44 +351,69 @@ ws::ConvBatch plane_conv(const ws_plane* pl, const ws::mark_t* rows, const ws::m
 }
 
 // ws_simulate_backward on an impact plane (M = sum_i R_i (*) S_i over the
-// fine rows S_i[w] = S_fine[w * I + i]): G's tick transform once; dL/dR_i
-// from the recomputed fine grid's rows i against it; dL/dS_fine row by row
-// of each position (its correlation with R_i, the inverse transform
-// storing every I-th fine row); then the depo gradients of the raster on
-// the fine grid.  The plane's fine grid holds S, then dL/dS.
+// fine rows S_i[w] = S_fine[w * I + i]): G's tick transform once (into Y);
+// dL/dR_i from the recomputed fine grid, its I positions transformed in
+// one launch (into X, I x nwires rows), correlated with G's spectrum slice
+// by slice and inverse-transformed in one launch; dL/dS_fine from the I
+// correlations of G's spectrum with the slices' adjoint taps (one launch
+// over I units into X) and one inverse transform storing every I-th fine
+// row per position; then the depo gradients of the raster on the fine
+// grid.  The plane's fine grid holds S, then dL/dS.
 ws_status backward_impacts(ws_plane* pl, const ws_depos* depos, const ws_params* params, const float* G,
                            float* gq, float* gx, float* gt, double* gDL, double* gDT, float* gR, cudaStream_t s) {
     const ws_plane_desc& d = pl->desc;
     const int I = pl->impacts, circ = d.conv_mode == WS_CONV_CIRCULAR;
     const int64_t fine_stride = (int64_t)I * d.nticks;
-    const size_t slice = (size_t)d.resp_nwires * pl->fstride;
+    const size_t slice = (size_t)d.resp_nwires * pl->fstride;   // one slice's response spectrum rows
+    const size_t rows = (size_t)d.nwires * pl->fstride;          // one position's spectra
     ws::RasterArgs a = raster_args(pl, depos, params);
-    WS_LAUNCH(pl, K_FWD, s, ws::launch_fwd_rows(pl->plan, pl->tw, G, d.nwires, d.nticks, d.nticks, pl->X,
+    WS_LAUNCH(pl, K_FWD, s, ws::launch_fwd_rows(pl->plan, pl->tw, G, d.nwires, d.nticks, d.nticks, pl->Y,
                                                 pl->fstride, pl->nfreq, 1.0f, s));
+    ws::RowBatch fb, ib;
+    fb.n = ib.n = I;
+    fb.status = ib.status = nullptr;
     if (gR) {
         const size_t fine_bytes = sizeof(float) * (size_t)I * d.nwires * d.nticks;
         WS_LAUNCH(pl, K_MEMSET, s, cudaMemsetAsync(pl->fine, 0, fine_bytes, s));
         WS_LAUNCH(pl, K_RASTER_SCATTER, s, ws::launch_raster_scatter(a, pl->fine, pl->large, s));
         for (int i = 0; i < I; ++i) {
-            WS_LAUNCH(pl, K_FWD, s, ws::launch_fwd_rows(pl->plan, pl->tw, pl->fine + (size_t)i * d.nticks, d.nwires,
-                                                        d.nticks, fine_stride, pl->Y, pl->fstride, pl->nfreq, 1.0f,
-                                                        s));
-            WS_CUDA(cudaMemsetAsync(pl->Racc, 0, sizeof(float2) * slice, s));
-            WS_LAUNCH(pl, K_RGRAD, s, ws::launch_resp_grad(pl->X, pl->Y, pl->Racc, d.nwires, pl->nfreq, pl->fstride,
-                                                           d.resp_nwires, d.resp_wire_center, circ,
-                                                           1.0f / (float)pl->plan.L, s));
-            WS_LAUNCH(pl, K_INV, s, ws::launch_inv_rows(pl->plan, pl->tw, pl->Racc, d.resp_nwires, pl->fstride,
-                                                        pl->nfreq, gR + (size_t)i * d.resp_nwires * d.resp_nticks,
-                                                        d.resp_nticks, d.resp_nticks, s));
+            fb.in[i] = pl->fine + (size_t)i * d.nticks;
+            fb.in2[i] = nullptr;
+            fb.out[i] = pl->X + (size_t)i * rows;
+            fb.nrows[i] = d.nwires;
+            ib.in[i] = pl->Racc + (size_t)i * slice;
+            ib.in2[i] = nullptr;
+            ib.out[i] = gR + (size_t)i * d.resp_nwires * d.resp_nticks;
+            ib.nrows[i] = d.resp_nwires;
         }
+        WS_LAUNCH(pl, K_FWD, s, ws::launch_fwd_rows_batch(pl->plan, pl->tw, fb, d.nticks, fine_stride, pl->fstride,
+                                                          pl->nfreq, 1.0f, s));
+        WS_CUDA(cudaMemsetAsync(pl->Racc, 0, sizeof(float2) * slice * I, s));
+        for (int i = 0; i < I; ++i)
+            WS_LAUNCH(pl, K_RGRAD, s, ws::launch_resp_grad(pl->Y, pl->X + (size_t)i * rows, pl->Racc + (size_t)i * slice,
+                                                           d.nwires, pl->nfreq, pl->fstride, d.resp_nwires,
+                                                           d.resp_wire_center, circ, 1.0f / (float)pl->plan.L, s));
+        WS_LAUNCH(pl, K_INV, s, ws::launch_inv_rows_batch(pl->plan, pl->tw, ib, pl->fstride, pl->nfreq, d.resp_nticks,
+                                                          d.resp_nticks, s));
     }
+    ws::ConvBatch cb;
+    cb.n = I;
     for (int i = 0; i < I; ++i) {
-        WS_LAUNCH(pl, K_WCONV, s, ws::launch_wire_conv(pl->X, pl->Y, pl->Radj + (size_t)i * slice, d.nwires,
-                                                       pl->nfreq, pl->fstride, d.resp_nwires,
-                                                       d.resp_nwires - 1 - d.resp_wire_center, circ, s, 0, pl->status));
-        WS_LAUNCH(pl, K_INV, s, ws::launch_inv_rows(pl->plan, pl->tw, pl->Y, d.nwires, pl->fstride, pl->nfreq,
-                                                    pl->fine + (size_t)i * d.nticks, d.nticks, fine_stride, s));
+        cb.X[i] = pl->Y;
+        cb.Y[i] = pl->X + (size_t)i * rows;
+        cb.Rt[i] = pl->Radj + (size_t)i * slice;
+        cb.nwires[i] = d.nwires;
+        ib.in[i] = pl->X + (size_t)i * rows;
+        ib.in2[i] = nullptr;
+        ib.out[i] = pl->fine + (size_t)i * d.nticks;
+        ib.nrows[i] = d.nwires;
     }
+    const int variant = (circ || !ws::tma_available()) ? 0 : 9;
+    WS_LAUNCH(pl, K_WCONV, s, ws::launch_wire_conv_batch(cb, pl->nfreq, pl->fstride, d.resp_nwires,
+                                                         d.resp_nwires - 1 - d.resp_wire_center, circ, s, variant,
+                                                         pl->status));
+    WS_LAUNCH(pl, K_INV, s, ws::launch_inv_rows_batch(pl->plan, pl->tw, ib, pl->fstride, pl->nfreq, d.nticks,
+                                                      fine_stride, s));
     if (gDL) WS_CUDA(cudaMemsetAsync(gDL, 0, sizeof(double), s));
     if (gDT) WS_CUDA(cudaMemsetAsync(gDT, 0, sizeof(double), s));
     WS_LAUNCH(pl, K_DGRAD, s, ws::launch_depo_grads(a, pl->fine, gq, gx, gt, gDL, gDT, params->DL_mm2_us,
