@@ -240,3 +240,20 @@ def test_batch_rejects_mixed_impact_counts(ws):
     events = [[ws.DeviceDepos.from_plane_depos(no_depos(40))] * 2]
     with pytest.raises(ws.WiresimError):
         ws.Batch(planes, events, ws.Params(), units_per_wave=2).run()
+
+
+def test_batch_with_the_most_impact_positions_takes_one_unit_per_launch(ws):
+    """32 sub-pitch positions: a launch of the impact wire convolution holds
+    the tensor maps of one unit only, so a wave of three units takes three
+    launches; the batch still equals per-unit calls."""
+    wires, nt, I = (16, 20, 24), 1000, 32
+    planes = [ws.Plane(nw, nt, inputs.impact_response("bipolar", impacts=I), plane_id=p) for p, nw in enumerate(wires)]
+    params = ws.Params(fluctuate=1, p_survive=0.7, seed=3, event_id=1)
+    events = [[ws.DeviceDepos.from_plane_depos(inputs.uniform_depos(150, nw, seed=10 * e + p, nticks=nt))
+               for p, nw in enumerate(wires)] for e in range(2)]
+    b = ws.Batch(planes, events, params, units_per_wave=3)
+    outs = [to_np(o) for o in b.run()]
+    for e in range(2):
+        for p, pl in enumerate(planes):
+            pe = ws.Params(**{**params.__dict__, "event_id": params.event_id + e})
+            assert rel(outs[e * 3 + p], to_np(pl.simulate(events[e][p], pe))) <= 1e-6, (e, p)
