@@ -101,9 +101,9 @@ typedef struct {
                                  raster bins the pitch axis at pitch/I into
                                  a fine grid of nwires*I rows (fine row
                                  w*I + i), and M = sum_i R_i (*) S_i.  FP32
-                                 only; ws_simulate, ws_simulate_batch (a
-                                 batch's planes share I) and the adjoint
-                                 take them                                  */
+                                 and FP32_COMP; ws_simulate,
+                                 ws_simulate_batch (a batch's planes share
+                                 I) and the adjoint take them               */
 } ws_plane_desc;
 
 /* Depos of one event as seen by one plane: structure of arrays of float32
@@ -154,9 +154,10 @@ typedef struct {
                                  (TwoSum) scatter-add and FP64 edge weights
                                  for axes narrower than 1/8 bin;
                                  WS_PREC_FP64: double throughout (needs a
-                                 plane created with fp64 != 0).  Only
-                                 ws_simulate honours it; the batch, patch
-                                 and adjoint entry points run FP32.         */
+                                 plane created with fp64 != 0; not on
+                                 impact planes).  Only ws_simulate honours
+                                 it; the batch, patch and adjoint entry
+                                 points run FP32.                           */
     uint32_t depo_offset;     /* index of depos[0] in the event's whole depo
                                  list: the random counters carry each
                                  depo's index in that list (depo_offset +
@@ -218,9 +219,9 @@ typedef struct ws_plane ws_plane;
  * spectrum, twiddles, two spectra of nwires x (L_t/2+1) complex64, status
  * word, scan scratch, noise spectra, a 64-bit row mark and a row class per
  * wire for ws_simulate's active rows; with impacts I > 1 also the fine grid
- * of nwires*I x nticks floats and I times the first spectrum, the
- * response spectrum, the adjoint's taps and the response gradient's
- * spectra).  Host-only; fails with WS_ERR_UNSUPPORTED_SIZE if the
+ * of nwires*I x nticks floats and I times the compensated path's low-part
+ * grid, the first spectrum, the response spectrum, the adjoint's taps and
+ * the response gradient's spectra).  Host-only; fails with WS_ERR_UNSUPPORTED_SIZE if the
  * FFT length is not 2/3/5-smooth or exceeds 14336, for FP64 buffers on an
  * impact plane, or for a grid (fine grid on an impact plane) of 2^31 cells
  * or more, and with WS_ERR_INVALID_ARG for impacts outside 0 .. 32. */

@@ -1421,8 +1421,10 @@ static cudaError_t launch_raster_units(const RasterUnits& U, const ws_patches& p
     const RasterArgs& a0 = U.a[0];
     const int rows = (a0.fluct && !a0.keep_all && a0.T != 0u) ? (a0.exact_max < kExactCap ? a0.exact_max : kExactCap) : 0;
     const size_t dyn = sizeof(float) * (size_t)rows * (rows + 1) / 2;
-    // a launch's units are all fine-pitch (impact) planes or none is
-    if constexpr (P == 0) {
+    // a launch's units are all fine-pitch (impact) planes or none is; the
+    // FP64 path's tables would not fit the wide variant's shared memory (its
+    // wide patches take the warp-per-depo kernel)
+    if constexpr (P <= 1) {
         if (a0.wide) return launch_raster_pair<MODE, P, kWideW>(U, p, L, rows, dyn, blocks, s);
     }
     return launch_raster_pair<MODE, P, kSmallW>(U, p, L, rows, dyn, blocks, s);

@@ -174,7 +174,7 @@ ws_status plan_layout(const ws_plane_desc* d, Layout* lay) {
     lay->off_large = o; o = align256(o + sizeof(long long) * (size_t)ws::kLargeListCap);
     lay->off_radj = o; o = align256(o + sizeof(float2) * (size_t)I * d->resp_nwires * lay->fstride);
     lay->off_racc = o; o = align256(o + sizeof(float2) * (size_t)I * d->resp_nwires * lay->fstride);
-    lay->off_grid2 = o; o = align256(o + sizeof(float) * (size_t)d->nwires * d->nticks);
+    lay->off_grid2 = o; o = align256(o + sizeof(float) * (size_t)I * d->nwires * d->nticks);
     lay->off_noise = o; o = align256(o + 2 * sizeof(float) * (size_t)lay->fstride);
     lay->off_rows = o; o = align256(o + sizeof(ws::mark_t) * (size_t)d->nwires);
     lay->off_cls = o; o = align256(o + sizeof(uint32_t) * (size_t)d->nwires);
@@ -473,11 +473,19 @@ ws_status simulate_marked(ws_plane* pl, ws::RasterArgs a, float* out, cudaStream
     return WS_OK;
 }
 
+// Eq. 2 on a grid (the fine grid of an impact plane), adding the plane's
+// noise term with noise_params; lo: the compensated grid's low parts (added
+// by the forward transform), or null.
 ws_status convolve_impl(ws_plane* pl, const float* grid, float* out, cudaStream_t s,
-                        const ws_params* noise_params = nullptr) {
+                        const ws_params* noise_params = nullptr, const float* lo = nullptr) {
     const ws_plane_desc& d = pl->desc;
-    WS_LAUNCH(pl, K_FWD, s, ws::launch_fwd_rows(pl->plan, pl->tw, grid, d.nwires * pl->impacts, d.nticks, d.nticks,
-                                                pl->X, pl->fstride, pl->nfreq, 1.0f, s, pl->status));
+    if (lo) {
+        WS_LAUNCH(pl, K_FWD, s, ws::launch_fwd_rows_comp(pl->plan, pl->tw, grid, lo, d.nwires * pl->impacts, d.nticks,
+                                                         d.nticks, pl->X, pl->fstride, pl->nfreq, s));
+    } else {
+        WS_LAUNCH(pl, K_FWD, s, ws::launch_fwd_rows(pl->plan, pl->tw, grid, d.nwires * pl->impacts, d.nticks,
+                                                    d.nticks, pl->X, pl->fstride, pl->nfreq, 1.0f, s, pl->status));
+    }
     if (pl->impacts > 1) {
         const ws_status st =
             impacts_wconv(pl, pl, plane_conv(pl, nullptr, nullptr), pl->sched, s, pl->wconv_variant);
@@ -836,11 +844,14 @@ ws_status ws_simulate(ws_plane* pl, const ws_depos* depos, const ws_params* para
     const size_t grid_bytes = sizeof(float) * (size_t)d.nwires * d.nticks;
     ws::RasterArgs a = raster_args(pl, depos, params);
     if (pl->impacts > 1) {
-        if (params->precision != WS_PREC_FP32) return WS_ERR_UNSUPPORTED_SIZE;
+        if (params->precision == WS_PREC_FP64) return WS_ERR_UNSUPPORTED_SIZE;
+        // compensated: the fine grid's low parts in grid2 (fine-sized on impact planes)
+        if (params->precision == WS_PREC_FP32_COMP) a.lo = pl->grid2;
         if (marks_apply(pl)) return simulate_marked(pl, a, out_dev, s);
         WS_LAUNCH(pl, K_MEMSET, s, cudaMemsetAsync(pl->fine, 0, grid_bytes * pl->impacts, s));
+        if (a.lo) WS_CUDA(cudaMemsetAsync(pl->grid2, 0, grid_bytes * pl->impacts, s));
         WS_LAUNCH(pl, K_RASTER_SCATTER, s, ws::launch_raster_scatter(a, pl->fine, pl->large, s));
-        return convolve_impl(pl, pl->fine, out_dev, s, params);
+        return convolve_impl(pl, pl->fine, out_dev, s, params, a.lo);
     }
     if (params->precision == WS_PREC_FP64) {
         if (!pl->fp64) return WS_ERR_WORKSPACE;

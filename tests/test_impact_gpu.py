@@ -99,8 +99,6 @@ def test_impact_planes_rejected_where_unsupported(ws):
         pl.simulate(d, ws.Params(precision=ws.WS_PREC_FP64))
     with pytest.raises(ws.WiresimError):
         pl.set_wire_conv_variant(4)      # impact planes: four tile shapes (0 .. 3)
-    with pytest.raises(ws.WiresimError):
-        pl.simulate(d, ws.Params(precision=ws.WS_PREC_FP32_COMP))
     import torch
     with pytest.raises(ws.WiresimError):  # the adjoint is of the expected-value path
         pl.backward(d, ws.Params(fluctuate=1), torch.zeros((16, 500), device="cuda"))

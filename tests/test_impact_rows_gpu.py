@@ -257,3 +257,23 @@ def test_batch_with_the_most_impact_positions_takes_one_unit_per_launch(ws):
         for p, pl in enumerate(planes):
             pe = ws.Params(**{**params.__dict__, "event_id": params.event_id + e})
             assert rel(outs[e * 3 + p], to_np(pl.simulate(events[e][p], pe))) <= 1e-6, (e, p)
+
+
+@pytest.mark.parametrize("bands,circular", [([(30, 42)], False), (None, False), (None, True)])
+def test_compensated_precision_on_impact_planes(ws, bands, circular):
+    """FP32_COMP on an impact plane (the fine grid's low parts kept beside
+    it and added by the forward transform), with active wires (a band), on
+    every wire, and in circular mode (every fine row transformed), against
+    the oracle and the FP32 path."""
+    R = inputs.impact_response("bipolar", impacts=I)
+    pl = ws.Plane(NW, NT, R, circular=circular)
+    d = band_depos(300, bands, seed=17) if bands else inputs.uniform_depos(3000, NW, seed=17, nticks=NT)
+    dd = ws.DeviceDepos.from_plane_depos(d)
+    comp = to_np(pl.simulate(dd, ws.Params(precision=ws.WS_PREC_FP32_COMP), out=nan_out()))
+    plain = to_np(pl.simulate(dd, ws.Params()))
+    ref = oracle.simulate_impacts(d.q, d.x_mm, d.t_us, NW, NT, R, CENTER, circular=circular)
+    assert np.isfinite(comp).all()
+    assert rel(comp, ref) <= 1e-5
+    assert rel(comp, plain) <= 1e-5
+    if bands:
+        assert (comp[far_rows(bands)] == 0).all()
