@@ -100,8 +100,8 @@ typedef struct {
                                  at [(w + i/I), (w + (i+1)/I)) pitches), the
                                  raster bins the pitch axis at pitch/I into
                                  a fine grid of nwires*I rows (fine row
-                                 w*I + i), and M = sum_i R_i (*) S_i.  FP32
-                                 and FP32_COMP; ws_simulate,
+                                 w*I + i), and M = sum_i R_i (*) S_i.
+                                 ws_simulate (every precision),
                                  ws_simulate_batch (a batch's planes share
                                  I) and the adjoint take them               */
 } ws_plane_desc;
@@ -154,10 +154,9 @@ typedef struct {
                                  (TwoSum) scatter-add and FP64 edge weights
                                  for axes narrower than 1/8 bin;
                                  WS_PREC_FP64: double throughout (needs a
-                                 plane created with fp64 != 0; not on
-                                 impact planes).  Only ws_simulate honours
-                                 it; the batch, patch and adjoint entry
-                                 points run FP32.                           */
+                                 plane created with fp64 != 0).  Only
+                                 ws_simulate honours it; the batch, patch
+                                 and adjoint entry points run FP32.         */
     uint32_t depo_offset;     /* index of depos[0] in the event's whole depo
                                  list: the random counters carry each
                                  depo's index in that list (depo_offset +
@@ -221,10 +220,11 @@ typedef struct ws_plane ws_plane;
  * wire for ws_simulate's active rows; with impacts I > 1 also the fine grid
  * of nwires*I x nticks floats and I times the compensated path's low-part
  * grid, the first spectrum, the response spectrum, the adjoint's taps and
- * the response gradient's spectra).  Host-only; fails with WS_ERR_UNSUPPORTED_SIZE if the
- * FFT length is not 2/3/5-smooth or exceeds 14336, for FP64 buffers on an
- * impact plane, or for a grid (fine grid on an impact plane) of 2^31 cells
- * or more, and with WS_ERR_INVALID_ARG for impacts outside 0 .. 32. */
+ * the response gradient's spectra, and with fp64 I times the double grid,
+ * first spectrum and response spectrum).  Host-only; fails with
+ * WS_ERR_UNSUPPORTED_SIZE if the FFT length is not 2/3/5-smooth or exceeds
+ * 14336, or for a grid (fine grid on an impact plane) of 2^31 cells or
+ * more, and with WS_ERR_INVALID_ARG for impacts outside 0 .. 32. */
 ws_status ws_plane_workspace_bytes(const ws_plane_desc* desc, size_t* bytes);
 
 /* Create a plane over a caller-owned device workspace (>= the size above,

@@ -1420,6 +1420,45 @@ cudaError_t launch_add_noise64(const NoiseBatch& nb, int nfreq, int L, int64_t s
     return add_noise_t<double2>(nb, nfreq, L, stride, s);
 }
 
+// The FP64 path of impact planes (a reference-precision path): a thread per
+// output (wire w, frequency k) sums the I x K_w complex products of
+// Y[w][k] = sum_i sum_r Rt[i kw + r][k] X[(w + c - r) I + i][k] straight
+// from global memory (coalesced over k; rows outside the wires are zero, or
+// wrap in circular mode).
+__global__ void wire_conv_impacts64_kernel(const double2* __restrict__ X, double2* __restrict__ Y,
+                                           const double2* __restrict__ Rt, int nwires, int impacts, int nfreq,
+                                           int64_t stride, int kw, int center, int circular) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    const int w = blockIdx.y;
+    if (k >= nfreq) return;
+    double re = 0.0, im = 0.0;
+    for (int r = 0; r < kw; ++r) {
+        int wi = w + center - r;
+        if (circular) {
+            wi %= nwires;
+            if (wi < 0) wi += nwires;
+        } else if (wi < 0 || wi >= nwires) {
+            continue;
+        }
+        for (int i = 0; i < impacts; ++i) {
+            const double2 t = Rt[((int64_t)i * kw + r) * stride + k];
+            const double2 x = X[((int64_t)wi * impacts + i) * stride + k];
+            re = fma(t.x, x.x, fma(-t.y, x.y, re));
+            im = fma(t.x, x.y, fma(t.y, x.x, im));
+        }
+    }
+    Y[(int64_t)w * stride + k] = make_double2(re, im);
+}
+
+cudaError_t launch_wire_conv_impacts64(const double2* X, double2* Y, const double2* Rt, int nwires, int impacts,
+                                       int nfreq, int64_t stride, int kw, int center, int circular, cudaStream_t s) {
+    if (nwires <= 0 || nfreq <= 0) return cudaSuccess;
+    if (nwires > 65535 || impacts < 1) return cudaErrorInvalidValue;
+    wire_conv_impacts64_kernel<<<dim3((nfreq + 127) / 128, nwires), 128, 0, s>>>(X, Y, Rt, nwires, impacts, nfreq,
+                                                                               stride, kw, center, circular);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_wire_conv64(const double2* X, double2* Y, const double2* Rt, int nwires, int nfreq, int64_t stride,
                                int kw, int center, int circular, cudaStream_t s) {
     if (nwires <= 0 || nfreq <= 0) return cudaSuccess;

@@ -144,7 +144,6 @@ ws_status plan_layout(const ws_plane_desc* d, Layout* lay) {
     if (d->resp_nwires > ws::kMaxRespWires) return WS_ERR_UNSUPPORTED_SIZE;
     if (d->impacts < 0 || d->impacts > ws::kMaxImpacts) return WS_ERR_INVALID_ARG;
     const int I = d->impacts > 1 ? d->impacts : 1;
-    if (I > 1 && d->fp64) return WS_ERR_UNSUPPORTED_SIZE;   // impact planes run FP32
     if ((int64_t)I * d->nwires * d->nticks > (int64_t)INT32_MAX) return WS_ERR_UNSUPPORTED_SIZE;   // 32-bit bin index
     lay->impacts = I;
     int L;
@@ -183,10 +182,10 @@ ws_status plan_layout(const ws_plane_desc* d, Layout* lay) {
     lay->off_tw64 = lay->off_rt64 = lay->off_x64 = lay->off_y64 = lay->off_g64 = 0;
     if (d->fp64) {
         lay->off_tw64 = o; o = align256(o + sizeof(double2) * (size_t)L);
-        lay->off_rt64 = o; o = align256(o + sizeof(double2) * (size_t)d->resp_nwires * lay->fstride);
-        lay->off_x64 = o; o = align256(o + sizeof(double2) * (size_t)d->nwires * lay->fstride);
+        lay->off_rt64 = o; o = align256(o + sizeof(double2) * (size_t)I * d->resp_nwires * lay->fstride);
+        lay->off_x64 = o; o = align256(o + sizeof(double2) * (size_t)I * d->nwires * lay->fstride);
         lay->off_y64 = o; o = align256(o + sizeof(double2) * (size_t)d->nwires * lay->fstride);
-        lay->off_g64 = o; o = align256(o + sizeof(double) * (size_t)d->nwires * d->nticks);
+        lay->off_g64 = o; o = align256(o + sizeof(double) * (size_t)I * d->nwires * d->nticks);
     }
     lay->total = o;
     return WS_OK;
@@ -613,7 +612,8 @@ ws_status ws_plane_create(const ws_plane_desc* desc, const float* response_dev, 
                                   lay.fstride, lay.nfreq, s);
     if (e == cudaSuccess && pl->fp64) e = ws::launch_twiddles64(pl->tw64, lay.plan, s);
     if (e == cudaSuccess && pl->fp64)
-        e = ws::launch_fwd_rows64(lay.plan, pl->tw64, response_dev, false, desc->resp_nwires, desc->resp_nticks,
+        e = ws::launch_fwd_rows64(lay.plan, pl->tw64, response_dev, false, lay.impacts * desc->resp_nwires,
+                                  desc->resp_nticks,
                                   desc->resp_nticks, pl->Rt64, lay.fstride, lay.nfreq, 1.0f / (float)lay.plan.L, s);
     // Autotune the wire convolution on this plane's own buffers: every
     // variant once to warm up, then three rounds over all variants of three
@@ -843,8 +843,25 @@ ws_status ws_simulate(ws_plane* pl, const ws_depos* depos, const ws_params* para
     const ws_plane_desc& d = pl->desc;
     const size_t grid_bytes = sizeof(float) * (size_t)d.nwires * d.nticks;
     ws::RasterArgs a = raster_args(pl, depos, params);
+    if (pl->impacts > 1 && params->precision == WS_PREC_FP64) {
+        // FP64 on the fine grid: double grid, transforms and impact sum
+        if (!pl->fp64) return WS_ERR_WORKSPACE;
+        const int I = pl->impacts;
+        WS_LAUNCH(pl, K_MEMSET, s, cudaMemsetAsync(pl->g64, 0, 2 * grid_bytes * I, s));
+        a.grid64 = pl->g64;
+        WS_LAUNCH(pl, K_RASTER_SCATTER, s, ws::launch_raster_scatter(a, out_dev, pl->large, s));
+        WS_LAUNCH(pl, K_FWD, s, ws::launch_fwd_rows64(pl->plan, pl->tw64, pl->g64, true, d.nwires * I, d.nticks,
+                                                      d.nticks, pl->X64, pl->fstride, pl->nfreq, 1.0f, s));
+        WS_LAUNCH(pl, K_WCONV, s, ws::launch_wire_conv_impacts64(pl->X64, pl->Y64, pl->Rt64, d.nwires, I, pl->nfreq,
+                                                                 pl->fstride, d.resp_nwires, d.resp_wire_center,
+                                                                 d.conv_mode == WS_CONV_CIRCULAR, s));
+        st = add_plane_noise(pl, params, pl->Y64, true, s);
+        if (st != WS_OK) return st;
+        WS_LAUNCH(pl, K_INV, s, ws::launch_inv_rows64(pl->plan, pl->tw64, pl->Y64, d.nwires, pl->fstride, pl->nfreq,
+                                                      out_dev, d.nticks, d.nticks, s));
+        return WS_OK;
+    }
     if (pl->impacts > 1) {
-        if (params->precision == WS_PREC_FP64) return WS_ERR_UNSUPPORTED_SIZE;
         // compensated: the fine grid's low parts in grid2 (fine-sized on impact planes)
         if (params->precision == WS_PREC_FP32_COMP) a.lo = pl->grid2;
         if (marks_apply(pl)) return simulate_marked(pl, a, out_dev, s);
@@ -926,7 +943,8 @@ ws_status ws_plane_set_response(ws_plane* pl, const float* response_dev, void* s
                                       pl->Radj + (size_t)i * d.resp_nwires * pl->fstride, d.resp_nwires,
                                       pl->fstride, pl->nfreq, s));
     if (pl->fp64)
-        WS_CUDA(ws::launch_fwd_rows64(pl->plan, pl->tw64, response_dev, false, d.resp_nwires, d.resp_nticks,
+        WS_CUDA(ws::launch_fwd_rows64(pl->plan, pl->tw64, response_dev, false, pl->impacts * d.resp_nwires,
+                                      d.resp_nticks,
                                       d.resp_nticks, pl->Rt64, pl->fstride, pl->nfreq, 1.0f / (float)pl->plan.L, s));
     return WS_OK;
 }

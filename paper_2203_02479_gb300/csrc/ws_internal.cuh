@@ -296,6 +296,10 @@ cudaError_t launch_inv_rows64(const FftPlan& plan, const double2* tw, const doub
                               int nfreq, float* out, int ncols, int64_t out_stride, cudaStream_t s);
 cudaError_t launch_wire_conv64(const double2* X, double2* Y, const double2* Rt, int nwires, int nfreq, int64_t stride,
                                int kw, int center, int circular, cudaStream_t s);
+// FP64 wire convolution over sub-pitch impact positions (X: nwires*impacts
+// fine rows; Y[w][k] = sum_i sum_r Rt[i*kw + r][k] X[(w + center - r)*impacts + i][k]).
+cudaError_t launch_wire_conv_impacts64(const double2* X, double2* Y, const double2* Rt, int nwires, int impacts,
+                                       int nfreq, int64_t stride, int kw, int center, int circular, cudaStream_t s);
 // Compensated input: rows are hi + lo (two float grids).
 cudaError_t launch_fwd_rows_comp(const FftPlan& plan, const float2* tw, const float* hi, const float* lo, int nrows,
                                  int ncols, int64_t in_stride, float2* out, int64_t out_stride, int nfreq,

@@ -87,15 +87,20 @@ def test_impact_planes_in_the_planner(lib):
     """Impact planes: the fine grid (nwires*I x nticks floats), I times the
     compensated path's low-part grid, and I times the first spectra, the
     response spectra, the adjoint's taps and the response gradient's
-    spectra; more than 32 positions and FP64 buffers with impacts are
-    refused before any device work."""
+    spectra; with FP64 buffers also I times their double grid, first
+    spectra and response spectra; more than 32 positions are refused before
+    any device work."""
     from paper_2203_02479_gb300 import wiresim
     plain = wiresim.ws_plane_workspace_bytes(_desc())
     imp = wiresim.ws_plane_workspace_bytes(_desc(impacts=10))
     extra = 2 * 960 * 10 * 6000 * 4 - 960 * 6000 * 4 + 9 * 960 * 3136 * 8 + 3 * 9 * 21 * 3136 * 8
     assert extra <= imp - plain < extra + 1024 * 1024
     assert wiresim.ws_plane_workspace_bytes(_desc(impacts=1)) == plain
-    for kw, code in ((dict(impacts=33), 1), (dict(impacts=-1), 1), (dict(impacts=4, fp64=1), 2)):
+    plain64 = wiresim.ws_plane_workspace_bytes(_desc(fp64=1))
+    imp64 = wiresim.ws_plane_workspace_bytes(_desc(impacts=10, fp64=1))
+    extra64 = 9 * 960 * 6000 * 8 + 9 * 960 * 3136 * 16 + 9 * 21 * 3136 * 16
+    assert extra + extra64 <= imp64 - plain64 < extra + extra64 + 2 * 1024 * 1024
+    for kw, code in ((dict(impacts=33), 1), (dict(impacts=-1), 1)):
         with pytest.raises(wiresim.WiresimError) as ei:
             wiresim.ws_plane_workspace_bytes(_desc(**kw))
         assert ei.value.status == code

@@ -277,3 +277,22 @@ def test_compensated_precision_on_impact_planes(ws, bands, circular):
     assert rel(comp, plain) <= 1e-5
     if bands:
         assert (comp[far_rows(bands)] == 0).all()
+
+
+@pytest.mark.parametrize("circular,fluct", [(False, 0), (True, 0), (False, 1)])
+def test_fp64_precision_on_impact_planes(ws, circular, fluct):
+    """WS_PREC_FP64 on an impact plane (double fine grid, transforms and
+    impact sum): the oracle's waveform up to the float output's rounding
+    (binomial mode: the same counts, the oracle's random stream)."""
+    nw = 60
+    R = inputs.impact_response("unipolar", impacts=I)
+    pl = ws.Plane(nw, NT, R, circular=circular, fp64=True, plane_id=1)
+    d = inputs.uniform_depos(800, nw, seed=23, nticks=NT)
+    params = ws.Params(precision=ws.WS_PREC_FP64, fluctuate=fluct, p_survive=0.7 if fluct else 1.0, seed=8,
+                       event_id=2)
+    got = to_np(pl.simulate(ws.DeviceDepos.from_plane_depos(d), params, out=nan_out(nw)))
+    ref = oracle.simulate_impacts(d.q, d.x_mm, d.t_us, nw, NT, R, CENTER, circular=circular, fluctuate=fluct,
+                                  p=0.7 if fluct else 1.0, seed=8, event_id=2, plane_id=1)
+    assert np.isfinite(got).all()
+    assert rel(got, ref) <= 1e-7
+    assert pl.status() == 0
