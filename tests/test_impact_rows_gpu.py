@@ -296,3 +296,38 @@ def test_fp64_precision_on_impact_planes(ws, circular, fluct):
     assert np.isfinite(got).all()
     assert rel(got, ref) <= 1e-7
     assert pl.status() == 0
+
+
+def test_noise_on_an_impact_plane_matches_oracle(ws):
+    """Eq. 1's noise term on an impact plane (every row live, so the
+    unmarked route): the impact simulation plus the oracle's noise."""
+    R = inputs.impact_response("bipolar", impacts=I)
+    pl = ws.Plane(NW, NT, R, plane_id=3)
+    L = pl.info.fft_len_tick
+    amp = inputs.noise_amplitudes(L, peak=2.0e4)
+    coh = inputs.noise_amplitudes(L, "coherent", peak=2.0e4)
+    pl.set_noise(amp, coh, 16)
+    d = band_depos(300, [(40, 60)], seed=29)
+    got = to_np(pl.simulate(ws.DeviceDepos.from_plane_depos(d), ws.Params(seed=12, event_id=6), out=nan_out()))
+    ref = oracle.simulate_impacts(d.q, d.x_mm, d.t_us, NW, NT, R, CENTER) + \
+        oracle.noise(NW, NT, L, amp, coh, 16, seed=12, event_id=6, plane_id=3)
+    assert np.isfinite(got).all()
+    assert rel(got, ref) <= 1e-5
+
+
+def test_given_widths_on_an_impact_plane(ws):
+    """Depos with their own widths (sigma_t, sigma_x given, no diffusion) on
+    an impact plane with active wires: marks from the given pitch widths at
+    pitch / I, against the oracle."""
+    R = inputs.impact_response("unipolar", impacts=I)
+    pl = ws.Plane(NW, NT, R)
+    d = band_depos(200, [(20, 35), (90, 100)], seed=31)
+    rng = np.random.Generator(np.random.PCG64(31))
+    st = rng.uniform(0.2, 3.0, len(d.q)).astype(np.float32)
+    sx = rng.uniform(0.05, 2.5, len(d.q)).astype(np.float32)
+    dd = ws.DeviceDepos(d.q, d.x_mm, d.t_us, sigma_t_us=st, sigma_x_mm=sx)
+    got = to_np(pl.simulate(dd, ws.Params(), out=nan_out()))
+    ref = oracle.simulate_impacts(d.q, d.x_mm, d.t_us, NW, NT, R, CENTER, sig_t_us=st, sig_x_mm=sx)
+    assert np.isfinite(got).all()
+    assert rel(got, ref) <= 1e-5
+    assert (got[far_rows([(20, 35), (90, 100)])] == 0).all()
